@@ -1,0 +1,354 @@
+"""Plain FP64 CPU oracle for the LCS flow-map / FTLE hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  The library under
+``paper_2209_13775_gb300`` never imports it, and it never imports the library:
+the two share no code.  Inputs reach both sides from
+``paper_2209_13775_gb300.inputs`` (seeded generators, none of the method's
+arithmetic).
+
+The C part (``lcs_oracle.c``) is the literal FP64 definition of each step of the
+paper's path (arXiv 2209.13775): the linear-in-time, (bi/tri)linear-in-space
+Interpolator and the Seed, Flow Map and Cauchy-Green filters of Sec. 2, Eq. 1 and
+Eq. 2, and the local tetrahedral cell search of Sec. 3.1.  This module only
+marshals numpy arrays into it.  ``oracle.mlp`` holds the FP64 network oracle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lcs_oracle.c")
+_HDR = os.path.join(_HERE, "lcs_oracle.h")
+_SO = os.path.join(_HERE, "liblcs_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, LEFT, OUTSIDE, MAXSTEPS = 0, 1, 2, 3
+AN_GYRE, AN_ABC, AN_AFFINE, AN_PIPE = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile ``lcs_oracle.c`` into ``liblcs_oracle.so`` (gcc, FP64, no FMA contraction)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+        return _SO
+    tmp = _SO + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
+           "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Rect(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("origin", ctypes.c_double * 3), ("spacing", ctypes.c_double * 3),
+                ("periodic", ctypes.c_int * 3), ("nframes", ctypes.c_int),
+                ("times", ctypes.c_void_p), ("time_periodic", ctypes.c_int),
+                ("period", ctypes.c_double), ("frames", ctypes.c_void_p)]
+
+
+class _Tet(ctypes.Structure):
+    _fields_ = [("nnodes", ctypes.c_longlong), ("ncells", ctypes.c_longlong),
+                ("xyz", ctypes.c_void_p), ("tets", ctypes.c_void_p), ("nbrs", ctypes.c_void_p),
+                ("nframes", ctypes.c_int), ("times", ctypes.c_void_p),
+                ("time_periodic", ctypes.c_int), ("period", ctypes.c_double),
+                ("frames", ctypes.c_void_p), ("walk_limit", ctypes.c_int)]
+
+
+class _Analytic(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dim", ctypes.c_int), ("p", ctypes.c_double * 24)]
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            P, I, LL, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+            L.ora_time_locate.argtypes = [P, I, I, D, D, P, P]
+            L.ora_rect_velocity.argtypes = [P, P, D, P]
+            L.ora_analytic_velocity.argtypes = [P, P, D, P]
+            L.ora_tet_velocity.argtypes = [P, P, D, P, P]
+            L.ora_seed_grid.argtypes = [I, P, P, P, P, P]
+            L.ora_rk4.argtypes = [I, P, I, LL, P, P, D, D, D, P, P, P]
+            L.ora_rk4.restype = LL
+            L.ora_dp45.argtypes = [I, P, I, LL, P, P, D, D, D, D, D, LL, I, I, P, P, P, P]
+            L.ora_dp45.restype = LL
+            L.ora_flowmap_gradient.argtypes = [I, P, P, P, P, P, P, P]
+            L.ora_cauchy_green.argtypes = [I, LL, P, P]
+            L.ora_eig_sym.argtypes = [I, P, P]
+            L.ora_ftle.argtypes = [I, LL, P, D, P, P]
+            L.ora_orient3d_exact.argtypes = [P, P, P, P]
+            L.ora_tet_contains.argtypes = [P, LL, P, P]
+            L.ora_tet_locate_brute.argtypes = [P, P]
+            L.ora_tet_locate_brute.restype = LL
+            L.ora_tet_locate_walk.argtypes = [P, LL, P]
+            L.ora_tet_locate_walk.restype = LL
+            L.ora_set_threads.argtypes = [I]
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads used over seeds (<=0 keeps the default); returns the count in effect."""
+    return int(lib().ora_set_threads(int(n)))
+
+
+# ----------------------------------------------------------------- fields
+
+class RectField:
+    """Rectilinear frames [nframes][nz][ny][nx][dim] FP32 (Sec. 2 Interpolator)."""
+
+    kind = 0
+
+    def __init__(self, frames, times, origin, spacing, periodic=(0, 0, 0),
+                 time_periodic=False, period=0.0):
+        self.frames = np.ascontiguousarray(frames, dtype=np.float32)
+        self.dim = int(self.frames.shape[-1])
+        grid = self.frames.shape[1:-1][::-1]          # (nx, ny[, nz])
+        self.n = list(grid) + [1] * (3 - len(grid))
+        self.times = np.ascontiguousarray(times, dtype=np.float64)
+        s = _Rect()
+        s.dim = self.dim
+        for a in range(3):
+            s.n[a] = int(self.n[a])
+            s.origin[a] = float(origin[a]) if a < len(origin) else 0.0
+            s.spacing[a] = float(spacing[a]) if a < len(spacing) else 1.0
+            s.periodic[a] = int(periodic[a]) if a < len(periodic) else 0
+        s.nframes = int(self.frames.shape[0])
+        s.times = self.times.ctypes.data
+        s.time_periodic = int(bool(time_periodic))
+        s.period = float(period)
+        s.frames = self.frames.ctypes.data
+        self.struct = s
+
+    def velocity(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        u = np.zeros(self.dim)
+        lib().ora_rect_velocity(ctypes.byref(self.struct), _p(x), float(t), _p(u))
+        return u
+
+
+class AnalyticField:
+    """Analytic velocity (pins only): gyre, ABC, affine, pipe."""
+
+    kind = 1
+
+    def __init__(self, kind: int, dim: int, params):
+        s = _Analytic()
+        s.kind, s.dim = int(kind), int(dim)
+        for i, v in enumerate(params):
+            s.p[i] = float(v)
+        self.dim = dim
+        self.struct = s
+
+    def velocity(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        u = np.zeros(self.dim)
+        lib().ora_analytic_velocity(ctypes.byref(self.struct), _p(x), float(t), _p(u))
+        return u
+
+
+def gyre(A=0.1, eps=0.25, omega=2 * np.pi / 10):
+    return AnalyticField(AN_GYRE, 2, [A, eps, omega])
+
+
+def abc(A=np.sqrt(3.0), B=np.sqrt(2.0), C=1.0, mod=0.5):
+    return AnalyticField(AN_ABC, 3, [A, B, C, mod])
+
+
+def affine(A0, A1=None, b0=None, b1=None):
+    A0 = np.asarray(A0, dtype=np.float64)
+    d = A0.shape[0]
+    p = np.zeros(24)
+    M0 = np.zeros((3, 3)); M0[:d, :d] = A0
+    M1 = np.zeros((3, 3))
+    if A1 is not None:
+        M1[:d, :d] = np.asarray(A1, dtype=np.float64)
+    p[0:9] = M0.ravel(); p[9:18] = M1.ravel()
+    if b0 is not None:
+        p[18:18 + d] = b0
+    if b1 is not None:
+        p[21:21 + d] = b1
+    return AnalyticField(AN_AFFINE, d, p)
+
+
+def pipe(R=1.0, L=10.0, amp=0.05, phases=(0.0, 0.0, 0.0, 0.0)):
+    return AnalyticField(AN_PIPE, 3, [R, L, amp] + list(phases))
+
+
+class TetField:
+    """Tetrahedral mesh with nodal frames [nframes][nnodes][3] FP32 (Sec. 3.1)."""
+
+    kind = 2
+    dim = 3
+
+    def __init__(self, xyz, tets, nbrs, frames, times, time_periodic=False, period=0.0,
+                 walk_limit=100000):
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+        self.tets = np.ascontiguousarray(tets, dtype=np.int32)
+        self.nbrs = np.ascontiguousarray(nbrs, dtype=np.int32)
+        self.frames = np.ascontiguousarray(frames, dtype=np.float32)
+        self.times = np.ascontiguousarray(times, dtype=np.float64)
+        s = _Tet()
+        s.nnodes = self.xyz.shape[0]
+        s.ncells = self.tets.shape[0]
+        s.xyz = self.xyz.ctypes.data
+        s.tets = self.tets.ctypes.data
+        s.nbrs = self.nbrs.ctypes.data
+        s.nframes = int(self.frames.shape[0])
+        s.times = self.times.ctypes.data
+        s.time_periodic = int(bool(time_periodic))
+        s.period = float(period)
+        s.frames = self.frames.ctypes.data
+        s.walk_limit = int(walk_limit)
+        self.struct = s
+
+    def velocity(self, x, t, cell=0):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        u = np.zeros(3)
+        c = ctypes.c_int(int(cell))
+        out = lib().ora_tet_velocity(ctypes.byref(self.struct), _p(x), float(t), ctypes.byref(c), _p(u))
+        return (None if out else u), c.value
+
+    def contains(self, t, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        onb = ctypes.c_int(0)
+        r = lib().ora_tet_contains(ctypes.byref(self.struct), int(t), _p(p), ctypes.byref(onb))
+        return bool(r), bool(onb.value)
+
+    def locate_brute(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        return int(lib().ora_tet_locate_brute(ctypes.byref(self.struct), _p(p)))
+
+    def locate_walk(self, p, start=0):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        return int(lib().ora_tet_locate_walk(ctypes.byref(self.struct), int(start), _p(p)))
+
+    def locate_seeds(self, seeds_soa):
+        """Exact cell of every FP32 seed (-1 outside), walking from the previous seed's cell."""
+        s = np.ascontiguousarray(np.asarray(seeds_soa, dtype=np.float32).T)
+        out = np.empty(s.shape[0], dtype=np.int32)
+        start = 0
+        for i in range(s.shape[0]):
+            c = self.locate_walk(s[i], start)
+            out[i] = c
+            if c >= 0:
+                start = c
+        return out
+
+
+def time_locate(times, t, time_periodic=False, period=0.0):
+    times = np.ascontiguousarray(times, dtype=np.float64)
+    k = ctypes.c_int(0)
+    a = ctypes.c_double(0.0)
+    lib().ora_time_locate(_p(times), len(times), int(bool(time_periodic)), float(period), float(t),
+                          ctypes.byref(k), ctypes.byref(a))
+    return k.value, a.value
+
+
+def orient3d(a, b, c, d) -> int:
+    arr = [np.ascontiguousarray(v, dtype=np.float32) for v in (a, b, c, d)]
+    return int(lib().ora_orient3d_exact(*[_p(v) for v in arr]))
+
+
+# ------------------------------------------------------------ path steps
+
+def seed_grid(dim, n, lo, hi, endpoint=(1, 1, 1)):
+    """FP32 seed lattice [dim][N] (Sec. 2 Seed)."""
+    nn = np.zeros(3, dtype=np.int32); nn[:dim] = n[:dim]
+    if dim == 2:
+        nn[2] = 1
+    l3 = np.zeros(3); l3[:dim] = lo[:dim]
+    h3 = np.zeros(3); h3[:dim] = hi[:dim]
+    e3 = np.ones(3, dtype=np.int32); e3[:dim] = endpoint[:dim]
+    N = int(np.prod(nn[:dim]))
+    out = np.empty((dim, N), dtype=np.float32)
+    lib().ora_seed_grid(dim, _p(nn), _p(l3), _p(h3), _p(e3), _p(out))
+    return out
+
+
+def lattice_spacing(dim, n, lo, hi, endpoint=(1, 1, 1)):
+    return np.array([(hi[a] - lo[a]) / ((n[a] - 1) if endpoint[a] else n[a]) for a in range(dim)])
+
+
+def rk4(field, x0, t0, T, dt, cells=None):
+    """Fixed-step RK4 flow map (Sec. 2 Flow Map, Sec. 3.1).  x0 [dim][N] -> (xT, status, t_exit)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    dim, n = x0.shape
+    xT = np.empty_like(x0)
+    st = np.empty(n, dtype=np.uint8)
+    te = np.empty(n, dtype=np.float64)
+    c = None if cells is None else np.ascontiguousarray(cells, dtype=np.int32)
+    lib().ora_rk4(field.kind, ctypes.byref(field.struct), dim, n, _p(x0),
+                  None if c is None else _p(c), float(t0), float(T), float(dt),
+                  _p(xT), _p(st), _p(te))
+    return xT, st, te
+
+
+def dp45(field, x0, t0, T, h0=0.01, rtol=1e-6, atol=1e-6, max_steps=1000000, group=1,
+         adaptive=True, cells=None):
+    """Dormand-Prince 5(4), per-tracer (group=1) or 32-lane shared step (group=32)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    dim, n = x0.shape
+    xT = np.empty_like(x0)
+    st = np.empty(n, dtype=np.uint8)
+    te = np.empty(n, dtype=np.float64)
+    ns = np.empty(n, dtype=np.int64)
+    c = None if cells is None else np.ascontiguousarray(cells, dtype=np.int32)
+    lib().ora_dp45(field.kind, ctypes.byref(field.struct), dim, n, _p(x0),
+                   None if c is None else _p(c), float(t0), float(T), float(h0), float(rtol),
+                   float(atol), int(max_steps), int(group), int(bool(adaptive)),
+                   _p(xT), _p(st), _p(te), _p(ns))
+    return xT, st, te, ns
+
+
+def flowmap_gradient(dim, n, h, periodic, period, xT, status):
+    """grad F [N][dim][dim] by lattice finite differences (Sec. 2 Cauchy-Green)."""
+    xT = np.ascontiguousarray(xT, dtype=np.float64)
+    N = xT.shape[1]
+    nn = np.ones(3, dtype=np.int32); nn[:dim] = n[:dim]
+    h3 = np.ones(3); h3[:dim] = h[:dim]
+    p3 = np.zeros(3, dtype=np.int32); p3[:dim] = periodic[:dim]
+    L3 = np.zeros(3); L3[:dim] = period[:dim]
+    st = np.ascontiguousarray(status, dtype=np.uint8)
+    grad = np.empty((N, dim, dim))
+    lib().ora_flowmap_gradient(dim, _p(nn), _p(h3), _p(p3), _p(L3), _p(xT), _p(st), _p(grad))
+    return grad
+
+
+def cauchy_green(grad):
+    """Eq. 1 packed: 2D (C00, C01, C11), 3D (C00, C01, C02, C11, C12, C22)."""
+    grad = np.ascontiguousarray(grad, dtype=np.float64)
+    N, dim, _ = grad.shape
+    C = np.empty((N, 3 if dim == 2 else 6))
+    lib().ora_cauchy_green(dim, N, _p(grad), _p(C))
+    return C
+
+
+def eig_sym(Cp, dim):
+    Cp = np.ascontiguousarray(Cp, dtype=np.float64)
+    e = np.empty(dim)
+    lib().ora_eig_sym(dim, _p(Cp), _p(e))
+    return e
+
+
+def ftle(C, dim, T):
+    """lambda_max of C and sigma = ln(sqrt(lambda_max)) / |T|."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    N = C.shape[0]
+    lam = np.empty(N)
+    sig = np.empty(N)
+    lib().ora_ftle(dim, N, _p(C), float(T), _p(lam), _p(sig))
+    return lam, sig

@@ -1,0 +1,892 @@
+/*
+ * lcs_oracle.c -- plain FP64 CPU oracle for the LCS flow-map / FTLE hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark, never by the library.  It is the slow,
+ * literal statement of what the GPU path computes, written from the paper
+ * (Ameli, Desai, Shadden, arXiv 2209.13775) and the textbook definitions it
+ * names.  Every routine follows the paper's order of operations; nothing is
+ * blocked, fused or reordered.  Compiled with -ffp-contract=off.
+ *
+ * Parity status of each part is pinned by tests/test_oracle_*.py.
+ */
+#include "lcs_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORA_PI 3.14159265358979323846
+
+int ora_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* ====================================================================
+ * Time bracket (Sec. 2 "Interpolator": a window of two frames, linear in
+ * time between them).
+ * ==================================================================== */
+void ora_time_locate(const double *times, int nframes, int time_periodic,
+                     double period, double t, int *k, double *alpha)
+{
+    double tt = t;
+    if (nframes <= 1) {
+        *k = 0;
+        *alpha = 0.0;
+        return;
+    }
+    if (time_periodic) tt = t - period * floor((t - times[0]) / period);
+    int kk = 0;
+    for (int i = 0; i < nframes; ++i)
+        if (times[i] <= tt) kk = i;
+    if (kk > nframes - 2) kk = nframes - 2;
+    double a = (tt - times[kk]) / (times[kk + 1] - times[kk]);
+    if (!time_periodic) {
+        if (a < 0.0) a = 0.0;
+        if (a > 1.0) a = 1.0;
+    }
+    *k = kk;
+    *alpha = a;
+}
+
+/* ====================================================================
+ * Rectilinear interpolation: bilinear (2D) / trilinear (3D) in space,
+ * u = (1 - alpha) I[u_k](x) + alpha I[u_{k+1}](x) in time (Sec. 2).
+ * ==================================================================== */
+
+/* Cell along one axis.  Non-periodic: clamp x into the box, cell i with
+ * node_i <= x < node_{i+1}, last cell closed.  Periodic: wrap the index.   */
+static void axis_cell(double x, double o, double h, int n, int periodic,
+                      int *i0, int *i1, double *frac)
+{
+    if (periodic) {
+        double s = (x - o) / h;
+        double fl = floor(s);
+        long long i = (long long)fl;
+        long long m = i % n;
+        if (m < 0) m += n;
+        *i0 = (int)m;
+        *i1 = (int)((m + 1) % n);
+        *frac = s - fl;
+    } else {
+        double hi = o + (double)(n - 1) * h;
+        double xc = x;
+        if (xc < o) xc = o;
+        if (xc > hi) xc = hi;
+        double s = (xc - o) / h;
+        int i = (int)floor(s);
+        if (i > n - 2) i = n - 2;
+        if (i < 0) i = 0;
+        *i0 = i;
+        *i1 = i + 1;
+        *frac = s - (double)i;
+    }
+}
+
+static double rect_node(const ora_rect_field *f, int frame, int i, int j, int k, int c)
+{
+    long long node = (long long)i + (long long)f->n[0] * ((long long)j + (long long)f->n[1] * (long long)k);
+    long long nn = (long long)f->n[0] * f->n[1] * (f->dim == 3 ? f->n[2] : 1);
+    return (double)f->frames[((long long)frame * nn + node) * f->dim + c];
+}
+
+/* spatial interpolation of one frame */
+static void rect_frame_interp(const ora_rect_field *f, int frame, const double *x, double *u)
+{
+    int i0, i1, j0, j1, k0 = 0, k1 = 0;
+    double fx, fy, fz = 0.0;
+    axis_cell(x[0], f->origin[0], f->spacing[0], f->n[0], f->periodic[0], &i0, &i1, &fx);
+    axis_cell(x[1], f->origin[1], f->spacing[1], f->n[1], f->periodic[1], &j0, &j1, &fy);
+    if (f->dim == 3)
+        axis_cell(x[2], f->origin[2], f->spacing[2], f->n[2], f->periodic[2], &k0, &k1, &fz);
+    for (int c = 0; c < f->dim; ++c) {
+        if (f->dim == 2) {
+            u[c] = (1.0 - fx) * (1.0 - fy) * rect_node(f, frame, i0, j0, 0, c)
+                 + fx * (1.0 - fy) * rect_node(f, frame, i1, j0, 0, c)
+                 + (1.0 - fx) * fy * rect_node(f, frame, i0, j1, 0, c)
+                 + fx * fy * rect_node(f, frame, i1, j1, 0, c);
+        } else {
+            u[c] = (1.0 - fx) * (1.0 - fy) * (1.0 - fz) * rect_node(f, frame, i0, j0, k0, c)
+                 + fx * (1.0 - fy) * (1.0 - fz) * rect_node(f, frame, i1, j0, k0, c)
+                 + (1.0 - fx) * fy * (1.0 - fz) * rect_node(f, frame, i0, j1, k0, c)
+                 + fx * fy * (1.0 - fz) * rect_node(f, frame, i1, j1, k0, c)
+                 + (1.0 - fx) * (1.0 - fy) * fz * rect_node(f, frame, i0, j0, k1, c)
+                 + fx * (1.0 - fy) * fz * rect_node(f, frame, i1, j0, k1, c)
+                 + (1.0 - fx) * fy * fz * rect_node(f, frame, i0, j1, k1, c)
+                 + fx * fy * fz * rect_node(f, frame, i1, j1, k1, c);
+        }
+    }
+}
+
+int ora_rect_velocity(const ora_rect_field *f, const double *x, double t, double *u)
+{
+    int k;
+    double a;
+    double ua[3], ub[3];
+    ora_time_locate(f->times, f->nframes, f->time_periodic, f->period, t, &k, &a);
+    int k1 = (f->nframes > 1) ? k + 1 : k;
+    rect_frame_interp(f, k, x, ua);
+    rect_frame_interp(f, k1, x, ub);
+    for (int c = 0; c < f->dim; ++c) u[c] = (1.0 - a) * ua[c] + a * ub[c];
+    return 0;
+}
+
+/* rectilinear tracer has left: more than one cell outside a non-periodic axis */
+static int rect_left(const ora_rect_field *f, const double *x)
+{
+    for (int a = 0; a < f->dim; ++a) {
+        if (f->periodic[a]) continue;
+        double lo = f->origin[a] - f->spacing[a];
+        double hi = f->origin[a] + (double)f->n[a] * f->spacing[a];
+        if (x[a] < lo || x[a] > hi) return 1;
+    }
+    return 0;
+}
+
+/* ====================================================================
+ * Analytic fields (pins only).
+ * Double gyre: Shadden, Lekien, Marsden 2005 (the paper's 2D Cartesian case,
+ * Sec. 3.2).  ABC: Arnold-Beltrami-Childress flow with a time-modulated A.
+ * Pipe: Poiseuille profile with pulsatile amplitude plus an azimuthal swirl.
+ * ==================================================================== */
+int ora_analytic_velocity(const ora_analytic_field *f, const double *x, double t, double *u)
+{
+    const double *p = f->p;
+    if (f->kind == ORA_AN_GYRE) {
+        double A = p[0], eps = p[1], om = p[2];
+        double a = eps * sin(om * t);
+        double b = 1.0 - 2.0 * eps * sin(om * t);
+        double fx = a * x[0] * x[0] + b * x[0];
+        double dfdx = 2.0 * a * x[0] + b;
+        u[0] = -ORA_PI * A * sin(ORA_PI * fx) * cos(ORA_PI * x[1]);
+        u[1] = ORA_PI * A * cos(ORA_PI * fx) * sin(ORA_PI * x[1]) * dfdx;
+    } else if (f->kind == ORA_AN_ABC) {
+        double At = p[0] + p[3] * t * sin(ORA_PI * t);
+        double B = p[1], C = p[2];
+        u[0] = At * sin(x[2]) + C * cos(x[1]);
+        u[1] = B * sin(x[0]) + At * cos(x[2]);
+        u[2] = C * sin(x[1]) + B * cos(x[0]);
+    } else if (f->kind == ORA_AN_AFFINE) {
+        int d = f->dim;
+        for (int r = 0; r < d; ++r) {
+            double s = p[18 + r] + t * p[21 + r];
+            for (int c = 0; c < d; ++c) s += (p[r * 3 + c] + t * p[9 + r * 3 + c]) * x[c];
+            u[r] = s;
+        }
+    } else if (f->kind == ORA_AN_PIPE) {
+        double R = p[0], L = p[1], amp = p[2];
+        double r2 = (x[0] * x[0] + x[1] * x[1]) / (R * R);
+        double prof = 1.0 - r2;
+        double sw = 0.0;
+        for (int m = 1; m <= 4; ++m)
+            sw += sin(2.0 * ORA_PI * m * x[2] / L + p[2 + m] + 2.0 * ORA_PI * t) / (double)m;
+        double s = amp * prof * sw;
+        u[0] = -s * x[1];
+        u[1] = s * x[0];
+        u[2] = prof * (1.0 + 0.5 * sin(2.0 * ORA_PI * t));
+    } else {
+        return 1;
+    }
+    return 0;
+}
+
+/* ====================================================================
+ * Tetrahedral meshes (Sec. 3.1: a single cell search for tetrahedralized
+ * data; local walk of Shadden, Astorino, Gerbeau 2010).
+ *
+ * Exact orientation: the 4x4 determinant with a column of ones expands
+ * into 24 products of three FP32 coordinates.  A product of two FP32 values
+ * is exact in FP64; the third factor is applied with an error-free product
+ * (FMA residual, Ogita-Rump-Oishi 2005).  The 48 doubles are summed exactly
+ * into a nonoverlapping expansion with Knuth's TwoSum (Shewchuk 1997,
+ * grow-expansion); the sign is that of its largest nonzero component.
+ * ==================================================================== */
+static void two_sum(double a, double b, double *s, double *e)
+{
+    double x = a + b;
+    double bv = x - a;
+    double av = x - bv;
+    double br = b - bv;
+    double ar = a - av;
+    *s = x;
+    *e = ar + br;
+}
+
+static int grow_expansion(int elen, const double *e, double b, double *h)
+{
+    double q = b;
+    int hi = 0;
+    for (int i = 0; i < elen; ++i) {
+        double qn, hn;
+        two_sum(q, e[i], &qn, &hn);
+        q = qn;
+        if (hn != 0.0) h[hi++] = hn;
+    }
+    h[hi++] = q;
+    return hi;
+}
+
+/* adds s * p*q*r exactly into the expansion (e, *len) */
+static void add_triple(double *e, int *len, double s, float p, float q, float r)
+{
+    double pq = (double)p * (double)q;   /* exact: 48 significant bits */
+    double hi = pq * (double)r;
+    double lo = fma(pq, (double)r, -hi); /* exact residual */
+    double tmp[128];
+    int n = grow_expansion(*len, e, s * hi, tmp);
+    n = grow_expansion(n, tmp, s * lo, e);
+    *len = n;
+}
+
+/* det of rows (p, q, r), 6 signed triple products */
+static void add_det3(double *e, int *len, double s, const float *p, const float *q, const float *r)
+{
+    add_triple(e, len, s, p[0], q[1], r[2]);
+    add_triple(e, len, -s, p[0], q[2], r[1]);
+    add_triple(e, len, -s, p[1], q[0], r[2]);
+    add_triple(e, len, s, p[1], q[2], r[0]);
+    add_triple(e, len, s, p[2], q[0], r[1]);
+    add_triple(e, len, -s, p[2], q[1], r[0]);
+}
+
+int ora_orient3d_exact(const float *a, const float *b, const float *c, const float *d)
+{
+    /* ((b-a) x (c-a)) . (d-a) = det3(b,c,d) - det3(a,c,d) + det3(a,b,d) - det3(a,b,c) */
+    double e[128];
+    int len = 0;
+    add_det3(e, &len, 1.0, b, c, d);
+    add_det3(e, &len, -1.0, a, c, d);
+    add_det3(e, &len, 1.0, a, b, d);
+    add_det3(e, &len, -1.0, a, b, c);
+    for (int i = len - 1; i >= 0; --i) {
+        if (e[i] > 0.0) return 1;
+        if (e[i] < 0.0) return -1;
+    }
+    return 0;
+}
+
+static const float *tet_vertex(const ora_tet_field *f, long long t, int v)
+{
+    return f->xyz + 3LL * f->tets[4 * t + v];
+}
+
+/* signs of the barycentric coordinates of p in tet t: lam_sign[i] =
+ * sign(orient with vertex i replaced by p) * sign(orient of the tet).       */
+static void tet_bary_signs(const ora_tet_field *f, long long t, const float *p, int *sg)
+{
+    const float *v[4];
+    for (int i = 0; i < 4; ++i) v[i] = tet_vertex(f, t, i);
+    int D = ora_orient3d_exact(v[0], v[1], v[2], v[3]);
+    for (int i = 0; i < 4; ++i) {
+        const float *w[4] = {v[0], v[1], v[2], v[3]};
+        w[i] = p;
+        sg[i] = D * ora_orient3d_exact(w[0], w[1], w[2], w[3]);
+    }
+}
+
+int ora_tet_contains(const ora_tet_field *f, long long t, const float *p, int *on_boundary)
+{
+    int sg[4];
+    tet_bary_signs(f, t, p, sg);
+    int inside = 1, onb = 0;
+    for (int i = 0; i < 4; ++i) {
+        if (sg[i] < 0) inside = 0;
+        if (sg[i] == 0) onb = 1;
+    }
+    if (on_boundary) *on_boundary = inside && onb;
+    return inside;
+}
+
+long long ora_tet_locate_brute(const ora_tet_field *f, const float *p)
+{
+    for (long long t = 0; t < f->ncells; ++t)
+        if (ora_tet_contains(f, t, p, NULL)) return t;
+    return -1;
+}
+
+/* FP64 barycentric coordinates of x in tet t (Cramer's rule on differences) */
+static double det3d(const double *a, const double *b, const double *c)
+{
+    return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0])
+         + a[2] * (b[0] * c[1] - b[1] * c[0]);
+}
+
+static void tet_bary(const ora_tet_field *f, long long t, const double *x, double *lam)
+{
+    double v[4][3];
+    for (int i = 0; i < 4; ++i) {
+        const float *q = tet_vertex(f, t, i);
+        v[i][0] = q[0];
+        v[i][1] = q[1];
+        v[i][2] = q[2];
+    }
+    double e1[3], e2[3], e3[3], r[3];
+    for (int c = 0; c < 3; ++c) {
+        e1[c] = v[1][c] - v[0][c];
+        e2[c] = v[2][c] - v[0][c];
+        e3[c] = v[3][c] - v[0][c];
+        r[c] = x[c] - v[0][c];
+    }
+    double D = det3d(e1, e2, e3);
+    lam[1] = det3d(r, e2, e3) / D;
+    lam[2] = det3d(e1, r, e3) / D;
+    lam[3] = det3d(e1, e2, r) / D;
+    lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
+}
+
+long long ora_tet_locate_walk(const ora_tet_field *f, long long start, const float *p)
+{
+    long long t = (start >= 0 && start < f->ncells) ? start : 0;
+    int found = 0;
+    int limit = f->walk_limit > 0 ? f->walk_limit : 100000;
+    double xp[3] = {p[0], p[1], p[2]};
+    for (int step = 0; step < limit; ++step) {
+        int sg[4];
+        tet_bary_signs(f, t, p, sg);
+        int best = -1;
+        double bestv = 0.0;
+        double lam[4];
+        tet_bary(f, t, xp, lam);
+        for (int i = 0; i < 4; ++i) {
+            if (sg[i] < 0 && (best < 0 || lam[i] < bestv)) {
+                best = i;
+                bestv = lam[i];
+            }
+        }
+        if (best < 0) {
+            found = 1;
+            break;
+        }
+        long long nb = f->nbrs[4 * t + best];
+        if (nb < 0) return -1; /* separated from the convex hull by a boundary face */
+        t = nb;
+    }
+    if (!found) return ora_tet_locate_brute(f, p);
+    int onb = 0;
+    ora_tet_contains(f, t, p, &onb);
+    if (!onb) return t;
+    /* tie-break: lowest id among the closed tets holding p, collected across
+     * faces that contain p (a face, edge or vertex star is face-connected)  */
+    long long stack[1024], seen[1024];
+    int ns = 0, nseen = 0;
+    stack[ns++] = t;
+    seen[nseen++] = t;
+    long long best = t;
+    while (ns > 0) {
+        long long c = stack[--ns];
+        if (c < best) best = c;
+        int sg[4];
+        tet_bary_signs(f, c, p, sg);
+        for (int i = 0; i < 4; ++i) {
+            if (sg[i] != 0) continue;
+            long long nb = f->nbrs[4 * c + i];
+            if (nb < 0) continue;
+            int dup = 0;
+            for (int s = 0; s < nseen; ++s)
+                if (seen[s] == nb) dup = 1;
+            if (dup) continue;
+            if (!ora_tet_contains(f, nb, p, NULL)) continue;
+            if (nseen >= 1024 || ns >= 1024) return ora_tet_locate_brute(f, p);
+            seen[nseen++] = nb;
+            stack[ns++] = nb;
+        }
+    }
+    return best;
+}
+
+/* Interpolation-time location of an FP64 point: walk on FP64 barycentric
+ * coordinates (P1 interpolation is continuous across faces, so which of two
+ * face-sharing tets is found does not change u beyond rounding).          */
+static long long tet_locate_fp64(const ora_tet_field *f, long long start, const double *x, double *lam)
+{
+    const double tol = 1e-12;
+    long long t = (start >= 0 && start < f->ncells) ? start : 0;
+    int limit = f->walk_limit > 0 ? f->walk_limit : 100000;
+    for (int step = 0; step < limit; ++step) {
+        tet_bary(f, t, x, lam);
+        int best = -1;
+        double bestv = -tol;
+        for (int i = 0; i < 4; ++i)
+            if (lam[i] < bestv) {
+                best = i;
+                bestv = lam[i];
+            }
+        if (best < 0) return t;
+        long long nb = f->nbrs[4 * t + best];
+        if (nb < 0) return -1;
+        t = nb;
+    }
+    for (long long c = 0; c < f->ncells; ++c) {
+        tet_bary(f, c, x, lam);
+        if (lam[0] >= -tol && lam[1] >= -tol && lam[2] >= -tol && lam[3] >= -tol) return c;
+    }
+    return -1;
+}
+
+int ora_tet_velocity(const ora_tet_field *f, const double *x, double t, int *cell, double *u)
+{
+    double lam[4];
+    long long c = tet_locate_fp64(f, *cell, x, lam);
+    if (c < 0) return 1;
+    *cell = (int)c;
+    int k;
+    double a;
+    ora_time_locate(f->times, f->nframes, f->time_periodic, f->period, t, &k, &a);
+    int k1 = (f->nframes > 1) ? k + 1 : k;
+    const float *fa = f->frames + 3LL * f->nnodes * k;
+    const float *fb = f->frames + 3LL * f->nnodes * k1;
+    for (int comp = 0; comp < 3; ++comp) {
+        double sa = 0.0, sb = 0.0;
+        for (int v = 0; v < 4; ++v) {
+            long long node = f->tets[4 * c + v];
+            sa += lam[v] * (double)fa[3 * node + comp];
+            sb += lam[v] * (double)fb[3 * node + comp];
+        }
+        u[comp] = (1.0 - a) * sa + a * sb;
+    }
+    return 0;
+}
+
+/* ====================================================================
+ * Seed lattice (Sec. 2 "Seed": structured grid of seed points).
+ * ==================================================================== */
+void ora_seed_grid(int dim, const int n[3], const double lo[3], const double hi[3],
+                   const int endpoint[3], float *out)
+{
+    long long nx = n[0], ny = n[1], nz = (dim == 3) ? n[2] : 1;
+    long long N = nx * ny * nz;
+    double step[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < dim; ++a) {
+        if (endpoint[a])
+            step[a] = (n[a] > 1) ? (hi[a] - lo[a]) / (double)(n[a] - 1) : 0.0;
+        else
+            step[a] = (hi[a] - lo[a]) / (double)n[a];
+    }
+    for (long long k = 0; k < nz; ++k)
+        for (long long j = 0; j < ny; ++j)
+            for (long long i = 0; i < nx; ++i) {
+                long long id = i + nx * (j + ny * k);
+                long long idx[3] = {i, j, k};
+                for (int a = 0; a < dim; ++a) {
+                    double xa = lo[a] + (double)idx[a] * step[a];
+                    out[a * N + id] = (float)xa;
+                }
+            }
+}
+
+/* ====================================================================
+ * Integrators of Eq. 2 (Sec. 2 "Flow Map").
+ * ==================================================================== */
+typedef struct {
+    int kind;
+    const void *field;
+    int dim;
+} vel_src;
+
+/* returns 0 inside, 1 outside (only tets can be outside) */
+static int eval_u(const vel_src *s, const double *x, double t, int *cell, double *u)
+{
+    if (s->kind == 0) return ora_rect_velocity((const ora_rect_field *)s->field, x, t, u);
+    if (s->kind == 1) return ora_analytic_velocity((const ora_analytic_field *)s->field, x, t, u);
+    return ora_tet_velocity((const ora_tet_field *)s->field, x, t, cell, u);
+}
+
+long long ora_rk4(int field_kind, const void *field, int dim, long long n,
+                  const double *x0, const int *cells, double t0, double T, double dt,
+                  double *xT, unsigned char *status, double *t_exit)
+{
+    vel_src src = {field_kind, field, dim};
+    double adt = fabs(dt);
+    long long nsteps = (long long)floor(fabs(T) / adt + 0.5);
+    double h = (T < 0.0) ? -adt : adt;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long long p = 0; p < n; ++p) {
+        double x[3] = {0, 0, 0};
+        for (int a = 0; a < dim; ++a) x[a] = x0[a * n + p];
+        int cell = cells ? cells[p] : 0;
+        unsigned char st = ORA_OK;
+        double te = t0 + T;
+        if (field_kind == 2 && cell < 0) {
+            st = ORA_OUTSIDE;
+            te = t0;
+        }
+        for (long long s = 0; s < nsteps && st == ORA_OK; ++s) {
+            double t = t0 + (double)s * h;
+            double k1[3], k2[3], k3[3], k4[3], y[3];
+            int out = eval_u(&src, x, t, &cell, k1);
+            if (!out) {
+                for (int a = 0; a < dim; ++a) y[a] = x[a] + 0.5 * h * k1[a];
+                out = eval_u(&src, y, t + 0.5 * h, &cell, k2);
+            }
+            if (!out) {
+                for (int a = 0; a < dim; ++a) y[a] = x[a] + 0.5 * h * k2[a];
+                out = eval_u(&src, y, t + 0.5 * h, &cell, k3);
+            }
+            if (!out) {
+                for (int a = 0; a < dim; ++a) y[a] = x[a] + h * k3[a];
+                out = eval_u(&src, y, t + h, &cell, k4);
+            }
+            if (out) { /* a stage left the mesh: freeze at the start of the step */
+                st = ORA_LEFT;
+                te = t;
+                break;
+            }
+            for (int a = 0; a < dim; ++a)
+                x[a] = x[a] + h / 6.0 * (k1[a] + 2.0 * k2[a] + 2.0 * k3[a] + k4[a]);
+            if (field_kind == 0 && rect_left((const ora_rect_field *)field, x)) {
+                st = ORA_LEFT;
+                te = t + h;
+            }
+        }
+        for (int a = 0; a < dim; ++a) xT[a * n + p] = x[a];
+        status[p] = st;
+        t_exit[p] = te;
+    }
+    return nsteps;
+}
+
+/* Dormand-Prince 5(4) tableau (Dormand & Prince 1980). */
+static const double DP_C[7] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 4.0 / 5.0, 8.0 / 9.0, 1.0, 1.0};
+static const double DP_A[7][6] = {
+    {0, 0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0, 0},
+    {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0, 0},
+    {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0, 0},
+    {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0, 0},
+    {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0}};
+static const double DP_B[7] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0,
+                               -2187.0 / 6784.0, 11.0 / 84.0, 0.0};
+static const double DP_BS[7] = {5179.0 / 57600.0, 0.0, 7571.0 / 16695.0, 393.0 / 640.0,
+                                -92097.0 / 339200.0, 187.0 / 2100.0, 1.0 / 40.0};
+
+typedef struct {
+    double x[3];
+    double k1[3];   /* FSAL: derivative at (x, t) */
+    int have_k1;
+    int cell;
+    unsigned char st;
+    double te;
+    long long attempts, accepted;
+} dp_tracer;
+
+/* One DP5(4) trial from (x, t) with step h.  Fills xn (5th order), err (the
+ * scaled norm) and k7 (derivative at xn, t + h).  Returns 1 if a stage point
+ * is outside the mesh.                                                      */
+static int dp_trial(const vel_src *src, int dim, dp_tracer *tr, double t, double h,
+                    double rtol, double atol, double *xn, double *k7, double *err)
+{
+    double k[7][3];
+    double y[3];
+    int cell = tr->cell;
+    if (!tr->have_k1) {
+        if (eval_u(src, tr->x, t, &cell, tr->k1)) return 1;
+        tr->have_k1 = 1;
+        tr->cell = cell;
+    }
+    for (int a = 0; a < dim; ++a) k[0][a] = tr->k1[a];
+    for (int s = 1; s < 7; ++s) {
+        for (int a = 0; a < dim; ++a) {
+            double acc = 0.0;
+            for (int j = 0; j < s; ++j) acc += DP_A[s][j] * k[j][a];
+            y[a] = tr->x[a] + h * acc;
+        }
+        if (eval_u(src, y, t + DP_C[s] * h, &cell, k[s])) return 1;
+    }
+    double e = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        /* 5th-order solution: same sum as the last stage point (b = a_7j) */
+        double acc = 0.0, ea = 0.0;
+        for (int j = 0; j < 6; ++j) acc += DP_B[j] * k[j][a];
+        for (int s = 0; s < 7; ++s) ea += (DP_B[s] - DP_BS[s]) * k[s][a];
+        ea = h * ea;
+        double x5 = tr->x[a] + h * acc;
+        xn[a] = x5;
+        k7[a] = k[6][a];
+        double sc = atol + rtol * fmax(fabs(tr->x[a]), fabs(x5));
+        double r = fabs(ea) / sc;
+        if (r > e) e = r;
+    }
+    *err = e;
+    tr->cell = cell;
+    return 0;
+}
+
+static double dp_factor(double err)
+{
+    if (err == 0.0) return 5.0;
+    double f = 0.9 * pow(err, -0.2);
+    if (f < 0.2) f = 0.2;
+    if (f > 5.0) f = 5.0;
+    return f;
+}
+
+long long ora_dp45(int field_kind, const void *field, int dim, long long n,
+                   const double *x0, const int *cells, double t0, double T,
+                   double h0, double rtol, double atol, long long max_steps,
+                   int group, int adaptive,
+                   double *xT, unsigned char *status, double *t_exit,
+                   long long *nsteps_out)
+{
+    vel_src src = {field_kind, field, dim};
+    if (group < 1) group = 1;
+    double dir = (T < 0.0) ? -1.0 : 1.0;
+    double tend = t0 + T;
+    long long ngroups = (n + group - 1) / group;
+    long long total_acc = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total_acc)
+    for (long long g = 0; g < ngroups; ++g) {
+        long long p0 = g * group;
+        long long p1 = p0 + group < n ? p0 + group : n;
+        int m = (int)(p1 - p0);
+        dp_tracer *tr = (dp_tracer *)calloc((size_t)m, sizeof(dp_tracer));
+        for (int q = 0; q < m; ++q) {
+            long long p = p0 + q;
+            for (int a = 0; a < dim; ++a) tr[q].x[a] = x0[a * n + p];
+            tr[q].cell = cells ? cells[p] : 0;
+            tr[q].st = ORA_OK;
+            tr[q].te = tend;
+            if (field_kind == 2 && tr[q].cell < 0) {
+                tr[q].st = ORA_OUTSIDE;
+                tr[q].te = t0;
+            }
+        }
+        double t = t0;
+        double h = dir * fabs(h0);
+        long long attempts = 0;
+        double xn[32][3], k7[32][3], err[32];
+        int outm[32];
+        while (1) {
+            int live = 0;
+            for (int q = 0; q < m; ++q) live += (tr[q].st == ORA_OK);
+            if (!live) break;
+            if (dir * (tend - t) <= 0.0) break;
+            if (attempts >= max_steps) {
+                for (int q = 0; q < m; ++q)
+                    if (tr[q].st == ORA_OK) {
+                        tr[q].st = ORA_MAXSTEPS;
+                        tr[q].te = t;
+                    }
+                break;
+            }
+            double hs = h;
+            if (dir * (t + hs - tend) > 0.0) hs = tend - t; /* land on t0 + T */
+            attempts++;
+            int all_ok = 1;
+            double hmin = 0.0;
+            int have_h = 0;
+            for (int q = 0; q < m; ++q) {
+                if (tr[q].st != ORA_OK) continue;
+                outm[q] = dp_trial(&src, dim, &tr[q], t, hs, rtol, atol, xn[q], k7[q], &err[q]);
+                if (outm[q]) continue;
+                if (adaptive && err[q] > 1.0) all_ok = 0;
+                double hq = hs * dp_factor(err[q]);
+                if (!have_h || fabs(hq) < fabs(hmin)) {
+                    hmin = hq;
+                    have_h = 1;
+                }
+            }
+            /* a stage outside the mesh: that tracer leaves, frozen at the
+             * start of the step, and takes no part in the vote             */
+            for (int q = 0; q < m; ++q)
+                if (tr[q].st == ORA_OK && outm[q]) {
+                    tr[q].st = ORA_LEFT;
+                    tr[q].te = t;
+                }
+            if (!adaptive || all_ok) {
+                for (int q = 0; q < m; ++q) {
+                    if (tr[q].st != ORA_OK) continue;
+                    for (int a = 0; a < dim; ++a) {
+                        tr[q].x[a] = xn[q][a];
+                        tr[q].k1[a] = k7[q][a];
+                    }
+                    tr[q].accepted++;
+                }
+                t = t + hs;
+            }
+            if (adaptive && have_h) h = hmin;
+        }
+        for (int q = 0; q < m; ++q) {
+            long long p = p0 + q;
+            for (int a = 0; a < dim; ++a) xT[a * n + p] = tr[q].x[a];
+            status[p] = tr[q].st;
+            t_exit[p] = tr[q].te;
+            if (nsteps_out) nsteps_out[p] = tr[q].accepted;
+            total_acc += tr[q].accepted;
+        }
+        free(tr);
+    }
+    return total_acc;
+}
+
+/* ====================================================================
+ * Flow-map gradient by finite differences on the seed lattice (Sec. 2
+ * "Cauchy-Green"), C = grad F^T grad F (Eq. 1), eigenvalues, FTLE.
+ * ==================================================================== */
+
+/* lattice neighbour of seed (i,j,k) at offset off along axis b; returns the id
+ * or -1 when it falls off a non-periodic edge; *wrap gets the number of
+ * periods crossed (positive upward).                                        */
+static long long lattice_nbr(int dim, const int n[3], const int periodic[3], const long long idx[3],
+                             int b, int off, int *wrap)
+{
+    long long c[3] = {idx[0], idx[1], dim == 3 ? idx[2] : 0};
+    long long v = c[b] + off;
+    *wrap = 0;
+    if (periodic[b]) {
+        while (v < 0) {
+            v += n[b];
+            (*wrap)--;
+        }
+        while (v >= n[b]) {
+            v -= n[b];
+            (*wrap)++;
+        }
+    } else if (v < 0 || v >= n[b]) {
+        return -1;
+    }
+    c[b] = v;
+    return c[0] + (long long)n[0] * (c[1] + (long long)n[1] * c[2]);
+}
+
+void ora_flowmap_gradient(int dim, const int n[3], const double h[3],
+                          const int periodic[3], const double period[3],
+                          const double *xT, const unsigned char *status, double *grad)
+{
+    long long nz = (dim == 3) ? n[2] : 1;
+    long long N = (long long)n[0] * n[1] * nz;
+#pragma omp parallel for schedule(static)
+    for (long long p = 0; p < N; ++p) {
+        long long idx[3] = {p % n[0], (p / n[0]) % n[1], p / ((long long)n[0] * n[1])};
+        double *G = grad + p * dim * dim;
+        for (int e = 0; e < dim * dim; ++e) G[e] = NAN;
+        if (status[p] != ORA_OK) continue;
+        for (int b = 0; b < dim; ++b) {
+            int wp1, wm1, wp2, wm2;
+            long long qp1 = lattice_nbr(dim, n, periodic, idx, b, 1, &wp1);
+            long long qm1 = lattice_nbr(dim, n, periodic, idx, b, -1, &wm1);
+            long long qp2 = lattice_nbr(dim, n, periodic, idx, b, 2, &wp2);
+            long long qm2 = lattice_nbr(dim, n, periodic, idx, b, -2, &wm2);
+            int okp1 = qp1 >= 0 && status[qp1] == ORA_OK;
+            int okm1 = qm1 >= 0 && status[qm1] == ORA_OK;
+            int okp2 = qp2 >= 0 && status[qp2] == ORA_OK;
+            int okm2 = qm2 >= 0 && status[qm2] == ORA_OK;
+            for (int a = 0; a < dim; ++a) {
+                /* neighbour position, shifted by the periods crossed on axis b */
+                double F0 = xT[a * N + p];
+                double Fp1 = 0, Fm1 = 0, Fp2 = 0, Fm2 = 0;
+                double sh = (a == b) ? period[b] : 0.0;
+                if (qp1 >= 0) Fp1 = xT[a * N + qp1] + (double)wp1 * sh;
+                if (qm1 >= 0) Fm1 = xT[a * N + qm1] + (double)wm1 * sh;
+                if (qp2 >= 0) Fp2 = xT[a * N + qp2] + (double)wp2 * sh;
+                if (qm2 >= 0) Fm2 = xT[a * N + qm2] + (double)wm2 * sh;
+                double d;
+                if (okp1 && okm1)
+                    d = (Fp1 - Fm1) / (2.0 * h[b]);
+                else if (okp1 && okp2)
+                    d = (-3.0 * F0 + 4.0 * Fp1 - Fp2) / (2.0 * h[b]);
+                else if (okm1 && okm2)
+                    d = (3.0 * F0 - 4.0 * Fm1 + Fm2) / (2.0 * h[b]);
+                else
+                    d = NAN;
+                G[a * dim + b] = d;
+            }
+        }
+    }
+}
+
+void ora_cauchy_green(int dim, long long n, const double *grad, double *C)
+{
+    int np = (dim == 2) ? 3 : 6;
+#pragma omp parallel for schedule(static)
+    for (long long p = 0; p < n; ++p) {
+        const double *G = grad + p * dim * dim;
+        double *Cp = C + p * np;
+        int o = 0;
+        for (int i = 0; i < dim; ++i)
+            for (int j = i; j < dim; ++j) {
+                double s = 0.0;
+                for (int a = 0; a < dim; ++a) s += G[a * dim + i] * G[a * dim + j];
+                Cp[o++] = s;
+            }
+    }
+}
+
+/* cyclic Jacobi eigenvalue iteration (Golub & Van Loan, Sec. 8.5) */
+int ora_eig_sym(int dim, const double *Cp, double *eig)
+{
+    double A[3][3];
+    int o = 0;
+    for (int i = 0; i < dim; ++i)
+        for (int j = i; j < dim; ++j) {
+            A[i][j] = Cp[o];
+            A[j][i] = Cp[o];
+            o++;
+        }
+    for (int i = 0; i < dim; ++i)
+        if (isnan(A[i][i])) {
+            for (int r = 0; r < dim; ++r) eig[r] = NAN;
+            return 0;
+        }
+    int sweep;
+    for (sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < dim; ++i) {
+            diag += A[i][i] * A[i][i];
+            for (int j = 0; j < dim; ++j)
+                if (i != j) off += A[i][j] * A[i][j];
+        }
+        if (off == 0.0 || off <= 1e-36 * diag) break;
+        for (int p = 0; p < dim - 1; ++p)
+            for (int q = p + 1; q < dim; ++q) {
+                if (A[p][q] == 0.0) continue;
+                double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0);
+                double s = t * c;
+                /* A <- J^T A J with the rotation in the (p, q) plane */
+                for (int k = 0; k < dim; ++k) {
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < dim; ++k) {
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+            }
+    }
+    for (int i = 0; i < dim; ++i) eig[i] = A[i][i];
+    for (int i = 0; i < dim; ++i) /* ascending insertion sort */
+        for (int j = i + 1; j < dim; ++j)
+            if (eig[j] < eig[i]) {
+                double tmp = eig[i];
+                eig[i] = eig[j];
+                eig[j] = tmp;
+            }
+    return sweep;
+}
+
+void ora_ftle(int dim, long long n, const double *C, double T, double *lambda_max, double *ftle)
+{
+    int np = (dim == 2) ? 3 : 6;
+#pragma omp parallel for schedule(static)
+    for (long long p = 0; p < n; ++p) {
+        double eig[3];
+        ora_eig_sym(dim, C + p * np, eig);
+        double lm = eig[dim - 1];
+        if (lambda_max) lambda_max[p] = lm;
+        ftle[p] = log(sqrt(lm)) / fabs(T);
+    }
+}
