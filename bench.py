@@ -1,0 +1,361 @@
+"""Benchmark of the flow-map / FTLE hot path on one GB300 (per rank).
+
+Workload (default): the 3D time-modulated ABC flow on a periodic 128^3 grid with
+64 FP32 frames over [0, 8]; a 256^3 periodic seed lattice (16.7M tracers); RK4,
+dt = 0.02, T = 8 (400 steps); grad F by finite differences, the full 3x3
+Cauchy-Green tensor (FP64) and the FTLE field.  Synthetic seeded data.
+
+A timed step = lcs_advect + lcs_ftle (FTLE and C written to device memory) with
+the field and the seed lattice resident.  `e2e` repeats the whole user-level
+sequence from host buffers each step: lcs_load_field from pinned host frames,
+lcs_seed_grid, lcs_flowmap_create, lcs_advect, lcs_ftle into pinned host
+buffers, and the frees.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (the baseline arm).  Under torchrun every rank runs
+its own independent copy of the workload (weak scaling, no data exchange);
+`value` is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FTLE seeds/s & tracer-steps/s on 1 GB300; surrogate/mixed vs plain at stated err"
+WORKLOAD = ("3D time-modulated ABC flow, periodic 128^3 FP32 velocity grid, 64 frames on [0,8]; "
+            "256^3 seed grid (16.7M tracers); RK4 dt=0.02, T=8 (400 steps); FD grad F, 3x3 Cauchy-Green "
+            "(FP64) and FTLE")
+L = 2 * math.pi
+N_SIDE, N_GRID, N_FRAMES, T_END, DT = 256, 128, 64, 8.0, 0.02
+NSTEPS = int(round(T_END / DT))
+# algorithmic FP32 work of one RK4 tracer-step on trilinear, linear-in-time data (FMA = 2):
+# per stage evaluation 9 (cell coordinates) + 15 (weights) + 96 (8-corner sums, 3 comps, 2 frames)
+# + 10 (time blend) = 130; 4 evaluations + 18 (stage points) + 18 (update) = 556
+FLOP_PER_TRACER_STEP = 556
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--seeds-side", type=int, default=N_SIDE,
+                   help="seed lattice side (default 256; smaller only for profiling captures)")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.TemporaryFile(mode="w+")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        self.out.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- reference arm
+
+def oracle_sample_run(g, side, threads=0):
+    """Oracle FTLE on a side^3 block of the 256^3 lattice (its stencils included); returns (seeds, s)."""
+    import oracle
+
+    oracle.build()
+    nthreads = oracle.set_threads(threads)
+    n = (N_SIDE, N_SIDE, N_SIDE)
+    h = L / N_SIDE
+    # block of side^3 seeds at the lattice origin plus a 2-seed halo (stencil neighbours, periodic)
+    idx = np.arange(-2, side + 2) % N_SIDE
+    xs = (idx * h).astype(np.float32)
+    Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+    x0 = np.stack([X.ravel(), Y.ravel(), Z.ravel()]).astype(np.float64)
+    F = oracle.RectField(g.frames, g.times, g.origin, g.spacing, g.periodic)
+    t = time.perf_counter()
+    xT, st, _ = oracle.rk4(F, x0, 0.0, T_END, DT)
+    m = side + 4
+    # the halo block is a non-periodic lattice of its own; FTLE of its interior side^3 seeds
+    G = oracle.flowmap_gradient(3, (m, m, m), (h, h, h), (0, 0, 0), (0, 0, 0), xT, st)
+    C = oracle.cauchy_green(G)
+    lam, sig = oracle.ftle(C, 3, T_END)
+    dt = time.perf_counter() - t
+    return side ** 3, dt, nthreads, x0.shape[1]
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2209_13775_gb300 import inputs
+
+    g = inputs.abc(n=N_GRID, nframes=N_FRAMES, t_end=T_END)
+    # calibrate: a small block first, then one sized for about 5 s per step
+    s_small, dt_small, _, _ = oracle_sample_run(g, 4)
+    per_seed = dt_small / ((4 + 4) ** 3)
+    side = int(max(4, min(48, (5.0 / max(per_seed, 1e-9)) ** (1 / 3) - 4)))
+    if args.warmup > 0:
+        oracle_sample_run(g, 4)
+    times = []
+    for _ in range(args.steps):
+        s, dt, nth, integrated = oracle_sample_run(g, side)
+        times.append(dt)
+    tmean = sum(times) / len(times)
+    value = s / tmean            # FTLE seeds/s of the sample (halo integration included in the time)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "%d^3-seed block (+2-seed halo, %d integrated)" % (side, integrated)},
+        "tracer_steps_per_s": value * NSTEPS,
+        "cpu_baseline": {"value": value, "unit": "seeds/s", "cores": nth, "kind": "oracle",
+                         "sample": "%d^3 seeds of the 256^3 lattice with their stencil halo, all 400 steps" % side},
+        "e2e": {"value": value, "unit": "seeds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def our_arm(args, rank, world, local):
+    import torch
+
+    from paper_2209_13775_gb300 import inputs, lcs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    storage = {"f32": lcs.F32, "f16": lcs.F16, "bf16": lcs.BF16}[args.storage]
+    stream = torch.cuda.current_stream()
+    ctx = lcs.lcs_create(local, stream)
+    g = inputs.abc(n=N_GRID, nframes=N_FRAMES, t_end=T_END)
+    desc = lcs.field_desc(3, g.n, g.origin, g.spacing, g.periodic, g.times, storage=storage)
+    frames_dev = torch.from_numpy(g.frames).cuda()
+    field = lcs.lcs_load_field(ctx, desc, frames_dev)
+    sd = lcs.seed_desc(3, (args.seeds_side,) * 3, (0.0,) * 3, (L,) * 3, (1, 1, 1))
+    seeds = lcs.lcs_seed_grid(ctx, sd)
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    opts = lcs.advect_opts(lcs.RK4, t0=0.0, T=T_END, dt=DT)
+    ftle = torch.empty(N, dtype=torch.float32, device="cuda")
+    C = torch.empty((N, 6), dtype=torch.float64, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(rec=None):
+        if rec is not None:
+            rec[0].record(stream)
+        lcs.lcs_advect(ctx, field, seeds, opts, fm)
+        if rec is not None:
+            rec[1].record(stream)
+        lcs.lcs_ftle(ctx, fm, 0, ftle, None, C)
+
+    for _ in range(args.warmup):
+        step()
+    lcs.lcs_synchronize(ctx)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    adv_events = [(ev(), ev()) for _ in range(args.steps)]
+    t_start, t_stop = ev(), ev()
+    with ClockSampler(local) as clk:
+        barrier()
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(adv_events[k])
+        t_stop.record(stream)
+        barrier()
+    lcs.lcs_synchronize(ctx)
+    elapsed = t_start.elapsed_time(t_stop) / 1e3
+    adv_ms = [a.elapsed_time(b) for a, b in adv_events]
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    ms_per_step = elapsed / args.steps * 1e3
+    value = world * N * args.steps / elapsed
+    clocks = clk.summary()
+
+    # end to end through the C ABI from host buffers
+    frames_pin = torch.from_numpy(g.frames).pin_memory()
+    ftle_h = torch.empty(N, dtype=torch.float32).pin_memory()
+    C_h = torch.empty((N, 6), dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for k in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
+        barrier()
+        t0 = time.perf_counter()
+        f2 = lcs.lcs_load_field(ctx, desc, frames_pin)
+        s2 = lcs.lcs_seed_grid(ctx, sd)
+        m2 = lcs.lcs_flowmap_create(ctx, s2, 1)
+        lcs.lcs_advect(ctx, f2, s2, opts, m2)
+        lcs.lcs_ftle(ctx, m2, 0, ftle_h, None, C_h)
+        lcs.lcs_synchronize(ctx)
+        lcs.lcs_free_flowmap(m2)
+        lcs.lcs_free_seeds(s2)
+        lcs.lcs_free_field(f2)
+        barrier()
+        if k > 0:  # the first round is a warm-up of the allocator paths
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_el = sum(e2e_t) / len(e2e_t) if e2e_t else float("nan")
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([e2e_el], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_el = float(t.item())
+    h2d = g.frames.nbytes
+    d2h = ftle_h.numel() * 4 + C_h.numel() * 8
+
+    pk, pk_kind = peaks()
+    adv_s = sum(adv_ms) / len(adv_ms) / 1e3
+    flops = float(N) * NSTEPS * FLOP_PER_TRACER_STEP
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s at the maximum SM clock
+    achieved = flops / adv_s / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            tj = json.load(open(prof))
+            if tj.get("kernel") == "rk4_gather_kernel<3,0>" and tj.get("source_sha") == _src_sha():
+                traffic = tj.get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}[args.storage],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.seeds_side == N_SIDE else
+                   WORKLOAD.replace("256^3 seed grid (16.7M tracers)", "%d^3 seed grid" % args.seeds_side),
+                   "seeds": N, "steps_per_tracer": NSTEPS, "storage": args.storage,
+                   "parallelism": "independent replica per GPU" if world > 1 else "single GPU",
+                   "l2": "no flush needed: each step writes 872 MB of outputs (C + FTLE) > 129 MB L2"},
+        "tracer_steps_per_s": value * NSTEPS,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": traffic,
+                     "kernel": "rk4_gather_kernel<3,f32>", "flop_per_launch": flops,
+                     "avg_launch_ms": adv_s * 1e3,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, pk_kind)},
+        "clocks": clocks,
+        "e2e": {"value": world * N / e2e_el if e2e_t else None, "unit": "seeds/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_el * 1e3},
+        "gpu_launches": 3 * args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, dts, _, _ = oracle_sample_run(g, 4)                 # calibration: 8^3 tracers
+        side = int(max(4, min(40, (10.0 / max(dts / 512.0, 1e-9)) ** (1 / 3) - 4)))
+        s, dt, nth, integrated = oracle_sample_run(g, side)
+        line["cpu_baseline"] = {"value": s / dt, "unit": "seeds/s", "cores": nth, "kind": "oracle",
+                                "sample": "%d^3-seed block of the 256^3 lattice with its 2-seed stencil halo "
+                                          "(%d tracers integrated, 400 steps each), FD/CG/FTLE; %.1f s"
+                                          % (side, integrated, dt)}
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    lcs.lcs_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def _src_sha():
+    import hashlib
+
+    h = hashlib.sha1()
+    for name in ("advect_rect.cu", "lcs_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2209_13775_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    our_arm(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

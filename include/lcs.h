@@ -1,0 +1,236 @@
+/*
+ * lcs.h -- C ABI of liblcs, a GB300 (sm_103a) library for the data-parallel hot
+ * path of Lagrangian coherent structure computation: sampling the flow map of
+ * an interpolated unsteady velocity field over a structured seed grid, then the
+ * flow-map gradient, the Cauchy-Green tensor, its largest eigenvalue and the
+ * FTLE field.
+ *
+ * Paper: S. Ameli, Y. Desai, S. C. Shadden, "Development of an efficient and
+ * flexible pipeline for Lagrangian coherent structure computation"
+ * (arXiv 2209.13775).  Each call below names the passage that defines it.
+ *
+ * Conventions (all calls):
+ *  - Every call returns lcs_status and never aborts; the message of the last
+ *    failure on a context is available from lcs_last_error().
+ *  - Work is stream-ordered on the context's CUDA stream.  A call that writes a
+ *    HOST buffer synchronises that stream before it returns; a call that writes
+ *    a DEVICE buffer returns as soon as the work is queued.
+ *  - The caller owns every array it passes; the library copies what it keeps.
+ *    Handles (lcs_field, lcs_seeds, lcs_flowmap) own device memory allocated by
+ *    the library until the matching lcs_free_*().
+ *  - Positions are SoA: x[0..N), y[0..N), z[0..N).  Seed index is x-fastest:
+ *    id = i + nx*(j + ny*k).  Batched outputs are job-major.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef LCS_H
+#define LCS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LCS_OK = 0,
+    LCS_EINVAL = 1,       /* bad argument or descriptor                         */
+    LCS_ENOMEM = 2,       /* device allocation failed                           */
+    LCS_ECUDA = 3,        /* a CUDA runtime call failed                          */
+    LCS_ETIMEOUT = 4,     /* a bounded device-side wait gave up                  */
+    LCS_EWALK = 5,        /* a tet walk hit its step limit                       */
+    LCS_EMAXSTEPS = 6,    /* an adaptive integration hit max_steps               */
+    LCS_EUNSUPPORTED = 7  /* combination not implemented                         */
+} lcs_status;
+
+/* grid kinds, storage precisions, integrators */
+enum { LCS_RECTILINEAR = 0, LCS_TET = 1 };
+enum { LCS_F32 = 0, LCS_F16 = 1, LCS_BF16 = 2 };
+enum { LCS_RK4 = 0, LCS_RK45 = 1, LCS_SURROGATE = 2 };
+
+/* per-tracer status written by lcs_advect */
+enum {
+    LCS_TRACER_OK = 0,        /* inside the domain at t0 + T                            */
+    LCS_TRACER_LEFT = 1,      /* left the domain; frozen, exit time recorded            */
+    LCS_TRACER_OUTSIDE = 2,   /* seed not inside the domain at t0                       */
+    LCS_TRACER_MAXSTEPS = 3,  /* adaptive step cap reached                              */
+    LCS_TRACER_WALKFAIL = 4   /* tet walk exceeded walk_limit                           */
+};
+
+typedef struct lcs_ctx lcs_ctx;
+typedef struct lcs_field lcs_field;
+typedef struct lcs_seeds lcs_seeds;
+typedef struct lcs_flowmap lcs_flowmap;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` that queues work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle.  Errors: LCS_EINVAL (NULL out, bad device), LCS_ECUDA.            */
+lcs_status lcs_create(lcs_ctx **out, int device, void *stream);
+
+/* Destroy a context (NULL is a no-op).  Handles created on it must be freed
+ * first.                                                                    */
+void lcs_destroy(lcs_ctx *ctx);
+
+/* Message of the last failure on ctx ("" when none).  Owned by ctx.        */
+const char *lcs_last_error(const lcs_ctx *ctx);
+
+/* Switch the stream later calls queue on.                                   */
+lcs_status lcs_set_stream(lcs_ctx *ctx, void *stream);
+
+/* Wait for the context's stream, then read and clear the device-side error
+ * word: LCS_EWALK / LCS_ETIMEOUT / LCS_EMAXSTEPS when a kernel recorded one.  */
+lcs_status lcs_synchronize(lcs_ctx *ctx);
+
+/* --------------------------------------------------------- field (a1, a3) */
+
+/* Velocity data (Sec. 2 "Reader"/"Cache"/"Interpolator"): nodal velocity
+ * frames at increasing times, interpolated linearly in time and
+ * bilinearly / trilinearly (rectilinear) or piecewise-linearly (tets) in
+ * space.  Rectilinear node (i,j,k) sits at origin + (i,j,k)*spacing; a
+ * periodic axis has n cells (node n-1 joins node 0) and period n*spacing;
+ * queries on a non-periodic axis are clamped to the box.  Time outside
+ * [t_first, t_last] uses the end frame unless time_periodic, which wraps t
+ * into [t_first, t_first + period).                                         */
+typedef struct {
+    int dim;                    /* 2 or 3 (tets: 3)                                  */
+    int kind;                   /* LCS_RECTILINEAR | LCS_TET                          */
+    int n[3];                   /* rectilinear nodes per axis (n[2] unused in 2D)     */
+    double origin[3];
+    double spacing[3];
+    int periodic[3];            /* per-axis spatial periodicity (rectilinear)         */
+    int nframes;                /* >= 1                                               */
+    const double *frame_times;  /* HOST, nframes, strictly increasing                 */
+    int time_periodic;
+    double period;
+    int storage;                /* LCS_F32 | LCS_F16 | LCS_BF16 (velocity storage)    */
+    /* tetrahedral meshes (kind == LCS_TET), HOST arrays:                              */
+    long long nnodes, ncells;
+    const float *node_xyz;      /* [nnodes][3]                                        */
+    const int *tets;            /* [ncells][4] node ids                               */
+    const int *nbrs;            /* [ncells][4] tet across the face opposite vertex j,
+                                   -1 on the boundary                                 */
+} lcs_field_desc;
+
+/* Copy velocity frames into device storage.  frames is FP32,
+ * [nframes][nz][ny][nx][dim] (rectilinear) or [nframes][nnodes][3] (tets),
+ * in host memory or, if frames_on_device, device memory.  The library
+ * converts to desc->storage (FP16/BF16 round to nearest).
+ * Errors: LCS_EINVAL (descriptor), LCS_ENOMEM, LCS_ECUDA.                   */
+lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *desc, const float *frames,
+                          int frames_on_device, lcs_field **out);
+
+/* Replace the frames of a loaded field with new data of the same shape
+ * (same conventions as lcs_load_field); no allocation.                      */
+lcs_status lcs_update_frames(lcs_ctx *ctx, lcs_field *field, const float *frames,
+                             int frames_on_device);
+
+void lcs_free_field(lcs_field *field);
+
+/* --------------------------------------------------------- seed grid (a2) */
+
+/* Structured seed lattice (Sec. 2 "Seed"): along axis a,
+ *   x_i = lo[a] + i * step,  step = (hi[a] - lo[a]) / (n[a] - 1)   (periodic[a] == 0)
+ *                            step = (hi[a] - lo[a]) / n[a]         (periodic[a] != 0)
+ * evaluated in FP64 with round-to-nearest and no fused operations, then
+ * rounded to FP32 -- bit-identical to that definition.  A periodic axis makes
+ * the finite differences of lcs_cauchy_green / lcs_ftle wrap with period
+ * hi[a] - lo[a].                                                            */
+typedef struct {
+    int dim;
+    int n[3];
+    double lo[3], hi[3];
+    int periodic[3];
+} lcs_seed_desc;
+
+/* Generate the lattice on the device.  If `field` is a tet mesh, also locate
+ * the tet holding each seed with exact orientation predicates: the lowest
+ * tet id among the closed tets containing the seed, -1 if none (Sec. 2
+ * "Seed": the cell of each seed on unstructured data).  field may be NULL.
+ * Errors: LCS_EINVAL, LCS_ENOMEM, LCS_ECUDA.                                */
+lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *desc, const lcs_field *field,
+                         lcs_seeds **out);
+
+/* Number of seeds of a lattice.                                             */
+long long lcs_seeds_count(const lcs_seeds *seeds);
+
+/* Copy seed positions ([dim][N] FP32) and/or cell ids ([N] int32, -1 outside,
+ * only for seeds made on a tet field) to host or device buffers (either may be
+ * NULL).                                                                    */
+lcs_status lcs_seeds_get(lcs_ctx *ctx, const lcs_seeds *seeds, float *xyz, int *cells,
+                         int on_device);
+
+void lcs_free_seeds(lcs_seeds *seeds);
+
+/* ------------------------------------------------- flow map (a3-a8, a12) */
+
+/* Integration options (Sec. 2 "Flow Map": single-step Runge-Kutta; Eq. 2
+ * integrated over (t0, t0 + T); T < 0 integrates backward).
+ *  LCS_RK4   fixed step |dt|, |T|/|dt| must be an integer (within 1e-9).
+ *            Steps at t_n = t0 + n*dt, stages at t_n, t_n + dt/2, t_n + dt.
+ *  LCS_RK45  Dormand-Prince 5(4) with one step size per warp of 32 seeds
+ *            (32 consecutive seed ids): a step is accepted only when every
+ *            live lane accepts (err <= 1, err = max_i |e_i| / (atol + rtol *
+ *            max(|x_i|, |x_new_i|))), and the next step is the smallest lane
+ *            proposal h * min(5, max(0.2, 0.9 err^-1/5)).
+ * Batches: njobs > 1 integrates the same seeds for each (job_t0[j], job_T[j])
+ * pair in one persistent launch.                                            */
+typedef struct {
+    int method;                 /* LCS_RK4 | LCS_RK45 | LCS_SURROGATE                */
+    double t0, T;               /* single job (njobs <= 1)                            */
+    int njobs;                  /* 0 or 1: single job; > 1: batch                     */
+    const double *job_t0;       /* HOST [njobs] when njobs > 1                        */
+    const double *job_T;        /* HOST [njobs]                                       */
+    double dt;                  /* RK4 step magnitude                                 */
+    double rtol, atol, h0;      /* RK45                                               */
+    long long max_steps;        /* RK45 attempted-step cap per warp (0 = 10^6)        */
+    int walk_limit;             /* tet walk steps per point location (0 = 512)        */
+    int block_threads;          /* 0 = library choice                                 */
+    int variant;                /* 0 = library choice; 1 = cached gather;
+                                   2 = shared-memory frame ring (2D rectilinear)      */
+    const void *surrogate;      /* reserved for LCS_SURROGATE                         */
+} lcs_advect_opts;
+
+/* Flow-map storage for `njobs` integrations of one lattice.                 */
+lcs_status lcs_flowmap_create(lcs_ctx *ctx, const lcs_seeds *seeds, int njobs, lcs_flowmap **out);
+
+/* Advect every seed through the field and write x(t0 + T) per job into fm,
+ * with per-tracer status and exit time (a tracer leaving the domain is
+ * frozen: rectilinear when more than one cell outside a non-periodic axis
+ * after a step, at that step's end time; tets when a stage point falls
+ * outside the mesh, at the start of that step).
+ * Errors: LCS_EINVAL (options), LCS_EUNSUPPORTED, LCS_ECUDA.               */
+lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *seeds,
+                      const lcs_advect_opts *opts, lcs_flowmap *fm);
+
+/* Copy job `job` of a flow map: positions [dim][N] FP32 (unwrapped across
+ * periodic axes), status [N] uint8, exit time [N] FP32.  Any may be NULL.   */
+lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *xyz,
+                           unsigned char *status, float *t_exit, int on_device);
+
+void lcs_free_flowmap(lcs_flowmap *fm);
+
+/* ---------------------------------------- grad F, C, lambda_max, FTLE (a9-a11) */
+
+/* Cauchy-Green tensor C = grad(F)^T grad(F) (Eq. 1) with grad F from finite
+ * differences of the final positions on the seed lattice (Sec. 2
+ * "Cauchy-Green"), in FP64 from the FP32 positions.  Per axis b the stencil
+ * is, in order of preference, central (F(p+e_b) - F(p-e_b)) / 2h_b, forward
+ * (-3F(p) + 4F(p+e_b) - F(p+2e_b)) / 2h_b or backward (3F(p) - 4F(p-e_b) +
+ * F(p-2e_b)) / 2h_b, using only lattice points with status OK; none -> NaN.
+ * Output packed per seed: 2D (C00, C01, C11), 3D (C00, C01, C02, C11, C12,
+ * C22), FP64.  job = -1 writes every job, job-major.                        */
+lcs_status lcs_cauchy_green(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double *C,
+                            int on_device);
+
+/* FTLE sigma = ln(sqrt(lambda_max(C))) / |T| (Sec. 1: the FTLE is derived from
+ * the largest eigenvalue of C) as FP32 [N], NaN where C is undefined;
+ * optionally lambda_max [N] FP64 and C (as lcs_cauchy_green) from the same
+ * pass.  lambda_max and C may be NULL.  job = -1 writes every job.         */
+lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
+                    double *C, int on_device);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

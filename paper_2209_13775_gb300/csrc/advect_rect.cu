@@ -1,0 +1,728 @@
+// advect_rect.cu -- fixed-step RK4 advection through rectilinear velocity frames.
+//
+// Paper: Eq. 2 integrated over (t0, t0 + T) from a structured seed grid with
+// the classical 4th-order Runge-Kutta method (Sec. 2 "Flow Map", Sec. 3.1),
+// velocity interpolated bilinearly / trilinearly in space and linearly in time
+// between two frames (Sec. 2 "Interpolator").
+//
+// Design (differs from the paper's split kernels, Sec. 3.1): one thread owns one
+// tracer for the whole integration, with its state in registers; a step is
+// four fused stage evaluations.  All tracers of a launch share the time
+// schedule, so the frame bracket (k, alpha) of every stage is computed once
+// per (job, step, stage) in FP64 by a small kernel and read as a warp-uniform
+// broadcast.  Two kernels:
+//   * gather: nodes read through L1/L2 (any field size, 2D and 3D);
+//   * ring (2D): a block keeps three whole frames in shared memory, staged by
+//     bulk asynchronous copies (cp.async.bulk + mbarrier) and prefetched one
+//     step ahead, so the stage evaluations read shared memory only.
+#include "lcs_internal.cuh"
+
+#include <math.h>
+
+// ===================================================================== schedule
+
+// Stage time of (step n, stage s): t_n = t0 + n h; s = 0: t_n, 1: t_n + h/2, 2: t_n + h.
+// Round-to-nearest FP64 operations, no fused multiply-add.
+__device__ __forceinline__ double stage_time(double t0, double h, int n, int s)
+{
+    double t = __dadd_rn(t0, __dmul_rn((double)n, h));
+    if (s == 1) t = __dadd_rn(t, __dmul_rn(0.5, h));
+    if (s == 2) t = __dadd_rn(t, h);
+    return t;
+}
+
+// frame bracket: largest k with t_k <= t (after the periodic wrap), clamped to [0, nf-2];
+// alpha = (t - t_k) / (t_{k+1} - t_k), clamped to [0, 1] unless time is periodic
+__device__ void frame_bracket(const double *__restrict__ times, int nf, int tp, double period, double t,
+                              int *k, double *alpha)
+{
+    if (nf <= 1) {
+        *k = 0;
+        *alpha = 0.0;
+        return;
+    }
+    double tt = t;
+    if (tp) tt = __dsub_rn(t, __dmul_rn(period, floor(__ddiv_rn(__dsub_rn(t, times[0]), period))));
+    int lo = 0, hi = nf - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (times[mid] <= tt)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    int kk = lo < nf - 2 ? lo : nf - 2;
+    double a = __ddiv_rn(__dsub_rn(tt, times[kk]), __dsub_rn(times[kk + 1], times[kk]));
+    if (!tp) a = fmin(fmax(a, 0.0), 1.0);
+    *k = kk;
+    *alpha = a;
+}
+
+__global__ void rk4_schedule_kernel(const double *__restrict__ times, int nf, int tp, double period,
+                                    const JobTable J, JobDev D, SchedEntry *__restrict__ sched)
+{
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int nsm = J.nsteps_max;
+    long long total = (long long)J.njobs * nsm * 3;
+    if (idx < J.njobs) {
+        int j = (int)idx;
+        D.nsteps[j] = J.nsteps[j];
+        D.h[j] = __double2float_rn(J.h[j]);
+        D.t0[j] = __double2float_rn(J.t0[j]);
+        D.tend[j] = __double2float_rn(__dadd_rn(J.t0[j], J.T[j]));
+        D.absT[j] = fabs(J.T[j]);
+    }
+    if (idx >= total) return;
+    int s = (int)(idx % 3);
+    int n = (int)((idx / 3) % nsm);
+    int job = (int)(idx / (3LL * nsm));
+    SchedEntry e = {0, 0.0f};
+    if (n < J.nsteps[job]) {
+        int k;
+        double a;
+        frame_bracket(times, nf, tp, period, stage_time(J.t0[job], J.h[job], n, s), &k, &a);
+        e.k = k;
+        e.a = __double2float_rn(a);
+    }
+    sched[idx] = e;
+}
+
+cudaError_t launch_rk4_schedule(const double *d_times, int nframes, int time_periodic, double period,
+                                const JobTable &J, JobDev D, SchedEntry *d_sched, cudaStream_t s)
+{
+    long long total = (long long)J.njobs * J.nsteps_max * 3;
+    if (total < J.njobs) total = J.njobs;
+    if (total == 0) return cudaSuccess;
+    int bt = 256;
+    unsigned grid = (unsigned)((total + bt - 1) / bt);
+    rk4_schedule_kernel<<<grid, bt, 0, s>>>(d_times, nframes, time_periodic, period, J, D, d_sched);
+    return cudaGetLastError();
+}
+
+// ================================================================ node loads
+
+// Node v of a frame -> FP32 components.  Storage: 2D = 2 components, 3D = 4
+// (the 4th is padding); FP16/BF16 are widened to FP32.
+template <int DIM, int ST>
+struct Node;
+
+template <>
+struct Node<2, LCS_F32> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *u)
+    {
+        float2 t = __ldg(reinterpret_cast<const float2 *>(f) + v);
+        u[0] = t.x;
+        u[1] = t.y;
+    }
+    static __device__ __forceinline__ void lds(const char *f, int v, float *u)
+    {
+        float2 t = reinterpret_cast<const float2 *>(f)[v];
+        u[0] = t.x;
+        u[1] = t.y;
+    }
+};
+
+template <>
+struct Node<3, LCS_F32> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *u)
+    {
+        float4 t = __ldg(reinterpret_cast<const float4 *>(f) + v);
+        u[0] = t.x;
+        u[1] = t.y;
+        u[2] = t.z;
+    }
+};
+
+__device__ __forceinline__ float2 h2f(unsigned r)
+{
+    __half2 h = *reinterpret_cast<__half2 *>(&r);
+    return __half22float2(h);
+}
+
+__device__ __forceinline__ float2 b2f(unsigned r)
+{
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&r);
+    return __bfloat1622float2(h);
+}
+
+template <>
+struct Node<2, LCS_F16> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *u)
+    {
+        float2 t = h2f(__ldg(reinterpret_cast<const unsigned *>(f) + v));
+        u[0] = t.x;
+        u[1] = t.y;
+    }
+    static __device__ __forceinline__ void lds(const char *f, int v, float *u)
+    {
+        float2 t = h2f(reinterpret_cast<const unsigned *>(f)[v]);
+        u[0] = t.x;
+        u[1] = t.y;
+    }
+};
+
+template <>
+struct Node<2, LCS_BF16> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *u)
+    {
+        float2 t = b2f(__ldg(reinterpret_cast<const unsigned *>(f) + v));
+        u[0] = t.x;
+        u[1] = t.y;
+    }
+    static __device__ __forceinline__ void lds(const char *f, int v, float *u)
+    {
+        float2 t = b2f(reinterpret_cast<const unsigned *>(f)[v]);
+        u[0] = t.x;
+        u[1] = t.y;
+    }
+};
+
+template <>
+struct Node<3, LCS_F16> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *u)
+    {
+        uint2 r = __ldg(reinterpret_cast<const uint2 *>(f) + v);
+        float2 a = h2f(r.x), b = h2f(r.y);
+        u[0] = a.x;
+        u[1] = a.y;
+        u[2] = b.x;
+    }
+};
+
+template <>
+struct Node<3, LCS_BF16> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *u)
+    {
+        uint2 r = __ldg(reinterpret_cast<const uint2 *>(f) + v);
+        float2 a = b2f(r.x), b = b2f(r.y);
+        u[0] = a.x;
+        u[1] = a.y;
+        u[2] = b.x;
+    }
+};
+
+// ============================================================ interpolation
+
+// Cell along axis d.  Non-periodic: clamp the query into the box, cell i with
+// node_i <= x < node_{i+1}, the last cell closed.  Periodic: wrap the index.
+__device__ __forceinline__ void axis_cell(const RectParams &P, int d, float x, int &i0, int &i1, float &f)
+{
+    if (P.periodic[d]) {
+        float s = (x - P.origin[d]) * P.inv_h[d];
+        float fl = floorf(s);
+        int i = (int)fl;
+        f = s - fl;
+        int n = P.n[d];
+        if (i < 0 || i >= n) {
+            i %= n;
+            if (i < 0) i += n;
+        }
+        i0 = i;
+        i1 = (i + 1 == n) ? 0 : i + 1;
+    } else {
+        float xc = fminf(fmaxf(x, P.origin[d]), P.hi_node[d]);
+        float s = (xc - P.origin[d]) * P.inv_h[d];
+        int i = min((int)s, P.n[d] - 2);
+        f = s - (float)i;
+        i0 = i;
+        i1 = i + 1;
+    }
+}
+
+// Spatial corners and weights of x (bilinear: 4, trilinear: 8).
+template <int DIM>
+struct Stencil {
+    int v[1 << DIM];
+    float w[1 << DIM];
+};
+
+template <int DIM>
+__device__ __forceinline__ void make_stencil(const RectParams &P, const float *x, Stencil<DIM> &S)
+{
+    int i0, i1, j0, j1;
+    float fx, fy;
+    axis_cell(P, 0, x[0], i0, i1, fx);
+    axis_cell(P, 1, x[1], j0, j1, fy);
+    float gx = 1.0f - fx, gy = 1.0f - fy;
+    int r0 = j0 * (int)P.sy, r1 = j1 * (int)P.sy;
+    if constexpr (DIM == 2) {
+        S.v[0] = i0 + r0;
+        S.v[1] = i1 + r0;
+        S.v[2] = i0 + r1;
+        S.v[3] = i1 + r1;
+        S.w[0] = gx * gy;
+        S.w[1] = fx * gy;
+        S.w[2] = gx * fy;
+        S.w[3] = fx * fy;
+    } else {
+        int k0, k1;
+        float fz;
+        axis_cell(P, 2, x[2], k0, k1, fz);
+        float gz = 1.0f - fz;
+        int p0 = k0 * (int)P.sz, p1 = k1 * (int)P.sz;
+        S.v[0] = i0 + r0 + p0;
+        S.v[1] = i1 + r0 + p0;
+        S.v[2] = i0 + r1 + p0;
+        S.v[3] = i1 + r1 + p0;
+        S.v[4] = i0 + r0 + p1;
+        S.v[5] = i1 + r0 + p1;
+        S.v[6] = i0 + r1 + p1;
+        S.v[7] = i1 + r1 + p1;
+        float a = gy * gz, b = fy * gz, c = gy * fz, d = fy * fz;
+        S.w[0] = gx * a;
+        S.w[1] = fx * a;
+        S.w[2] = gx * b;
+        S.w[3] = fx * b;
+        S.w[4] = gx * c;
+        S.w[5] = fx * c;
+        S.w[6] = gx * d;
+        S.w[7] = fx * d;
+    }
+}
+
+// u = (1 - a) I[frame fa](x) + a I[frame fb](x); frame fb is not read when a == 0
+template <int DIM, int ST, bool SMEM>
+__device__ __forceinline__ void interp(const Stencil<DIM> &S, const char *fa, const char *fb, float a, float *u)
+{
+    float ua[DIM], ub[DIM], v[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) ua[c] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < (1 << DIM); ++q) {
+        if constexpr (SMEM)
+            Node<DIM, ST>::lds(fa, S.v[q], v);
+        else
+            Node<DIM, ST>::ld(fa, S.v[q], v);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) ua[c] = fmaf(S.w[q], v[c], ua[c]);
+    }
+    if (a == 0.0f) {
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) u[c] = ua[c];
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) ub[c] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < (1 << DIM); ++q) {
+        if constexpr (SMEM)
+            Node<DIM, ST>::lds(fb, S.v[q], v);
+        else
+            Node<DIM, ST>::ld(fb, S.v[q], v);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) ub[c] = fmaf(S.w[q], v[c], ub[c]);
+    }
+    float g = 1.0f - a;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) u[c] = fmaf(a, ub[c], g * ua[c]);
+}
+
+struct Rk4Args {
+    const float *seeds;
+    long long N;
+    int nsteps_max;
+    const SchedEntry *sched;
+    const int *job_nsteps;
+    const float *job_h;
+    const float *job_t0;
+    const float *job_tend;
+    float *out_xyz;
+    unsigned char *out_status;
+    float *out_texit;
+};
+
+__device__ __forceinline__ SchedEntry load_sched(const SchedEntry *p)
+{
+    int2 r = __ldg(reinterpret_cast<const int2 *>(p));
+    SchedEntry e;
+    e.k = r.x;
+    e.a = __int_as_float(r.y);
+    return e;
+}
+
+// periodic axes: keep x in [origin, origin + L) with an integer count of periods
+template <int DIM>
+__device__ __forceinline__ void wrap_periodic(const RectParams &P, float *x, int *img)
+{
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        if (!P.periodic[d]) continue;
+        float hiL = P.origin[d] + P.L[d];
+        if (x[d] >= hiL) {
+            x[d] -= P.L[d];
+            img[d] += 1;
+        } else if (x[d] < P.origin[d]) {
+            x[d] += P.L[d];
+            img[d] -= 1;
+        }
+        if (!(x[d] >= P.origin[d] && x[d] < hiL) && isfinite(x[d])) {  // far outside: full reduction
+            float m = floorf((x[d] - P.origin[d]) / P.L[d]);
+            x[d] -= m * P.L[d];
+            img[d] += (int)m;
+            if (x[d] >= hiL) x[d] = P.origin[d];
+        }
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ bool rect_left(const RectParams &P, const float *x)
+{
+    bool out = false;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+        if (!P.periodic[d]) out |= (x[d] < P.left_lo[d]) || (x[d] > P.left_hi[d]);
+    return out;
+}
+
+template <int DIM>
+__device__ __forceinline__ void store_tracer(const RectParams &P, const Rk4Args &A, int job, long long i,
+                                             const float *x, const int *img, unsigned char st, float te)
+{
+    float *o = A.out_xyz + (size_t)job * DIM * A.N;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o[d * A.N + i] = P.periodic[d] ? fmaf((float)img[d], P.L[d], x[d]) : x[d];
+    A.out_status[(size_t)job * A.N + i] = st;
+    A.out_texit[(size_t)job * A.N + i] = te;
+}
+
+// one RK4 step; stage frames given by (fa, fb, a) triples
+template <int DIM, int ST, bool SMEM>
+__device__ __forceinline__ void rk4_step(const RectParams &P, float *x, float h, const char *fa0, const char *fb0,
+                                         float a0, const char *fa1, const char *fb1, float a1, const char *fa2,
+                                         const char *fb2, float a2)
+{
+    float k1[DIM], k2[DIM], k3[DIM], k4[DIM], y[DIM];
+    Stencil<DIM> S;
+    const float hh = 0.5f * h;
+    make_stencil<DIM>(P, x, S);
+    interp<DIM, ST, SMEM>(S, fa0, fb0, a0, k1);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) y[c] = fmaf(hh, k1[c], x[c]);
+    make_stencil<DIM>(P, y, S);
+    interp<DIM, ST, SMEM>(S, fa1, fb1, a1, k2);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) y[c] = fmaf(hh, k2[c], x[c]);
+    make_stencil<DIM>(P, y, S);
+    interp<DIM, ST, SMEM>(S, fa1, fb1, a1, k3);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) y[c] = fmaf(h, k3[c], x[c]);
+    make_stencil<DIM>(P, y, S);
+    interp<DIM, ST, SMEM>(S, fa2, fb2, a2, k4);
+    const float h6 = h * (1.0f / 6.0f);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
+}
+
+// ============================================================ gather kernel
+
+template <int DIM, int ST>
+__global__ void __launch_bounds__(256) rk4_gather_kernel(RectParams P, const char *__restrict__ frames,
+                                                         size_t fstride, Rk4Args A)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int job = blockIdx.y;
+    if (i >= A.N) return;
+    float x[DIM];
+    int img[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        x[d] = A.seeds[d * A.N + i];
+        img[d] = 0;
+    }
+    wrap_periodic<DIM>(P, x, img);
+    const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
+    const int ns = A.job_nsteps[job];
+    const float h = A.job_h[job];
+    unsigned char st = LCS_TRACER_OK;
+    float te = A.job_tend[job];
+    for (int n = 0; n < ns; ++n) {
+        SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
+        rk4_step<DIM, ST, false>(P, x, h, frames + (size_t)e0.k * fstride, frames + (size_t)(e0.k + 1) * fstride,
+                                 e0.a, frames + (size_t)e1.k * fstride, frames + (size_t)(e1.k + 1) * fstride, e1.a,
+                                 frames + (size_t)e2.k * fstride, frames + (size_t)(e2.k + 1) * fstride, e2.a);
+        wrap_periodic<DIM>(P, x, img);
+        if (rect_left<DIM>(P, x)) {
+            st = LCS_TRACER_LEFT;
+            te = fmaf((float)(n + 1), h, A.job_t0[job]);
+            break;
+        }
+    }
+    store_tracer<DIM>(P, A, job, i, x, img, st, te);
+}
+
+// ============================================================== ring kernel
+
+// Three frame slots in shared memory, tagged with the frame they hold.  Thread 0
+// makes the frames of step n resident (bulk copies into slots no stage of step n
+// needs), prefetches those of step n + 1 into a free slot, and publishes the
+// slot of every stage frame; a frame that cannot get a slot is read from global
+// memory for that step.
+#define RING_SLOTS 3
+#define RING_GLOBAL (-2)
+#define RING_NONE (-1)
+
+struct RingState {
+    uint64_t bar[RING_SLOTS];
+    int tag[RING_SLOTS];
+    unsigned nload[RING_SLOTS];
+    int slot[6];   // per stage (0..2): slot of frame k, slot of frame k + 1 (or NONE / GLOBAL)
+    int kf[6];     // frame ids for the GLOBAL case
+    int abort;     // a wait timed out: the block stops issuing copies and computing
+};
+
+__device__ __forceinline__ int ring_find(const RingState &R, int f)
+{
+    for (int s = 0; s < RING_SLOTS; ++s)
+        if (R.tag[s] == f) return s;
+    return -1;
+}
+
+// frames a step reads: k of each stage, and k + 1 where alpha != 0
+__device__ __forceinline__ int step_frames(const SchedEntry *e, int *F)
+{
+    int m = 0;
+    for (int s = 0; s < 3; ++s) {
+        int c[2] = {e[s].k, e[s].a != 0.0f ? e[s].k + 1 : -1};
+        for (int q = 0; q < 2; ++q) {
+            if (c[q] < 0) continue;
+            bool dup = false;
+            for (int r = 0; r < m; ++r) dup |= (F[r] == c[q]);
+            if (!dup) F[m++] = c[q];
+        }
+    }
+    return m;
+}
+
+__device__ __forceinline__ bool in_list(const int *F, int m, int f)
+{
+    for (int r = 0; r < m; ++r)
+        if (F[r] == f) return true;
+    return false;
+}
+
+// thread 0: load frame f into a slot that holds none of the protected frames
+__device__ int ring_load(RingState &R, char *slots, const char *frames, size_t fstride, int f, const int *keep,
+                         int nkeep, unsigned *errword)
+{
+    int v = -1;
+    for (int s = 0; s < RING_SLOTS && v < 0; ++s)
+        if (R.tag[s] < 0) v = s;
+    for (int s = 0; s < RING_SLOTS && v < 0; ++s)
+        if (!in_list(keep, nkeep, R.tag[s])) v = s;
+    if (v < 0) return RING_GLOBAL;
+    if (R.nload[v] > 0 && !mbar_wait_bounded(&R.bar[v], (R.nload[v] - 1) & 1)) {  // previous copy into v
+        atomicOr(errword, LCS_ERRBIT_TIMEOUT);
+        R.abort = 1;
+        return RING_GLOBAL;
+    }
+    R.tag[v] = f;
+    R.nload[v] += 1;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&R.bar[v], (unsigned)fstride);
+    bulk_g2s(slots + (size_t)v * fstride, frames + (size_t)f * fstride, (unsigned)fstride, &R.bar[v]);
+    return v;
+}
+
+template <int ST>
+__global__ void __launch_bounds__(512) rk4_ring2d_kernel(RectParams P, const char *__restrict__ frames,
+                                                         size_t fstride, Rk4Args A, unsigned *errword)
+{
+    extern __shared__ __align__(128) char slots[];
+    __shared__ RingState R;
+    const int tid = threadIdx.x;
+    const long long i = blockIdx.x * (long long)blockDim.x + tid;
+    const int job = blockIdx.y;
+    const bool active = i < A.N;
+    if (tid == 0) {
+        for (int s = 0; s < RING_SLOTS; ++s) {
+            mbar_init(&R.bar[s], 1);
+            R.tag[s] = -1;
+            R.nload[s] = 0;
+        }
+        R.abort = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    float x[2] = {0.0f, 0.0f};
+    int img[2] = {0, 0};
+    if (active) {
+        x[0] = A.seeds[i];
+        x[1] = A.seeds[A.N + i];
+    }
+    wrap_periodic<2>(P, x, img);
+    const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
+    const int ns = A.job_nsteps[job];
+    const float h = A.job_h[job];
+    unsigned char st = LCS_TRACER_OK;
+    float te = A.job_tend[job];
+    bool live = active;
+    for (int n = 0; n < ns; ++n) {
+        __syncthreads();  // every thread is done with the previous step's slots
+        if (R.abort) break;
+        if (tid == 0) {
+            SchedEntry e[3] = {sc[3 * n], sc[3 * n + 1], sc[3 * n + 2]};
+            int F[6], Fn[6];
+            int m = step_frames(e, F);
+            for (int r = 0; r < m; ++r)
+                if (ring_find(R, F[r]) < 0) ring_load(R, slots, frames, fstride, F[r], F, m, errword);
+            for (int s = 0; s < 3; ++s) {
+                int fa = e[s].k, fb = e[s].k + 1;
+                int sa = ring_find(R, fa);
+                R.slot[2 * s] = sa >= 0 ? sa : RING_GLOBAL;
+                R.kf[2 * s] = fa;
+                if (e[s].a != 0.0f) {
+                    int sb = ring_find(R, fb);
+                    R.slot[2 * s + 1] = sb >= 0 ? sb : RING_GLOBAL;
+                } else {
+                    R.slot[2 * s + 1] = RING_NONE;
+                }
+                R.kf[2 * s + 1] = fb;
+            }
+            if (n + 1 < ns) {  // prefetch the next step's frames into slots this step leaves alone
+                SchedEntry en[3] = {sc[3 * n + 3], sc[3 * n + 4], sc[3 * n + 5]};
+                int mn = step_frames(en, Fn);
+                int keep[12];
+                int nk = 0;
+                for (int r = 0; r < m; ++r) keep[nk++] = F[r];
+                for (int r = 0; r < mn; ++r) keep[nk++] = Fn[r];
+                for (int r = 0; r < mn; ++r)
+                    if (ring_find(R, Fn[r]) < 0) ring_load(R, slots, frames, fstride, Fn[r], keep, nk, errword);
+            }
+        }
+        __syncthreads();
+        // wait for the copies this step reads
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            int s = R.slot[q];
+            if (s >= 0 && !R.abort && !mbar_wait_bounded(&R.bar[s], (R.nload[s] - 1) & 1)) {
+                atomicOr(errword, LCS_ERRBIT_TIMEOUT);
+                R.abort = 1;
+            }
+        }
+        if (!live || R.abort) continue;
+        const char *p[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            int s = R.slot[q];
+            p[q] = s >= 0 ? slots + (size_t)s * fstride : frames + (size_t)R.kf[q] * fstride;
+        }
+        const SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
+        bool all_smem = (R.slot[0] != RING_GLOBAL) && (R.slot[1] != RING_GLOBAL) && (R.slot[2] != RING_GLOBAL) &&
+                        (R.slot[3] != RING_GLOBAL) && (R.slot[4] != RING_GLOBAL) && (R.slot[5] != RING_GLOBAL);
+        if (all_smem)
+            rk4_step<2, ST, true>(P, x, h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
+        else
+            rk4_step<2, ST, false>(P, x, h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
+        wrap_periodic<2>(P, x, img);
+        if (rect_left<2>(P, x)) {
+            st = LCS_TRACER_LEFT;
+            te = fmaf((float)(n + 1), h, A.job_t0[job]);
+            live = false;
+        }
+    }
+    // drain copies still in flight (prefetches nobody read) before the block exits
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < RING_SLOTS; ++s)
+            if (R.nload[s] > 0 && !mbar_wait_bounded(&R.bar[s], (R.nload[s] - 1) & 1))
+                atomicOr(errword, LCS_ERRBIT_TIMEOUT);
+    __syncthreads();
+    if (active) store_tracer<2>(P, A, job, i, x, img, st, te);
+}
+
+// ================================================================ dispatch
+
+RectParams make_rect_params(const lcs_field *f)
+{
+    RectParams P;
+    for (int d = 0; d < 3; ++d) {
+        int dd = d < f->dim ? d : 0;
+        P.n[d] = f->n[dd];
+        P.periodic[d] = d < f->dim ? f->periodic[d] : 0;
+        P.origin[d] = (float)f->origin[dd];
+        P.inv_h[d] = (float)(1.0 / f->spacing[dd]);
+        P.hi_node[d] = (float)(f->origin[dd] + (f->n[dd] - 1) * f->spacing[dd]);
+        P.left_lo[d] = (float)(f->origin[dd] - f->spacing[dd]);
+        P.left_hi[d] = (float)(f->origin[dd] + f->n[dd] * f->spacing[dd]);
+        P.L[d] = (float)(f->n[dd] * f->spacing[dd]);
+    }
+    P.sy = f->n[0];
+    P.sz = (long long)f->n[0] * f->n[1];
+    P.fstride = (long long)(f->frame_stride / (f->vec * f->elem_bytes));
+    return P;
+}
+
+template <int DIM, int ST>
+static cudaError_t launch_gather(const RectParams &P, const lcs_field *f, const Rk4Args &A, int njobs, int bt,
+                                 cudaStream_t s)
+{
+    dim3 grid((unsigned)((A.N + bt - 1) / bt), (unsigned)njobs);
+    rk4_gather_kernel<DIM, ST><<<grid, bt, 0, s>>>(P, (const char *)f->d_frames, f->frame_stride, A);
+    return cudaGetLastError();
+}
+
+template <int ST>
+static cudaError_t launch_ring(lcs_ctx *ctx, const RectParams &P, const lcs_field *f, const Rk4Args &A, int njobs,
+                               int bt, cudaStream_t s)
+{
+    size_t smem = RING_SLOTS * f->frame_stride;
+    cudaError_t e = cudaFuncSetAttribute(rk4_ring2d_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((A.N + bt - 1) / bt), (unsigned)njobs);
+    rk4_ring2d_kernel<ST><<<grid, bt, smem, s>>>(P, (const char *)f->d_frames, f->frame_stride, A, ctx->d_errword);
+    return cudaGetLastError();
+}
+
+int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
+{
+    const lcs_field *f = L.field;
+    RectParams P = make_rect_params(f);
+    Rk4Args A;
+    A.seeds = L.seeds;
+    A.N = L.N;
+    A.nsteps_max = L.nsteps_max;
+    A.sched = L.sched;
+    A.job_nsteps = L.job_nsteps;
+    A.job_h = L.job_h;
+    A.job_t0 = L.job_t0;
+    A.job_tend = L.job_tend;
+    A.out_xyz = L.out_xyz;
+    A.out_status = L.out_status;
+    A.out_texit = L.out_texit;
+    if (L.N == 0 || L.njobs == 0) return 1;
+    bool ring_fits = f->dim == 2 && RING_SLOTS * f->frame_stride <= ctx->smem_optin;
+    int variant = L.variant;
+    if (variant == 0) variant = ring_fits ? 2 : 1;
+    if (variant == 2 && !ring_fits) variant = 1;
+    cudaError_t e;
+    if (variant == 2) {
+        int bt = L.block_threads > 0 ? L.block_threads : 512;
+        if (bt > 512) bt = 512;
+        if (f->storage == LCS_F32)
+            e = launch_ring<LCS_F32>(ctx, P, f, A, L.njobs, bt, s);
+        else if (f->storage == LCS_F16)
+            e = launch_ring<LCS_F16>(ctx, P, f, A, L.njobs, bt, s);
+        else
+            e = launch_ring<LCS_BF16>(ctx, P, f, A, L.njobs, bt, s);
+    } else {
+        int bt = L.block_threads > 0 ? L.block_threads : 256;
+        if (bt > 256) bt = 256;
+        if (f->dim == 2) {
+            if (f->storage == LCS_F32)
+                e = launch_gather<2, LCS_F32>(P, f, A, L.njobs, bt, s);
+            else if (f->storage == LCS_F16)
+                e = launch_gather<2, LCS_F16>(P, f, A, L.njobs, bt, s);
+            else
+                e = launch_gather<2, LCS_BF16>(P, f, A, L.njobs, bt, s);
+        } else {
+            if (f->storage == LCS_F32)
+                e = launch_gather<3, LCS_F32>(P, f, A, L.njobs, bt, s);
+            else if (f->storage == LCS_F16)
+                e = launch_gather<3, LCS_F16>(P, f, A, L.njobs, bt, s);
+            else
+                e = launch_gather<3, LCS_BF16>(P, f, A, L.njobs, bt, s);
+        }
+    }
+    return e == cudaSuccess ? variant : -1;
+}

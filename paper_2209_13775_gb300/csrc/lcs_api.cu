@@ -1,0 +1,593 @@
+// lcs_api.cu -- the C ABI of liblcs (declared in include/lcs.h): handles,
+// argument checks, device memory, and the order of launches for each call.
+//
+// Paper passages per call are given in lcs.h.  This file holds only host logic
+// plus the two bulk conversion kernels (frame storage, seed lattice).
+#include "lcs_internal.cuh"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+// ------------------------------------------------------------------- errors
+
+static lcs_status fail(lcs_ctx *ctx, lcs_status st, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                                        \
+    do {                                                                                           \
+        cudaError_t e__ = (call);                                                                  \
+        if (e__ != cudaSuccess)                                                                    \
+            return fail((ctx), e__ == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e__));                                           \
+    } while (0)
+
+// ------------------------------------------------------------------ context
+
+extern "C" lcs_status lcs_create(lcs_ctx **out, int device, void *stream)
+{
+    if (!out) return LCS_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return LCS_EINVAL;
+    lcs_ctx *c = new (std::nothrow) lcs_ctx();
+    if (!c) return LCS_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    int sms = 0, optin = 0;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+        cudaMalloc(&c->d_errword, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(c->d_errword, 0, sizeof(unsigned)) != cudaSuccess) {
+        if (c->d_errword) cudaFree(c->d_errword);
+        delete c;
+        return LCS_ECUDA;
+    }
+    c->num_sms = sms;
+    c->smem_optin = (size_t)optin - 1024;  // room for the kernels' static shared state
+    *out = c;
+    return LCS_OK;
+}
+
+extern "C" void lcs_destroy(lcs_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->d_errword) cudaFree(ctx->d_errword);
+    if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+    delete ctx;
+}
+
+extern "C" const char *lcs_last_error(const lcs_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+extern "C" lcs_status lcs_set_stream(lcs_ctx *ctx, void *stream)
+{
+    if (!ctx) return LCS_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_synchronize(lcs_ctx *ctx)
+{
+    if (!ctx) return LCS_EINVAL;
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    unsigned w = 0;
+    CUDA_TRY(ctx, cudaMemcpy(&w, ctx->d_errword, sizeof w, cudaMemcpyDeviceToHost));
+    if (w) {
+        CUDA_TRY(ctx, cudaMemset(ctx->d_errword, 0, sizeof w));
+        if (w & LCS_ERRBIT_TIMEOUT) return fail(ctx, LCS_ETIMEOUT, "a device-side wait gave up");
+        if (w & LCS_ERRBIT_WALK) return fail(ctx, LCS_EWALK, "a tet walk exceeded walk_limit");
+        if (w & LCS_ERRBIT_MAXSTEPS) return fail(ctx, LCS_EMAXSTEPS, "an adaptive integration hit max_steps");
+    }
+    return LCS_OK;
+}
+
+// grow the context's reusable device scratch to at least `bytes`
+static lcs_status scratch_reserve(lcs_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->scratch_bytes) return LCS_OK;
+    if (ctx->d_scratch) {
+        CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaFree(ctx->d_scratch);
+        ctx->d_scratch = nullptr;
+        ctx->scratch_bytes = 0;
+    }
+    size_t b = std::max(bytes, (size_t)1 << 20);
+    CUDA_TRY(ctx, cudaMalloc(&ctx->d_scratch, b));
+    ctx->scratch_bytes = b;
+    return LCS_OK;
+}
+
+// ----------------------------------------------------------- frame storage
+
+// FP32 [nframes][nodes][dim] -> [nframes][frame_stride bytes] of `vec` stored components
+template <typename T>
+__device__ __forceinline__ T to_store(float v);
+template <>
+__device__ __forceinline__ float to_store<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+template <typename T>
+__global__ void convert_rect_kernel(const float *__restrict__ src, int nframes, long long nodes, int dim, int vec,
+                                    size_t frame_stride, char *__restrict__ dst)
+{
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)nframes * nodes) return;
+    long long f = idx / nodes, v = idx % nodes;
+    T *o = reinterpret_cast<T *>(dst + (size_t)f * frame_stride) + v * vec;
+    const float *s = src + idx * dim;
+    for (int c = 0; c < vec; ++c) o[c] = to_store<T>(c < dim ? s[c] : 0.0f);
+}
+
+cudaError_t launch_convert_rect(const float *src, int nframes, long long nodes, int dim, int vec, int storage,
+                                size_t frame_stride, void *dst, cudaStream_t s)
+{
+    long long total = (long long)nframes * nodes;
+    if (total == 0) return cudaSuccess;
+    int bt = 256;
+    unsigned grid = (unsigned)((total + bt - 1) / bt);
+    if (storage == LCS_F32)
+        convert_rect_kernel<float><<<grid, bt, 0, s>>>(src, nframes, nodes, dim, vec, frame_stride, (char *)dst);
+    else if (storage == LCS_F16)
+        convert_rect_kernel<__half><<<grid, bt, 0, s>>>(src, nframes, nodes, dim, vec, frame_stride, (char *)dst);
+    else
+        convert_rect_kernel<__nv_bfloat16>
+            <<<grid, bt, 0, s>>>(src, nframes, nodes, dim, vec, frame_stride, (char *)dst);
+    return cudaGetLastError();
+}
+
+static lcs_status upload_frames(lcs_ctx *ctx, lcs_field *f, const float *frames, int on_device)
+{
+    size_t n_in = (size_t)f->nframes * f->nodes * f->dim;
+    const float *src = frames;
+    float *tmp = nullptr;
+    if (!on_device) {
+        CUDA_TRY(ctx, cudaMallocAsync((void **)&tmp, n_in * sizeof(float), ctx->stream));
+        cudaError_t e = cudaMemcpyAsync(tmp, frames, n_in * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(tmp, ctx->stream);
+            return fail(ctx, LCS_ECUDA, "frame upload: %s", cudaGetErrorString(e));
+        }
+        src = tmp;
+    }
+    cudaError_t e = launch_convert_rect(src, f->nframes, f->nodes, f->dim, f->vec, f->storage, f->frame_stride,
+                                        f->d_frames, ctx->stream);
+    if (tmp) cudaFreeAsync(tmp, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "frame conversion: %s", cudaGetErrorString(e));
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *d, const float *frames,
+                                     int frames_on_device, lcs_field **out)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!d || !frames || !out) return fail(ctx, LCS_EINVAL, "lcs_load_field: null argument");
+    *out = nullptr;
+    if (d->kind != LCS_RECTILINEAR) return fail(ctx, LCS_EUNSUPPORTED, "lcs_load_field: tet meshes not built in");
+    if (d->dim != 2 && d->dim != 3) return fail(ctx, LCS_EINVAL, "lcs_load_field: dim must be 2 or 3");
+    if (d->storage < LCS_F32 || d->storage > LCS_BF16) return fail(ctx, LCS_EINVAL, "lcs_load_field: storage");
+    if (d->nframes < 1 || !d->frame_times) return fail(ctx, LCS_EINVAL, "lcs_load_field: need >= 1 frame");
+    for (int k = 1; k < d->nframes; ++k)
+        if (!(d->frame_times[k] > d->frame_times[k - 1]))
+            return fail(ctx, LCS_EINVAL, "lcs_load_field: frame_times must increase");
+    if (d->time_periodic && !(d->period > 0.0)) return fail(ctx, LCS_EINVAL, "lcs_load_field: period must be > 0");
+    long long nodes = 1;
+    for (int a = 0; a < d->dim; ++a) {
+        int minn = d->periodic[a] ? 3 : 2;
+        if (d->n[a] < minn) return fail(ctx, LCS_EINVAL, "lcs_load_field: axis %d needs >= %d nodes", a, minn);
+        if (!(d->spacing[a] > 0.0)) return fail(ctx, LCS_EINVAL, "lcs_load_field: spacing must be > 0");
+        nodes *= d->n[a];
+    }
+    if (nodes >= (1LL << 31)) return fail(ctx, LCS_EINVAL, "lcs_load_field: more than 2^31 nodes per frame");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    lcs_field *f = new (std::nothrow) lcs_field();
+    if (!f) return fail(ctx, LCS_ENOMEM, "host allocation");
+    f->ctx = ctx;
+    f->dim = d->dim;
+    f->kind = d->kind;
+    f->storage = d->storage;
+    for (int a = 0; a < 3; ++a) {
+        f->n[a] = a < d->dim ? d->n[a] : 1;
+        f->origin[a] = a < d->dim ? d->origin[a] : 0.0;
+        f->spacing[a] = a < d->dim ? d->spacing[a] : 1.0;
+        f->periodic[a] = a < d->dim ? (d->periodic[a] != 0) : 0;
+    }
+    f->nframes = d->nframes;
+    f->times.assign(d->frame_times, d->frame_times + d->nframes);
+    f->time_periodic = d->time_periodic != 0;
+    f->period = d->period;
+    f->nodes = nodes;
+    f->vec = d->dim == 2 ? 2 : 4;
+    f->elem_bytes = d->storage == LCS_F32 ? 4 : 2;
+    f->frame_bytes = (size_t)nodes * f->vec * f->elem_bytes;
+    f->frame_stride = (f->frame_bytes + 255) & ~(size_t)255;
+    lcs_status st = LCS_OK;
+    cudaError_t e = cudaMalloc(&f->d_frames, f->frame_stride * f->nframes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_frames, 0, f->frame_stride * f->nframes, ctx->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_times, sizeof(double) * f->nframes);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(f->d_times, f->times.data(), sizeof(double) * f->nframes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        st = fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_load_field: %s",
+                  cudaGetErrorString(e));
+    } else {
+        st = upload_frames(ctx, f, frames, frames_on_device);
+    }
+    if (st != LCS_OK) {
+        lcs_free_field(f);
+        return st;
+    }
+    *out = f;
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_update_frames(lcs_ctx *ctx, lcs_field *f, const float *frames, int frames_on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!f || !frames) return fail(ctx, LCS_EINVAL, "lcs_update_frames: null argument");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return upload_frames(ctx, f, frames, frames_on_device);
+}
+
+extern "C" void lcs_free_field(lcs_field *f)
+{
+    if (!f) return;
+    if (f->ctx) cudaSetDevice(f->ctx->device);
+    cudaFree(f->d_frames);
+    cudaFree(f->d_times);
+    cudaFree(f->d_xyz);
+    cudaFree(f->d_tets);
+    cudaFree(f->d_nbrs);
+    cudaFree(f->d_tetmap);
+    delete f;
+}
+
+// -------------------------------------------------------------- seed grid
+
+// x_i = lo + i * step with step = (hi - lo) / (n - 1) (or / n on periodic axes);
+// FP64 round-to-nearest, no fused operations, then rounded to FP32
+__global__ void seed_grid_kernel(int dim, int nx, int ny, double lo0, double lo1, double lo2, double hi0,
+                                 double hi1, double hi2, int n0, int n1, int n2, int p0, int p1, int p2,
+                                 long long N, float *__restrict__ out)
+{
+    long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (id >= N) return;
+    long long i = id % nx, j = (id / nx) % ny, k = id / ((long long)nx * ny);
+    const double lo[3] = {lo0, lo1, lo2}, hi[3] = {hi0, hi1, hi2};
+    const int n[3] = {n0, n1, n2}, per[3] = {p0, p1, p2};
+    const long long ix[3] = {i, j, k};
+    for (int a = 0; a < dim; ++a) {
+        double step;
+        if (per[a])
+            step = __ddiv_rn(__dsub_rn(hi[a], lo[a]), (double)n[a]);
+        else
+            step = n[a] > 1 ? __ddiv_rn(__dsub_rn(hi[a], lo[a]), (double)(n[a] - 1)) : 0.0;
+        double x = __dadd_rn(lo[a], __dmul_rn((double)ix[a], step));
+        out[a * N + id] = __double2float_rn(x);
+    }
+}
+
+cudaError_t launch_seed_grid(int dim, const int n[3], const double lo[3], const double hi[3], const int periodic[3],
+                             long long N, float *out, cudaStream_t s)
+{
+    if (N == 0) return cudaSuccess;
+    int bt = 256;
+    unsigned grid = (unsigned)((N + bt - 1) / bt);
+    seed_grid_kernel<<<grid, bt, 0, s>>>(dim, n[0], n[1], lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], n[0], n[1],
+                                         n[2], periodic[0], periodic[1], periodic[2], N, out);
+    return cudaGetLastError();
+}
+
+extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const lcs_field *field, lcs_seeds **out)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!d || !out) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: null argument");
+    *out = nullptr;
+    if (d->dim != 2 && d->dim != 3) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: dim must be 2 or 3");
+    if (field && field->dim != d->dim) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: dim differs from the field's");
+    if (field && field->kind == LCS_TET) return fail(ctx, LCS_EUNSUPPORTED, "lcs_seed_grid: tet location");
+    long long N = 1;
+    for (int a = 0; a < d->dim; ++a) {
+        if (d->n[a] < 1) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: n[%d] < 1", a);
+        if (!(d->hi[a] >= d->lo[a])) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: hi < lo on axis %d", a);
+        N *= d->n[a];
+    }
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    lcs_seeds *s = new (std::nothrow) lcs_seeds();
+    if (!s) return fail(ctx, LCS_ENOMEM, "host allocation");
+    s->dim = d->dim;
+    s->N = N;
+    for (int a = 0; a < 3; ++a) {
+        s->n[a] = a < d->dim ? d->n[a] : 1;
+        s->lo[a] = a < d->dim ? d->lo[a] : 0.0;
+        s->hi[a] = a < d->dim ? d->hi[a] : 0.0;
+        s->periodic[a] = a < d->dim ? (d->periodic[a] != 0) : 0;
+        if (s->periodic[a]) {
+            s->h[a] = (s->hi[a] - s->lo[a]) / s->n[a];
+            s->period[a] = s->hi[a] - s->lo[a];
+        } else {
+            s->h[a] = s->n[a] > 1 ? (s->hi[a] - s->lo[a]) / (s->n[a] - 1) : 1.0;
+            s->period[a] = 0.0;
+        }
+    }
+    cudaError_t e = cudaMalloc(&s->d_xyz, sizeof(float) * s->dim * (size_t)N);
+    if (e == cudaSuccess) e = launch_seed_grid(s->dim, s->n, s->lo, s->hi, s->periodic, N, s->d_xyz, ctx->stream);
+    if (e != cudaSuccess) {
+        lcs_free_seeds(s);
+        return fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_seed_grid: %s",
+                    cudaGetErrorString(e));
+    }
+    *out = s;
+    return LCS_OK;
+}
+
+extern "C" long long lcs_seeds_count(const lcs_seeds *s)
+{
+    return s ? s->N : 0;
+}
+
+extern "C" lcs_status lcs_seeds_get(lcs_ctx *ctx, const lcs_seeds *s, float *xyz, int *cells, int on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!s) return fail(ctx, LCS_EINVAL, "lcs_seeds_get: null seeds");
+    if (cells && !s->d_cells) return fail(ctx, LCS_EINVAL, "lcs_seeds_get: seeds carry no cell ids");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (xyz) CUDA_TRY(ctx, cudaMemcpyAsync(xyz, s->d_xyz, sizeof(float) * s->dim * s->N, k, ctx->stream));
+    if (cells) CUDA_TRY(ctx, cudaMemcpyAsync(cells, s->d_cells, sizeof(int) * s->N, k, ctx->stream));
+    if (!on_device) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return LCS_OK;
+}
+
+extern "C" void lcs_free_seeds(lcs_seeds *s)
+{
+    if (!s) return;
+    cudaFree(s->d_xyz);
+    cudaFree(s->d_cells);
+    delete s;
+}
+
+// --------------------------------------------------------------- flow map
+
+extern "C" lcs_status lcs_flowmap_create(lcs_ctx *ctx, const lcs_seeds *s, int njobs, lcs_flowmap **out)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!s || !out) return fail(ctx, LCS_EINVAL, "lcs_flowmap_create: null argument");
+    *out = nullptr;
+    if (njobs < 1 || njobs > LCS_MAX_JOBS) return fail(ctx, LCS_EINVAL, "lcs_flowmap_create: njobs in [1, %d]", LCS_MAX_JOBS);
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    lcs_flowmap *fm = new (std::nothrow) lcs_flowmap();
+    if (!fm) return fail(ctx, LCS_ENOMEM, "host allocation");
+    fm->ctx = ctx;
+    fm->seeds = s;
+    fm->dim = s->dim;
+    fm->njobs = njobs;
+    fm->N = s->N;
+    fm->T.assign(njobs, 0.0);
+    size_t N = (size_t)s->N;
+    cudaError_t e = cudaMalloc(&fm->d_xyz, sizeof(float) * fm->dim * N * njobs);
+    if (e == cudaSuccess) e = cudaMalloc(&fm->d_status, N * njobs);
+    if (e == cudaSuccess) e = cudaMalloc(&fm->d_texit, sizeof(float) * N * njobs);
+    if (e == cudaSuccess) e = cudaMalloc(&fm->d_absT, sizeof(double) * njobs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fm->d_status, LCS_TRACER_OUTSIDE, N * njobs, ctx->stream);
+    if (e != cudaSuccess) {
+        lcs_free_flowmap(fm);
+        return fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_flowmap_create: %s",
+                    cudaGetErrorString(e));
+    }
+    *out = fm;
+    return LCS_OK;
+}
+
+extern "C" void lcs_free_flowmap(lcs_flowmap *fm)
+{
+    if (!fm) return;
+    cudaFree(fm->d_xyz);
+    cudaFree(fm->d_status);
+    cudaFree(fm->d_texit);
+    cudaFree(fm->d_absT);
+    delete fm;
+}
+
+// scratch layout for one lcs_advect call
+struct AdvectScratch {
+    JobDev jd;
+    SchedEntry *sched;
+};
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
+                                  lcs_flowmap *fm, JobTable &J)
+{
+    size_t jb = align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs);
+    size_t sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
+    lcs_status st = scratch_reserve(ctx, jb + sb);
+    if (st != LCS_OK) return st;
+    char *p = (char *)ctx->d_scratch;
+    JobDev D;
+    D.nsteps = (int *)p;
+    p += align256(sizeof(int) * J.njobs);
+    D.h = (float *)p;
+    p += align256(sizeof(float) * J.njobs);
+    D.t0 = (float *)p;
+    p += align256(sizeof(float) * J.njobs);
+    D.tend = (float *)p;
+    p += align256(sizeof(float) * J.njobs);
+    D.absT = fm->d_absT;
+    SchedEntry *sched = (SchedEntry *)p;
+    CUDA_TRY(ctx, launch_rk4_schedule(f->d_times, f->nframes, f->time_periodic, f->period, J, D, sched, ctx->stream));
+    Rk4Launch L;
+    L.field = f;
+    L.seeds = s->d_xyz;
+    L.N = s->N;
+    L.njobs = J.njobs;
+    L.nsteps_max = J.nsteps_max;
+    L.sched = sched;
+    L.job_nsteps = D.nsteps;
+    L.job_h = D.h;
+    L.job_t0 = D.t0;
+    L.job_tend = D.tend;
+    L.out_xyz = fm->d_xyz;
+    L.out_status = fm->d_status;
+    L.out_texit = fm->d_texit;
+    L.block_threads = o->block_threads;
+    L.variant = o->variant;
+    if (launch_rk4_rect(ctx, L, ctx->stream) < 0)
+        return fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
+                                 lcs_flowmap *fm)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!f || !s || !o || !fm) return fail(ctx, LCS_EINVAL, "lcs_advect: null argument");
+    if (f->dim != s->dim) return fail(ctx, LCS_EINVAL, "lcs_advect: field and seeds differ in dim");
+    if (fm->seeds != s) return fail(ctx, LCS_EINVAL, "lcs_advect: flow map was made for other seeds");
+    int njobs = o->njobs > 1 ? o->njobs : 1;
+    if (njobs > fm->njobs) return fail(ctx, LCS_EINVAL, "lcs_advect: %d jobs > flow map's %d", njobs, fm->njobs);
+    if (o->njobs > 1 && (!o->job_t0 || !o->job_T)) return fail(ctx, LCS_EINVAL, "lcs_advect: job arrays missing");
+    if (o->method != LCS_RK4) return fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: method %d not built in", o->method);
+    if (f->kind != LCS_RECTILINEAR) return fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: tet RK4 not built in");
+    double adt = fabs(o->dt);
+    if (!(adt > 0.0) || !isfinite(adt)) return fail(ctx, LCS_EINVAL, "lcs_advect: dt must be finite and > 0");
+    JobTable *J = new (std::nothrow) JobTable();
+    if (!J) return fail(ctx, LCS_ENOMEM, "host allocation");
+    J->njobs = njobs;
+    J->nsteps_max = 0;
+    for (int j = 0; j < njobs; ++j) {
+        double t0 = o->njobs > 1 ? o->job_t0[j] : o->t0;
+        double T = o->njobs > 1 ? o->job_T[j] : o->T;
+        if (!isfinite(t0) || !isfinite(T)) {
+            delete J;
+            return fail(ctx, LCS_EINVAL, "lcs_advect: job %d has a non-finite t0 or T", j);
+        }
+        double r = fabs(T) / adt;
+        long long ns = (long long)floor(r + 0.5);
+        if (fabs(r - (double)ns) > 1e-9 * std::max(1.0, r) || ns > (1LL << 30)) {
+            delete J;
+            return fail(ctx, LCS_EINVAL, "lcs_advect: |T|/|dt| = %.17g is not an integer (job %d)", r, j);
+        }
+        J->t0[j] = t0;
+        J->T[j] = T;
+        J->h[j] = T < 0.0 ? -adt : adt;
+        J->nsteps[j] = (int)ns;
+        J->nsteps_max = std::max(J->nsteps_max, (int)ns);
+        fm->T[j] = T;
+    }
+    lcs_status st;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess)
+        st = fail(ctx, LCS_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    else
+        st = advect_rk4_rect(ctx, f, s, o, fm, *J);
+    delete J;
+    return st;
+}
+
+extern "C" lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *xyz,
+                                      unsigned char *status, float *t_exit, int on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!fm) return fail(ctx, LCS_EINVAL, "lcs_flowmap_get: null flow map");
+    if (job < 0 || job >= fm->njobs) return fail(ctx, LCS_EINVAL, "lcs_flowmap_get: job %d out of range", job);
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    size_t N = (size_t)fm->N;
+    if (xyz)
+        CUDA_TRY(ctx, cudaMemcpyAsync(xyz, fm->d_xyz + (size_t)job * fm->dim * N, sizeof(float) * fm->dim * N, k,
+                                      ctx->stream));
+    if (status) CUDA_TRY(ctx, cudaMemcpyAsync(status, fm->d_status + (size_t)job * N, N, k, ctx->stream));
+    if (t_exit)
+        CUDA_TRY(ctx, cudaMemcpyAsync(t_exit, fm->d_texit + (size_t)job * N, sizeof(float) * N, k, ctx->stream));
+    if (!on_device) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return LCS_OK;
+}
+
+// ------------------------------------------------------ grad F, C, FTLE
+
+static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lam, double *C,
+                          int on_device, const char *who)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!fm) return fail(ctx, LCS_EINVAL, "%s: null flow map", who);
+    if (job < -1 || job >= fm->njobs) return fail(ctx, LCS_EINVAL, "%s: job %d out of range", who, job);
+    const lcs_seeds *s = fm->seeds;
+    for (int a = 0; a < s->dim; ++a)
+        if (s->n[a] < 3) return fail(ctx, LCS_EINVAL, "%s: the lattice needs >= 3 seeds per axis", who);
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    int j0 = job < 0 ? 0 : job, nj = job < 0 ? fm->njobs : 1;
+    size_t N = (size_t)fm->N;
+    int np = fm->dim == 2 ? 3 : 6;
+    CgLaunch L;
+    L.dim = fm->dim;
+    for (int a = 0; a < 3; ++a) {
+        L.n[a] = s->n[a];
+        L.periodic[a] = s->periodic[a];
+        L.h[a] = s->h[a];
+        L.period[a] = s->period[a];
+    }
+    L.N = fm->N;
+    L.job0 = j0;
+    L.njobs = nj;
+    L.xyz = fm->d_xyz;
+    L.status = fm->d_status;
+    L.absT = fm->d_absT;
+    size_t bC = C ? sizeof(double) * np * N * nj : 0, bL = lam ? sizeof(double) * N * nj : 0,
+           bF = ftle ? sizeof(float) * N * nj : 0;
+    char *tmp = nullptr;
+    if (!on_device && (bC + bL + bF) > 0)
+        CUDA_TRY(ctx, cudaMallocAsync((void **)&tmp, align256(bC) + align256(bL) + align256(bF), ctx->stream));
+    char *q = tmp;
+    L.C = C ? (on_device ? C : (double *)q) : nullptr;
+    if (C && !on_device) q += align256(bC);
+    L.lam = lam ? (on_device ? lam : (double *)q) : nullptr;
+    if (lam && !on_device) q += align256(bL);
+    L.ftle = ftle ? (on_device ? ftle : (float *)q) : nullptr;
+    cudaError_t e = launch_cg_ftle(L, ctx->stream);
+    if (e == cudaSuccess && !on_device) {
+        if (C) e = cudaMemcpyAsync(C, L.C, bC, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && lam) e = cudaMemcpyAsync(lam, L.lam, bL, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && ftle) e = cudaMemcpyAsync(ftle, L.ftle, bF, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (tmp) cudaFreeAsync(tmp, ctx->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_cauchy_green(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double *C, int on_device)
+{
+    if (ctx && !C) return fail(ctx, LCS_EINVAL, "lcs_cauchy_green: null output");
+    return cg_call(ctx, fm, job, nullptr, nullptr, C, on_device, "lcs_cauchy_green");
+}
+
+extern "C" lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
+                               double *C, int on_device)
+{
+    if (ctx && !ftle) return fail(ctx, LCS_EINVAL, "lcs_ftle: null output");
+    return cg_call(ctx, fm, job, ftle, lambda_max, C, on_device, "lcs_ftle");
+}

@@ -1,0 +1,254 @@
+// lcs_internal.cuh -- shared declarations of liblcs's translation units.
+//
+// Library-private: handle layouts, kernel parameter blocks, launchers and the
+// small device helpers (storage loads, bounded mbarrier waits) that more than
+// one kernel file uses.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "lcs.h"
+
+// device error word bits (OR-ed by kernels, read by lcs_synchronize)
+#define LCS_ERRBIT_TIMEOUT 1u
+#define LCS_ERRBIT_WALK 2u
+#define LCS_ERRBIT_MAXSTEPS 4u
+
+// bound on any device-side wait: a copy that has not landed after this long is
+// treated as failed (error bit set, the waiting block stops its work)
+#define LCS_WAIT_LIMIT_NS 1000000000ull
+
+struct lcs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    unsigned int *d_errword = nullptr;   // device error flags
+    int num_sms = 0;
+    size_t smem_optin = 0;               // max dynamic shared memory per block
+    // scratch: device memory the library reuses across calls (queue counters)
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+struct lcs_field {
+    lcs_ctx *ctx = nullptr;
+    int dim = 0, kind = 0, storage = 0;
+    int n[3] = {1, 1, 1};
+    double origin[3] = {0, 0, 0}, spacing[3] = {1, 1, 1};
+    int periodic[3] = {0, 0, 0};
+    int nframes = 0;
+    std::vector<double> times;
+    int time_periodic = 0;
+    double period = 0.0;
+    double *d_times = nullptr;
+    // frames: [nframes][frame_stride_bytes]; node v occupies vec components
+    void *d_frames = nullptr;
+    int vec = 0;                       // stored components per node (2 in 2D, 4 in 3D)
+    size_t elem_bytes = 4;             // bytes per stored component
+    size_t frame_bytes = 0;            // unpadded bytes per frame
+    size_t frame_stride = 0;           // padded bytes per frame (multiple of 256)
+    long long nodes = 0;
+    // tetrahedral mesh
+    long long ncells = 0;
+    float4 *d_xyz = nullptr;           // [nodes]
+    int4 *d_tets = nullptr;            // [ncells]
+    int4 *d_nbrs = nullptr;            // [ncells]
+    float4 *d_tetmap = nullptr;        // [ncells][3]: rows of the inverse affine map + v0
+};
+
+struct lcs_seeds {
+    int dim = 0;
+    int n[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int periodic[3] = {0, 0, 0};
+    long long N = 0;
+    float *d_xyz = nullptr;            // [dim][N]
+    int *d_cells = nullptr;            // [N] when made on a tet field
+    double h[3] = {1, 1, 1};           // lattice step per axis
+    double period[3] = {0, 0, 0};      // hi - lo on periodic axes
+};
+
+struct lcs_flowmap {
+    lcs_ctx *ctx = nullptr;
+    const lcs_seeds *seeds = nullptr;
+    int dim = 0, njobs = 0;
+    long long N = 0;
+    float *d_xyz = nullptr;            // [njobs][dim][N]
+    unsigned char *d_status = nullptr; // [njobs][N]
+    float *d_texit = nullptr;          // [njobs][N]
+    std::vector<double> T;             // per job
+    double *d_absT = nullptr;          // [njobs] |T|, written by the schedule kernel
+};
+
+// ------------------------------------------------------------ rectilinear
+
+struct RectParams {
+    int n[3];
+    int periodic[3];
+    float origin[3];
+    float inv_h[3];
+    float hi_node[3];     // origin + (n-1) h  (clamp limit, non-periodic axes)
+    float left_lo[3];     // origin - h        (LEFT below)
+    float left_hi[3];     // origin + n h      (LEFT above)
+    float L[3];           // n h               (period, periodic axes)
+    long long sy, sz;     // node strides
+    long long fstride;    // nodes per padded frame (in stored vectors)
+};
+
+// stage schedule entry: frame k and the FP32 weight alpha of frame k+1
+struct SchedEntry {
+    int k;
+    float a;
+};
+
+// Batch of integrations passed by value to the schedule kernel (no host copy).
+#define LCS_MAX_JOBS 1024
+struct JobTable {
+    int njobs;
+    int nsteps_max;
+    double t0[LCS_MAX_JOBS];
+    double h[LCS_MAX_JOBS];     // signed step
+    double T[LCS_MAX_JOBS];     // requested horizon
+    int nsteps[LCS_MAX_JOBS];
+};
+
+// per-job values the schedule kernel leaves in device scratch for the advection kernels
+struct JobDev {
+    int *nsteps;     // [njobs]
+    float *h;        // [njobs]
+    float *t0;       // [njobs]
+    float *tend;     // [njobs]
+    double *absT;    // [njobs] (the flow map's copy, for the FTLE)
+};
+
+struct Rk4Launch {
+    const lcs_field *field;
+    const float *seeds;       // [dim][N]
+    long long N;
+    int njobs;
+    int nsteps_max;
+    const SchedEntry *sched;  // [njobs][nsteps_max][3]
+    const int *job_nsteps;    // [njobs]
+    const float *job_h;       // [njobs] signed step
+    const float *job_t0;      // [njobs]
+    const float *job_tend;    // [njobs]
+    float *out_xyz;           // [njobs][dim][N]
+    unsigned char *out_status;
+    float *out_texit;
+    int block_threads;
+    int variant;              // 1 gather, 2 shared-memory ring
+};
+
+RectParams make_rect_params(const lcs_field *f);
+
+cudaError_t launch_rk4_schedule(const double *d_times, int nframes, int time_periodic, double period,
+                                const JobTable &J, JobDev D, SchedEntry *d_sched, cudaStream_t s);
+
+// returns the variant actually used (1 or 2), or -1 on a launch error
+int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s);
+
+// ------------------------------------------------------ grad F / C / FTLE
+
+struct CgLaunch {
+    int dim;
+    int n[3];
+    int periodic[3];
+    double h[3];
+    double period[3];
+    long long N;
+    int job0, njobs;
+    const float *xyz;            // flow map base [njobs_total][dim][N]
+    const unsigned char *status; // [njobs_total][N]
+    const double *absT;          // [njobs_total] |T|
+    double *C;                   // [njobs][N][np] or null
+    double *lam;                 // [njobs][N] or null
+    float *ftle;                 // [njobs][N] or null
+};
+
+cudaError_t launch_cg_ftle(const CgLaunch &L, cudaStream_t s);
+
+// ------------------------------------------------------------------ misc
+
+cudaError_t launch_seed_grid(int dim, const int n[3], const double lo[3], const double hi[3],
+                             const int periodic[3], long long N, float *out, cudaStream_t s);
+
+cudaError_t launch_convert_rect(const float *src, int nframes, long long nodes, int dim, int vec,
+                                int storage, size_t frame_stride, void *dst, cudaStream_t s);
+
+// ---------------------------------------------------------- device helpers
+
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1D bulk copy global -> shared, completion counted on bar (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the phase with the given parity; false when the time limit ran out
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > LCS_WAIT_LIMIT_NS) return false;
+    return true;
+}
+
+#endif  // __CUDACC__

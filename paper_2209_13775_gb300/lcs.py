@@ -1,0 +1,284 @@
+"""Thin ctypes binding of liblcs (include/lcs.h), one Python function per C entry point.
+
+Argument marshalling only: numpy arrays are host buffers, torch tensors on a
+CUDA device are device buffers, and every step of the path runs in the CUDA
+library.  A non-OK status raises ``LcsError`` carrying ``lcs_last_error``.
+There is no fallback: importing this module on a machine where liblcs.so cannot
+be loaded raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RECTILINEAR, TET = 0, 1
+F32, F16, BF16 = 0, 1, 2
+RK4, RK45, SURROGATE = 0, 1, 2
+TRACER_OK, TRACER_LEFT, TRACER_OUTSIDE, TRACER_MAXSTEPS, TRACER_WALKFAIL = 0, 1, 2, 3, 4
+STATUS_NAMES = {0: "LCS_OK", 1: "LCS_EINVAL", 2: "LCS_ENOMEM", 3: "LCS_ECUDA", 4: "LCS_ETIMEOUT",
+                5: "LCS_EWALK", 6: "LCS_EMAXSTEPS", 7: "LCS_EUNSUPPORTED"}
+
+EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs_synchronize",
+           "lcs_load_field", "lcs_update_frames", "lcs_free_field", "lcs_seed_grid", "lcs_seeds_count",
+           "lcs_seeds_get", "lcs_free_seeds", "lcs_flowmap_create", "lcs_advect", "lcs_flowmap_get",
+           "lcs_free_flowmap", "lcs_cauchy_green", "lcs_ftle"]
+
+
+class LcsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class FieldDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("kind", ctypes.c_int), ("n", ctypes.c_int * 3),
+                ("origin", ctypes.c_double * 3), ("spacing", ctypes.c_double * 3),
+                ("periodic", ctypes.c_int * 3), ("nframes", ctypes.c_int),
+                ("frame_times", ctypes.c_void_p), ("time_periodic", ctypes.c_int),
+                ("period", ctypes.c_double), ("storage", ctypes.c_int),
+                ("nnodes", ctypes.c_longlong), ("ncells", ctypes.c_longlong),
+                ("node_xyz", ctypes.c_void_p), ("tets", ctypes.c_void_p), ("nbrs", ctypes.c_void_p)]
+
+
+class SeedDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("periodic", ctypes.c_int * 3)]
+
+
+class AdvectOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("t0", ctypes.c_double), ("T", ctypes.c_double),
+                ("njobs", ctypes.c_int), ("job_t0", ctypes.c_void_p), ("job_T", ctypes.c_void_p),
+                ("dt", ctypes.c_double), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+                ("h0", ctypes.c_double), ("max_steps", ctypes.c_longlong), ("walk_limit", ctypes.c_int),
+                ("block_threads", ctypes.c_int), ("variant", ctypes.c_int), ("surrogate", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load liblcs.so (building it first when missing); raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB) and build_if_missing:
+        _build.build()
+    L = ctypes.CDLL(_build.LIB)
+    P, I, LL, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_int
+    sig = {
+        "lcs_create": ([P, I, P], S), "lcs_destroy": ([P], None), "lcs_last_error": ([P], ctypes.c_char_p),
+        "lcs_set_stream": ([P, P], S), "lcs_synchronize": ([P], S),
+        "lcs_load_field": ([P, P, P, I, P], S), "lcs_update_frames": ([P, P, P, I], S),
+        "lcs_free_field": ([P], None), "lcs_seed_grid": ([P, P, P, P], S), "lcs_seeds_count": ([P], LL),
+        "lcs_seeds_get": ([P, P, P, P, I], S), "lcs_free_seeds": ([P], None),
+        "lcs_flowmap_create": ([P, P, I, P], S), "lcs_advect": ([P, P, P, P, P], S),
+        "lcs_flowmap_get": ([P, P, I, P, P, P, I], S), "lcs_free_flowmap": ([P], None),
+        "lcs_cauchy_green": ([P, P, I, P, I], S), "lcs_ftle": ([P, P, I, P, P, P, I], S),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or torch tensor; (None, 0) for None."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError("expected a numpy array or a torch tensor, got %r" % type(a))
+
+
+def _check(ctx, st):
+    if st != 0:
+        msg = load().lcs_last_error(ctx)
+        raise LcsError(st, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------- context
+
+def lcs_create(device: int = 0, stream=None):
+    """Context on `device` queuing work on `stream` (a torch.cuda.Stream, an int handle or None)."""
+    L = load()
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    out = ctypes.c_void_p()
+    st = L.lcs_create(ctypes.byref(out), int(device), ctypes.c_void_p(stream or 0))
+    if st != 0:
+        raise LcsError(st, "lcs_create(device=%d)" % device)
+    return out.value
+
+
+def lcs_destroy(ctx):
+    load().lcs_destroy(ctx)
+
+
+def lcs_last_error(ctx) -> str:
+    m = load().lcs_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def lcs_set_stream(ctx, stream):
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    _check(ctx, load().lcs_set_stream(ctx, ctypes.c_void_p(stream or 0)))
+
+
+def lcs_synchronize(ctx):
+    _check(ctx, load().lcs_synchronize(ctx))
+
+
+# ----------------------------------------------------------------- field
+
+def field_desc(dim, n=(1, 1, 1), origin=(0, 0, 0), spacing=(1, 1, 1), periodic=(0, 0, 0), times=(0.0,),
+               time_periodic=False, period=0.0, storage=F32, kind=RECTILINEAR, mesh=None):
+    """Build an lcs_field_desc; the returned object keeps its arrays alive."""
+    d = FieldDesc()
+    d.dim, d.kind, d.storage = int(dim), int(kind), int(storage)
+    for a in range(3):
+        d.n[a] = int(n[a]) if a < len(n) else 1
+        d.origin[a] = float(origin[a]) if a < len(origin) else 0.0
+        d.spacing[a] = float(spacing[a]) if a < len(spacing) else 1.0
+        d.periodic[a] = int(periodic[a]) if a < len(periodic) else 0
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    d.nframes = len(t)
+    d.frame_times = t.ctypes.data
+    d.time_periodic = int(bool(time_periodic))
+    d.period = float(period)
+    keep = [t]
+    if mesh is not None:
+        xyz = np.ascontiguousarray(mesh[0], dtype=np.float32)
+        tets = np.ascontiguousarray(mesh[1], dtype=np.int32)
+        nbrs = None if mesh[2] is None else np.ascontiguousarray(mesh[2], dtype=np.int32)
+        d.nnodes, d.ncells = xyz.shape[0], tets.shape[0]
+        d.node_xyz, d.tets = xyz.ctypes.data, tets.ctypes.data
+        d.nbrs = None if nbrs is None else nbrs.ctypes.data
+        keep += [xyz, tets, nbrs]
+    d._keep = keep
+    return d
+
+
+def lcs_load_field(ctx, desc: FieldDesc, frames):
+    p, dev = _ptr(frames)
+    out = ctypes.c_void_p()
+    _check(ctx, load().lcs_load_field(ctx, ctypes.byref(desc), ctypes.c_void_p(p), dev, ctypes.byref(out)))
+    return out.value
+
+
+def lcs_update_frames(ctx, field, frames):
+    p, dev = _ptr(frames)
+    _check(ctx, load().lcs_update_frames(ctx, field, ctypes.c_void_p(p), dev))
+
+
+def lcs_free_field(field):
+    load().lcs_free_field(field)
+
+
+# ------------------------------------------------------------- seed grid
+
+def seed_desc(dim, n, lo, hi, periodic=(0, 0, 0)):
+    d = SeedDesc()
+    d.dim = int(dim)
+    for a in range(3):
+        d.n[a] = int(n[a]) if a < dim else 1
+        d.lo[a] = float(lo[a]) if a < dim else 0.0
+        d.hi[a] = float(hi[a]) if a < dim else 0.0
+        d.periodic[a] = int(periodic[a]) if a < len(periodic) and a < dim else 0
+    return d
+
+
+def lcs_seed_grid(ctx, desc: SeedDesc, field=None):
+    out = ctypes.c_void_p()
+    _check(ctx, load().lcs_seed_grid(ctx, ctypes.byref(desc), field, ctypes.byref(out)))
+    return out.value
+
+
+def lcs_seeds_count(seeds) -> int:
+    return int(load().lcs_seeds_count(seeds))
+
+
+def lcs_seeds_get(ctx, seeds, xyz=None, cells=None):
+    px, dx = _ptr(xyz)
+    pc, dc = _ptr(cells)
+    on_dev = dx if xyz is not None else dc
+    if xyz is not None and cells is not None and dx != dc:
+        raise ValueError("xyz and cells must both be host or both be device buffers")
+    _check(ctx, load().lcs_seeds_get(ctx, seeds, ctypes.c_void_p(px), ctypes.c_void_p(pc), on_dev))
+
+
+def lcs_free_seeds(seeds):
+    load().lcs_free_seeds(seeds)
+
+
+# -------------------------------------------------------------- flow map
+
+def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol=1e-6, atol=1e-6, h0=0.01,
+                max_steps=0, walk_limit=0, block_threads=0, variant=0):
+    o = AdvectOpts()
+    o.method, o.t0, o.T, o.dt = int(method), float(t0), float(T), float(dt)
+    o.rtol, o.atol, o.h0, o.max_steps = float(rtol), float(atol), float(h0), int(max_steps)
+    o.walk_limit, o.block_threads, o.variant = int(walk_limit), int(block_threads), int(variant)
+    if job_t0 is not None:
+        a = np.ascontiguousarray(job_t0, dtype=np.float64)
+        b = np.ascontiguousarray(job_T, dtype=np.float64)
+        o.njobs = len(a)
+        o.job_t0, o.job_T = a.ctypes.data, b.ctypes.data
+        o._keep = (a, b)
+    else:
+        o.njobs = 1
+    return o
+
+
+def lcs_flowmap_create(ctx, seeds, njobs=1):
+    out = ctypes.c_void_p()
+    _check(ctx, load().lcs_flowmap_create(ctx, seeds, int(njobs), ctypes.byref(out)))
+    return out.value
+
+
+def lcs_advect(ctx, field, seeds, opts: AdvectOpts, fm):
+    _check(ctx, load().lcs_advect(ctx, field, seeds, ctypes.byref(opts), fm))
+
+
+def lcs_flowmap_get(ctx, fm, job=0, xyz=None, status=None, t_exit=None):
+    ptrs = [_ptr(a) for a in (xyz, status, t_exit)]
+    devs = {d for (p, d), a in zip(ptrs, (xyz, status, t_exit)) if a is not None}
+    if len(devs) > 1:
+        raise ValueError("outputs must all be host or all be device buffers")
+    _check(ctx, load().lcs_flowmap_get(ctx, fm, int(job), *[ctypes.c_void_p(p) for p, _ in ptrs],
+                                       devs.pop() if devs else 0))
+
+
+def lcs_free_flowmap(fm):
+    load().lcs_free_flowmap(fm)
+
+
+# ----------------------------------------------------- grad F, C, FTLE
+
+def lcs_cauchy_green(ctx, fm, job, C):
+    p, dev = _ptr(C)
+    _check(ctx, load().lcs_cauchy_green(ctx, fm, int(job), ctypes.c_void_p(p), dev))
+
+
+def lcs_ftle(ctx, fm, job, ftle, lambda_max=None, C=None):
+    ptrs = [_ptr(a) for a in (ftle, lambda_max, C)]
+    devs = {d for (p, d), a in zip(ptrs, (ftle, lambda_max, C)) if a is not None}
+    if len(devs) > 1:
+        raise ValueError("outputs must all be host or all be device buffers")
+    _check(ctx, load().lcs_ftle(ctx, fm, int(job), *[ctypes.c_void_p(p) for p, _ in ptrs], devs.pop()))

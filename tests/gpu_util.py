@@ -1,0 +1,140 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI
+and the FP64 oracle on the same seeded inputs, and compare with the stated
+tolerances.
+
+Tolerances (fixed-step FP32 path against the FP64 oracle):
+  * seed lattice, status: bit-exact;
+  * flow map: ||x_gpu - x_oracle||_inf / L <= 1e-5 * exp(sigma_max * |T|) per OK seed,
+    L the domain extent, sigma_max the oracle's largest FTLE;
+  * FTLE: median |d sigma| <= 1e-5 and 99.9th percentile <= 1e-3 over seeds valid
+    in both.
+"""
+import numpy as np
+import torch
+
+import oracle
+from paper_2209_13775_gb300 import lcs
+
+
+def rect_desc(g, storage=lcs.F32):
+    return lcs.field_desc(g.dim, g.n, g.origin, g.spacing, g.periodic, g.times, g.time_periodic, g.period,
+                          storage=storage)
+
+
+def gpu_run(ctx, g, n, lo, hi, periodic, T, dt, t0=0.0, storage=lcs.F32, variant=0, block_threads=0,
+            jobs=None, want_C=False):
+    """Load, seed, advect, FTLE through the C ABI.  Returns dict of host arrays (job 0 unless jobs)."""
+    dim = g.dim
+    field = lcs.lcs_load_field(ctx, rect_desc(g, storage), g.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(dim, n, lo, hi, periodic))
+    N = lcs.lcs_seeds_count(seeds)
+    njobs = 1 if jobs is None else len(jobs[0])
+    fm = lcs.lcs_flowmap_create(ctx, seeds, njobs)
+    if jobs is None:
+        opts = lcs.advect_opts(lcs.RK4, t0=t0, T=T, dt=dt, variant=variant, block_threads=block_threads)
+    else:
+        opts = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1], variant=variant,
+                               block_threads=block_threads)
+    lcs.lcs_advect(ctx, field, seeds, opts, fm)
+    out = {"N": N, "seeds": np.empty((dim, N), dtype=np.float32)}
+    lcs.lcs_seeds_get(ctx, seeds, out["seeds"])
+    out["xyz"], out["status"], out["t_exit"], out["ftle"], out["lam"], out["C"] = [], [], [], [], [], []
+    np_ = 3 if dim == 2 else 6
+    for j in range(njobs):
+        x = np.empty((dim, N), dtype=np.float32)
+        s = np.empty(N, dtype=np.uint8)
+        te = np.empty(N, dtype=np.float32)
+        lcs.lcs_flowmap_get(ctx, fm, j, x, s, te)
+        f = np.empty(N, dtype=np.float32)
+        lam = np.empty(N, dtype=np.float64)
+        C = np.empty((N, np_), dtype=np.float64) if want_C else None
+        lcs.lcs_ftle(ctx, fm, j, f, lam, C)
+        for k, v in (("xyz", x), ("status", s), ("t_exit", te), ("ftle", f), ("lam", lam), ("C", C)):
+            out[k].append(v)
+    lcs.lcs_synchronize(ctx)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return out
+
+
+def oracle_field(g):
+    return oracle.RectField(g.frames, g.times, g.origin, g.spacing, g.periodic, g.time_periodic, g.period)
+
+
+def oracle_run(g, n, lo, hi, periodic, T, dt, t0=0.0, sample=None):
+    """Oracle flow map and FTLE; `sample` restricts the FTLE to those seed ids (advecting them and
+    their lattice neighbours only)."""
+    dim = g.dim
+    endpoint = [0 if p else 1 for p in periodic]
+    x0 = oracle.seed_grid(dim, n, lo, hi, endpoint)
+    F = oracle_field(g)
+    h = oracle.lattice_spacing(dim, n, lo, hi, endpoint)
+    period = [hi[a] - lo[a] if periodic[a] else 0.0 for a in range(dim)]
+    if sample is None:
+        xT, st, te = oracle.rk4(F, x0.astype(np.float64), t0, T, dt)
+        G = oracle.flowmap_gradient(dim, n, h, periodic, period, xT, st)
+        C = oracle.cauchy_green(G)
+        lam, sig = oracle.ftle(C, dim, T)
+        return {"seeds": x0, "xyz": xT, "status": st, "t_exit": te, "ftle": sig, "lam": lam, "C": C}
+    # stencils of the sampled seeds: +-1, +-2 along each axis (one-sided fallbacks need 2)
+    ids = set()
+    strides = [1, n[0], n[0] * n[1]][:dim]
+    for p in sample:
+        idx = [(p // strides[a]) % n[a] for a in range(dim)]
+        for a in range(dim):
+            for off in (-2, -1, 0, 1, 2):
+                q = list(idx)
+                q[a] = q[a] + off
+                if periodic[a]:
+                    q[a] %= n[a]
+                elif not (0 <= q[a] < n[a]):
+                    continue
+                ids.add(sum(q[b] * strides[b] for b in range(dim)))
+    ids = np.array(sorted(ids))
+    xT_s, st_s, te_s = oracle.rk4(F, x0[:, ids].astype(np.float64), t0, T, dt)
+    N = x0.shape[1]
+    # scatter into full-size arrays; seeds not integrated are marked LEFT so no stencil uses them
+    xT = np.zeros((dim, N))
+    st = np.full(N, oracle.LEFT, dtype=np.uint8)
+    xT[:, ids] = xT_s
+    st[ids] = st_s
+    return {"seeds": x0, "ids": ids, "xyz_s": xT_s, "status_s": st_s, "t_exit_s": te_s, "xT": xT, "st": st,
+            "h": h, "period": period}
+
+
+def oracle_ftle_at(sample, dim, n, h, periodic, period, xT, st, T):
+    """Oracle FTLE at `sample` from (partial) full-size flow-map arrays."""
+    G = oracle.flowmap_gradient(dim, n, h, periodic, period, xT, st)[sample]
+    C = oracle.cauchy_green(G)
+    lam, sig = oracle.ftle(C, dim, T)
+    return sig, lam, C
+
+
+def check_flowmap(x_gpu, x_ora, st_gpu, st_ora, L, sigma_max, T):
+    np.testing.assert_array_equal(st_gpu, st_ora)
+    ok = st_ora == oracle.OK
+    err = np.abs(x_gpu[:, ok].astype(np.float64) - x_ora[:, ok]).max(axis=0) / L
+    bound = 1e-5 * np.exp(sigma_max * abs(T))
+    assert err.max() <= bound, (err.max(), bound)
+    return err
+
+
+def check_ftle(f_gpu, f_ora):
+    both = np.isfinite(f_gpu) & np.isfinite(f_ora)
+    np.testing.assert_array_equal(np.isfinite(f_gpu), np.isfinite(f_ora))
+    d = np.abs(f_gpu[both].astype(np.float64) - f_ora[both])
+    med, p999 = float(np.median(d)), float(np.quantile(d, 0.999))
+    assert med <= 1e-5 and p999 <= 1e-3, (med, p999)
+    return med, p999, float(d.max())
+
+
+def round_bf16(a):
+    """FP32 -> nearest-even BF16 -> FP32 (what BF16 storage holds)."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).reshape(np.shape(a))
+
+
+def round_fp16(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float16).astype(np.float32)

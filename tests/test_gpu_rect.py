@@ -1,0 +1,225 @@
+"""GPU parity of the rectilinear RK4 path through the C ABI against the FP64 oracle
+(Sec. 2 Seed / Interpolator / Flow Map / Cauchy-Green, Eq. 1-2).
+
+Sizes: the small cases are ones the oracle finishes in seconds, with ragged seed
+counts that are not multiples of any block size; the full-size cases (256x128
+seeds on the 129x65x101 double gyre; 256^3 seeds on the 128^3x64 ABC flow) run
+the launch configuration bench.py times and compare sampled seeds.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_13775_gb300 import inputs, lcs
+from gpu_util import (check_flowmap, check_ftle, gpu_run, oracle_ftle_at, oracle_run, round_bf16,
+                      round_fp16)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    c = lcs.lcs_create(0, torch.cuda.current_stream())
+    yield c
+    lcs.lcs_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def gyre():
+    return inputs.double_gyre()
+
+
+@pytest.mark.parametrize("dim,n,lo,hi,periodic", [
+    (2, (256, 128), (0.0, 0.0), (2.0, 1.0), (0, 0)),
+    (2, (251, 7), (-1.5, 0.1), (2.5, 0.3), (0, 0)),
+    (3, (17, 9, 5), (0.0, 0.0, 0.0), (2 * np.pi, 2 * np.pi, 2 * np.pi), (1, 1, 1)),
+    (3, (33, 3, 40), (-1.0, 0.5, 2.0), (1.0, 0.75, 3.0), (1, 0, 1)),
+])
+def test_seed_lattice_bit_exact(ctx, dim, n, lo, hi, periodic):
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(dim, n, lo, hi, periodic))
+    N = lcs.lcs_seeds_count(seeds)
+    assert N == int(np.prod(n))
+    got = np.empty((dim, N), dtype=np.float32)
+    lcs.lcs_seeds_get(ctx, seeds, got)
+    dev = torch.empty((dim, N), dtype=torch.float32, device="cuda")
+    lcs.lcs_seeds_get(ctx, seeds, dev)
+    lcs.lcs_free_seeds(seeds)
+    ref = oracle.seed_grid(dim, n, lo, hi, [0 if p else 1 for p in periodic])
+    np.testing.assert_array_equal(got.view(np.uint32), ref.view(np.uint32))
+    np.testing.assert_array_equal(dev.cpu().numpy(), got)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("n", [(256, 128), (250, 130)])
+def test_gyre_rk4_parity(ctx, gyre, variant, n):
+    lo, hi, T, dt = (0.0, 0.0), (2.0, 1.0), 10.0, 0.05
+    g = gpu_run(ctx, gyre, n, lo, hi, (0, 0), T, dt, variant=variant)
+    o = oracle_run(gyre, n, lo, hi, (0, 0), T, dt)
+    smax = float(np.nanmax(o["ftle"]))
+    check_flowmap(g["xyz"][0], o["xyz"], g["status"][0], o["status"], 2.0, smax, T)
+    med, p999, mx = check_ftle(g["ftle"][0], o["ftle"])
+    print("gyre variant %d n=%s: FTLE median %.2e p99.9 %.2e max %.2e" % (variant, n, med, p999, mx))
+    np.testing.assert_allclose(g["t_exit"][0], np.float32(T), rtol=0, atol=0)
+
+
+def test_ring_and_gather_agree(ctx, gyre):
+    # both kernels evaluate the same FP32 arithmetic; shared-memory staging must not change a bit
+    a = gpu_run(ctx, gyre, (200, 100), (0.0, 0.0), (2.0, 1.0), (0, 0), 5.0, 0.05, t0=2.5, variant=1)
+    b = gpu_run(ctx, gyre, (200, 100), (0.0, 0.0), (2.0, 1.0), (0, 0), 5.0, 0.05, t0=2.5, variant=2)
+    np.testing.assert_array_equal(a["xyz"][0], b["xyz"][0])
+    np.testing.assert_array_equal(a["ftle"][0], b["ftle"][0])
+
+
+def test_gyre_backward_and_periodic_time_wrap(ctx, gyre):
+    # t0 = 9, T = -10 crosses t = 0 backward; t0 = 7, T = 8 crosses the period forward
+    for t0, T in ((9.0, -10.0), (7.0, 8.0)):
+        n, lo, hi = (96, 48), (0.0, 0.0), (2.0, 1.0)
+        g = gpu_run(ctx, gyre, n, lo, hi, (0, 0), T, 0.05, t0=t0)
+        o = oracle_run(gyre, n, lo, hi, (0, 0), T, 0.05, t0=t0)
+        check_flowmap(g["xyz"][0], o["xyz"], g["status"][0], o["status"], 2.0, float(np.nanmax(o["ftle"])), T)
+        check_ftle(g["ftle"][0], o["ftle"])
+
+
+def test_batched_jobs_equal_single_jobs(ctx, gyre):
+    n, lo, hi, dt = (64, 32), (0.0, 0.0), (2.0, 1.0), 0.05
+    t0s, Ts = [0.0, 2.5, 7.75, 5.0], [2.0, -4.0, 8.0, 0.0]
+    b = gpu_run(ctx, gyre, n, lo, hi, (0, 0), None, dt, jobs=(t0s, Ts))
+    for j, (t0, T) in enumerate(zip(t0s, Ts)):
+        s = gpu_run(ctx, gyre, n, lo, hi, (0, 0), T, dt, t0=t0)
+        np.testing.assert_array_equal(b["xyz"][j], s["xyz"][0])
+        np.testing.assert_array_equal(b["status"][j], s["status"][0])
+        if T != 0.0:
+            np.testing.assert_array_equal(b["ftle"][j], s["ftle"][0])
+    # T = 0: the flow map is the identity
+    np.testing.assert_array_equal(b["xyz"][3], b["seeds"])
+
+
+def test_cauchy_green_matches_oracle_on_gpu_positions(ctx, gyre):
+    # same FP32 positions in: grad F and C are bit-identical, lambda_max within rounding
+    n, lo, hi, T = (128, 64), (0.0, 0.0), (2.0, 1.0), 10.0
+    g = gpu_run(ctx, gyre, n, lo, hi, (0, 0), T, 0.05, want_C=True)
+    x = g["xyz"][0].astype(np.float64)
+    G = oracle.flowmap_gradient(2, n, oracle.lattice_spacing(2, n, lo, hi), (0, 0), (0, 0), x, g["status"][0])
+    C = oracle.cauchy_green(G)
+    np.testing.assert_array_equal(g["C"][0], C)
+    lam, sig = oracle.ftle(C, 2, T)
+    np.testing.assert_allclose(g["lam"][0], lam, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(g["ftle"][0], sig.astype(np.float32), rtol=1e-6, atol=0)
+
+
+def test_affine_field_closed_form(ctx):
+    # u = A x on a dyadic grid is interpolated exactly: x_N = R(hA)^N x0 up to FP32 rounding
+    A = np.array([[0.125, -1.0], [1.0, -0.125]])
+    g = inputs.affine_frames(A, np.zeros((2, 2)), [0.0, 0.0], (33, 33), (-4.0, -4.0), (0.25, 0.25), [0.0, 5.0])
+    n, lo, hi, dt, T = (41, 37), (-1.0, -1.0), (1.0, 1.0), 0.05, 2.0
+    r = gpu_run(ctx, g, n, lo, hi, (0, 0), T, dt)
+    Z = dt * A
+    R = np.eye(2) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+    M = np.linalg.matrix_power(R, 40)
+    expect = M @ r["seeds"].astype(np.float64)
+    assert np.abs(r["xyz"][0] - expect).max() < 2e-5
+    # grad F = M everywhere, so C and FTLE are constant
+    lam_exact = np.linalg.eigvalsh(M.T @ M)[-1]
+    assert np.abs(r["lam"][0] / lam_exact - 1).max() < 1e-4
+
+
+def test_leaving_tracers_status_and_exit_time(ctx):
+    # uniform u = (1, 0.25) on the box [0,1]^2: tracers exit through x = 1 + h at known times
+    g = inputs.affine_frames(np.zeros((2, 2)), np.zeros((2, 2)), [1.0, 0.25], (9, 9), (0.0, 0.0),
+                             (0.125, 0.125), [0.0, 1.0])
+    n, lo, hi, T, dt = (21, 11), (0.0, 0.0), (1.0, 1.0), 1.5, 0.01
+    r = gpu_run(ctx, g, n, lo, hi, (0, 0), T, dt)
+    o = oracle_run(g, n, lo, hi, (0, 0), T, dt)
+    np.testing.assert_array_equal(r["status"][0], o["status"])
+    assert (o["status"] == oracle.LEFT).sum() > 100
+    np.testing.assert_allclose(r["t_exit"][0], o["t_exit"], rtol=0, atol=1e-5)
+    # FTLE is NaN exactly where the oracle has no valid stencil
+    np.testing.assert_array_equal(np.isnan(r["ftle"][0]), np.isnan(o["ftle"]))
+
+
+def test_steady_single_frame_field(ctx, gyre):
+    from dataclasses import replace
+    g1 = replace(gyre, frames=gyre.frames[:1].copy(), times=np.array([0.0]), time_periodic=False, period=0.0)
+    n, lo, hi = (64, 32), (0.0, 0.0), (2.0, 1.0)
+    r = gpu_run(ctx, g1, n, lo, hi, (0, 0), 3.0, 0.05)
+    o = oracle_run(g1, n, lo, hi, (0, 0), 3.0, 0.05)
+    check_flowmap(r["xyz"][0], o["xyz"], r["status"][0], o["status"], 2.0, float(np.nanmax(o["ftle"])), 3.0)
+
+
+def test_invalid_arguments_raise(ctx, gyre):
+    field = lcs.lcs_load_field(ctx, lcs.field_desc(2, gyre.n, gyre.origin, gyre.spacing, times=gyre.times),
+                               gyre.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (8, 8), (0, 0), (2, 1)))
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    for bad in (dict(T=1.0, dt=0.0), dict(T=1.0, dt=0.3), dict(T=float("nan"), dt=0.1)):
+        with pytest.raises(lcs.LcsError) as e:
+            lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, **bad), fm)
+        assert e.value.status == 1
+    with pytest.raises(lcs.LcsError):
+        lcs.lcs_flowmap_get(ctx, fm, 3, np.empty((2, 64), dtype=np.float32))
+    bad_desc = lcs.field_desc(2, (1, 5), (0, 0), (1, 1), times=[0.0])
+    with pytest.raises(lcs.LcsError):
+        lcs.lcs_load_field(ctx, bad_desc, np.zeros((1, 5, 1, 2), dtype=np.float32))
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+
+
+@pytest.fixture(scope="module")
+def abc_small():
+    return inputs.abc(n=32, nframes=17, t_end=2.0)
+
+
+@pytest.mark.parametrize("storage", [lcs.F32, lcs.F16, lcs.BF16])
+def test_abc_periodic_3d_parity(ctx, abc_small, storage):
+    # FP16/BF16 storage: the oracle reads the frames rounded to that format, which is exactly what the
+    # kernel widens back to FP32, so the same tolerances apply
+    from dataclasses import replace
+    g = abc_small
+    if storage == lcs.F16:
+        g = replace(g, frames=round_fp16(g.frames))
+    elif storage == lcs.BF16:
+        g = replace(g, frames=round_bf16(g.frames))
+    L = 2 * np.pi
+    n, lo, hi, T, dt = (37, 30, 29), (0.0, 0.0, 0.0), (L, L, L), 2.0, 0.02
+    r = gpu_run(ctx, g if storage == lcs.F32 else g, n, lo, hi, (1, 1, 1), T, dt, storage=storage)
+    o = oracle_run(g, n, lo, hi, (1, 1, 1), T, dt)
+    check_flowmap(r["xyz"][0], o["xyz"], r["status"][0], o["status"], L, float(np.nanmax(o["ftle"])), T)
+    check_ftle(r["ftle"][0], o["ftle"])
+
+
+def test_abc_shift_by_period(ctx, abc_small):
+    # seeds shifted by 2 pi along x: the flow map shifts by exactly 2 pi (index-only wrap)
+    L = 2 * np.pi
+    n = (16, 8, 8)
+    a = gpu_run(ctx, abc_small, n, (0.0, 0.5, 0.5), (1.0, 1.5, 1.5), (0, 0, 0), 1.0, 0.02)
+    b = gpu_run(ctx, abc_small, n, (L, 0.5, 0.5), (L + 1.0, 1.5, 1.5), (0, 0, 0), 1.0, 0.02)
+    d = b["xyz"][0].astype(np.float64) - a["xyz"][0]
+    assert np.abs(d[0] - (b["seeds"][0].astype(np.float64) - a["seeds"][0])).max() < 2e-5
+    assert np.abs(d[1:]).max() < 2e-5
+
+
+# ---------------------------------------------------------------- full size
+
+def test_full_size_abc_sampled(ctx):
+    """256^3 seeds on the 128^3 x 64-frame ABC flow, dt 0.02, T 8 (the benchmark workload),
+    compared at sampled seeds with the oracle (which integrates only their stencils)."""
+    g = inputs.abc()
+    L = 2 * np.pi
+    n, lo, hi, T, dt = (256, 256, 256), (0.0, 0.0, 0.0), (L, L, L), 8.0, 0.02
+    r = gpu_run(ctx, g, n, lo, hi, (1, 1, 1), T, dt)
+    rng = np.random.default_rng(7)
+    N = 256 ** 3
+    sample = np.unique(np.concatenate([rng.integers(0, N, 40), [0, N - 1, 255, 256 * 255]]))
+    o = oracle_run(g, n, lo, hi, (1, 1, 1), T, dt, sample=sample)
+    ids = o["ids"]
+    sig, lam, C = oracle_ftle_at(sample, 3, n, o["h"], (1, 1, 1), o["period"], o["xT"], o["st"], T)
+    check_flowmap(r["xyz"][0][:, ids], o["xyz_s"], r["status"][0][ids], o["status_s"], L,
+                  float(np.nanmax(sig)), T)
+    d = np.abs(r["ftle"][0][sample].astype(np.float64) - sig)
+    assert np.median(d) <= 1e-5 and d.max() <= 1e-3, (np.median(d), d.max())
+    # every output finite, every tracer OK on the periodic domain
+    assert np.isfinite(r["ftle"][0]).all() and (r["status"][0] == 0).all()
