@@ -106,6 +106,15 @@ cudaError_t launch_rk4_schedule(const double *d_times, int nframes, int time_per
 template <int DIM, int ST>
 struct Node;
 
+// ld: global memory (read-only path); lds: generic address (shared or global);
+// lss: shared memory only (explicit shared-space load)
+__device__ __forceinline__ unsigned ld_shared_u32(const char *f, int v)
+{
+    unsigned r;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r) : "r"(smem_u32(f) + 4u * (unsigned)v));
+    return r;
+}
+
 template <>
 struct Node<2, LCS_F32> {
     static __device__ __forceinline__ void ld(const char *f, int v, float *u)
@@ -119,6 +128,10 @@ struct Node<2, LCS_F32> {
         float2 t = reinterpret_cast<const float2 *>(f)[v];
         u[0] = t.x;
         u[1] = t.y;
+    }
+    static __device__ __forceinline__ void lss(const char *f, int v, float *u)
+    {
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(u[0]), "=f"(u[1]) : "r"(smem_u32(f) + 8u * (unsigned)v));
     }
 };
 
@@ -159,6 +172,12 @@ struct Node<2, LCS_F16> {
         u[0] = t.x;
         u[1] = t.y;
     }
+    static __device__ __forceinline__ void lss(const char *f, int v, float *u)
+    {
+        float2 t = h2f(ld_shared_u32(f, v));
+        u[0] = t.x;
+        u[1] = t.y;
+    }
 };
 
 template <>
@@ -172,6 +191,12 @@ struct Node<2, LCS_BF16> {
     static __device__ __forceinline__ void lds(const char *f, int v, float *u)
     {
         float2 t = b2f(reinterpret_cast<const unsigned *>(f)[v]);
+        u[0] = t.x;
+        u[1] = t.y;
+    }
+    static __device__ __forceinline__ void lss(const char *f, int v, float *u)
+    {
+        float2 t = b2f(ld_shared_u32(f, v));
         u[0] = t.x;
         u[1] = t.y;
     }
@@ -280,8 +305,22 @@ __device__ __forceinline__ void make_stencil(const RectParams &P, const float *x
     }
 }
 
+// where stage frames live: global memory, any (generic address), shared memory
+enum { SRC_GLOBAL = 0, SRC_GENERIC = 1, SRC_SHARED = 2 };
+
+template <int DIM, int ST, int SRC>
+__device__ __forceinline__ void node_load(const char *f, int v, float *u)
+{
+    if constexpr (SRC == SRC_GLOBAL)
+        Node<DIM, ST>::ld(f, v, u);
+    else if constexpr (SRC == SRC_GENERIC)
+        Node<DIM, ST>::lds(f, v, u);
+    else
+        Node<DIM, ST>::lss(f, v, u);
+}
+
 // u = (1 - a) I[frame fa](x) + a I[frame fb](x); frame fb is not read when a == 0
-template <int DIM, int ST, bool SMEM>
+template <int DIM, int ST, int SRC>
 __device__ __forceinline__ void interp(const Stencil<DIM> &S, const char *fa, const char *fb, float a, float *u)
 {
     float ua[DIM], ub[DIM], v[DIM];
@@ -289,10 +328,7 @@ __device__ __forceinline__ void interp(const Stencil<DIM> &S, const char *fa, co
     for (int c = 0; c < DIM; ++c) ua[c] = 0.0f;
 #pragma unroll
     for (int q = 0; q < (1 << DIM); ++q) {
-        if constexpr (SMEM)
-            Node<DIM, ST>::lds(fa, S.v[q], v);
-        else
-            Node<DIM, ST>::ld(fa, S.v[q], v);
+        node_load<DIM, ST, SRC>(fa, S.v[q], v);
 #pragma unroll
         for (int c = 0; c < DIM; ++c) ua[c] = fmaf(S.w[q], v[c], ua[c]);
     }
@@ -305,10 +341,7 @@ __device__ __forceinline__ void interp(const Stencil<DIM> &S, const char *fa, co
     for (int c = 0; c < DIM; ++c) ub[c] = 0.0f;
 #pragma unroll
     for (int q = 0; q < (1 << DIM); ++q) {
-        if constexpr (SMEM)
-            Node<DIM, ST>::lds(fb, S.v[q], v);
-        else
-            Node<DIM, ST>::ld(fb, S.v[q], v);
+        node_load<DIM, ST, SRC>(fb, S.v[q], v);
 #pragma unroll
         for (int c = 0; c < DIM; ++c) ub[c] = fmaf(S.w[q], v[c], ub[c]);
     }
@@ -386,7 +419,7 @@ __device__ __forceinline__ void store_tracer(const RectParams &P, const Rk4Args 
 }
 
 // one RK4 step; stage frames given by (fa, fb, a) triples
-template <int DIM, int ST, bool SMEM>
+template <int DIM, int ST, int SRC>
 __device__ __forceinline__ void rk4_step(const RectParams &P, float *x, float h, const char *fa0, const char *fb0,
                                          float a0, const char *fa1, const char *fb1, float a1, const char *fa2,
                                          const char *fb2, float a2)
@@ -395,19 +428,19 @@ __device__ __forceinline__ void rk4_step(const RectParams &P, float *x, float h,
     Stencil<DIM> S;
     const float hh = 0.5f * h;
     make_stencil<DIM>(P, x, S);
-    interp<DIM, ST, SMEM>(S, fa0, fb0, a0, k1);
+    interp<DIM, ST, SRC>(S, fa0, fb0, a0, k1);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) y[c] = fmaf(hh, k1[c], x[c]);
     make_stencil<DIM>(P, y, S);
-    interp<DIM, ST, SMEM>(S, fa1, fb1, a1, k2);
+    interp<DIM, ST, SRC>(S, fa1, fb1, a1, k2);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) y[c] = fmaf(hh, k2[c], x[c]);
     make_stencil<DIM>(P, y, S);
-    interp<DIM, ST, SMEM>(S, fa1, fb1, a1, k3);
+    interp<DIM, ST, SRC>(S, fa1, fb1, a1, k3);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) y[c] = fmaf(h, k3[c], x[c]);
     make_stencil<DIM>(P, y, S);
-    interp<DIM, ST, SMEM>(S, fa2, fb2, a2, k4);
+    interp<DIM, ST, SRC>(S, fa2, fb2, a2, k4);
     const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
@@ -437,7 +470,7 @@ __global__ void __launch_bounds__(256) rk4_gather_kernel(RectParams P, const cha
     float te = A.job_tend[job];
     for (int n = 0; n < ns; ++n) {
         SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
-        rk4_step<DIM, ST, false>(P, x, h, frames + (size_t)e0.k * fstride, frames + (size_t)(e0.k + 1) * fstride,
+        rk4_step<DIM, ST, SRC_GLOBAL>(P, x, h, frames + (size_t)e0.k * fstride, frames + (size_t)(e0.k + 1) * fstride,
                                  e0.a, frames + (size_t)e1.k * fstride, frames + (size_t)(e1.k + 1) * fstride, e1.a,
                                  frames + (size_t)e2.k * fstride, frames + (size_t)(e2.k + 1) * fstride, e2.a);
         wrap_periodic<DIM>(P, x, img);
@@ -604,15 +637,22 @@ __global__ void __launch_bounds__(512) rk4_ring2d_kernel(RectParams P, const cha
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             int s = R.slot[q];
-            p[q] = s >= 0 ? slots + (size_t)s * fstride : frames + (size_t)R.kf[q] * fstride;
+            if (s >= 0)
+                p[q] = slots + (size_t)s * fstride;
+            else if (s == RING_NONE)
+                p[q] = p[q - 1];  // alpha == 0: frame k + 1 is never read; keep a pointer of the same space
+            else
+                p[q] = frames + (size_t)R.kf[q] * fstride;
         }
         const SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
         bool all_smem = (R.slot[0] != RING_GLOBAL) && (R.slot[1] != RING_GLOBAL) && (R.slot[2] != RING_GLOBAL) &&
                         (R.slot[3] != RING_GLOBAL) && (R.slot[4] != RING_GLOBAL) && (R.slot[5] != RING_GLOBAL);
+        // a step whose frames did not all get a slot (e.g. one straddling the periodic wrap, which
+        // reads four frames) mixes shared and global pointers: generic loads serve both
         if (all_smem)
-            rk4_step<2, ST, true>(P, x, h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
+            rk4_step<2, ST, SRC_SHARED>(P, x, h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
         else
-            rk4_step<2, ST, false>(P, x, h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
+            rk4_step<2, ST, SRC_GENERIC>(P, x, h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
         wrap_periodic<2>(P, x, img);
         if (rect_left<2>(P, x)) {
             st = LCS_TRACER_LEFT;
