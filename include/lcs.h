@@ -230,6 +230,39 @@ lcs_status lcs_cauchy_green(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double
 lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
                     double *C, int on_device);
 
+/* ------------------------------------- advection without device allocation */
+
+/* No counterpart in the paper: an interface for callers that cannot allocate
+ * device memory.  lcs_advect grows a context-owned scratch buffer with
+ * cudaMalloc when a call needs more room; some callers must not let that
+ * happen -- a plugin running inside another runtime's execution phase, where
+ * that runtime owns the device memory and forbids allocation; a process that
+ * handed nearly all device memory to a pool up front; a latency-bound loop
+ * that cannot afford an allocation that may synchronise the device.
+ *
+ * lcs_advect_rk4_noalloc integrates one job with fixed-step RK4 (the same
+ * schedule and kernels, so the same results as lcs_advect with method
+ * LCS_RK4) on a field already loaded by lcs_load_field, and allocates
+ * nothing: its working memory (the per-stage frame schedule) is a 1 MiB array
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.  The caller passes every input and output as
+ * DEVICE pointers on ctx's device:
+ *   seeds   [3 or 2][n] FP32 SoA start positions (e.g. from lcs_seeds_get)
+ *   xyz     [dim][n] FP32 final positions (unwrapped on periodic axes)
+ *   status  [n] uint8, t_exit [n] FP32 (as lcs_flowmap_get)
+ * Limits: |T|/|dt| must be an integer <= LCS_NOALLOC_MAX_STEPS, else
+ * LCS_EINVAL with nothing queued.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the one array: two calls whose
+ * work overlaps on the GPU (different streams, or different contexts on one
+ * device) race on it; calls queued on one stream are ordered and safe.
+ * Nothing in the array needs to start at zero: each call writes every entry
+ * it reads before reading it.                                               */
+#define LCS_NOALLOC_MAX_STEPS 43680
+lcs_status lcs_advect_rk4_noalloc(lcs_ctx *ctx, const lcs_field *field, const float *seeds, long long n,
+                                  double t0, double T, double dt, float *xyz, unsigned char *status,
+                                  float *t_exit);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "LCS_OK", 1: "LCS_EINVAL", 2: "LCS_ENOMEM", 3: "LCS_ECUDA", 4
 EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs_synchronize",
            "lcs_load_field", "lcs_update_frames", "lcs_free_field", "lcs_seed_grid", "lcs_seeds_count",
            "lcs_seeds_get", "lcs_free_seeds", "lcs_flowmap_create", "lcs_advect", "lcs_flowmap_get",
-           "lcs_free_flowmap", "lcs_cauchy_green", "lcs_ftle"]
+           "lcs_free_flowmap", "lcs_cauchy_green", "lcs_ftle", "lcs_advect_rk4_noalloc"]
+NOALLOC_MAX_STEPS = 43680
 
 
 class LcsError(RuntimeError):
@@ -82,6 +83,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_flowmap_create": ([P, P, I, P], S), "lcs_advect": ([P, P, P, P, P], S),
         "lcs_flowmap_get": ([P, P, I, P, P, P, I], S), "lcs_free_flowmap": ([P], None),
         "lcs_cauchy_green": ([P, P, I, P, I], S), "lcs_ftle": ([P, P, I, P, P, P, I], S),
+        "lcs_advect_rk4_noalloc": ([P, P, P, LL, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P], S),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -282,3 +284,19 @@ def lcs_ftle(ctx, fm, job, ftle, lambda_max=None, C=None):
     if len(devs) > 1:
         raise ValueError("outputs must all be host or all be device buffers")
     _check(ctx, load().lcs_ftle(ctx, fm, int(job), *[ctypes.c_void_p(p) for p, _ in ptrs], devs.pop()))
+
+
+# ---------------------------------------------- advection without allocation
+
+def lcs_advect_rk4_noalloc(ctx, field, seeds, t0, T, dt, xyz, status, t_exit):
+    """RK4 flow map of one job into caller-provided DEVICE tensors; the library allocates nothing.
+
+    For callers that cannot allocate device memory (see include/lcs.h).  `seeds` is a [dim][n] FP32
+    device tensor; `xyz` [dim][n] FP32, `status` [n] uint8 and `t_exit` [n] FP32 are device outputs.
+    """
+    ptrs = [_ptr(a) for a in (seeds, xyz, status, t_exit)]
+    if not all(d for _, d in ptrs):
+        raise ValueError("lcs_advect_rk4_noalloc takes device tensors only")
+    n = int(seeds.shape[-1])
+    _check(ctx, load().lcs_advect_rk4_noalloc(ctx, field, ctypes.c_void_p(ptrs[0][0]), n, float(t0), float(T),
+                                              float(dt), *[ctypes.c_void_p(p) for p, _ in ptrs[1:]]))
