@@ -135,17 +135,6 @@ struct Node<2, LCS_F32> {
     }
 };
 
-template <>
-struct Node<3, LCS_F32> {
-    static __device__ __forceinline__ void ld(const char *f, int v, float *u)
-    {
-        float4 t = __ldg(reinterpret_cast<const float4 *>(f) + v);
-        u[0] = t.x;
-        u[1] = t.y;
-        u[2] = t.z;
-    }
-};
-
 __device__ __forceinline__ float2 h2f(unsigned r)
 {
     __half2 h = *reinterpret_cast<__half2 *>(&r);
@@ -202,27 +191,51 @@ struct Node<2, LCS_BF16> {
     }
 };
 
+// 3D nodes are stored as interval pairs: node v of pair k holds (u_k, 0, u_{k+1}, 0),
+// so one 32-byte (FP32) or 16-byte (FP16/BF16) load brings both frames of a corner.
+template <int ST>
+struct Pair3;
+
 template <>
-struct Node<3, LCS_F16> {
-    static __device__ __forceinline__ void ld(const char *f, int v, float *u)
+struct Pair3<LCS_F32> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *ua, float *ub)
     {
-        uint2 r = __ldg(reinterpret_cast<const uint2 *>(f) + v);
-        float2 a = h2f(r.x), b = h2f(r.y);
-        u[0] = a.x;
-        u[1] = a.y;
-        u[2] = b.x;
+        float p3, p7;
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(ua[0]), "=f"(ua[1]), "=f"(ua[2]), "=f"(p3), "=f"(ub[0]), "=f"(ub[1]), "=f"(ub[2]), "=f"(p7)
+            : "l"(f + 32 * (size_t)v));
+        (void)p3;
+        (void)p7;
     }
 };
 
 template <>
-struct Node<3, LCS_BF16> {
-    static __device__ __forceinline__ void ld(const char *f, int v, float *u)
+struct Pair3<LCS_F16> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *ua, float *ub)
     {
-        uint2 r = __ldg(reinterpret_cast<const uint2 *>(f) + v);
-        float2 a = b2f(r.x), b = b2f(r.y);
-        u[0] = a.x;
-        u[1] = a.y;
-        u[2] = b.x;
+        uint4 r = __ldg(reinterpret_cast<const uint4 *>(f) + v);
+        float2 a = h2f(r.x), b = h2f(r.y), c = h2f(r.z), d = h2f(r.w);
+        ua[0] = a.x;
+        ua[1] = a.y;
+        ua[2] = b.x;
+        ub[0] = c.x;
+        ub[1] = c.y;
+        ub[2] = d.x;
+    }
+};
+
+template <>
+struct Pair3<LCS_BF16> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *ua, float *ub)
+    {
+        uint4 r = __ldg(reinterpret_cast<const uint4 *>(f) + v);
+        float2 a = b2f(r.x), b = b2f(r.y), c = b2f(r.z), d = b2f(r.w);
+        ua[0] = a.x;
+        ua[1] = a.y;
+        ua[2] = b.x;
+        ub[0] = c.x;
+        ub[1] = c.y;
+        ub[2] = d.x;
     }
 };
 
@@ -350,6 +363,36 @@ __device__ __forceinline__ void interp(const Stencil<DIM> &S, const char *fa, co
     for (int c = 0; c < DIM; ++c) u[c] = fmaf(a, ub[c], g * ua[c]);
 }
 
+// 3D: u = (1 - a) I[u_k](x) + a I[u_{k+1}](x) from the interval pair k
+template <int ST>
+__device__ __forceinline__ void interp3p(const Stencil<3> &S, const char *fp, float a, float *u)
+{
+    float ua[3] = {0.0f, 0.0f, 0.0f}, ub[3] = {0.0f, 0.0f, 0.0f}, va[3], vb[3];
+    if (a == 0.0f) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            Pair3<ST>::ld(fp, S.v[q], va, vb);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ua[c] = fmaf(S.w[q], va[c], ua[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[c] = ua[c];
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        Pair3<ST>::ld(fp, S.v[q], va, vb);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ua[c] = fmaf(S.w[q], va[c], ua[c]);
+            ub[c] = fmaf(S.w[q], vb[c], ub[c]);
+        }
+    }
+    float g = 1.0f - a;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = fmaf(a, ub[c], g * ua[c]);
+}
+
 struct Rk4Args {
     const float *seeds;
     long long N;
@@ -446,6 +489,33 @@ __device__ __forceinline__ void rk4_step(const RectParams &P, float *x, float h,
     for (int c = 0; c < DIM; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
 }
 
+// one RK4 step in 3D; stage s reads interval pair ps with weight as
+template <int ST>
+__device__ __forceinline__ void rk4_step3p(const RectParams &P, float *x, float h, const char *p0, float a0,
+                                           const char *p1, float a1, const char *p2, float a2)
+{
+    float k1[3], k2[3], k3[3], k4[3], y[3];
+    Stencil<3> S;
+    const float hh = 0.5f * h;
+    make_stencil<3>(P, x, S);
+    interp3p<ST>(S, p0, a0, k1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k1[c], x[c]);
+    make_stencil<3>(P, y, S);
+    interp3p<ST>(S, p1, a1, k2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k2[c], x[c]);
+    make_stencil<3>(P, y, S);
+    interp3p<ST>(S, p1, a1, k3);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(h, k3[c], x[c]);
+    make_stencil<3>(P, y, S);
+    interp3p<ST>(S, p2, a2, k4);
+    const float h6 = h * (1.0f / 6.0f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
+}
+
 // ============================================================ gather kernel
 
 template <int DIM, int ST>
@@ -470,9 +540,14 @@ __global__ void __launch_bounds__(256) rk4_gather_kernel(RectParams P, const cha
     float te = A.job_tend[job];
     for (int n = 0; n < ns; ++n) {
         SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
-        rk4_step<DIM, ST, SRC_GLOBAL>(P, x, h, frames + (size_t)e0.k * fstride, frames + (size_t)(e0.k + 1) * fstride,
-                                 e0.a, frames + (size_t)e1.k * fstride, frames + (size_t)(e1.k + 1) * fstride, e1.a,
-                                 frames + (size_t)e2.k * fstride, frames + (size_t)(e2.k + 1) * fstride, e2.a);
+        if constexpr (DIM == 2)
+            rk4_step<2, ST, SRC_GLOBAL>(P, x, h, frames + (size_t)e0.k * fstride,
+                                        frames + (size_t)(e0.k + 1) * fstride, e0.a, frames + (size_t)e1.k * fstride,
+                                        frames + (size_t)(e1.k + 1) * fstride, e1.a, frames + (size_t)e2.k * fstride,
+                                        frames + (size_t)(e2.k + 1) * fstride, e2.a);
+        else
+            rk4_step3p<ST>(P, x, h, frames + (size_t)e0.k * fstride, e0.a, frames + (size_t)e1.k * fstride, e1.a,
+                           frames + (size_t)e2.k * fstride, e2.a);
         wrap_periodic<DIM>(P, x, img);
         if (rect_left<DIM>(P, x)) {
             st = LCS_TRACER_LEFT;
@@ -670,6 +745,302 @@ __global__ void __launch_bounds__(512) rk4_ring2d_kernel(RectParams P, const cha
     if (active) store_tracer<2>(P, A, job, i, x, img, st, te);
 }
 
+// ======================================================= re-bundled episodes (3D)
+//
+// Tracers of one warp drift apart in a mixing flow, so after a few hundred steps
+// the 32 lanes of a warp read 32 unrelated cells and every load turns into ~30 L1
+// wavefronts.  The integration is therefore cut into episodes of E steps; before
+// each episode the tracer states are re-bundled by the cell they sit in (a
+// counting sort on the x-fastest cell index), so that consecutive threads sit in
+// the same rows of cells again (the spatial re-bundling the paper cites, Sec. 3.2).
+// Each tracer's arithmetic does not depend on where it sits, so the result is
+// bit-identical to the unsorted kernel.
+
+struct TState {
+    float *x, *y, *z;      // positions, wrapped into [origin, origin + L) on periodic axes
+    short *ix, *iy, *iz;   // periods crossed per axis
+    int *id;               // seed index
+    unsigned char *st;     // tracer status
+    float *te;             // exit time
+};
+
+__global__ void ep_init_kernel(RectParams P, const float *__restrict__ seeds, long long N, TState S,
+                               const float *__restrict__ job_tend, int job)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float x[3] = {seeds[i], seeds[N + i], seeds[2 * N + i]};
+    int img[3] = {0, 0, 0};
+    wrap_periodic<3>(P, x, img);
+    S.x[i] = x[0];
+    S.y[i] = x[1];
+    S.z[i] = x[2];
+    S.ix[i] = (short)img[0];
+    S.iy[i] = (short)img[1];
+    S.iz[i] = (short)img[2];
+    S.id[i] = (int)i;
+    S.st[i] = LCS_TRACER_OK;
+    S.te[i] = job_tend[job];
+}
+
+// key = x-fastest index of the cell holding the tracer (coarsened by `shift` bits)
+__global__ void ep_key_kernel(RectParams P, TState S, long long N, int shift, unsigned *__restrict__ keys,
+                              unsigned *__restrict__ hist)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float x[3] = {S.x[i], S.y[i], S.z[i]};
+    int c[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float sd = (x[d] - P.origin[d]) * P.inv_h[d];
+        int v = isfinite(sd) ? (int)floorf(fminf(fmaxf(sd, 0.0f), (float)P.n[d])) : 0;
+        int hi = P.periodic[d] ? P.n[d] - 1 : P.n[d] - 2;
+        c[d] = min(max(v, 0), hi);
+    }
+    unsigned key = (unsigned)((c[0] + P.sy * (long long)c[1] + P.sz * (long long)c[2]) >> shift);
+    keys[i] = key;
+    atomicAdd(hist + key, 1u);
+}
+
+// exclusive scan of a 1024-thread block (one value per thread)
+__device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned *total)
+{
+    __shared__ unsigned wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned t = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        wsum[lane] = t;
+    }
+    __syncthreads();
+    unsigned pre = (w > 0 ? wsum[w - 1] : 0u) + x - v;
+    *total = wsum[nw - 1];
+    __syncthreads();
+    return pre;
+}
+
+#define SCAN_ITEMS 4
+#define SCAN_TILE (1024 * SCAN_ITEMS)
+
+__global__ void __launch_bounds__(1024) scan_reduce_kernel(const unsigned *__restrict__ in, long long n,
+                                                           unsigned *__restrict__ bsum)
+{
+    long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    unsigned t = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q)
+        if (base + q < n) t += in[base + q];
+    unsigned tot;
+    block_excl_scan(t, &tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// one block: exclusive scan of up to 1024 * SCAN_ITEMS block sums, in place
+__global__ void __launch_bounds__(1024) scan_top_kernel(unsigned *__restrict__ bsum, int nb)
+{
+    int base = threadIdx.x * SCAN_ITEMS;
+    unsigned v[SCAN_ITEMS], t = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        v[q] = base + q < nb ? bsum[base + q] : 0u;
+        t += v[q];
+    }
+    unsigned tot;
+    unsigned pre = block_excl_scan(t, &tot);
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        if (base + q < nb) bsum[base + q] = pre;
+        pre += v[q];
+    }
+}
+
+__global__ void __launch_bounds__(1024) scan_down_kernel(const unsigned *__restrict__ in, long long n,
+                                                         const unsigned *__restrict__ bsum,
+                                                         unsigned *__restrict__ out)
+{
+    long long base = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    unsigned v[SCAN_ITEMS], t = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        v[q] = base + q < n ? in[base + q] : 0u;
+        t += v[q];
+    }
+    unsigned tot;
+    unsigned pre = block_excl_scan(t, &tot) + bsum[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        if (base + q < n) out[base + q] = pre;
+        pre += v[q];
+    }
+}
+
+__global__ void ep_scatter_kernel(TState A, TState B, long long N, const unsigned *__restrict__ keys,
+                                  unsigned *__restrict__ cursor)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    unsigned p = atomicAdd(cursor + keys[i], 1u);
+    B.x[p] = A.x[i];
+    B.y[p] = A.y[i];
+    B.z[p] = A.z[i];
+    B.ix[p] = A.ix[i];
+    B.iy[p] = A.iy[i];
+    B.iz[p] = A.iz[i];
+    B.id[p] = A.id[i];
+    B.st[p] = A.st[i];
+    B.te[p] = A.te[i];
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256) ep_advect3_kernel(RectParams P, const char *__restrict__ pairs, size_t fstride,
+                                                         Rk4Args A, TState S, int job, int s0, int s1)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= A.N) return;
+    if (S.st[i] != LCS_TRACER_OK) return;
+    float x[3] = {S.x[i], S.y[i], S.z[i]};
+    int img[3] = {S.ix[i], S.iy[i], S.iz[i]};
+    const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
+    const int ns = A.job_nsteps[job];
+    const float h = A.job_h[job];
+    const int e = min(s1, ns);
+    unsigned char st = LCS_TRACER_OK;
+    float te = 0.0f;
+    for (int n = s0; n < e; ++n) {
+        SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
+        rk4_step3p<ST>(P, x, h, pairs + (size_t)e0.k * fstride, e0.a, pairs + (size_t)e1.k * fstride, e1.a,
+                       pairs + (size_t)e2.k * fstride, e2.a);
+        wrap_periodic<3>(P, x, img);
+        if (rect_left<3>(P, x)) {
+            st = LCS_TRACER_LEFT;
+            te = fmaf((float)(n + 1), h, A.job_t0[job]);
+            break;
+        }
+    }
+    S.x[i] = x[0];
+    S.y[i] = x[1];
+    S.z[i] = x[2];
+    S.ix[i] = (short)img[0];
+    S.iy[i] = (short)img[1];
+    S.iz[i] = (short)img[2];
+    if (st != LCS_TRACER_OK) {
+        S.st[i] = st;
+        S.te[i] = te;
+    }
+}
+
+__global__ void ep_finalize_kernel(RectParams P, TState S, long long N, float *__restrict__ out_xyz,
+                                   unsigned char *__restrict__ out_st, float *__restrict__ out_te)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    long long id = S.id[i];
+    float x[3] = {S.x[i], S.y[i], S.z[i]};
+    int img[3] = {S.ix[i], S.iy[i], S.iz[i]};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out_xyz[d * N + id] = P.periodic[d] ? fmaf((float)img[d], P.L[d], x[d]) : x[d];
+    out_st[id] = S.st[i];
+    out_te[id] = S.te[i];
+}
+
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// coarsen cell keys so that at most 2^24 bins exist (the scan handles 4096 tiles of 4096)
+static int sort_shift(long long nodes)
+{
+    int shift = 0;
+    while (((nodes - 1) >> shift) + 1 > (1LL << 24)) ++shift;
+    return shift;
+}
+
+size_t rk4_sorted_scratch_bytes(long long N, long long nodes)
+{
+    long long nbins = ((nodes - 1) >> sort_shift(nodes)) + 1;
+    size_t per = al256(4 * N) * 3 + al256(2 * N) * 3 + al256(4 * N) + al256(N) + al256(4 * N);
+    long long nb = (nbins + SCAN_TILE - 1) / SCAN_TILE;
+    return 2 * per + al256(4 * N) + 2 * al256(4 * nbins) + al256(4 * nb);
+}
+
+static TState carve_state(char *&p, long long N)
+{
+    TState S;
+    S.x = (float *)p;
+    p += al256(4 * N);
+    S.y = (float *)p;
+    p += al256(4 * N);
+    S.z = (float *)p;
+    p += al256(4 * N);
+    S.ix = (short *)p;
+    p += al256(2 * N);
+    S.iy = (short *)p;
+    p += al256(2 * N);
+    S.iz = (short *)p;
+    p += al256(2 * N);
+    S.id = (int *)p;
+    p += al256(4 * N);
+    S.st = (unsigned char *)p;
+    p += al256(N);
+    S.te = (float *)p;
+    p += al256(4 * N);
+    return S;
+}
+
+template <int ST>
+static cudaError_t launch_sorted3(const RectParams &P, const lcs_field *f, const Rk4Args &A, const Rk4Launch &L,
+                                  cudaStream_t s)
+{
+    const long long N = A.N;
+    const int shift = sort_shift(f->nodes);
+    const long long nbins = ((f->nodes - 1) >> shift) + 1;
+    const long long nb = (nbins + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb > 1024 * SCAN_ITEMS) return cudaErrorInvalidValue;
+    char *p = (char *)L.work;
+    TState SA = carve_state(p, N), SB = carve_state(p, N);
+    unsigned *keys = (unsigned *)p;
+    p += al256(4 * N);
+    unsigned *hist = (unsigned *)p;
+    p += al256(4 * nbins);
+    unsigned *cursor = (unsigned *)p;
+    p += al256(4 * nbins);
+    unsigned *bsum = (unsigned *)p;
+    const int bt = 256;
+    const unsigned grid = (unsigned)((N + bt - 1) / bt);
+    const int E = L.episode_steps > 0 ? L.episode_steps : 16;
+    for (int job = 0; job < L.njobs; ++job) {
+        ep_init_kernel<<<grid, bt, 0, s>>>(P, A.seeds, N, SA, A.job_tend, job);
+        const int ns = L.host_nsteps[job];
+        for (int s0 = 0; s0 < ns; s0 += E) {
+            cudaMemsetAsync(hist, 0, 4 * nbins, s);
+            ep_key_kernel<<<grid, bt, 0, s>>>(P, SA, N, shift, keys, hist);
+            scan_reduce_kernel<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum);
+            scan_top_kernel<<<1, 1024, 0, s>>>(bsum, (int)nb);
+            scan_down_kernel<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum, cursor);
+            ep_scatter_kernel<<<grid, bt, 0, s>>>(SA, SB, N, keys, cursor);
+            ep_advect3_kernel<ST><<<grid, bt, 0, s>>>(P, (const char *)f->d_frames, f->frame_stride, A, SB, job, s0,
+                                                      s0 + E);
+            TState t = SA;
+            SA = SB;
+            SB = t;
+        }
+        ep_finalize_kernel<<<grid, bt, 0, s>>>(P, SA, N, A.out_xyz + (size_t)job * 3 * N, A.out_status + (size_t)job * N,
+                                               A.out_texit + (size_t)job * N);
+    }
+    return cudaGetLastError();
+}
+
 // ================================================================ dispatch
 
 RectParams make_rect_params(const lcs_field *f)
@@ -732,11 +1103,20 @@ int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
     A.out_texit = L.out_texit;
     if (L.N == 0 || L.njobs == 0) return 1;
     bool ring_fits = f->dim == 2 && RING_SLOTS * f->frame_stride <= ctx->smem_optin;
+    bool sorted_ok = f->dim == 3 && L.work != nullptr;
     int variant = L.variant;
-    if (variant == 0) variant = ring_fits ? 2 : 1;
+    if (variant == 0) variant = ring_fits ? 2 : (sorted_ok && L.N >= LCS_SORTED_MIN_SEEDS ? 3 : 1);
     if (variant == 2 && !ring_fits) variant = 1;
+    if (variant == 3 && !sorted_ok) variant = 1;
     cudaError_t e;
-    if (variant == 2) {
+    if (variant == 3) {
+        if (f->storage == LCS_F32)
+            e = launch_sorted3<LCS_F32>(P, f, A, L, s);
+        else if (f->storage == LCS_F16)
+            e = launch_sorted3<LCS_F16>(P, f, A, L, s);
+        else
+            e = launch_sorted3<LCS_BF16>(P, f, A, L, s);
+    } else if (variant == 2) {
         int bt = L.block_threads > 0 ? L.block_threads : 512;
         if (bt > 512) bt = 512;
         if (f->storage == LCS_F32)

@@ -129,32 +129,49 @@ __device__ __forceinline__ __half to_store<__half>(float v) { return __float2hal
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
+// 2D: slab f = frame f, node v = (u, v).  3D: slab k = interval pair (k, k+1), node v =
+// (u_k, 0, u_{k+1}, 0) so that one load brings both frames of a node (a single frame is
+// paired with itself).
 template <typename T>
-__global__ void convert_rect_kernel(const float *__restrict__ src, int nframes, long long nodes, int dim, int vec,
-                                    size_t frame_stride, char *__restrict__ dst)
+__global__ void convert_rect_kernel(const float *__restrict__ src, int nframes, int nslabs, long long nodes, int dim,
+                                    int vec, size_t slab_stride, char *__restrict__ dst)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= (long long)nframes * nodes) return;
+    if (idx >= (long long)nslabs * nodes) return;
     long long f = idx / nodes, v = idx % nodes;
-    T *o = reinterpret_cast<T *>(dst + (size_t)f * frame_stride) + v * vec;
-    const float *s = src + idx * dim;
-    for (int c = 0; c < vec; ++c) o[c] = to_store<T>(c < dim ? s[c] : 0.0f);
+    T *o = reinterpret_cast<T *>(dst + (size_t)f * slab_stride) + v * vec;
+    if (dim == 2) {
+        const float *s = src + idx * 2;
+        o[0] = to_store<T>(s[0]);
+        o[1] = to_store<T>(s[1]);
+    } else {
+        long long f1 = f + 1 < nframes ? f + 1 : f;
+        const float *a = src + (f * nodes + v) * 3, *b = src + (f1 * nodes + v) * 3;
+        for (int c = 0; c < 3; ++c) {
+            o[c] = to_store<T>(a[c]);
+            o[4 + c] = to_store<T>(b[c]);
+        }
+        o[3] = to_store<T>(0.0f);
+        o[7] = to_store<T>(0.0f);
+    }
 }
 
-cudaError_t launch_convert_rect(const float *src, int nframes, long long nodes, int dim, int vec, int storage,
-                                size_t frame_stride, void *dst, cudaStream_t s)
+cudaError_t launch_convert_rect(const float *src, int nframes, int nslabs, long long nodes, int dim, int vec,
+                                int storage, size_t slab_stride, void *dst, cudaStream_t s)
 {
-    long long total = (long long)nframes * nodes;
+    long long total = (long long)nslabs * nodes;
     if (total == 0) return cudaSuccess;
     int bt = 256;
     unsigned grid = (unsigned)((total + bt - 1) / bt);
     if (storage == LCS_F32)
-        convert_rect_kernel<float><<<grid, bt, 0, s>>>(src, nframes, nodes, dim, vec, frame_stride, (char *)dst);
+        convert_rect_kernel<float>
+            <<<grid, bt, 0, s>>>(src, nframes, nslabs, nodes, dim, vec, slab_stride, (char *)dst);
     else if (storage == LCS_F16)
-        convert_rect_kernel<__half><<<grid, bt, 0, s>>>(src, nframes, nodes, dim, vec, frame_stride, (char *)dst);
+        convert_rect_kernel<__half>
+            <<<grid, bt, 0, s>>>(src, nframes, nslabs, nodes, dim, vec, slab_stride, (char *)dst);
     else
         convert_rect_kernel<__nv_bfloat16>
-            <<<grid, bt, 0, s>>>(src, nframes, nodes, dim, vec, frame_stride, (char *)dst);
+            <<<grid, bt, 0, s>>>(src, nframes, nslabs, nodes, dim, vec, slab_stride, (char *)dst);
     return cudaGetLastError();
 }
 
@@ -172,8 +189,8 @@ static lcs_status upload_frames(lcs_ctx *ctx, lcs_field *f, const float *frames,
         }
         src = tmp;
     }
-    cudaError_t e = launch_convert_rect(src, f->nframes, f->nodes, f->dim, f->vec, f->storage, f->frame_stride,
-                                        f->d_frames, ctx->stream);
+    cudaError_t e = launch_convert_rect(src, f->nframes, f->nslabs, f->nodes, f->dim, f->vec, f->storage,
+                                        f->frame_stride, f->d_frames, ctx->stream);
     if (tmp) cudaFreeAsync(tmp, ctx->stream);
     if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "frame conversion: %s", cudaGetErrorString(e));
     return LCS_OK;
@@ -219,13 +236,14 @@ extern "C" lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *d, cons
     f->time_periodic = d->time_periodic != 0;
     f->period = d->period;
     f->nodes = nodes;
-    f->vec = d->dim == 2 ? 2 : 4;
+    f->vec = d->dim == 2 ? 2 : 8;
+    f->nslabs = d->dim == 2 ? f->nframes : (f->nframes > 1 ? f->nframes - 1 : 1);
     f->elem_bytes = d->storage == LCS_F32 ? 4 : 2;
     f->frame_bytes = (size_t)nodes * f->vec * f->elem_bytes;
     f->frame_stride = (f->frame_bytes + 255) & ~(size_t)255;
     lcs_status st = LCS_OK;
-    cudaError_t e = cudaMalloc(&f->d_frames, f->frame_stride * f->nframes);
-    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_frames, 0, f->frame_stride * f->nframes, ctx->stream);
+    cudaError_t e = cudaMalloc(&f->d_frames, f->frame_stride * f->nslabs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->d_frames, 0, f->frame_stride * f->nslabs, ctx->stream);
     if (e == cudaSuccess) e = cudaMalloc(&f->d_times, sizeof(double) * f->nframes);
     if (e == cudaSuccess)
         e = cudaMemcpy(f->d_times, f->times.data(), sizeof(double) * f->nframes, cudaMemcpyHostToDevice);
@@ -424,7 +442,9 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
 {
     size_t jb = align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs);
     size_t sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
-    lcs_status st = scratch_reserve(ctx, jb + sb);
+    bool want_sorted = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
+    size_t wb = want_sorted ? rk4_sorted_scratch_bytes(s->N, f->nodes) : 0;
+    lcs_status st = scratch_reserve(ctx, jb + sb + wb);
     if (st != LCS_OK) return st;
     char *p = (char *)ctx->d_scratch;
     JobDev D;
@@ -455,6 +475,9 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.out_texit = fm->d_texit;
     L.block_threads = o->block_threads;
     L.variant = o->variant;
+    L.episode_steps = 0;
+    L.host_nsteps = J.nsteps;
+    L.work = want_sorted ? (char *)ctx->d_scratch + jb + sb : nullptr;
     if (launch_rk4_rect(ctx, L, ctx->stream) < 0)
         return fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return LCS_OK;

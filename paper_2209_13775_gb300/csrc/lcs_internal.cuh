@@ -47,12 +47,15 @@ struct lcs_field {
     int time_periodic = 0;
     double period = 0.0;
     double *d_times = nullptr;
-    // frames: [nframes][frame_stride_bytes]; node v occupies vec components
+    // velocity slabs: [nslabs][frame_stride bytes]; node v occupies vec stored components.
+    // 2D: one slab per frame, (u, v) per node.  3D: one slab per frame interval k holding
+    // (u_k, 0, u_{k+1}, 0) per node, so one load brings both frames of a corner.
     void *d_frames = nullptr;
-    int vec = 0;                       // stored components per node (2 in 2D, 4 in 3D)
+    int nslabs = 0;
+    int vec = 0;                       // stored components per node (2 in 2D, 8 in 3D)
     size_t elem_bytes = 4;             // bytes per stored component
-    size_t frame_bytes = 0;            // unpadded bytes per frame
-    size_t frame_stride = 0;           // padded bytes per frame (multiple of 256)
+    size_t frame_bytes = 0;            // unpadded bytes per slab
+    size_t frame_stride = 0;           // padded bytes per slab (multiple of 256)
     long long nodes = 0;
     // tetrahedral mesh
     long long ncells = 0;
@@ -142,8 +145,16 @@ struct Rk4Launch {
     unsigned char *out_status;
     float *out_texit;
     int block_threads;
-    int variant;              // 1 gather, 2 shared-memory ring
+    int variant;              // 1 gather, 2 shared-memory ring (2D), 3 re-bundled episodes (3D)
+    int episode_steps;        // variant 3: steps between re-bundling (0 = default)
+    const int *host_nsteps;   // [njobs] host copy of the step counts
+    void *work;               // variant 3 working memory (rk4_sorted_scratch_bytes), or null
 };
+
+// smallest seed count for which lcs_advect picks the re-bundled kernel by default
+#define LCS_SORTED_MIN_SEEDS 262144
+
+size_t rk4_sorted_scratch_bytes(long long N, long long nodes);
 
 RectParams make_rect_params(const lcs_field *f);
 
@@ -178,8 +189,8 @@ cudaError_t launch_cg_ftle(const CgLaunch &L, cudaStream_t s);
 cudaError_t launch_seed_grid(int dim, const int n[3], const double lo[3], const double hi[3],
                              const int periodic[3], long long N, float *out, cudaStream_t s);
 
-cudaError_t launch_convert_rect(const float *src, int nframes, long long nodes, int dim, int vec,
-                                int storage, size_t frame_stride, void *dst, cudaStream_t s);
+cudaError_t launch_convert_rect(const float *src, int nframes, int nslabs, long long nodes, int dim, int vec,
+                                int storage, size_t slab_stride, void *dst, cudaStream_t s);
 
 // ---------------------------------------------------------- device helpers
 

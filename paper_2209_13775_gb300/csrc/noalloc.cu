@@ -106,7 +106,10 @@ extern "C" lcs_status lcs_advect_rk4_noalloc(lcs_ctx *ctx, const lcs_field *f, c
     L.out_status = status;
     L.out_texit = t_exit;
     L.block_threads = 0;
-    L.variant = 0;
+    L.variant = f->dim == 3 ? 1 : 0;   // the re-bundled 3D kernel needs allocated working memory
+    L.episode_steps = 0;
+    L.host_nsteps = J.nsteps;
+    L.work = nullptr;
     if (launch_rk4_rect(ctx, L, ctx->stream) < 0)
         return na_fail(ctx, LCS_ECUDA, "lcs_advect_rk4_noalloc: advection launch failed");
     return LCS_OK;

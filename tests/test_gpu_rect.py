@@ -194,6 +194,17 @@ def test_abc_periodic_3d_parity(ctx, abc_small, storage):
     check_ftle(r["ftle"][0], o["ftle"])
 
 
+def test_abc_rebundled_equals_gather(ctx, abc_small):
+    # re-bundling tracers between episodes moves them between threads but not their arithmetic
+    L = 2 * np.pi
+    n, lo, hi = (70, 61, 64), (0.0, 0.0, 0.0), (L, L, L)
+    a = gpu_run(ctx, abc_small, n, lo, hi, (1, 1, 1), 2.0, 0.02, variant=1)
+    b = gpu_run(ctx, abc_small, n, lo, hi, (1, 1, 1), 2.0, 0.02, variant=3)
+    np.testing.assert_array_equal(a["xyz"][0], b["xyz"][0])
+    np.testing.assert_array_equal(a["status"][0], b["status"][0])
+    np.testing.assert_array_equal(a["ftle"][0], b["ftle"][0])
+
+
 def test_abc_shift_by_period(ctx, abc_small):
     # seeds shifted by 2 pi along x: the flow map shifts by exactly 2 pi (index-only wrap)
     L = 2 * np.pi
