@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seeds-side", type=int, default=N_SIDE,
                    help="seed lattice side (default 256; smaller only for profiling captures)")
+    p.add_argument("--grid", type=int, default=N_GRID,
+                   help="velocity grid side (default 128; smaller only for profiling captures)")
     return p.parse_args()
 
 
@@ -198,7 +200,7 @@ def our_arm(args, rank, world, local):
     storage = {"f32": lcs.F32, "f16": lcs.F16, "bf16": lcs.BF16}[args.storage]
     stream = torch.cuda.current_stream()
     ctx = lcs.lcs_create(local, stream)
-    g = inputs.abc(n=N_GRID, nframes=N_FRAMES, t_end=T_END)
+    g = inputs.abc(n=args.grid, nframes=N_FRAMES, t_end=T_END)
     desc = lcs.field_desc(3, g.n, g.origin, g.spacing, g.periodic, g.times, storage=storage)
     frames_dev = torch.from_numpy(g.frames).cuda()
     field = lcs.lcs_load_field(ctx, desc, frames_dev)
@@ -302,8 +304,9 @@ def our_arm(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}[args.storage],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.seeds_side == N_SIDE else
-                   WORKLOAD.replace("256^3 seed grid (16.7M tracers)", "%d^3 seed grid" % args.seeds_side),
+        "config": {"workload": WORKLOAD if (args.seeds_side, args.grid) == (N_SIDE, N_GRID) else
+                   WORKLOAD.replace("256^3 seed grid (16.7M tracers)", "%d^3 seed grid" % args.seeds_side)
+                   .replace("128^3 FP32 velocity grid", "%d^3 FP32 velocity grid" % args.grid),
                    "seeds": N, "steps_per_tracer": NSTEPS, "storage": args.storage,
                    "parallelism": "independent replica per GPU" if world > 1 else "single GPU",
                    "l2": "no flush needed: each step writes 872 MB of outputs (C + FTLE) > 129 MB L2"},

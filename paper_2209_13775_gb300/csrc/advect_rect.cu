@@ -200,12 +200,16 @@ template <>
 struct Pair3<LCS_F32> {
     static __device__ __forceinline__ void ld(const char *f, int v, float *ua, float *ub)
     {
-        float p3, p7;
+        float t[8];
         asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-            : "=f"(ua[0]), "=f"(ua[1]), "=f"(ua[2]), "=f"(p3), "=f"(ub[0]), "=f"(ub[1]), "=f"(ub[2]), "=f"(p7)
+            : "=f"(t[0]), "=f"(t[1]), "=f"(t[2]), "=f"(t[3]), "=f"(t[4]), "=f"(t[5]), "=f"(t[6]), "=f"(t[7])
             : "l"(f + 32 * (size_t)v));
-        (void)p3;
-        (void)p7;
+        ua[0] = t[0];
+        ua[1] = t[1];
+        ua[2] = t[2];
+        ub[0] = t[4];
+        ub[1] = t[5];
+        ub[2] = t[6];
     }
 };
 
@@ -363,34 +367,52 @@ __device__ __forceinline__ void interp(const Stencil<DIM> &S, const char *fa, co
     for (int c = 0; c < DIM; ++c) u[c] = fmaf(a, ub[c], g * ua[c]);
 }
 
-// 3D: u = (1 - a) I[u_k](x) + a I[u_{k+1}](x) from the interval pair k
+// Time blend of one node, FP32: u = (1 - a) u_k + a u_{k+1} (exactly u_k when a == 0).
+// 3D fields blend at the nodes first, then interpolate in space; both orders are the
+// same linear map, and every 3D kernel uses this one so that they agree bit for bit.
+__device__ __forceinline__ float tblend(float ua, float ub, float a, float g)
+{
+    return fmaf(a, ub, g * ua);
+}
+
+// 3D: u(x, t) from the interval pair k with weight a of frame k + 1
 template <int ST>
 __device__ __forceinline__ void interp3p(const Stencil<3> &S, const char *fp, float a, float *u)
 {
-    float ua[3] = {0.0f, 0.0f, 0.0f}, ub[3] = {0.0f, 0.0f, 0.0f}, va[3], vb[3];
+    float acc[3] = {0.0f, 0.0f, 0.0f}, va[3], vb[3];
+    const float g = 1.0f - a;
     if (a == 0.0f) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             Pair3<ST>::ld(fp, S.v[q], va, vb);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) ua[c] = fmaf(S.w[q], va[c], ua[c]);
+            for (int c = 0; c < 3; ++c) acc[c] = fmaf(S.w[q], va[c], acc[c]);
         }
+    } else {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) u[c] = ua[c];
-        return;
+        for (int q = 0; q < 8; ++q) {
+            Pair3<ST>::ld(fp, S.v[q], va, vb);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[c] = fmaf(S.w[q], tblend(va[c], vb[c], a, g), acc[c]);
+        }
     }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = acc[c];
+}
+
+// 3D: u(x, t) from a time slice (nodes already blended to the stage time), float4 per node
+__device__ __forceinline__ void interp3s(const Stencil<3> &S, const float4 *__restrict__ sl, float *u)
+{
+    float acc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        Pair3<ST>::ld(fp, S.v[q], va, vb);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ua[c] = fmaf(S.w[q], va[c], ua[c]);
-            ub[c] = fmaf(S.w[q], vb[c], ub[c]);
-        }
+        float4 v = __ldg(sl + S.v[q]);
+        acc[0] = fmaf(S.w[q], v.x, acc[0]);
+        acc[1] = fmaf(S.w[q], v.y, acc[1]);
+        acc[2] = fmaf(S.w[q], v.z, acc[2]);
     }
-    float g = 1.0f - a;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) u[c] = fmaf(a, ub[c], g * ua[c]);
+    for (int c = 0; c < 3; ++c) u[c] = acc[c];
 }
 
 struct Rk4Args {
@@ -511,6 +533,32 @@ __device__ __forceinline__ void rk4_step3p(const RectParams &P, float *x, float 
     for (int c = 0; c < 3; ++c) y[c] = fmaf(h, k3[c], x[c]);
     make_stencil<3>(P, y, S);
     interp3p<ST>(S, p2, a2, k4);
+    const float h6 = h * (1.0f / 6.0f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
+}
+
+// one RK4 step in 3D from three time slices (stage times t_n, t_n + h/2, t_n + h)
+__device__ __forceinline__ void rk4_step3s(const RectParams &P, float *x, float h, const float4 *s0,
+                                           const float4 *s1, const float4 *s2)
+{
+    float k1[3], k2[3], k3[3], k4[3], y[3];
+    Stencil<3> S;
+    const float hh = 0.5f * h;
+    make_stencil<3>(P, x, S);
+    interp3s(S, s0, k1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k1[c], x[c]);
+    make_stencil<3>(P, y, S);
+    interp3s(S, s1, k2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k2[c], x[c]);
+    make_stencil<3>(P, y, S);
+    interp3s(S, s1, k3);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(h, k3[c], x[c]);
+    make_stencil<3>(P, y, S);
+    interp3s(S, s2, k4);
     const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
     for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
@@ -956,6 +1004,91 @@ __global__ void ep_finalize_kernel(RectParams P, TState S, long long N, float *_
     out_te[id] = S.te[i];
 }
 
+// Time slices of one episode: every distinct stage time of steps [s0, s1) gets the
+// field blended to it at every node (consecutive equal schedule entries -- the end of
+// step n and the start of step n + 1 -- share one slice).  One thread builds the
+// table: smap[3 (n - s0) + stage] = slice, stab[slice] = (k, alpha), count in *nsl.
+__global__ void ep_slice_table_kernel(const SchedEntry *__restrict__ sched, int nsteps_max, int job, int s0,
+                                      int s1, int *__restrict__ smap, SchedEntry *__restrict__ stab,
+                                      int *__restrict__ nsl)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const SchedEntry *sc = sched + (size_t)job * nsteps_max * 3;
+    int m = 0;
+    SchedEntry last = {-1, 0.0f};
+    for (int n = s0; n < s1; ++n)
+        for (int st = 0; st < 3; ++st) {
+            SchedEntry e = sc[3 * n + st];
+            bool same = m > 0 && e.k == last.k && __float_as_int(e.a) == __float_as_int(last.a);
+            if (!same) {
+                stab[m++] = e;
+                last = e;
+            }
+            smap[3 * (n - s0) + st] = m - 1;
+        }
+    *nsl = m;
+}
+
+// slice j, node v = blend of interval pair stab[j].k at weight stab[j].a (same arithmetic as interp3p)
+__global__ void ep_slice_fill_kernel(const char *__restrict__ pairs, size_t fstride, long long nodes,
+                                     const SchedEntry *__restrict__ stab, const int *__restrict__ nsl,
+                                     float4 *__restrict__ slices, size_t slice_stride)
+{
+    const int j = blockIdx.y;
+    if (j >= *nsl) return;
+    long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= nodes) return;
+    const SchedEntry e = stab[j];
+    float va[3], vb[3];
+    Pair3<LCS_F32>::ld(pairs + (size_t)e.k * fstride, (int)v, va, vb);
+    const float g = 1.0f - e.a;
+    float4 o;
+    if (e.a == 0.0f) {
+        o = make_float4(va[0], va[1], va[2], 0.0f);
+    } else {
+        o = make_float4(tblend(va[0], vb[0], e.a, g), tblend(va[1], vb[1], e.a, g), tblend(va[2], vb[2], e.a, g),
+                        0.0f);
+    }
+    slices[(size_t)j * slice_stride + v] = o;
+}
+
+__global__ void __launch_bounds__(256) ep_advect3s_kernel(RectParams P, const float4 *__restrict__ slices,
+                                                          size_t slice_stride, const int *__restrict__ smap, Rk4Args A,
+                                                          TState S, int job, int s0, int s1)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= A.N) return;
+    if (S.st[i] != LCS_TRACER_OK) return;
+    float x[3] = {S.x[i], S.y[i], S.z[i]};
+    int img[3] = {S.ix[i], S.iy[i], S.iz[i]};
+    const int ns = A.job_nsteps[job];
+    const float h = A.job_h[job];
+    const int e = min(s1, ns);
+    unsigned char st = LCS_TRACER_OK;
+    float te = 0.0f;
+    for (int n = s0; n < e; ++n) {
+        const int *m = smap + 3 * (n - s0);
+        rk4_step3s(P, x, h, slices + (size_t)__ldg(m) * slice_stride, slices + (size_t)__ldg(m + 1) * slice_stride,
+                   slices + (size_t)__ldg(m + 2) * slice_stride);
+        wrap_periodic<3>(P, x, img);
+        if (rect_left<3>(P, x)) {
+            st = LCS_TRACER_LEFT;
+            te = fmaf((float)(n + 1), h, A.job_t0[job]);
+            break;
+        }
+    }
+    S.x[i] = x[0];
+    S.y[i] = x[1];
+    S.z[i] = x[2];
+    S.ix[i] = (short)img[0];
+    S.iy[i] = (short)img[1];
+    S.iz[i] = (short)img[2];
+    if (st != LCS_TRACER_OK) {
+        S.st[i] = st;
+        S.te[i] = te;
+    }
+}
+
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // coarsen cell keys so that at most 2^24 bins exist (the scan handles 4096 tiles of 4096)
@@ -966,12 +1099,19 @@ static int sort_shift(long long nodes)
     return shift;
 }
 
-size_t rk4_sorted_scratch_bytes(long long N, long long nodes)
+static size_t slice_bytes(long long nodes, int E)
+{
+    return al256(16 * (size_t)nodes) * 3 * E + al256(sizeof(int) * 3 * E) + al256(sizeof(SchedEntry) * 3 * E) + 256;
+}
+
+size_t rk4_sorted_scratch_bytes(long long N, long long nodes, int storage, int E)
 {
     long long nbins = ((nodes - 1) >> sort_shift(nodes)) + 1;
     size_t per = al256(4 * N) * 3 + al256(2 * N) * 3 + al256(4 * N) + al256(N) + al256(4 * N);
     long long nb = (nbins + SCAN_TILE - 1) / SCAN_TILE;
-    return 2 * per + al256(4 * N) + 2 * al256(4 * nbins) + al256(4 * nb);
+    size_t b = 2 * per + al256(4 * N) + 2 * al256(4 * nbins) + al256(4 * nb);
+    if (storage == LCS_F32) b += slice_bytes(nodes, E);
+    return b;
 }
 
 static TState carve_state(char *&p, long long N)
@@ -1016,9 +1156,25 @@ static cudaError_t launch_sorted3(const RectParams &P, const lcs_field *f, const
     unsigned *cursor = (unsigned *)p;
     p += al256(4 * nbins);
     unsigned *bsum = (unsigned *)p;
+    p += al256(4 * nb);
     const int bt = 256;
     const unsigned grid = (unsigned)((N + bt - 1) / bt);
-    const int E = L.episode_steps > 0 ? L.episode_steps : 16;
+    const int E = L.episode_steps > 0 ? L.episode_steps : LCS_EPISODE_STEPS;
+    // FP32 storage: time slices (16-byte nodes) instead of 32-byte interval pairs per corner
+    const bool use_slices = ST == LCS_F32;
+    const size_t slice_stride = al256(16 * (size_t)f->nodes) / 16;
+    float4 *slices = nullptr;
+    int *smap = nullptr, *nsl = nullptr;
+    SchedEntry *stab = nullptr;
+    if (use_slices) {
+        slices = (float4 *)p;
+        p += al256(16 * (size_t)f->nodes) * 3 * E;
+        smap = (int *)p;
+        p += al256(sizeof(int) * 3 * E);
+        stab = (SchedEntry *)p;
+        p += al256(sizeof(SchedEntry) * 3 * E);
+        nsl = (int *)p;
+    }
     for (int job = 0; job < L.njobs; ++job) {
         ep_init_kernel<<<grid, bt, 0, s>>>(P, A.seeds, N, SA, A.job_tend, job);
         const int ns = L.host_nsteps[job];
@@ -1029,8 +1185,17 @@ static cudaError_t launch_sorted3(const RectParams &P, const lcs_field *f, const
             scan_top_kernel<<<1, 1024, 0, s>>>(bsum, (int)nb);
             scan_down_kernel<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum, cursor);
             ep_scatter_kernel<<<grid, bt, 0, s>>>(SA, SB, N, keys, cursor);
-            ep_advect3_kernel<ST><<<grid, bt, 0, s>>>(P, (const char *)f->d_frames, f->frame_stride, A, SB, job, s0,
-                                                      s0 + E);
+            const int s1 = s0 + E < ns ? s0 + E : ns;
+            if (use_slices) {
+                ep_slice_table_kernel<<<1, 32, 0, s>>>(A.sched, A.nsteps_max, job, s0, s1, smap, stab, nsl);
+                dim3 fg((unsigned)((f->nodes + 255) / 256), (unsigned)(3 * (s1 - s0)));
+                ep_slice_fill_kernel<<<fg, 256, 0, s>>>((const char *)f->d_frames, f->frame_stride, f->nodes, stab,
+                                                         nsl, slices, slice_stride);
+                ep_advect3s_kernel<<<grid, bt, 0, s>>>(P, slices, slice_stride, smap, A, SB, job, s0, s1);
+            } else {
+                ep_advect3_kernel<ST><<<grid, bt, 0, s>>>(P, (const char *)f->d_frames, f->frame_stride, A, SB, job,
+                                                          s0, s1);
+            }
             TState t = SA;
             SA = SB;
             SB = t;

@@ -443,7 +443,7 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     size_t jb = align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs);
     size_t sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
     bool want_sorted = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
-    size_t wb = want_sorted ? rk4_sorted_scratch_bytes(s->N, f->nodes) : 0;
+    size_t wb = want_sorted ? rk4_sorted_scratch_bytes(s->N, f->nodes, f->storage, LCS_EPISODE_STEPS) : 0;
     lcs_status st = scratch_reserve(ctx, jb + sb + wb);
     if (st != LCS_OK) return st;
     char *p = (char *)ctx->d_scratch;
