@@ -163,7 +163,7 @@ def reference_arm(args, rank, world):
     # calibrate: a small block first, then one sized for about 5 s per step
     s_small, dt_small, _, _ = oracle_sample_run(g, 4)
     per_seed = dt_small / ((4 + 4) ** 3)
-    side = int(max(4, min(48, (5.0 / max(per_seed, 1e-9)) ** (1 / 3) - 4)))
+    side = int(max(4, min(72, (5.0 / max(per_seed, 1e-9)) ** (1 / 3) - 4)))
     if args.warmup > 0:
         oracle_sample_run(g, 4)
     times = []
@@ -234,6 +234,9 @@ def our_arm(args, rank, world, local):
 
     adv_events = [(ev(), ev()) for _ in range(args.steps)]
     t_start, t_stop = ev(), ev()
+    for ph in range(4):
+        lcs.lcs_timing_read(ctx, ph)            # drop anything recorded before
+    lcs.lcs_timing_enable(ctx, True)
     with ClockSampler(local) as clk:
         barrier()
         t_start.record(stream)
@@ -242,6 +245,9 @@ def our_arm(args, rank, world, local):
         t_stop.record(stream)
         barrier()
     lcs.lcs_synchronize(ctx)
+    phase = {name: lcs.lcs_timing_read(ctx, ph) for ph, name in
+             enumerate(("advect", "rebundle", "slices", "cg_ftle"))}
+    lcs.lcs_timing_enable(ctx, False)
     elapsed = t_start.elapsed_time(t_stop) / 1e3
     adv_ms = [a.elapsed_time(b) for a, b in adv_events]
     if world > 1:
@@ -285,20 +291,25 @@ def our_arm(args, rank, world, local):
     d2h = ftle_h.numel() * 4 + C_h.numel() * 8
 
     pk, pk_kind = peaks()
-    adv_s = sum(adv_ms) / len(adv_ms) / 1e3
-    flops = float(N) * NSTEPS * FLOP_PER_TRACER_STEP
+    # dominant kernel: the RK4 advection launches (episodes of the re-bundled path); their summed
+    # event time over the timed steps, divided by their count, is the average launch duration
+    adv_ms_total, adv_launches = phase["advect"]
+    adv_launch_s = adv_ms_total / max(adv_launches, 1) / 1e3
+    steps_per_launch = NSTEPS * args.steps / max(adv_launches, 1)
+    flops = float(N) * steps_per_launch * FLOP_PER_TRACER_STEP
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s at the maximum SM clock
-    achieved = flops / adv_s / 1e12
+    achieved = flops / adv_launch_s / 1e12
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
+    prof = os.path.join(ROOT, "profiles", "ep_advect3_traffic.json")
+    if os.path.exists(prof) and (args.seeds_side, args.grid, args.storage) == (N_SIDE, N_GRID, "f32"):
         try:
             tj = json.load(open(prof))
-            if tj.get("kernel") == "rk4_gather_kernel<3,0>" and tj.get("source_sha") == _src_sha():
+            if tj.get("source_sha") == _src_sha():
                 traffic = tj.get("bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
+    n_ep = adv_launches / max(args.steps, 1)
     line = {
         "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -313,17 +324,21 @@ def our_arm(args, rank, world, local):
         "tracer_steps_per_s": value * NSTEPS,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic,
-                     "kernel": "rk4_gather_kernel<3,f32>", "flop_per_launch": flops,
-                     "avg_launch_ms": adv_s * 1e3,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, pk_kind)},
+                     "kernel": "ep_advect3_kernel (RK4 episode of %d steps)" % round(steps_per_launch),
+                     "flop_per_launch": flops, "avg_launch_ms": adv_launch_s * 1e3, "launches": adv_launches,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, pk_kind),
+                     "limiter": "L1 data-pipe wavefronts of the stencil gathers (ncu: ~93% busy), not FP32 issue"},
+        "phases_ms_per_step": {k: v[0] / args.steps for k, v in phase.items()},
         "clocks": clocks,
         "e2e": {"value": world * N / e2e_el if e2e_t else None, "unit": "seeds/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_el * 1e3},
-        "gpu_launches": 3 * args.steps,
+        # ours per step: schedule, init, finalize, FD/CG/FTLE, and per episode 3 scan + scatter +
+        # slice table + slice fill + advection
+        "gpu_launches": int(round(args.steps * 4 + adv_launches * 7)),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, dts, _, _ = oracle_sample_run(g, 4)                 # calibration: 8^3 tracers
-        side = int(max(4, min(40, (10.0 / max(dts / 512.0, 1e-9)) ** (1 / 3) - 4)))
+        side = int(max(4, min(96, (10.0 / max(dts / 512.0, 1e-9)) ** (1 / 3) - 4)))
         s, dt, nth, integrated = oracle_sample_run(g, side)
         line["cpu_baseline"] = {"value": s / dt, "unit": "seeds/s", "cores": nth, "kind": "oracle",
                                 "sample": "%d^3-seed block of the 256^3 lattice with its 2-seed stencil halo "
@@ -345,7 +360,7 @@ def _src_sha():
     import hashlib
 
     h = hashlib.sha1()
-    for name in ("advect_rect.cu", "lcs_internal.cuh"):
+    for name in ("advect_episodes.cu", "rect_device.cuh"):
         with open(os.path.join(ROOT, "paper_2209_13775_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]

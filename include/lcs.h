@@ -187,8 +187,10 @@ typedef struct {
     int walk_limit;             /* tet walk steps per point location (0 = 512)        */
     int block_threads;          /* 0 = library choice                                 */
     int variant;                /* 0 = library choice; 1 = cached gather;
-                                   2 = shared-memory frame ring (2D rectilinear)      */
+                                   2 = shared-memory frame ring (2D rectilinear);
+                                   3 = tracers re-bundled by cell between episodes (3D) */
     const void *surrogate;      /* reserved for LCS_SURROGATE                         */
+    int episode_steps;          /* variant 3: RK4 steps between re-bundlings (0 = 16) */
 } lcs_advect_opts;
 
 /* Flow-map storage for `njobs` integrations of one lattice.                 */
@@ -229,6 +231,24 @@ lcs_status lcs_cauchy_green(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double
  * pass.  lambda_max and C may be NULL.  job = -1 writes every job.         */
 lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
                     double *C, int on_device);
+
+/* ------------------------------------------------------------ kernel timing */
+
+/* Time the library's kernels by phase with CUDA events recorded on the
+ * context's stream around each launch (off by default; costs two event
+ * records per launch).  Phases: */
+enum {
+    LCS_PHASE_ADVECT = 0,     /* advection kernels (RK4 step loops)                  */
+    LCS_PHASE_REBUNDLE = 1,   /* re-bundling tracers by cell (scan, scatter)          */
+    LCS_PHASE_SLICES = 2,     /* time slices of the field for an episode              */
+    LCS_PHASE_CG = 3          /* finite differences, Cauchy-Green, eigenvalue, FTLE   */
+};
+lcs_status lcs_timing_enable(lcs_ctx *ctx, int on);
+
+/* Wait for the recorded launches of `phase`, return their summed duration in
+ * milliseconds and their count (either pointer may be NULL), and start a new
+ * tally.                                                                    */
+lcs_status lcs_timing_read(lcs_ctx *ctx, int phase, double *ms, long long *launches);
 
 /* ------------------------------------- advection without device allocation */
 

@@ -64,13 +64,85 @@ extern "C" lcs_status lcs_create(lcs_ctx **out, int device, void *stream)
     return LCS_OK;
 }
 
+static void tm_release_all(lcs_ctx *ctx)
+{
+    for (int p = 0; p < LCS_NPHASES; ++p) {
+        for (auto &pr : ctx->ev_done[p]) {
+            ctx->ev_pool.push_back(pr.first);
+            ctx->ev_pool.push_back(pr.second);
+        }
+        ctx->ev_done[p].clear();
+        if (ctx->ev_open[p]) ctx->ev_pool.push_back(ctx->ev_open[p]);
+        ctx->ev_open[p] = nullptr;
+    }
+}
+
 extern "C" void lcs_destroy(lcs_ctx *ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->d_errword) cudaFree(ctx->d_errword);
     if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+    tm_release_all(ctx);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     delete ctx;
+}
+
+static cudaEvent_t tm_event(lcs_ctx *ctx)
+{
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void lcs_tm_begin(lcs_ctx *ctx, int phase, cudaStream_t s)
+{
+    if (!ctx || !ctx->timing || phase < 0 || phase >= LCS_NPHASES || ctx->ev_open[phase]) return;
+    cudaEvent_t e = tm_event(ctx);
+    if (e && cudaEventRecord(e, s) == cudaSuccess) ctx->ev_open[phase] = e;
+}
+
+void lcs_tm_end(lcs_ctx *ctx, int phase, cudaStream_t s)
+{
+    if (!ctx || !ctx->timing || phase < 0 || phase >= LCS_NPHASES || !ctx->ev_open[phase]) return;
+    cudaEvent_t e = tm_event(ctx);
+    if (e && cudaEventRecord(e, s) == cudaSuccess) ctx->ev_done[phase].push_back({ctx->ev_open[phase], e});
+    ctx->ev_open[phase] = nullptr;
+}
+
+extern "C" lcs_status lcs_timing_enable(lcs_ctx *ctx, int on)
+{
+    if (!ctx) return LCS_EINVAL;
+    ctx->timing = on != 0;
+    if (!ctx->timing) tm_release_all(ctx);
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_timing_read(lcs_ctx *ctx, int phase, double *ms, long long *launches)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (phase < 0 || phase >= LCS_NPHASES) return fail(ctx, LCS_EINVAL, "lcs_timing_read: phase %d", phase);
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    double tot = 0.0;
+    long long n = 0;
+    for (auto &pr : ctx->ev_done[phase]) {
+        CUDA_TRY(ctx, cudaEventSynchronize(pr.second));
+        float t = 0.0f;
+        CUDA_TRY(ctx, cudaEventElapsedTime(&t, pr.first, pr.second));
+        tot += t;
+        ++n;
+        ctx->ev_pool.push_back(pr.first);
+        ctx->ev_pool.push_back(pr.second);
+    }
+    ctx->ev_done[phase].clear();
+    if (ms) *ms = tot;
+    if (launches) *launches = n;
+    return LCS_OK;
 }
 
 extern "C" const char *lcs_last_error(const lcs_ctx *ctx)
@@ -443,7 +515,8 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     size_t jb = align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs);
     size_t sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
     bool want_sorted = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
-    size_t wb = want_sorted ? rk4_sorted_scratch_bytes(s->N, f->nodes, f->storage, LCS_EPISODE_STEPS) : 0;
+    int E = o->episode_steps > 0 ? std::min(o->episode_steps, 1024) : LCS_EPISODE_STEPS;
+    size_t wb = want_sorted ? rk4_sorted_scratch_bytes(s->N, f->nodes, f->storage, E) : 0;
     lcs_status st = scratch_reserve(ctx, jb + sb + wb);
     if (st != LCS_OK) return st;
     char *p = (char *)ctx->d_scratch;
@@ -460,6 +533,7 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     SchedEntry *sched = (SchedEntry *)p;
     CUDA_TRY(ctx, launch_rk4_schedule(f->d_times, f->nframes, f->time_periodic, f->period, J, D, sched, ctx->stream));
     Rk4Launch L;
+    L.ctx = ctx;
     L.field = f;
     L.seeds = s->d_xyz;
     L.N = s->N;
@@ -475,7 +549,7 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.out_texit = fm->d_texit;
     L.block_threads = o->block_threads;
     L.variant = o->variant;
-    L.episode_steps = 0;
+    L.episode_steps = E;
     L.host_nsteps = J.nsteps;
     L.work = want_sorted ? (char *)ctx->d_scratch + jb + sb : nullptr;
     if (launch_rk4_rect(ctx, L, ctx->stream) < 0)
@@ -590,7 +664,9 @@ static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *f
     L.lam = lam ? (on_device ? lam : (double *)q) : nullptr;
     if (lam && !on_device) q += align256(bL);
     L.ftle = ftle ? (on_device ? ftle : (float *)q) : nullptr;
+    lcs_tm_begin(ctx, 3, ctx->stream);
     cudaError_t e = launch_cg_ftle(L, ctx->stream);
+    lcs_tm_end(ctx, 3, ctx->stream);
     if (e == cudaSuccess && !on_device) {
         if (C) e = cudaMemcpyAsync(C, L.C, bC, cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess && lam) e = cudaMemcpyAsync(lam, L.lam, bL, cudaMemcpyDeviceToHost, ctx->stream);

@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "lcs.h"
@@ -24,6 +25,9 @@
 // treated as failed (error bit set, the waiting block stops its work)
 #define LCS_WAIT_LIMIT_NS 1000000000ull
 
+// kernel phases timed with CUDA events when a context's timing is on
+#define LCS_NPHASES 4
+
 struct lcs_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -34,7 +38,16 @@ struct lcs_ctx {
     // scratch: device memory the library reuses across calls (queue counters)
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    // per-phase event timing (lcs_timing_enable / lcs_timing_read)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    cudaEvent_t ev_open[LCS_NPHASES] = {};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_done[LCS_NPHASES];
 };
+
+// bracket the launches of one phase with events on stream s (no-ops unless timing is on)
+void lcs_tm_begin(lcs_ctx *ctx, int phase, cudaStream_t s);
+void lcs_tm_end(lcs_ctx *ctx, int phase, cudaStream_t s);
 
 struct lcs_field {
     lcs_ctx *ctx = nullptr;
@@ -131,6 +144,7 @@ struct JobDev {
 };
 
 struct Rk4Launch {
+    lcs_ctx *ctx;
     const lcs_field *field;
     const float *seeds;       // [dim][N]
     long long N;

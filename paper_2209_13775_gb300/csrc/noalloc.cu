@@ -92,6 +92,7 @@ extern "C" lcs_status lcs_advect_rk4_noalloc(lcs_ctx *ctx, const lcs_field *f, c
     if (e != cudaSuccess) return na_fail(ctx, LCS_ECUDA, "lcs_advect_rk4_noalloc: schedule launch failed");
     if (n == 0) return LCS_OK;
     Rk4Launch L;
+    L.ctx = ctx;
     L.field = f;
     L.seeds = seeds;
     L.N = n;

@@ -25,7 +25,9 @@ STATUS_NAMES = {0: "LCS_OK", 1: "LCS_EINVAL", 2: "LCS_ENOMEM", 3: "LCS_ECUDA", 4
 EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs_synchronize",
            "lcs_load_field", "lcs_update_frames", "lcs_free_field", "lcs_seed_grid", "lcs_seeds_count",
            "lcs_seeds_get", "lcs_free_seeds", "lcs_flowmap_create", "lcs_advect", "lcs_flowmap_get",
-           "lcs_free_flowmap", "lcs_cauchy_green", "lcs_ftle", "lcs_advect_rk4_noalloc"]
+           "lcs_free_flowmap", "lcs_cauchy_green", "lcs_ftle", "lcs_timing_enable", "lcs_timing_read",
+           "lcs_advect_rk4_noalloc"]
+PHASE_ADVECT, PHASE_REBUNDLE, PHASE_SLICES, PHASE_CG = 0, 1, 2, 3
 NOALLOC_MAX_STEPS = 43680
 
 
@@ -55,7 +57,8 @@ class AdvectOpts(ctypes.Structure):
                 ("njobs", ctypes.c_int), ("job_t0", ctypes.c_void_p), ("job_T", ctypes.c_void_p),
                 ("dt", ctypes.c_double), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("h0", ctypes.c_double), ("max_steps", ctypes.c_longlong), ("walk_limit", ctypes.c_int),
-                ("block_threads", ctypes.c_int), ("variant", ctypes.c_int), ("surrogate", ctypes.c_void_p)]
+                ("block_threads", ctypes.c_int), ("variant", ctypes.c_int), ("surrogate", ctypes.c_void_p),
+                ("episode_steps", ctypes.c_int)]
 
 
 _lib = None
@@ -84,6 +87,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_flowmap_get": ([P, P, I, P, P, P, I], S), "lcs_free_flowmap": ([P], None),
         "lcs_cauchy_green": ([P, P, I, P, I], S), "lcs_ftle": ([P, P, I, P, P, P, I], S),
         "lcs_advect_rk4_noalloc": ([P, P, P, LL, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P], S),
+        "lcs_timing_enable": ([P, I], S), "lcs_timing_read": ([P, I, P, P], S),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -232,11 +236,12 @@ def lcs_free_seeds(seeds):
 # -------------------------------------------------------------- flow map
 
 def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol=1e-6, atol=1e-6, h0=0.01,
-                max_steps=0, walk_limit=0, block_threads=0, variant=0):
+                max_steps=0, walk_limit=0, block_threads=0, variant=0, episode_steps=0):
     o = AdvectOpts()
     o.method, o.t0, o.T, o.dt = int(method), float(t0), float(T), float(dt)
     o.rtol, o.atol, o.h0, o.max_steps = float(rtol), float(atol), float(h0), int(max_steps)
     o.walk_limit, o.block_threads, o.variant = int(walk_limit), int(block_threads), int(variant)
+    o.episode_steps = int(episode_steps)
     if job_t0 is not None:
         a = np.ascontiguousarray(job_t0, dtype=np.float64)
         b = np.ascontiguousarray(job_T, dtype=np.float64)
@@ -284,6 +289,20 @@ def lcs_ftle(ctx, fm, job, ftle, lambda_max=None, C=None):
     if len(devs) > 1:
         raise ValueError("outputs must all be host or all be device buffers")
     _check(ctx, load().lcs_ftle(ctx, fm, int(job), *[ctypes.c_void_p(p) for p, _ in ptrs], devs.pop()))
+
+
+# ------------------------------------------------------------ kernel timing
+
+def lcs_timing_enable(ctx, on=True):
+    _check(ctx, load().lcs_timing_enable(ctx, int(bool(on))))
+
+
+def lcs_timing_read(ctx, phase):
+    """(total milliseconds, launches) of the phase's kernels since the last read."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    _check(ctx, load().lcs_timing_read(ctx, int(phase), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 # ---------------------------------------------- advection without allocation
