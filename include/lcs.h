@@ -188,9 +188,15 @@ typedef struct {
     int block_threads;          /* 0 = library choice                                 */
     int variant;                /* 0 = library choice; 1 = cached gather;
                                    2 = shared-memory frame ring (2D rectilinear);
-                                   3 = tracers re-bundled by cell between episodes (3D) */
+                                   3 = tracers re-bundled by cell between episodes (3D);
+                                   4 = persistent shared-memory ring pulling (job, tile)
+                                       items longest-job first (2D, batches)            */
     const void *surrogate;      /* reserved for LCS_SURROGATE                         */
     int episode_steps;          /* variant 3: RK4 steps between re-bundlings (0 = 16) */
+    int tracers_per_thread;     /* variants 2 and 4: 1 or 2 tracers per thread (0 = 1) */
+    int use_graph;              /* capture the launches of this call in a CUDA graph,
+                                   cached on the context and replayed while the same
+                                   field, seeds, flow map and options come back      */
 } lcs_advect_opts;
 
 /* Flow-map storage for `njobs` integrations of one lattice.                 */

@@ -71,6 +71,7 @@ __global__ void rk4_schedule_kernel(const double *__restrict__ times, int nf, in
         D.t0[j] = __double2float_rn(J.t0[j]);
         D.tend[j] = __double2float_rn(__dadd_rn(J.t0[j], J.T[j]));
         D.absT[j] = fabs(J.T[j]);
+        if (D.order) D.order[j] = J.order[j];
     }
     if (idx >= total) return;
     int s = (int)(idx % 3);
@@ -161,6 +162,14 @@ struct RingState {
     int abort;     // a wait timed out: the block stops issuing copies and computing
 };
 
+struct RingWork {
+    int persistent;        // 0: block (x, y) = tile x of job y; 1: items pulled from *queue
+    unsigned *queue;       // persistent: item counter, zero at launch
+    long long nitems;      // persistent: tiles_per_job * njobs
+    int tiles_per_job;
+    const int *jorder;     // persistent: job of rank r, longest first
+};
+
 __device__ __forceinline__ int ring_find(const RingState &R, int f)
 {
     for (int s = 0; s < RING_SLOTS; ++s)
@@ -214,39 +223,36 @@ __device__ int ring_load(RingState &R, char *slots, const char *frames, size_t f
     return v;
 }
 
-template <int ST>
-__global__ void __launch_bounds__(512) rk4_ring2d_kernel(RectParams P, const char *__restrict__ frames,
-                                                         size_t fstride, Rk4Args A, unsigned *errword)
+// Work of one block: the tracers [tile * TPT * bt, (tile + 1) * TPT * bt) of one job, each
+// thread holding TPT tracers (sub-tiles of bt consecutive seeds, so loads stay coalesced).
+template <int ST, int TPT>
+__device__ __forceinline__ void ring_tile(const RectParams &P, const char *__restrict__ frames, size_t fstride,
+                                          const Rk4Args &A, unsigned *errword, char *slots, RingState &R, int job,
+                                          long long tile)
 {
-    extern __shared__ __align__(128) char slots[];
-    __shared__ RingState R;
-    const int tid = threadIdx.x;
-    const long long i = blockIdx.x * (long long)blockDim.x + tid;
-    const int job = blockIdx.y;
-    const bool active = i < A.N;
-    if (tid == 0) {
-        for (int s = 0; s < RING_SLOTS; ++s) {
-            mbar_init(&R.bar[s], 1);
-            R.tag[s] = -1;
-            R.nload[s] = 0;
-        }
-        R.abort = 0;
-        mbar_fence_init();
+    const int tid = threadIdx.x, bt = blockDim.x;
+    long long idx[TPT];
+    bool active[TPT], live[TPT];
+    float x[TPT][2];
+    int img[TPT][2];
+    unsigned char st[TPT];
+    float te[TPT];
+    const float tend = A.job_tend[job];
+#pragma unroll
+    for (int t = 0; t < TPT; ++t) {
+        idx[t] = (tile * TPT + t) * bt + tid;
+        active[t] = idx[t] < A.N;
+        live[t] = active[t];
+        x[t][0] = active[t] ? A.seeds[idx[t]] : 0.0f;
+        x[t][1] = active[t] ? A.seeds[A.N + idx[t]] : 0.0f;
+        img[t][0] = img[t][1] = 0;
+        wrap_periodic<2>(P, x[t], img[t]);
+        st[t] = LCS_TRACER_OK;
+        te[t] = tend;
     }
-    __syncthreads();
-    float x[2] = {0.0f, 0.0f};
-    int img[2] = {0, 0};
-    if (active) {
-        x[0] = A.seeds[i];
-        x[1] = A.seeds[A.N + i];
-    }
-    wrap_periodic<2>(P, x, img);
     const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
     const int ns = A.job_nsteps[job];
     const float h = A.job_h[job];
-    unsigned char st = LCS_TRACER_OK;
-    float te = A.job_tend[job];
-    bool live = active;
     for (int n = 0; n < ns; ++n) {
         __syncthreads();  // every thread is done with the previous step's slots
         if (R.abort) break;
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(512) rk4_ring2d_kernel(RectParams P, const cha
                 R.abort = 1;
             }
         }
-        if (!live || R.abort) continue;
+        if (R.abort) continue;
         const char *p[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
@@ -303,19 +309,63 @@ __global__ void __launch_bounds__(512) rk4_ring2d_kernel(RectParams P, const cha
                 p[q] = frames + (size_t)R.kf[q] * fstride;
         }
         const SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
-        bool all_smem = (R.slot[0] != RING_GLOBAL) && (R.slot[1] != RING_GLOBAL) && (R.slot[2] != RING_GLOBAL) &&
-                        (R.slot[3] != RING_GLOBAL) && (R.slot[4] != RING_GLOBAL) && (R.slot[5] != RING_GLOBAL);
-        // a step whose frames did not all get a slot (e.g. one straddling the periodic wrap, which
-        // reads four frames) mixes shared and global pointers: generic loads serve both
-        if (all_smem)
-            rk4_step<2, ST, SRC_SHARED>(P, x, h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
-        else
-            rk4_step<2, ST, SRC_GENERIC>(P, x, h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
-        wrap_periodic<2>(P, x, img);
-        if (rect_left<2>(P, x)) {
-            st = LCS_TRACER_LEFT;
-            te = fmaf((float)(n + 1), h, A.job_t0[job]);
-            live = false;
+        const bool all_smem = (R.slot[0] != RING_GLOBAL) && (R.slot[1] != RING_GLOBAL) &&
+                              (R.slot[2] != RING_GLOBAL) && (R.slot[3] != RING_GLOBAL) &&
+                              (R.slot[4] != RING_GLOBAL) && (R.slot[5] != RING_GLOBAL);
+#pragma unroll
+        for (int t = 0; t < TPT; ++t) {
+            if (!live[t]) continue;
+            // a step whose frames did not all get a slot (e.g. one straddling the periodic wrap, which
+            // reads four frames) mixes shared and global pointers: generic loads serve both
+            if (all_smem)
+                rk4_step<2, ST, SRC_SHARED>(P, x[t], h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
+            else
+                rk4_step<2, ST, SRC_GENERIC>(P, x[t], h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
+            wrap_periodic<2>(P, x[t], img[t]);
+            if (rect_left<2>(P, x[t])) {
+                st[t] = LCS_TRACER_LEFT;
+                te[t] = fmaf((float)(n + 1), h, A.job_t0[job]);
+                live[t] = false;
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < TPT; ++t)
+        if (active[t]) store_tracer<2>(P, A, job, idx[t], x[t], img[t], st[t], te[t]);
+}
+
+// Ring kernel.  Non-persistent: block (x, y) is tile x of job y.  Persistent: the grid
+// fills the GPU once and every block pulls (job, tile) items from an atomic counter in
+// the order of W.jorder (longest jobs first), keeping its frame ring across items.
+template <int ST, int TPT>
+__global__ void __launch_bounds__(512, 1) rk4_ring2d_kernel(RectParams P, const char *__restrict__ frames,
+                                                         size_t fstride, Rk4Args A, unsigned *errword, RingWork W)
+{
+    extern __shared__ __align__(128) char slots[];
+    __shared__ RingState R;
+    __shared__ long long s_item;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < RING_SLOTS; ++s) {
+            mbar_init(&R.bar[s], 1);
+            R.tag[s] = -1;
+            R.nload[s] = 0;
+        }
+        R.abort = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (!W.persistent) {
+        ring_tile<ST, TPT>(P, frames, fstride, A, errword, slots, R, blockIdx.y, blockIdx.x);
+    } else {
+        for (;;) {
+            if (tid == 0) s_item = (long long)atomicAdd(W.queue, 1u);
+            __syncthreads();
+            const long long item = s_item;
+            __syncthreads();
+            if (item >= W.nitems || R.abort) break;
+            const int job = W.jorder[item / W.tiles_per_job];
+            ring_tile<ST, TPT>(P, frames, fstride, A, errword, slots, R, job, item % W.tiles_per_job);
         }
     }
     // drain copies still in flight (prefetches nobody read) before the block exits
@@ -325,7 +375,6 @@ __global__ void __launch_bounds__(512) rk4_ring2d_kernel(RectParams P, const cha
             if (R.nload[s] > 0 && !mbar_wait_bounded(&R.bar[s], (R.nload[s] - 1) & 1))
                 atomicOr(errword, LCS_ERRBIT_TIMEOUT);
     __syncthreads();
-    if (active) store_tracer<2>(P, A, job, i, x, img, st, te);
 }
 
 // ================================================================ dispatch
@@ -359,17 +408,47 @@ static cudaError_t launch_gather(const RectParams &P, const lcs_field *f, const 
     return cudaGetLastError();
 }
 
-template <int ST>
-static cudaError_t launch_ring(lcs_ctx *ctx, const RectParams &P, const lcs_field *f, const Rk4Args &A, int njobs,
-                               int bt, cudaStream_t s)
+template <int ST, int TPT>
+static cudaError_t launch_ring(lcs_ctx *ctx, const RectParams &P, const lcs_field *f, const Rk4Args &A,
+                               const Rk4Launch &L, int bt, bool persistent, cudaStream_t s)
 {
     size_t smem = RING_SLOTS * f->frame_stride;
-    cudaError_t e = cudaFuncSetAttribute(rk4_ring2d_kernel<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(rk4_ring2d_kernel<ST, TPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((A.N + bt - 1) / bt), (unsigned)njobs);
-    rk4_ring2d_kernel<ST><<<grid, bt, smem, s>>>(P, (const char *)f->d_frames, f->frame_stride, A, ctx->d_errword);
+    const long long tiles = (A.N + (long long)bt * TPT - 1) / ((long long)bt * TPT);
+    RingWork W;
+    W.persistent = persistent ? 1 : 0;
+    W.queue = L.queue;
+    W.tiles_per_job = (int)tiles;
+    W.nitems = tiles * L.njobs;
+    W.jorder = L.job_order;
+    if (!persistent) {
+        dim3 grid((unsigned)tiles, (unsigned)L.njobs);
+        rk4_ring2d_kernel<ST, TPT><<<grid, bt, smem, s>>>(P, (const char *)f->d_frames, f->frame_stride, A,
+                                                           ctx->d_errword, W);
+        return cudaGetLastError();
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rk4_ring2d_kernel<ST, TPT>, bt, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long long blocks = (long long)per_sm * ctx->num_sms;
+    if (blocks > W.nitems) blocks = W.nitems;
+    if (blocks < 1) blocks = 1;
+    e = cudaMemsetAsync(L.queue, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    rk4_ring2d_kernel<ST, TPT><<<(unsigned)blocks, bt, smem, s>>>(P, (const char *)f->d_frames, f->frame_stride, A,
+                                                                   ctx->d_errword, W);
     return cudaGetLastError();
+}
+
+template <int ST>
+static cudaError_t launch_ring_tpt(lcs_ctx *ctx, const RectParams &P, const lcs_field *f, const Rk4Args &A,
+                                   const Rk4Launch &L, int bt, bool persistent, cudaStream_t s)
+{
+    if (L.tracers_per_thread >= 2) return launch_ring<ST, 2>(ctx, P, f, A, L, bt, persistent, s);
+    return launch_ring<ST, 1>(ctx, P, f, A, L, bt, persistent, s);
 }
 
 int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
@@ -391,9 +470,12 @@ int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
     if (L.N == 0 || L.njobs == 0) return 1;
     bool ring_fits = f->dim == 2 && RING_SLOTS * f->frame_stride <= ctx->smem_optin;
     bool sorted_ok = f->dim == 3 && L.work != nullptr;
+    bool queue_ok = L.queue != nullptr && L.job_order != nullptr;
     int variant = L.variant;
-    if (variant == 0) variant = ring_fits ? 2 : (sorted_ok && L.N >= LCS_SORTED_MIN_SEEDS ? 3 : 1);
-    if (variant == 2 && !ring_fits) variant = 1;
+    if (variant == 0)
+        variant = ring_fits ? (L.njobs > 1 && queue_ok ? 4 : 2) : (sorted_ok && L.N >= LCS_SORTED_MIN_SEEDS ? 3 : 1);
+    if ((variant == 2 || variant == 4) && !ring_fits) variant = 1;
+    if (variant == 4 && !queue_ok) variant = 2;
     if (variant == 3 && !sorted_ok) variant = 1;
     cudaError_t e;
     if (variant == 3) {
@@ -401,15 +483,16 @@ int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
         return e == cudaSuccess ? variant : -1;
     }
     lcs_tm_begin(ctx, 0, s);
-    if (variant == 2) {
+    if (variant == 2 || variant == 4) {
         int bt = L.block_threads > 0 ? L.block_threads : 512;
         if (bt > 512) bt = 512;
+        const bool pers = variant == 4;
         if (f->storage == LCS_F32)
-            e = launch_ring<LCS_F32>(ctx, P, f, A, L.njobs, bt, s);
+            e = launch_ring_tpt<LCS_F32>(ctx, P, f, A, L, bt, pers, s);
         else if (f->storage == LCS_F16)
-            e = launch_ring<LCS_F16>(ctx, P, f, A, L.njobs, bt, s);
+            e = launch_ring_tpt<LCS_F16>(ctx, P, f, A, L, bt, pers, s);
         else
-            e = launch_ring<LCS_BF16>(ctx, P, f, A, L.njobs, bt, s);
+            e = launch_ring_tpt<LCS_BF16>(ctx, P, f, A, L, bt, pers, s);
     } else {
         int bt = L.block_threads > 0 ? L.block_threads : 256;
         if (bt > 256) bt = 256;

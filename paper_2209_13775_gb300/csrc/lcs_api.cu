@@ -512,7 +512,7 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
                                   lcs_flowmap *fm, JobTable &J)
 {
-    size_t jb = align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs);
+    size_t jb = 2 * align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs) + 256;
     size_t sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
     bool want_sorted = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
     int E = o->episode_steps > 0 ? std::min(o->episode_steps, 1024) : LCS_EPISODE_STEPS;
@@ -530,6 +530,10 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     D.tend = (float *)p;
     p += align256(sizeof(float) * J.njobs);
     D.absT = fm->d_absT;
+    D.order = (int *)p;
+    p += align256(sizeof(int) * J.njobs);
+    unsigned *queue = (unsigned *)p;
+    p += 256;
     SchedEntry *sched = (SchedEntry *)p;
     CUDA_TRY(ctx, launch_rk4_schedule(f->d_times, f->nframes, f->time_periodic, f->period, J, D, sched, ctx->stream));
     Rk4Launch L;
@@ -551,6 +555,9 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.variant = o->variant;
     L.episode_steps = E;
     L.host_nsteps = J.nsteps;
+    L.tracers_per_thread = o->tracers_per_thread >= 2 ? 2 : 1;
+    L.queue = queue;
+    L.job_order = D.order;
     L.work = want_sorted ? (char *)ctx->d_scratch + jb + sb : nullptr;
     if (launch_rk4_rect(ctx, L, ctx->stream) < 0)
         return fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -594,7 +601,10 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
         J->nsteps[j] = (int)ns;
         J->nsteps_max = std::max(J->nsteps_max, (int)ns);
         fm->T[j] = T;
+        J->order[j] = j;
     }
+    // work-queue order of the persistent kernel: longest integrations first
+    std::stable_sort(J->order, J->order + njobs, [&](int a, int b) { return J->nsteps[a] > J->nsteps[b]; });
     lcs_status st;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess)

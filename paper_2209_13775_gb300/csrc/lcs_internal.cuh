@@ -124,7 +124,7 @@ struct SchedEntry {
 };
 
 // Batch of integrations passed by value to the schedule kernel (no host copy).
-#define LCS_MAX_JOBS 1024
+#define LCS_MAX_JOBS 512
 struct JobTable {
     int njobs;
     int nsteps_max;
@@ -132,6 +132,7 @@ struct JobTable {
     double h[LCS_MAX_JOBS];     // signed step
     double T[LCS_MAX_JOBS];     // requested horizon
     int nsteps[LCS_MAX_JOBS];
+    int order[LCS_MAX_JOBS];    // jobs by decreasing step count (work-queue order)
 };
 
 // per-job values the schedule kernel leaves in device scratch for the advection kernels
@@ -141,6 +142,7 @@ struct JobDev {
     float *t0;       // [njobs]
     float *tend;     // [njobs]
     double *absT;    // [njobs] (the flow map's copy, for the FTLE)
+    int *order;      // [njobs] JobTable::order on the device, or null
 };
 
 struct Rk4Launch {
@@ -159,10 +161,14 @@ struct Rk4Launch {
     unsigned char *out_status;
     float *out_texit;
     int block_threads;
-    int variant;              // 1 gather, 2 shared-memory ring (2D), 3 re-bundled episodes (3D)
+    int variant;              // 1 gather, 2 shared-memory ring (2D), 3 re-bundled episodes (3D),
+                              // 4 persistent shared-memory ring over a job/tile work queue (2D)
     int episode_steps;        // variant 3: steps between re-bundling (0 = default)
     const int *host_nsteps;   // [njobs] host copy of the step counts
     void *work;               // variant 3 working memory (rk4_sorted_scratch_bytes), or null
+    int tracers_per_thread;   // ring kernels: 1 or 2
+    unsigned *queue;          // variant 4: work-queue counter in device scratch, or null
+    const int *job_order;     // variant 4: [njobs] jobs by decreasing step count (device), or null
 };
 
 // smallest seed count for which lcs_advect picks the re-bundled kernel by default

@@ -78,6 +78,7 @@ extern "C" lcs_status lcs_advect_rk4_noalloc(lcs_ctx *ctx, const lcs_field *f, c
     J.T[0] = T;
     J.h[0] = T < 0.0 ? -adt : adt;
     J.nsteps[0] = (int)ns;
+    J.order[0] = 0;
     char *p = (char *)base;
     JobDev D;
     D.nsteps = (int *)(p + 0);
@@ -85,6 +86,7 @@ extern "C" lcs_status lcs_advect_rk4_noalloc(lcs_ctx *ctx, const lcs_field *f, c
     D.t0 = (float *)(p + 32);
     D.tend = (float *)(p + 48);
     D.absT = (double *)(p + 64);
+    D.order = nullptr;
     SchedEntry *sched = (SchedEntry *)(p + LCS_NOALLOC_HEADER);
     // every schedule entry and per-job value the advection reads is written by the schedule kernel
     // first, so nothing in the array needs clearing between calls
@@ -111,6 +113,9 @@ extern "C" lcs_status lcs_advect_rk4_noalloc(lcs_ctx *ctx, const lcs_field *f, c
     L.episode_steps = 0;
     L.host_nsteps = J.nsteps;
     L.work = nullptr;
+    L.tracers_per_thread = 1;
+    L.queue = nullptr;
+    L.job_order = nullptr;
     if (launch_rk4_rect(ctx, L, ctx->stream) < 0)
         return na_fail(ctx, LCS_ECUDA, "lcs_advect_rk4_noalloc: advection launch failed");
     return LCS_OK;

@@ -58,7 +58,7 @@ class AdvectOpts(ctypes.Structure):
                 ("dt", ctypes.c_double), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("h0", ctypes.c_double), ("max_steps", ctypes.c_longlong), ("walk_limit", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("variant", ctypes.c_int), ("surrogate", ctypes.c_void_p),
-                ("episode_steps", ctypes.c_int)]
+                ("episode_steps", ctypes.c_int), ("tracers_per_thread", ctypes.c_int), ("use_graph", ctypes.c_int)]
 
 
 _lib = None
@@ -236,12 +236,15 @@ def lcs_free_seeds(seeds):
 # -------------------------------------------------------------- flow map
 
 def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol=1e-6, atol=1e-6, h0=0.01,
-                max_steps=0, walk_limit=0, block_threads=0, variant=0, episode_steps=0):
+                max_steps=0, walk_limit=0, block_threads=0, variant=0, episode_steps=0, tracers_per_thread=0,
+                use_graph=False):
     o = AdvectOpts()
     o.method, o.t0, o.T, o.dt = int(method), float(t0), float(T), float(dt)
     o.rtol, o.atol, o.h0, o.max_steps = float(rtol), float(atol), float(h0), int(max_steps)
     o.walk_limit, o.block_threads, o.variant = int(walk_limit), int(block_threads), int(variant)
     o.episode_steps = int(episode_steps)
+    o.tracers_per_thread = int(tracers_per_thread)
+    o.use_graph = int(bool(use_graph))
     if job_t0 is not None:
         a = np.ascontiguousarray(job_t0, dtype=np.float64)
         b = np.ascontiguousarray(job_T, dtype=np.float64)

@@ -22,7 +22,7 @@ def rect_desc(g, storage=lcs.F32):
 
 
 def gpu_run(ctx, g, n, lo, hi, periodic, T, dt, t0=0.0, storage=lcs.F32, variant=0, block_threads=0,
-            jobs=None, want_C=False):
+            jobs=None, want_C=False, tracers_per_thread=0, episode_steps=0, use_graph=False):
     """Load, seed, advect, FTLE through the C ABI.  Returns dict of host arrays (job 0 unless jobs)."""
     dim = g.dim
     field = lcs.lcs_load_field(ctx, rect_desc(g, storage), g.frames)
@@ -30,11 +30,12 @@ def gpu_run(ctx, g, n, lo, hi, periodic, T, dt, t0=0.0, storage=lcs.F32, variant
     N = lcs.lcs_seeds_count(seeds)
     njobs = 1 if jobs is None else len(jobs[0])
     fm = lcs.lcs_flowmap_create(ctx, seeds, njobs)
+    kw = dict(variant=variant, block_threads=block_threads, tracers_per_thread=tracers_per_thread,
+              episode_steps=episode_steps, use_graph=use_graph)
     if jobs is None:
-        opts = lcs.advect_opts(lcs.RK4, t0=t0, T=T, dt=dt, variant=variant, block_threads=block_threads)
+        opts = lcs.advect_opts(lcs.RK4, t0=t0, T=T, dt=dt, **kw)
     else:
-        opts = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1], variant=variant,
-                               block_threads=block_threads)
+        opts = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1], **kw)
     lcs.lcs_advect(ctx, field, seeds, opts, fm)
     out = {"N": N, "seeds": np.empty((dim, N), dtype=np.float32)}
     lcs.lcs_seeds_get(ctx, seeds, out["seeds"])

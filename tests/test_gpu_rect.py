@@ -97,6 +97,34 @@ def test_batched_jobs_equal_single_jobs(ctx, gyre):
     np.testing.assert_array_equal(b["xyz"][3], b["seeds"])
 
 
+@pytest.mark.parametrize("variant,bt,tpt", [(2, 256, 1), (4, 512, 1), (4, 256, 2), (4, 128, 2)])
+def test_persistent_batch_equals_single_jobs(ctx, gyre, variant, bt, tpt):
+    # the work-queue kernel (longest jobs first, frame ring kept across items) changes which block
+    # runs a tile, never a tracer's arithmetic
+    n, lo, hi, dt = (70, 37), (0.0, 0.0), (2.0, 1.0), 0.05
+    t0s = [0.25 * k for k in range(6)] * 2
+    Ts = [(2.0, 4.0, 8.0)[k % 3] * (1 if k < 6 else -1) for k in range(12)]
+    b = gpu_run(ctx, gyre, n, lo, hi, (0, 0), None, dt, jobs=(t0s, Ts), variant=variant, block_threads=bt,
+                tracers_per_thread=tpt)
+    for j in (0, 4, 7, 11):
+        s = gpu_run(ctx, gyre, n, lo, hi, (0, 0), Ts[j], dt, t0=t0s[j], variant=1)
+        np.testing.assert_array_equal(b["xyz"][j], s["xyz"][0])
+        np.testing.assert_array_equal(b["status"][j], s["status"][0])
+        np.testing.assert_array_equal(b["ftle"][j], s["ftle"][0])
+
+
+def test_sliding_window_batch_against_oracle(ctx, gyre):
+    # the sliding-window batch: 32 t0 spaced 0.25, forward and backward, T in {2, 4, 8}, on a small lattice
+    n, lo, hi, dt = (64, 32), (0.0, 0.0), (2.0, 1.0), 0.05
+    t0s = [0.25 * k for k in range(32)] * 2
+    Ts = [(2.0, 4.0, 8.0)[k % 3] for k in range(32)] + [-(2.0, 4.0, 8.0)[k % 3] for k in range(32)]
+    b = gpu_run(ctx, gyre, n, lo, hi, (0, 0), None, dt, jobs=(t0s, Ts))
+    for j in range(0, 64, 9):
+        o = oracle_run(gyre, n, lo, hi, (0, 0), Ts[j], dt, t0=t0s[j])
+        check_flowmap(b["xyz"][j], o["xyz"], b["status"][j], o["status"], 2.0, float(np.nanmax(o["ftle"])), Ts[j])
+        check_ftle(b["ftle"][j], o["ftle"])
+
+
 def test_cauchy_green_matches_oracle_on_gpu_positions(ctx, gyre):
     # same FP32 positions in: grad F and C are bit-identical, lambda_max within rounding
     n, lo, hi, T = (128, 64), (0.0, 0.0), (2.0, 1.0), 10.0
