@@ -218,6 +218,18 @@ lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *
 
 void lcs_free_flowmap(lcs_flowmap *fm);
 
+/* Choose the launch options of an lcs_advect call (variant, block_threads,
+ * tracers_per_thread, episode_steps) by timing candidates with CUDA events on
+ * these very inputs, and write the fastest back into *opts (other fields are
+ * read, not changed).  The choice is remembered in the text file cache_path
+ * (NULL: no cache), keyed by device, field shape, seed count and jobs; a later
+ * call with the same key returns without timing.  Tuning runs lcs_advect into
+ * a temporary flow map (allocated and freed here).
+ * Errors: LCS_EINVAL, LCS_EUNSUPPORTED (not RK4 on a rectilinear field), and
+ * those of lcs_advect.                                                      */
+lcs_status lcs_autotune(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *seeds, lcs_advect_opts *opts,
+                        const char *cache_path);
+
 /* ---------------------------------------- grad F, C, lambda_max, FTLE (a9-a11) */
 
 /* Cauchy-Green tensor C = grad(F)^T grad(F) (Eq. 1) with grad F from finite

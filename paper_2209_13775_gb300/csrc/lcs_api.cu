@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 
 // ------------------------------------------------------------------- errors
@@ -37,6 +38,21 @@ static lcs_status fail(lcs_ctx *ctx, lcs_status st, const char *fmt, ...)
     } while (0)
 
 // ------------------------------------------------------------------ context
+
+unsigned long long lcs_next_uid()
+{
+    static std::atomic<unsigned long long> next{1};
+    return next.fetch_add(1);
+}
+
+static void graph_cache_clear(lcs_ctx *ctx)
+{
+    for (auto &g : ctx->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    ctx->graphs.clear();
+}
 
 extern "C" lcs_status lcs_create(lcs_ctx **out, int device, void *stream)
 {
@@ -85,6 +101,8 @@ extern "C" void lcs_destroy(lcs_ctx *ctx)
     if (ctx->d_scratch) cudaFree(ctx->d_scratch);
     tm_release_all(ctx);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    graph_cache_clear(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
 }
 
@@ -179,6 +197,7 @@ static lcs_status scratch_reserve(lcs_ctx *ctx, size_t bytes)
     if (bytes <= ctx->scratch_bytes) return LCS_OK;
     if (ctx->d_scratch) {
         CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        graph_cache_clear(ctx);  // captured graphs point into the old scratch
         cudaFree(ctx->d_scratch);
         ctx->d_scratch = nullptr;
         ctx->scratch_bytes = 0;
@@ -294,6 +313,7 @@ extern "C" lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *d, cons
     lcs_field *f = new (std::nothrow) lcs_field();
     if (!f) return fail(ctx, LCS_ENOMEM, "host allocation");
     f->ctx = ctx;
+    f->uid = lcs_next_uid();
     f->dim = d->dim;
     f->kind = d->kind;
     f->storage = d->storage;
@@ -407,6 +427,7 @@ extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const 
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     lcs_seeds *s = new (std::nothrow) lcs_seeds();
     if (!s) return fail(ctx, LCS_ENOMEM, "host allocation");
+    s->uid = lcs_next_uid();
     s->dim = d->dim;
     s->N = N;
     for (int a = 0; a < 3; ++a) {
@@ -471,6 +492,7 @@ extern "C" lcs_status lcs_flowmap_create(lcs_ctx *ctx, const lcs_seeds *s, int n
     lcs_flowmap *fm = new (std::nothrow) lcs_flowmap();
     if (!fm) return fail(ctx, LCS_ENOMEM, "host allocation");
     fm->ctx = ctx;
+    fm->uid = lcs_next_uid();
     fm->seeds = s;
     fm->dim = s->dim;
     fm->njobs = njobs;
@@ -509,15 +531,31 @@ struct AdvectScratch {
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+struct AdvectLayout {
+    size_t jb, sb, wb;
+    bool want_sorted;
+    int E;
+};
+
+static AdvectLayout advect_layout(const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o, const JobTable &J)
+{
+    AdvectLayout Ly;
+    Ly.jb = 2 * align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs) + 256;
+    Ly.sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
+    Ly.want_sorted = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
+    Ly.E = o->episode_steps > 0 ? std::min(o->episode_steps, 1024) : LCS_EPISODE_STEPS;
+    Ly.wb = Ly.want_sorted ? rk4_sorted_scratch_bytes(s->N, f->nodes, f->storage, Ly.E) : 0;
+    return Ly;
+}
+
 static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
                                   lcs_flowmap *fm, JobTable &J)
 {
-    size_t jb = 2 * align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs) + 256;
-    size_t sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
-    bool want_sorted = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
-    int E = o->episode_steps > 0 ? std::min(o->episode_steps, 1024) : LCS_EPISODE_STEPS;
-    size_t wb = want_sorted ? rk4_sorted_scratch_bytes(s->N, f->nodes, f->storage, E) : 0;
-    lcs_status st = scratch_reserve(ctx, jb + sb + wb);
+    const AdvectLayout Ly = advect_layout(f, s, o, J);
+    const size_t jb = Ly.jb, sb = Ly.sb;
+    const bool want_sorted = Ly.want_sorted;
+    const int E = Ly.E;
+    lcs_status st = scratch_reserve(ctx, jb + sb + Ly.wb);
     if (st != LCS_OK) return st;
     char *p = (char *)ctx->d_scratch;
     JobDev D;
@@ -561,6 +599,80 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.work = want_sorted ? (char *)ctx->d_scratch + jb + sb : nullptr;
     if (launch_rk4_rect(ctx, L, ctx->stream) < 0)
         return fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return LCS_OK;
+}
+
+// graph cache key: the handles' unique ids, the options that shape the launches, the jobs
+static std::string graph_key(const lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
+                             const lcs_flowmap *fm, const JobTable &J)
+{
+    std::string k;
+    char buf[160];
+    snprintf(buf, sizeof buf, "%llu/%llu/%llu/%p/%zu/%d/%d/%d/%d/%d/%d/%a|", f->uid, s->uid, fm->uid, ctx->d_scratch,
+             ctx->scratch_bytes, o->method, o->variant, o->block_threads, o->episode_steps, o->tracers_per_thread,
+             J.njobs, o->dt);
+    k += buf;
+    for (int j = 0; j < J.njobs; ++j) {
+        snprintf(buf, sizeof buf, "%a,%a;", J.t0[j], J.T[j]);
+        k += buf;
+    }
+    return k;
+}
+
+// Capture the launches of one lcs_advect call into a CUDA graph (once per key), then replay it
+// on the context stream.  The scratch is reserved before capture, since capture forbids allocation.
+static lcs_status advect_graph(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
+                               lcs_flowmap *fm, JobTable &J)
+{
+    const AdvectLayout Ly = advect_layout(f, s, o, J);
+    lcs_status st = scratch_reserve(ctx, Ly.jb + Ly.sb + Ly.wb);
+    if (st != LCS_OK) return st;
+    const std::string key = graph_key(ctx, f, s, o, fm, J);
+    ctx->graph_clock++;
+    for (auto &g : ctx->graphs)
+        if (g.key == key) {
+            g.last_use = ctx->graph_clock;
+            CUDA_TRY(ctx, cudaGraphLaunch(g.exec, ctx->stream));
+            return LCS_OK;
+        }
+    if (!ctx->cap_stream) CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = ctx->stream;
+    const bool timing = ctx->timing;
+    ctx->stream = ctx->cap_stream;
+    ctx->timing = false;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) st = advect_rk4_rect(ctx, f, s, o, fm, J);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->cap_stream, &graph) : e;
+    ctx->stream = user;
+    ctx->timing = timing;
+    if (e != cudaSuccess || e2 != cudaSuccess || st != LCS_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        if (st != LCS_OK) return st;
+        return fail(ctx, LCS_ECUDA, "lcs_advect: graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(ctx, LCS_ECUDA, "lcs_advect: graph instantiate: %s", cudaGetErrorString(e));
+    }
+    if (ctx->graphs.size() >= 8) {  // evict the least recently used
+        auto it = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                   [](const lcs_ctx::GraphEntry &a, const lcs_ctx::GraphEntry &b) {
+                                       return a.last_use < b.last_use;
+                                   });
+        cudaGraphExecDestroy(it->exec);
+        cudaGraphDestroy(it->graph);
+        ctx->graphs.erase(it);
+    }
+    lcs_ctx::GraphEntry g;
+    g.key = key;
+    g.graph = graph;
+    g.exec = exec;
+    g.last_use = ctx->graph_clock;
+    ctx->graphs.push_back(g);
+    CUDA_TRY(ctx, cudaGraphLaunch(exec, ctx->stream));
     return LCS_OK;
 }
 
@@ -609,6 +721,8 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess)
         st = fail(ctx, LCS_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    else if (o->use_graph)
+        st = advect_graph(ctx, f, s, o, fm, *J);
     else
         st = advect_rk4_rect(ctx, f, s, o, fm, *J);
     delete J;

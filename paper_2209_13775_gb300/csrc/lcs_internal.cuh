@@ -38,6 +38,16 @@ struct lcs_ctx {
     // scratch: device memory the library reuses across calls (queue counters)
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    // CUDA graphs of lcs_advect calls (opts.use_graph), keyed by handles and options
+    struct GraphEntry {
+        std::string key;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long last_use = 0;
+    };
+    std::vector<GraphEntry> graphs;
+    unsigned long long graph_clock = 0;
+    cudaStream_t cap_stream = nullptr;   // capture stream (graphs launch on `stream`)
     // per-phase event timing (lcs_timing_enable / lcs_timing_read)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -45,11 +55,15 @@ struct lcs_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_done[LCS_NPHASES];
 };
 
+// next unique handle id
+unsigned long long lcs_next_uid();
+
 // bracket the launches of one phase with events on stream s (no-ops unless timing is on)
 void lcs_tm_begin(lcs_ctx *ctx, int phase, cudaStream_t s);
 void lcs_tm_end(lcs_ctx *ctx, int phase, cudaStream_t s);
 
 struct lcs_field {
+    unsigned long long uid = 0;          // unique for the process lifetime (graph cache keys)
     lcs_ctx *ctx = nullptr;
     int dim = 0, kind = 0, storage = 0;
     int n[3] = {1, 1, 1};
@@ -79,6 +93,7 @@ struct lcs_field {
 };
 
 struct lcs_seeds {
+    unsigned long long uid = 0;          // unique for the process lifetime (graph cache keys)
     int dim = 0;
     int n[3] = {1, 1, 1};
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -91,6 +106,7 @@ struct lcs_seeds {
 };
 
 struct lcs_flowmap {
+    unsigned long long uid = 0;          // unique for the process lifetime (graph cache keys)
     lcs_ctx *ctx = nullptr;
     const lcs_seeds *seeds = nullptr;
     int dim = 0, njobs = 0;

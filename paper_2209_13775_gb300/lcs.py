@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "LCS_OK", 1: "LCS_EINVAL", 2: "LCS_ENOMEM", 3: "LCS_ECUDA", 4
 EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs_synchronize",
            "lcs_load_field", "lcs_update_frames", "lcs_free_field", "lcs_seed_grid", "lcs_seeds_count",
            "lcs_seeds_get", "lcs_free_seeds", "lcs_flowmap_create", "lcs_advect", "lcs_flowmap_get",
-           "lcs_free_flowmap", "lcs_cauchy_green", "lcs_ftle", "lcs_timing_enable", "lcs_timing_read",
+           "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_timing_enable",
+           "lcs_timing_read",
            "lcs_advect_rk4_noalloc"]
 PHASE_ADVECT, PHASE_REBUNDLE, PHASE_SLICES, PHASE_CG = 0, 1, 2, 3
 NOALLOC_MAX_STEPS = 43680
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_cauchy_green": ([P, P, I, P, I], S), "lcs_ftle": ([P, P, I, P, P, P, I], S),
         "lcs_advect_rk4_noalloc": ([P, P, P, LL, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P], S),
         "lcs_timing_enable": ([P, I], S), "lcs_timing_read": ([P, I, P, P], S),
+        "lcs_autotune": ([P, P, P, P, ctypes.c_char_p], S),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -277,6 +279,13 @@ def lcs_flowmap_get(ctx, fm, job=0, xyz=None, status=None, t_exit=None):
 
 def lcs_free_flowmap(fm):
     load().lcs_free_flowmap(fm)
+
+
+def lcs_autotune(ctx, field, seeds, opts: AdvectOpts, cache_path=None):
+    """Tune opts in place (variant, block_threads, tracers_per_thread, episode_steps); returns opts."""
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(ctx, load().lcs_autotune(ctx, field, seeds, ctypes.byref(opts), path))
+    return opts
 
 
 # ----------------------------------------------------- grad F, C, FTLE

@@ -125,6 +125,61 @@ def test_sliding_window_batch_against_oracle(ctx, gyre):
         check_ftle(b["ftle"][j], o["ftle"])
 
 
+def test_graph_replay_equals_direct_launch(ctx, gyre):
+    # a captured lcs_advect replays the same launches; changing the jobs captures a new graph
+    n, lo, hi, dt = (96, 48), (0.0, 0.0), (2.0, 1.0), 0.05
+    jobs = ([0.0, 1.0, 2.5], [2.0, -4.0, 8.0])
+    a = gpu_run(ctx, gyre, n, lo, hi, (0, 0), None, dt, jobs=jobs)
+    field = lcs.lcs_load_field(ctx, lcs.field_desc(2, gyre.n, gyre.origin, gyre.spacing, gyre.periodic, gyre.times,
+                                                   gyre.time_periodic, gyre.period), gyre.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, lo, hi))
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 3)
+    N = n[0] * n[1]
+    for rep in range(3):
+        o = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1], use_graph=True)
+        lcs.lcs_advect(ctx, field, seeds, o, fm)
+        for j in range(3):
+            x = np.empty((2, N), dtype=np.float32)
+            lcs.lcs_flowmap_get(ctx, fm, j, x)
+            np.testing.assert_array_equal(x, a["xyz"][j])
+    o2 = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=[0.5, 1.0, 2.5], job_T=jobs[1], use_graph=True)
+    lcs.lcs_advect(ctx, field, seeds, o2, fm)
+    x = np.empty((2, N), dtype=np.float32)
+    lcs.lcs_flowmap_get(ctx, fm, 0, x)
+    s = gpu_run(ctx, gyre, n, lo, hi, (0, 0), 2.0, dt, t0=0.5)
+    np.testing.assert_array_equal(x, s["xyz"][0])
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+
+
+def test_autotune_picks_valid_options_and_caches(ctx, gyre, tmp_path):
+    n, lo, hi, dt = (128, 64), (0.0, 0.0), (2.0, 1.0), 0.05
+    field = lcs.lcs_load_field(ctx, lcs.field_desc(2, gyre.n, gyre.origin, gyre.spacing, gyre.periodic, gyre.times,
+                                                   gyre.time_periodic, gyre.period), gyre.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, lo, hi))
+    jobs = ([0.25 * k for k in range(8)], [(2.0, 4.0)[k % 2] for k in range(8)])
+    cache = str(tmp_path / "tune.txt")
+    o = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1])
+    lcs.lcs_autotune(ctx, field, seeds, o, cache)
+    assert o.variant in (1, 2, 4) and o.block_threads in (128, 256, 512) and o.tracers_per_thread in (1, 2)
+    lines = open(cache).read().strip().splitlines()
+    assert len(lines) == 1 and "\t" in lines[0]
+    o2 = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1])
+    lcs.lcs_autotune(ctx, field, seeds, o2, cache)          # cache hit: same choice, no new line
+    assert (o2.variant, o2.block_threads, o2.tracers_per_thread) == (o.variant, o.block_threads,
+                                                                     o.tracers_per_thread)
+    assert len(open(cache).read().strip().splitlines()) == 1
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    # the tuned options compute the same flow map as the defaults
+    a = gpu_run(ctx, gyre, n, lo, hi, (0, 0), None, dt, jobs=jobs)
+    b = gpu_run(ctx, gyre, n, lo, hi, (0, 0), None, dt, jobs=jobs, variant=o.variant, block_threads=o.block_threads,
+                tracers_per_thread=o.tracers_per_thread)
+    for j in range(8):
+        np.testing.assert_array_equal(a["xyz"][j], b["xyz"][j])
+
+
 def test_cauchy_green_matches_oracle_on_gpu_positions(ctx, gyre):
     # same FP32 positions in: grad F and C are bit-identical, lambda_max within rounding
     n, lo, hi, T = (128, 64), (0.0, 0.0), (2.0, 1.0), 10.0
