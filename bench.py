@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seeds-side", type=int, default=N_SIDE,
                    help="seed lattice side (default 256; smaller only for profiling captures)")
+    p.add_argument("--config", default="c2", choices=["c2", "c3"],
+                   help="c2: the 3D ABC workload (default, the headline); c3: the batched sliding-window workload")
     p.add_argument("--grid", type=int, default=N_GRID,
                    help="velocity grid side (default 128; smaller only for profiling captures)")
     return p.parse_args()
@@ -356,6 +358,102 @@ def our_arm(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------ batched sliding-window arm
+
+C3_WORKLOAD = ("batched sliding-window FTLE on the double gyre (129x65 FP32, 101 frames): 32 t0 spaced 0.25, "
+               "forward and backward, T in {2,4,8} (64 jobs), 2048x1024 seeds each (2^21), RK4 dt=0.05; "
+               "one persistent launch in a CUDA graph with autotuned block/tile; FP64 FD + eigenvalue + FTLE")
+# algorithmic FP32 work of one RK4 tracer-step on bilinear, linear-in-time data (FMA = 2): per evaluation
+# 6 (cell coordinates) + 6 (weights) + 32 (4 corners x 2 components x 2 frames) + 6 (time blend) = 50;
+# 4 evaluations + 12 (stage points) + 12 (update) = 224
+FLOP_PER_TRACER_STEP_2D = 224
+
+
+def c3_arm(args, rank, world, local):
+    import torch
+
+    from paper_2209_13775_gb300 import inputs, lcs
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = lcs.lcs_create(local, stream)
+    g = inputs.double_gyre()
+    field = lcs.lcs_load_field(ctx, lcs.field_desc(2, g.n, g.origin, g.spacing, g.periodic, g.times,
+                                                   g.time_periodic, g.period), g.frames)
+    sd = lcs.seed_desc(2, (2048, 1024), (0.0, 0.0), (2.0, 1.0))
+    seeds = lcs.lcs_seed_grid(ctx, sd)
+    N = lcs.lcs_seeds_count(seeds)
+    t0s = [0.25 * k for k in range(32)] * 2
+    Ts = [(2.0, 4.0, 8.0)[k % 3] for k in range(32)] + [-(2.0, 4.0, 8.0)[k % 3] for k in range(32)]
+    nj = len(t0s)
+    tracer_steps = N * sum(int(round(abs(T) / 0.05)) for T in Ts)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, nj)
+    opts = lcs.advect_opts(lcs.RK4, dt=0.05, job_t0=t0s, job_T=Ts, use_graph=True)
+    cache = os.path.join(tempfile.gettempdir(), "lcs_tune_%d.txt" % os.getpid())
+    lcs.lcs_autotune(ctx, field, seeds, opts, cache)
+    ftle = torch.empty((nj, N), dtype=torch.float32, device="cuda")
+    lam = torch.empty((nj, N), dtype=torch.float64, device="cuda")
+
+    def step():
+        lcs.lcs_advect(ctx, field, seeds, opts, fm)
+        lcs.lcs_ftle(ctx, fm, -1, ftle, lam)
+
+    for _ in range(args.warmup):
+        step()
+    lcs.lcs_synchronize(ctx)
+    for ph in range(4):
+        lcs.lcs_timing_read(ctx, ph)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+    el = a.elapsed_time(b) / 1e3
+    # kernel-only time of the advection launches: one untimed-graph pass with phase events
+    lcs.lcs_timing_enable(ctx, True)
+    o2 = lcs.advect_opts(lcs.RK4, dt=0.05, job_t0=t0s, job_T=Ts, variant=opts.variant,
+                         block_threads=opts.block_threads, tracers_per_thread=opts.tracers_per_thread)
+    lcs.lcs_advect(ctx, field, seeds, o2, fm)
+    lcs.lcs_ftle(ctx, fm, -1, ftle, lam)
+    lcs.lcs_synchronize(ctx)
+    adv_ms, adv_n = lcs.lcs_timing_read(ctx, 0)
+    cg_ms, _ = lcs.lcs_timing_read(ctx, 3)
+    lcs.lcs_timing_enable(ctx, False)
+    pk, pk_kind = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    flops = float(tracer_steps) * FLOP_PER_TRACER_STEP_2D
+    achieved = flops / (adv_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": nj * N * args.steps / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": C3_WORKLOAD, "jobs": nj, "seeds_per_job": N, "tracer_steps": tracer_steps,
+                   "tuned": {"variant": opts.variant, "block_threads": opts.block_threads,
+                             "tracers_per_thread": opts.tracers_per_thread}},
+        "tracer_steps_per_s": tracer_steps * args.steps / el,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "rk4_ring2d_kernel (variant %d)" % opts.variant, "flop_per_launch": flops,
+                     "avg_launch_ms": adv_ms / max(adv_n, 1), "launches": adv_n,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, pk_kind)},
+        "phases_ms": {"advect": adv_ms, "cg_ftle": cg_ms},
+        "clocks": clk.summary(),
+    }
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    lcs.lcs_destroy(ctx)
+    try:
+        os.remove(cache)
+    except OSError:
+        pass
+    print(json.dumps(line), flush=True)
+
+
 def _src_sha():
     import hashlib
 
@@ -371,6 +469,9 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.config == "c3":
+        c3_arm(args, rank, world, local)
         return
     our_arm(args, rank, world, local)
 
