@@ -680,7 +680,8 @@ long long ora_dp45(int field_kind, const void *field, int dim, long long n,
                 break;
             }
             double hs = h;
-            if (dir * (t + hs - tend) > 0.0) hs = tend - t; /* land on t0 + T */
+            int last = dir * (t + hs - tend) >= 0.0;
+            if (last) hs = tend - t; /* land on t0 + T */
             attempts++;
             int all_ok = 1;
             double hmin = 0.0;
@@ -712,7 +713,7 @@ long long ora_dp45(int field_kind, const void *field, int dim, long long n,
                     }
                     tr[q].accepted++;
                 }
-                t = t + hs;
+                t = last ? tend : t + hs; /* the interval of Eq. 2 ends exactly at t0 + T */
             }
             if (adaptive && have_h) h = hmin;
         }
