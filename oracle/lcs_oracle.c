@@ -705,6 +705,7 @@ long long ora_dp45(int field_kind, const void *field, int dim, long long n,
                     tr[q].te = t;
                 }
             if (!adaptive || all_ok) {
+                double tn = last ? tend : t + hs; /* the interval of Eq. 2 ends exactly at t0 + T */
                 for (int q = 0; q < m; ++q) {
                     if (tr[q].st != ORA_OK) continue;
                     for (int a = 0; a < dim; ++a) {
@@ -712,8 +713,14 @@ long long ora_dp45(int field_kind, const void *field, int dim, long long n,
                         tr[q].k1[a] = k7[q][a];
                     }
                     tr[q].accepted++;
+                    /* same rule as the fixed-step path: a rectilinear tracer more than one
+                     * cell outside a non-periodic axis has left the domain              */
+                    if (field_kind == 0 && rect_left((const ora_rect_field *)field, tr[q].x)) {
+                        tr[q].st = ORA_LEFT;
+                        tr[q].te = tn;
+                    }
                 }
-                t = last ? tend : t + hs; /* the interval of Eq. 2 ends exactly at t0 + T */
+                t = tn;
             }
             if (adaptive && have_h) h = hmin;
         }

@@ -137,6 +137,25 @@ def test_dp45_lands_on_final_time(ora):
     assert np.all(te == 1.234)
 
 
+def test_dp45_leaving_a_rectilinear_box(ora):
+    # uniform stream u = (1, 0, 0) sampled on the box [0, 1]^3: every trial has zero error, so
+    # steps grow fivefold from h0 (0.01, 0.05, 0.25, 1.25) and the tracer at x = 0.5 ends its
+    # fourth step at x = 2.06, more than one cell (0.125) past x = 1: LEFT with t_exit = 1.56
+    g = inputs.affine_frames(np.zeros((3, 3)), np.zeros((3, 3)), [1.0, 0.0, 0.0], (9, 9, 9), (0, 0, 0),
+                             (0.125, 0.125, 0.125), [0.0, 10.0])
+    F = ora.RectField(g.frames, g.times, g.origin, g.spacing)
+    x0 = np.array([[0.5, 0.5], [0.5, 0.25], [0.5, 0.75]])
+    xT, st, te, ns = ora.dp45(F, x0, 0.0, 10.0, h0=0.01, rtol=1e-6, atol=1e-6)
+    assert (st == ora.LEFT).all() and (ns == 4).all()
+    np.testing.assert_allclose(te, 1.56, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(xT[0], 2.06, rtol=0, atol=1e-14)
+    np.testing.assert_array_equal(xT[1:], x0[1:])
+    # the same stream backwards from x = 0.5 leaves through x = 0 (past -0.125) at t = -1.56
+    _, st, te, _ = ora.dp45(F, x0, 0.0, -10.0, h0=0.01, rtol=1e-6, atol=1e-6)
+    assert (st == ora.LEFT).all()
+    np.testing.assert_allclose(te, -1.56, rtol=0, atol=1e-14)
+
+
 def test_dp45_group_mode_equals_per_tracer_when_errors_agree(ora):
     # space-constant field and a pure absolute tolerance: every lane has the same error, so a
     # shared step equals per-tracer stepping bit for bit
