@@ -109,7 +109,7 @@ typedef struct {
     const float *node_xyz;      /* [nnodes][3]                                        */
     const int *tets;            /* [ncells][4] node ids                               */
     const int *nbrs;            /* [ncells][4] tet across the face opposite vertex j,
-                                   -1 on the boundary                                 */
+                                   -1 on the boundary; NULL: built by the library     */
 } lcs_field_desc;
 
 /* Copy velocity frames into device storage.  frames is FP32,
@@ -215,6 +215,11 @@ lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *see
  * periodic axes), status [N] uint8, exit time [N] FP32.  Any may be NULL.   */
 lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *xyz,
                            unsigned char *status, float *t_exit, int on_device);
+
+/* Accepted steps per tracer of job `job` after an LCS_RK45 integration ([N]
+ * int32; every lane of a 32-seed group reports the group's count).
+ * Errors: LCS_EINVAL when no adaptive integration wrote this flow map.      */
+lcs_status lcs_flowmap_steps(lcs_ctx *ctx, const lcs_flowmap *fm, int job, int *steps, int on_device);
 
 void lcs_free_flowmap(lcs_flowmap *fm);
 

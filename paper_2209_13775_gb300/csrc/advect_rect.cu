@@ -72,8 +72,10 @@ __global__ void rk4_schedule_kernel(const double *__restrict__ times, int nf, in
         D.tend[j] = __double2float_rn(__dadd_rn(J.t0[j], J.T[j]));
         D.absT[j] = fabs(J.T[j]);
         if (D.order) D.order[j] = J.order[j];
+        if (D.t0d) D.t0d[j] = J.t0[j];
+        if (D.Td) D.Td[j] = J.T[j];
     }
-    if (idx >= total) return;
+    if (idx >= total || !sched) return;
     int s = (int)(idx % 3);
     int n = (int)((idx / 3) % nsm);
     int job = (int)(idx / (3LL * nsm));

@@ -4,6 +4,7 @@
 // Paper passages per call are given in lcs.h.  This file holds only host logic
 // plus the two bulk conversion kernels (frame storage, seed lattice).
 #include "lcs_internal.cuh"
+#include "dp45_args.cuh"
 
 #include <math.h>
 #include <stdarg.h>
@@ -287,13 +288,75 @@ static lcs_status upload_frames(lcs_ctx *ctx, lcs_field *f, const float *frames,
     return LCS_OK;
 }
 
+// Tetrahedral mesh (Sec. 3.1): frames as interval pairs per node, plus the mesh store.
+static lcs_status load_tet_field(lcs_ctx *ctx, const lcs_field_desc *d, const float *frames, int frames_on_device,
+                                 lcs_field **out)
+{
+    if (d->dim != 3) return fail(ctx, LCS_EINVAL, "lcs_load_field: tet meshes are 3D");
+    if (d->storage < LCS_F32 || d->storage > LCS_BF16) return fail(ctx, LCS_EINVAL, "lcs_load_field: storage");
+    if (d->nnodes < 4 || d->ncells < 1 || !d->node_xyz || !d->tets)
+        return fail(ctx, LCS_EINVAL, "lcs_load_field: a tet mesh needs nnodes >= 4, ncells >= 1, node_xyz, tets");
+    if (d->nnodes >= (1LL << 31) || d->ncells >= (1LL << 31))
+        return fail(ctx, LCS_EINVAL, "lcs_load_field: more than 2^31 nodes or tets");
+    if (d->nframes < 1 || !d->frame_times) return fail(ctx, LCS_EINVAL, "lcs_load_field: need >= 1 frame");
+    for (int k = 1; k < d->nframes; ++k)
+        if (!(d->frame_times[k] > d->frame_times[k - 1]))
+            return fail(ctx, LCS_EINVAL, "lcs_load_field: frame_times must increase");
+    if (d->time_periodic && !(d->period > 0.0)) return fail(ctx, LCS_EINVAL, "lcs_load_field: period must be > 0");
+    for (long long q = 0; q < 4 * d->ncells; ++q) {
+        if (d->tets[q] < 0 || d->tets[q] >= d->nnodes)
+            return fail(ctx, LCS_EINVAL, "lcs_load_field: tet %lld names node %d", q / 4, d->tets[q]);
+        if (d->nbrs && (d->nbrs[q] < -1 || d->nbrs[q] >= d->ncells))
+            return fail(ctx, LCS_EINVAL, "lcs_load_field: tet %lld has neighbour %d", q / 4, d->nbrs[q]);
+    }
+    for (long long q = 0; q < 3 * d->nnodes; ++q)
+        if (!isfinite(d->node_xyz[q])) return fail(ctx, LCS_EINVAL, "lcs_load_field: non-finite node coordinate");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    lcs_field *f = new (std::nothrow) lcs_field();
+    if (!f) return fail(ctx, LCS_ENOMEM, "host allocation");
+    f->ctx = ctx;
+    f->uid = lcs_next_uid();
+    f->dim = 3;
+    f->kind = LCS_TET;
+    f->storage = d->storage;
+    f->nframes = d->nframes;
+    f->times.assign(d->frame_times, d->frame_times + d->nframes);
+    f->time_periodic = d->time_periodic != 0;
+    f->period = d->period;
+    f->nodes = d->nnodes;
+    f->ncells = d->ncells;
+    f->vec = 8;
+    f->nslabs = f->nframes > 1 ? f->nframes - 1 : 1;
+    f->elem_bytes = d->storage == LCS_F32 ? 4 : 2;
+    f->frame_bytes = (size_t)f->nodes * f->vec * f->elem_bytes;
+    f->frame_stride = (f->frame_bytes + 255) & ~(size_t)255;
+    lcs_status st = LCS_OK;
+    cudaError_t e = cudaMalloc(&f->d_frames, f->frame_stride * f->nslabs);
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_times, sizeof(double) * f->nframes);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(f->d_times, f->times.data(), sizeof(double) * f->nframes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = tet_build_store(f, d->node_xyz, d->tets, d->nbrs, ctx->stream);
+    if (e != cudaSuccess)
+        st = fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_load_field: %s",
+                  cudaGetErrorString(e));
+    else
+        st = upload_frames(ctx, f, frames, frames_on_device);
+    if (st != LCS_OK) {
+        lcs_free_field(f);
+        return st;
+    }
+    *out = f;
+    return LCS_OK;
+}
+
 extern "C" lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *d, const float *frames,
                                      int frames_on_device, lcs_field **out)
 {
     if (!ctx) return LCS_EINVAL;
     if (!d || !frames || !out) return fail(ctx, LCS_EINVAL, "lcs_load_field: null argument");
     *out = nullptr;
-    if (d->kind != LCS_RECTILINEAR) return fail(ctx, LCS_EUNSUPPORTED, "lcs_load_field: tet meshes not built in");
+    if (d->kind == LCS_TET) return load_tet_field(ctx, d, frames, frames_on_device, out);
+    if (d->kind != LCS_RECTILINEAR) return fail(ctx, LCS_EINVAL, "lcs_load_field: unknown kind %d", d->kind);
     if (d->dim != 2 && d->dim != 3) return fail(ctx, LCS_EINVAL, "lcs_load_field: dim must be 2 or 3");
     if (d->storage < LCS_F32 || d->storage > LCS_BF16) return fail(ctx, LCS_EINVAL, "lcs_load_field: storage");
     if (d->nframes < 1 || !d->frame_times) return fail(ctx, LCS_EINVAL, "lcs_load_field: need >= 1 frame");
@@ -371,6 +434,7 @@ extern "C" void lcs_free_field(lcs_field *f)
     cudaFree(f->d_tets);
     cudaFree(f->d_nbrs);
     cudaFree(f->d_tetmap);
+    cudaFree(f->d_bins);
     delete f;
 }
 
@@ -417,7 +481,7 @@ extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const 
     *out = nullptr;
     if (d->dim != 2 && d->dim != 3) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: dim must be 2 or 3");
     if (field && field->dim != d->dim) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: dim differs from the field's");
-    if (field && field->kind == LCS_TET) return fail(ctx, LCS_EUNSUPPORTED, "lcs_seed_grid: tet location");
+    if (field && field->kind == LCS_TET && d->dim != 3) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: tets are 3D");
     long long N = 1;
     for (int a = 0; a < d->dim; ++a) {
         if (d->n[a] < 1) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: n[%d] < 1", a);
@@ -445,6 +509,11 @@ extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const 
     }
     cudaError_t e = cudaMalloc(&s->d_xyz, sizeof(float) * s->dim * (size_t)N);
     if (e == cudaSuccess) e = launch_seed_grid(s->dim, s->n, s->lo, s->hi, s->periodic, N, s->d_xyz, ctx->stream);
+    if (e == cudaSuccess && field && field->kind == LCS_TET) {
+        s->field_uid = field->uid;
+        e = cudaMalloc(&s->d_cells, sizeof(int) * (size_t)N);
+        if (e == cudaSuccess) e = tet_locate_seeds(field, s->d_xyz, N, 1 << 20, s->d_cells, ctx->stream);
+    }
     if (e != cudaSuccess) {
         lcs_free_seeds(s);
         return fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_seed_grid: %s",
@@ -520,6 +589,7 @@ extern "C" void lcs_free_flowmap(lcs_flowmap *fm)
     cudaFree(fm->d_status);
     cudaFree(fm->d_texit);
     cudaFree(fm->d_absT);
+    cudaFree(fm->d_steps);
     delete fm;
 }
 
@@ -568,6 +638,8 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     D.tend = (float *)p;
     p += align256(sizeof(float) * J.njobs);
     D.absT = fm->d_absT;
+    D.t0d = nullptr;
+    D.Td = nullptr;
     D.order = (int *)p;
     p += align256(sizeof(int) * J.njobs);
     unsigned *queue = (unsigned *)p;
@@ -597,8 +669,103 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.queue = queue;
     L.job_order = D.order;
     L.work = want_sorted ? (char *)ctx->d_scratch + jb + sb : nullptr;
+    if (f->kind == LCS_TET) {
+        cudaError_t e = launch_rk4_tet(ctx, L, s->d_cells, o->walk_limit, ctx->stream);
+        if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(e));
+        return LCS_OK;
+    }
     if (launch_rk4_rect(ctx, L, ctx->stream) < 0)
         return fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return LCS_OK;
+}
+
+// Adaptive DP5(4) with one step per warp (tets, 3D rectilinear fields)
+static lcs_status advect_rk45(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
+                              lcs_flowmap *fm)
+{
+    if (f->dim != 3) return fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: RK45 on 2D fields not built in");
+    const int njobs = o->njobs > 1 ? o->njobs : 1;
+    const double rtol = o->rtol > 0 ? o->rtol : 1e-6, atol = o->atol > 0 ? o->atol : 1e-6;
+    const double h0 = o->h0 != 0 ? fabs(o->h0) : 0.01;
+    if (!isfinite(rtol) || !isfinite(atol) || !isfinite(h0))
+        return fail(ctx, LCS_EINVAL, "lcs_advect: rtol, atol and h0 must be finite");
+    JobTable *J = new (std::nothrow) JobTable();
+    if (!J) return fail(ctx, LCS_ENOMEM, "host allocation");
+    J->njobs = njobs;
+    J->nsteps_max = 0;
+    for (int j = 0; j < njobs; ++j) {
+        double t0 = o->njobs > 1 ? o->job_t0[j] : o->t0;
+        double T = o->njobs > 1 ? o->job_T[j] : o->T;
+        if (!isfinite(t0) || !isfinite(T)) {
+            delete J;
+            return fail(ctx, LCS_EINVAL, "lcs_advect: job %d has a non-finite t0 or T", j);
+        }
+        J->t0[j] = t0;
+        J->T[j] = T;
+        J->h[j] = 0.0;
+        J->nsteps[j] = 0;
+        J->order[j] = j;
+        fm->T[j] = T;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    size_t need = 2 * align256(sizeof(int) * njobs) + 3 * align256(sizeof(float) * njobs) + 2 * align256(8 * njobs);
+    lcs_status st = e == cudaSuccess ? scratch_reserve(ctx, need) : fail(ctx, LCS_ECUDA, "cudaSetDevice failed");
+    if (st == LCS_OK && !fm->d_steps && cudaMalloc(&fm->d_steps, sizeof(int) * (size_t)fm->N * fm->njobs) != cudaSuccess)
+        st = fail(ctx, LCS_ENOMEM, "lcs_advect: step counts");
+    if (st != LCS_OK) {
+        delete J;
+        return st;
+    }
+    char *p = (char *)ctx->d_scratch;
+    JobDev D;
+    D.nsteps = (int *)p;
+    p += align256(sizeof(int) * njobs);
+    D.h = (float *)p;
+    p += align256(sizeof(float) * njobs);
+    D.t0 = (float *)p;
+    p += align256(sizeof(float) * njobs);
+    D.tend = (float *)p;
+    p += align256(sizeof(float) * njobs);
+    D.order = (int *)p;
+    p += align256(sizeof(int) * njobs);
+    D.t0d = (double *)p;
+    p += align256(8 * njobs);
+    D.Td = (double *)p;
+    D.absT = fm->d_absT;
+    e = launch_rk4_schedule(f->d_times, f->nframes, f->time_periodic, f->period, *J, D, nullptr,
+                            ctx->stream);  // per-job values only (no RK4 steps)
+    delete J;
+    if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "lcs_advect: %s", cudaGetErrorString(e));
+    Dp45Args A;
+    memset(&A, 0, sizeof A);
+    A.seeds = s->d_xyz;
+    A.cells0 = f->kind == LCS_TET ? s->d_cells : nullptr;
+    A.N = s->N;
+    A.job_t0 = D.t0d;
+    A.job_T = D.Td;
+    A.h0 = (float)h0;
+    A.rtol = (float)rtol;
+    A.atol = (float)atol;
+    A.max_steps = o->max_steps > 0 ? o->max_steps : 1000000;
+    A.out_xyz = fm->d_xyz;
+    A.out_status = fm->d_status;
+    A.out_texit = fm->d_texit;
+    A.out_steps = fm->d_steps;
+    e = launch_dp45(ctx, f, A, njobs, o->block_threads, o->walk_limit, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "lcs_advect: RK45 launch failed: %s", cudaGetErrorString(e));
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_flowmap_steps(lcs_ctx *ctx, const lcs_flowmap *fm, int job, int *steps, int on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!fm || !steps) return fail(ctx, LCS_EINVAL, "lcs_flowmap_steps: null argument");
+    if (job < 0 || job >= fm->njobs) return fail(ctx, LCS_EINVAL, "lcs_flowmap_steps: job %d out of range", job);
+    if (!fm->d_steps) return fail(ctx, LCS_EINVAL, "lcs_flowmap_steps: no adaptive integration wrote this flow map");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    CUDA_TRY(ctx, cudaMemcpyAsync(steps, fm->d_steps + (size_t)job * fm->N, sizeof(int) * (size_t)fm->N,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (!on_device) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return LCS_OK;
 }
 
@@ -686,8 +853,11 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
     int njobs = o->njobs > 1 ? o->njobs : 1;
     if (njobs > fm->njobs) return fail(ctx, LCS_EINVAL, "lcs_advect: %d jobs > flow map's %d", njobs, fm->njobs);
     if (o->njobs > 1 && (!o->job_t0 || !o->job_T)) return fail(ctx, LCS_EINVAL, "lcs_advect: job arrays missing");
-    if (o->method != LCS_RK4) return fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: method %d not built in", o->method);
-    if (f->kind != LCS_RECTILINEAR) return fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: tet RK4 not built in");
+    if (o->method != LCS_RK4 && o->method != LCS_RK45)
+        return fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: method %d not built in", o->method);
+    if (f->kind == LCS_TET && (!s->d_cells || s->field_uid != f->uid))
+        return fail(ctx, LCS_EINVAL, "lcs_advect: on a tet field the seeds must come from lcs_seed_grid on that field");
+    if (o->method == LCS_RK45) return advect_rk45(ctx, f, s, o, fm);
     double adt = fabs(o->dt);
     if (!(adt > 0.0) || !isfinite(adt)) return fail(ctx, LCS_EINVAL, "lcs_advect: dt must be finite and > 0");
     JobTable *J = new (std::nothrow) JobTable();

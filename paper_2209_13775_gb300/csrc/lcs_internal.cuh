@@ -90,7 +90,17 @@ struct lcs_field {
     int4 *d_tets = nullptr;            // [ncells]
     int4 *d_nbrs = nullptr;            // [ncells]
     float4 *d_tetmap = nullptr;        // [ncells][3]: rows of the inverse affine map + v0
+    int *d_bins = nullptr;             // walk starts: a tet near each bin of a uniform grid
+    int bin_n[3] = {0, 0, 0};
+    float bin_lo[3] = {0, 0, 0}, bin_inv[3] = {0, 0, 0};
 };
+
+// tetrahedral store (tet_store.cu): positions, tets, neighbours (built when null), inverse
+// affine maps and the bin grid; exact seed location
+cudaError_t tet_build_store(lcs_field *f, const float *xyz_host, const int *tets_host, const int *nbrs_host,
+                            cudaStream_t s);
+cudaError_t tet_locate_seeds(const lcs_field *f, const float *seeds, long long N, int walk_limit, int *cells,
+                             cudaStream_t s);
 
 struct lcs_seeds {
     unsigned long long uid = 0;          // unique for the process lifetime (graph cache keys)
@@ -101,6 +111,7 @@ struct lcs_seeds {
     long long N = 0;
     float *d_xyz = nullptr;            // [dim][N]
     int *d_cells = nullptr;            // [N] when made on a tet field
+    unsigned long long field_uid = 0;  // the tet field the cells refer to
     double h[3] = {1, 1, 1};           // lattice step per axis
     double period[3] = {0, 0, 0};      // hi - lo on periodic axes
 };
@@ -114,6 +125,7 @@ struct lcs_flowmap {
     float *d_xyz = nullptr;            // [njobs][dim][N]
     unsigned char *d_status = nullptr; // [njobs][N]
     float *d_texit = nullptr;          // [njobs][N]
+    int *d_steps = nullptr;            // [njobs][N] accepted adaptive steps (after an RK45 advect)
     std::vector<double> T;             // per job
     double *d_absT = nullptr;          // [njobs] |T|, written by the schedule kernel
 };
@@ -159,6 +171,8 @@ struct JobDev {
     float *tend;     // [njobs]
     double *absT;    // [njobs] (the flow map's copy, for the FTLE)
     int *order;      // [njobs] JobTable::order on the device, or null
+    double *t0d;     // [njobs] FP64 start times, or null
+    double *Td;      // [njobs] FP64 horizons, or null
 };
 
 struct Rk4Launch {
@@ -201,6 +215,10 @@ cudaError_t launch_rk4_schedule(const double *d_times, int nframes, int time_per
 
 // returns the variant actually used (1 or 2), or -1 on a launch error
 int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s);
+
+// ------------------------------------------------- tets and adaptive stepping
+
+cudaError_t launch_rk4_tet(lcs_ctx *ctx, const Rk4Launch &L, const int *cells0, int walk_limit, cudaStream_t s);
 
 // ------------------------------------------------------ grad F / C / FTLE
 

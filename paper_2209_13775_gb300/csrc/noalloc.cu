@@ -87,6 +87,8 @@ extern "C" lcs_status lcs_advect_rk4_noalloc(lcs_ctx *ctx, const lcs_field *f, c
     D.tend = (float *)(p + 48);
     D.absT = (double *)(p + 64);
     D.order = nullptr;
+    D.t0d = nullptr;
+    D.Td = nullptr;
     SchedEntry *sched = (SchedEntry *)(p + LCS_NOALLOC_HEADER);
     // every schedule entry and per-job value the advection reads is written by the schedule kernel
     // first, so nothing in the array needs clearing between calls

@@ -175,17 +175,18 @@ def pipe_frames(mesh: TetInput, nframes=50, period=1.0, R=1.0, L=10.0, seed=SEED
     """Pulsatile Poiseuille u_z = (1 - r^2/R^2)(1 + 0.5 sin 2 pi t) plus swirl s(r,z,t)(-y, x, 0).
 
     s = amp (1 - r^2/R^2) sum_{m=1..4} sin(2 pi m z / L + phi_m + 2 pi t) / m with
-    phi_m ~ U[0, 2 pi) from the seed; frames at t_k = k * period / nframes,
-    time-periodic.  The field is divergence-free.
+    phi_m ~ U[0, 2 pi) from the seed; nframes frames per period at t_k = k * period / nframes,
+    plus the closing frame t = period (equal to the first), time-periodic.  The field is
+    divergence-free.
     """
     rng = np.random.default_rng(seed)
     phases = rng.uniform(0.0, 2 * np.pi, 4)
-    times = np.array([period * k / nframes for k in range(nframes)], dtype=np.float64)
+    times = np.array([period * k / nframes for k in range(nframes + 1)], dtype=np.float64)
     amp = pipe_swirl_amp(mesh, times, phases, R, L)
     x = mesh.xyz.astype(np.float64)
     r2 = (x[:, 0] ** 2 + x[:, 1] ** 2) / (R * R)
     prof = 1.0 - r2
-    frames = np.empty((nframes, x.shape[0], 3), dtype=np.float32)
+    frames = np.empty((nframes + 1, x.shape[0], 3), dtype=np.float32)
     for k, t in enumerate(times):
         sw = sum(np.sin(2 * np.pi * m * x[:, 2] / L + phases[m - 1] + 2 * np.pi * t) / m
                  for m in range(1, 5))

@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "LCS_OK", 1: "LCS_EINVAL", 2: "LCS_ENOMEM", 3: "LCS_ECUDA", 4
 EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs_synchronize",
            "lcs_load_field", "lcs_update_frames", "lcs_free_field", "lcs_seed_grid", "lcs_seeds_count",
            "lcs_seeds_get", "lcs_free_seeds", "lcs_flowmap_create", "lcs_advect", "lcs_flowmap_get",
+           "lcs_flowmap_steps",
            "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_timing_enable",
            "lcs_timing_read",
            "lcs_advect_rk4_noalloc"]
@@ -90,6 +91,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_advect_rk4_noalloc": ([P, P, P, LL, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P], S),
         "lcs_timing_enable": ([P, I], S), "lcs_timing_read": ([P, I, P, P], S),
         "lcs_autotune": ([P, P, P, P, ctypes.c_char_p], S),
+        "lcs_flowmap_steps": ([P, P, I, P, I], S),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -275,6 +277,11 @@ def lcs_flowmap_get(ctx, fm, job=0, xyz=None, status=None, t_exit=None):
         raise ValueError("outputs must all be host or all be device buffers")
     _check(ctx, load().lcs_flowmap_get(ctx, fm, int(job), *[ctypes.c_void_p(p) for p, _ in ptrs],
                                        devs.pop() if devs else 0))
+
+
+def lcs_flowmap_steps(ctx, fm, job, steps):
+    p, dev = _ptr(steps)
+    _check(ctx, load().lcs_flowmap_steps(ctx, fm, int(job), ctypes.c_void_p(p), dev))
 
 
 def lcs_free_flowmap(fm):

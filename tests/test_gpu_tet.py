@@ -1,0 +1,350 @@
+"""GPU parity of the tetrahedral path and of the adaptive integrator through the C ABI
+against the FP64 oracle.
+
+* Seed cells (Sec. 2 "Seed" on unstructured data, Sec. 3.1 local cell search): the
+  lowest-id closed tet holding each FP32 seed, -1 outside.  Both sides decide with
+  exact orientation predicates, so the comparison is bit-exact -- on a Kuhn mesh whose
+  seeds sit on vertices, edges and faces (the tie-break runs) and on a Delaunay pipe.
+* Fixed-step RK4 on tets (P1 interpolation, Sec. 3.1 walk per stage): closed form on
+  affine fields; the pipe flow against the oracle with the rectilinear tolerances.
+  A stage point outside the mesh freezes the tracer at the start of that step; near the
+  outlet plane the FP32 and FP64 decisions can fall on either side of a stage point that
+  lies within rounding of the plane, so statuses may differ there, and then only by one
+  step of exit time.
+* DP5(4) with one step size per warp (Sec. 2 "Flow Map", Runge-Kutta family): against
+  the closed-form flow of affine fields and against the oracle's 32-lane shared-step
+  mode, whose step sequence the kernel follows up to FP32 rounding of the error norms.
+"""
+import numpy as np
+import pytest
+import torch
+from scipy.linalg import expm
+
+import oracle
+from meshes import kuhn_mesh
+from paper_2209_13775_gb300 import inputs, lcs
+from gpu_util import round_bf16, round_fp16
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    c = lcs.lcs_create(0, torch.cuda.current_stream())
+    yield c
+    lcs.lcs_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def pipe():
+    m = inputs.pipe_mesh(h=0.1, R=1.0, L=2.0)
+    return inputs.pipe_frames(m, nframes=50, period=1.0, L=2.0)
+
+
+def tet_desc(xyz, tets, nbrs, times, storage=lcs.F32, time_periodic=False, period=0.0):
+    return lcs.field_desc(3, times=times, time_periodic=time_periodic, period=period, storage=storage,
+                          kind=lcs.TET, mesh=(xyz, tets, nbrs))
+
+
+def gpu_tet(ctx, desc, frames, n, lo, hi, opts, want_steps=False):
+    """Load a tet field, seed a lattice on it, advect; host arrays of job 0 (or every job)."""
+    field = lcs.lcs_load_field(ctx, desc, frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, n, lo, hi), field)
+    N = lcs.lcs_seeds_count(seeds)
+    out = {"seeds": np.empty((3, N), dtype=np.float32), "cells": np.empty(N, dtype=np.int32)}
+    lcs.lcs_seeds_get(ctx, seeds, out["seeds"], out["cells"])
+    if opts is not None:
+        njobs = max(1, opts.njobs)
+        fm = lcs.lcs_flowmap_create(ctx, seeds, njobs)
+        lcs.lcs_advect(ctx, field, seeds, opts, fm)
+        out["xyz"], out["status"], out["t_exit"], out["steps"] = [], [], [], []
+        for j in range(njobs):
+            x = np.empty((3, N), dtype=np.float32)
+            s = np.empty(N, dtype=np.uint8)
+            te = np.empty(N, dtype=np.float32)
+            lcs.lcs_flowmap_get(ctx, fm, j, x, s, te)
+            out["xyz"].append(x)
+            out["status"].append(s)
+            out["t_exit"].append(te)
+            if want_steps:
+                ns = np.empty(N, dtype=np.int32)
+                lcs.lcs_flowmap_steps(ctx, fm, j, ns)
+                out["steps"].append(ns)
+        lcs.lcs_free_flowmap(fm)
+    lcs.lcs_synchronize(ctx)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return out
+
+
+def ora_seeds(n, lo, hi):
+    return oracle.seed_grid(3, n, lo, hi)
+
+
+# ------------------------------------------------------------------ seed cells
+
+def test_seed_cells_on_kuhn_mesh_with_ties(ctx):
+    # lattice step 1/2 on integer nodes: most seeds lie on a vertex, edge or face shared by several
+    # tets; the lattice also reaches one cell outside the mesh on every side
+    pts, tets, nbrs = kuhn_mesh(4)
+    F = oracle.TetField(pts, tets, nbrs, np.zeros((1, len(pts), 3), np.float32), [0.0])
+    n, lo, hi = (13, 13, 13), (-1.0, -1.0, -1.0), (5.0, 5.0, 5.0)
+    fr = np.zeros((1, len(pts), 3), np.float32)
+    g = gpu_tet(ctx, tet_desc(pts, tets, nbrs, [0.0]), fr, n, lo, hi, None)
+    x0 = ora_seeds(n, lo, hi)
+    np.testing.assert_array_equal(g["seeds"], x0)
+    want = F.locate_seeds(x0)
+    np.testing.assert_array_equal(g["cells"], want)
+    ties = sum(len([t for t in range(len(tets)) if F.contains(t, x0[:, i])[0]]) > 1
+               for i in range(0, x0.shape[1], 3) if want[i] >= 0)
+    assert ties > 150 and (want < 0).sum() > 500 and (want >= 0).sum() > 500
+
+
+def test_seed_cells_on_delaunay_pipe(ctx, pipe):
+    n, lo, hi = (23, 23, 31), (-1.1, -1.1, -0.1), (1.1, 1.1, 2.1)
+    F = oracle.TetField(pipe.xyz, pipe.tets, pipe.nbrs, pipe.frames[:1], [0.0])
+    x0 = ora_seeds(n, lo, hi)
+    want = F.locate_seeds(x0)
+    for nbrs in (pipe.nbrs, None):   # None: the library builds the face neighbours itself
+        g = gpu_tet(ctx, tet_desc(pipe.xyz, pipe.tets, nbrs, [0.0]), pipe.frames[:1], n, lo, hi, None)
+        np.testing.assert_array_equal(g["cells"], want)
+    assert (want < 0).sum() > 1000 and (want >= 0).sum() > 5000
+
+
+# ------------------------------------------------------------------ RK4 on tets
+
+def test_rk4_tet_affine_rotation_closed_form(ctx):
+    pts, tets, nbrs = kuhn_mesh(4)
+    pts = pts - np.float32(2.0)                       # box [-2, 2]^3
+    A = np.array([[0.0, -0.5, 0.0], [0.5, 0.0, 0.0], [0.0, 0.0, 0.0]])   # rotation about z
+    fr = np.stack([pts @ A.T, pts @ A.T]).astype(np.float32)
+    n, lo, hi = (9, 9, 7), (-1.0, -1.0, -1.5), (1.0, 1.0, 1.5)
+    opts = lcs.advect_opts(lcs.RK4, t0=0.0, T=2.0, dt=0.1)
+    g = gpu_tet(ctx, tet_desc(pts, tets, nbrs, [0.0, 10.0]), fr, n, lo, hi, opts)
+    x0 = ora_seeds(n, lo, hi).astype(np.float64)
+    Z = 0.1 * A
+    R = np.eye(3) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+    want = np.linalg.matrix_power(R, 20) @ x0
+    assert (g["status"][0] == lcs.TRACER_OK).all()
+    err = np.abs(g["xyz"][0] - want).max()
+    assert err <= 4e-6, err
+
+
+def test_rk4_tet_uniform_stream_leaves_at_the_top(ctx):
+    # u = (0, 0, 1) on [-2, 2]^3: a tracer at z0 is frozen at the start of the first step with a
+    # stage point above z = 2; the last stage is the highest, so t_e = dt floor((2 - z0) / dt) when
+    # (2 - z0) / dt is not an integer (the lattice keeps it 0.3 away from one)
+    pts, tets, nbrs = kuhn_mesh(4)
+    pts = pts - np.float32(2.0)
+    fr = np.zeros((2, len(pts), 3), np.float32)
+    fr[..., 2] = 1.0
+    n, lo, hi = (4, 4, 9), (-1.5, -1.5, -1.73), (1.5, 1.5, 1.47)
+    opts = lcs.advect_opts(lcs.RK4, t0=0.0, T=5.0, dt=0.1)
+    g = gpu_tet(ctx, tet_desc(pts, tets, nbrs, [0.0, 10.0]), fr, n, lo, hi, opts)
+    x0 = ora_seeds(n, lo, hi).astype(np.float64)
+    te_want = 0.1 * np.floor((2.0 - x0[2]) / 0.1)
+    assert (g["status"][0] == lcs.TRACER_LEFT).all()
+    np.testing.assert_allclose(g["t_exit"][0], te_want, rtol=0, atol=2e-6)
+    np.testing.assert_allclose(g["xyz"][0][2], x0[2] + te_want, rtol=0, atol=4e-6)
+    np.testing.assert_array_equal(g["xyz"][0][:2], x0[:2].astype(np.float32))
+
+
+def _pipe_oracle(pipe, frames, n, lo, hi, t0, T, dt):
+    F = oracle.TetField(pipe.xyz, pipe.tets, pipe.nbrs, frames, pipe.times, True, pipe.period)
+    x0 = ora_seeds(n, lo, hi)
+    cells = F.locate_seeds(x0)
+    return F, x0, cells, oracle.rk4(F, x0.astype(np.float64), t0, T, dt, cells=cells)
+
+
+def check_exit_statuses(st_g, te_g, st_o, te_o, dt, frac=2e-3):
+    """Statuses agree except where an exit was decided one step apart (stage points within
+    rounding of a boundary face); returns the seeds where both are OK or both left at the same step."""
+    diff = st_g != st_o
+    assert diff.mean() <= frac, diff.sum()
+    assert set(np.unique(st_g[diff])) <= {lcs.TRACER_OK, lcs.TRACER_LEFT}
+    dte = np.abs(te_g.astype(np.float64) - te_o)
+    assert (dte[diff] <= dt * (1 + 1e-4)).all(), dte[diff].max()
+    same = ~diff & (dte <= 1e-4 * dt)
+    assert ((~diff) & ~same).sum() <= frac * len(st_g)
+    return same
+
+
+@pytest.mark.parametrize("storage", [lcs.F32, lcs.F16, lcs.BF16])
+def test_rk4_tet_pipe_matches_oracle(ctx, pipe, storage):
+    # seeds inside the pipe; the pulsatile centreline carries many of them out through z = L
+    n, lo, hi = (24, 24, 40), (-0.69, -0.69, 0.05), (0.69, 0.69, 1.95)
+    frames = pipe.frames
+    if storage == lcs.F16:
+        frames = round_fp16(frames)
+    elif storage == lcs.BF16:
+        frames = round_bf16(frames)
+    t0, T, dt = 0.3, 1.0, 0.01
+    opts = lcs.advect_opts(lcs.RK4, t0=t0, T=T, dt=dt)
+    g = gpu_tet(ctx, tet_desc(pipe.xyz, pipe.tets, pipe.nbrs, pipe.times, storage, True, pipe.period),
+                pipe.frames, n, lo, hi, opts)
+    F, x0, cells, (xT, st, te) = _pipe_oracle(pipe, frames, n, lo, hi, t0, T, dt)
+    np.testing.assert_array_equal(g["cells"], cells)
+    assert (st == oracle.LEFT).sum() > 1000 and (st == oracle.OK).sum() > 5000
+    same = check_exit_statuses(g["status"][0], g["t_exit"][0], st, te, dt)
+    err = np.abs(g["xyz"][0][:, same].astype(np.float64) - xT[:, same]).max()
+    assert err <= 2e-5, err
+
+
+def test_rk4_tet_backward_and_batched_jobs(ctx, pipe):
+    # two jobs (one backward) in one launch equal two single-job launches bit for bit
+    n, lo, hi = (16, 16, 20), (-0.6, -0.6, 0.2), (0.6, 0.6, 1.8)
+    desc = tet_desc(pipe.xyz, pipe.tets, pipe.nbrs, pipe.times, lcs.F32, True, pipe.period)
+    both = gpu_tet(ctx, desc, pipe.frames, n, lo, hi,
+                   lcs.advect_opts(lcs.RK4, dt=0.02, job_t0=[0.1, 0.9], job_T=[0.6, -0.8]))
+    one = gpu_tet(ctx, desc, pipe.frames, n, lo, hi, lcs.advect_opts(lcs.RK4, t0=0.9, T=-0.8, dt=0.02))
+    np.testing.assert_array_equal(both["xyz"][1], one["xyz"][0])
+    np.testing.assert_array_equal(both["status"][1], one["status"][0])
+    _, _, _, (xT, st, te) = _pipe_oracle(pipe, pipe.frames, n, lo, hi, 0.9, -0.8, 0.02)
+    same = check_exit_statuses(one["status"][0], one["t_exit"][0], st, te, 0.02)
+    assert np.abs(one["xyz"][0][:, same] - xT[:, same]).max() <= 2e-5
+    assert (st == oracle.LEFT).sum() > 50     # backwards through the inlet z = 0
+
+
+# ------------------------------------------------------------------ DP5(4)
+
+def rect_affine(A, b, n=(17, 17, 17), origin=(-2.0, -2.0, -2.0), spacing=(0.25, 0.25, 0.25)):
+    return inputs.affine_frames(A, np.zeros((3, 3)), b, n, origin, spacing, [0.0, 100.0])
+
+
+def gpu_rect_rk45(ctx, g, n, lo, hi, opts):
+    desc = lcs.field_desc(3, g.n, g.origin, g.spacing, g.periodic, g.times)
+    field = lcs.lcs_load_field(ctx, desc, g.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, n, lo, hi))
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    lcs.lcs_advect(ctx, field, seeds, opts, fm)
+    x = np.empty((3, N), dtype=np.float32)
+    s = np.empty(N, dtype=np.uint8)
+    te = np.empty(N, dtype=np.float32)
+    ns = np.empty(N, dtype=np.int32)
+    lcs.lcs_flowmap_get(ctx, fm, 0, x, s, te)
+    lcs.lcs_flowmap_steps(ctx, fm, 0, ns)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return x, s, te, ns
+
+
+def test_rk45_rect_affine_matches_expm_and_oracle(ctx):
+    # a stable spiral with strain; trilinear interpolation of an affine field is exact, so the exact
+    # flow map is expm(T A) x0 and the DP5(4) error is set by the tolerance (and FP32 rounding)
+    A = np.array([[-0.25, -1.0, 0.0], [1.0, -0.25, 0.5], [0.0, -0.5, -0.125]])
+    g = rect_affine(A, [0.0, 0.0, 0.0])
+    n, lo, hi = (10, 9, 7), (-1.2, -1.1, -1.0), (1.2, 1.1, 1.0)
+    T = 3.0
+    x, s, te, ns = gpu_rect_rk45(ctx, g, n, lo, hi, lcs.advect_opts(lcs.RK45, t0=0.0, T=T, rtol=1e-5,
+                                                                     atol=1e-5, h0=0.01))
+    x0 = ora_seeds(n, lo, hi).astype(np.float64)
+    exact = expm(T * A) @ x0
+    assert (s == lcs.TRACER_OK).all() and np.all(te == np.float32(T))
+    assert np.abs(x - exact).max() <= 2e-4
+    F = oracle.RectField(g.frames, g.times, g.origin, g.spacing)
+    xo, so, teo, nso = oracle.dp45(F, x0, 0.0, T, h0=0.01, rtol=1e-5, atol=1e-5, group=32)
+    assert np.abs(x - xo).max() <= 1e-4
+    # every lane of a 32-seed group reports the group's count; counts track the oracle's
+    N = x0.shape[1]
+    for q in range(0, N, 32):
+        assert len(set(ns[q:q + 32].tolist())) == 1
+    assert np.abs(ns.astype(np.int64) - nso).max() <= 3
+
+
+def test_rk45_rect_uniform_stream_leaves(ctx):
+    # a uniform stream has a zero error estimate up to FP32 rounding of the interpolation weights
+    # (about 1e-3 of a 1e-6 tolerance, 1e-6 of a 1e-3 one): at tolerance 1e-3 every step grows
+    # fivefold (0.01, 0.05, 0.25, 1.25) and a seed at x = 0.5 on the box [0, 1]^3 ends its fourth
+    # step at x = 2.06, past x = 1.125: LEFT at t = 1.56
+    g = inputs.affine_frames(np.zeros((3, 3)), np.zeros((3, 3)), [1.0, 0.0, 0.0], (9, 9, 9), (0, 0, 0),
+                             (0.125, 0.125, 0.125), [0.0, 10.0])
+    n, lo, hi = (1, 5, 5), (0.5, 0.0, 0.0), (0.5, 1.0, 1.0)
+    x, s, te, ns = gpu_rect_rk45(ctx, g, n, lo, hi, lcs.advect_opts(lcs.RK45, T=10.0, h0=0.01, rtol=1e-3,
+                                                                     atol=1e-3))
+    assert (s == lcs.TRACER_LEFT).all() and (ns == 4).all()
+    np.testing.assert_allclose(te, 1.56, rtol=0, atol=2e-6)
+    np.testing.assert_allclose(x[0], 2.06, rtol=0, atol=4e-6)
+    # at tolerance 1e-6 the steps grow more slowly; the frozen position still equals the elapsed time
+    x, s, te, ns = gpu_rect_rk45(ctx, g, n, lo, hi, lcs.advect_opts(lcs.RK45, T=-10.0, h0=0.01))
+    assert (s == lcs.TRACER_LEFT).all() and (ns >= 4).all()
+    np.testing.assert_allclose(x[0] - 0.5, te, rtol=0, atol=2e-6)
+    assert (x[0] < -0.125).all()
+
+
+def test_rk45_tet_affine_closed_form(ctx):
+    pts, tets, nbrs = kuhn_mesh(4)
+    pts = pts - np.float32(2.0)
+    A = np.array([[-0.125, -0.5, 0.0], [0.5, -0.125, 0.0], [0.0, 0.0, -0.25]])
+    fr = np.stack([pts @ A.T, pts @ A.T]).astype(np.float32)
+    n, lo, hi = (8, 8, 8), (-1.5, -1.5, -1.5), (1.5, 1.5, 1.5)
+    T = 4.0
+    opts = lcs.advect_opts(lcs.RK45, t0=0.0, T=T, rtol=1e-5, atol=1e-5, h0=0.05)
+    g = gpu_tet(ctx, tet_desc(pts, tets, nbrs, [0.0, 10.0]), fr, n, lo, hi, opts, want_steps=True)
+    x0 = ora_seeds(n, lo, hi).astype(np.float64)
+    assert (g["status"][0] == lcs.TRACER_OK).all()
+    assert np.abs(g["xyz"][0] - expm(T * A) @ x0).max() <= 2e-4
+    F = oracle.TetField(pts, tets, nbrs, fr, [0.0, 10.0])
+    xo, so, _, nso = oracle.dp45(F, x0, 0.0, T, h0=0.05, rtol=1e-5, atol=1e-5, group=32,
+                                 cells=F.locate_seeds(x0))
+    assert np.abs(g["xyz"][0] - xo).max() <= 1e-4
+    assert np.abs(g["steps"][0].astype(np.int64) - nso).max() <= 3
+
+
+def test_rk45_tet_pipe_matches_oracle(ctx, pipe):
+    n, lo, hi = (16, 16, 24), (-0.65, -0.65, 0.1), (0.65, 0.65, 1.9)
+    t0, T = 0.2, 1.0
+    opts = lcs.advect_opts(lcs.RK45, t0=t0, T=T, rtol=1e-6, atol=1e-6, h0=0.01)
+    g = gpu_tet(ctx, tet_desc(pipe.xyz, pipe.tets, pipe.nbrs, pipe.times, lcs.F32, True, pipe.period),
+                pipe.frames, n, lo, hi, opts, want_steps=True)
+    F = oracle.TetField(pipe.xyz, pipe.tets, pipe.nbrs, pipe.frames, pipe.times, True, pipe.period)
+    x0 = ora_seeds(n, lo, hi)
+    cells = F.locate_seeds(x0)
+    xo, so, teo, nso = oracle.dp45(F, x0.astype(np.float64), t0, T, h0=0.01, rtol=1e-6, atol=1e-6,
+                                   group=32, cells=cells)
+    st = g["status"][0]
+    assert (so == oracle.LEFT).sum() > 300 and (so == oracle.OK).sum() > 2000
+    diff = st != so
+    assert diff.mean() <= 5e-3, diff.sum()
+    ok = (st == so) & (so == oracle.OK)
+    assert np.abs(g["xyz"][0][:, ok] - xo[:, ok]).max() <= 2e-4
+    steps_ok = np.abs(g["steps"][0].astype(np.int64) - nso)
+    assert np.median(steps_ok) <= 1 and steps_ok.max() <= 10
+
+
+# ------------------------------------------------------------------ errors
+
+def test_rk45_and_tet_argument_errors(ctx, pipe):
+    g2 = inputs.double_gyre(nx=17, ny=9, nframes=3, t_end=1.0)
+    field = lcs.lcs_load_field(ctx, lcs.field_desc(2, g2.n, g2.origin, g2.spacing, times=g2.times), g2.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (8, 8), (0, 0), (2, 1)))
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    with pytest.raises(lcs.LcsError) as e:
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK45, T=1.0), fm)
+    assert e.value.status == 7                      # LCS_EUNSUPPORTED: no 2D adaptive path
+    lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=1.0, dt=0.1), fm)
+    with pytest.raises(lcs.LcsError) as e:          # no adaptive integration wrote step counts
+        lcs.lcs_flowmap_steps(ctx, fm, 0, np.empty(64, dtype=np.int32))
+    assert e.value.status == 1
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    # tet fields: seeds must be located on that field; bad node ids are rejected at load
+    desc = tet_desc(pipe.xyz, pipe.tets, pipe.nbrs, pipe.times, lcs.F32, True, pipe.period)
+    tf = lcs.lcs_load_field(ctx, desc, pipe.frames)
+    plain = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, (4, 4, 4), (-0.5, -0.5, 0.5), (0.5, 0.5, 1.5)))
+    fm = lcs.lcs_flowmap_create(ctx, plain, 1)
+    with pytest.raises(lcs.LcsError) as e:
+        lcs.lcs_advect(ctx, tf, plain, lcs.advect_opts(lcs.RK4, T=0.1, dt=0.01), fm)
+    assert e.value.status == 1
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(plain)
+    lcs.lcs_free_field(tf)
+    bad = pipe.tets.copy()
+    bad[5, 2] = len(pipe.xyz)
+    with pytest.raises(lcs.LcsError) as e:
+        lcs.lcs_load_field(ctx, tet_desc(pipe.xyz, bad, None, pipe.times), pipe.frames)
+    assert e.value.status == 1

@@ -11,13 +11,13 @@ holding each seed).
 * P1 interpolation reproduces affine fields; RK4 on them is R(hA)^N.
 * A uniform stream leaves a box mesh at a time known in closed form.
 """
-import itertools
 from fractions import Fraction
 
 import numpy as np
 import pytest
 
 from paper_2209_13775_gb300 import inputs
+from meshes import kuhn_mesh
 
 
 def _orient_exact(a, b, c, d):
@@ -60,35 +60,6 @@ def test_orient3d_matches_rational_arithmetic(ora):
     # tiny coordinates (subnormal FP32) still decided exactly
     t = np.float32(1e-44)
     assert ora.orient3d([0, 0, 0], [t, 0, 0], [0, t, 0], [0, 0, t]) == 1
-
-
-def kuhn_mesh(n):
-    """n^3 unit cubes, each split into 6 tets along its main diagonal; neighbours by face matching."""
-    idx = lambda i, j, k: i + (n + 1) * (j + (n + 1) * k)
-    pts = np.array([[i, j, k] for k in range(n + 1) for j in range(n + 1) for i in range(n + 1)],
-                   dtype=np.float32)
-    tets = []
-    E = np.eye(3, dtype=int)
-    for k, j, i in itertools.product(range(n), range(n), range(n)):
-        for perm in itertools.permutations(range(3)):
-            v = np.array([i, j, k])
-            vs = [idx(*v)]
-            for ax in perm:
-                v = v + E[ax]
-                vs.append(idx(*v))
-            tets.append(vs)
-    tets = np.array(tets, dtype=np.int32)
-    faces = {}
-    nbrs = -np.ones_like(tets)
-    for t, vs in enumerate(tets):
-        for j in range(4):
-            key = tuple(sorted(np.delete(vs, j)))
-            if key in faces:
-                s, sj = faces[key]
-                nbrs[t, j], nbrs[s, sj] = s, t
-            else:
-                faces[key] = (t, j)
-    return pts, tets, nbrs
 
 
 def _field(ora, pts, tets, nbrs, frames=None, times=(0.0,)):
