@@ -58,8 +58,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seeds-side", type=int, default=N_SIDE,
                    help="seed lattice side (default 256; smaller only for profiling captures)")
-    p.add_argument("--config", default="c2", choices=["c2", "c3"],
-                   help="c2: the 3D ABC workload (default, the headline); c3: the batched sliding-window workload")
+    p.add_argument("--config", default="c2", choices=["c2", "c3", "c4"],
+                   help="c2: the 3D ABC workload (default, the headline); c3: the batched sliding-window "
+                        "workload; c4: adaptive DP5(4) on the tetrahedral pipe")
     p.add_argument("--grid", type=int, default=N_GRID,
                    help="velocity grid side (default 128; smaller only for profiling captures)")
     return p.parse_args()
@@ -454,6 +455,140 @@ def c3_arm(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ tetrahedral RK45 arm
+
+C4_WORKLOAD = ("pipe on tetrahedra: Delaunay tets of a jittered lattice in a cylinder R=1, L=10 (h=0.0466), "
+               "pulsatile Poiseuille flow + 5% random-phase swirl, 50 FP32 frames per period 1 (time-periodic); "
+               "64x64x512 seed lattice on [-1,1]^2x[0,10] (2,097,152 seeds); DP5(4) rtol=atol=1e-6, t0=0, T=1, "
+               "cell walk per stage; FD grad F, 3x3 Cauchy-Green (FP64) and FTLE")
+C4_N = (64, 64, 512)
+C4_LO, C4_HI = (-1.0, -1.0, 0.0), (1.0, 1.0, 10.0)
+C4_T, C4_TOL, C4_H0 = 1.0, 1e-6, 0.01
+# algorithmic bytes of one stage evaluation on tets: one walk step (48 B inverse map + 16 B neighbours),
+# 16 B connectivity, 4 vertices x 2 frames x 3 components x 4 B = 96 B of velocity; 6 new stages per
+# accepted DP5(4) step (the first stage is the previous step's last)
+C4_BYTES_PER_STAGE = 48 + 16 + 16 + 96
+C4_STAGES_PER_STEP = 6
+
+
+def c4_oracle_block(mesh, side, nz, threads=0):
+    """Oracle DP5(4) (32-lane groups) + FD/CG/FTLE on a side x side x nz block of the C4 lattice
+    centred in the pipe, with a 2-seed stencil halo; returns (interior seeds, seconds, threads, integrated)."""
+    import oracle
+
+    oracle.build()
+    nth = oracle.set_threads(threads)
+    h = [(C4_HI[a] - C4_LO[a]) / (C4_N[a] - 1) for a in range(3)]
+    c = [C4_N[0] // 2 - side // 2, C4_N[1] // 2 - side // 2, C4_N[2] // 2 - nz // 2]
+    m = (side + 4, side + 4, nz + 4)
+    axes = [(C4_LO[a] + (c[a] - 2 + np.arange(m[a])) * h[a]).astype(np.float32) for a in range(3)]
+    Z, Y, X = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+    x0 = np.stack([X.ravel(), Y.ravel(), Z.ravel()])
+    F = oracle.TetField(mesh.xyz, mesh.tets, mesh.nbrs, mesh.frames, mesh.times, True, mesh.period)
+    t = time.perf_counter()
+    cells = F.locate_seeds(x0)
+    xT, st, _, _ = oracle.dp45(F, x0.astype(np.float64), 0.0, C4_T, h0=C4_H0, rtol=C4_TOL, atol=C4_TOL,
+                               group=32, cells=cells)
+    G = oracle.flowmap_gradient(3, m, h, (0, 0, 0), (0, 0, 0), xT, st)
+    lam, sig = oracle.ftle(oracle.cauchy_green(G), 3, C4_T)
+    return side * side * nz, time.perf_counter() - t, nth, x0.shape[1]
+
+
+def c4_arm(args, rank, world, local):
+    import torch
+
+    from paper_2209_13775_gb300 import inputs, lcs
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = lcs.lcs_create(local, stream)
+    t_mesh = time.perf_counter()
+    mesh = inputs.pipe_frames(inputs.pipe_mesh(), nframes=50, period=1.0)
+    t_mesh = time.perf_counter() - t_mesh
+    desc = lcs.field_desc(3, times=mesh.times, time_periodic=True, period=mesh.period, kind=lcs.TET,
+                          mesh=(mesh.xyz, mesh.tets, mesh.nbrs))
+    field = lcs.lcs_load_field(ctx, desc, mesh.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, C4_N, C4_LO, C4_HI), field)
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    opts = lcs.advect_opts(lcs.RK45, t0=0.0, T=C4_T, rtol=C4_TOL, atol=C4_TOL, h0=C4_H0)
+    ftle = torch.empty(N, dtype=torch.float32, device="cuda")
+    C = torch.empty((N, 6), dtype=torch.float64, device="cuda")
+
+    def step():
+        lcs.lcs_advect(ctx, field, seeds, opts, fm)
+        lcs.lcs_ftle(ctx, fm, 0, ftle, None, C)
+
+    for _ in range(args.warmup):
+        step()
+    lcs.lcs_synchronize(ctx)
+    for ph in range(4):
+        lcs.lcs_timing_read(ctx, ph)
+    lcs.lcs_timing_enable(ctx, True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+    el = a.elapsed_time(b) / 1e3
+    adv_ms, adv_n = lcs.lcs_timing_read(ctx, 0)
+    cg_ms, _ = lcs.lcs_timing_read(ctx, 3)
+    lcs.lcs_timing_enable(ctx, False)
+    steps = np.empty(N, dtype=np.int32)
+    status = np.empty(N, dtype=np.uint8)
+    lcs.lcs_flowmap_steps(ctx, fm, 0, steps)
+    lcs.lcs_flowmap_get(ctx, fm, 0, None, status, None)
+    tracer_steps = int(steps.astype(np.int64).sum())
+    counts = {name: int((status == v).sum()) for name, v in
+              (("ok", lcs.TRACER_OK), ("left", lcs.TRACER_LEFT), ("outside", lcs.TRACER_OUTSIDE),
+               ("maxsteps", lcs.TRACER_MAXSTEPS), ("walkfail", lcs.TRACER_WALKFAIL))}
+    live = status != lcs.TRACER_OUTSIDE
+    pk, pk_kind = peaks()
+    launch_s = adv_ms / max(adv_n, 1) / 1e3
+    alg_bytes = float(tracer_steps) * C4_STAGES_PER_STEP * C4_BYTES_PER_STAGE
+    achieved = alg_bytes / launch_s / 1e9
+    hbm = pk.get("hbm_gbs", 6800.0)
+    line = {
+        "metric": METRIC, "value": N * args.steps / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": C4_WORKLOAD, "seeds": N, "nodes": int(mesh.xyz.shape[0]),
+                   "tets": int(mesh.tets.shape[0]), "mesh_build_s": round(t_mesh, 1),
+                   "status": counts, "accepted_steps_per_live_tracer": float(steps[live].mean()),
+                   "l2": "no flush: the mesh store (geometry + 50 slabs, %.0f MB) exceeds the 129 MB L2"
+                         % ((mesh.tets.shape[0] * (16 + 16 + 48) + mesh.xyz.shape[0] * 16
+                             + 50 * mesh.xyz.shape[0] * 32) / 1e6)},
+        "tracer_steps_per_s": tracer_steps * args.steps / el,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": "dp45_kernel<TetEval<F32>>",
+                     "bytes_per_launch": alg_bytes, "avg_launch_ms": launch_s * 1e3, "launches": adv_n,
+                     "peak_basis": "hbm_gbs (%s)" % pk_kind,
+                     "basis": "%d B per stage x 6 stages per accepted step x accepted tracer-steps"
+                              % C4_BYTES_PER_STAGE},
+        "phases_ms_per_step": {"advect": adv_ms / args.steps, "cg_ftle": cg_ms / args.steps},
+        "clocks": clk.summary(),
+        # per step: the per-job values kernel, the DP5(4) kernel, FD/CG/FTLE
+        "gpu_launches": 3 * args.steps,
+    }
+    if not args.no_cpu_baseline:
+        _, dts, _, _ = c4_oracle_block(mesh, 12, 12)           # calibration: 16^3 tracers
+        per = dts / 16 ** 3
+        nz = int(max(4, min(500, (12.0 / max(per, 1e-9)) / (44 * 44) - 4)))
+        s, dt, nth, integrated = c4_oracle_block(mesh, 40, nz)
+        line["cpu_baseline"] = {"value": s / dt, "unit": "seeds/s", "cores": nth, "kind": "oracle",
+                                "sample": "40x40x%d block of the 64x64x512 lattice at the pipe centre with its "
+                                          "2-seed halo (%d tracers, DP5(4) in 32-lane groups), FD/CG/FTLE; %.1f s"
+                                          % (nz, integrated, dt)}
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    lcs.lcs_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def _src_sha():
     import hashlib
 
@@ -472,6 +607,9 @@ def main():
         return
     if args.config == "c3":
         c3_arm(args, rank, world, local)
+        return
+    if args.config == "c4":
+        c4_arm(args, rank, world, local)
         return
     our_arm(args, rank, world, local)
 

@@ -217,7 +217,9 @@ lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *
                            unsigned char *status, float *t_exit, int on_device);
 
 /* Accepted steps per tracer of job `job` after an LCS_RK45 integration ([N]
- * int32; every lane of a 32-seed group reports the group's count).
+ * int32; 32 consecutive seeds step together, so the tracers of a group that
+ * stay live to the end report the same count, and a tracer that stopped early
+ * the count it had reached).
  * Errors: LCS_EINVAL when no adaptive integration wrote this flow map.      */
 lcs_status lcs_flowmap_steps(lcs_ctx *ctx, const lcs_flowmap *fm, int job, int *steps, int on_device);
 
