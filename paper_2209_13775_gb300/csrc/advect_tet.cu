@@ -159,7 +159,7 @@ __device__ __forceinline__ int dp_eval(const EV &E, const Dp45Args &A, const flo
 }
 
 template <class EV>
-__global__ void __launch_bounds__(256) dp45_kernel(EV E, Dp45Args A, RectParams P)
+__global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectParams P)
 {
     extern __shared__ float s_times[];
     for (int q = threadIdx.x; q < A.nf; q += blockDim.x) s_times[q] = (float)A.times[q];

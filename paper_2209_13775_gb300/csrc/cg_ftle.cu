@@ -5,11 +5,16 @@
 // the eigenvalues of C; Sec. 1: the FTLE is derived from the largest one,
 // sigma = ln(sqrt(lambda_max)) / |T|.
 //
-// One thread per seed, FP64 from the FP32 flow map.  Every difference, product
-// and sum uses round-to-nearest operations without contraction, so grad F and C
-// equal the plain FP64 definition bit for bit on the same positions.
-// lambda_max is closed-form: 2x2 from the quadratic formula, 3x3 from the
-// trigonometric solution of the characteristic cubic (Smith 1961).
+// One thread per seed, FP64 from the FP32 flow map.  FP64 issue is the limit of this
+// kernel on GB300, so the FP64 work is kept to what the results need:
+//  * grad F and C: every difference, product and sum is a round-to-nearest operation
+//    without contraction, and the division by 2h is correctly rounded (Markstein's
+//    method below), so both equal the plain FP64 definition bit for bit;
+//  * lambda_max: 2x2 from the quadratic formula; 3x3 from the characteristic cubic of
+//    the shifted, scaled matrix (Smith 1961), whose trigonometric root is taken in FP32
+//    and polished by two FP64 Newton steps (relative error ~1e-16 for a simple root);
+//  * FTLE = log1p(lambda_max - 1) / (2 |T|) in FP32 from the FP64 difference, which
+//    keeps its relative accuracy (a few FP32 ulps) also where lambda_max is near 1.
 #include "lcs_internal.cuh"
 
 #include <math.h>
@@ -35,37 +40,87 @@ __device__ __forceinline__ long long lattice_nbr(const CgLaunch &L, const long l
     return c[0] + (long long)L.n[0] * (c[1] + (long long)L.n[1] * c[2]);
 }
 
-template <int DIM>
-__device__ __forceinline__ double eig_max(const double *C)
+// RN(x / d) for a fixed divisor d with y = RN(1 / d): q = RN(x y) is within about one
+// ulp of x / d, one FMA-corrected step q1 = RN(q + RN(x - q d) y) makes it faithful, so
+// the remainder x - q1 d is exact, and then RN(q1 + (x - q1 d) y) is the correctly
+// rounded quotient (Markstein 1990, Theorem 8: a faithful quotient corrected with the
+// correctly rounded reciprocal).  No overflow or underflow occurs for lattice spacings
+// and flow-map differences.
+__device__ __forceinline__ double div_fixed(double x, double d, double y)
 {
-    if (DIM == 2) {
-        // C = [[a, b], [b, c]]: lambda_max = (a + c)/2 + sqrt(((a - c)/2)^2 + b^2)
-        double a = C[0], b = C[1], c = C[2];
-        double m = __dmul_rn(0.5, __dadd_rn(a, c));
-        double d = __dmul_rn(0.5, __dsub_rn(a, c));
-        return __dadd_rn(m, sqrt(__dadd_rn(__dmul_rn(d, d), __dmul_rn(b, b))));
-    } else {
-        double a00 = C[0], a01 = C[1], a02 = C[2], a11 = C[3], a12 = C[4], a22 = C[5];
-        double p1 = a01 * a01 + a02 * a02 + a12 * a12;
-        if (p1 == 0.0) return fmax(a00, fmax(a11, a22));
-        double q = (a00 + a11 + a22) / 3.0;
-        double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
-        double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1;
-        double p = sqrt(p2 / 6.0);
-        double ip = 1.0 / p;
-        // det((C - qI) / p) / 2
-        double c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
-        double det = c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02);
-        double r = 0.5 * det;
-        double phi;
-        if (r <= -1.0)
-            phi = M_PI / 3.0;
-        else if (r >= 1.0)
-            phi = 0.0;
-        else
-            phi = acos(r) / 3.0;
-        return q + 2.0 * p * cos(phi);
+    const double q = __dmul_rn(x, y);
+    const double q1 = __fma_rn(__fma_rn(-q, d, x), y, q);
+    return __fma_rn(__fma_rn(-q1, d, x), y, q1);
+}
+
+// neighbour position with the periodic shift of axis b (a == b only; w in {-1, 0, 1})
+__device__ __forceinline__ double nbr_pos(float x, int w, double sh, bool shifted)
+{
+    double v = (double)x;
+    if (shifted && w != 0) v = __dadd_rn(v, w > 0 ? sh : -sh);
+    return v;
+}
+
+__device__ __forceinline__ double eig_max2(const double *C)
+{
+    // C = [[a, b], [b, c]]: lambda_max = (a + c)/2 + sqrt(((a - c)/2)^2 + b^2)
+    double a = C[0], b = C[1], c = C[2];
+    double m = __dmul_rn(0.5, __dadd_rn(a, c));
+    double d = __dmul_rn(0.5, __dsub_rn(a, c));
+    return __dadd_rn(m, sqrt(__dadd_rn(__dmul_rn(d, d), __dmul_rn(b, b))));
+}
+
+// trigonometric form in FP64 throughout (kept for matrices outside the scaled range)
+__device__ __noinline__ double eig_max3_slow(double a00, double a01, double a02, double a11, double a12,
+                                             double a22)
+{
+    double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+    double q = (a00 + a11 + a22) / 3.0;
+    double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1;
+    if (!(p2 > 0.0)) return q;
+    double p = sqrt(p2 / 6.0);
+    double ip = 1.0 / p;
+    double c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = a01 * ip, c02 = a02 * ip, c12 = a12 * ip;
+    double det = c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02);
+    double r = fmin(fmax(0.5 * det, -1.0), 1.0);
+    return q + 2.0 * p * cos(acos(r) / 3.0);
+}
+
+__device__ __forceinline__ double eig_max3(const double *C)
+{
+    const double dmax = fmax(C[0], fmax(C[3], C[5]));
+    const double p1 = C[1] * C[1] + C[2] * C[2] + C[4] * C[4];
+    if (p1 == 0.0) return dmax;  // diagonal (or NaN, which fmax passes on only if all are NaN)
+    // scale by a power of two s so that the largest diagonal entry lies in [1, 2): exact, and it
+    // keeps the FP32 steps below in range.  C is positive semidefinite, so dmax > 0 here.
+    const int hi = __double2hiint(dmax);
+    const int ex = ((hi >> 20) & 0x7ff) - 1023;
+    if (!(dmax > 0.0) || ex < -1000 || ex > 1000) return eig_max3_slow(C[0], C[1], C[2], C[3], C[4], C[5]);
+    const double s = __hiloint2double((1023 - ex) << 20, 0), is = __hiloint2double((1023 + ex) << 20, 0);
+    const double a00 = C[0] * s, a01 = C[1] * s, a02 = C[2] * s, a11 = C[3] * s, a12 = C[4] * s, a22 = C[5] * s;
+    const double q = (a00 + a11 + a22) * (1.0 / 3.0);
+    const double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+    const double p2 = (b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * (p1 * s * s)) * (1.0 / 6.0);
+    // eigenvalues are q + 2 p cos(.), p = sqrt(p2) and q >= 1/3: below 1e-28, lambda_max = q to 1e-13
+    if (!(p2 >= 1e-28)) return p2 < 1e-28 ? q * is : eig_max3_slow(C[0], C[1], C[2], C[3], C[4], C[5]);
+    // y = 1/sqrt(p2): FP32 estimate, two FP64 Newton steps (relative error 1e-7 -> 1e-14 -> 1e-16)
+    double y = (double)rsqrtf((float)p2);
+    y = y * (1.5 - 0.5 * p2 * y * y);
+    y = y * (1.5 - 0.5 * p2 * y * y);
+    const double p = p2 * y;
+    // r = det((C - qI) / p) / 2 in [-1, 1]; beta = 2 cos(acos(r) / 3) is the largest root of
+    // beta^3 - 3 beta - 2 r = 0
+    const double det = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) + a02 * (a01 * a12 - b11 * a02);
+    const double r = fmin(fmax(0.5 * det * (y * y * y), -1.0), 1.0);
+    double beta = (double)(2.0f * cosf(acosf((float)r) * (1.0f / 3.0f)));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double f = fma(beta, fma(beta, beta, -3.0), -2.0 * r);
+        const double fp = 3.0 * fma(beta, beta, -1.0);
+        if (fp > 1e-6) beta -= f * (double)__frcp_rn((float)fp);
     }
+    return (q + p * beta) * is;
 }
 
 template <int DIM>
@@ -94,26 +149,23 @@ __global__ void __launch_bounds__(256) cg_ftle_kernel(CgLaunch L)
         bool okp2 = qp2 >= 0 && S[qp2] == LCS_TRACER_OK;
         bool okm2 = qm2 >= 0 && S[qm2] == LCS_TRACER_OK;
         int mode = !valid ? 0 : (okp1 && okm1) ? 1 : (okp1 && okp2) ? 2 : (okm1 && okm2) ? 3 : 0;
-        const double h2 = __dmul_rn(2.0, L.h[b]);
+        const double h2 = L.h2[b], rh2 = L.rh2[b], sh = L.period[b];
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            const double sh = (a == b) ? L.period[b] : 0.0;
+            const bool on = a == b;
             const float *Xa = X + (size_t)a * N;
             double d;
             if (mode == 1) {
-                double Fp1 = __dadd_rn((double)Xa[qp1], __dmul_rn((double)wp1, sh));
-                double Fm1 = __dadd_rn((double)Xa[qm1], __dmul_rn((double)wm1, sh));
-                d = __ddiv_rn(__dsub_rn(Fp1, Fm1), h2);
+                const double Fp1 = nbr_pos(Xa[qp1], wp1, sh, on), Fm1 = nbr_pos(Xa[qm1], wm1, sh, on);
+                d = div_fixed(__dsub_rn(Fp1, Fm1), h2, rh2);
             } else if (mode == 2) {
-                double F0 = (double)Xa[p];
-                double Fp1 = __dadd_rn((double)Xa[qp1], __dmul_rn((double)wp1, sh));
-                double Fp2 = __dadd_rn((double)Xa[qp2], __dmul_rn((double)wp2, sh));
-                d = __ddiv_rn(__dsub_rn(__dadd_rn(__dmul_rn(-3.0, F0), __dmul_rn(4.0, Fp1)), Fp2), h2);
+                const double F0 = (double)Xa[p];
+                const double Fp1 = nbr_pos(Xa[qp1], wp1, sh, on), Fp2 = nbr_pos(Xa[qp2], wp2, sh, on);
+                d = div_fixed(__dsub_rn(__dadd_rn(__dmul_rn(-3.0, F0), __dmul_rn(4.0, Fp1)), Fp2), h2, rh2);
             } else if (mode == 3) {
-                double F0 = (double)Xa[p];
-                double Fm1 = __dadd_rn((double)Xa[qm1], __dmul_rn((double)wm1, sh));
-                double Fm2 = __dadd_rn((double)Xa[qm2], __dmul_rn((double)wm2, sh));
-                d = __ddiv_rn(__dadd_rn(__dsub_rn(__dmul_rn(3.0, F0), __dmul_rn(4.0, Fm1)), Fm2), h2);
+                const double F0 = (double)Xa[p];
+                const double Fm1 = nbr_pos(Xa[qm1], wm1, sh, on), Fm2 = nbr_pos(Xa[qm2], wm2, sh, on);
+                d = div_fixed(__dadd_rn(__dsub_rn(__dmul_rn(3.0, F0), __dmul_rn(4.0, Fm1)), Fm2), h2, rh2);
             } else {
                 d = __longlong_as_double(0x7ff8000000000000LL);  // NaN
             }
@@ -138,15 +190,21 @@ __global__ void __launch_bounds__(256) cg_ftle_kernel(CgLaunch L)
         for (int q = 0; q < NP; ++q) L.C[out * NP + q] = C[q];
     }
     if (L.lam || L.ftle) {
-        double lm = eig_max<DIM>(C);
+        const double lm = DIM == 2 ? eig_max2(C) : eig_max3(C);
         if (L.lam) L.lam[out] = lm;
-        if (L.ftle) L.ftle[out] = __double2float_rn(log(sqrt(lm)) / L.absT[job]);
+        // sigma = ln(sqrt(lm)) / |T| = log1p(lm - 1) / (2 |T|)
+        if (L.ftle) L.ftle[out] = log1pf((float)(lm - 1.0)) * (0.5f / (float)L.absT[job]);
     }
 }
 
-cudaError_t launch_cg_ftle(const CgLaunch &L, cudaStream_t s)
+cudaError_t launch_cg_ftle(const CgLaunch &L0, cudaStream_t s)
 {
-    if (L.N == 0 || L.njobs == 0) return cudaSuccess;
+    if (L0.N == 0 || L0.njobs == 0) return cudaSuccess;
+    CgLaunch L = L0;
+    for (int b = 0; b < 3; ++b) {
+        L.h2[b] = 2.0 * L.h[b];  // exact
+        L.rh2[b] = 1.0 / L.h2[b];
+    }
     int bt = 256;
     dim3 grid((unsigned)((L.N + bt - 1) / bt), (unsigned)L.njobs);
     if (L.dim == 2)

@@ -228,6 +228,7 @@ struct CgLaunch {
     int periodic[3];
     double h[3];
     double period[3];
+    double h2[3], rh2[3];        // 2 h and RN(1 / (2 h)), filled by launch_cg_ftle
     long long N;
     int job0, njobs;
     const float *xyz;            // flow map base [njobs_total][dim][N]

@@ -277,6 +277,28 @@ def test_abc_periodic_3d_parity(ctx, abc_small, storage):
     check_ftle(r["ftle"][0], o["ftle"])
 
 
+def test_cauchy_green_3d_matches_oracle_on_gpu_positions(ctx, abc_small):
+    # same FP32 positions in: grad F and C bit-identical (the division by 2h is correctly rounded),
+    # lambda_max within 1e-12 of the oracle's Jacobi eigenvalue, FTLE within a few FP32 ulps
+    L = 2 * np.pi
+    cases = [((37, 30, 29), (0.0, 0.0, 0.0), (L, L, L), (1, 1, 1), 2.0),
+             ((21, 19, 17), (0.5, 1.0, 0.25), (5.5, 4.0, 6.0), (0, 0, 0), -1.5)]
+    for n, lo, hi, per, T in cases:
+        g = gpu_run(ctx, abc_small, n, lo, hi, per, T, 0.02, want_C=True)
+        x = g["xyz"][0].astype(np.float64)
+        endpoint = [0 if p else 1 for p in per]
+        h = oracle.lattice_spacing(3, n, lo, hi, endpoint)
+        period = [hi[a] - lo[a] if per[a] else 0.0 for a in range(3)]
+        G = oracle.flowmap_gradient(3, n, h, per, period, x, g["status"][0])
+        C = oracle.cauchy_green(G)
+        np.testing.assert_array_equal(g["C"][0], C)
+        lam, sig = oracle.ftle(C, 3, T)
+        ok = np.isfinite(lam)
+        np.testing.assert_array_equal(np.isfinite(g["lam"][0]), ok)
+        np.testing.assert_allclose(g["lam"][0][ok], lam[ok], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(g["ftle"][0][ok], sig[ok].astype(np.float32), rtol=1e-6, atol=0)
+
+
 def test_abc_rebundled_equals_gather(ctx, abc_small):
     # re-bundling tracers between episodes moves them between threads but not their arithmetic
     L = 2 * np.pi
