@@ -237,6 +237,18 @@ void lcs_free_flowmap(lcs_flowmap *fm);
 lcs_status lcs_autotune(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *seeds, lcs_advect_opts *opts,
                         const char *cache_path);
 
+/* ------------------------------------------------ tensor-core GEMM (BF16) */
+
+/* C[M x N] = A[M x K] * B[N x K]^T (accumulate = 1: C += ...) on the tcgen05
+ * tensor cores, FP32 accumulation; the trainer of the surrogate is built on it.
+ * Device pointers: A, B BF16 with K contiguous (row strides lda, ldb in elements,
+ * multiples of 8), C FP32 (row stride ldc).  K must be a multiple of 16 and N
+ * be 16 or a multiple of 128; splits > 1 cuts K into that many ranges summed
+ * with atomics.  No counterpart in the paper.
+ * Errors: LCS_EINVAL (shapes), LCS_ECUDA.                                   */
+lcs_status lcs_gemm_bf16(lcs_ctx *ctx, long long M, int N, long long K, const void *A, long long lda, const void *B,
+                         long long ldb, float *C, long long ldc, int splits, int accumulate);
+
 /* ---------------------------------------- grad F, C, lambda_max, FTLE (a9-a11) */
 
 /* Cauchy-Green tensor C = grad(F)^T grad(F) (Eq. 1) with grad F from finite

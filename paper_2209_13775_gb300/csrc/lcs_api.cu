@@ -17,7 +17,7 @@
 
 // ------------------------------------------------------------------- errors
 
-static lcs_status fail(lcs_ctx *ctx, lcs_status st, const char *fmt, ...)
+lcs_status lcs_fail(lcs_ctx *ctx, lcs_status st, const char *fmt, ...)
 {
     if (ctx) {
         char buf[512];
@@ -34,7 +34,7 @@ static lcs_status fail(lcs_ctx *ctx, lcs_status st, const char *fmt, ...)
     do {                                                                                           \
         cudaError_t e__ = (call);                                                                  \
         if (e__ != cudaSuccess)                                                                    \
-            return fail((ctx), e__ == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "%s: %s", \
+            return lcs_fail((ctx), e__ == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "%s: %s", \
                         #call, cudaGetErrorString(e__));                                           \
     } while (0)
 
@@ -145,7 +145,7 @@ extern "C" lcs_status lcs_timing_enable(lcs_ctx *ctx, int on)
 extern "C" lcs_status lcs_timing_read(lcs_ctx *ctx, int phase, double *ms, long long *launches)
 {
     if (!ctx) return LCS_EINVAL;
-    if (phase < 0 || phase >= LCS_NPHASES) return fail(ctx, LCS_EINVAL, "lcs_timing_read: phase %d", phase);
+    if (phase < 0 || phase >= LCS_NPHASES) return lcs_fail(ctx, LCS_EINVAL, "lcs_timing_read: phase %d", phase);
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     double tot = 0.0;
     long long n = 0;
@@ -185,9 +185,9 @@ extern "C" lcs_status lcs_synchronize(lcs_ctx *ctx)
     CUDA_TRY(ctx, cudaMemcpy(&w, ctx->d_errword, sizeof w, cudaMemcpyDeviceToHost));
     if (w) {
         CUDA_TRY(ctx, cudaMemset(ctx->d_errword, 0, sizeof w));
-        if (w & LCS_ERRBIT_TIMEOUT) return fail(ctx, LCS_ETIMEOUT, "a device-side wait gave up");
-        if (w & LCS_ERRBIT_WALK) return fail(ctx, LCS_EWALK, "a tet walk exceeded walk_limit");
-        if (w & LCS_ERRBIT_MAXSTEPS) return fail(ctx, LCS_EMAXSTEPS, "an adaptive integration hit max_steps");
+        if (w & LCS_ERRBIT_TIMEOUT) return lcs_fail(ctx, LCS_ETIMEOUT, "a device-side wait gave up");
+        if (w & LCS_ERRBIT_WALK) return lcs_fail(ctx, LCS_EWALK, "a tet walk exceeded walk_limit");
+        if (w & LCS_ERRBIT_MAXSTEPS) return lcs_fail(ctx, LCS_EMAXSTEPS, "an adaptive integration hit max_steps");
     }
     return LCS_OK;
 }
@@ -277,14 +277,14 @@ static lcs_status upload_frames(lcs_ctx *ctx, lcs_field *f, const float *frames,
         cudaError_t e = cudaMemcpyAsync(tmp, frames, n_in * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
         if (e != cudaSuccess) {
             cudaFreeAsync(tmp, ctx->stream);
-            return fail(ctx, LCS_ECUDA, "frame upload: %s", cudaGetErrorString(e));
+            return lcs_fail(ctx, LCS_ECUDA, "frame upload: %s", cudaGetErrorString(e));
         }
         src = tmp;
     }
     cudaError_t e = launch_convert_rect(src, f->nframes, f->nslabs, f->nodes, f->dim, f->vec, f->storage,
                                         f->frame_stride, f->d_frames, ctx->stream);
     if (tmp) cudaFreeAsync(tmp, ctx->stream);
-    if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "frame conversion: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "frame conversion: %s", cudaGetErrorString(e));
     return LCS_OK;
 }
 
@@ -292,28 +292,28 @@ static lcs_status upload_frames(lcs_ctx *ctx, lcs_field *f, const float *frames,
 static lcs_status load_tet_field(lcs_ctx *ctx, const lcs_field_desc *d, const float *frames, int frames_on_device,
                                  lcs_field **out)
 {
-    if (d->dim != 3) return fail(ctx, LCS_EINVAL, "lcs_load_field: tet meshes are 3D");
-    if (d->storage < LCS_F32 || d->storage > LCS_BF16) return fail(ctx, LCS_EINVAL, "lcs_load_field: storage");
+    if (d->dim != 3) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: tet meshes are 3D");
+    if (d->storage < LCS_F32 || d->storage > LCS_BF16) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: storage");
     if (d->nnodes < 4 || d->ncells < 1 || !d->node_xyz || !d->tets)
-        return fail(ctx, LCS_EINVAL, "lcs_load_field: a tet mesh needs nnodes >= 4, ncells >= 1, node_xyz, tets");
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: a tet mesh needs nnodes >= 4, ncells >= 1, node_xyz, tets");
     if (d->nnodes >= (1LL << 31) || d->ncells >= (1LL << 31))
-        return fail(ctx, LCS_EINVAL, "lcs_load_field: more than 2^31 nodes or tets");
-    if (d->nframes < 1 || !d->frame_times) return fail(ctx, LCS_EINVAL, "lcs_load_field: need >= 1 frame");
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: more than 2^31 nodes or tets");
+    if (d->nframes < 1 || !d->frame_times) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: need >= 1 frame");
     for (int k = 1; k < d->nframes; ++k)
         if (!(d->frame_times[k] > d->frame_times[k - 1]))
-            return fail(ctx, LCS_EINVAL, "lcs_load_field: frame_times must increase");
-    if (d->time_periodic && !(d->period > 0.0)) return fail(ctx, LCS_EINVAL, "lcs_load_field: period must be > 0");
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: frame_times must increase");
+    if (d->time_periodic && !(d->period > 0.0)) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: period must be > 0");
     for (long long q = 0; q < 4 * d->ncells; ++q) {
         if (d->tets[q] < 0 || d->tets[q] >= d->nnodes)
-            return fail(ctx, LCS_EINVAL, "lcs_load_field: tet %lld names node %d", q / 4, d->tets[q]);
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: tet %lld names node %d", q / 4, d->tets[q]);
         if (d->nbrs && (d->nbrs[q] < -1 || d->nbrs[q] >= d->ncells))
-            return fail(ctx, LCS_EINVAL, "lcs_load_field: tet %lld has neighbour %d", q / 4, d->nbrs[q]);
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: tet %lld has neighbour %d", q / 4, d->nbrs[q]);
     }
     for (long long q = 0; q < 3 * d->nnodes; ++q)
-        if (!isfinite(d->node_xyz[q])) return fail(ctx, LCS_EINVAL, "lcs_load_field: non-finite node coordinate");
+        if (!isfinite(d->node_xyz[q])) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: non-finite node coordinate");
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     lcs_field *f = new (std::nothrow) lcs_field();
-    if (!f) return fail(ctx, LCS_ENOMEM, "host allocation");
+    if (!f) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
     f->ctx = ctx;
     f->uid = lcs_next_uid();
     f->dim = 3;
@@ -337,7 +337,7 @@ static lcs_status load_tet_field(lcs_ctx *ctx, const lcs_field_desc *d, const fl
         e = cudaMemcpy(f->d_times, f->times.data(), sizeof(double) * f->nframes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = tet_build_store(f, d->node_xyz, d->tets, d->nbrs, ctx->stream);
     if (e != cudaSuccess)
-        st = fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_load_field: %s",
+        st = lcs_fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_load_field: %s",
                   cudaGetErrorString(e));
     else
         st = upload_frames(ctx, f, frames, frames_on_device);
@@ -353,28 +353,28 @@ extern "C" lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *d, cons
                                      int frames_on_device, lcs_field **out)
 {
     if (!ctx) return LCS_EINVAL;
-    if (!d || !frames || !out) return fail(ctx, LCS_EINVAL, "lcs_load_field: null argument");
+    if (!d || !frames || !out) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: null argument");
     *out = nullptr;
     if (d->kind == LCS_TET) return load_tet_field(ctx, d, frames, frames_on_device, out);
-    if (d->kind != LCS_RECTILINEAR) return fail(ctx, LCS_EINVAL, "lcs_load_field: unknown kind %d", d->kind);
-    if (d->dim != 2 && d->dim != 3) return fail(ctx, LCS_EINVAL, "lcs_load_field: dim must be 2 or 3");
-    if (d->storage < LCS_F32 || d->storage > LCS_BF16) return fail(ctx, LCS_EINVAL, "lcs_load_field: storage");
-    if (d->nframes < 1 || !d->frame_times) return fail(ctx, LCS_EINVAL, "lcs_load_field: need >= 1 frame");
+    if (d->kind != LCS_RECTILINEAR) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: unknown kind %d", d->kind);
+    if (d->dim != 2 && d->dim != 3) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: dim must be 2 or 3");
+    if (d->storage < LCS_F32 || d->storage > LCS_BF16) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: storage");
+    if (d->nframes < 1 || !d->frame_times) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: need >= 1 frame");
     for (int k = 1; k < d->nframes; ++k)
         if (!(d->frame_times[k] > d->frame_times[k - 1]))
-            return fail(ctx, LCS_EINVAL, "lcs_load_field: frame_times must increase");
-    if (d->time_periodic && !(d->period > 0.0)) return fail(ctx, LCS_EINVAL, "lcs_load_field: period must be > 0");
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: frame_times must increase");
+    if (d->time_periodic && !(d->period > 0.0)) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: period must be > 0");
     long long nodes = 1;
     for (int a = 0; a < d->dim; ++a) {
         int minn = d->periodic[a] ? 3 : 2;
-        if (d->n[a] < minn) return fail(ctx, LCS_EINVAL, "lcs_load_field: axis %d needs >= %d nodes", a, minn);
-        if (!(d->spacing[a] > 0.0)) return fail(ctx, LCS_EINVAL, "lcs_load_field: spacing must be > 0");
+        if (d->n[a] < minn) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: axis %d needs >= %d nodes", a, minn);
+        if (!(d->spacing[a] > 0.0)) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: spacing must be > 0");
         nodes *= d->n[a];
     }
-    if (nodes >= (1LL << 31)) return fail(ctx, LCS_EINVAL, "lcs_load_field: more than 2^31 nodes per frame");
+    if (nodes >= (1LL << 31)) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: more than 2^31 nodes per frame");
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     lcs_field *f = new (std::nothrow) lcs_field();
-    if (!f) return fail(ctx, LCS_ENOMEM, "host allocation");
+    if (!f) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
     f->ctx = ctx;
     f->uid = lcs_next_uid();
     f->dim = d->dim;
@@ -403,7 +403,7 @@ extern "C" lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *d, cons
     if (e == cudaSuccess)
         e = cudaMemcpy(f->d_times, f->times.data(), sizeof(double) * f->nframes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        st = fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_load_field: %s",
+        st = lcs_fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_load_field: %s",
                   cudaGetErrorString(e));
     } else {
         st = upload_frames(ctx, f, frames, frames_on_device);
@@ -419,7 +419,7 @@ extern "C" lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *d, cons
 extern "C" lcs_status lcs_update_frames(lcs_ctx *ctx, lcs_field *f, const float *frames, int frames_on_device)
 {
     if (!ctx) return LCS_EINVAL;
-    if (!f || !frames) return fail(ctx, LCS_EINVAL, "lcs_update_frames: null argument");
+    if (!f || !frames) return lcs_fail(ctx, LCS_EINVAL, "lcs_update_frames: null argument");
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     return upload_frames(ctx, f, frames, frames_on_device);
 }
@@ -477,20 +477,20 @@ cudaError_t launch_seed_grid(int dim, const int n[3], const double lo[3], const 
 extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const lcs_field *field, lcs_seeds **out)
 {
     if (!ctx) return LCS_EINVAL;
-    if (!d || !out) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: null argument");
+    if (!d || !out) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_grid: null argument");
     *out = nullptr;
-    if (d->dim != 2 && d->dim != 3) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: dim must be 2 or 3");
-    if (field && field->dim != d->dim) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: dim differs from the field's");
-    if (field && field->kind == LCS_TET && d->dim != 3) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: tets are 3D");
+    if (d->dim != 2 && d->dim != 3) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_grid: dim must be 2 or 3");
+    if (field && field->dim != d->dim) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_grid: dim differs from the field's");
+    if (field && field->kind == LCS_TET && d->dim != 3) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_grid: tets are 3D");
     long long N = 1;
     for (int a = 0; a < d->dim; ++a) {
-        if (d->n[a] < 1) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: n[%d] < 1", a);
-        if (!(d->hi[a] >= d->lo[a])) return fail(ctx, LCS_EINVAL, "lcs_seed_grid: hi < lo on axis %d", a);
+        if (d->n[a] < 1) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_grid: n[%d] < 1", a);
+        if (!(d->hi[a] >= d->lo[a])) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_grid: hi < lo on axis %d", a);
         N *= d->n[a];
     }
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     lcs_seeds *s = new (std::nothrow) lcs_seeds();
-    if (!s) return fail(ctx, LCS_ENOMEM, "host allocation");
+    if (!s) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
     s->uid = lcs_next_uid();
     s->dim = d->dim;
     s->N = N;
@@ -516,7 +516,7 @@ extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const 
     }
     if (e != cudaSuccess) {
         lcs_free_seeds(s);
-        return fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_seed_grid: %s",
+        return lcs_fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_seed_grid: %s",
                     cudaGetErrorString(e));
     }
     *out = s;
@@ -531,8 +531,8 @@ extern "C" long long lcs_seeds_count(const lcs_seeds *s)
 extern "C" lcs_status lcs_seeds_get(lcs_ctx *ctx, const lcs_seeds *s, float *xyz, int *cells, int on_device)
 {
     if (!ctx) return LCS_EINVAL;
-    if (!s) return fail(ctx, LCS_EINVAL, "lcs_seeds_get: null seeds");
-    if (cells && !s->d_cells) return fail(ctx, LCS_EINVAL, "lcs_seeds_get: seeds carry no cell ids");
+    if (!s) return lcs_fail(ctx, LCS_EINVAL, "lcs_seeds_get: null seeds");
+    if (cells && !s->d_cells) return lcs_fail(ctx, LCS_EINVAL, "lcs_seeds_get: seeds carry no cell ids");
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (xyz) CUDA_TRY(ctx, cudaMemcpyAsync(xyz, s->d_xyz, sizeof(float) * s->dim * s->N, k, ctx->stream));
@@ -554,12 +554,12 @@ extern "C" void lcs_free_seeds(lcs_seeds *s)
 extern "C" lcs_status lcs_flowmap_create(lcs_ctx *ctx, const lcs_seeds *s, int njobs, lcs_flowmap **out)
 {
     if (!ctx) return LCS_EINVAL;
-    if (!s || !out) return fail(ctx, LCS_EINVAL, "lcs_flowmap_create: null argument");
+    if (!s || !out) return lcs_fail(ctx, LCS_EINVAL, "lcs_flowmap_create: null argument");
     *out = nullptr;
-    if (njobs < 1 || njobs > LCS_MAX_JOBS) return fail(ctx, LCS_EINVAL, "lcs_flowmap_create: njobs in [1, %d]", LCS_MAX_JOBS);
+    if (njobs < 1 || njobs > LCS_MAX_JOBS) return lcs_fail(ctx, LCS_EINVAL, "lcs_flowmap_create: njobs in [1, %d]", LCS_MAX_JOBS);
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     lcs_flowmap *fm = new (std::nothrow) lcs_flowmap();
-    if (!fm) return fail(ctx, LCS_ENOMEM, "host allocation");
+    if (!fm) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
     fm->ctx = ctx;
     fm->uid = lcs_next_uid();
     fm->seeds = s;
@@ -575,7 +575,7 @@ extern "C" lcs_status lcs_flowmap_create(lcs_ctx *ctx, const lcs_seeds *s, int n
     if (e == cudaSuccess) e = cudaMemsetAsync(fm->d_status, LCS_TRACER_OUTSIDE, N * njobs, ctx->stream);
     if (e != cudaSuccess) {
         lcs_free_flowmap(fm);
-        return fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_flowmap_create: %s",
+        return lcs_fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_flowmap_create: %s",
                     cudaGetErrorString(e));
     }
     *out = fm;
@@ -671,11 +671,11 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.work = want_sorted ? (char *)ctx->d_scratch + jb + sb : nullptr;
     if (f->kind == LCS_TET) {
         cudaError_t e = launch_rk4_tet(ctx, L, s->d_cells, o->walk_limit, ctx->stream);
-        if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(e));
         return LCS_OK;
     }
     if (launch_rk4_rect(ctx, L, ctx->stream) < 0)
-        return fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return lcs_fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return LCS_OK;
 }
 
@@ -683,14 +683,14 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
 static lcs_status advect_rk45(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
                               lcs_flowmap *fm)
 {
-    if (f->dim != 3) return fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: RK45 on 2D fields not built in");
+    if (f->dim != 3) return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: RK45 on 2D fields not built in");
     const int njobs = o->njobs > 1 ? o->njobs : 1;
     const double rtol = o->rtol > 0 ? o->rtol : 1e-6, atol = o->atol > 0 ? o->atol : 1e-6;
     const double h0 = o->h0 != 0 ? fabs(o->h0) : 0.01;
     if (!isfinite(rtol) || !isfinite(atol) || !isfinite(h0))
-        return fail(ctx, LCS_EINVAL, "lcs_advect: rtol, atol and h0 must be finite");
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: rtol, atol and h0 must be finite");
     JobTable *J = new (std::nothrow) JobTable();
-    if (!J) return fail(ctx, LCS_ENOMEM, "host allocation");
+    if (!J) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
     J->njobs = njobs;
     J->nsteps_max = 0;
     for (int j = 0; j < njobs; ++j) {
@@ -698,7 +698,7 @@ static lcs_status advect_rk45(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds 
         double T = o->njobs > 1 ? o->job_T[j] : o->T;
         if (!isfinite(t0) || !isfinite(T)) {
             delete J;
-            return fail(ctx, LCS_EINVAL, "lcs_advect: job %d has a non-finite t0 or T", j);
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: job %d has a non-finite t0 or T", j);
         }
         J->t0[j] = t0;
         J->T[j] = T;
@@ -709,9 +709,9 @@ static lcs_status advect_rk45(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds 
     }
     cudaError_t e = cudaSetDevice(ctx->device);
     size_t need = 2 * align256(sizeof(int) * njobs) + 3 * align256(sizeof(float) * njobs) + 2 * align256(8 * njobs);
-    lcs_status st = e == cudaSuccess ? scratch_reserve(ctx, need) : fail(ctx, LCS_ECUDA, "cudaSetDevice failed");
+    lcs_status st = e == cudaSuccess ? scratch_reserve(ctx, need) : lcs_fail(ctx, LCS_ECUDA, "cudaSetDevice failed");
     if (st == LCS_OK && !fm->d_steps && cudaMalloc(&fm->d_steps, sizeof(int) * (size_t)fm->N * fm->njobs) != cudaSuccess)
-        st = fail(ctx, LCS_ENOMEM, "lcs_advect: step counts");
+        st = lcs_fail(ctx, LCS_ENOMEM, "lcs_advect: step counts");
     if (st != LCS_OK) {
         delete J;
         return st;
@@ -735,7 +735,7 @@ static lcs_status advect_rk45(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds 
     e = launch_rk4_schedule(f->d_times, f->nframes, f->time_periodic, f->period, *J, D, nullptr,
                             ctx->stream);  // per-job values only (no RK4 steps)
     delete J;
-    if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "lcs_advect: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_advect: %s", cudaGetErrorString(e));
     Dp45Args A;
     memset(&A, 0, sizeof A);
     A.seeds = s->d_xyz;
@@ -752,16 +752,16 @@ static lcs_status advect_rk45(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds 
     A.out_texit = fm->d_texit;
     A.out_steps = fm->d_steps;
     e = launch_dp45(ctx, f, A, njobs, o->block_threads, o->walk_limit, ctx->stream);
-    if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "lcs_advect: RK45 launch failed: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_advect: RK45 launch failed: %s", cudaGetErrorString(e));
     return LCS_OK;
 }
 
 extern "C" lcs_status lcs_flowmap_steps(lcs_ctx *ctx, const lcs_flowmap *fm, int job, int *steps, int on_device)
 {
     if (!ctx) return LCS_EINVAL;
-    if (!fm || !steps) return fail(ctx, LCS_EINVAL, "lcs_flowmap_steps: null argument");
-    if (job < 0 || job >= fm->njobs) return fail(ctx, LCS_EINVAL, "lcs_flowmap_steps: job %d out of range", job);
-    if (!fm->d_steps) return fail(ctx, LCS_EINVAL, "lcs_flowmap_steps: no adaptive integration wrote this flow map");
+    if (!fm || !steps) return lcs_fail(ctx, LCS_EINVAL, "lcs_flowmap_steps: null argument");
+    if (job < 0 || job >= fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "lcs_flowmap_steps: job %d out of range", job);
+    if (!fm->d_steps) return lcs_fail(ctx, LCS_EINVAL, "lcs_flowmap_steps: no adaptive integration wrote this flow map");
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     CUDA_TRY(ctx, cudaMemcpyAsync(steps, fm->d_steps + (size_t)job * fm->N, sizeof(int) * (size_t)fm->N,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
@@ -816,13 +816,13 @@ static lcs_status advect_graph(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds
     if (e != cudaSuccess || e2 != cudaSuccess || st != LCS_OK) {
         if (graph) cudaGraphDestroy(graph);
         if (st != LCS_OK) return st;
-        return fail(ctx, LCS_ECUDA, "lcs_advect: graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return lcs_fail(ctx, LCS_ECUDA, "lcs_advect: graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(graph);
-        return fail(ctx, LCS_ECUDA, "lcs_advect: graph instantiate: %s", cudaGetErrorString(e));
+        return lcs_fail(ctx, LCS_ECUDA, "lcs_advect: graph instantiate: %s", cudaGetErrorString(e));
     }
     if (ctx->graphs.size() >= 8) {  // evict the least recently used
         auto it = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
@@ -847,21 +847,21 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
                                  lcs_flowmap *fm)
 {
     if (!ctx) return LCS_EINVAL;
-    if (!f || !s || !o || !fm) return fail(ctx, LCS_EINVAL, "lcs_advect: null argument");
-    if (f->dim != s->dim) return fail(ctx, LCS_EINVAL, "lcs_advect: field and seeds differ in dim");
-    if (fm->seeds != s) return fail(ctx, LCS_EINVAL, "lcs_advect: flow map was made for other seeds");
+    if (!f || !s || !o || !fm) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: null argument");
+    if (f->dim != s->dim) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: field and seeds differ in dim");
+    if (fm->seeds != s) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: flow map was made for other seeds");
     int njobs = o->njobs > 1 ? o->njobs : 1;
-    if (njobs > fm->njobs) return fail(ctx, LCS_EINVAL, "lcs_advect: %d jobs > flow map's %d", njobs, fm->njobs);
-    if (o->njobs > 1 && (!o->job_t0 || !o->job_T)) return fail(ctx, LCS_EINVAL, "lcs_advect: job arrays missing");
+    if (njobs > fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: %d jobs > flow map's %d", njobs, fm->njobs);
+    if (o->njobs > 1 && (!o->job_t0 || !o->job_T)) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: job arrays missing");
     if (o->method != LCS_RK4 && o->method != LCS_RK45)
-        return fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: method %d not built in", o->method);
+        return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: method %d not built in", o->method);
     if (f->kind == LCS_TET && (!s->d_cells || s->field_uid != f->uid))
-        return fail(ctx, LCS_EINVAL, "lcs_advect: on a tet field the seeds must come from lcs_seed_grid on that field");
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: on a tet field the seeds must come from lcs_seed_grid on that field");
     if (o->method == LCS_RK45) return advect_rk45(ctx, f, s, o, fm);
     double adt = fabs(o->dt);
-    if (!(adt > 0.0) || !isfinite(adt)) return fail(ctx, LCS_EINVAL, "lcs_advect: dt must be finite and > 0");
+    if (!(adt > 0.0) || !isfinite(adt)) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: dt must be finite and > 0");
     JobTable *J = new (std::nothrow) JobTable();
-    if (!J) return fail(ctx, LCS_ENOMEM, "host allocation");
+    if (!J) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
     J->njobs = njobs;
     J->nsteps_max = 0;
     for (int j = 0; j < njobs; ++j) {
@@ -869,13 +869,13 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
         double T = o->njobs > 1 ? o->job_T[j] : o->T;
         if (!isfinite(t0) || !isfinite(T)) {
             delete J;
-            return fail(ctx, LCS_EINVAL, "lcs_advect: job %d has a non-finite t0 or T", j);
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: job %d has a non-finite t0 or T", j);
         }
         double r = fabs(T) / adt;
         long long ns = (long long)floor(r + 0.5);
         if (fabs(r - (double)ns) > 1e-9 * std::max(1.0, r) || ns > (1LL << 30)) {
             delete J;
-            return fail(ctx, LCS_EINVAL, "lcs_advect: |T|/|dt| = %.17g is not an integer (job %d)", r, j);
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: |T|/|dt| = %.17g is not an integer (job %d)", r, j);
         }
         J->t0[j] = t0;
         J->T[j] = T;
@@ -890,7 +890,7 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
     lcs_status st;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess)
-        st = fail(ctx, LCS_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+        st = lcs_fail(ctx, LCS_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
     else if (o->use_graph)
         st = advect_graph(ctx, f, s, o, fm, *J);
     else
@@ -903,8 +903,8 @@ extern "C" lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int j
                                       unsigned char *status, float *t_exit, int on_device)
 {
     if (!ctx) return LCS_EINVAL;
-    if (!fm) return fail(ctx, LCS_EINVAL, "lcs_flowmap_get: null flow map");
-    if (job < 0 || job >= fm->njobs) return fail(ctx, LCS_EINVAL, "lcs_flowmap_get: job %d out of range", job);
+    if (!fm) return lcs_fail(ctx, LCS_EINVAL, "lcs_flowmap_get: null flow map");
+    if (job < 0 || job >= fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "lcs_flowmap_get: job %d out of range", job);
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     size_t N = (size_t)fm->N;
@@ -924,11 +924,11 @@ static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *f
                           int on_device, const char *who)
 {
     if (!ctx) return LCS_EINVAL;
-    if (!fm) return fail(ctx, LCS_EINVAL, "%s: null flow map", who);
-    if (job < -1 || job >= fm->njobs) return fail(ctx, LCS_EINVAL, "%s: job %d out of range", who, job);
+    if (!fm) return lcs_fail(ctx, LCS_EINVAL, "%s: null flow map", who);
+    if (job < -1 || job >= fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "%s: job %d out of range", who, job);
     const lcs_seeds *s = fm->seeds;
     for (int a = 0; a < s->dim; ++a)
-        if (s->n[a] < 3) return fail(ctx, LCS_EINVAL, "%s: the lattice needs >= 3 seeds per axis", who);
+        if (s->n[a] < 3) return lcs_fail(ctx, LCS_EINVAL, "%s: the lattice needs >= 3 seeds per axis", who);
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     int j0 = job < 0 ? 0 : job, nj = job < 0 ? fm->njobs : 1;
     size_t N = (size_t)fm->N;
@@ -968,19 +968,19 @@ static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *f
     }
     if (tmp) cudaFreeAsync(tmp, ctx->stream);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return fail(ctx, LCS_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+    if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "%s: %s", who, cudaGetErrorString(e));
     return LCS_OK;
 }
 
 extern "C" lcs_status lcs_cauchy_green(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double *C, int on_device)
 {
-    if (ctx && !C) return fail(ctx, LCS_EINVAL, "lcs_cauchy_green: null output");
+    if (ctx && !C) return lcs_fail(ctx, LCS_EINVAL, "lcs_cauchy_green: null output");
     return cg_call(ctx, fm, job, nullptr, nullptr, C, on_device, "lcs_cauchy_green");
 }
 
 extern "C" lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
                                double *C, int on_device)
 {
-    if (ctx && !ftle) return fail(ctx, LCS_EINVAL, "lcs_ftle: null output");
+    if (ctx && !ftle) return lcs_fail(ctx, LCS_EINVAL, "lcs_ftle: null output");
     return cg_call(ctx, fm, job, ftle, lambda_max, C, on_device, "lcs_ftle");
 }

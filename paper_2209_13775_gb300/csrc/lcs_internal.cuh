@@ -241,6 +241,17 @@ struct CgLaunch {
 
 cudaError_t launch_cg_ftle(const CgLaunch &L, cudaStream_t s);
 
+// set the context's last error (printf-style) and return st (lcs_api.cu)
+lcs_status lcs_fail(lcs_ctx *ctx, lcs_status st, const char *fmt, ...);
+
+#define LCS_CUDA_TRY(ctx, call)                                                                        \
+    do {                                                                                               \
+        cudaError_t e__ = (call);                                                                      \
+        if (e__ != cudaSuccess)                                                                        \
+            return lcs_fail((ctx), e__ == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "%s: %s", \
+                            #call, cudaGetErrorString(e__));                                           \
+    } while (0)
+
 // ------------------------------------------------------------------ misc
 
 cudaError_t launch_seed_grid(int dim, const int n[3], const double lo[3], const double hi[3],

@@ -28,7 +28,7 @@ EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs
            "lcs_flowmap_steps",
            "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_timing_enable",
            "lcs_timing_read",
-           "lcs_advect_rk4_noalloc"]
+           "lcs_advect_rk4_noalloc", "lcs_gemm_bf16"]
 PHASE_ADVECT, PHASE_REBUNDLE, PHASE_SLICES, PHASE_CG = 0, 1, 2, 3
 NOALLOC_MAX_STEPS = 43680
 
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_timing_enable": ([P, I], S), "lcs_timing_read": ([P, I, P, P], S),
         "lcs_autotune": ([P, P, P, P, ctypes.c_char_p], S),
         "lcs_flowmap_steps": ([P, P, I, P, I], S),
+        "lcs_gemm_bf16": ([P, LL, I, LL, P, LL, P, LL, P, LL, I, I], S),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -338,3 +339,14 @@ def lcs_advect_rk4_noalloc(ctx, field, seeds, t0, T, dt, xyz, status, t_exit):
     n = int(seeds.shape[-1])
     _check(ctx, load().lcs_advect_rk4_noalloc(ctx, field, ctypes.c_void_p(ptrs[0][0]), n, float(t0), float(T),
                                               float(dt), *[ctypes.c_void_p(p) for p, _ in ptrs[1:]]))
+
+
+# ------------------------------------------------------------ tensor-core GEMM
+
+def lcs_gemm_bf16(ctx, A, B, C, splits=1, accumulate=False):
+    """C[M x N] (+)= A[M x K] @ B[N x K]^T; A, B bf16 CUDA tensors, C float32 CUDA tensor."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(ctx, load().lcs_gemm_bf16(ctx, M, N, K, ctypes.c_void_p(A.data_ptr()), A.stride(0),
+                                     ctypes.c_void_p(B.data_ptr()), B.stride(0), ctypes.c_void_p(C.data_ptr()),
+                                     C.stride(0), int(splits), int(bool(accumulate))))
