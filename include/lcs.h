@@ -173,6 +173,15 @@ void lcs_free_seeds(lcs_seeds *seeds);
  *            live lane accepts (err <= 1, err = max_i |e_i| / (atol + rtol *
  *            max(|x_i|, |x_new_i|))), and the next step is the smallest lane
  *            proposal h * min(5, max(0.2, 0.9 err^-1/5)).
+ *  LCS_SURROGATE  2D non-periodic rectilinear fields, one job, T = K tau > 0
+ *            with tau the network's step and tau = S dt: per sub-interval k
+ *            every tracer proposes x + displacement(x, t0 + k tau); in each
+ *            group of 32 consecutive seeds one audited lane (lowbias32 hash of
+ *            k and the group index, modulo the group size) integrates RK4 (step
+ *            dt) over the sub-interval, and the whole group integrates RK4
+ *            instead when |proposal - RK4| > gate_tol or any lane's
+ *            rho > log10(gate_tol).  The RK4 arithmetic is that of LCS_RK4, so
+ *            gate_tol = 0 reproduces it bit for bit.
  * Batches: njobs > 1 integrates the same seeds for each (job_t0[j], job_T[j])
  * pair in one persistent launch.                                            */
 typedef struct {
@@ -191,12 +200,14 @@ typedef struct {
                                    3 = tracers re-bundled by cell between episodes (3D);
                                    4 = persistent shared-memory ring pulling (job, tile)
                                        items longest-job first (2D, batches)            */
-    const void *surrogate;      /* reserved for LCS_SURROGATE                         */
+    const void *surrogate;      /* LCS_SURROGATE: the lcs_mlp to step with            */
     int episode_steps;          /* variant 3: RK4 steps between re-bundlings (0 = 16) */
     int tracers_per_thread;     /* variants 2 and 4: 1 or 2 tracers per thread (0 = 1) */
     int use_graph;              /* capture the launches of this call in a CUDA graph,
                                    cached on the context and replayed while the same
                                    field, seeds, flow map and options come back      */
+    double gate_tol;            /* LCS_SURROGATE: audit threshold (0 = every
+                                   sub-interval by RK4, +inf = never)              */
 } lcs_advect_opts;
 
 /* Flow-map storage for `njobs` integrations of one lattice.                 */
@@ -216,11 +227,12 @@ lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *see
 lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *xyz,
                            unsigned char *status, float *t_exit, int on_device);
 
-/* Accepted steps per tracer of job `job` after an LCS_RK45 integration ([N]
- * int32; 32 consecutive seeds step together, so the tracers of a group that
+/* Per-tracer step counts of job `job` ([N] int32).  After LCS_RK45: accepted
+ * steps (32 consecutive seeds step together, so the tracers of a group that
  * stay live to the end report the same count, and a tracer that stopped early
- * the count it had reached).
- * Errors: LCS_EINVAL when no adaptive integration wrote this flow map.      */
+ * the count it had reached).  After LCS_SURROGATE: the sub-intervals the
+ * tracer integrated with RK4 because its group failed the audit.
+ * Errors: LCS_EINVAL when neither integration wrote this flow map.          */
 lcs_status lcs_flowmap_steps(lcs_ctx *ctx, const lcs_flowmap *fm, int job, int *steps, int on_device);
 
 void lcs_free_flowmap(lcs_flowmap *fm);
@@ -236,6 +248,44 @@ void lcs_free_flowmap(lcs_flowmap *fm);
  * those of lcs_advect.                                                      */
 lcs_status lcs_autotune(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *seeds, lcs_advect_opts *opts,
                         const char *cache_path);
+
+/* ------------------------------------------ learned surrogate (a13, a14) */
+
+/* A multilayer perceptron 7 -> 128 -> 128 -> 128 -> 128 -> 3 with SiLU after each
+ * hidden layer maps features of a point (x, y) at time t of a 2D field,
+ *   phi = (x - cx, y - cy, sin(omega t), cos(omega t), sin(kx x), cos(kx x), sin(ky y)),
+ * to outputs o: the displacement over one step tau is out_scale * (o0, o1), and
+ * o2 = rho predicts log10 of that displacement's error.  It stands in for the
+ * integrator over a sub-interval (the paper has no such network; the local
+ * flow-map approximations it mentions among related work, Sec. 5, are the
+ * nearest idea).  Parameters: LCS_MLP_NPARAMS FP32 values packed as
+ *   W0[128][7] b0[128] W1[128][128] b1 W2 b2 W3 b3 W4[3][128] b4[3]
+ * (row-major W[out][in]); the library keeps them in FP32 and computes with BF16
+ * copies of the weights and BF16 activations, FP32 accumulation and FP32 biases,
+ * on the tensor cores.                                                      */
+#define LCS_MLP_NPARAMS 50947
+
+typedef struct lcs_mlp lcs_mlp;
+
+typedef struct {
+    double center[2];           /* (cx, cy)                                         */
+    double kx, ky, omega;       /* spatial and temporal frequencies of phi         */
+    double tau;                 /* step of the surrogate (> 0)                     */
+    double out_scale;           /* displacement = out_scale * (o0, o1) (> 0)       */
+} lcs_mlp_desc;
+
+/* Network with the given parameters (host or device, copied).
+ * Errors: LCS_EINVAL (descriptor), LCS_ENOMEM, LCS_ECUDA.                    */
+lcs_status lcs_mlp_create(lcs_ctx *ctx, const lcs_mlp_desc *desc, const float *params, int on_device,
+                          lcs_mlp **out);
+/* Replace / read the FP32 parameters; setting them also resets Adam's state. */
+lcs_status lcs_mlp_set_params(lcs_ctx *ctx, lcs_mlp *mlp, const float *params, int on_device);
+lcs_status lcs_mlp_get_params(lcs_ctx *ctx, const lcs_mlp *mlp, float *params, int on_device);
+void lcs_mlp_free(lcs_mlp *mlp);
+
+/* Outputs o [3][n] (o0, o1, o2 rows) at points xyt [3][n] (x, y, t rows).    */
+lcs_status lcs_mlp_forward(lcs_ctx *ctx, const lcs_mlp *mlp, long long n, const float *xyt, float *out,
+                           int on_device);
 
 /* ------------------------------------------------ tensor-core GEMM (BF16) */
 

@@ -5,6 +5,7 @@
 // plus the two bulk conversion kernels (frame storage, seed lattice).
 #include "lcs_internal.cuh"
 #include "dp45_args.cuh"
+#include "mlp_internal.cuh"
 
 #include <math.h>
 #include <stdarg.h>
@@ -193,7 +194,7 @@ extern "C" lcs_status lcs_synchronize(lcs_ctx *ctx)
 }
 
 // grow the context's reusable device scratch to at least `bytes`
-static lcs_status scratch_reserve(lcs_ctx *ctx, size_t bytes)
+lcs_status lcs_scratch_reserve(lcs_ctx *ctx, size_t bytes)
 {
     if (bytes <= ctx->scratch_bytes) return LCS_OK;
     if (ctx->d_scratch) {
@@ -625,7 +626,7 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     const size_t jb = Ly.jb, sb = Ly.sb;
     const bool want_sorted = Ly.want_sorted;
     const int E = Ly.E;
-    lcs_status st = scratch_reserve(ctx, jb + sb + Ly.wb);
+    lcs_status st = lcs_scratch_reserve(ctx, jb + sb + Ly.wb);
     if (st != LCS_OK) return st;
     char *p = (char *)ctx->d_scratch;
     JobDev D;
@@ -709,7 +710,7 @@ static lcs_status advect_rk45(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds 
     }
     cudaError_t e = cudaSetDevice(ctx->device);
     size_t need = 2 * align256(sizeof(int) * njobs) + 3 * align256(sizeof(float) * njobs) + 2 * align256(8 * njobs);
-    lcs_status st = e == cudaSuccess ? scratch_reserve(ctx, need) : lcs_fail(ctx, LCS_ECUDA, "cudaSetDevice failed");
+    lcs_status st = e == cudaSuccess ? lcs_scratch_reserve(ctx, need) : lcs_fail(ctx, LCS_ECUDA, "cudaSetDevice failed");
     if (st == LCS_OK && !fm->d_steps && cudaMalloc(&fm->d_steps, sizeof(int) * (size_t)fm->N * fm->njobs) != cudaSuccess)
         st = lcs_fail(ctx, LCS_ENOMEM, "lcs_advect: step counts");
     if (st != LCS_OK) {
@@ -792,7 +793,7 @@ static lcs_status advect_graph(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds
                                lcs_flowmap *fm, JobTable &J)
 {
     const AdvectLayout Ly = advect_layout(f, s, o, J);
-    lcs_status st = scratch_reserve(ctx, Ly.jb + Ly.sb + Ly.wb);
+    lcs_status st = lcs_scratch_reserve(ctx, Ly.jb + Ly.sb + Ly.wb);
     if (st != LCS_OK) return st;
     const std::string key = graph_key(ctx, f, s, o, fm, J);
     ctx->graph_clock++;
@@ -853,8 +854,9 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
     int njobs = o->njobs > 1 ? o->njobs : 1;
     if (njobs > fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: %d jobs > flow map's %d", njobs, fm->njobs);
     if (o->njobs > 1 && (!o->job_t0 || !o->job_T)) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: job arrays missing");
-    if (o->method != LCS_RK4 && o->method != LCS_RK45)
+    if (o->method != LCS_RK4 && o->method != LCS_RK45 && o->method != LCS_SURROGATE)
         return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: method %d not built in", o->method);
+    if (o->method == LCS_SURROGATE) return advect_surrogate(ctx, f, s, o, fm);
     if (f->kind == LCS_TET && (!s->d_cells || s->field_uid != f->uid))
         return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: on a tet field the seeds must come from lcs_seed_grid on that field");
     if (o->method == LCS_RK45) return advect_rk45(ctx, f, s, o, fm);

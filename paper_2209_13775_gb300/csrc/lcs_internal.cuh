@@ -241,6 +241,9 @@ struct CgLaunch {
 
 cudaError_t launch_cg_ftle(const CgLaunch &L, cudaStream_t s);
 
+// grow the context's reusable device scratch (dropping captured graphs that point into it)
+lcs_status lcs_scratch_reserve(lcs_ctx *ctx, size_t bytes);
+
 // set the context's last error (printf-style) and return st (lcs_api.cu)
 lcs_status lcs_fail(lcs_ctx *ctx, lcs_status st, const char *fmt, ...);
 

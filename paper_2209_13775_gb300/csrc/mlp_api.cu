@@ -1,5 +1,10 @@
 // mlp_api.cu -- C ABI of the learned surrogate and of the tensor-core GEMM under it.
 #include "mlp_internal.cuh"
+#include "tc_common.cuh"
+
+#include <math.h>
+
+#include <new>
 
 extern "C" lcs_status lcs_gemm_bf16(lcs_ctx *ctx, long long M, int N, long long K, const void *A, long long lda,
                                     const void *B, long long ldb, float *C, long long ldc, int splits, int accumulate)
@@ -15,5 +20,317 @@ extern "C" lcs_status lcs_gemm_bf16(lcs_ctx *ctx, long long M, int N, long long 
     LCS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     LCS_CUDA_TRY(ctx, launch_gemm_bf16((const __nv_bfloat16 *)A, lda, (const __nv_bfloat16 *)B, ldb, C, ldc, M, N, K,
                                        splits, accumulate, ctx->d_errword, ctx->stream));
+    return LCS_OK;
+}
+
+// ------------------------------------------------------------------ network state
+
+namespace {
+
+// FP32 master parameters -> the inference block (canonical operand tiles + biases) and the
+// trainer's K-major BF16 operands and their transposes; one thread per destination element
+__global__ void mlp_refresh_kernel(const float *__restrict__ p, unsigned char *__restrict__ tiles,
+                                   __nv_bfloat16 *__restrict__ wk, __nv_bfloat16 *__restrict__ wt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // inference tiles: W0 (128 x 16), W1..W3 (128 x 128), W4 (16 x 128) as BF16 elements
+    const int n_w0 = 128 * 16, n_w = 128 * 128, n_w4 = 16 * 128;
+    const int n_tiles = n_w0 + 3 * n_w + n_w4;
+    const int n_k = n_tiles;                // trainer operands, same element counts
+    const int n_t = 3 * n_w + 128 * 16;     // transposes of W1..W3 and W4
+    if (i < n_tiles) {
+        int r, k, R, l;
+        uint32_t base;
+        float v;
+        if (i < n_w0) {
+            l = 0, R = 128, r = i / 16, k = i % 16, base = 0;
+            v = k < 7 ? p[MLP_OFF_W0 + r * 7 + k] : 0.0f;
+        } else if (i < n_w0 + 3 * n_w) {
+            const int j = i - n_w0;
+            l = 1 + j / n_w, R = 128, r = (j % n_w) / 128, k = j % 128, base = 4096 + 32768u * (l - 1);
+            v = p[MLP_OFF_W1 + (l - 1) * MLP_LAYER_STRIDE + r * 128 + k];
+        } else {
+            const int j = i - n_w0 - 3 * n_w;
+            l = 4, R = 16, r = j / 128, k = j % 128, base = 102400;
+            v = r < 3 ? p[MLP_OFF_W4 + r * 128 + k] : 0.0f;
+        }
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16 *>(tiles + base + ckm_offset(R, r, k)) = b;
+        // trainer operand, row-major [out][in] with the same padding
+        wk[i] = b;
+        (void)l;
+    } else if (i < n_tiles + n_t) {
+        const int j = i - n_tiles;
+        if (j < 3 * n_w) {  // W_l^T [in][out]
+            const int l = 1 + j / n_w, in = (j % n_w) / 128, out = j % 128;
+            wt[j] = __float2bfloat16_rn(p[MLP_OFF_W1 + (l - 1) * MLP_LAYER_STRIDE + out * 128 + in]);
+        } else {            // W4^T [128 in][16 out]
+            const int q = j - 3 * n_w, in = q / 16, out = q % 16;
+            wt[j] = __float2bfloat16_rn(out < 3 ? p[MLP_OFF_W4 + out * 128 + in] : 0.0f);
+        }
+    } else if (i < n_tiles + n_t + 528) {
+        const int j = i - n_tiles - n_t;     // biases b0..b3, then b4 padded to 16
+        float v;
+        if (j < 512)
+            v = p[MLP_OFF_B0 + (j / 128) * MLP_LAYER_STRIDE + (j % 128)];
+        else
+            v = j - 512 < 3 ? p[MLP_OFF_B4 + (j - 512)] : 0.0f;
+        reinterpret_cast<float *>(tiles + 106496)[j] = v;
+    }
+    (void)n_k;
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_refresh(lcs_mlp *m, cudaStream_t s)
+{
+    const int total = (128 * 16 + 3 * 128 * 128 + 16 * 128) + (3 * 128 * 128 + 128 * 16) + 528;
+    mlp_refresh_kernel<<<(total + 255) / 256, 256, 0, s>>>(m->d_params, m->d_tiles, m->d_wk, m->d_wt);
+    return cudaGetLastError();
+}
+
+static bool desc_ok(const lcs_mlp_desc *d)
+{
+    return d && isfinite(d->center[0]) && isfinite(d->center[1]) && isfinite(d->kx) && isfinite(d->ky) &&
+           isfinite(d->omega) && d->tau > 0.0 && isfinite(d->tau) && d->out_scale > 0.0 && isfinite(d->out_scale);
+}
+
+extern "C" lcs_status lcs_mlp_create(lcs_ctx *ctx, const lcs_mlp_desc *d, const float *params, int on_device,
+                                     lcs_mlp **out)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!out || !params) return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_create: null argument");
+    *out = nullptr;
+    if (!desc_ok(d)) return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_create: descriptor (tau, out_scale > 0, finite)");
+    LCS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    lcs_mlp *m = new (std::nothrow) lcs_mlp();
+    if (!m) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
+    m->uid = lcs_next_uid();
+    m->ctx = ctx;
+    m->d = *d;
+    const size_t pb = sizeof(float) * MLP_NPARAMS;
+    cudaError_t e = cudaMalloc(&m->d_params, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_m, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_v, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_grad, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_tiles, MLP_TILE_BYTES);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_wk, sizeof(__nv_bfloat16) * (128 * 16 + 3 * 128 * 128 + 16 * 128));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_wt, sizeof(__nv_bfloat16) * (3 * 128 * 128 + 128 * 16));
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_m, 0, pb, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d_v, 0, pb, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->d_params, params, pb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            ctx->stream);
+    if (e == cudaSuccess) e = launch_mlp_refresh(m, ctx->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        lcs_mlp_free(m);
+        return lcs_fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_mlp_create: %s",
+                        cudaGetErrorString(e));
+    }
+    *out = m;
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_mlp_set_params(lcs_ctx *ctx, lcs_mlp *m, const float *params, int on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!m || !params) return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_set_params: null argument");
+    LCS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    LCS_CUDA_TRY(ctx, cudaMemcpyAsync(m->d_params, params, sizeof(float) * MLP_NPARAMS,
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    LCS_CUDA_TRY(ctx, cudaMemsetAsync(m->d_m, 0, sizeof(float) * MLP_NPARAMS, ctx->stream));
+    LCS_CUDA_TRY(ctx, cudaMemsetAsync(m->d_v, 0, sizeof(float) * MLP_NPARAMS, ctx->stream));
+    m->adam_steps = 0;
+    LCS_CUDA_TRY(ctx, launch_mlp_refresh(m, ctx->stream));
+    if (!on_device) LCS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_mlp_get_params(lcs_ctx *ctx, const lcs_mlp *m, float *params, int on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!m || !params) return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_get_params: null argument");
+    LCS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    LCS_CUDA_TRY(ctx, cudaMemcpyAsync(params, m->d_params, sizeof(float) * MLP_NPARAMS,
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (!on_device) LCS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return LCS_OK;
+}
+
+extern "C" void lcs_mlp_free(lcs_mlp *m)
+{
+    if (!m) return;
+    if (m->ctx) cudaSetDevice(m->ctx->device);
+    cudaFree(m->d_params);
+    cudaFree(m->d_m);
+    cudaFree(m->d_v);
+    cudaFree(m->d_grad);
+    cudaFree(m->d_tiles);
+    cudaFree(m->d_wk);
+    cudaFree(m->d_wt);
+    cudaFree(m->d_work);
+    delete m;
+}
+
+extern "C" lcs_status lcs_mlp_forward(lcs_ctx *ctx, const lcs_mlp *m, long long n, const float *xyt, float *out,
+                                      int on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!m || (n > 0 && (!xyt || !out))) return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_forward: null argument");
+    if (n < 0) return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_forward: n < 0");
+    if (n == 0) return LCS_OK;
+    LCS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    float *din = nullptr, *dout = nullptr;
+    const float *src = xyt;
+    float *dst = out;
+    if (!on_device) {
+        LCS_CUDA_TRY(ctx, cudaMallocAsync((void **)&din, sizeof(float) * 3 * n, ctx->stream));
+        LCS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dout, sizeof(float) * 3 * n, ctx->stream));
+        LCS_CUDA_TRY(ctx, cudaMemcpyAsync(din, xyt, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        src = din;
+        dst = dout;
+    }
+    MlpStepArgs A;
+    A.tiles = m->d_tiles;
+    A.x = src;
+    A.stride = n;
+    A.n = n;
+    A.t = src + 2 * n;
+    A.t_uniform = 0.0f;
+    A.cx = (float)m->d.center[0];
+    A.cy = (float)m->d.center[1];
+    A.kx = (float)m->d.kx;
+    A.ky = (float)m->d.ky;
+    A.omega = (float)m->d.omega;
+    A.out_scale = (float)m->d.out_scale;
+    A.mode = 0;
+    A.out0 = dst;
+    A.out1 = dst + n;
+    A.out2 = dst + 2 * n;
+    A.errword = ctx->d_errword;
+    cudaError_t e = launch_mlp_step(A, ctx->num_sms, ctx->stream);
+    if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(out, dout, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (din) cudaFreeAsync(din, ctx->stream);
+    if (dout) cudaFreeAsync(dout, ctx->stream);
+    if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_mlp_forward: %s", cudaGetErrorString(e));
+    if (!on_device) return lcs_synchronize(ctx);
+    return LCS_OK;
+}
+
+// ------------------------------------------------------------------ gated advection
+
+lcs_status advect_surrogate(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
+                            lcs_flowmap *fm)
+{
+    const lcs_mlp *m = (const lcs_mlp *)o->surrogate;
+    if (!m) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: LCS_SURROGATE needs opts->surrogate (an lcs_mlp)");
+    if (f->kind != LCS_RECTILINEAR || f->dim != 2 || f->periodic[0] || f->periodic[1])
+        return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: the surrogate runs on 2D non-periodic rectilinear fields");
+    if (o->njobs > 1) return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: the surrogate integrates one job per call");
+    const double tau = m->d.tau, adt = fabs(o->dt), T = o->T;
+    const double rk = T / tau, rs = tau / adt;
+    const long long K = (long long)floor(rk + 0.5), S = (long long)floor(rs + 0.5);
+    if (!(T > 0.0) || !(adt > 0.0) || K < 1 || fabs(rk - K) > 1e-9 * rk || S < 1 || fabs(rs - S) > 1e-9 * rs ||
+        K * S > (1LL << 30))
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: the surrogate needs T = K tau (K >= 1) and tau = S dt, T > 0");
+    if (!isfinite(o->t0)) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: t0 must be finite");
+    const long long N = s->N;
+    const long long ngrp = (N + 31) / 32;
+    JobTable *J = new (std::nothrow) JobTable();
+    if (!J) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
+    J->njobs = 1;
+    J->nsteps_max = (int)(K * S);
+    J->t0[0] = o->t0;
+    J->T[0] = T;
+    J->h[0] = adt;
+    J->nsteps[0] = (int)(K * S);
+    J->order[0] = 0;
+    fm->T[0] = T;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t sched_b = al(sizeof(SchedEntry) * 3 * (size_t)K * S);
+    const size_t need = sched_b + al(sizeof(float) * 3 * N) + al(ngrp) + 8 * al(64);
+    LCS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    lcs_status st = lcs_scratch_reserve(ctx, need);
+    if (st != LCS_OK) {
+        delete J;
+        return st;
+    }
+    if (!fm->d_steps) LCS_CUDA_TRY(ctx, cudaMalloc(&fm->d_steps, sizeof(int) * (size_t)fm->N * fm->njobs));
+    char *p = (char *)ctx->d_scratch;
+    SchedEntry *sched = (SchedEntry *)p;
+    p += sched_b;
+    float *xp = (float *)p;
+    p += al(sizeof(float) * 3 * N);
+    unsigned char *flag = (unsigned char *)p;
+    p += al(ngrp);
+    JobDev D;
+    D.nsteps = (int *)p;
+    p += al(64);
+    D.h = (float *)p;
+    p += al(64);
+    D.t0 = (float *)p;
+    p += al(64);
+    D.tend = (float *)p;
+    p += al(64);
+    D.order = nullptr;
+    D.t0d = nullptr;
+    D.Td = nullptr;
+    D.absT = fm->d_absT;
+    cudaError_t e = launch_rk4_schedule(f->d_times, f->nframes, f->time_periodic, f->period, *J, D, sched, ctx->stream);
+    delete J;
+    // tracer state: the flow map starts at the seeds, OK, exit time t0 + T, no fallbacks
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(fm->d_xyz, s->d_xyz, sizeof(float) * 2 * N, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fm->d_status, LCS_TRACER_OK, N, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fm->d_steps, 0, sizeof(int) * N, ctx->stream);
+    if (e == cudaSuccess) e = launch_fill_f32(fm->d_texit, N, (float)(o->t0 + T), ctx->stream);
+    const float h32 = (float)adt, t032 = (float)o->t0;
+    for (long long k = 0; k < K && e == cudaSuccess; ++k) {
+        MlpStepArgs A;
+        A.tiles = m->d_tiles;
+        A.x = fm->d_xyz;
+        A.stride = N;
+        A.n = N;
+        A.t = nullptr;
+        A.t_uniform = (float)(o->t0 + (double)k * tau);
+        A.cx = (float)m->d.center[0];
+        A.cy = (float)m->d.center[1];
+        A.kx = (float)m->d.kx;
+        A.ky = (float)m->d.ky;
+        A.omega = (float)m->d.omega;
+        A.out_scale = (float)m->d.out_scale;
+        A.mode = 1;
+        A.out0 = xp;
+        A.out1 = xp + N;
+        A.out2 = xp + 2 * N;
+        A.errword = ctx->d_errword;
+        lcs_tm_begin(ctx, 0, ctx->stream);
+        e = launch_mlp_step(A, ctx->num_sms, ctx->stream);
+        lcs_tm_end(ctx, 0, ctx->stream);
+        if (e != cudaSuccess) break;
+        SurGateArgs G;
+        G.n = N;
+        G.step = (int)k;
+        G.S = (int)S;
+        G.h = h32;
+        G.t0 = t032;
+        G.tol = (float)o->gate_tol;
+        G.log_tol = o->gate_tol > 0 ? (float)log10(o->gate_tol) : -INFINITY;
+        G.rho = xp + 2 * N;
+        G.xp = xp;
+        G.xyz = fm->d_xyz;
+        G.status = fm->d_status;
+        G.texit = fm->d_texit;
+        G.counts = fm->d_steps;
+        G.flag = flag;
+        G.sched = sched;
+        G.errword = ctx->d_errword;
+        lcs_tm_begin(ctx, 1, ctx->stream);
+        e = launch_sur_gate(G, f, ctx->stream);
+        lcs_tm_end(ctx, 1, ctx->stream);
+    }
+    if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_advect (surrogate): %s", cudaGetErrorString(e));
     return LCS_OK;
 }

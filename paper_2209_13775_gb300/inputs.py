@@ -208,3 +208,29 @@ def random_points(n, lo, hi, seed=SEED):
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     return (lo[:, None] + (hi - lo)[:, None] * rng.random((len(lo), n))).astype(np.float32)
+
+
+# ------------------------------------------------------------ surrogate network
+
+MLP_SHAPES = [(128, 7), (128,), (128, 128), (128,), (128, 128), (128,), (128, 128), (128,), (3, 128), (3,)]
+
+
+def mlp_init(seed=SEED, gain=1.0):
+    """Packed FP32 parameters of the 7-128x4-3 network (W0 b0 ... W4 b4, row-major W[out][in]):
+    weights uniform in +-gain*sqrt(6/fan_in) (He-uniform for SiLU), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in MLP_SHAPES:
+        if len(s) == 2:
+            lim = gain * np.sqrt(6.0 / s[1])
+            parts.append(rng.uniform(-lim, lim, s))
+        else:
+            parts.append(np.zeros(s))
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def surrogate_samples(n, t_period=10.0, lo=(0.0, 0.0), hi=(2.0, 1.0), seed=SEED):
+    """Training points (x0, y0, t0) [3][n] FP32, uniform in the box and over one period."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.uniform(lo[0], hi[0], n), rng.uniform(lo[1], hi[1], n),
+                     rng.uniform(0.0, t_period, n)]).astype(np.float32)

@@ -28,9 +28,11 @@ EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs
            "lcs_flowmap_steps",
            "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_timing_enable",
            "lcs_timing_read",
-           "lcs_advect_rk4_noalloc", "lcs_gemm_bf16"]
+           "lcs_advect_rk4_noalloc", "lcs_gemm_bf16", "lcs_mlp_create", "lcs_mlp_set_params",
+           "lcs_mlp_get_params", "lcs_mlp_free", "lcs_mlp_forward"]
 PHASE_ADVECT, PHASE_REBUNDLE, PHASE_SLICES, PHASE_CG = 0, 1, 2, 3
 NOALLOC_MAX_STEPS = 43680
+MLP_NPARAMS = 50947
 
 
 class LcsError(RuntimeError):
@@ -60,7 +62,8 @@ class AdvectOpts(ctypes.Structure):
                 ("dt", ctypes.c_double), ("rtol", ctypes.c_double), ("atol", ctypes.c_double),
                 ("h0", ctypes.c_double), ("max_steps", ctypes.c_longlong), ("walk_limit", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("variant", ctypes.c_int), ("surrogate", ctypes.c_void_p),
-                ("episode_steps", ctypes.c_int), ("tracers_per_thread", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("episode_steps", ctypes.c_int), ("tracers_per_thread", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("gate_tol", ctypes.c_double)]
 
 
 _lib = None
@@ -93,6 +96,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_autotune": ([P, P, P, P, ctypes.c_char_p], S),
         "lcs_flowmap_steps": ([P, P, I, P, I], S),
         "lcs_gemm_bf16": ([P, LL, I, LL, P, LL, P, LL, P, LL, I, I], S),
+        "lcs_mlp_create": ([P, P, P, I, P], S), "lcs_mlp_set_params": ([P, P, P, I], S),
+        "lcs_mlp_get_params": ([P, P, P, I], S), "lcs_mlp_free": ([P], None),
+        "lcs_mlp_forward": ([P, P, LL, P, P, I], S),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -242,7 +248,7 @@ def lcs_free_seeds(seeds):
 
 def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol=1e-6, atol=1e-6, h0=0.01,
                 max_steps=0, walk_limit=0, block_threads=0, variant=0, episode_steps=0, tracers_per_thread=0,
-                use_graph=False):
+                use_graph=False, surrogate=None, gate_tol=1e-3):
     o = AdvectOpts()
     o.method, o.t0, o.T, o.dt = int(method), float(t0), float(T), float(dt)
     o.rtol, o.atol, o.h0, o.max_steps = float(rtol), float(atol), float(h0), int(max_steps)
@@ -250,6 +256,8 @@ def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol
     o.episode_steps = int(episode_steps)
     o.tracers_per_thread = int(tracers_per_thread)
     o.use_graph = int(bool(use_graph))
+    o.surrogate = surrogate
+    o.gate_tol = float(gate_tol)
     if job_t0 is not None:
         a = np.ascontiguousarray(job_t0, dtype=np.float64)
         b = np.ascontiguousarray(job_T, dtype=np.float64)
@@ -350,3 +358,48 @@ def lcs_gemm_bf16(ctx, A, B, C, splits=1, accumulate=False):
     _check(ctx, load().lcs_gemm_bf16(ctx, M, N, K, ctypes.c_void_p(A.data_ptr()), A.stride(0),
                                      ctypes.c_void_p(B.data_ptr()), B.stride(0), ctypes.c_void_p(C.data_ptr()),
                                      C.stride(0), int(splits), int(bool(accumulate))))
+
+
+# ------------------------------------------------------------ learned surrogate
+
+class MlpDesc(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_double * 2), ("kx", ctypes.c_double), ("ky", ctypes.c_double),
+                ("omega", ctypes.c_double), ("tau", ctypes.c_double), ("out_scale", ctypes.c_double)]
+
+
+def mlp_desc(center, kx, ky, omega, tau, out_scale):
+    d = MlpDesc()
+    d.center[0], d.center[1] = float(center[0]), float(center[1])
+    d.kx, d.ky, d.omega, d.tau, d.out_scale = float(kx), float(ky), float(omega), float(tau), float(out_scale)
+    return d
+
+
+def lcs_mlp_create(ctx, desc, params):
+    p, dev = _ptr(params)
+    out = ctypes.c_void_p()
+    _check(ctx, load().lcs_mlp_create(ctx, ctypes.byref(desc), ctypes.c_void_p(p), dev, ctypes.byref(out)))
+    return out.value
+
+
+def lcs_mlp_set_params(ctx, mlp, params):
+    p, dev = _ptr(params)
+    _check(ctx, load().lcs_mlp_set_params(ctx, mlp, ctypes.c_void_p(p), dev))
+
+
+def lcs_mlp_get_params(ctx, mlp, params):
+    p, dev = _ptr(params)
+    _check(ctx, load().lcs_mlp_get_params(ctx, mlp, ctypes.c_void_p(p), dev))
+
+
+def lcs_mlp_free(mlp):
+    load().lcs_mlp_free(mlp)
+
+
+def lcs_mlp_forward(ctx, mlp, xyt, out):
+    """out [3][n] = network outputs at xyt [3][n] (x, y, t rows)."""
+    p, dev = _ptr(xyt)
+    q, dev2 = _ptr(out)
+    if dev != dev2:
+        raise ValueError("xyt and out must both be host or both be device buffers")
+    n = xyt.shape[1]
+    _check(ctx, load().lcs_mlp_forward(ctx, mlp, n, ctypes.c_void_p(p), ctypes.c_void_p(q), dev))

@@ -42,3 +42,139 @@ def test_gemm_bf16_matches_fp32_product(ctx, M, N, K, splits):
     lcs.lcs_gemm_bf16(ctx, Ad, Bd, C, splits=1, accumulate=True)
     lcs.lcs_synchronize(ctx)
     assert ((C.cpu().double() - 2 * want).abs() <= 2 * bound).all()
+
+
+# ------------------------------------------------------------------ the network
+
+import math
+
+import oracle
+from oracle import mlp as omlp
+from paper_2209_13775_gb300 import inputs
+
+GYRE_FEAT = dict(center=(1.0, 0.5), kx=math.pi, ky=math.pi, omega=2 * math.pi / 10)
+
+
+def bf16_params(p):
+    """The parameters the kernels compute with: BF16 weights, FP32 biases (as FP64)."""
+    W = omlp.unpack(p.astype(np.float64))
+    out = []
+    for i, w in enumerate(W):
+        if i % 2 == 0:
+            out.append(torch.from_numpy(np.asarray(w, dtype=np.float32)).to(torch.bfloat16).double().numpy())
+        else:
+            out.append(w)
+    return omlp.pack(out)
+
+
+def mlp_handle(ctx, params, tau=0.5, out_scale=0.1):
+    d = lcs.mlp_desc(GYRE_FEAT["center"], GYRE_FEAT["kx"], GYRE_FEAT["ky"], GYRE_FEAT["omega"], tau, out_scale)
+    return lcs.lcs_mlp_create(ctx, d, params)
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def cosine(a, b):
+    return float((a * b).sum() / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+@pytest.mark.parametrize("n,gain", [(1000, 1.0), (128, 2.0), (4099, 0.5)])
+def test_forward_matches_oracle(ctx, n, gain):
+    p = inputs.mlp_init(seed=50 + n, gain=gain)
+    p[omlp.NPARAMS - 3:] = [0.1, -0.2, -3.0]                       # nonzero output biases
+    m = mlp_handle(ctx, p)
+    xyt = inputs.surrogate_samples(n, seed=51 + n)
+    out = np.empty((3, n), dtype=np.float32)
+    lcs.lcs_mlp_forward(ctx, m, xyt, out)
+    q = np.empty(omlp.NPARAMS, dtype=np.float32)
+    lcs.lcs_mlp_get_params(ctx, m, q)
+    np.testing.assert_array_equal(q, p)
+    lcs.lcs_mlp_free(m)
+    phi = omlp.features(xyt[0].astype(np.float64), xyt[1].astype(np.float64), xyt[2].astype(np.float64),
+                        **GYRE_FEAT)
+    want, _ = omlp.forward(bf16_params(p), phi)
+    for c in range(3):
+        assert rel_err(out[c], want[c]) <= 2e-2, (c, rel_err(out[c], want[c]))
+        assert cosine(out[c], want[c]) >= 0.999
+    assert np.isfinite(out).all()
+
+
+@pytest.fixture(scope="module")
+def gyre():
+    return inputs.double_gyre()
+
+
+def gyre_field(ctx, g):
+    return lcs.lcs_load_field(ctx, lcs.field_desc(2, g.n, g.origin, g.spacing, g.periodic, g.times,
+                                                  g.time_periodic, g.period), g.frames)
+
+
+def run_surrogate(ctx, g, m, n, T, tol, dt=0.05, t0=0.0):
+    field = gyre_field(ctx, g)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, (0.0, 0.0), (2.0, 1.0)))
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    method = lcs.RK4 if m is None else lcs.SURROGATE
+    lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(method, t0=t0, T=T, dt=dt, surrogate=m, gate_tol=tol), fm)
+    x = np.empty((2, N), dtype=np.float32)
+    st = np.empty(N, dtype=np.uint8)
+    cnt = np.empty(N, dtype=np.int32)
+    lcs.lcs_flowmap_get(ctx, fm, 0, x, st)
+    if m is not None:
+        lcs.lcs_flowmap_steps(ctx, fm, 0, cnt)
+    x0 = np.empty((2, N), dtype=np.float32)
+    lcs.lcs_seeds_get(ctx, seeds, x0)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return x0, x, st, cnt
+
+
+def test_gated_advection_limits_and_groups(ctx, gyre):
+    p = inputs.mlp_init(seed=60, gain=0.5)
+    p[-1] = -10.0                          # rho far below any threshold: only the audit decides
+    m = mlp_handle(ctx, p)
+    n, K = (41, 23), 4                     # 943 seeds: 29 full groups and a ragged one
+    T = 0.5 * K
+    x0, xr, _, _ = run_surrogate(ctx, gyre, None, n, T, 0.0)
+    # gate 0: every group integrates every sub-interval with the fixed-step arithmetic
+    _, x, st, cnt = run_surrogate(ctx, gyre, m, n, T, 0.0)
+    np.testing.assert_array_equal(x, xr)
+    assert (cnt == K).all()
+    # gate inf: the network composed K times, against the FP64 oracle on the same BF16 weights
+    _, xi, _, cnt = run_surrogate(ctx, gyre, m, n, T, math.inf)
+    assert (cnt == 0).all()
+    y = x0.astype(np.float64)
+    pb = bf16_params(p)
+    for k in range(K):
+        o, _ = omlp.forward(pb, omlp.features(y[0], y[1], 0.5 * k, **GYRE_FEAT))
+        y = y + 0.1 * o[:2]
+    assert rel_err(xi - x0, y - x0) <= 3e-2, rel_err(xi - x0, y - x0)
+    # an audit threshold in between: each group's result is either the network's or RK4's
+    # trajectory, step by step; groups never audited out equal the gate-inf run, groups always
+    # audited out equal plain RK4, and all lanes of a group share a count
+    # threshold: the median audit residual of the first sub-interval (oracle, FP64), so that
+    # about half of the groups fail there
+    N = x0.shape[1]
+    F = oracle.RectField(gyre.frames, gyre.times, gyre.origin, gyre.spacing, gyre.periodic, gyre.time_periodic,
+                         gyre.period)
+    o0, _ = omlp.forward(pb, omlp.features(x0[0].astype(np.float64), x0[1].astype(np.float64), 0.0, **GYRE_FEAT))
+    res = []
+    for w in range((N + 31) // 32):
+        mm = min(32, N - 32 * w)
+        a = 32 * w + omlp.audit_lane(0, w, mm)
+        ra, _, _ = oracle.rk4(F, x0[:, a:a + 1].astype(np.float64), 0.0, 0.5, 0.05)
+        res.append(np.hypot(*(x0[:, a] + 0.1 * o0[:2, a] - ra[:, 0])))
+    tol = float(np.median(res))
+    _, xm, _, cnt = run_surrogate(ctx, gyre, m, n, T, tol)
+    for g0 in range(0, N, 32):
+        c = cnt[g0:g0 + 32]
+        assert (c == c[0]).all()
+        if c[0] == 0:
+            np.testing.assert_array_equal(xm[:, g0:g0 + 32], xi[:, g0:g0 + 32])
+        if c[0] == K:
+            np.testing.assert_array_equal(xm[:, g0:g0 + 32], xr[:, g0:g0 + 32])
+    assert len(np.unique(cnt)) >= 2
+    lcs.lcs_mlp_free(m)
