@@ -287,6 +287,40 @@ void lcs_mlp_free(lcs_mlp *mlp);
 lcs_status lcs_mlp_forward(lcs_ctx *ctx, const lcs_mlp *mlp, long long n, const float *xyt, float *out,
                            int on_device);
 
+/* Mean loss over n samples (n a positive multiple of 128) and its gradient
+ * [LCS_MLP_NPARAMS] (grads may be NULL; loss: host pointer or NULL):
+ *   loss = mean of (o0 - dx/s)^2 + (o1 - dy/s)^2
+ *          + rho_weight (o2 - log10(|s (o0, o1) - d| + 1e-7))^2,
+ * s = out_scale, d = disp [2][n] the integrator's displacement over tau from
+ * the points xyt [3][n]; the log10 target is a constant of the gradient.
+ * The gradient also stays in the network for lcs_mlp_adam.                 */
+lcs_status lcs_mlp_loss_grad(lcs_ctx *ctx, lcs_mlp *mlp, long long n, const float *xyt, const float *disp,
+                             double rho_weight, float *grads, double *loss, int on_device);
+
+/* One Adam step (Kingma & Ba) on the FP32 parameters with gradient grads
+ * (NULL: the last lcs_mlp_loss_grad), learning rate lr, moments beta1, beta2,
+ * and eps; bias corrections use the network's own step count.              */
+lcs_status lcs_mlp_adam(lcs_ctx *ctx, lcs_mlp *mlp, const float *grads, int on_device, double lr, double beta1,
+                        double beta2, double eps);
+
+typedef struct {
+    long long batch;            /* samples per step, a positive multiple of 128     */
+    int epochs;                 /* passes over the samples                         */
+    double lr, lr_min;          /* cosine decay from lr to lr_min over all steps   */
+    double beta1, beta2, eps;   /* Adam                                            */
+    double rho_weight;          /* weight of the error head's loss term            */
+    double dt;                  /* RK4 step of the targets (tau a multiple of it)  */
+} lcs_train_desc;
+
+/* Train on the field: targets are the RK4 (step dt) displacements over tau from
+ * every sample (x0, y0, t0) of samples [3][ns], then epochs of Adam steps over
+ * consecutive batches (ns / batch of them; the samples are taken in the given
+ * order, so pass them shuffled).  loss_per_epoch (host, [epochs], or NULL):
+ * mean training loss of each epoch.  2D rectilinear fields.
+ * Errors: LCS_EINVAL, LCS_EUNSUPPORTED, LCS_ECUDA.                          */
+lcs_status lcs_surrogate_train(lcs_ctx *ctx, const lcs_field *field, lcs_mlp *mlp, const lcs_train_desc *desc,
+                               long long ns, const float *samples, int on_device, double *loss_per_epoch);
+
 /* ------------------------------------------------ tensor-core GEMM (BF16) */
 
 /* C[M x N] = A[M x K] * B[N x K]^T (accumulate = 1: C += ...) on the tcgen05

@@ -334,3 +334,123 @@ lcs_status advect_surrogate(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s
     if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_advect (surrogate): %s", cudaGetErrorString(e));
     return LCS_OK;
 }
+
+// ------------------------------------------------------------------ training
+
+extern "C" lcs_status lcs_mlp_loss_grad(lcs_ctx *ctx, lcs_mlp *m, long long n, const float *xyt, const float *disp,
+                                        double rho_weight, float *grads, double *loss, int on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!m || !xyt || !disp) return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_loss_grad: null argument");
+    if (n <= 0 || n % 128) return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_loss_grad: n must be a positive multiple of 128");
+    if (!(rho_weight >= 0.0) || !isfinite(rho_weight))
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_loss_grad: rho_weight must be finite and >= 0");
+    LCS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const float *dx = xyt, *dd = disp;
+    float *tmp = nullptr;
+    double *dl = nullptr;
+    if (!on_device) {
+        LCS_CUDA_TRY(ctx, cudaMallocAsync((void **)&tmp, sizeof(float) * 5 * n, ctx->stream));
+        LCS_CUDA_TRY(ctx, cudaMemcpyAsync(tmp, xyt, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        LCS_CUDA_TRY(ctx, cudaMemcpyAsync(tmp + 3 * n, disp, sizeof(float) * 2 * n, cudaMemcpyHostToDevice, ctx->stream));
+        dx = tmp;
+        dd = tmp + 3 * n;
+    }
+    LCS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dl, sizeof(double), ctx->stream));
+    cudaError_t e = mlp_loss_grad(m, dx, n, dd, n, n, (float)rho_weight, ctx->num_sms, ctx->d_errword, dl, ctx->stream);
+    double lsum = 0.0;
+    if (e == cudaSuccess && grads)
+        e = cudaMemcpyAsync(grads, m->d_grad, sizeof(float) * MLP_NPARAMS,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(&lsum, dl, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && loss) e = cudaStreamSynchronize(ctx->stream);
+    if (tmp) cudaFreeAsync(tmp, ctx->stream);
+    cudaFreeAsync(dl, ctx->stream);
+    if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_mlp_loss_grad: %s", cudaGetErrorString(e));
+    if (loss) *loss = lsum / (double)n;
+    if (!on_device) return lcs_synchronize(ctx);
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_mlp_adam(lcs_ctx *ctx, lcs_mlp *m, const float *grads, int on_device, double lr, double beta1,
+                                   double beta2, double eps)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!m) return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_adam: null network");
+    if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_mlp_adam: lr >= 0, 0 <= beta < 1, eps > 0");
+    LCS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const float *g = m->d_grad;
+    float *tmp = nullptr;
+    if (grads && !on_device) {
+        LCS_CUDA_TRY(ctx, cudaMallocAsync((void **)&tmp, sizeof(float) * MLP_NPARAMS, ctx->stream));
+        LCS_CUDA_TRY(ctx, cudaMemcpyAsync(tmp, grads, sizeof(float) * MLP_NPARAMS, cudaMemcpyHostToDevice, ctx->stream));
+        g = tmp;
+    } else if (grads) {
+        g = grads;
+    }
+    cudaError_t e = mlp_adam(m, g, lr, beta1, beta2, eps, ctx->stream);
+    if (tmp) cudaFreeAsync(tmp, ctx->stream);
+    if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_mlp_adam: %s", cudaGetErrorString(e));
+    if (grads && !on_device) return lcs_synchronize(ctx);
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_surrogate_train(lcs_ctx *ctx, const lcs_field *f, lcs_mlp *m, const lcs_train_desc *d,
+                                          long long ns, const float *samples, int on_device, double *loss_per_epoch)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!f || !m || !d || !samples) return lcs_fail(ctx, LCS_EINVAL, "lcs_surrogate_train: null argument");
+    if (f->kind != LCS_RECTILINEAR || f->dim != 2)
+        return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_surrogate_train: 2D rectilinear fields");
+    const long long B = d->batch;
+    if (B <= 0 || B % 128 || ns < B || d->epochs < 1)
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_surrogate_train: batch a positive multiple of 128, ns >= batch, epochs >= 1");
+    const double rs = m->d.tau / d->dt;
+    const long long S = (long long)floor(rs + 0.5);
+    if (!(d->dt > 0.0) || S < 1 || fabs(rs - S) > 1e-9 * rs || S > (1 << 20))
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_surrogate_train: tau must be a multiple of dt > 0");
+    if (!(d->lr >= 0.0) || !(d->lr_min >= 0.0) || !(d->beta1 >= 0.0 && d->beta1 < 1.0) ||
+        !(d->beta2 >= 0.0 && d->beta2 < 1.0) || !(d->eps > 0.0) || !(d->rho_weight >= 0.0))
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_surrogate_train: optimiser settings");
+    LCS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const long long nb = ns / B, total = nb * d->epochs;
+    float *xs = nullptr, *disp = nullptr;
+    double *losses = nullptr;
+    LCS_CUDA_TRY(ctx, cudaMallocAsync((void **)&disp, sizeof(float) * 2 * ns, ctx->stream));
+    LCS_CUDA_TRY(ctx, cudaMallocAsync((void **)&losses, sizeof(double) * total, ctx->stream));
+    const float *xyt = samples;
+    if (!on_device) {
+        LCS_CUDA_TRY(ctx, cudaMallocAsync((void **)&xs, sizeof(float) * 3 * ns, ctx->stream));
+        LCS_CUDA_TRY(ctx, cudaMemcpyAsync(xs, samples, sizeof(float) * 3 * ns, cudaMemcpyHostToDevice, ctx->stream));
+        xyt = xs;
+    }
+    // integrator targets: RK4 displacement over tau from every sample
+    cudaError_t e = mlp_targets(f, xyt, ns, (int)S, d->dt, disp, ctx->stream);
+    if (e == cudaSuccess) e = mlp_reserve(m, B, ctx->stream);
+    for (long long it = 0; it < total && e == cudaSuccess; ++it) {
+        const long long b = it % nb;
+        e = mlp_loss_grad(m, xyt + b * B, ns, disp + b * B, ns, B, (float)d->rho_weight, ctx->num_sms, ctx->d_errword,
+                          losses + it, ctx->stream);
+        if (e != cudaSuccess) break;
+        const double lr = d->lr_min + 0.5 * (d->lr - d->lr_min) * (1.0 + cos(M_PI * (double)it / (double)total));
+        e = mlp_adam(m, m->d_grad, lr, d->beta1, d->beta2, d->eps, ctx->stream);
+    }
+    std::vector<double> h;
+    if (e == cudaSuccess && loss_per_epoch) {
+        h.resize((size_t)total);
+        e = cudaMemcpyAsync(h.data(), losses, sizeof(double) * total, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFreeAsync(disp, ctx->stream);
+    cudaFreeAsync(losses, ctx->stream);
+    if (xs) cudaFreeAsync(xs, ctx->stream);
+    if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_surrogate_train: %s", cudaGetErrorString(e));
+    if (loss_per_epoch)
+        for (int ep = 0; ep < d->epochs; ++ep) {
+            double s = 0.0;
+            for (long long b = 0; b < nb; ++b) s += h[(size_t)(ep * nb + b)];
+            loss_per_epoch[ep] = s / (double)(nb * B);
+        }
+    return lcs_synchronize(ctx);
+}

@@ -90,3 +90,11 @@ cudaError_t launch_sur_gate(const SurGateArgs &G, const lcs_field *f, cudaStream
 cudaError_t launch_mlp_refresh(lcs_mlp *m, cudaStream_t s);
 lcs_status advect_surrogate(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
                             lcs_flowmap *fm);
+
+// trainer (mlp_train.cu)
+cudaError_t mlp_reserve(lcs_mlp *m, long long B, cudaStream_t s);
+cudaError_t mlp_loss_grad(lcs_mlp *m, const float *xyt, long long xstride, const float *disp, long long dstride,
+                          long long B, float rho_weight, int num_sms, unsigned *errword, double *d_loss, cudaStream_t s);
+cudaError_t mlp_adam(lcs_mlp *m, const float *grad, double lr, double b1, double b2, double eps, cudaStream_t s);
+cudaError_t mlp_targets(const lcs_field *f, const float *xyt, long long n, int S, double dt, float *disp,
+                        cudaStream_t s);

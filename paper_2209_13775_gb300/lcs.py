@@ -29,7 +29,8 @@ EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs
            "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_timing_enable",
            "lcs_timing_read",
            "lcs_advect_rk4_noalloc", "lcs_gemm_bf16", "lcs_mlp_create", "lcs_mlp_set_params",
-           "lcs_mlp_get_params", "lcs_mlp_free", "lcs_mlp_forward"]
+           "lcs_mlp_get_params", "lcs_mlp_free", "lcs_mlp_forward", "lcs_mlp_loss_grad", "lcs_mlp_adam",
+           "lcs_surrogate_train"]
 PHASE_ADVECT, PHASE_REBUNDLE, PHASE_SLICES, PHASE_CG = 0, 1, 2, 3
 NOALLOC_MAX_STEPS = 43680
 MLP_NPARAMS = 50947
@@ -99,6 +100,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_mlp_create": ([P, P, P, I, P], S), "lcs_mlp_set_params": ([P, P, P, I], S),
         "lcs_mlp_get_params": ([P, P, P, I], S), "lcs_mlp_free": ([P], None),
         "lcs_mlp_forward": ([P, P, LL, P, P, I], S),
+        "lcs_mlp_loss_grad": ([P, P, LL, P, P, ctypes.c_double, P, P, I], S),
+        "lcs_mlp_adam": ([P, P, P, I, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double], S),
+        "lcs_surrogate_train": ([P, P, P, P, LL, P, I, P], S),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -403,3 +407,45 @@ def lcs_mlp_forward(ctx, mlp, xyt, out):
         raise ValueError("xyt and out must both be host or both be device buffers")
     n = xyt.shape[1]
     _check(ctx, load().lcs_mlp_forward(ctx, mlp, n, ctypes.c_void_p(p), ctypes.c_void_p(q), dev))
+
+
+def lcs_mlp_loss_grad(ctx, mlp, xyt, disp, rho_weight, grads=None):
+    """Mean loss (returned) and its gradient (into grads, if given) over the points xyt [3][n]."""
+    p, dev = _ptr(xyt)
+    q, dev2 = _ptr(disp)
+    g, dev3 = _ptr(grads)
+    if dev != dev2 or (grads is not None and dev3 != dev):
+        raise ValueError("xyt, disp and grads must all be host or all be device buffers")
+    loss = ctypes.c_double(0.0)
+    _check(ctx, load().lcs_mlp_loss_grad(ctx, mlp, xyt.shape[1], ctypes.c_void_p(p), ctypes.c_void_p(q),
+                                         float(rho_weight), ctypes.c_void_p(g), ctypes.byref(loss), dev))
+    return loss.value
+
+
+def lcs_mlp_adam(ctx, mlp, grads=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    g, dev = _ptr(grads)
+    _check(ctx, load().lcs_mlp_adam(ctx, mlp, ctypes.c_void_p(g), dev, float(lr), float(beta1), float(beta2),
+                                    float(eps)))
+
+
+class TrainDesc(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_longlong), ("epochs", ctypes.c_int), ("lr", ctypes.c_double),
+                ("lr_min", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("rho_weight", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+def train_desc(batch=65536, epochs=10, lr=1e-3, lr_min=1e-5, beta1=0.9, beta2=0.999, eps=1e-8, rho_weight=0.01,
+               dt=0.05):
+    d = TrainDesc()
+    d.batch, d.epochs, d.lr, d.lr_min = int(batch), int(epochs), float(lr), float(lr_min)
+    d.beta1, d.beta2, d.eps, d.rho_weight, d.dt = float(beta1), float(beta2), float(eps), float(rho_weight), float(dt)
+    return d
+
+
+def lcs_surrogate_train(ctx, field, mlp, desc, samples):
+    """Train on samples [3][ns] (x0, y0, t0); returns the mean loss of each epoch."""
+    p, dev = _ptr(samples)
+    out = np.empty(desc.epochs, dtype=np.float64)
+    _check(ctx, load().lcs_surrogate_train(ctx, field, mlp, ctypes.byref(desc), samples.shape[1], ctypes.c_void_p(p),
+                                           dev, out.ctypes.data))
+    return out

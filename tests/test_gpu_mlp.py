@@ -178,3 +178,73 @@ def test_gated_advection_limits_and_groups(ctx, gyre):
             np.testing.assert_array_equal(xm[:, g0:g0 + 32], xr[:, g0:g0 + 32])
     assert len(np.unique(cnt)) >= 2
     lcs.lcs_mlp_free(m)
+
+
+# ------------------------------------------------------------------ training
+
+def test_loss_and_gradients_match_oracle(ctx):
+    n = 1024
+    p = inputs.mlp_init(seed=70, gain=1.0)
+    p[-3:] = [0.05, -0.02, -2.0]
+    m = mlp_handle(ctx, p)
+    xyt = inputs.surrogate_samples(n, seed=71)
+    disp = (np.random.default_rng(72).normal(scale=0.05, size=(2, n))).astype(np.float32)
+    g = np.empty(omlp.NPARAMS, dtype=np.float32)
+    loss = lcs.lcs_mlp_loss_grad(ctx, m, xyt, disp, 0.25, g)
+    lcs.lcs_mlp_free(m)
+    phi = omlp.features(xyt[0].astype(np.float64), xyt[1].astype(np.float64), xyt[2].astype(np.float64),
+                        **GYRE_FEAT)
+    pb = bf16_params(p)
+    lo, go = omlp.loss_and_grad(pb, phi, disp.astype(np.float64), 0.1, 0.25)
+    assert abs(loss - lo) <= 1e-2 * abs(lo), (loss, lo)
+    o = 0
+    for i, s in enumerate(omlp.SHAPES):
+        k = int(np.prod(s))
+        a, b = g[o:o + k].astype(np.float64), go[o:o + k]
+        assert rel_err(a, b) <= 2e-2, (i, rel_err(a, b))
+        assert cosine(a, b) >= 0.999, (i, cosine(a, b))
+        o += k
+
+
+def test_adam_matches_oracle(ctx):
+    p = inputs.mlp_init(seed=80)
+    m = mlp_handle(ctx, p)
+    rng = np.random.default_rng(81)
+    mo = np.zeros(omlp.NPARAMS)
+    vo = np.zeros(omlp.NPARAMS)
+    po = p.astype(np.float64)
+    for step in (1, 2, 3):
+        g = (rng.normal(size=omlp.NPARAMS) * 10.0 ** rng.uniform(-4, 0, omlp.NPARAMS)).astype(np.float32)
+        lcs.lcs_mlp_adam(ctx, m, g, lr=1e-3 * step)
+        po, mo, vo = omlp.adam(po, g.astype(np.float64), mo, vo, step, 1e-3 * step)
+    q = np.empty(omlp.NPARAMS, dtype=np.float32)
+    lcs.lcs_mlp_get_params(ctx, m, q)
+    lcs.lcs_mlp_free(m)
+    assert np.abs(q - po).max() <= 1e-6 * np.abs(po).max() + 1e-7
+
+
+def test_training_learns_the_gyre_step(ctx, gyre):
+    # a short training run must cut the displacement error well below the displacement itself, and
+    # the trained network then passes most audits at a loose threshold
+    field = gyre_field(ctx, gyre)
+    m = mlp_handle(ctx, inputs.mlp_init(seed=90))
+    samples = inputs.surrogate_samples(1 << 18, seed=91)
+    hist = lcs.lcs_surrogate_train(ctx, field, m, lcs.train_desc(batch=8192, epochs=6, lr=2e-3, lr_min=1e-4), samples)
+    assert hist[-1] < 0.05 * hist[0], hist
+    # held-out points against the oracle's RK4 over tau = 0.5
+    test = inputs.surrogate_samples(512, seed=92)
+    F = oracle.RectField(gyre.frames, gyre.times, gyre.origin, gyre.spacing, gyre.periodic, gyre.time_periodic,
+                         gyre.period)
+    want = np.empty((2, 512))
+    for t0 in np.unique(test[2]):
+        sel = test[2] == t0
+        xr, _, _ = oracle.rk4(F, test[:2, sel].astype(np.float64), float(t0), 0.5, 0.05)
+        want[:, sel] = xr - test[:2, sel]
+    out = np.empty((3, 512), dtype=np.float32)
+    lcs.lcs_mlp_forward(ctx, m, test, out)
+    err = np.hypot(*(0.1 * out[:2] - want))
+    rel = np.sqrt((err ** 2).mean()) / np.sqrt((np.hypot(*want) ** 2).mean())
+    print("surrogate training: loss per epoch", hist, "held-out relative RMS error", rel)
+    assert rel < 0.1, (rel, hist)
+    lcs.lcs_mlp_free(m)
+    lcs.lcs_free_field(field)
