@@ -58,9 +58,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seeds-side", type=int, default=N_SIDE,
                    help="seed lattice side (default 256; smaller only for profiling captures)")
-    p.add_argument("--config", default="c2", choices=["c2", "c3", "c4"],
+    p.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
                    help="c2: the 3D ABC workload (default, the headline); c3: the batched sliding-window "
-                        "workload; c4: adaptive DP5(4) on the tetrahedral pipe")
+                        "workload; c4: adaptive DP5(4) on the tetrahedral pipe; c5: the learned surrogate")
+    p.add_argument("--train-epochs", type=int, default=4, help="c5: training epochs over the 50M samples")
     p.add_argument("--grid", type=int, default=N_GRID,
                    help="velocity grid side (default 128; smaller only for profiling captures)")
     return p.parse_args()
@@ -339,6 +340,23 @@ def our_arm(args, rank, world, local):
         # slice table + slice fill + advection
         "gpu_launches": int(round(args.steps * 4 + adv_launches * 7)),
     }
+    if args.storage != "f32":
+        # reduced-precision storage against FP32 storage on the same lattice (outside the timed region)
+        d32 = lcs.field_desc(3, g.n, g.origin, g.spacing, g.periodic, g.times, storage=lcs.F32)
+        f32 = lcs.lcs_load_field(ctx, d32, frames_dev)
+        ftle32 = torch.empty(N, dtype=torch.float32, device="cuda")
+        lcs.lcs_advect(ctx, f32, seeds, opts, fm)
+        lcs.lcs_ftle(ctx, fm, 0, ftle32)
+        lcs.lcs_advect(ctx, field, seeds, opts, fm)
+        lcs.lcs_ftle(ctx, fm, 0, ftle)
+        lcs.lcs_synchronize(ctx)
+        lcs.lcs_free_field(f32)
+        a, b = ftle.cpu().double().numpy(), ftle32.cpu().double().numpy()
+        ok = np.isfinite(a) & np.isfinite(b)
+        dd = np.abs(a[ok] - b[ok])
+        line["ftle_err_vs_f32_storage"] = {"median": float(np.median(dd)), "p99.9": float(np.quantile(dd, 0.999)),
+                                           "max": float(dd.max()), "ftle_range": [float(b[ok].min()),
+                                                                                  float(b[ok].max())]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, dts, _, _ = oracle_sample_run(g, 4)                 # calibration: 8^3 tracers
         side = int(max(4, min(96, (10.0 / max(dts / 512.0, 1e-9)) ** (1 / 3) - 4)))
@@ -589,6 +607,158 @@ def c4_arm(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ surrogate arm
+
+C5_WORKLOAD = ("learned surrogate on the double gyre (129x65 FP32, 101 frames, period 10): MLP 7->128x4->3 (SiLU, "
+               "BF16 weights/activations, FP32 accumulate, tcgen05) trained on 50,331,648 RK4 (dt=0.05) "
+               "displacements over tau=0.5 from (x0,y0,t0) ~ U([0,2]x[0,1]x[0,10)); FTLE from K=16 gated "
+               "surrogate steps (T=8, t0=0) on a 16384x8192 seed lattice (2^27 seeds), audit threshold 1e-3 with "
+               "RK4 fallback; FTLE error against plain RK4 on the same lattice")
+C5_N = (16384, 8192)
+C5_TAU, C5_K, C5_DT, C5_TOL = 0.5, 16, 0.05, 1e-3
+C5_FEAT = dict(center=(1.0, 0.5), kx=math.pi, ky=math.pi, omega=2 * math.pi / 10)
+C5_SAMPLES, C5_BATCH = 768 * 65536, 65536
+# algorithmic work of one network evaluation: 2 (7*128 + 3*128*128 + 128*3) FLOP
+C5_FLOP_PER_EVAL = 2 * (7 * 128 + 3 * 128 * 128 + 128 * 3)
+
+
+def c5_oracle_block(gyre, params, side, threads=0):
+    """Oracle gated surrogate (FP64 network on the trained parameters) + FD/CG/FTLE on a side x side block
+    of the C5 lattice with a 2-seed halo; returns (interior seeds, seconds, threads, integrated)."""
+    import oracle
+    from oracle import mlp as omlp
+
+    oracle.build()
+    nth = oracle.set_threads(threads)
+    h = [2.0 / (C5_N[0] - 1), 1.0 / (C5_N[1] - 1)]
+    c0 = [C5_N[0] // 3, C5_N[1] // 3]
+    m = side + 4
+    xs = (0.0 + (c0[0] - 2 + np.arange(m)) * h[0]).astype(np.float32)
+    ys = (0.0 + (c0[1] - 2 + np.arange(m)) * h[1]).astype(np.float32)
+    Y, X = np.meshgrid(ys, xs, indexing="ij")
+    x0 = np.stack([X.ravel(), Y.ravel()]).astype(np.float64)
+    F = oracle.RectField(gyre.frames, gyre.times, gyre.origin, gyre.spacing, gyre.periodic, gyre.time_periodic,
+                         gyre.period)
+    t = time.perf_counter()
+    xT, _, _ = omlp.surrogate_advect(params.astype(np.float64), F, x0, 0.0, C5_K, C5_TAU, C5_DT, C5_TOL,
+                                     **C5_FEAT, out_scale=0.1)
+    st = np.zeros(x0.shape[1], dtype=np.uint8)
+    G = oracle.flowmap_gradient(2, (m, m), h, (0, 0), (0, 0), xT, st)
+    lam, sig = oracle.ftle(oracle.cauchy_green(G), 2, C5_K * C5_TAU)
+    return side * side, time.perf_counter() - t, nth, x0.shape[1]
+
+
+def c5_arm(args, rank, world, local):
+    import torch
+
+    from paper_2209_13775_gb300 import inputs, lcs
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = lcs.lcs_create(local, stream)
+    g = inputs.double_gyre()
+    field = lcs.lcs_load_field(ctx, lcs.field_desc(2, g.n, g.origin, g.spacing, g.periodic, g.times,
+                                                   g.time_periodic, g.period), g.frames)
+    desc = lcs.mlp_desc(C5_FEAT["center"], C5_FEAT["kx"], C5_FEAT["ky"], C5_FEAT["omega"], C5_TAU, 0.1)
+    mlp = lcs.lcs_mlp_create(ctx, desc, inputs.mlp_init())
+    samples = torch.from_numpy(inputs.surrogate_samples(C5_SAMPLES)).cuda()
+    torch.cuda.synchronize()
+    t_train = time.perf_counter()
+    hist = lcs.lcs_surrogate_train(ctx, field, mlp, lcs.train_desc(batch=C5_BATCH, epochs=args.train_epochs,
+                                                                   lr=2e-3, lr_min=1e-5, rho_weight=0.01,
+                                                                   dt=C5_DT), samples)
+    t_train = time.perf_counter() - t_train
+    del samples
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, C5_N, (0.0, 0.0), (2.0, 1.0)))
+    N = lcs.lcs_seeds_count(seeds)
+    T = C5_K * C5_TAU
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    sur = lcs.advect_opts(lcs.SURROGATE, t0=0.0, T=T, dt=C5_DT, surrogate=mlp, gate_tol=C5_TOL)
+    plain = lcs.advect_opts(lcs.RK4, t0=0.0, T=T, dt=C5_DT)
+    ftle = torch.empty(N, dtype=torch.float32, device="cuda")
+    ftle_p = torch.empty(N, dtype=torch.float32, device="cuda")
+
+    def step(opts, out):
+        lcs.lcs_advect(ctx, field, seeds, opts, fm)
+        lcs.lcs_ftle(ctx, fm, 0, out)
+
+    def timed(opts, out, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(k):
+            step(opts, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / k
+
+    for _ in range(args.warmup):
+        step(sur, ftle)
+    step(plain, ftle_p)
+    lcs.lcs_synchronize(ctx)
+    for ph in range(4):
+        lcs.lcs_timing_read(ctx, ph)
+    lcs.lcs_timing_enable(ctx, True)
+    with ClockSampler(local) as clk:
+        el = timed(sur, ftle, args.steps)
+    mlp_ms, mlp_n = lcs.lcs_timing_read(ctx, 0)
+    gate_ms, gate_n = lcs.lcs_timing_read(ctx, 1)
+    cg_ms, _ = lcs.lcs_timing_read(ctx, 3)
+    lcs.lcs_timing_enable(ctx, False)
+    counts = np.empty(N, dtype=np.int32)
+    lcs.lcs_flowmap_steps(ctx, fm, 0, counts)
+    fb_frac = float(counts.astype(np.int64).sum()) / (N * C5_K)
+    el_plain = timed(plain, ftle_p, max(1, args.steps // 2))
+    a, b = ftle.cpu().double().numpy(), ftle_p.cpu().double().numpy()
+    ok = np.isfinite(a) & np.isfinite(b)
+    d = np.abs(a[ok] - b[ok])
+    pk, pk_kind = peaks()
+    peak = pk.get("bf16_tflops", 1900.0)
+    launch_s = mlp_ms / max(mlp_n, 1) / 1e3
+    flops = float(N) * C5_FLOP_PER_EVAL
+    achieved = flops / launch_s / 1e12
+    line = {
+        "metric": METRIC, "value": N * 1.0 / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (network), f32 (integrator)", "data": "synthetic",
+        "config": {"workload": C5_WORKLOAD, "seeds": N, "K": C5_K, "tau": C5_TAU, "gate_tol": C5_TOL,
+                   "train_samples": C5_SAMPLES, "train_batch": C5_BATCH, "train_epochs": args.train_epochs,
+                   "l2": "no flush: each step writes 2.7 GB of flow map and FTLE (> 129 MB L2)"},
+        "surrogate": {"train_s": round(t_train, 2), "loss_per_epoch": [float(x) for x in hist],
+                      "fallback_fraction": fb_frac,
+                      "ftle_err_vs_plain": {"median": float(np.median(d)), "p99.9": float(np.quantile(d, 0.999)),
+                                            "max": float(d.max())},
+                      "plain_rk4_ms_per_step": el_plain * 1e3, "plain_rk4_seeds_per_s": N / el_plain,
+                      "speedup_vs_plain": el_plain / el},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "mlp_step_kernel (tcgen05, 5 layers)",
+                     "flop_per_launch": flops, "avg_launch_ms": launch_s * 1e3, "launches": mlp_n,
+                     "peak_basis": "bf16_tflops (%s, burst)" % pk_kind},
+        "phases_ms_per_step": {"network": mlp_ms / args.steps, "audit_and_fallback": gate_ms / args.steps,
+                               "cg_ftle": cg_ms / args.steps},
+        "clocks": clk.summary(),
+        # per step: schedule, state init (3), K x (network, audit, apply), FD/CG/FTLE
+        "gpu_launches": args.steps * (1 + 3 + 3 * C5_K + 1),
+    }
+    if not args.no_cpu_baseline:
+        params = np.empty(lcs.MLP_NPARAMS, dtype=np.float32)
+        lcs.lcs_mlp_get_params(ctx, mlp, params)
+        _, dts, _, _ = c5_oracle_block(g, params, 4)
+        per = dts / 64.0
+        side = int(max(4, min(64, math.sqrt(10.0 / max(per, 1e-9)) - 4)))
+        s, dt, nth, integrated = c5_oracle_block(g, params, side)
+        line["cpu_baseline"] = {"value": s / dt, "unit": "seeds/s", "cores": nth, "kind": "oracle",
+                                "sample": "%dx%d block of the 16384x8192 lattice with its 2-seed halo (%d tracers, "
+                                          "FP64 network + audits + RK4 fallback), FD/CG/FTLE; %.1f s"
+                                          % (side, side, integrated, dt)}
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_mlp_free(mlp)
+    lcs.lcs_free_field(field)
+    lcs.lcs_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 def _src_sha():
     import hashlib
 
@@ -610,6 +780,9 @@ def main():
         return
     if args.config == "c4":
         c4_arm(args, rank, world, local)
+        return
+    if args.config == "c5":
+        c5_arm(args, rank, world, local)
         return
     our_arm(args, rank, world, local)
 

@@ -4,10 +4,10 @@
 // Network (7 -> 128 -> 128 -> 128 -> 128 -> 3, SiLU): per tile of 128 tracers, features
 // phi(x, y, t) are rounded to BF16 into a shared-memory operand tile; each layer is one
 // 128 x N x K MMA chain into a TMEM accumulator (FP32), and its epilogue adds the FP32
-// bias, applies SiLU (z/2 + z/2 tanh(z/2)) and writes the BF16 activations back as the
-// next layer's operand.  The weights (104 KB of BF16 operand tiles) and biases stay in
-// shared memory for the whole persistent launch.  Two warpgroups work on two tiles at a
-// time, so one tile's epilogue overlaps the other's MMAs on the tensor core.
+// bias, applies SiLU (h + h tanh(h) with h = z/2, in packed BF16 arithmetic) and writes the
+// BF16 activations back as the next layer's operand.  The weights (104 KB of BF16 operand tiles) and biases stay in
+// shared memory for the whole persistent launch.  Three warpgroups work on three tiles at a
+// time, so each tile's epilogue overlaps the others' MMAs on the tensor core.
 //
 // Gated advection over one surrogate step tau (the audit of each 32-tracer group against
 // the integrator of Eq. 2, and the integrator where the audit fails) runs in two SIMT
@@ -25,16 +25,10 @@ namespace {
 constexpr uint32_t OFF_W0 = 0, OFF_W1 = 4096, OFF_W2 = 36864, OFF_W3 = 69632, OFF_W4 = 102400, OFF_BIAS = 106496;
 constexpr uint32_t OFF_WG = MLP_TILE_BYTES;  // per-warpgroup region: phi tile (4 KB) + activations (32 KB)
 constexpr uint32_t WG_BYTES = 4096 + 32768;
-constexpr uint32_t INFER_SMEM = MLP_TILE_BYTES + 2 * WG_BYTES;
+constexpr int NWG = 3;  // warpgroups (tiles in flight) per CTA
+constexpr uint32_t INFER_SMEM = MLP_TILE_BYTES + NWG * WG_BYTES;
 
 __device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
-
-__device__ __forceinline__ float tanh_approx(float x)
-{
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
@@ -42,38 +36,66 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// 16 accumulator columns + bias -> SiLU -> BF16 into row r, columns c .. c+15 of the operand tile
-__device__ __forceinline__ void silu_store16(const float *v, const float *bias, unsigned char *tile, int r, int c)
+__device__ __forceinline__ uint32_t tanh_bf16x2(uint32_t h)
 {
-    uint32_t w[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        float z0 = v[2 * j] + bias[2 * j], z1 = v[2 * j + 1] + bias[2 * j + 1];
-        float h0 = 0.5f * z0, h1 = 0.5f * z1;
-        w[j] = pack_bf16(fmaf(h0, tanh_approx(h0), h0), fmaf(h1, tanh_approx(h1), h1));
-    }
-    *reinterpret_cast<uint4 *>(tile + ckm_offset(128, r, c)) = make_uint4(w[0], w[1], w[2], w[3]);
-    *reinterpret_cast<uint4 *>(tile + ckm_offset(128, r, c + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
+    uint32_t t;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(h));
+    return t;
 }
 
-__global__ void __launch_bounds__(256, 1) mlp_step_kernel(MlpStepArgs A)
+__device__ __forceinline__ uint32_t fma_bf16x2(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// one hidden layer's epilogue for tile row r: the 128 FP32 accumulator columns (all loads in
+// flight before one wait), h = z/2 = acc/2 + b/2 (hb holds b/2) rounded to BF16 pairs, and
+// SiLU(z) = h + h tanh(h) in packed BF16 arithmetic, stored as row r of the next operand tile
+__device__ __forceinline__ void hidden_epilogue(uint32_t ta, const float *hb, unsigned char *tile, int r)
+{
+#pragma unroll
+    for (int half = 0; half < 128; half += 64) {
+        uint32_t acc[64];
+        tmem_ld32_async(ta + half, acc);
+        tmem_ld32_async(ta + half + 32, acc + 32);
+        tmem_wait_ld32(acc);
+        tmem_wait_ld32(acc + 32);
+#pragma unroll
+        for (int c = 0; c < 64; c += 8) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float h0 = fmaf(__uint_as_float(acc[c + 2 * j]), 0.5f, hb[half + c + 2 * j]);
+                const float h1 = fmaf(__uint_as_float(acc[c + 2 * j + 1]), 0.5f, hb[half + c + 2 * j + 1]);
+                const uint32_t h2 = pack_bf16(h0, h1);
+                w[j] = fma_bf16x2(h2, tanh_bf16x2(h2), h2);
+            }
+            *reinterpret_cast<uint4 *>(tile + ckm_offset(128, r, half + c)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NWG * 128, 1) mlp_step_kernel(MlpStepArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t bar_w, bar_g[2];
+    __shared__ uint64_t bar_w, bar_g[NWG];
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag[2];
+    __shared__ int abort_flag[NWG];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = warp >> 2;           // warpgroup
     const int r = tid & 127;           // tile row = TMEM lane
     const int wq = warp & 3;
     if (tid == 0) {
         mbar_init(&bar_w, 1);
-        mbar_init(&bar_g[0], 1);
-        mbar_init(&bar_g[1], 1);
-        abort_flag[0] = abort_flag[1] = 0;
+        for (int q = 0; q < NWG; ++q) {
+            mbar_init(&bar_g[q], 1);
+            abort_flag[q] = 0;
+        }
         mbar_fence_init();
     }
-    if (warp == 0) tmem_alloc(&tmem_base, 256);
+    if (warp == 0) tmem_alloc(&tmem_base, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -82,6 +104,11 @@ __global__ void __launch_bounds__(256, 1) mlp_step_kernel(MlpStepArgs A)
         bulk_g2s(smem, A.tiles, MLP_TILE_BYTES, &bar_w);
     }
     const bool have_w = !__syncthreads_or(!tc_wait(&bar_w, 0, A.errword));
+    if (have_w) {  // hidden-layer biases are used halved (the epilogue works with z / 2)
+        float *b = reinterpret_cast<float *>(smem + OFF_BIAS);
+        for (int q = tid; q < 512; q += blockDim.x) b[q] *= 0.5f;
+        __syncthreads();
+    }
     const uint32_t tmem = tmem_base + (uint32_t)(g * 128);
     unsigned char *sPhi = smem + OFF_WG + g * WG_BYTES;
     unsigned char *sAct = sPhi + 4096;
@@ -90,7 +117,7 @@ __global__ void __launch_bounds__(256, 1) mlp_step_kernel(MlpStepArgs A)
     const uint32_t id128 = tc_idesc_bf16(128, 128), id16 = tc_idesc_bf16(128, 16);
     const long long ntiles = (A.n + 127) / 128;
     unsigned phase = 0;
-    for (long long tile = (long long)blockIdx.x * 2 + g; have_w && tile < ntiles; tile += 2LL * gridDim.x) {
+    for (long long tile = (long long)blockIdx.x * NWG + g; have_w && tile < ntiles; tile += (long long)NWG * gridDim.x) {
         const long long i = tile * 128 + r;
         const bool live = i < A.n;
         float x = 0.0f, y = 0.0f, t = A.t_uniform;
@@ -137,12 +164,7 @@ __global__ void __launch_bounds__(256, 1) mlp_step_kernel(MlpStepArgs A)
             tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(wq * 32) << 16);
             if (l < 4) {
-#pragma unroll 1
-                for (int c = 0; c < 128; c += 16) {
-                    float v[16];
-                    tmem_ld16(ta + c, v);
-                    silu_store16(v, bias + l * 128 + c, sAct, r, c);
-                }
+                hidden_epilogue(ta, bias + l * 128, sAct, r);
             } else {
                 float v[16];
                 tmem_ld16(ta, v);
@@ -166,7 +188,7 @@ __global__ void __launch_bounds__(256, 1) mlp_step_kernel(MlpStepArgs A)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_free(tmem_base, 256);
+    if (warp == 0) tmem_free(tmem_base, 512);
 }
 
 // one thread per 32-tracer group: audit lane's RK4 over the sub-interval vs its proposal,
@@ -259,9 +281,9 @@ cudaError_t launch_mlp_step(const MlpStepArgs &A, int num_sms, cudaStream_t s)
     if (A.n <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(mlp_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM);
     if (e != cudaSuccess) return e;
-    const long long pairs = ((A.n + 127) / 128 + 1) / 2;
+    const long long pairs = ((A.n + 127) / 128 + NWG - 1) / NWG;
     const int grid = (int)(pairs < num_sms ? pairs : num_sms);
-    mlp_step_kernel<<<grid, 256, INFER_SMEM, s>>>(A);
+    mlp_step_kernel<<<grid, NWG * 128, INFER_SMEM, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -24,11 +24,15 @@ __device__ __forceinline__ float tanh_a(float x)
     return y;
 }
 
-// SiLU(z) = z sigma(z) with sigma(z) = 1/2 + 1/2 tanh(z/2), the form the inference kernel uses
-__device__ __forceinline__ float silu_f(float z)
+// SiLU of a pair of pre-activations exactly as the inference kernel computes it: h = z/2 rounded to
+// BF16, then h + h tanh(h) in packed BF16 arithmetic
+__device__ __forceinline__ __nv_bfloat162 silu_pair(float z0, float z1)
 {
-    const float h = 0.5f * z;
-    return fmaf(h, tanh_a(h), h);
+    __nv_bfloat162 h = __floats2bfloat162_rn(0.5f * z0, 0.5f * z1);
+    uint32_t hu = *reinterpret_cast<uint32_t *>(&h), t, d;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(hu));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(hu), "r"(t), "r"(hu));
+    return *reinterpret_cast<__nv_bfloat162 *>(&d);
 }
 
 __device__ __forceinline__ float silu_grad_f(float z)
@@ -67,15 +71,17 @@ __global__ void __launch_bounds__(256) tr_silu_kernel(float *__restrict__ Z, con
 {
     __shared__ __nv_bfloat16 tile[128][34];
     const long long r0 = (long long)blockIdx.x * 32;
-    for (int e = threadIdx.x; e < 32 * 128; e += 256) {
-        const int rr = e >> 7, c = e & 127;
+    for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+        const int rr = e >> 6, c = (e & 63) * 2;
         const long long row = r0 + rr;
         if (row >= B) continue;
-        float z = Z[row * 128 + c] + bias[c];
-        Z[row * 128 + c] = z;
-        const __nv_bfloat16 h = __float2bfloat16_rn(silu_f(z));
-        H[row * 128 + c] = h;
-        tile[c][rr] = h;
+        const float z0 = Z[row * 128 + c] + bias[c], z1 = Z[row * 128 + c + 1] + bias[c + 1];
+        Z[row * 128 + c] = z0;
+        Z[row * 128 + c + 1] = z1;
+        const __nv_bfloat162 h = silu_pair(z0, z1);
+        *reinterpret_cast<__nv_bfloat162 *>(H + row * 128 + c) = h;
+        tile[c][rr] = h.x;
+        tile[c + 1][rr] = h.y;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 32 * 128; e += 256) {

@@ -342,3 +342,24 @@ def test_full_size_abc_sampled(ctx):
     assert np.median(d) <= 1e-5 and d.max() <= 1e-3, (np.median(d), d.max())
     # every output finite, every tracer OK on the periodic domain
     assert np.isfinite(r["ftle"][0]).all() and (r["status"][0] == 0).all()
+
+
+@pytest.mark.parametrize("storage", [lcs.F16, lcs.BF16])
+def test_full_size_abc_storage_error(ctx, storage):
+    """Reduced-precision velocity storage on the benchmark workload against the FP64 oracle on the FP32
+    frames (the storage error itself, reported rather than gated; a loose sanity bound only)."""
+    g = inputs.abc()
+    L = 2 * np.pi
+    n, lo, hi, T, dt = (256, 256, 256), (0.0, 0.0, 0.0), (L, L, L), 8.0, 0.02
+    r = gpu_run(ctx, g, n, lo, hi, (1, 1, 1), T, dt, storage=storage)
+    rng = np.random.default_rng(8)
+    N = 256 ** 3
+    sample = np.unique(rng.integers(0, N, 40))
+    o = oracle_run(g, n, lo, hi, (1, 1, 1), T, dt, sample=sample)
+    sig, lam, C = oracle_ftle_at(sample, 3, n, o["h"], (1, 1, 1), o["period"], o["xT"], o["st"], T)
+    d = np.abs(r["ftle"][0][sample].astype(np.float64) - sig)
+    dx = np.abs(r["xyz"][0][:, o["ids"]].astype(np.float64) - o["xyz_s"]).max(axis=0)
+    print("storage", storage, "FTLE |err| median %.3g p99.9 %.3g max %.3g; flow map max %.3g"
+          % (np.median(d), np.quantile(d, 0.999), d.max(), dx.max()))
+    assert np.median(d) <= 5e-2 and np.isfinite(r["ftle"][0]).all()
+
