@@ -525,8 +525,14 @@ def c4_arm(args, rank, world, local):
     t_mesh = time.perf_counter() - t_mesh
     desc = lcs.field_desc(3, times=mesh.times, time_periodic=True, period=mesh.period, kind=lcs.TET,
                           mesh=(mesh.xyz, mesh.tets, mesh.nbrs))
+    t_load = time.perf_counter()
     field = lcs.lcs_load_field(ctx, desc, mesh.frames)
+    lcs.lcs_synchronize(ctx)
+    t_load = time.perf_counter() - t_load
+    t_seed = time.perf_counter()
     seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, C4_N, C4_LO, C4_HI), field)
+    lcs.lcs_synchronize(ctx)
+    t_seed = time.perf_counter() - t_seed
     N = lcs.lcs_seeds_count(seeds)
     fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
     opts = lcs.advect_opts(lcs.RK45, t0=0.0, T=C4_T, rtol=C4_TOL, atol=C4_TOL, h0=C4_H0)
@@ -575,6 +581,7 @@ def c4_arm(args, rank, world, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": C4_WORKLOAD, "seeds": N, "nodes": int(mesh.xyz.shape[0]),
                    "tets": int(mesh.tets.shape[0]), "mesh_build_s": round(t_mesh, 1),
+                   "field_load_ms": round(t_load * 1e3, 1), "seed_location_ms": round(t_seed * 1e3, 1),
                    "status": counts, "accepted_steps_per_live_tracer": float(steps[live].mean()),
                    "l2": "no flush: the mesh store (geometry + 50 slabs, %.0f MB) exceeds the 129 MB L2"
                          % ((mesh.tets.shape[0] * (16 + 16 + 48) + mesh.xyz.shape[0] * 16

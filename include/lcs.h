@@ -115,13 +115,15 @@ typedef struct {
 /* Copy velocity frames into device storage.  frames is FP32,
  * [nframes][nz][ny][nx][dim] (rectilinear) or [nframes][nnodes][3] (tets),
  * in host memory or, if frames_on_device, device memory.  The library
- * converts to desc->storage (FP16/BF16 round to nearest).
- * Errors: LCS_EINVAL (descriptor), LCS_ENOMEM, LCS_ECUDA.                   */
+ * converts to desc->storage (FP16/BF16 round to nearest).  The call checks
+ * every value for finiteness on the device and synchronises the stream.
+ * Errors: LCS_EINVAL (descriptor, a non-finite velocity), LCS_ENOMEM,
+ * LCS_ECUDA.                                                                */
 lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *desc, const float *frames,
                           int frames_on_device, lcs_field **out);
 
 /* Replace the frames of a loaded field with new data of the same shape
- * (same conventions as lcs_load_field); no allocation.                      */
+ * (same conventions and finiteness check as lcs_load_field).               */
 lcs_status lcs_update_frames(lcs_ctx *ctx, lcs_field *field, const float *frames,
                              int frames_on_device);
 

@@ -268,6 +268,16 @@ cudaError_t launch_convert_rect(const float *src, int nframes, int nslabs, long 
     return cudaGetLastError();
 }
 
+// any non-finite value among n floats sets *flag
+__global__ void nonfinite_kernel(const float *__restrict__ p, size_t n, int *__restrict__ flag)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        if (!isfinite(p[i])) {
+            atomicOr(flag, 1);
+            return;
+        }
+}
+
 static lcs_status upload_frames(lcs_ctx *ctx, lcs_field *f, const float *frames, int on_device)
 {
     size_t n_in = (size_t)f->nframes * f->nodes * f->dim;
@@ -284,8 +294,20 @@ static lcs_status upload_frames(lcs_ctx *ctx, lcs_field *f, const float *frames,
     }
     cudaError_t e = launch_convert_rect(src, f->nframes, f->nslabs, f->nodes, f->dim, f->vec, f->storage,
                                         f->frame_stride, f->d_frames, ctx->stream);
+    // velocity data must be finite (a NaN would spread through every tracer that touches it)
+    int *dflag = nullptr, hflag = 0;
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dflag, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dflag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) {
+        nonfinite_kernel<<<(unsigned)std::min<size_t>((n_in + 255) / 256, 4096), 256, 0, ctx->stream>>>(src, n_in, dflag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (dflag) cudaFreeAsync(dflag, ctx->stream);
     if (tmp) cudaFreeAsync(tmp, ctx->stream);
     if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "frame conversion: %s", cudaGetErrorString(e));
+    if (hflag) return lcs_fail(ctx, LCS_EINVAL, "frames hold a non-finite velocity value");
     return LCS_OK;
 }
 
@@ -513,7 +535,7 @@ extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const 
     if (e == cudaSuccess && field && field->kind == LCS_TET) {
         s->field_uid = field->uid;
         e = cudaMalloc(&s->d_cells, sizeof(int) * (size_t)N);
-        if (e == cudaSuccess) e = tet_locate_seeds(field, s->d_xyz, N, 1 << 20, s->d_cells, ctx->stream);
+        if (e == cudaSuccess) e = tet_locate_seeds(field, s->d_xyz, N, 1 << 16, s->d_cells, ctx->stream);
     }
     if (e != cudaSuccess) {
         lcs_free_seeds(s);

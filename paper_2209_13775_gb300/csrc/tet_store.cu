@@ -11,6 +11,17 @@
 
 #define BIN_EMPTY 0x7f7f7f7f  // what a 0x7f byte fill leaves in an int
 
+// 32-bit integer hash (Wellons' lowbias32): face order of the stochastic walk
+__device__ __forceinline__ unsigned lowbias32_t(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
 // ------------------------------------------------------------ device kernels
 
 __global__ void tet_xyz_kernel(const float *__restrict__ xyz, long long n, float4 *__restrict__ out)
@@ -146,9 +157,15 @@ __device__ int exact_brute(const TetDev &T, const float *p)
     return -1;
 }
 
-// Lowest id among the closed tets holding p, -1 outside the mesh: walk with exact signs
-// (crossing the face of the most negative FP32 coordinate among the faces whose exact
-// sign is negative), then collect the tets sharing the face, edge or vertex p lies on.
+// Lowest id among the closed tets holding p, -1 outside the mesh.
+//  1. An FP32 walk (as in the integrator) from the bin's tet gets next to p cheaply.
+//  2. An exact walk from there: exact orientation signs decide containment, and among the faces
+//     whose exact sign is negative the walk crosses the first one in an order rotated by a
+//     hash of (seed, step) -- a remembering stochastic walk, which cannot cycle on degenerate
+//     (cospherical) configurations the way a deterministic choice can.  The result does not
+//     depend on the path: it is the unique lowest-id closed tet holding p.
+//  3. Where p lies on a face, edge or vertex, a breadth-first search over the closed tets across
+//     faces holding p collects every holder and keeps the lowest id.
 __global__ void tet_seed_locate_kernel(TetDev T, const float *__restrict__ seeds, long long N, BinGrid B,
                                        const int *__restrict__ bins, int walk_limit, int *__restrict__ cells)
 {
@@ -156,19 +173,41 @@ __global__ void tet_seed_locate_kernel(TetDev T, const float *__restrict__ seeds
     if (i >= N) return;
     const float p[3] = {seeds[i], seeds[N + i], seeds[2 * N + i]};
     int c = bins[bin_of(B, p[0], p[1], p[2])];
+    {   // 1. FP32 walk, bounded
+        float lam[4];
+        for (int it = 0; it < 1024; ++it) {
+            tet_bary(T, c, p, lam);
+            int jm = 0;
+            float lm = lam[0];
+            for (int j = 1; j < 4; ++j)
+                if (lam[j] < lm) {
+                    lm = lam[j];
+                    jm = j;
+                }
+            if (!(lm < -1e-6f)) break;
+            const int4 nb = T.nbrs[c];
+            const int n = jm == 0 ? nb.x : jm == 1 ? nb.y : jm == 2 ? nb.z : nb.w;
+            if (n < 0) break;
+            c = n;
+        }
+    }
     int res = -2;
     int sg[4];
-    for (int it = 0; it < walk_limit; ++it) {
+    for (int it = 0; it < walk_limit; ++it) {  // 2. exact walk
         exact_signs(T, c, p, sg);
         if (sg[0] >= 0 && sg[1] >= 0 && sg[2] >= 0 && sg[3] >= 0) {
             res = c;
             break;
         }
-        float lam[4];
-        tet_bary(T, c, p, lam);
-        int jm = -1;
-        for (int j = 0; j < 4; ++j)
-            if (sg[j] < 0 && (jm < 0 || lam[j] < lam[jm])) jm = j;
+        const int rot = (int)(lowbias32_t((unsigned)i * 0x9E3779B9u ^ (unsigned)it) & 3u);
+        int jm = 0;
+        for (int q = 0; q < 4; ++q) {
+            const int j = (q + rot) & 3;
+            if (sg[j] < 0) {
+                jm = j;
+                break;
+            }
+        }
         const int4 nb = T.nbrs[c];
         const int n = jm == 0 ? nb.x : jm == 1 ? nb.y : jm == 2 ? nb.z : nb.w;
         if (n < 0) {
@@ -185,8 +224,9 @@ __global__ void tet_seed_locate_kernel(TetDev T, const float *__restrict__ seeds
         cells[i] = res;
         return;
     }
-    // p on a face, edge or vertex of res: breadth-first over the closed tets across faces holding p
-    int stack[64], seen[64];
+    // 3. p on a face, edge or vertex of res: breadth-first over the closed tets across faces holding p
+    constexpr int CAP = 128;
+    int stack[CAP], seen[CAP];
     int ns = 0, nseen = 0, best = res;
     stack[ns++] = res;
     seen[nseen++] = res;
@@ -202,7 +242,7 @@ __global__ void tet_seed_locate_kernel(TetDev T, const float *__restrict__ seeds
             bool dup = false;
             for (int q = 0; q < nseen; ++q) dup |= seen[q] == nn[j];
             if (dup || !exact_contains(T, nn[j], p)) continue;
-            if (nseen >= 64 || ns >= 64) {
+            if (nseen >= CAP || ns >= CAP) {
                 cells[i] = exact_brute(T, p);
                 return;
             }
