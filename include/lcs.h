@@ -203,7 +203,7 @@ typedef struct {
                                    4 = persistent shared-memory ring pulling (job, tile)
                                        items longest-job first (2D, batches)            */
     const void *surrogate;      /* LCS_SURROGATE: the lcs_mlp to step with            */
-    int episode_steps;          /* variant 3: RK4 steps between re-bundlings (0 = 16) */
+    int episode_steps;          /* variant 3: RK4 steps between re-bundlings (0 = 32) */
     int tracers_per_thread;     /* variants 2 and 4: 1 or 2 tracers per thread (0 = 1) */
     int use_graph;              /* capture the launches of this call in a CUDA graph,
                                    cached on the context and replayed while the same

@@ -20,6 +20,19 @@
 // stencil row.  FP16/BF16 storage reads the 16-byte interval pairs directly.
 #include "rect_device.cuh"
 
+// Resident 256-thread blocks per SM the advection kernel is compiled for, with time
+// slices (FP32) and with interval pairs (FP16/BF16): 4 caps both at 64 registers
+// (32 warps per SM).  Their stencil gathers are latency-bound, and the occupancy
+// pays more than the few bytes spilled cost (the full-size ABC workload: 217 -> 145 ms
+// per 400 steps with slices; 199 -> 173 ms with FP16 pairs).  5 (48 registers) is
+// slower again.
+#ifndef LCS_EP_MINB
+#define LCS_EP_MINB 4
+#endif
+#ifndef LCS_EP_MINB_PAIRS
+#define LCS_EP_MINB_PAIRS 4
+#endif
+
 // 32-byte tracer record: one sector per tracer for the re-bundling scatter
 struct __align__(16) Tracer {
     float x, y, z;          // wrapped into [origin, origin + L) on periodic axes
@@ -230,7 +243,7 @@ __global__ void ep_slice_fill_kernel(RectParams P, const char *__restrict__ pair
 // Steps [s0, min(s1, nsteps)) of every tracer record, then the cell key of its new
 // position for the next re-bundling.  SLICES: FP32 time slices; else interval pairs.
 template <int ST, bool SLICES, int PM>
-__global__ void __launch_bounds__(256) ep_advect3_kernel(RectParams P, const char *__restrict__ pairs,
+__global__ void __launch_bounds__(256, SLICES ? LCS_EP_MINB : LCS_EP_MINB_PAIRS) ep_advect3_kernel(RectParams P, const char *__restrict__ pairs,
                                                          size_t fstride, const float2 *__restrict__ slices,
                                                          size_t plane_stride, const int *__restrict__ smap, Rk4Args A,
                                                          Tracer *__restrict__ S, int job, int s0, int s1, int shift,
@@ -246,17 +259,21 @@ __global__ void __launch_bounds__(256) ep_advect3_kernel(RectParams P, const cha
         const float h = A.job_h[job];
         const int e = min(s1, ns);
         const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
-        const size_t ss = 3 * plane_stride;
+        CornerCache cc;       // SLICES
+        cc.v0 = -1;
+        cc.slice = -1;
+        PairCache pc;         // interval pairs
+        pc.v0 = -1;
+        pc.k = -1;
+        pc.a = 0.0f;
         for (int n = s0; n < e; ++n) {
             if constexpr (SLICES) {
                 const int *m = smap + 3 * (n - s0);
-                rk4_step3s<PM>(P, x, h, slices + (size_t)__ldg(m) * ss, slices + (size_t)__ldg(m + 1) * ss,
-                           slices + (size_t)__ldg(m + 2) * ss, plane_stride);
+                rk4_step3c<PM>(P, x, h, slices, __ldg(m), __ldg(m + 1), __ldg(m + 2), plane_stride, cc);
             } else {
                 SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1),
                            e2 = load_sched(sc + 3 * n + 2);
-                rk4_step3p<ST, PM>(P, x, h, pairs + (size_t)e0.k * fstride, e0.a, pairs + (size_t)e1.k * fstride, e1.a,
-                               pairs + (size_t)e2.k * fstride, e2.a);
+                rk4_step3pc<ST, PM>(P, x, h, pairs, fstride, e0, e1, e2, pc);
             }
             wrap_periodic<3, PM>(P, x, img);
             if (rect_left<3, PM>(P, x)) {

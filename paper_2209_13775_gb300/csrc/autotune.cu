@@ -120,7 +120,7 @@ extern "C" lcs_status lcs_autotune(lcs_ctx *ctx, const lcs_field *f, const lcs_s
     } else {
         cands.push_back({1, 256, 1, 0});
         if (s->N >= 32 * 1024)
-            for (int E : {8, 12, 16, 24})
+            for (int E : {8, 16, 32, 48})
                 for (int bt : {128, 256})
                     cands.push_back({3, bt, 1, E});
     }

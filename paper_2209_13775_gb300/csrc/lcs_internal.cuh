@@ -204,7 +204,7 @@ struct Rk4Launch {
 // smallest seed count for which lcs_advect picks the re-bundled kernel by default
 #define LCS_SORTED_MIN_SEEDS 262144
 // default RK4 steps per re-bundled episode
-#define LCS_EPISODE_STEPS 16
+#define LCS_EPISODE_STEPS 32
 
 size_t rk4_sorted_scratch_bytes(long long N, long long nodes, int storage, int episode_steps);
 

@@ -326,21 +326,6 @@ __device__ __forceinline__ void interp3p(const Stencil<3> &S, const char *fp, fl
     for (int c = 0; c < 3; ++c) u[c] = acc[c];
 }
 
-// 3D: u(x, t) from a time slice (nodes already blended to the stage time), float4 per node
-__device__ __forceinline__ void interp3s(const Stencil<3> &S, const float4 *__restrict__ sl, float *u)
-{
-    float acc[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        float4 v = __ldg(sl + S.v[q]);
-        acc[0] = fmaf(S.w[q], v.x, acc[0]);
-        acc[1] = fmaf(S.w[q], v.y, acc[1]);
-        acc[2] = fmaf(S.w[q], v.z, acc[2]);
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) u[c] = acc[c];
-}
-
 struct Rk4Args {
     const float *seeds;
     long long N;
@@ -464,55 +449,144 @@ __device__ __forceinline__ void rk4_step3p(const RectParams &P, float *x, float 
     for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
 }
 
-// 3D: u(x, t) from a time slice stored as three component planes of x-neighbour pairs:
-// plane c holds, at node (i, j, k), the pair (u_c(i, j, k), u_c(i + 1, j, k)) (i + 1 wrapped
-// on a periodic axis).  A corner row (j, k) of the trilinear stencil is one 8-byte load
-// per component, and the lanes of a warp on neighbouring cells fall in the same sectors.
-// Same products and summation order as interp3p (rows in order, i0 before i1).
-__device__ __forceinline__ void interp3sp(const Stencil<3> &S, const float2 *__restrict__ pl,
-                                          size_t plane_stride, float *u)
+// 3D time slices (the field blended to one stage time) are stored as three component
+// planes of x-neighbour pairs: plane c holds, at node (i, j, k), the pair
+// (u_c(i, j, k), u_c(i + 1, j, k)) (i + 1 wrapped on a periodic axis).  A corner row
+// (j, k) of the trilinear stencil is one 8-byte load per component, and the lanes of
+// a warp on neighbouring cells fall in the same sectors.  The products and their
+// summation order are those of interp3p (rows in order, i0 before i1).
+//
+// CornerCache: the 12 x-pairs (4 stencil rows x 3 components) of the cell a tracer's
+// last stage evaluation read, with the cell's base node and the slice they came from.  Stage 3 of
+// an RK4 step reads the same slice as stage 2 (t_n + h/2), and stage 1 of step n + 1 the
+// same slice as stage 4 of step n (t_n + h) whenever the schedule gives both the same
+// (k, alpha); in a smooth flow the second point of each pair is almost always in the
+// same cell as the first, so its corner values are already in registers.  A cell is
+// identified by its base node v[0] (the other seven corners follow from it), so a
+// reuse reads exactly what a reload would: the result is bit-identical.
+struct CornerCache {
+    float2 q[4][3];
+    int v0;
+    int slice;
+};
+
+__device__ __forceinline__ void interp3sc(const Stencil<3> &S, const float2 *__restrict__ pl, int slice,
+                                          size_t plane_stride, CornerCache &cc, float *u)
 {
+    if (S.v[0] != cc.v0 || slice != cc.slice) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cc.q[r][c] = __ldg(pl + c * plane_stride + S.v[2 * r]);
+        cc.v0 = S.v[0];
+        cc.slice = slice;
+    }
     float acc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float2 q = __ldg(pl + c * plane_stride + S.v[2 * r]);
-            acc[c] = fmaf(S.w[2 * r], q.x, acc[c]);
-            acc[c] = fmaf(S.w[2 * r + 1], q.y, acc[c]);
+            acc[c] = fmaf(S.w[2 * r], cc.q[r][c].x, acc[c]);
+            acc[c] = fmaf(S.w[2 * r + 1], cc.q[r][c].y, acc[c]);
         }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) u[c] = acc[c];
 }
 
-// one RK4 step in 3D from three time slices (stage times t_n, t_n + h/2, t_n + h)
+// One RK4 step in 3D from time slices m0, m1, m2 (indices into `slices`, each 3 planes
+// of plane_stride pairs) at stage times t_n, t_n + h/2, t_n + h, through the corner cache.
 template <int PM = -1>
-__device__ __forceinline__ void rk4_step3s(const RectParams &P, float *x, float h, const float2 *s0,
-                                           const float2 *s1, const float2 *s2, size_t ps)
+__device__ __forceinline__ void rk4_step3c(const RectParams &P, float *x, float h, const float2 *__restrict__ slices,
+                                           int m0, int m1, int m2, size_t ps, CornerCache &cc)
 {
     float k1[3], k2[3], k3[3], k4[3], y[3];
     Stencil<3> S;
     const float hh = 0.5f * h;
+    const size_t ss = 3 * ps;
     make_stencil<3, PM>(P, x, S);
-    interp3sp(S, s0, ps, k1);
+    interp3sc(S, slices + (size_t)m0 * ss, m0, ps, cc, k1);
 #pragma unroll
     for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k1[c], x[c]);
     make_stencil<3, PM>(P, y, S);
-    interp3sp(S, s1, ps, k2);
+    interp3sc(S, slices + (size_t)m1 * ss, m1, ps, cc, k2);
 #pragma unroll
     for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k2[c], x[c]);
     make_stencil<3, PM>(P, y, S);
-    interp3sp(S, s1, ps, k3);
+    interp3sc(S, slices + (size_t)m1 * ss, m1, ps, cc, k3);
 #pragma unroll
     for (int c = 0; c < 3; ++c) y[c] = fmaf(h, k3[c], x[c]);
     make_stencil<3, PM>(P, y, S);
-    interp3sp(S, s2, ps, k4);
+    interp3sc(S, slices + (size_t)m2 * ss, m2, ps, cc, k4);
     const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
     for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
 }
 
+// The corner cache of the interval-pair path (FP16/BF16 storage): the 8 corners of the
+// last evaluation's cell blended to its stage time (pair k, weight a), as interp3p
+// blends them, so a reuse gives the same products in the same order.
+struct PairCache {
+    float u[8][3];
+    int v0, k;
+    float a;
+};
+
+template <int ST>
+__device__ __forceinline__ void interp3pc(const Stencil<3> &S, const char *__restrict__ pairs, size_t fstride,
+                                          SchedEntry e, PairCache &cc, float *u)
+{
+    if (S.v[0] != cc.v0 || e.k != cc.k || __float_as_int(e.a) != __float_as_int(cc.a)) {
+        const char *fp = pairs + (size_t)e.k * fstride;
+        const float g = 1.0f - e.a;
+        float va[3], vb[3];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            Pair3<ST>::ld(fp, S.v[q], va, vb);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cc.u[q][c] = e.a == 0.0f ? va[c] : tblend(va[c], vb[c], e.a, g);
+        }
+        cc.v0 = S.v[0];
+        cc.k = e.k;
+        cc.a = e.a;
+    }
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = fmaf(S.w[q], cc.u[q][c], acc[c]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = acc[c];
+}
+
+// rk4_step3p through the corner cache: schedule entries e0, e1, e2 of stage times
+// t_n, t_n + h/2, t_n + h.
+template <int ST, int PM = -1>
+__device__ __forceinline__ void rk4_step3pc(const RectParams &P, float *x, float h, const char *__restrict__ pairs,
+                                            size_t fstride, SchedEntry e0, SchedEntry e1, SchedEntry e2,
+                                            PairCache &cc)
+{
+    float k1[3], k2[3], k3[3], k4[3], y[3];
+    Stencil<3> S;
+    const float hh = 0.5f * h;
+    make_stencil<3, PM>(P, x, S);
+    interp3pc<ST>(S, pairs, fstride, e0, cc, k1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k1[c], x[c]);
+    make_stencil<3, PM>(P, y, S);
+    interp3pc<ST>(S, pairs, fstride, e1, cc, k2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k2[c], x[c]);
+    make_stencil<3, PM>(P, y, S);
+    interp3pc<ST>(S, pairs, fstride, e1, cc, k3);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(h, k3[c], x[c]);
+    make_stencil<3, PM>(P, y, S);
+    interp3pc<ST>(S, pairs, fstride, e2, cc, k4);
+    const float h6 = h * (1.0f / 6.0f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
+}
 
 // 3D RK4 with tracers re-bundled by cell between episodes (advect_episodes.cu)
 cudaError_t launch_rk4_episodes(const RectParams &P, const lcs_field *f, const Rk4Args &A, const Rk4Launch &L,

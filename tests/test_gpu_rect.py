@@ -299,15 +299,28 @@ def test_cauchy_green_3d_matches_oracle_on_gpu_positions(ctx, abc_small):
         np.testing.assert_allclose(g["ftle"][0][ok], sig[ok].astype(np.float32), rtol=1e-6, atol=0)
 
 
-def test_abc_rebundled_equals_gather(ctx, abc_small):
-    # re-bundling tracers between episodes moves them between threads but not their arithmetic
+@pytest.mark.parametrize("storage", [lcs.F32, lcs.F16, lcs.BF16])
+@pytest.mark.parametrize("field_periodic", [(1, 1, 1), (0, 0, 0), (1, 0, 1)])
+def test_abc_rebundled_equals_gather(ctx, abc_small, storage, field_periodic):
+    # Re-bundling tracers between episodes moves them between threads but not their arithmetic, and
+    # the episode kernel's corner cache (stage 3 reusing stage 2's cell, stage 1 of the next step
+    # reusing stage 4's) reads exactly what a reload would: bit-identical to the one-pass kernel.
+    # A non-periodic field (the same samples on a bounded box) also sends tracers out of the box.
+    from dataclasses import replace
+    g = replace(abc_small, periodic=field_periodic)
     L = 2 * np.pi
-    n, lo, hi = (70, 61, 64), (0.0, 0.0, 0.0), (L, L, L)
-    a = gpu_run(ctx, abc_small, n, lo, hi, (1, 1, 1), 2.0, 0.02, variant=1)
-    b = gpu_run(ctx, abc_small, n, lo, hi, (1, 1, 1), 2.0, 0.02, variant=3)
-    np.testing.assert_array_equal(a["xyz"][0], b["xyz"][0])
+    if field_periodic == (1, 1, 1):
+        n, lo, hi, per = (70, 61, 64), (0.0, 0.0, 0.0), (L, L, L), (1, 1, 1)
+    else:
+        n, lo, hi, per = (70, 61, 64), (0.3, 0.2, 0.4), (5.5, 5.7, 5.6), (0, 0, 0)
+    a = gpu_run(ctx, g, n, lo, hi, per, 2.0, 0.02, variant=1, storage=storage)
+    b = gpu_run(ctx, g, n, lo, hi, per, 2.0, 0.02, variant=3, storage=storage, episode_steps=7)
     np.testing.assert_array_equal(a["status"][0], b["status"][0])
+    np.testing.assert_array_equal(a["t_exit"][0], b["t_exit"][0])
+    np.testing.assert_array_equal(a["xyz"][0], b["xyz"][0])
     np.testing.assert_array_equal(a["ftle"][0], b["ftle"][0])
+    if field_periodic != (1, 1, 1):
+        assert (a["status"][0] == lcs.TRACER_LEFT).any()
 
 
 def test_abc_shift_by_period(ctx, abc_small):
