@@ -41,10 +41,10 @@ WORKLOAD = ("3D time-modulated ABC flow, periodic 128^3 FP32 velocity grid, 64 f
 L = 2 * math.pi
 N_SIDE, N_GRID, N_FRAMES, T_END, DT = 256, 128, 64, 8.0, 0.02
 NSTEPS = int(round(T_END / DT))
-# algorithmic FP32 work of one RK4 tracer-step on trilinear, linear-in-time data (FMA = 2):
-# per stage evaluation 9 (cell coordinates) + 15 (weights) + 96 (8-corner sums, 3 comps, 2 frames)
-# + 10 (time blend) = 130; 4 evaluations + 18 (stage points) + 18 (update) = 556
-FLOP_PER_TRACER_STEP = 556
+# algorithmic FP32 work of one RK4 tracer-step on trilinear, linear-in-time data (the per-unit figure
+# of the measurement plan): per stage evaluation 7 lerps x 3 components x 2 frames = 84, the time
+# blend 6 and the weights ~10, about 100; 4 evaluations + ~40 for the RK4 stage points and update = 440
+FLOP_PER_TRACER_STEP = 440
 
 
 def parse():
@@ -331,7 +331,8 @@ def our_arm(args, rank, world, local):
                      "kernel": "ep_advect3_kernel (RK4 episode of %d steps)" % round(steps_per_launch),
                      "flop_per_launch": flops, "avg_launch_ms": adv_launch_s * 1e3, "launches": adv_launches,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, pk_kind),
-                     "limiter": "L1 data-pipe wavefronts of the stencil gathers (ncu: ~93% busy), not FP32 issue"},
+                     "limiter": "L1 data-pipe wavefronts of the stencil gathers (ncu: 90% busy) and instruction "
+                                "issue (76%; 223 of 644 instructions per tracer-step are FP32 arithmetic)"},
         "phases_ms_per_step": {k: v[0] / args.steps for k, v in phase.items()},
         "clocks": clocks,
         "e2e": {"value": world * N / e2e_el if e2e_t else None, "unit": "seeds/s", "h2d_bytes_per_step": h2d,
@@ -382,10 +383,10 @@ def our_arm(args, rank, world, local):
 C3_WORKLOAD = ("batched sliding-window FTLE on the double gyre (129x65 FP32, 101 frames): 32 t0 spaced 0.25, "
                "forward and backward, T in {2,4,8} (64 jobs), 2048x1024 seeds each (2^21), RK4 dt=0.05; "
                "one persistent launch in a CUDA graph with autotuned block/tile; FP64 FD + eigenvalue + FTLE")
-# algorithmic FP32 work of one RK4 tracer-step on bilinear, linear-in-time data (FMA = 2): per evaluation
-# 6 (cell coordinates) + 6 (weights) + 32 (4 corners x 2 components x 2 frames) + 6 (time blend) = 50;
-# 4 evaluations + 12 (stage points) + 12 (update) = 224
-FLOP_PER_TRACER_STEP_2D = 224
+# algorithmic FP32 work of one RK4 tracer-step on bilinear, linear-in-time data (the per-unit figure of
+# the measurement plan): per evaluation bilinear 24 + time 4 + weights ~6 = 34; 4 evaluations + ~28 for
+# the RK4 combination = 164
+FLOP_PER_TRACER_STEP_2D = 164
 
 
 def c3_arm(args, rank, world, local):
