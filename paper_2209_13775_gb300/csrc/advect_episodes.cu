@@ -206,36 +206,200 @@ __global__ void ep_slice_table_kernel(const SchedEntry *__restrict__ sched, int 
     *nsl = m;
 }
 
-__device__ __forceinline__ void blend_node(const char *pair, int v, float a, float *u)
+// Time slices (FP32 storage).  Slice j is the field blended to stage time stab[j]
+// (interp3p's arithmetic), as three component planes of xy-quads on a lattice extended by
+// a halo of SLICE_HALO nodes on each side of every periodic axis: plane c holds, at
+// extended node (I, J, K), the float4 (u_c(i, j, k), u_c(i1, j, k), u_c(i, j1, k), u_c(i1, j1, k))
+// with (i, j, k) the field node the extended node wraps to and i1, j1 the next node along
+// x and y (wrapped, or clamped on a closed axis).  A trilinear stencil is then two 16-byte
+// loads per component (its two z-rows), and stencil points a few cells outside the
+// periodic box need no index wrapping: the halo holds the wrapped values.
+#define SLICE_HALO 2
+
+struct SliceGeom {
+    int H[3];        // halo nodes on each side of an axis (periodic axes only)
+    int N[3];        // extended node counts n + 2H
+    long long nxy;   // N[0] * N[1]
+    long long nodes; // extended nodes of one plane
+};
+
+static SliceGeom slice_geom(const lcs_field *f)
 {
-    float va[3], vb[3];
-    Pair3<LCS_F32>::ld(pair, v, va, vb);
-    const float g = 1.0f - a;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) u[c] = a == 0.0f ? va[c] : tblend(va[c], vb[c], a, g);
+    SliceGeom G;
+    for (int d = 0; d < 3; ++d) {
+        G.H[d] = f->periodic[d] ? SLICE_HALO : 0;
+        G.N[d] = f->n[d] + 2 * G.H[d];
+    }
+    G.nxy = (long long)G.N[0] * G.N[1];
+    G.nodes = G.nxy * G.N[2];
+    return G;
 }
 
-// slice j = the field blended to stab[j] (interp3p's arithmetic), as three planes:
-// plane c, node v -> (u_c(v), u_c(v + x)), x wrapped on a periodic axis
-__global__ void ep_slice_fill_kernel(RectParams P, const char *__restrict__ pairs, size_t fstride, long long nodes,
-                                     const SchedEntry *__restrict__ stab, const int *__restrict__ nsl,
-                                     float2 *__restrict__ slices, size_t plane_stride)
+// field node of extended index I along an axis (any n >= 1: the halo may span several periods)
+__device__ __forceinline__ int slice_src(int I, int H, int n, bool per)
 {
-    const int j = blockIdx.y;
-    if (j >= *nsl) return;
+    if (!per) return I;
+    int i = (I - H) % n;
+    return i < 0 ? i + n : i;
+}
+
+// One thread per extended node writes that node's quads in every slice of the episode:
+// the four interval-pair records of its quad are read once per frame interval k and
+// blended to each slice time in registers, u = (1 - a) u_k + a u_{k+1} as interp3p blends
+// (u_k itself when a = 0), so the slices cost little more than their writes.
+__global__ void ep_slice_fill_kernel(RectParams P, SliceGeom G, const char *__restrict__ pairs, size_t fstride,
+                                     const SchedEntry *__restrict__ stab, const int *__restrict__ nsl,
+                                     float4 *__restrict__ slices, size_t plane_stride)
+{
     long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (v >= nodes) return;
-    const SchedEntry e = stab[j];
-    const char *pair = pairs + (size_t)e.k * fstride;
-    const int nx = P.n[0];
-    const int i = (int)(v % nx);
-    const int i1 = P.periodic[0] ? (i + 1 == nx ? 0 : i + 1) : min(i + 1, nx - 1);
-    float u0[3], u1[3];
-    blend_node(pair, (int)v, e.a, u0);
-    blend_node(pair, (int)(v - i + i1), e.a, u1);
-    float2 *base = slices + (size_t)j * 3 * plane_stride;
+    if (v >= G.nodes) return;
+    const int I = (int)(v % G.N[0]);
+    const int J = (int)((v / G.N[0]) % G.N[1]);
+    const int K = (int)(v / G.nxy);
+    const bool px = P.periodic[0], py = P.periodic[1];
+    const int i = slice_src(I, G.H[0], P.n[0], px);
+    const int jj = slice_src(J, G.H[1], P.n[1], py);
+    const int k = slice_src(K, G.H[2], P.n[2], P.periodic[2]);
+    const int i1 = px ? (i + 1 == P.n[0] ? 0 : i + 1) : min(i + 1, P.n[0] - 1);
+    const int j1 = py ? (jj + 1 == P.n[1] ? 0 : jj + 1) : min(jj + 1, P.n[1] - 1);
+    const long long zk = k * P.sz;
+    const int corner[4] = {(int)(i + jj * P.sy + zk), (int)(i1 + jj * P.sy + zk), (int)(i + j1 * P.sy + zk),
+                           (int)(i1 + j1 * P.sy + zk)};
+    const int m = __ldg(nsl);
+    float ua[4][3], ub[4][3];
+    int kc = -1;
+    for (int j = 0; j < m; ++j) {
+        const SchedEntry e = load_sched(stab + j);
+        if (e.k != kc) {
+            const char *pair = pairs + (size_t)e.k * fstride;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) base[c * plane_stride + v] = make_float2(u0[c], u1[c]);
+            for (int q = 0; q < 4; ++q) Pair3<LCS_F32>::ld(pair, corner[q], ua[q], ub[q]);
+            kc = e.k;
+        }
+        const float g = 1.0f - e.a;
+        float4 *base = slices + (size_t)j * 3 * plane_stride + v;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float u[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) u[q] = e.a == 0.0f ? ua[q][c] : tblend(ua[q][c], ub[q][c], e.a, g);
+            base[c * plane_stride] = make_float4(u[0], u[1], u[2], u[3]);
+        }
+    }
+}
+
+// Cell of x along axis d on the extended lattice, with the fraction f: the same s, floor and
+// f as axis_cell, so the weights are the same; a periodic index beyond the halo (a stencil
+// point more than SLICE_HALO - 1 cells outside the box) is wrapped first.
+template <int PM>
+__device__ __forceinline__ int axis_cell_ext(const RectParams &P, const SliceGeom &G, int d, float x, float &f)
+{
+    if (per_axis<PM>(P, d)) {
+        float s = (x - P.origin[d]) * P.inv_h[d];
+        float fl = floorf(s);
+        int i = (int)fl;
+        f = s - fl;
+        int e = i + G.H[d];
+        if ((unsigned)e > (unsigned)(G.N[d] - 2)) e = wrap_index_slow(i, P.n[d]) + G.H[d];
+        return e;
+    } else {
+        float xc = fminf(fmaxf(x, P.origin[d]), P.hi_node[d]);
+        float s = (xc - P.origin[d]) * P.inv_h[d];
+        int i = min((int)s, P.n[d] - 2);
+        f = s - (float)i;
+        return i;
+    }
+}
+
+// Trilinear weights of x (make_stencil's products) and the extended base node of its cell.
+template <int PM>
+__device__ __forceinline__ int stencil_ext(const RectParams &P, const SliceGeom &G, const float *x, float *w)
+{
+    float fx, fy, fz;
+    const int ix = axis_cell_ext<PM>(P, G, 0, x[0], fx);
+    const int iy = axis_cell_ext<PM>(P, G, 1, x[1], fy);
+    const int iz = axis_cell_ext<PM>(P, G, 2, x[2], fz);
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    const float a = gy * gz, b = fy * gz, c = gy * fz, d = fy * fz;
+    w[0] = gx * a;
+    w[1] = fx * a;
+    w[2] = gx * b;
+    w[3] = fx * b;
+    w[4] = gx * c;
+    w[5] = fx * c;
+    w[6] = gx * d;
+    w[7] = fx * d;
+    return ix + iy * G.N[0] + iz * (int)G.nxy;
+}
+
+// Corner cache: the two z-row quads of the 3 components of the cell a tracer's last stage
+// evaluation read, with the cell's extended base node and the slice they came from.
+// Stage 3 of an RK4 step reads the same slice as stage 2 (t_n + h/2), and stage 1 of step
+// n + 1 the same slice as stage 4 of step n (t_n + h) whenever the schedule gives both the
+// same (k, alpha); in a smooth flow the second point of each pair is almost always in the
+// same cell as the first, so its corners are already in registers.  The base node fixes
+// all eight corners, so a reuse reads exactly what a reload would: bit-identical results.
+struct QuadCache {
+    float4 q[2][3];
+    int v0;
+    int slice;
+};
+
+// u(x) from slice `slice` (3 planes of plane_stride quads at pl); the products and their
+// order are interp3p's: corners (i0,j0,k0), (i1,j0,k0), (i0,j1,k0), (i1,j1,k0), then k1.
+__device__ __forceinline__ void interp3q(int v0, const float *w, const float4 *__restrict__ pl, int slice,
+                                         size_t plane_stride, int nxy, QuadCache &cc, float *u)
+{
+    if (v0 != cc.v0 || slice != cc.slice) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cc.q[r][c] = __ldg(pl + c * plane_stride + (v0 + r * nxy));
+        cc.v0 = v0;
+        cc.slice = slice;
+    }
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            acc[c] = fmaf(w[4 * r], cc.q[r][c].x, acc[c]);
+            acc[c] = fmaf(w[4 * r + 1], cc.q[r][c].y, acc[c]);
+            acc[c] = fmaf(w[4 * r + 2], cc.q[r][c].z, acc[c]);
+            acc[c] = fmaf(w[4 * r + 3], cc.q[r][c].w, acc[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = acc[c];
+}
+
+// One RK4 step in 3D from slices m0, m1, m2 (stage times t_n, t_n + h/2, t_n + h).
+template <int PM>
+__device__ __forceinline__ void rk4_step3q(const RectParams &P, const SliceGeom &G, float *x, float h,
+                                           const float4 *__restrict__ slices, int m0, int m1, int m2, size_t ps,
+                                           QuadCache &cc)
+{
+    float k1[3], k2[3], k3[3], k4[3], y[3], w[8];
+    const float hh = 0.5f * h;
+    const size_t ss = 3 * ps;
+    const int nxy = (int)G.nxy;
+    int v = stencil_ext<PM>(P, G, x, w);
+    interp3q(v, w, slices + (size_t)m0 * ss, m0, ps, nxy, cc, k1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k1[c], x[c]);
+    v = stencil_ext<PM>(P, G, y, w);
+    interp3q(v, w, slices + (size_t)m1 * ss, m1, ps, nxy, cc, k2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k2[c], x[c]);
+    v = stencil_ext<PM>(P, G, y, w);
+    interp3q(v, w, slices + (size_t)m1 * ss, m1, ps, nxy, cc, k3);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[c] = fmaf(h, k3[c], x[c]);
+    v = stencil_ext<PM>(P, G, y, w);
+    interp3q(v, w, slices + (size_t)m2 * ss, m2, ps, nxy, cc, k4);
+    const float h6 = h * (1.0f / 6.0f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
 }
 
 // ---------------------------------------------------------------- advection
@@ -243,8 +407,8 @@ __global__ void ep_slice_fill_kernel(RectParams P, const char *__restrict__ pair
 // Steps [s0, min(s1, nsteps)) of every tracer record, then the cell key of its new
 // position for the next re-bundling.  SLICES: FP32 time slices; else interval pairs.
 template <int ST, bool SLICES, int PM>
-__global__ void __launch_bounds__(256, SLICES ? LCS_EP_MINB : LCS_EP_MINB_PAIRS) ep_advect3_kernel(RectParams P, const char *__restrict__ pairs,
-                                                         size_t fstride, const float2 *__restrict__ slices,
+__global__ void __launch_bounds__(256, SLICES ? LCS_EP_MINB : LCS_EP_MINB_PAIRS) ep_advect3_kernel(RectParams P, SliceGeom G, const char *__restrict__ pairs,
+                                                         size_t fstride, const float4 *__restrict__ slices,
                                                          size_t plane_stride, const int *__restrict__ smap, Rk4Args A,
                                                          Tracer *__restrict__ S, int job, int s0, int s1, int shift,
                                                          unsigned *__restrict__ keys, unsigned *__restrict__ hist)
@@ -259,7 +423,7 @@ __global__ void __launch_bounds__(256, SLICES ? LCS_EP_MINB : LCS_EP_MINB_PAIRS)
         const float h = A.job_h[job];
         const int e = min(s1, ns);
         const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
-        CornerCache cc;       // SLICES
+        QuadCache cc;         // SLICES
         cc.v0 = -1;
         cc.slice = -1;
         PairCache pc;         // interval pairs
@@ -269,7 +433,7 @@ __global__ void __launch_bounds__(256, SLICES ? LCS_EP_MINB : LCS_EP_MINB_PAIRS)
         for (int n = s0; n < e; ++n) {
             if constexpr (SLICES) {
                 const int *m = smap + 3 * (n - s0);
-                rk4_step3c<PM>(P, x, h, slices, __ldg(m), __ldg(m + 1), __ldg(m + 2), plane_stride, cc);
+                rk4_step3q<PM>(P, G, x, h, slices, __ldg(m), __ldg(m + 1), __ldg(m + 2), plane_stride, cc);
             } else {
                 SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1),
                            e2 = load_sched(sc + 3 * n + 2);
@@ -324,17 +488,20 @@ static int sort_shift(long long nodes)
     return shift;
 }
 
-static size_t slice_bytes(long long nodes, int E)
+// up to 3 distinct stage times per step, 3 component planes per slice
+static size_t slice_bytes(const SliceGeom &G, int E)
 {
-    return al256(8 * (size_t)nodes) * 9 * E + al256(sizeof(int) * 3 * E) + al256(sizeof(SchedEntry) * 3 * E) + 256;
+    return al256(16 * (size_t)G.nodes) * 9 * E + al256(sizeof(int) * 3 * E) + al256(sizeof(SchedEntry) * 3 * E) +
+           256;
 }
 
-size_t rk4_sorted_scratch_bytes(long long N, long long nodes, int storage, int E)
+size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int E)
 {
+    const long long nodes = f->nodes;
     long long nbins = ((nodes - 1) >> sort_shift(nodes)) + 1;
     long long nb = (nbins + SCAN_TILE - 1) / SCAN_TILE;
     size_t b = 2 * al256(sizeof(Tracer) * N) + al256(4 * N) + 2 * al256(4 * nbins) + al256(4 * nb);
-    if (storage == LCS_F32) b += slice_bytes(nodes, E);
+    if (f->storage == LCS_F32) b += slice_bytes(slice_geom(f), E);
     return b;
 }
 
@@ -362,13 +529,15 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
     unsigned *bsum = (unsigned *)p;
     p += al256(4 * nb);
     constexpr bool SL = ST == LCS_F32;
-    const size_t plane_stride = al256(8 * (size_t)f->nodes) / 8;
-    float2 *slices = nullptr;
+    const SliceGeom G = slice_geom(f);
+    if (SL && G.nodes > (1LL << 30)) return cudaErrorInvalidValue;
+    const size_t plane_stride = al256(16 * (size_t)G.nodes) / 16;
+    float4 *slices = nullptr;
     int *smap = nullptr, *nsl = nullptr;
     SchedEntry *stab = nullptr;
     if (SL) {
-        slices = (float2 *)p;
-        p += al256(8 * (size_t)f->nodes) * 9 * E;
+        slices = (float4 *)p;
+        p += al256(16 * (size_t)G.nodes) * 9 * E;
         smap = (int *)p;
         p += al256(sizeof(int) * 3 * E);
         stab = (SchedEntry *)p;
@@ -396,9 +565,8 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
             lcs_tm_begin(L.ctx, 2, s);
             if (SL) {
                 ep_slice_table_kernel<<<1, 32, 0, s>>>(A.sched, A.nsteps_max, job, s0, s1, smap, stab, nsl);
-                dim3 fg((unsigned)((f->nodes + 255) / 256), (unsigned)(3 * (s1 - s0)));
-                ep_slice_fill_kernel<<<fg, 256, 0, s>>>(P, (const char *)f->d_frames, f->frame_stride, f->nodes, stab,
-                                                         nsl, slices, plane_stride);
+                ep_slice_fill_kernel<<<(unsigned)((G.nodes + 255) / 256), 256, 0, s>>>(P, G, (const char *)f->d_frames, f->frame_stride, stab, nsl,
+                                                         slices, plane_stride);
             }
             lcs_tm_end(L.ctx, 2, s);
             lcs_tm_begin(L.ctx, 0, s);
@@ -407,13 +575,13 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
             unsigned *kk = last ? nullptr : keys;
             const char *pr = (const char *)f->d_frames;
             if (pm == 7)
-                ep_advect3_kernel<ST, SL, 7><<<agrid, abt, 0, s>>>(P, pr, f->frame_stride, slices, plane_stride, smap,
+                ep_advect3_kernel<ST, SL, 7><<<agrid, abt, 0, s>>>(P, G, pr, f->frame_stride, slices, plane_stride, smap,
                                                                    A, SB, job, s0, s1, shift, kk, hist);
             else if (pm == 0)
-                ep_advect3_kernel<ST, SL, 0><<<agrid, abt, 0, s>>>(P, pr, f->frame_stride, slices, plane_stride, smap,
+                ep_advect3_kernel<ST, SL, 0><<<agrid, abt, 0, s>>>(P, G, pr, f->frame_stride, slices, plane_stride, smap,
                                                                    A, SB, job, s0, s1, shift, kk, hist);
             else
-                ep_advect3_kernel<ST, SL, -1><<<agrid, abt, 0, s>>>(P, pr, f->frame_stride, slices, plane_stride,
+                ep_advect3_kernel<ST, SL, -1><<<agrid, abt, 0, s>>>(P, G, pr, f->frame_stride, slices, plane_stride,
                                                                     smap, A, SB, job, s0, s1, shift, kk, hist);
             lcs_tm_end(L.ctx, 0, s);
             Tracer *tmp = SA;

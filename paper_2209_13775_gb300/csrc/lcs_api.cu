@@ -637,7 +637,7 @@ static AdvectLayout advect_layout(const lcs_field *f, const lcs_seeds *s, const 
     Ly.sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
     Ly.want_sorted = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
     Ly.E = o->episode_steps > 0 ? std::min(o->episode_steps, 1024) : LCS_EPISODE_STEPS;
-    Ly.wb = Ly.want_sorted ? rk4_sorted_scratch_bytes(s->N, f->nodes, f->storage, Ly.E) : 0;
+    Ly.wb = Ly.want_sorted ? rk4_sorted_scratch_bytes(s->N, f, Ly.E) : 0;
     return Ly;
 }
 

@@ -206,7 +206,7 @@ struct Rk4Launch {
 // default RK4 steps per re-bundled episode
 #define LCS_EPISODE_STEPS 32
 
-size_t rk4_sorted_scratch_bytes(long long N, long long nodes, int storage, int episode_steps);
+size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int episode_steps);
 
 RectParams make_rect_params(const lcs_field *f);
 

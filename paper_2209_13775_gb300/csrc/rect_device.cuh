@@ -449,83 +449,13 @@ __device__ __forceinline__ void rk4_step3p(const RectParams &P, float *x, float 
     for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
 }
 
-// 3D time slices (the field blended to one stage time) are stored as three component
-// planes of x-neighbour pairs: plane c holds, at node (i, j, k), the pair
-// (u_c(i, j, k), u_c(i + 1, j, k)) (i + 1 wrapped on a periodic axis).  A corner row
-// (j, k) of the trilinear stencil is one 8-byte load per component, and the lanes of
-// a warp on neighbouring cells fall in the same sectors.  The products and their
-// summation order are those of interp3p (rows in order, i0 before i1).
-//
-// CornerCache: the 12 x-pairs (4 stencil rows x 3 components) of the cell a tracer's
-// last stage evaluation read, with the cell's base node and the slice they came from.  Stage 3 of
-// an RK4 step reads the same slice as stage 2 (t_n + h/2), and stage 1 of step n + 1 the
-// same slice as stage 4 of step n (t_n + h) whenever the schedule gives both the same
-// (k, alpha); in a smooth flow the second point of each pair is almost always in the
-// same cell as the first, so its corner values are already in registers.  A cell is
-// identified by its base node v[0] (the other seven corners follow from it), so a
-// reuse reads exactly what a reload would: the result is bit-identical.
-struct CornerCache {
-    float2 q[4][3];
-    int v0;
-    int slice;
-};
-
-__device__ __forceinline__ void interp3sc(const Stencil<3> &S, const float2 *__restrict__ pl, int slice,
-                                          size_t plane_stride, CornerCache &cc, float *u)
-{
-    if (S.v[0] != cc.v0 || slice != cc.slice) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) cc.q[r][c] = __ldg(pl + c * plane_stride + S.v[2 * r]);
-        cc.v0 = S.v[0];
-        cc.slice = slice;
-    }
-    float acc[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            acc[c] = fmaf(S.w[2 * r], cc.q[r][c].x, acc[c]);
-            acc[c] = fmaf(S.w[2 * r + 1], cc.q[r][c].y, acc[c]);
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) u[c] = acc[c];
-}
-
-// One RK4 step in 3D from time slices m0, m1, m2 (indices into `slices`, each 3 planes
-// of plane_stride pairs) at stage times t_n, t_n + h/2, t_n + h, through the corner cache.
-template <int PM = -1>
-__device__ __forceinline__ void rk4_step3c(const RectParams &P, float *x, float h, const float2 *__restrict__ slices,
-                                           int m0, int m1, int m2, size_t ps, CornerCache &cc)
-{
-    float k1[3], k2[3], k3[3], k4[3], y[3];
-    Stencil<3> S;
-    const float hh = 0.5f * h;
-    const size_t ss = 3 * ps;
-    make_stencil<3, PM>(P, x, S);
-    interp3sc(S, slices + (size_t)m0 * ss, m0, ps, cc, k1);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k1[c], x[c]);
-    make_stencil<3, PM>(P, y, S);
-    interp3sc(S, slices + (size_t)m1 * ss, m1, ps, cc, k2);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k2[c], x[c]);
-    make_stencil<3, PM>(P, y, S);
-    interp3sc(S, slices + (size_t)m1 * ss, m1, ps, cc, k3);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) y[c] = fmaf(h, k3[c], x[c]);
-    make_stencil<3, PM>(P, y, S);
-    interp3sc(S, slices + (size_t)m2 * ss, m2, ps, cc, k4);
-    const float h6 = h * (1.0f / 6.0f);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
-}
-
-// The corner cache of the interval-pair path (FP16/BF16 storage): the 8 corners of the
-// last evaluation's cell blended to its stage time (pair k, weight a), as interp3p
-// blends them, so a reuse gives the same products in the same order.
+// Corner cache of the interval-pair path (FP16/BF16 storage): the 8 corners of the cell a
+// tracer's last stage evaluation read, blended to its stage time (pair k, weight a) as
+// interp3p blends them.  Stage 3 of an RK4 step has the stage time of stage 2, and stage 1
+// of step n + 1 that of stage 4 of step n whenever the schedule gives both the same
+// (k, a); in a smooth flow the second point of each pair is almost always in the cell of
+// the first.  The base node v[0] fixes all eight corners, so a reuse gives the same
+// products in the same order as a reload: bit-identical results.
 struct PairCache {
     float u[8][3];
     int v0, k;
