@@ -323,6 +323,22 @@ def test_abc_rebundled_equals_gather(ctx, abc_small, storage, field_periodic):
         assert (a["status"][0] == lcs.TRACER_LEFT).any()
 
 
+@pytest.mark.parametrize("storage", [lcs.F32, lcs.F16])
+def test_abc_rebundled_batch_equals_gather(ctx, abc_small, storage):
+    # several jobs (forward, backward, ragged horizons) through the re-bundled path, each restarting
+    # the tracer records and the time slices: the one-pass kernel's flow maps bit for bit
+    L = 2 * np.pi
+    n, lo, hi = (40, 37, 35), (0.0, 0.0, 0.0), (L, L, L)
+    jobs = ([0.0, 0.3, 0.5, 1.1], [1.0, -0.6, 0.84, 0.1])
+    a = gpu_run(ctx, abc_small, n, lo, hi, (1, 1, 1), None, 0.02, jobs=jobs, variant=1, storage=storage)
+    b = gpu_run(ctx, abc_small, n, lo, hi, (1, 1, 1), None, 0.02, jobs=jobs, variant=3, storage=storage,
+                episode_steps=6)
+    for j in range(len(jobs[0])):
+        np.testing.assert_array_equal(a["xyz"][j], b["xyz"][j])
+        np.testing.assert_array_equal(a["status"][j], b["status"][j])
+        np.testing.assert_array_equal(a["ftle"][j], b["ftle"][j])
+
+
 def test_abc_shift_by_period(ctx, abc_small):
     # seeds shifted by 2 pi along x: the flow map shifts by exactly 2 pi (index-only wrap)
     L = 2 * np.pi
