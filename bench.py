@@ -331,8 +331,9 @@ def our_arm(args, rank, world, local):
                      "kernel": "ep_advect3_kernel (RK4 episode of %d steps)" % round(steps_per_launch),
                      "flop_per_launch": flops, "avg_launch_ms": adv_launch_s * 1e3, "launches": adv_launches,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, pk_kind),
-                     "limiter": "L1 data-pipe wavefronts of the stencil gathers (ncu: 90% busy) and instruction "
-                                "issue (76%; 223 of 644 instructions per tracer-step are FP32 arithmetic)"},
+                     "limiter": "latency of the stencil gathers (ncu, small case: long-scoreboard stalls lead; L1 "
+                                "data pipe 80%, issue 69%; 223 of 473 instructions per tracer-step are FP32 "
+                                "arithmetic)"},
         "phases_ms_per_step": {k: v[0] / args.steps for k, v in phase.items()},
         "clocks": clocks,
         "e2e": {"value": world * N / e2e_el if e2e_t else None, "unit": "seeds/s", "h2d_bytes_per_step": h2d,

@@ -14,23 +14,20 @@
 // does not depend on which thread runs it, so the flow map is bit-identical to the
 // one-pass kernel.
 //
-// Per episode (FP32 storage): the field is blended once to every distinct stage
-// time of the episode (a "time slice", stored as three component planes of
-// x-neighbour pairs); the advection then reads 8-byte entries of three planes per
-// stencil row.  FP16/BF16 storage reads the 16-byte interval pairs directly.
+// Per episode the field is blended once, in FP32, to every distinct stage time of the
+// episode (a "time slice", stored as three component planes of xy-quads on a lattice with
+// a halo on periodic axes); the advection then reads two 16-byte quads per component and
+// stencil, and keeps the last stencil's corners in registers for the next stage that
+// reads the same slice from the same cell.  FP16/BF16 storage is widened in the fill.
 #include "rect_device.cuh"
 
-// Resident 256-thread blocks per SM the advection kernel is compiled for, with time
-// slices (FP32) and with interval pairs (FP16/BF16): 4 caps both at 64 registers
-// (32 warps per SM).  Their stencil gathers are latency-bound, and the occupancy
-// pays more than the few bytes spilled cost (the full-size ABC workload: 217 -> 145 ms
-// per 400 steps with slices; 199 -> 173 ms with FP16 pairs).  5 (48 registers) is
-// slower again.
+// Resident 256-thread blocks per SM the advection kernel is compiled for: 4 caps it at
+// 64 registers (32 warps per SM).  Its stencil gathers are latency-bound, and the
+// occupancy pays more than the few bytes spilled cost (the full-size ABC workload:
+// 217 -> 145 ms per 400 steps when introduced); 5 (48 registers, more spills) and a
+// 56-register cap with 128-thread blocks (36 warps) are slower.
 #ifndef LCS_EP_MINB
 #define LCS_EP_MINB 4
-#endif
-#ifndef LCS_EP_MINB_PAIRS
-#define LCS_EP_MINB_PAIRS 4
 #endif
 
 // 32-byte tracer record: one sector per tracer for the re-bundling scatter
@@ -227,8 +224,8 @@ __global__ void ep_slice_table_kernel(const SchedEntry *__restrict__ sched, int 
     *nsl = m;
 }
 
-// Time slices (FP32 storage).  Slice j is the field blended to stage time stab[j]
-// (interp3p's arithmetic), as three component planes of xy-quads on a lattice extended by
+// Time slices.  Slice j is the field blended to stage time stab[j] in FP32 (interp3p's
+// arithmetic on the stored frames, widened from FP16/BF16 storage), as three component planes of xy-quads on a lattice extended by
 // a halo of SLICE_HALO nodes on each side of every periodic axis: plane c holds, at
 // extended node (I, J, K), the float4 (u_c(i, j, k), u_c(i1, j, k), u_c(i, j1, k), u_c(i1, j1, k))
 // with (i, j, k) the field node the extended node wraps to and i1, j1 the next node along
@@ -268,6 +265,7 @@ __device__ __forceinline__ int slice_src(int I, int H, int n, bool per)
 // the four interval-pair records of its quad are read once per frame interval k and
 // blended to each slice time in registers, u = (1 - a) u_k + a u_{k+1} as interp3p blends
 // (u_k itself when a = 0), so the slices cost little more than their writes.
+template <int ST>
 __global__ void ep_slice_fill_kernel(RectParams P, SliceGeom G, const char *__restrict__ pairs, size_t fstride,
                                      const SchedEntry *__restrict__ stab, const int *__restrict__ nsl,
                                      float4 *__restrict__ slices, size_t plane_stride)
@@ -294,7 +292,7 @@ __global__ void ep_slice_fill_kernel(RectParams P, SliceGeom G, const char *__re
         if (e.k != kc) {
             const char *pair = pairs + (size_t)e.k * fstride;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) Pair3<LCS_F32>::ld(pair, corner[q], ua[q], ub[q]);
+            for (int q = 0; q < 4; ++q) Pair3<ST>::ld(pair, corner[q], ua[q], ub[q]);
             kc = e.k;
         }
         const float g = 1.0f - e.a;
@@ -435,14 +433,16 @@ __device__ __forceinline__ void rk4_step3q(const RectParams &P, const SliceGeom 
 
 // ---------------------------------------------------------------- advection
 
-// Steps [s0, min(s1, nsteps)) of every tracer record, then the cell key of its new
-// position for the next re-bundling.  SLICES: FP32 time slices; else interval pairs.
-template <int ST, bool SLICES, int PM>
-__global__ void __launch_bounds__(256, SLICES ? LCS_EP_MINB : LCS_EP_MINB_PAIRS) ep_advect3_kernel(RectParams P, SliceGeom G, const char *__restrict__ pairs,
-                                                         size_t fstride, const float4 *__restrict__ slices,
-                                                         size_t plane_stride, const int *__restrict__ smap, Rk4Args A,
-                                                         Tracer *__restrict__ S, int job, int s0, int s1, int shift,
-                                                         unsigned *__restrict__ keys, unsigned *__restrict__ hist)
+// Steps [s0, min(s1, nsteps)) of every tracer record through the episode's time slices,
+// then the cell key of its new position for the next re-bundling.
+template <int PM>
+__global__ void __launch_bounds__(256, LCS_EP_MINB) ep_advect3_kernel(RectParams P, SliceGeom G,
+                                                                      const float4 *__restrict__ slices,
+                                                                      size_t plane_stride, const int *__restrict__ smap,
+                                                                      Rk4Args A, Tracer *__restrict__ S, int job,
+                                                                      int s0, int s1, int shift,
+                                                                      unsigned *__restrict__ keys,
+                                                                      unsigned *__restrict__ hist)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= A.N) return;
@@ -453,23 +453,12 @@ __global__ void __launch_bounds__(256, SLICES ? LCS_EP_MINB : LCS_EP_MINB_PAIRS)
         const int ns = A.job_nsteps[job];
         const float h = A.job_h[job];
         const int e = min(s1, ns);
-        const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
-        QuadCache cc;         // SLICES
+        QuadCache cc;
         cc.v0 = -1;
         cc.slice = -1;
-        PairCache pc;         // interval pairs
-        pc.v0 = -1;
-        pc.k = -1;
-        pc.a = 0.0f;
         for (int n = s0; n < e; ++n) {
-            if constexpr (SLICES) {
-                const int *m = smap + 3 * (n - s0);
-                rk4_step3q<PM>(P, G, x, h, slices, __ldg(m), __ldg(m + 1), __ldg(m + 2), plane_stride, cc);
-            } else {
-                SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1),
-                           e2 = load_sched(sc + 3 * n + 2);
-                rk4_step3pc<ST, PM>(P, x, h, pairs, fstride, e0, e1, e2, pc);
-            }
+            const int *m = smap + 3 * (n - s0);
+            rk4_step3q<PM>(P, G, x, h, slices, __ldg(m), __ldg(m + 1), __ldg(m + 2), plane_stride, cc);
             wrap_periodic<3, PM>(P, x, img);
             if (rect_left<3, PM>(P, x)) {
                 t.st = LCS_TRACER_LEFT;
@@ -532,7 +521,7 @@ size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int E)
     long long nbins = ((keys - 1) >> sort_shift(keys)) + 1;
     long long nb = (nbins + SCAN_TILE - 1) / SCAN_TILE;
     size_t b = 2 * al256(sizeof(Tracer) * N) + al256(4 * N) + 2 * al256(4 * nbins) + al256(4 * nb);
-    if (f->storage == LCS_F32) b += slice_bytes(slice_geom(f), E);
+    b += slice_bytes(slice_geom(f), E);
     return b;
 }
 
@@ -560,14 +549,13 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
     p += al256(4 * nbins);
     unsigned *bsum = (unsigned *)p;
     p += al256(4 * nb);
-    constexpr bool SL = ST == LCS_F32;
     const SliceGeom G = slice_geom(f);
-    if (SL && G.nodes > (1LL << 30)) return cudaErrorInvalidValue;
+    if (G.nodes > (1LL << 30)) return cudaErrorInvalidValue;
     const size_t plane_stride = al256(16 * (size_t)G.nodes) / 16;
     float4 *slices = nullptr;
     int *smap = nullptr, *nsl = nullptr;
     SchedEntry *stab = nullptr;
-    if (SL) {
+    {
         slices = (float4 *)p;
         p += al256(16 * (size_t)G.nodes) * 9 * E;
         smap = (int *)p;
@@ -595,26 +583,23 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
             if (!last) cudaMemsetAsync(hist, 0, 4 * nbins, s);
             lcs_tm_end(L.ctx, 1, s);
             lcs_tm_begin(L.ctx, 2, s);
-            if (SL) {
-                ep_slice_table_kernel<<<1, 32, 0, s>>>(A.sched, A.nsteps_max, job, s0, s1, smap, stab, nsl);
-                ep_slice_fill_kernel<<<(unsigned)((G.nodes + 255) / 256), 256, 0, s>>>(P, G, (const char *)f->d_frames, f->frame_stride, stab, nsl,
-                                                         slices, plane_stride);
-            }
+            ep_slice_table_kernel<<<1, 32, 0, s>>>(A.sched, A.nsteps_max, job, s0, s1, smap, stab, nsl);
+            ep_slice_fill_kernel<ST><<<(unsigned)((G.nodes + 255) / 256), 256, 0, s>>>(
+                P, G, (const char *)f->d_frames, f->frame_stride, stab, nsl, slices, plane_stride);
             lcs_tm_end(L.ctx, 2, s);
             lcs_tm_begin(L.ctx, 0, s);
             // compile-time periodicity for the common all-periodic and non-periodic boxes
             const int pm = P.periodic[0] | (P.periodic[1] << 1) | (P.periodic[2] << 2);
             unsigned *kk = last ? nullptr : keys;
-            const char *pr = (const char *)f->d_frames;
             if (pm == 7)
-                ep_advect3_kernel<ST, SL, 7><<<agrid, abt, 0, s>>>(P, G, pr, f->frame_stride, slices, plane_stride, smap,
-                                                                   A, SB, job, s0, s1, shift, kk, hist);
+                ep_advect3_kernel<7><<<agrid, abt, 0, s>>>(P, G, slices, plane_stride, smap, A, SB, job, s0, s1, shift,
+                                                          kk, hist);
             else if (pm == 0)
-                ep_advect3_kernel<ST, SL, 0><<<agrid, abt, 0, s>>>(P, G, pr, f->frame_stride, slices, plane_stride, smap,
-                                                                   A, SB, job, s0, s1, shift, kk, hist);
+                ep_advect3_kernel<0><<<agrid, abt, 0, s>>>(P, G, slices, plane_stride, smap, A, SB, job, s0, s1, shift,
+                                                          kk, hist);
             else
-                ep_advect3_kernel<ST, SL, -1><<<agrid, abt, 0, s>>>(P, G, pr, f->frame_stride, slices, plane_stride,
-                                                                    smap, A, SB, job, s0, s1, shift, kk, hist);
+                ep_advect3_kernel<-1><<<agrid, abt, 0, s>>>(P, G, slices, plane_stride, smap, A, SB, job, s0, s1,
+                                                           shift, kk, hist);
             lcs_tm_end(L.ctx, 0, s);
             Tracer *tmp = SA;
             SA = SB;

@@ -449,75 +449,6 @@ __device__ __forceinline__ void rk4_step3p(const RectParams &P, float *x, float 
     for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
 }
 
-// Corner cache of the interval-pair path (FP16/BF16 storage): the 8 corners of the cell a
-// tracer's last stage evaluation read, blended to its stage time (pair k, weight a) as
-// interp3p blends them.  Stage 3 of an RK4 step has the stage time of stage 2, and stage 1
-// of step n + 1 that of stage 4 of step n whenever the schedule gives both the same
-// (k, a); in a smooth flow the second point of each pair is almost always in the cell of
-// the first.  The base node v[0] fixes all eight corners, so a reuse gives the same
-// products in the same order as a reload: bit-identical results.
-struct PairCache {
-    float u[8][3];
-    int v0, k;
-    float a;
-};
-
-template <int ST>
-__device__ __forceinline__ void interp3pc(const Stencil<3> &S, const char *__restrict__ pairs, size_t fstride,
-                                          SchedEntry e, PairCache &cc, float *u)
-{
-    if (S.v[0] != cc.v0 || e.k != cc.k || __float_as_int(e.a) != __float_as_int(cc.a)) {
-        const char *fp = pairs + (size_t)e.k * fstride;
-        const float g = 1.0f - e.a;
-        float va[3], vb[3];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            Pair3<ST>::ld(fp, S.v[q], va, vb);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) cc.u[q][c] = e.a == 0.0f ? va[c] : tblend(va[c], vb[c], e.a, g);
-        }
-        cc.v0 = S.v[0];
-        cc.k = e.k;
-        cc.a = e.a;
-    }
-    float acc[3] = {0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] = fmaf(S.w[q], cc.u[q][c], acc[c]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) u[c] = acc[c];
-}
-
-// rk4_step3p through the corner cache: schedule entries e0, e1, e2 of stage times
-// t_n, t_n + h/2, t_n + h.
-template <int ST, int PM = -1>
-__device__ __forceinline__ void rk4_step3pc(const RectParams &P, float *x, float h, const char *__restrict__ pairs,
-                                            size_t fstride, SchedEntry e0, SchedEntry e1, SchedEntry e2,
-                                            PairCache &cc)
-{
-    float k1[3], k2[3], k3[3], k4[3], y[3];
-    Stencil<3> S;
-    const float hh = 0.5f * h;
-    make_stencil<3, PM>(P, x, S);
-    interp3pc<ST>(S, pairs, fstride, e0, cc, k1);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k1[c], x[c]);
-    make_stencil<3, PM>(P, y, S);
-    interp3pc<ST>(S, pairs, fstride, e1, cc, k2);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) y[c] = fmaf(hh, k2[c], x[c]);
-    make_stencil<3, PM>(P, y, S);
-    interp3pc<ST>(S, pairs, fstride, e1, cc, k3);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) y[c] = fmaf(h, k3[c], x[c]);
-    make_stencil<3, PM>(P, y, S);
-    interp3pc<ST>(S, pairs, fstride, e2, cc, k4);
-    const float h6 = h * (1.0f / 6.0f);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
-}
-
 // 3D RK4 with tracers re-bundled by cell between episodes (advect_episodes.cu)
 cudaError_t launch_rk4_episodes(const RectParams &P, const lcs_field *f, const Rk4Args &A, const Rk4Launch &L,
                                 cudaStream_t s);
