@@ -58,9 +58,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seeds-side", type=int, default=N_SIDE,
                    help="seed lattice side (default 256; smaller only for profiling captures)")
-    p.add_argument("--config", default="c2", choices=["c2", "c3", "c4", "c5"],
+    p.add_argument("--config", default="c2", choices=["c2", "c3", "c3x", "c4", "c5"],
                    help="c2: the 3D ABC workload (default, the headline); c3: the batched sliding-window "
-                        "workload; c4: adaptive DP5(4) on the tetrahedral pipe; c5: the learned surrogate")
+                        "workload; c3x: its full cross product of horizons from multi-horizon snapshots; "
+                        "c4: adaptive DP5(4) on the tetrahedral pipe; c5: the learned surrogate")
     p.add_argument("--train-epochs", type=int, default=4, help="c5: training epochs over the 50M samples")
     p.add_argument("--grid", type=int, default=N_GRID,
                    help="velocity grid side (default 128; smaller only for profiling captures)")
@@ -475,6 +476,109 @@ def c3_arm(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------- sliding windows, every horizon, snapshots
+
+C3X_WORKLOAD = ("sliding-window FTLE on the double gyre (129x65 FP32, 101 frames): 32 t0 spaced 0.25, forward and "
+                "backward, every horizon T in {2,4,8} (192 FTLE fields), 2048x1024 seeds each (2^21), RK4 dt=0.05; "
+                "one T=8 integration per (t0, direction) with snapshots at |T| = 2 and 4; FP64 FD + eigenvalue + FTLE")
+
+
+def c3x_arm(args, rank, world, local):
+    """The C3 field and lattice with the full cross product of horizons: 64 integrations of |T| = 8 whose
+    snapshots at |T| = 2 and 4 give the other 128 flow maps, against 192 separate integrations."""
+    import torch
+
+    from paper_2209_13775_gb300 import inputs, lcs
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = lcs.lcs_create(local, stream)
+    g = inputs.double_gyre()
+    field = lcs.lcs_load_field(ctx, lcs.field_desc(2, g.n, g.origin, g.spacing, g.periodic, g.times,
+                                                   g.time_periodic, g.period), g.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (2048, 1024), (0.0, 0.0), (2.0, 1.0)))
+    N = lcs.lcs_seeds_count(seeds)
+    t0s = [0.25 * k for k in range(32)] * 2
+    Ts = [8.0] * 32 + [-8.0] * 32
+    nj, snaps = len(t0s), [2.0, 4.0]
+    nslot = nj * (1 + len(snaps))
+    fm = lcs.lcs_flowmap_create(ctx, seeds, nslot)
+    cache = os.path.join(tempfile.gettempdir(), "lcs_tune_x_%d.txt" % os.getpid())
+    opts = lcs.advect_opts(lcs.RK4, dt=0.05, job_t0=t0s, job_T=Ts, snap_T=snaps)
+    lcs.lcs_autotune(ctx, field, seeds, opts, cache)
+    opts = lcs.advect_opts(lcs.RK4, dt=0.05, job_t0=t0s, job_T=Ts, snap_T=snaps, variant=opts.variant,
+                           block_threads=opts.block_threads, tracers_per_thread=opts.tracers_per_thread,
+                           use_graph=True)
+    ftle = torch.empty((nslot, N), dtype=torch.float32, device="cuda")
+
+    def step():
+        lcs.lcs_advect(ctx, field, seeds, opts, fm)
+        lcs.lcs_ftle(ctx, fm, -1, ftle)
+
+    for _ in range(args.warmup):
+        step()
+    lcs.lcs_synchronize(ctx)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+    el = a.elapsed_time(b) / 1e3
+    tracer_steps = N * nj * 160
+    # the same 192 FTLE fields as 192 separate integrations (one warm-up, one timed)
+    Ta = [sgn * h for sgn in (1.0, -1.0) for _ in range(32) for h in (2.0, 4.0, 8.0)]
+    t0a = [0.25 * k for k in range(32) for _ in range(3)] * 2
+    fm2 = lcs.lcs_flowmap_create(ctx, seeds, len(t0a))
+    o2 = lcs.advect_opts(lcs.RK4, dt=0.05, job_t0=t0a, job_T=Ta, variant=opts.variant,
+                         block_threads=opts.block_threads, tracers_per_thread=opts.tracers_per_thread)
+    ftle2 = torch.empty((len(t0a), N), dtype=torch.float32, device="cuda")
+    lcs.lcs_advect(ctx, field, seeds, o2, fm2)
+    lcs.lcs_ftle(ctx, fm2, -1, ftle2)
+    torch.cuda.synchronize()
+    a.record(stream)
+    lcs.lcs_advect(ctx, field, seeds, o2, fm2)
+    lcs.lcs_ftle(ctx, fm2, -1, ftle2)
+    b.record(stream)
+    torch.cuda.synchronize()
+    el2 = a.elapsed_time(b) / 1e3
+    # the snapshot fields are the separate runs' fields bit for bit (slot order differs)
+    same = True
+    for j in range(nj):
+        sgn = 1.0 if Ts[j] > 0 else -1.0
+        k = j % 32
+        base = (0 if sgn > 0 else 96) + 3 * k
+        pairs = [(j, base + 2), (nj + 2 * j, base), (nj + 2 * j + 1, base + 1)]
+        for p, q in pairs:
+            same = same and bool(torch.equal(ftle[p].nan_to_num(-7.0), ftle2[q].nan_to_num(-7.0)))
+    line = {
+        "metric": METRIC, "value": nslot * N * args.steps / el, "unit": "seeds/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": C3X_WORKLOAD, "integrations": nj, "ftle_fields": nslot, "seeds_per_field": N,
+                   "tracer_steps": tracer_steps,
+                   "tuned": {"variant": opts.variant, "block_threads": opts.block_threads,
+                             "tracers_per_thread": opts.tracers_per_thread}},
+        "tracer_steps_per_s": tracer_steps * args.steps / el,
+        "separate_runs": {"ms_per_step": el2 * 1e3, "seeds_per_s": nslot * N / el2,
+                          "tracer_steps": N * sum(int(round(abs(T) / 0.05)) for T in Ta),
+                          "snapshot_speedup": el2 / (el / args.steps), "bit_identical_ftle": same},
+        "clocks": clk.summary(),
+    }
+    lcs.lcs_free_flowmap(fm2)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    lcs.lcs_destroy(ctx)
+    try:
+        os.remove(cache)
+    except OSError:
+        pass
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------ tetrahedral RK45 arm
 
 C4_WORKLOAD = ("pipe on tetrahedra: Delaunay tets of a jittered lattice in a cylinder R=1, L=10 (h=0.0466), "
@@ -786,6 +890,9 @@ def main():
         return
     if args.config == "c3":
         c3_arm(args, rank, world, local)
+        return
+    if args.config == "c3x":
+        c3x_arm(args, rank, world, local)
         return
     if args.config == "c4":
         c4_arm(args, rank, world, local)

@@ -185,7 +185,17 @@ void lcs_free_seeds(lcs_seeds *seeds);
  *            rho > log10(gate_tol).  The RK4 arithmetic is that of LCS_RK4, so
  *            gate_tol = 0 reproduces it bit for bit.
  * Batches: njobs > 1 integrates the same seeds for each (job_t0[j], job_T[j])
- * pair in one persistent launch.                                            */
+ * pair in one persistent launch.
+ * Snapshots (LCS_RK4 on rectilinear fields): nsnap > 0 also keeps the flow
+ * map at intermediate horizons of every integration, so one run yields the
+ * Cauchy-Green tensor at several times (Sec. 3.1 and Sec. 4: the flow map of
+ * an interval from the steps of a longer integration).  Snapshot s of job j
+ * lands in flow-map slot njobs + j * nsnap + s and holds the state after
+ * min(|snap_T[s]|, |T_j|) / dt steps (position, status, exit time; a tracer
+ * that left before keeps its frozen state), with |T| = min(|snap_T[s]|, |T_j|)
+ * for lcs_ftle; it equals, bit for bit, a separate run with that horizon.
+ * The flow map then needs njobs * (1 + nsnap) slots.                       */
+#define LCS_MAX_SNAP 8
 typedef struct {
     int method;                 /* LCS_RK4 | LCS_RK45 | LCS_SURROGATE                */
     double t0, T;               /* single job (njobs <= 1)                            */
@@ -210,6 +220,9 @@ typedef struct {
                                    field, seeds, flow map and options come back      */
     double gate_tol;            /* LCS_SURROGATE: audit threshold (0 = every
                                    sub-interval by RK4, +inf = never)              */
+    int nsnap;                  /* 0..LCS_MAX_SNAP snapshots per integration        */
+    const double *snap_T;       /* HOST [nsnap]: horizon magnitudes, > 0, strictly
+                                   increasing, each a whole number of steps dt    */
 } lcs_advect_opts;
 
 /* Flow-map storage for `njobs` integrations of one lattice.                 */
@@ -220,7 +233,8 @@ lcs_status lcs_flowmap_create(lcs_ctx *ctx, const lcs_seeds *seeds, int njobs, l
  * frozen: rectilinear when more than one cell outside a non-periodic axis
  * after a step, at that step's end time; tets when a stage point falls
  * outside the mesh, at the start of that step).
- * Errors: LCS_EINVAL (options), LCS_EUNSUPPORTED, LCS_ECUDA.               */
+ * Errors: LCS_EINVAL (options, a flow map with too few slots),
+ * LCS_EUNSUPPORTED (e.g. snapshots with RK45, the surrogate or tets), LCS_ECUDA. */
 lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *seeds,
                       const lcs_advect_opts *opts, lcs_flowmap *fm);
 

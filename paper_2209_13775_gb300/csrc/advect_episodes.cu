@@ -433,6 +433,20 @@ __device__ __forceinline__ void rk4_step3q(const RectParams &P, const SliceGeom 
 
 // ---------------------------------------------------------------- advection
 
+// tracer record t into output slot `slot`; snap >= 0: the slot is snapshot entry snap
+// (job * nsnap + s) of the call, whose end time a tracer still OK records as its exit time
+__device__ __forceinline__ void ep_store(const RectParams &P, const Rk4Args &A, int slot, const Tracer &t, int snap)
+{
+    const long long N = A.N, id = t.id;
+    const float x[3] = {t.x, t.y, t.z};
+    const int img[3] = {t.ix, t.iy, t.iz};
+    float *o = A.out_xyz + (size_t)slot * 3 * N;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) o[d * N + id] = P.periodic[d] ? fmaf((float)img[d], P.L[d], x[d]) : x[d];
+    A.out_status[(size_t)slot * N + id] = t.st;
+    A.out_texit[(size_t)slot * N + id] = snap >= 0 && t.st == LCS_TRACER_OK ? __ldg(A.snap_te + snap) : t.te;
+}
+
 // Steps [s0, min(s1, nsteps)) of every tracer record through the episode's time slices,
 // then the cell key of its new position for the next re-bundling.
 template <int PM>
@@ -481,19 +495,26 @@ __global__ void __launch_bounds__(256, LCS_EP_MINB) ep_advect3_kernel(RectParams
     }
 }
 
-__global__ void ep_finalize_kernel(RectParams P, const Tracer *__restrict__ S, long long N, float *__restrict__ out_xyz,
-                                   unsigned char *__restrict__ out_st, float *__restrict__ out_te)
+// every tracer record into flow-map slot `slot` (snapshot entry snap, see ep_store): an episode
+// ends at each snapshot step before the end of the integration
+__global__ void ep_snapshot_kernel(RectParams P, const Tracer *__restrict__ S, Rk4Args A, int slot, int snap)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    if (i >= A.N) return;
+    ep_store(P, A, slot, S[i], snap);
+}
+
+// final state of every tracer record into slot `job`, and into the job's snapshot slots whose
+// horizon is the whole integration
+__global__ void ep_finalize_kernel(RectParams P, const Tracer *__restrict__ S, Rk4Args A, int job)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= A.N) return;
     const Tracer t = S[i];
-    const long long id = t.id;
-    const float x[3] = {t.x, t.y, t.z};
-    const int img[3] = {t.ix, t.iy, t.iz};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) out_xyz[d * N + id] = P.periodic[d] ? fmaf((float)img[d], P.L[d], x[d]) : x[d];
-    out_st[id] = t.st;
-    out_te[id] = t.te;
+    ep_store(P, A, job, t, -1);
+    const int ns = A.job_nsteps[job];
+    for (int q = 0; q < A.nsnap; ++q)
+        if (snap_step(A, q, ns) == ns) ep_store(P, A, snap_slot(A, job, q), t, job * A.nsnap + q);
 }
 
 // ------------------------------------------------------------------- driver
@@ -572,8 +593,16 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
         const int ns = L.host_nsteps[job];
         cudaMemsetAsync(hist, 0, 4 * nbins, s);
         ep_init_kernel<<<grid, bt, 0, s>>>(P, A.seeds, N, SA, A.job_tend, job, shift, keys, hist);
-        for (int s0 = 0; s0 < ns; s0 += E) {
-            const int s1 = s0 + E < ns ? s0 + E : ns;
+        int snext = 0;   // next snapshot before the end of the job: episodes end there
+        while (snext < L.nsnap && L.host_snap_n[snext] <= 0) ++snext;
+        for (int s0 = 0, s1; s0 < ns; s0 = s1) {
+            s1 = s0 + E < ns ? s0 + E : ns;
+            int snap_out = -1;
+            if (snext < L.nsnap && L.host_snap_n[snext] < ns && L.host_snap_n[snext] <= s1) {
+                s1 = L.host_snap_n[snext];
+                snap_out = L.njobs + job * L.nsnap + snext;
+                ++snext;
+            }
             const bool last = s1 >= ns;
             lcs_tm_begin(L.ctx, 1, s);
             scan_reduce_kernel<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum);
@@ -601,12 +630,13 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
                 ep_advect3_kernel<-1><<<agrid, abt, 0, s>>>(P, G, slices, plane_stride, smap, A, SB, job, s0, s1,
                                                            shift, kk, hist);
             lcs_tm_end(L.ctx, 0, s);
+            if (snap_out >= 0)
+                ep_snapshot_kernel<<<grid, bt, 0, s>>>(P, SB, A, snap_out, snap_out - L.njobs);
             Tracer *tmp = SA;
             SA = SB;
             SB = tmp;
         }
-        ep_finalize_kernel<<<grid, bt, 0, s>>>(P, SA, N, A.out_xyz + (size_t)job * 3 * N, A.out_status + (size_t)job * N,
-                                               A.out_texit + (size_t)job * N);
+        ep_finalize_kernel<<<grid, bt, 0, s>>>(P, SA, A, job);
     }
     return cudaGetLastError();
 }

@@ -71,6 +71,15 @@ __global__ void rk4_schedule_kernel(const double *__restrict__ times, int nf, in
         D.t0[j] = __double2float_rn(J.t0[j]);
         D.tend[j] = __double2float_rn(__dadd_rn(J.t0[j], J.T[j]));
         D.absT[j] = fabs(J.T[j]);
+        for (int q = 0; q < J.nsnap; ++q)   // snapshot slots: |T| of the horizon they hold
+            D.absT[J.njobs + j * J.nsnap + q] = fmin(J.snap_T[q], fabs(J.T[j]));
+        if (j == 0 && D.snap_n)
+            for (int q = 0; q < J.nsnap; ++q) D.snap_n[q] = J.snap_n[q];
+        if (D.snap_te)   // t0 + T of the horizon a snapshot holds, as a run with that horizon computes it
+            for (int q = 0; q < J.nsnap; ++q) {
+                const double a = fmin(J.snap_T[q], fabs(J.T[j]));
+                D.snap_te[j * J.nsnap + q] = __double2float_rn(__dadd_rn(J.t0[j], J.T[j] < 0.0 ? -a : a));
+            }
         if (D.order) D.order[j] = J.order[j];
         if (D.t0d) D.t0d[j] = J.t0[j];
         if (D.Td) D.Td[j] = J.T[j];
@@ -124,6 +133,7 @@ __global__ void __launch_bounds__(256) rk4_gather_kernel(RectParams P, const cha
     const float h = A.job_h[job];
     unsigned char st = LCS_TRACER_OK;
     float te = A.job_tend[job];
+    int si = 0;   // next snapshot
     for (int n = 0; n < ns; ++n) {
         SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
         if constexpr (DIM == 2)
@@ -140,7 +150,11 @@ __global__ void __launch_bounds__(256) rk4_gather_kernel(RectParams P, const cha
             te = fmaf((float)(n + 1), h, A.job_t0[job]);
             break;
         }
+        for (; si < A.nsnap && snap_step(A, si, ns) == n + 1; ++si)
+            store_tracer<DIM>(P, A, snap_slot(A, job, si), i, x, img, st, snap_exit(A, job, si, st, te));
     }
+    for (; si < A.nsnap; ++si)  // snapshots after the tracer stopped (or of a zero-step job)
+        store_tracer<DIM>(P, A, snap_slot(A, job, si), i, x, img, st, snap_exit(A, job, si, st, te));
     store_tracer<DIM>(P, A, job, i, x, img, st, te);
 }
 
@@ -255,6 +269,7 @@ __device__ __forceinline__ void ring_tile(const RectParams &P, const char *__res
     const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
     const int ns = A.job_nsteps[job];
     const float h = A.job_h[job];
+    int si = 0;   // next snapshot
     for (int n = 0; n < ns; ++n) {
         __syncthreads();  // every thread is done with the previous step's slots
         if (R.abort) break;
@@ -330,7 +345,19 @@ __device__ __forceinline__ void ring_tile(const RectParams &P, const char *__res
                 live[t] = false;
             }
         }
+        for (; si < A.nsnap && snap_step(A, si, ns) == n + 1; ++si)
+#pragma unroll
+            for (int t = 0; t < TPT; ++t)
+                if (active[t])
+                    store_tracer<2>(P, A, snap_slot(A, job, si), idx[t], x[t], img[t], st[t],
+                                    snap_exit(A, job, si, st[t], te[t]));
     }
+    for (; si < A.nsnap; ++si)  // a zero-step job, or a block that stopped on a copy timeout
+#pragma unroll
+        for (int t = 0; t < TPT; ++t)
+            if (active[t])
+                store_tracer<2>(P, A, snap_slot(A, job, si), idx[t], x[t], img[t], st[t],
+                                snap_exit(A, job, si, st[t], te[t]));
 #pragma unroll
     for (int t = 0; t < TPT; ++t)
         if (active[t]) store_tracer<2>(P, A, job, idx[t], x[t], img[t], st[t], te[t]);
@@ -469,6 +496,10 @@ int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
     A.out_xyz = L.out_xyz;
     A.out_status = L.out_status;
     A.out_texit = L.out_texit;
+    A.njobs = L.njobs;
+    A.nsnap = L.nsnap;
+    A.snap_n = L.snap_n;
+    A.snap_te = L.snap_te;
     if (L.N == 0 || L.njobs == 0) return 1;
     bool ring_fits = f->dim == 2 && RING_SLOTS * f->frame_stride <= ctx->smem_optin;
     bool sorted_ok = f->dim == 3 && L.work != nullptr;

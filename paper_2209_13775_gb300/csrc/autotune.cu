@@ -35,9 +35,10 @@ std::string signature(int device, const lcs_field *f, const lcs_seeds *s, const 
         smax = n > smax ? n : smax;
     }
     char buf[512];
-    snprintf(buf, sizeof buf, "%s|sm%d%d|dim%d|n%d,%d,%d|nf%d|st%d|per%d%d%d|N%lld|jobs%d|steps%lld|max%lld|m%d", prop.name,
-             prop.major, prop.minor, f->dim, f->n[0], f->n[1], f->n[2], f->nframes, f->storage, f->periodic[0],
-             f->periodic[1], f->periodic[2], s->N, njobs, steps, smax, o->method);
+    snprintf(buf, sizeof buf, "%s|sm%d%d|dim%d|n%d,%d,%d|nf%d|st%d|per%d%d%d|N%lld|jobs%d|steps%lld|max%lld|m%d|snap%d",
+             prop.name, prop.major, prop.minor, f->dim, f->n[0], f->n[1], f->n[2], f->nframes, f->storage,
+             f->periodic[0], f->periodic[1], f->periodic[2], s->N, njobs, steps, smax, o->method,
+             o->nsnap > 0 ? o->nsnap : 0);
     std::string sig = buf;
     for (auto &c : sig)
         if (c == ' ' || c == '\t' || c == '\n') c = '_';
@@ -125,7 +126,8 @@ extern "C" lcs_status lcs_autotune(lcs_ctx *ctx, const lcs_field *f, const lcs_s
                     cands.push_back({3, bt, 1, E});
     }
     lcs_flowmap *fm = nullptr;
-    lcs_status st = lcs_flowmap_create(ctx, s, njobs, &fm);
+    const int nsnap = o->nsnap > 0 && o->nsnap <= LCS_MAX_SNAP ? o->nsnap : 0;
+    lcs_status st = lcs_flowmap_create(ctx, s, njobs * (1 + nsnap), &fm);
     if (st != LCS_OK) return st;
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {

@@ -633,7 +633,8 @@ struct AdvectLayout {
 static AdvectLayout advect_layout(const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o, const JobTable &J)
 {
     AdvectLayout Ly;
-    Ly.jb = 2 * align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs) + 256;
+    Ly.jb = 2 * align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs) + 256 +
+            align256(sizeof(int) * LCS_MAX_SNAP) + align256(sizeof(float) * J.njobs * LCS_MAX_SNAP);
     Ly.sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
     Ly.want_sorted = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
     Ly.E = o->episode_steps > 0 ? std::min(o->episode_steps, 1024) : LCS_EPISODE_STEPS;
@@ -667,6 +668,10 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     p += align256(sizeof(int) * J.njobs);
     unsigned *queue = (unsigned *)p;
     p += 256;
+    D.snap_n = (int *)p;
+    p += align256(sizeof(int) * LCS_MAX_SNAP);
+    D.snap_te = (float *)p;
+    p += align256(sizeof(float) * J.njobs * LCS_MAX_SNAP);
     SchedEntry *sched = (SchedEntry *)p;
     CUDA_TRY(ctx, launch_rk4_schedule(f->d_times, f->nframes, f->time_periodic, f->period, J, D, sched, ctx->stream));
     Rk4Launch L;
@@ -691,6 +696,10 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.tracers_per_thread = o->tracers_per_thread >= 2 ? 2 : 1;
     L.queue = queue;
     L.job_order = D.order;
+    L.nsnap = J.nsnap;
+    L.snap_n = D.snap_n;
+    L.host_snap_n = J.snap_n;
+    L.snap_te = D.snap_te;
     L.work = want_sorted ? (char *)ctx->d_scratch + jb + sb : nullptr;
     if (f->kind == LCS_TET) {
         cudaError_t e = launch_rk4_tet(ctx, L, s->d_cells, o->walk_limit, ctx->stream);
@@ -806,6 +815,10 @@ static std::string graph_key(const lcs_ctx *ctx, const lcs_field *f, const lcs_s
         snprintf(buf, sizeof buf, "%a,%a;", J.t0[j], J.T[j]);
         k += buf;
     }
+    for (int q = 0; q < J.nsnap; ++q) {
+        snprintf(buf, sizeof buf, "s%d,%a;", J.snap_n[q], J.snap_T[q]);
+        k += buf;
+    }
     return k;
 }
 
@@ -875,6 +888,15 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
     if (fm->seeds != s) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: flow map was made for other seeds");
     int njobs = o->njobs > 1 ? o->njobs : 1;
     if (njobs > fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: %d jobs > flow map's %d", njobs, fm->njobs);
+    if (o->nsnap < 0 || o->nsnap > LCS_MAX_SNAP || (o->nsnap > 0 && !o->snap_T))
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: nsnap must be 0..%d with snap_T given", LCS_MAX_SNAP);
+    if (o->nsnap > 0) {
+        if (o->method != LCS_RK4 || f->kind != LCS_RECTILINEAR)
+            return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: snapshots need LCS_RK4 on a rectilinear field");
+        if ((long long)njobs * (1 + o->nsnap) > fm->njobs)
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: %d jobs with %d snapshots need %lld flow-map slots, not %d",
+                            njobs, o->nsnap, (long long)njobs * (1 + o->nsnap), fm->njobs);
+    }
     if (o->njobs > 1 && (!o->job_t0 || !o->job_T)) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: job arrays missing");
     if (o->method != LCS_RK4 && o->method != LCS_RK45 && o->method != LCS_SURROGATE)
         return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: method %d not built in", o->method);
@@ -908,6 +930,23 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
         J->nsteps_max = std::max(J->nsteps_max, (int)ns);
         fm->T[j] = T;
         J->order[j] = j;
+    }
+    J->nsnap = o->nsnap;
+    for (int q = 0; q < o->nsnap; ++q) {
+        const double a = o->snap_T[q], r = a / adt;
+        const long long n = (long long)floor(r + 0.5);
+        if (!(a > 0.0) || !isfinite(a) || fabs(r - (double)n) > 1e-9 * std::max(1.0, r) || n > (1LL << 30) ||
+            (q > 0 && !(a > o->snap_T[q - 1]))) {
+            delete J;
+            return lcs_fail(ctx, LCS_EINVAL,
+                            "lcs_advect: snap_T[%d] = %.17g must be > 0, increasing and a whole number of steps", q, a);
+        }
+        J->snap_n[q] = (int)n;
+        J->snap_T[q] = a;
+        for (int j = 0; j < njobs; ++j) {
+            const double Tj = J->T[j];
+            fm->T[njobs + j * o->nsnap + q] = Tj < 0.0 ? -std::min(a, -Tj) : std::min(a, Tj);
+        }
     }
     // work-queue order of the persistent kernel: longest integrations first
     std::stable_sort(J->order, J->order + njobs, [&](int a, int b) { return J->nsteps[a] > J->nsteps[b]; });

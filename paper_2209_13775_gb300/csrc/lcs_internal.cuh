@@ -161,6 +161,9 @@ struct JobTable {
     double T[LCS_MAX_JOBS];     // requested horizon
     int nsteps[LCS_MAX_JOBS];
     int order[LCS_MAX_JOBS];    // jobs by decreasing step count (work-queue order)
+    int nsnap = 0;              // snapshots per job (lcs_advect_opts.nsnap)
+    int snap_n[LCS_MAX_SNAP];   // their step counts |snap_T| / dt (capped per job at nsteps)
+    double snap_T[LCS_MAX_SNAP];// their horizon magnitudes
 };
 
 // per-job values the schedule kernel leaves in device scratch for the advection kernels
@@ -173,6 +176,8 @@ struct JobDev {
     int *order;      // [njobs] JobTable::order on the device, or null
     double *t0d;     // [njobs] FP64 start times, or null
     double *Td;      // [njobs] FP64 horizons, or null
+    int *snap_n = nullptr;  // [LCS_MAX_SNAP] snapshot step counts, or null
+    float *snap_te = nullptr;  // [njobs][nsnap] end time t0 + T of each snapshot (a tracer still OK there)
 };
 
 struct Rk4Launch {
@@ -199,6 +204,10 @@ struct Rk4Launch {
     int tracers_per_thread;   // ring kernels: 1 or 2
     unsigned *queue;          // variant 4: work-queue counter in device scratch, or null
     const int *job_order;     // variant 4: [njobs] jobs by decreasing step count (device), or null
+    int nsnap = 0;            // snapshots per job: slot njobs + job * nsnap + s after min(snap_n[s], nsteps)
+    const int *snap_n = nullptr;  // [nsnap] on the device (written by the schedule kernel)
+    const int *host_snap_n = nullptr;  // [nsnap] the same on the host
+    const float *snap_te = nullptr;    // [njobs][nsnap] snapshot end times (device)
 };
 
 // smallest seed count for which lcs_advect picks the re-bundled kernel by default

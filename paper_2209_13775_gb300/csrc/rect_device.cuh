@@ -338,7 +338,22 @@ struct Rk4Args {
     float *out_xyz;
     unsigned char *out_status;
     float *out_texit;
+    int njobs = 0;                   // jobs of the call: snapshot s of job j goes to slot njobs + j nsnap + s
+    int nsnap = 0;
+    const int *snap_n = nullptr;     // [nsnap] snapshot step counts (device; capped per job at use)
+    const float *snap_te = nullptr;  // [njobs][nsnap] snapshot end times, the exit time of a tracer OK there
 };
+
+// Step after which snapshot s of a job with ns steps is taken.
+__device__ __forceinline__ int snap_step(const Rk4Args &A, int s, int ns) { return min(__ldg(A.snap_n + s), ns); }
+
+__device__ __forceinline__ int snap_slot(const Rk4Args &A, int job, int s) { return A.njobs + job * A.nsnap + s; }
+
+// exit time recorded in snapshot s of a tracer with status st and exit time te
+__device__ __forceinline__ float snap_exit(const Rk4Args &A, int job, int s, unsigned char st, float te)
+{
+    return st == LCS_TRACER_OK ? __ldg(A.snap_te + job * A.nsnap + s) : te;
+}
 
 __device__ __forceinline__ SchedEntry load_sched(const SchedEntry *p)
 {

@@ -33,6 +33,7 @@ EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs
            "lcs_surrogate_train"]
 PHASE_ADVECT, PHASE_REBUNDLE, PHASE_SLICES, PHASE_CG = 0, 1, 2, 3
 NOALLOC_MAX_STEPS = 43680
+MAX_SNAP = 8
 MLP_NPARAMS = 50947
 
 
@@ -64,7 +65,7 @@ class AdvectOpts(ctypes.Structure):
                 ("h0", ctypes.c_double), ("max_steps", ctypes.c_longlong), ("walk_limit", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("variant", ctypes.c_int), ("surrogate", ctypes.c_void_p),
                 ("episode_steps", ctypes.c_int), ("tracers_per_thread", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("gate_tol", ctypes.c_double)]
+                ("gate_tol", ctypes.c_double), ("nsnap", ctypes.c_int), ("snap_T", ctypes.c_void_p)]
 
 
 _lib = None
@@ -252,7 +253,7 @@ def lcs_free_seeds(seeds):
 
 def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol=1e-6, atol=1e-6, h0=0.01,
                 max_steps=0, walk_limit=0, block_threads=0, variant=0, episode_steps=0, tracers_per_thread=0,
-                use_graph=False, surrogate=None, gate_tol=1e-3):
+                use_graph=False, surrogate=None, gate_tol=1e-3, snap_T=None):
     o = AdvectOpts()
     o.method, o.t0, o.T, o.dt = int(method), float(t0), float(T), float(dt)
     o.rtol, o.atol, o.h0, o.max_steps = float(rtol), float(atol), float(h0), int(max_steps)
@@ -262,14 +263,22 @@ def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol
     o.use_graph = int(bool(use_graph))
     o.surrogate = surrogate
     o.gate_tol = float(gate_tol)
+    keep = []
+    if snap_T is not None and len(snap_T) > 0:
+        sn = np.ascontiguousarray(snap_T, dtype=np.float64)
+        o.nsnap, o.snap_T = len(sn), sn.ctypes.data
+        keep.append(sn)
     if job_t0 is not None:
         a = np.ascontiguousarray(job_t0, dtype=np.float64)
         b = np.ascontiguousarray(job_T, dtype=np.float64)
         o.njobs = len(a)
         o.job_t0, o.job_T = a.ctypes.data, b.ctypes.data
-        o._keep = (a, b)
+        keep += [a, b]
+        if len(a) == 1:   # the library reads a single job from t0 and T
+            o.t0, o.T = float(a[0]), float(b[0])
     else:
         o.njobs = 1
+    o._keep = tuple(keep)
     return o
 
 
