@@ -273,7 +273,7 @@ lcs_status lcs_autotune(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *s
  * to outputs o: the displacement over one step tau is out_scale * (o0, o1), and
  * o2 = rho predicts log10 of that displacement's error.  It stands in for the
  * integrator over a sub-interval (the paper has no such network; the local
- * flow-map approximations it mentions among related work, Sec. 5, are the
+ * flow-map approximations it mentions among related work, Sec. 4, are the
  * nearest idea).  Parameters: LCS_MLP_NPARAMS FP32 values packed as
  *   W0[128][7] b0[128] W1[128][128] b1 W2 b2 W3 b3 W4[3][128] b4[3]
  * (row-major W[out][in]); the library keeps them in FP32 and computes with BF16

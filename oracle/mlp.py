@@ -7,7 +7,7 @@ gradients are written out layer by layer (reverse-mode chain rule), and the
 integrator targets come from the oracle's own RK4 (``oracle.rk4``).
 
 The surrogate is not in the paper.  Its role is the one of the local flow-map
-approximations mentioned among the related work (Sec. 5): a cheap map
+approximations mentioned among the related work (Sec. 4, Discussion): a cheap map
 x(t) -> x(t + tau) that replaces integration over one sub-interval, checked by an
 audit against the integrator (Eq. 2) and replaced by it where the check fails.
 
