@@ -84,6 +84,8 @@ def lib() -> ctypes.CDLL:
             L.ora_flowmap_gradient.argtypes = [I, P, P, P, P, P, P, P]
             L.ora_cauchy_green.argtypes = [I, LL, P, P]
             L.ora_eig_sym.argtypes = [I, P, P]
+            L.ora_eigvec_sym.argtypes = [I, P, P, P]
+            L.ora_cg_eigen.argtypes = [I, LL, P, P, P]
             L.ora_ftle.argtypes = [I, LL, P, D, P, P]
             L.ora_orient3d_exact.argtypes = [P, P, P, P]
             L.ora_tet_contains.argtypes = [P, LL, P, P]
@@ -342,6 +344,25 @@ def eig_sym(Cp, dim):
     e = np.empty(dim)
     lib().ora_eig_sym(dim, _p(Cp), _p(e))
     return e
+
+
+def eigvec_sym(Cp, dim):
+    """Eigenvalues (ascending) and unit eigenvectors (rows) of one packed symmetric matrix."""
+    Cp = np.ascontiguousarray(Cp, dtype=np.float64)
+    e = np.empty(dim)
+    v = np.empty((dim, dim))
+    lib().ora_eigvec_sym(dim, _p(Cp), _p(e), _p(v))
+    return e, v
+
+
+def cg_eigen(C, dim):
+    """Eigenvalues [N][dim] (ascending) and eigenvectors [N][dim][dim] (row k: that of eigenvalue k)."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    N = C.shape[0]
+    e = np.empty((N, dim))
+    v = np.empty((N, dim, dim))
+    lib().ora_cg_eigen(dim, N, _p(C), _p(e), _p(v))
+    return e, v
 
 
 def ftle(C, dim, T):

@@ -830,10 +830,12 @@ void ora_cauchy_green(int dim, long long n, const double *grad, double *C)
     }
 }
 
-/* cyclic Jacobi eigenvalue iteration (Golub & Van Loan, Sec. 8.5) */
-int ora_eig_sym(int dim, const double *Cp, double *eig)
+/* cyclic Jacobi eigenvalue iteration (Golub & Van Loan, Sec. 8.5); with vec != NULL the
+ * rotations are also accumulated, V <- V J, so column i of V is the eigenvector of A[i][i]
+ * (Sec. 2 "Cauchy-Green": eigenvalues and eigenvectors of C at each seed) */
+int ora_eigvec_sym(int dim, const double *Cp, double *eig, double *vec)
 {
-    double A[3][3];
+    double A[3][3], V[3][3];
     int o = 0;
     for (int i = 0; i < dim; ++i)
         for (int j = i; j < dim; ++j) {
@@ -842,8 +844,12 @@ int ora_eig_sym(int dim, const double *Cp, double *eig)
             o++;
         }
     for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    for (int i = 0; i < dim; ++i)
         if (isnan(A[i][i])) {
             for (int r = 0; r < dim; ++r) eig[r] = NAN;
+            if (vec)
+                for (int r = 0; r < dim * dim; ++r) vec[r] = NAN;
             return 0;
         }
     int sweep;
@@ -873,17 +879,39 @@ int ora_eig_sym(int dim, const double *Cp, double *eig)
                     A[p][k] = c * apk - s * aqk;
                     A[q][k] = s * apk + c * aqk;
                 }
+                for (int k = 0; k < dim; ++k) {
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
             }
     }
+    int idx[3] = {0, 1, 2};
     for (int i = 0; i < dim; ++i) eig[i] = A[i][i];
-    for (int i = 0; i < dim; ++i) /* ascending insertion sort */
+    for (int i = 0; i < dim; ++i) /* ascending insertion sort, carrying the columns */
         for (int j = i + 1; j < dim; ++j)
             if (eig[j] < eig[i]) {
                 double tmp = eig[i];
                 eig[i] = eig[j];
                 eig[j] = tmp;
+                int ti = idx[i];
+                idx[i] = idx[j];
+                idx[j] = ti;
             }
+    if (vec)
+        for (int k = 0; k < dim; ++k)
+            for (int r = 0; r < dim; ++r) vec[k * dim + r] = V[r][idx[k]];
     return sweep;
+}
+
+int ora_eig_sym(int dim, const double *Cp, double *eig) { return ora_eigvec_sym(dim, Cp, eig, NULL); }
+
+/* eigenvalues (ascending) and unit eigenvectors of n packed tensors */
+void ora_cg_eigen(int dim, long long n, const double *C, double *eig, double *vec)
+{
+    int np = (dim == 2) ? 3 : 6;
+#pragma omp parallel for schedule(static)
+    for (long long p = 0; p < n; ++p) ora_eigvec_sym(dim, C + p * np, eig + p * dim, vec + p * dim * dim);
 }
 
 void ora_ftle(int dim, long long n, const double *C, double T, double *lambda_max, double *ftle)

@@ -167,6 +167,13 @@ void ora_cauchy_green(int dim, long long n, const double *grad, double *C);
  * rotations to convergence; ascending order.  Returns sweeps used.          */
 int ora_eig_sym(int dim, const double *Cpacked, double *eig);
 
+/* The same with eigenvectors (Sec. 2 "Cauchy-Green"): vec[k * dim + r] is
+ * component r of the unit eigenvector of eig[k] (vec may be NULL).          */
+int ora_eigvec_sym(int dim, const double *Cpacked, double *eig, double *vec);
+
+/* ora_eigvec_sym over n packed tensors: eig [n][dim], vec [n][dim][dim].     */
+void ora_cg_eigen(int dim, long long n, const double *C, double *eig, double *vec);
+
 /* FTLE from the largest eigenvalue of C: sigma = ln(sqrt(lambda_max)) / |T|.
  * lambda_max out (may be NULL); NaN in C gives NaN.                         */
 void ora_ftle(int dim, long long n, const double *C, double T, double *lambda_max, double *ftle);

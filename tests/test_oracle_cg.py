@@ -167,3 +167,55 @@ def test_oracle_matches_stored_gyre_fixture(ora):
     spec.loader.exec_module(mg)
     stored = np.loadtxt(os.path.join(here, "gyre_ftle_32x16.txt"))
     np.testing.assert_allclose(mg.gyre_ftle_32x16(), stored, rtol=1e-12, atol=1e-13)
+
+
+def _packed(M):
+    return [M[0, 0], M[0, 1], M[1, 1]] if M.shape[0] == 2 else [M[0, 0], M[0, 1], M[0, 2], M[1, 1], M[1, 2], M[2, 2]]
+
+
+def test_eigvec_2x2_closed_form(ora):
+    # eigenvector of lambda_max of [[a, b], [b, c]] is (b, lambda_max - a) normalised (up to sign)
+    rng = np.random.default_rng(9)
+    for _ in range(100):
+        a, b, c = rng.normal(size=3) * [3, 2, 1]
+        e, v = ora.eigvec_sym([a, b, c], 2)
+        e0 = ora.eig_sym([a, b, c], 2)
+        np.testing.assert_array_equal(e, e0)   # the eigenvalues are the same arithmetic
+        u = np.array([b, e[1] - a])
+        u /= np.linalg.norm(u)
+        assert abs(abs(v[1] @ u) - 1.0) < 1e-12
+        assert abs(v[0] @ v[1]) < 1e-13
+
+
+@pytest.mark.parametrize("logk", [0, 4, 8, 14])
+def test_eigvec_3x3_known_basis(ora, logk):
+    # Q diag(lam) Q^T with a random orthogonal Q: eigenvector k is column k of Q up to sign, the
+    # residual |M v - lam v| is at rounding level of lam_max, and V is orthonormal
+    rng = np.random.default_rng(20 + logk)
+    for _ in range(20):
+        Q = ortho_group.rvs(3, random_state=rng)
+        lam = np.sort(np.array([1.0, 10 ** (-logk / 2), 10 ** (-logk)]) * rng.uniform(0.5, 2))
+        if logk == 0:
+            lam = np.array([0.5, 1.0, 2.0]) * rng.uniform(0.5, 2)   # distinct eigenvalues
+        M = Q @ np.diag(lam) @ Q.T
+        e, v = ora.eigvec_sym(_packed(M), 3)
+        np.testing.assert_allclose(v @ v.T, np.eye(3), atol=1e-14)
+        for k in range(3):
+            assert np.linalg.norm(M @ v[k] - e[k] * v[k]) <= 1e-14 * lam[2] * 8
+        # the top eigenvector is well separated for every logk
+        assert abs(abs(v[2] @ Q[:, 2]) - 1.0) < 1e-12
+
+
+def test_cg_eigen_batch_and_nan(ora):
+    rng = np.random.default_rng(11)
+    G = rng.normal(size=(5, 3, 3))
+    C = ora.cauchy_green(G)
+    C[3] = np.nan
+    e, v = ora.cg_eigen(C, 3)
+    for p in (0, 1, 2, 4):
+        e1, v1 = ora.eigvec_sym(C[p], 3)
+        np.testing.assert_array_equal(e[p], e1)
+        np.testing.assert_array_equal(v[p], v1)
+        # eigenvalues of G^T G are the squared singular values of G
+        np.testing.assert_allclose(e[p], np.sort(np.linalg.svd(G[p], compute_uv=False) ** 2), rtol=1e-12)
+    assert np.isnan(e[3]).all() and np.isnan(v[3]).all()
