@@ -369,6 +369,18 @@ lcs_status lcs_cauchy_green(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double
 lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
                     double *C, int on_device);
 
+/* Eigenvalues and eigenvectors of C at every seed (Sec. 2 "Cauchy-Green":
+ * the filter computes the eigenvalues and eigenvectors of the CG tensor at
+ * each seed point), C as lcs_cauchy_green.  eigval [N][dim] FP64 in
+ * ascending order; eigvec [N][dim][dim] FP64, eigvec[(p*dim + k)*dim + r]
+ * = component r of the unit eigenvector of eigval[p][k], its largest-magnitude
+ * component positive.  Cyclic Jacobi rotations in FP64 to a relative
+ * off-diagonal threshold (16 sweeps at most).  NaN where C is undefined.
+ * Either output may be NULL; job = -1 writes every job.
+ * Errors: LCS_EINVAL, LCS_ECUDA.                                            */
+lcs_status lcs_cg_eigen(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double *eigval, double *eigvec,
+                        int on_device);
+
 /* ------------------------------------------------------------ kernel timing */
 
 /* Time the library's kernels by phase with CUDA events recorded on the

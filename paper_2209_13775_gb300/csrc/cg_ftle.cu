@@ -123,7 +123,92 @@ __device__ __forceinline__ double eig_max3(const double *C)
     return (q + p * beta) * is;
 }
 
+// All eigenpairs of the packed symmetric C by cyclic Jacobi rotations in FP64.  Each
+// rotation zeroes a_pq with t = tan(theta) the smaller root of t^2 + 2 tau t - 1 = 0,
+// tau = (a_qq - a_pp) / (2 a_pq), updates the diagonal as a_pp - t a_pq and a_qq + t a_pq
+// (Rutishauser's form), rotates the other row of the pair and accumulates V <- V J.  A pair
+// counts as converged when |a_pq| <= 1e-18 sqrt(|a_pp a_qq|), a relative test that keeps
+// the small eigenvalues of a graded C accurate; at most 16 sweeps.  Ascending order, each
+// eigenvector with its largest-magnitude component positive.
 template <int DIM>
+__device__ __forceinline__ void eig_jacobi(const double *Cp, double *ev, double *V)
+{
+    double A[DIM][DIM];
+    int o = 0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = i; j < DIM; ++j) {
+            A[i][j] = Cp[o];
+            A[j][i] = Cp[o];
+            ++o;
+        }
+    double W[DIM][DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) W[i][j] = i == j ? 1.0 : 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) bad |= isnan(A[i][i]);
+    for (int sweep = 0; sweep < 16 && !bad; ++sweep) {
+        bool rotated = false;
+#pragma unroll
+        for (int p = 0; p < DIM - 1; ++p)
+#pragma unroll
+            for (int q = p + 1; q < DIM; ++q) {
+                const double apq = A[p][q];
+                if (!(fabs(apq) > 1e-18 * sqrt(fabs(A[p][p] * A[q][q])))) continue;
+                rotated = true;
+                const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
+                const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
+                const double c = rsqrt(fma(t, t, 1.0)), s = t * c;
+                A[p][p] = fma(-t, apq, A[p][p]);
+                A[q][q] = fma(t, apq, A[q][q]);
+                A[p][q] = A[q][p] = 0.0;
+#pragma unroll
+                for (int r = 0; r < DIM; ++r) {
+                    if (r == p || r == q) continue;
+                    const double arp = A[r][p], arq = A[r][q];
+                    A[r][p] = A[p][r] = c * arp - s * arq;
+                    A[r][q] = A[q][r] = s * arp + c * arq;
+                }
+#pragma unroll
+                for (int r = 0; r < DIM; ++r) {
+                    const double wp = W[r][p], wq = W[r][q];
+                    W[r][p] = c * wp - s * wq;
+                    W[r][q] = s * wp + c * wq;
+                }
+            }
+        if (!rotated) break;
+    }
+    int ord[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) ord[i] = i;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = i + 1; j < DIM; ++j)
+            if (A[ord[j]][ord[j]] < A[ord[i]][ord[i]]) {
+                const int t = ord[i];
+                ord[i] = ord[j];
+                ord[j] = t;
+            }
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        int m = 0;
+#pragma unroll
+        for (int r = 1; r < DIM; ++r)
+            if (fabs(W[r][ord[k]]) > fabs(W[m][ord[k]])) m = r;
+        const double sg = W[m][ord[k]] < 0.0 ? -1.0 : 1.0;
+        ev[k] = bad ? nan : A[ord[k]][ord[k]];
+#pragma unroll
+        for (int r = 0; r < DIM; ++r) V[k * DIM + r] = bad ? nan : sg * W[r][ord[k]];
+    }
+}
+
+template <int DIM, bool EIG>
 __global__ void __launch_bounds__(256) cg_ftle_kernel(CgLaunch L)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -189,6 +274,19 @@ __global__ void __launch_bounds__(256) cg_ftle_kernel(CgLaunch L)
 #pragma unroll
         for (int q = 0; q < NP; ++q) L.C[out * NP + q] = C[q];
     }
+    if constexpr (EIG) {   // lcs_cg_eigen
+        double ev[DIM], V[DIM * DIM];
+        eig_jacobi<DIM>(C, ev, V);
+        if (L.eigval) {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) L.eigval[out * DIM + k] = ev[k];
+        }
+        if (L.eigvec) {
+#pragma unroll
+            for (int k = 0; k < DIM * DIM; ++k) L.eigvec[out * DIM * DIM + k] = V[k];
+        }
+        return;
+    }
     if (L.lam || L.ftle) {
         const double lm = DIM == 2 ? eig_max2(C) : eig_max3(C);
         if (L.lam) L.lam[out] = lm;
@@ -207,9 +305,10 @@ cudaError_t launch_cg_ftle(const CgLaunch &L0, cudaStream_t s)
     }
     int bt = 256;
     dim3 grid((unsigned)((L.N + bt - 1) / bt), (unsigned)L.njobs);
+    const bool eig = L.eigval || L.eigvec;
     if (L.dim == 2)
-        cg_ftle_kernel<2><<<grid, bt, 0, s>>>(L);
+        eig ? cg_ftle_kernel<2, true><<<grid, bt, 0, s>>>(L) : cg_ftle_kernel<2, false><<<grid, bt, 0, s>>>(L);
     else
-        cg_ftle_kernel<3><<<grid, bt, 0, s>>>(L);
+        eig ? cg_ftle_kernel<3, true><<<grid, bt, 0, s>>>(L) : cg_ftle_kernel<3, false><<<grid, bt, 0, s>>>(L);
     return cudaGetLastError();
 }

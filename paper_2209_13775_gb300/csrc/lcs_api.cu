@@ -984,7 +984,7 @@ extern "C" lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int j
 // ------------------------------------------------------ grad F, C, FTLE
 
 static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lam, double *C,
-                          int on_device, const char *who)
+                          int on_device, const char *who, double *eigval = nullptr, double *eigvec = nullptr)
 {
     if (!ctx) return LCS_EINVAL;
     if (!fm) return lcs_fail(ctx, LCS_EINVAL, "%s: null flow map", who);
@@ -1010,17 +1010,25 @@ static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *f
     L.xyz = fm->d_xyz;
     L.status = fm->d_status;
     L.absT = fm->d_absT;
+    const size_t dim = (size_t)fm->dim;
     size_t bC = C ? sizeof(double) * np * N * nj : 0, bL = lam ? sizeof(double) * N * nj : 0,
-           bF = ftle ? sizeof(float) * N * nj : 0;
+           bF = ftle ? sizeof(float) * N * nj : 0, bE = eigval ? sizeof(double) * dim * N * nj : 0,
+           bV = eigvec ? sizeof(double) * dim * dim * N * nj : 0;
     char *tmp = nullptr;
-    if (!on_device && (bC + bL + bF) > 0)
-        CUDA_TRY(ctx, cudaMallocAsync((void **)&tmp, align256(bC) + align256(bL) + align256(bF), ctx->stream));
+    if (!on_device && (bC + bL + bF + bE + bV) > 0)
+        CUDA_TRY(ctx, cudaMallocAsync((void **)&tmp,
+                                      align256(bC) + align256(bL) + align256(bF) + align256(bE) + align256(bV),
+                                      ctx->stream));
     char *q = tmp;
     L.C = C ? (on_device ? C : (double *)q) : nullptr;
     if (C && !on_device) q += align256(bC);
     L.lam = lam ? (on_device ? lam : (double *)q) : nullptr;
     if (lam && !on_device) q += align256(bL);
     L.ftle = ftle ? (on_device ? ftle : (float *)q) : nullptr;
+    if (ftle && !on_device) q += align256(bF);
+    L.eigval = eigval ? (on_device ? eigval : (double *)q) : nullptr;
+    if (eigval && !on_device) q += align256(bE);
+    L.eigvec = eigvec ? (on_device ? eigvec : (double *)q) : nullptr;
     lcs_tm_begin(ctx, 3, ctx->stream);
     cudaError_t e = launch_cg_ftle(L, ctx->stream);
     lcs_tm_end(ctx, 3, ctx->stream);
@@ -1028,6 +1036,10 @@ static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *f
         if (C) e = cudaMemcpyAsync(C, L.C, bC, cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess && lam) e = cudaMemcpyAsync(lam, L.lam, bL, cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess && ftle) e = cudaMemcpyAsync(ftle, L.ftle, bF, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && eigval)
+            e = cudaMemcpyAsync(eigval, L.eigval, bE, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && eigvec)
+            e = cudaMemcpyAsync(eigvec, L.eigvec, bV, cudaMemcpyDeviceToHost, ctx->stream);
     }
     if (tmp) cudaFreeAsync(tmp, ctx->stream);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(ctx->stream);
@@ -1046,4 +1058,11 @@ extern "C" lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, flo
 {
     if (ctx && !ftle) return lcs_fail(ctx, LCS_EINVAL, "lcs_ftle: null output");
     return cg_call(ctx, fm, job, ftle, lambda_max, C, on_device, "lcs_ftle");
+}
+
+extern "C" lcs_status lcs_cg_eigen(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double *eigval, double *eigvec,
+                                   int on_device)
+{
+    if (ctx && !eigval && !eigvec) return lcs_fail(ctx, LCS_EINVAL, "lcs_cg_eigen: null outputs");
+    return cg_call(ctx, fm, job, nullptr, nullptr, nullptr, on_device, "lcs_cg_eigen", eigval, eigvec);
 }

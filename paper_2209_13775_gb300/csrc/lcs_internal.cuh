@@ -246,6 +246,8 @@ struct CgLaunch {
     double *C;                   // [njobs][N][np] or null
     double *lam;                 // [njobs][N] or null
     float *ftle;                 // [njobs][N] or null
+    double *eigval;              // [njobs][N][dim] or null (lcs_cg_eigen)
+    double *eigvec;              // [njobs][N][dim][dim] or null
 };
 
 cudaError_t launch_cg_ftle(const CgLaunch &L, cudaStream_t s);

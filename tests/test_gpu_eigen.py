@@ -1,0 +1,121 @@
+"""Eigenvalues and eigenvectors of the Cauchy-Green tensor at every seed (Sec. 2 "Cauchy-Green")
+through lcs_cg_eigen, against the FP64 oracle's Jacobi eigen-decomposition of the same C.
+
+C itself is bit-identical to the oracle's from the same FP32 positions (lcs_cauchy_green), so the
+comparison isolates the eigen-solver: eigenvalues to 1e-12 of lambda_max (and 1e-10 relative for the
+small ones), eigenvectors to 1e-10 in direction wherever the eigenvalue is separated from the others
+by more than 1e-6 lambda_max, residuals |C v - lambda v| at rounding level everywhere, and the
+library's sign convention (largest-magnitude component positive).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_13775_gb300 import inputs, lcs
+from gpu_util import rect_desc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    c = lcs.lcs_create(0, torch.cuda.current_stream())
+    yield c
+    lcs.lcs_destroy(c)
+
+
+def run(ctx, g, n, lo, hi, periodic, T, dt):
+    field = lcs.lcs_load_field(ctx, rect_desc(g), g.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(g.dim, n, lo, hi, periodic))
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=T, dt=dt), fm)
+    d, np_ = g.dim, (3 if g.dim == 2 else 6)
+    C = np.empty((N, np_))
+    lcs.lcs_cauchy_green(ctx, fm, 0, C)
+    f = np.empty(N, dtype=np.float32)
+    lam = np.empty(N)
+    lcs.lcs_ftle(ctx, fm, 0, f, lam)
+    ev = np.empty((N, d))
+    V = np.empty((N, d, d))
+    lcs.lcs_cg_eigen(ctx, fm, 0, ev, V)
+    # device outputs, and one output alone, give the same values
+    evd = torch.empty((N, d), dtype=torch.float64, device="cuda")
+    lcs.lcs_cg_eigen(ctx, fm, 0, evd, None)
+    lcs.lcs_synchronize(ctx)
+    np.testing.assert_array_equal(evd.cpu().numpy(), ev)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return C, lam, ev, V
+
+
+def unpack(C, d):
+    if d == 2:
+        a, b, c = C.T
+        return np.stack([np.stack([a, b], -1), np.stack([b, c], -1)], -2)
+    a, b, c, e, f, g = C.T
+    return np.stack([np.stack([a, b, c], -1), np.stack([b, e, f], -1), np.stack([c, f, g], -1)], -2)
+
+
+def check(C, lam, ev, V, d):
+    eo, vo = oracle.cg_eigen(C, d)
+    bad = np.isnan(C).any(axis=1)
+    assert np.isnan(ev[bad]).all() and np.isnan(V[bad]).all()
+    ok = ~bad
+    C, lam, ev, V, eo, vo = C[ok], lam[ok], ev[ok], V[ok], eo[ok], vo[ok]
+    lmax = eo[:, -1]
+    assert np.all(np.abs(ev - eo) <= 1e-12 * lmax[:, None] + 1e-10 * np.abs(eo))
+    np.testing.assert_allclose(ev[:, -1], lam, rtol=1e-12)       # lcs_ftle's lambda_max
+    M = unpack(C, d)
+    for k in range(d):
+        v = V[:, k, :]
+        np.testing.assert_allclose(np.linalg.norm(v, axis=1), 1.0, atol=1e-14)
+        r = np.linalg.norm(np.einsum("nij,nj->ni", M, v) - ev[:, k, None] * v, axis=1)
+        assert np.all(r <= 1e-12 * lmax), r.max() / lmax[r.argmax()]
+        # sign convention
+        big = np.take_along_axis(v, np.abs(v).argmax(axis=1)[:, None], 1)[:, 0]
+        assert np.all(big > 0)
+        gap = np.full(len(ev), np.inf)
+        for j in range(d):
+            if j != k:
+                gap = np.minimum(gap, np.abs(eo[:, j] - eo[:, k]))
+        sep = gap > 1e-6 * lmax
+        dots = np.abs(np.einsum("ni,ni->n", v[sep], vo[sep, k, :]))
+        assert np.all(dots >= 1 - 1e-10), 1 - dots.min()
+    return int(ok.sum())
+
+
+def test_eigen_gyre(ctx):
+    g = inputs.double_gyre()
+    # a box wider than the gyre's: tracers leave, their stencils give NaN
+    C, lam, ev, V = run(ctx, g, (201, 99), (-0.02, -0.02), (2.02, 1.02), (0, 0), 5.0, 0.05)
+    assert np.isnan(C).any()
+    assert check(C, lam, ev, V, 2) > 15000
+
+
+def test_eigen_abc(ctx):
+    g = inputs.abc(n=32, nframes=17, t_end=2.0)
+    L = 2 * np.pi
+    C, lam, ev, V = run(ctx, g, (37, 30, 29), (0.0, 0.0, 0.0), (L, L, L), (1, 1, 1), 2.0, 0.02)
+    check(C, lam, ev, V, 3)
+
+
+def test_eigen_rejects_null_outputs(ctx):
+    g = inputs.double_gyre(nx=17, ny=9, nframes=3, t_end=1.0)
+    field = lcs.lcs_load_field(ctx, rect_desc(g), g.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (8, 4), (0.0, 0.0), (2.0, 1.0)))
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    try:
+        with pytest.raises(lcs.LcsError) as e:
+            lcs.lcs_cg_eigen(ctx, fm, 0, None, None)
+        assert e.value.status == 1
+        with pytest.raises(lcs.LcsError):
+            lcs.lcs_cg_eigen(ctx, fm, 3, np.empty((32, 2)), None)
+    finally:
+        lcs.lcs_free_flowmap(fm)
+        lcs.lcs_free_seeds(seeds)
+        lcs.lcs_free_field(field)
