@@ -365,6 +365,74 @@ def cg_eigen(C, dim):
     return e, v
 
 
+def fd_stencil_members(dim, n, periodic):
+    """Lattice neighbours the finite differences of a seed use by geometry alone (Sec. 2
+    "Cauchy-Green"): per axis the two central neighbours, or at a non-periodic lattice edge the two
+    on the inner side.  Returns [N][2 dim] seed ids."""
+    N = int(np.prod(n[:dim]))
+    p = np.arange(N)
+    idx = [(p // int(np.prod(n[:a]))) % n[a] for a in range(dim)]
+    strides = [int(np.prod(n[:a])) for a in range(dim)]
+    out = np.empty((N, 2 * dim), dtype=np.int64)
+    for a in range(dim):
+        i = idx[a]
+        if periodic[a]:
+            o1, o2 = (i + 1) % n[a] - i, (i - 1) % n[a] - i
+        else:
+            central = (i >= 1) & (i <= n[a] - 2)
+            fwd = i == 0
+            o1 = np.where(central, 1, np.where(fwd, 1, -1))
+            o2 = np.where(central, -1, np.where(fwd, 2, -2))
+        out[:, 2 * a] = p + o1 * strides[a]
+        out[:, 2 * a + 1] = p + o2 * strides[a]
+    return out
+
+
+def ftle_early(field, n, lo, hi, periodic, t0, T, dt, xT, status, t_exit, endpoint=None):
+    """Early Cauchy-Green evaluation (Sec. 2 "Flow Map": where a trajectory leaves the domain, the CG
+    tensor is evaluated early at every location relying on it) for fixed-step RK4 on a rectilinear
+    field, from a full run's (xT, status, t_exit) over (t0, t0 + T).
+
+    Per seed: m = the fewest steps that the seed or any lattice neighbour its finite differences use
+    (fd_stencil_members) stayed in the domain -- all steps for a tracer still OK at the end, one less
+    than the step it left in otherwise.  m = all steps: the regular FTLE over |T|.  0 < m: grad F
+    from those tracers re-integrated over m steps, C (Eq. 1), lambda_max and
+    sigma = ln sqrt(lambda_max) / (m dt).  m = 0: NaN.  Returns (ftle, t_eval)."""
+    dim = len(n)
+    N = int(np.prod(n[:dim]))
+    endpoint = endpoint if endpoint is not None else [0 if q else 1 for q in periodic]
+    h = lattice_spacing(dim, n, lo, hi, endpoint)
+    period = [hi[a] - lo[a] if periodic[a] else 0.0 for a in range(dim)]
+    adt = abs(dt)
+    ns = int(round(abs(T) / adt))
+    ne = np.where(status == OK, ns, np.rint(np.abs(t_exit - t0) / adt).astype(np.int64) - 1)
+    ne = np.maximum(ne, 0)
+    mem = fd_stencil_members(dim, n, periodic)
+    m = np.minimum(ne, ne[mem].min(axis=1))
+    G = flowmap_gradient(dim, n, h, periodic, period, xT, status)
+    lam, sig = ftle(cauchy_green(G), dim, T)
+    t_eval = np.full(N, abs(T))
+    x0 = seed_grid(dim, n, lo, hi, endpoint).astype(np.float64)
+    sgn = -1.0 if T < 0 else 1.0
+    for mm in np.unique(m[m < ns]):
+        seeds = np.nonzero(m == mm)[0]
+        t_eval[seeds] = mm * adt
+        if mm == 0:
+            sig[seeds] = np.nan
+            continue
+        ids = np.unique(np.concatenate([seeds, mem[seeds].ravel()]))
+        xm, stm, _ = rk4(field, x0[:, ids], t0, sgn * mm * adt, dt)
+        assert (stm == OK).all()
+        xf = np.zeros((dim, N))
+        sf = np.full(N, LEFT, dtype=np.uint8)
+        xf[:, ids] = xm
+        sf[ids] = OK
+        Gm = flowmap_gradient(dim, n, h, periodic, period, xf, sf)[seeds]
+        _, sg = ftle(cauchy_green(Gm), dim, mm * adt)
+        sig[seeds] = sg
+    return sig, t_eval
+
+
 def ftle(C, dim, T):
     """lambda_max of C and sigma = ln(sqrt(lambda_max)) / |T|."""
     C = np.ascontiguousarray(C, dtype=np.float64)
