@@ -369,6 +369,23 @@ lcs_status lcs_cauchy_green(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double
 lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
                     double *C, int on_device);
 
+/* Early Cauchy-Green evaluation (Sec. 2 "Flow Map": where a trajectory leaves
+ * the domain, the CG tensor is evaluated early at every location relying on
+ * it).  fm holds job `job` of an lcs_advect call made with field, seeds and
+ * opts (LCS_RK4 on a rectilinear field).  Each seed's finite differences use
+ * fixed lattice neighbours (as lcs_cauchy_green: central, or one-sided at a
+ * non-periodic lattice edge); m = the fewest steps the seed or one of them
+ * stayed in the domain (all steps if still OK at the end, one less than the
+ * step it left in otherwise).  m = all steps: the FTLE of lcs_ftle; 0 < m:
+ * grad F from those tracers re-integrated over m steps (the same arithmetic,
+ * so the positions they had after step m), C, lambda_max and
+ * sigma = ln(sqrt(lambda_max)) / (m |dt|); m = 0: NaN.  ftle [N] FP32,
+ * t_eval [N] FP32 (optional): the horizon each value belongs to.
+ * Synchronises the context's stream (the number of early seeds sizes the
+ * second pass).  Errors: LCS_EINVAL, LCS_EUNSUPPORTED, LCS_ENOMEM, LCS_ECUDA. */
+lcs_status lcs_ftle_early(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *seeds, const lcs_advect_opts *opts,
+                          const lcs_flowmap *fm, int job, float *ftle, float *t_eval, int on_device);
+
 /* Eigenvalues and eigenvectors of C at every seed (Sec. 2 "Cauchy-Green":
  * the filter computes the eigenvalues and eigenvectors of the CG tensor at
  * each seed point), C as lcs_cauchy_green.  eigval [N][dim] FP64 in

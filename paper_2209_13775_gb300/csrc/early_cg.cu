@@ -1,0 +1,227 @@
+// early_cg.cu -- early Cauchy-Green evaluation where a stencil leaves the domain.
+//
+// Paper: Sec. 2 "Flow Map": when a trajectory leaves the spatial domain of the velocity
+// data, the CG tensor can be evaluated early at all locations relying on it (and Sec. 3.1:
+// synchronous updates let the CG tensor be evaluated at any step of the interval).
+//
+// After a fixed-step RK4 integration over (t0, t0 + T) (lcs_advect), each seed's finite
+// differences use a fixed set of lattice neighbours (central, or one-sided at a lattice
+// edge).  m(p) = the fewest steps that the seed or one of those neighbours stayed in the
+// domain: ns for a tracer still OK at the end, one less than the step it left in (its exit
+// time t0 + (n + 1) h) otherwise.  Seeds with m = ns keep the regular FTLE over |T|; seeds
+// with 0 < m < ns get the flow map of their stencil re-integrated over m steps (the same
+// arithmetic as the integration, so the positions are those the tracers had after step m),
+// grad F, C, lambda_max and sigma = ln sqrt(lambda_max) / (m |h|); m = 0 gives NaN.
+//
+// Three launches: a scan that finds m and lists the early seeds (one thread per seed), the
+// re-integration (one thread per listed seed and stencil member), the differences (one
+// thread per listed seed).  The list is short where few tracers leave.
+#include "cg_device.cuh"
+#include "rect_device.cuh"
+
+namespace {
+
+// stencil member s (0: the seed, then two per axis) of seed idx on a lattice of L.n, by
+// geometry only: central (+1, -1) on periodic axes and inside, forward (+1, +2) at the low
+// edge, backward (-1, -2) at the high edge.  Returns the id; *wrap = periods crossed.
+__device__ __forceinline__ long long member(const CgLaunch &L, const long long *idx, int s, int *wrap, int *mode)
+{
+    *wrap = 0;
+    if (s == 0) return idx[0] + (long long)L.n[0] * (idx[1] + (long long)L.n[1] * idx[2]);
+    const int b = (s - 1) >> 1, second = (s - 1) & 1;
+    int m;
+    if (L.periodic[b] || (idx[b] >= 1 && idx[b] <= L.n[b] - 2))
+        m = 1;
+    else
+        m = idx[b] == 0 ? 2 : 3;
+    *mode = m;
+    const int off = m == 1 ? (second ? -1 : 1) : m == 2 ? (second ? 2 : 1) : (second ? -2 : -1);
+    return lattice_nbr(L, idx, b, off, wrap);
+}
+
+// steps a tracer of this slot stayed in the domain
+__device__ __forceinline__ int in_steps(unsigned char st, float te, int ns, double t0, double adt)
+{
+    if (st == LCS_TRACER_OK) return ns;
+    if (st != LCS_TRACER_LEFT) return 0;
+    const int n1 = (int)rint(fabs((double)te - t0) / adt);   // the step it left in
+    return max(n1 - 1, 0);
+}
+
+template <int DIM>
+__global__ void early_scan_kernel(CgLaunch L, int job, int ns, double t0, double adt, float absT,
+                                  unsigned *__restrict__ count, int2 *__restrict__ list, float *__restrict__ t_eval)
+{
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= L.N) return;
+    const unsigned char *S = L.status + (size_t)job * L.N;
+    const float *TE = L.texit + (size_t)job * L.N;
+    const long long idx[3] = {p % L.n[0], (p / L.n[0]) % L.n[1], DIM == 3 ? p / ((long long)L.n[0] * L.n[1]) : 0};
+    int m = ns;
+#pragma unroll
+    for (int s = 0; s < 2 * DIM + 1; ++s) {
+        int w, mode;
+        const long long q = member(L, idx, s, &w, &mode);
+        m = min(m, q < 0 ? 0 : in_steps(S[q], TE[q], ns, t0, adt));
+    }
+    if (m >= ns) {
+        if (t_eval) t_eval[p] = absT;
+        return;
+    }
+    if (t_eval) t_eval[p] = (float)((double)m * adt);
+    if (m > 0) {
+        const unsigned e = atomicAdd(count, 1u);
+        list[e] = make_int2((int)p, m);
+    }
+}
+
+// re-integration of member (e % (2 DIM + 1)) of listed seed e / (2 DIM + 1) over m steps,
+// with the one-pass kernel's arithmetic; the unwrapped FP32 position goes to pos
+template <int DIM, int ST>
+__global__ void early_advect_kernel(CgLaunch L, RectParams P, const char *__restrict__ frames, size_t fstride,
+                                    Rk4Args A, int job, const unsigned *__restrict__ count,
+                                    const int2 *__restrict__ list, float *__restrict__ pos)
+{
+    constexpr int NM = 2 * DIM + 1;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long e = t / NM;
+    const int s = (int)(t % NM);
+    if (e >= (long long)*count) return;
+    const int2 it = list[e];
+    const long long p = it.x;
+    const long long idx[3] = {p % L.n[0], (p / L.n[0]) % L.n[1], DIM == 3 ? p / ((long long)L.n[0] * L.n[1]) : 0};
+    int w, mode;
+    const long long q = member(L, idx, s, &w, &mode);
+    float x[DIM];
+    int img[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        x[d] = A.seeds[d * A.N + q];
+        img[d] = 0;
+    }
+    wrap_periodic<DIM>(P, x, img);
+    const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
+    const float h = A.job_h[job];
+    for (int n = 0; n < it.y; ++n) {
+        SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
+        if constexpr (DIM == 2)
+            rk4_step<2, ST, SRC_GLOBAL>(P, x, h, frames + (size_t)e0.k * fstride,
+                                        frames + (size_t)(e0.k + 1) * fstride, e0.a, frames + (size_t)e1.k * fstride,
+                                        frames + (size_t)(e1.k + 1) * fstride, e1.a, frames + (size_t)e2.k * fstride,
+                                        frames + (size_t)(e2.k + 1) * fstride, e2.a);
+        else
+            rk4_step3p<ST>(P, x, h, frames + (size_t)e0.k * fstride, e0.a, frames + (size_t)e1.k * fstride, e1.a,
+                           frames + (size_t)e2.k * fstride, e2.a);
+        wrap_periodic<DIM>(P, x, img);
+    }
+    float *o = pos + (size_t)t * DIM;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o[d] = P.periodic[d] ? fmaf((float)img[d], P.L[d], x[d]) : x[d];
+}
+
+// grad F from the re-integrated stencil (the regular pass's formulas), C, lambda_max, FTLE
+template <int DIM>
+__global__ void early_fd_kernel(CgLaunch L, const unsigned *__restrict__ count, const int2 *__restrict__ list,
+                                const float *__restrict__ pos, double adt, float *__restrict__ ftle)
+{
+    constexpr int NM = 2 * DIM + 1;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)*count) return;
+    const int2 it = list[e];
+    const long long p = it.x;
+    const long long idx[3] = {p % L.n[0], (p / L.n[0]) % L.n[1], DIM == 3 ? p / ((long long)L.n[0] * L.n[1]) : 0};
+    const float *X = pos + (size_t)e * NM * DIM;
+    double G[DIM][DIM];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+        int w1, w2, mode;
+        member(L, idx, 1 + 2 * b, &w1, &mode);
+        member(L, idx, 2 + 2 * b, &w2, &mode);
+        const double h2 = L.h2[b], rh2 = L.rh2[b], sh = L.period[b];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const bool on = a == b;
+            const double F0 = (double)X[a];
+            const double F1 = nbr_pos(X[(1 + 2 * b) * DIM + a], w1, sh, on);
+            const double F2 = nbr_pos(X[(2 + 2 * b) * DIM + a], w2, sh, on);
+            double d;
+            if (mode == 1)
+                d = div_fixed(__dsub_rn(F1, F2), h2, rh2);
+            else if (mode == 2)
+                d = div_fixed(__dsub_rn(__dadd_rn(__dmul_rn(-3.0, F0), __dmul_rn(4.0, F1)), F2), h2, rh2);
+            else
+                d = div_fixed(__dadd_rn(__dsub_rn(__dmul_rn(3.0, F0), __dmul_rn(4.0, F1)), F2), h2, rh2);
+            G[a][b] = d;
+        }
+    }
+    constexpr int NP = DIM == 2 ? 3 : 6;
+    double C[NP];
+    int o = 0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = i; j < DIM; ++j) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) s = __dadd_rn(s, __dmul_rn(G[a][i], G[a][j]));
+            C[o++] = s;
+        }
+    const double lm = DIM == 2 ? eig_max2(C) : eig_max3(C);
+    // sigma = ln(sqrt(lm)) / (m |h|), as the regular pass forms it
+    ftle[p] = log1pf((float)(lm - 1.0)) * (0.5f / (float)((double)it.y * adt));
+}
+
+}  // namespace
+
+cudaError_t launch_early_cg(const EarlyLaunch &E, cudaStream_t s)
+{
+    CgLaunch L = E.cg;
+    for (int b = 0; b < 3; ++b) {
+        L.h2[b] = 2.0 * L.h[b];
+        L.rh2[b] = 1.0 / L.h2[b];
+    }
+    const int bt = 256;
+    const unsigned grid = (unsigned)((L.N + bt - 1) / bt);
+    if (E.phase == 0) {
+        if (L.dim == 2)
+            early_scan_kernel<2><<<grid, bt, 0, s>>>(L, E.job, E.ns, E.t0, E.adt, E.absT, E.count, E.list, E.t_eval);
+        else
+            early_scan_kernel<3><<<grid, bt, 0, s>>>(L, E.job, E.ns, E.t0, E.adt, E.absT, E.count, E.list, E.t_eval);
+        return cudaGetLastError();
+    }
+    if (E.nlisted == 0) return cudaSuccess;
+    const lcs_field *f = E.field;
+    const RectParams P = make_rect_params(f);
+    Rk4Args A;
+    A.seeds = E.seeds;
+    A.N = L.N;
+    A.nsteps_max = E.nsteps_max;
+    A.sched = E.sched;
+    A.job_nsteps = nullptr;
+    A.job_h = E.job_h;
+    A.job_t0 = nullptr;
+    A.job_tend = nullptr;
+    A.out_xyz = nullptr;
+    A.out_status = nullptr;
+    A.out_texit = nullptr;
+    const int nm = 2 * L.dim + 1;
+    const unsigned ga = (unsigned)((E.nlisted * nm + bt - 1) / bt);
+    const char *fr = (const char *)f->d_frames;
+#define EARLY_ADVECT(D, ST) early_advect_kernel<D, ST><<<ga, bt, 0, s>>>(L, P, fr, f->frame_stride, A, E.job, E.count, E.list, E.pos)
+    if (L.dim == 2) {
+        if (f->storage == LCS_F32) EARLY_ADVECT(2, LCS_F32);
+        else if (f->storage == LCS_F16) EARLY_ADVECT(2, LCS_F16);
+        else EARLY_ADVECT(2, LCS_BF16);
+    } else {
+        if (f->storage == LCS_F32) EARLY_ADVECT(3, LCS_F32);
+        else if (f->storage == LCS_F16) EARLY_ADVECT(3, LCS_F16);
+        else EARLY_ADVECT(3, LCS_BF16);
+    }
+#undef EARLY_ADVECT
+    const unsigned gf = (unsigned)((E.nlisted + bt - 1) / bt);
+    if (L.dim == 2)
+        early_fd_kernel<2><<<gf, bt, 0, s>>>(L, E.count, E.list, E.pos, E.adt, E.ftle);
+    else
+        early_fd_kernel<3><<<gf, bt, 0, s>>>(L, E.count, E.list, E.pos, E.adt, E.ftle);
+    return cudaGetLastError();
+}

@@ -879,6 +879,43 @@ static lcs_status advect_graph(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds
     return LCS_OK;
 }
 
+// The fixed-step jobs of an RK4 call (and its snapshot steps) from the options: |T| / |dt|
+// must be a whole number of steps for every job and snapshot.
+static lcs_status rk4_jobs(lcs_ctx *ctx, const lcs_advect_opts *o, int njobs, JobTable *J, const char *who)
+{
+    const double adt = fabs(o->dt);
+    if (!(adt > 0.0) || !isfinite(adt)) return lcs_fail(ctx, LCS_EINVAL, "%s: dt must be finite and > 0", who);
+    J->njobs = njobs;
+    J->nsteps_max = 0;
+    for (int j = 0; j < njobs; ++j) {
+        double t0 = o->njobs > 1 ? o->job_t0[j] : o->t0;
+        double T = o->njobs > 1 ? o->job_T[j] : o->T;
+        if (!isfinite(t0) || !isfinite(T)) return lcs_fail(ctx, LCS_EINVAL, "%s: job %d has a non-finite t0 or T", who, j);
+        double r = fabs(T) / adt;
+        long long ns = (long long)floor(r + 0.5);
+        if (fabs(r - (double)ns) > 1e-9 * std::max(1.0, r) || ns > (1LL << 30))
+            return lcs_fail(ctx, LCS_EINVAL, "%s: |T|/|dt| = %.17g is not an integer (job %d)", who, r, j);
+        J->t0[j] = t0;
+        J->T[j] = T;
+        J->h[j] = T < 0.0 ? -adt : adt;
+        J->nsteps[j] = (int)ns;
+        J->nsteps_max = std::max(J->nsteps_max, (int)ns);
+        J->order[j] = j;
+    }
+    J->nsnap = o->nsnap;
+    for (int q = 0; q < o->nsnap; ++q) {
+        const double a = o->snap_T[q], r = a / adt;
+        const long long n = (long long)floor(r + 0.5);
+        if (!(a > 0.0) || !isfinite(a) || fabs(r - (double)n) > 1e-9 * std::max(1.0, r) || n > (1LL << 30) ||
+            (q > 0 && !(a > o->snap_T[q - 1])))
+            return lcs_fail(ctx, LCS_EINVAL, "%s: snap_T[%d] = %.17g must be > 0, increasing and a whole number of steps",
+                            who, q, a);
+        J->snap_n[q] = (int)n;
+        J->snap_T[q] = a;
+    }
+    return LCS_OK;
+}
+
 extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
                                  lcs_flowmap *fm)
 {
@@ -904,48 +941,18 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
     if (f->kind == LCS_TET && (!s->d_cells || s->field_uid != f->uid))
         return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: on a tet field the seeds must come from lcs_seed_grid on that field");
     if (o->method == LCS_RK45) return advect_rk45(ctx, f, s, o, fm);
-    double adt = fabs(o->dt);
-    if (!(adt > 0.0) || !isfinite(adt)) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: dt must be finite and > 0");
     JobTable *J = new (std::nothrow) JobTable();
     if (!J) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
-    J->njobs = njobs;
-    J->nsteps_max = 0;
-    for (int j = 0; j < njobs; ++j) {
-        double t0 = o->njobs > 1 ? o->job_t0[j] : o->t0;
-        double T = o->njobs > 1 ? o->job_T[j] : o->T;
-        if (!isfinite(t0) || !isfinite(T)) {
-            delete J;
-            return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: job %d has a non-finite t0 or T", j);
-        }
-        double r = fabs(T) / adt;
-        long long ns = (long long)floor(r + 0.5);
-        if (fabs(r - (double)ns) > 1e-9 * std::max(1.0, r) || ns > (1LL << 30)) {
-            delete J;
-            return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: |T|/|dt| = %.17g is not an integer (job %d)", r, j);
-        }
-        J->t0[j] = t0;
-        J->T[j] = T;
-        J->h[j] = T < 0.0 ? -adt : adt;
-        J->nsteps[j] = (int)ns;
-        J->nsteps_max = std::max(J->nsteps_max, (int)ns);
-        fm->T[j] = T;
-        J->order[j] = j;
+    lcs_status bs = rk4_jobs(ctx, o, njobs, J, "lcs_advect");
+    if (bs != LCS_OK) {
+        delete J;
+        return bs;
     }
-    J->nsnap = o->nsnap;
-    for (int q = 0; q < o->nsnap; ++q) {
-        const double a = o->snap_T[q], r = a / adt;
-        const long long n = (long long)floor(r + 0.5);
-        if (!(a > 0.0) || !isfinite(a) || fabs(r - (double)n) > 1e-9 * std::max(1.0, r) || n > (1LL << 30) ||
-            (q > 0 && !(a > o->snap_T[q - 1]))) {
-            delete J;
-            return lcs_fail(ctx, LCS_EINVAL,
-                            "lcs_advect: snap_T[%d] = %.17g must be > 0, increasing and a whole number of steps", q, a);
-        }
-        J->snap_n[q] = (int)n;
-        J->snap_T[q] = a;
-        for (int j = 0; j < njobs; ++j) {
-            const double Tj = J->T[j];
-            fm->T[njobs + j * o->nsnap + q] = Tj < 0.0 ? -std::min(a, -Tj) : std::min(a, Tj);
+    for (int j = 0; j < njobs; ++j) {
+        fm->T[j] = J->T[j];
+        for (int q = 0; q < J->nsnap; ++q) {
+            const double a = J->snap_T[q], Tj = J->T[j];
+            fm->T[njobs + j * J->nsnap + q] = Tj < 0.0 ? -std::min(a, -Tj) : std::min(a, Tj);
         }
     }
     // work-queue order of the persistent kernel: longest integrations first
@@ -1058,6 +1065,142 @@ extern "C" lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, flo
 {
     if (ctx && !ftle) return lcs_fail(ctx, LCS_EINVAL, "lcs_ftle: null output");
     return cg_call(ctx, fm, job, ftle, lambda_max, C, on_device, "lcs_ftle");
+}
+
+extern "C" lcs_status lcs_ftle_early(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
+                                     const lcs_flowmap *fm, int job, float *ftle, float *t_eval, int on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    const char *who = "lcs_ftle_early";
+    if (!f || !s || !o || !fm || !ftle) return lcs_fail(ctx, LCS_EINVAL, "%s: null argument", who);
+    if (o->method != LCS_RK4 || f->kind != LCS_RECTILINEAR)
+        return lcs_fail(ctx, LCS_EUNSUPPORTED, "%s: fixed-step RK4 on a rectilinear field only", who);
+    if (f->dim != s->dim || fm->seeds != s) return lcs_fail(ctx, LCS_EINVAL, "%s: field, seeds and flow map differ", who);
+    const int njobs = o->njobs > 1 ? o->njobs : 1;
+    if (job < 0 || job >= njobs || njobs > fm->njobs)
+        return lcs_fail(ctx, LCS_EINVAL, "%s: job %d out of range of the options' %d jobs", who, job, njobs);
+    for (int a = 0; a < s->dim; ++a)
+        if (s->n[a] < 3) return lcs_fail(ctx, LCS_EINVAL, "%s: the lattice needs >= 3 seeds per axis", who);
+    if ((long long)fm->N > (1LL << 31) - 1) return lcs_fail(ctx, LCS_EINVAL, "%s: too many seeds", who);
+    JobTable *J = new (std::nothrow) JobTable();
+    if (!J) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
+    lcs_status st = rk4_jobs(ctx, o, njobs, J, who);
+    if (st != LCS_OK) {
+        delete J;
+        return st;
+    }
+    J->nsnap = 0;
+    const double t0 = J->t0[job], adt = fabs(J->h[job]), absT = fabs(J->T[job]);
+    const int ns = J->nsteps[job];
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const size_t N = (size_t)fm->N;
+    // one block of temporaries: per-job values, schedule, count, list, host-output staging
+    const size_t bj = align256(sizeof(int) * njobs), bf = align256(sizeof(float) * njobs),
+                 bd = align256(sizeof(double) * njobs),
+                 bs = align256(sizeof(SchedEntry) * 3 * (size_t)njobs * std::max(J->nsteps_max, 1)),
+                 bl = align256(sizeof(int2) * N), bo = on_device ? 0 : align256(sizeof(float) * N);
+    char *tmp = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&tmp, 2 * bj + 3 * bf + bd + bs + 256 + bl + 2 * bo, ctx->stream);
+    if (e != cudaSuccess) {
+        delete J;
+        return lcs_fail(ctx, LCS_ENOMEM, "%s: %s", who, cudaGetErrorString(e));
+    }
+    char *p = tmp;
+    JobDev D;
+    D.nsteps = (int *)p;
+    p += bj;
+    D.order = (int *)p;
+    p += bj;
+    D.h = (float *)p;
+    p += bf;
+    D.t0 = (float *)p;
+    p += bf;
+    D.tend = (float *)p;
+    p += bf;
+    D.absT = (double *)p;
+    p += bd;
+    D.t0d = nullptr;
+    D.Td = nullptr;
+    SchedEntry *sched = (SchedEntry *)p;
+    p += bs;
+    unsigned *count = (unsigned *)p;
+    p += 256;
+    int2 *list = (int2 *)p;
+    p += bl;
+    float *out_f = on_device ? ftle : (float *)p;
+    p += bo;
+    float *out_t = on_device ? t_eval : (t_eval ? (float *)p : nullptr);
+    float *pos = nullptr;
+    EarlyLaunch E;
+    e = launch_rk4_schedule(f->d_times, f->nframes, f->time_periodic, f->period, *J, D, sched, ctx->stream);
+    const int nsteps_max = J->nsteps_max;
+    delete J;
+    // the regular FTLE of every seed, then the early seeds overwrite theirs
+    CgLaunch L;
+    L.dim = fm->dim;
+    for (int a = 0; a < 3; ++a) {
+        L.n[a] = s->n[a];
+        L.periodic[a] = s->periodic[a];
+        L.h[a] = s->h[a];
+        L.period[a] = s->period[a];
+    }
+    L.N = fm->N;
+    L.job0 = job;
+    L.njobs = 1;
+    L.xyz = fm->d_xyz;
+    L.status = fm->d_status;
+    L.texit = fm->d_texit;
+    L.absT = fm->d_absT;
+    L.C = nullptr;
+    L.lam = nullptr;
+    L.ftle = out_f;
+    L.eigval = nullptr;
+    L.eigvec = nullptr;
+    lcs_tm_begin(ctx, 3, ctx->stream);
+    if (e == cudaSuccess) e = launch_cg_ftle(L, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(unsigned), ctx->stream);
+    E.cg = L;
+    E.phase = 0;
+    E.job = job;
+    E.ns = ns;
+    E.t0 = t0;
+    E.adt = adt;
+    E.absT = (float)absT;
+    E.count = count;
+    E.list = list;
+    E.nlisted = 0;
+    E.pos = nullptr;
+    E.t_eval = out_t;
+    E.ftle = out_f;
+    E.field = f;
+    E.seeds = s->d_xyz;
+    E.nsteps_max = nsteps_max;
+    E.sched = sched;
+    E.job_h = D.h;
+    unsigned nl = 0;
+    if (e == cudaSuccess) e = launch_early_cg(E, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, count, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && nl > 0) {
+        e = cudaMallocAsync((void **)&pos, sizeof(float) * (size_t)nl * (2 * fm->dim + 1) * fm->dim, ctx->stream);
+        if (e == cudaSuccess) {
+            E.phase = 1;
+            E.nlisted = nl;
+            E.pos = pos;
+            e = launch_early_cg(E, ctx->stream);
+        }
+    }
+    lcs_tm_end(ctx, 3, ctx->stream);
+    if (e == cudaSuccess && !on_device) {
+        e = cudaMemcpyAsync(ftle, out_f, sizeof(float) * N, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess && t_eval)
+            e = cudaMemcpyAsync(t_eval, out_t, sizeof(float) * N, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (pos) cudaFreeAsync(pos, ctx->stream);
+    cudaFreeAsync(tmp, ctx->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+    return LCS_OK;
 }
 
 extern "C" lcs_status lcs_cg_eigen(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double *eigval, double *eigvec,

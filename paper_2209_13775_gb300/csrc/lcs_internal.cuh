@@ -242,6 +242,7 @@ struct CgLaunch {
     int job0, njobs;
     const float *xyz;            // flow map base [njobs_total][dim][N]
     const unsigned char *status; // [njobs_total][N]
+    const float *texit = nullptr; // [njobs_total][N] (early evaluation only)
     const double *absT;          // [njobs_total] |T|
     double *C;                   // [njobs][N][np] or null
     double *lam;                 // [njobs][N] or null
@@ -251,6 +252,28 @@ struct CgLaunch {
 };
 
 cudaError_t launch_cg_ftle(const CgLaunch &L, cudaStream_t s);
+
+// early Cauchy-Green evaluation (early_cg.cu): phase 0 scans the seeds of slot `job` (writes
+// t_eval and lists the early ones), phase 1 re-integrates the listed stencils and writes their FTLE
+struct EarlyLaunch {
+    CgLaunch cg;                 // lattice, flow map (positions, status, exit times), outputs unused
+    int phase;
+    int job, ns;                 // slot and its RK4 step count
+    double t0, adt;              // the job's start time and |dt|
+    float absT;                  // |T| (the regular seeds' horizon)
+    unsigned *count;             // listed seeds (device)
+    int2 *list;                  // [N] (seed, steps m) of the listed seeds
+    long long nlisted;           // phase 1: the count, read back
+    float *pos;                  // phase 1: [nlisted][2 dim + 1][dim] re-integrated stencil positions
+    float *t_eval, *ftle;        // [N] outputs (device)
+    const lcs_field *field;
+    const float *seeds;          // [dim][N]
+    int nsteps_max;
+    const SchedEntry *sched;     // [njobs][nsteps_max][3]
+    const float *job_h;          // [njobs]
+};
+
+cudaError_t launch_early_cg(const EarlyLaunch &E, cudaStream_t s);
 
 // grow the context's reusable device scratch (dropping captured graphs that point into it)
 lcs_status lcs_scratch_reserve(lcs_ctx *ctx, size_t bytes);

@@ -26,7 +26,8 @@ EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs
            "lcs_load_field", "lcs_update_frames", "lcs_free_field", "lcs_seed_grid", "lcs_seeds_count",
            "lcs_seeds_get", "lcs_free_seeds", "lcs_flowmap_create", "lcs_advect", "lcs_flowmap_get",
            "lcs_flowmap_steps",
-           "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_cg_eigen", "lcs_timing_enable",
+           "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_cg_eigen", "lcs_ftle_early",
+           "lcs_timing_enable",
            "lcs_timing_read",
            "lcs_advect_rk4_noalloc", "lcs_gemm_bf16", "lcs_mlp_create", "lcs_mlp_set_params",
            "lcs_mlp_get_params", "lcs_mlp_free", "lcs_mlp_forward", "lcs_mlp_loss_grad", "lcs_mlp_adam",
@@ -93,7 +94,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_flowmap_create": ([P, P, I, P], S), "lcs_advect": ([P, P, P, P, P], S),
         "lcs_flowmap_get": ([P, P, I, P, P, P, I], S), "lcs_free_flowmap": ([P], None),
         "lcs_cauchy_green": ([P, P, I, P, I], S), "lcs_ftle": ([P, P, I, P, P, P, I], S),
-        "lcs_cg_eigen": ([P, P, I, P, P, I], S),
+        "lcs_cg_eigen": ([P, P, I, P, P, I], S), "lcs_ftle_early": ([P, P, P, P, P, I, P, P, I], S),
         "lcs_advect_rk4_noalloc": ([P, P, P, LL, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P], S),
         "lcs_timing_enable": ([P, I], S), "lcs_timing_read": ([P, I, P, P], S),
         "lcs_autotune": ([P, P, P, P, ctypes.c_char_p], S),
@@ -331,6 +332,17 @@ def lcs_ftle(ctx, fm, job, ftle, lambda_max=None, C=None):
     if len(devs) > 1:
         raise ValueError("outputs must all be host or all be device buffers")
     _check(ctx, load().lcs_ftle(ctx, fm, int(job), *[ctypes.c_void_p(p) for p, _ in ptrs], devs.pop()))
+
+
+def lcs_ftle_early(ctx, field, seeds, opts: AdvectOpts, fm, job, ftle, t_eval=None):
+    """FTLE with early Cauchy-Green evaluation where a seed's stencil leaves the domain; t_eval gets the
+    horizon of each value."""
+    ptrs = [_ptr(a) for a in (ftle, t_eval)]
+    devs = {d for (p, d), a in zip(ptrs, (ftle, t_eval)) if a is not None}
+    if len(devs) > 1:
+        raise ValueError("outputs must all be host or all be device buffers")
+    _check(ctx, load().lcs_ftle_early(ctx, field, seeds, ctypes.byref(opts), fm, int(job),
+                                      *[ctypes.c_void_p(p) for p, _ in ptrs], devs.pop()))
 
 
 def lcs_cg_eigen(ctx, fm, job, eigval=None, eigvec=None):
