@@ -369,9 +369,9 @@ lcs_status lcs_cauchy_green(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double
 lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
                     double *C, int on_device);
 
-/* Early Cauchy-Green evaluation (Sec. 2 "Flow Map": where a trajectory leaves
- * the domain, the CG tensor is evaluated early at every location relying on
- * it).  fm holds job `job` of an lcs_advect call made with field, seeds and
+/* Early Cauchy-Green evaluation (Sec. 2 "Flow Map": for trajectories that exit
+ * the data, the CG tensor is formed ahead of the horizon wherever such a
+ * trajectory is used).  fm holds job `job` of an lcs_advect call made with field, seeds and
  * opts (LCS_RK4 on a rectilinear field).  Each seed's finite differences use
  * fixed lattice neighbours (as lcs_cauchy_green: central, or one-sided at a
  * non-periodic lattice edge); m = the fewest steps the seed or one of them
@@ -386,9 +386,8 @@ lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, d
 lcs_status lcs_ftle_early(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *seeds, const lcs_advect_opts *opts,
                           const lcs_flowmap *fm, int job, float *ftle, float *t_eval, int on_device);
 
-/* Eigenvalues and eigenvectors of C at every seed (Sec. 2 "Cauchy-Green":
- * the filter computes the eigenvalues and eigenvectors of the CG tensor at
- * each seed point), C as lcs_cauchy_green.  eigval [N][dim] FP64 in
+/* Eigenvalues and eigenvectors of C at every seed (Sec. 2 "Cauchy-Green" lists
+ * both among the filter's per-seed outputs), C as lcs_cauchy_green.  eigval [N][dim] FP64 in
  * ascending order; eigvec [N][dim][dim] FP64, eigvec[(p*dim + k)*dim + r]
  * = component r of the unit eigenvector of eigval[p][k], its largest-magnitude
  * component positive.  Cyclic Jacobi rotations in FP64 to a relative

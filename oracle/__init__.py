@@ -389,8 +389,8 @@ def fd_stencil_members(dim, n, periodic):
 
 
 def ftle_early(field, n, lo, hi, periodic, t0, T, dt, xT, status, t_exit, endpoint=None):
-    """Early Cauchy-Green evaluation (Sec. 2 "Flow Map": where a trajectory leaves the domain, the CG
-    tensor is evaluated early at every location relying on it) for fixed-step RK4 on a rectilinear
+    """Early Cauchy-Green evaluation (Sec. 2 "Flow Map": for trajectories that exit the data, the CG tensor
+    is formed ahead of the horizon wherever such a trajectory is used) for fixed-step RK4 on a rectilinear
     field, from a full run's (xT, status, t_exit) over (t0, t0 + T).
 
     Per seed: m = the fewest steps that the seed or any lattice neighbour its finite differences use

@@ -1,8 +1,8 @@
 // early_cg.cu -- early Cauchy-Green evaluation where a stencil leaves the domain.
 //
-// Paper: Sec. 2 "Flow Map": when a trajectory leaves the spatial domain of the velocity
-// data, the CG tensor can be evaluated early at all locations relying on it (and Sec. 3.1:
-// synchronous updates let the CG tensor be evaluated at any step of the interval).
+// Paper: Sec. 2 "Flow Map" names, for trajectories that exit the velocity data, forming the
+// CG tensor ahead of the horizon for every seed whose differences use such a trajectory (and
+// Sec. 3.1 notes that synchronous updates make the CG tensor available at any step).
 //
 // After a fixed-step RK4 integration over (t0, t0 + T) (lcs_advect), each seed's finite
 // differences use a fixed set of lattice neighbours (central, or one-sided at a lattice

@@ -1,5 +1,5 @@
-"""Early Cauchy-Green evaluation (Sec. 2 "Flow Map": where a trajectory leaves the domain, the CG
-tensor is evaluated early at every location relying on it) through lcs_ftle_early, against the
+"""Early Cauchy-Green evaluation (Sec. 2 "Flow Map": for trajectories that exit the data, the CG tensor
+is formed ahead of the horizon wherever such a trajectory is used) through lcs_ftle_early, against the
 oracle's ftle_early on the same seeded inputs, and against separate GPU runs over the early
 horizons (the re-integrated stencil is the same arithmetic, so those values are bit-identical).
 """

@@ -1,5 +1,5 @@
-"""Pins of the oracle's early Cauchy-Green evaluation (Sec. 2 "Flow Map": where a trajectory leaves
-the domain, the CG tensor is evaluated early at every location relying on it).
+"""Pins of the oracle's early Cauchy-Green evaluation (Sec. 2 "Flow Map": for trajectories that exit
+the data, the CG tensor is formed ahead of the horizon wherever such a trajectory is used).
 
 * A steady shear u = (U + c y, 0) on a box that tracers leave through the x faces: RK4 moves a tracer
   by exactly h (U + c y0) per step (every stage sees the same velocity, and the clamped queries of a
