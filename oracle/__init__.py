@@ -433,6 +433,37 @@ def ftle_early(field, n, lo, hi, periodic, t0, T, dt, xT, status, t_exit, endpoi
     return sig, t_eval
 
 
+def aux_points(x0, delta):
+    """Auxiliary points around each seed of x0 [dim][N] FP32 (Sec. 2 "Seed"): point (p dim + b) 2 + s is
+    seed p moved by +delta[b] (s = 0) or -delta[b] (s = 1) along axis b, in FP64, rounded to FP32."""
+    x0 = np.asarray(x0, dtype=np.float32)
+    dim, N = x0.shape
+    out = np.repeat(x0[:, :, None, None], dim, axis=2).repeat(2, axis=3)      # [dim][N][dim][2]
+    for b in range(dim):
+        base = x0[b].astype(np.float64)
+        out[b, :, b, 0] = (base + float(delta[b])).astype(np.float32)
+        out[b, :, b, 1] = (base - float(delta[b])).astype(np.float32)
+    return out.reshape(dim, N * 2 * dim)
+
+
+def aux_gradient(x0aux, xT, status):
+    """grad F per lattice seed from its auxiliary points (Sec. 2 "Cauchy-Green", the auxiliary-point
+    variant): grad F[a][b] = (F_a(+) - F_a(-)) / (x0_b(+) - x0_b(-)) with the FP32 starting points; NaN
+    unless all 2 dim points are OK.  Returns [N][dim][dim]."""
+    dim, M = np.shape(xT)
+    N = M // (2 * dim)
+    X = np.asarray(xT, dtype=np.float64).reshape(dim, N, dim, 2)
+    X0 = np.asarray(x0aux, dtype=np.float32).astype(np.float64).reshape(dim, N, dim, 2)
+    G = np.empty((N, dim, dim))
+    for b in range(dim):
+        den = X0[b, :, b, 0] - X0[b, :, b, 1]
+        for a in range(dim):
+            G[:, a, b] = (X[a, :, b, 0] - X[a, :, b, 1]) / den
+    ok = (np.asarray(status).reshape(N, 2 * dim) == OK).all(axis=1)
+    G[~ok] = np.nan
+    return G
+
+
 def ftle(C, dim, T):
     """lambda_max of C and sigma = ln(sqrt(lambda_max)) / |T|."""
     C = np.ascontiguousarray(C, dtype=np.float64)
