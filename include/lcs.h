@@ -164,6 +164,22 @@ lcs_status lcs_seeds_get(lcs_ctx *ctx, const lcs_seeds *seeds, float *xyz, int *
 
 void lcs_free_seeds(lcs_seeds *seeds);
 
+/* Auxiliary points around each seed (Sec. 2 "Seed" and "Cauchy-Green": a
+ * second way to difference the flow map, with points placed close around
+ * each seed instead of its lattice neighbours).  From a lattice of N seeds
+ * made by lcs_seed_grid on a rectilinear field, a point set of N * 2 * dim
+ * points: point (p * dim + b) * 2 + s is seed p moved by +delta[b] (s = 0) or
+ * -delta[b] (s = 1) along axis b, computed in FP64 and rounded to FP32.
+ * lcs_advect advects it like any seeds (lcs_seeds_count gives the points);
+ * lcs_cauchy_green, lcs_ftle and lcs_cg_eigen on its flow map then form, per
+ * lattice seed (N outputs),
+ *   grad F[a][b] = (F_a(p, b, 0) - F_a(p, b, 1)) / (x0_b(p, b, 0) - x0_b(p, b, 1))
+ * in FP64 from the FP32 positions, x0 the FP32 starting points (so the divisor
+ * is the spacing the points really have); NaN unless all 2 dim points are OK.
+ * delta [dim] HOST, each > 0 and finite.  Not for tet fields or
+ * lcs_ftle_early.  Errors: LCS_EINVAL, LCS_ENOMEM, LCS_ECUDA.               */
+lcs_status lcs_seed_aux(lcs_ctx *ctx, const lcs_seeds *lattice, const double *delta, lcs_seeds **out);
+
 /* ------------------------------------------------- flow map (a3-a8, a12) */
 
 /* Integration options (Sec. 2 "Flow Map": single-step Runge-Kutta; Eq. 2

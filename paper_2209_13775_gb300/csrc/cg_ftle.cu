@@ -106,7 +106,30 @@ __device__ __forceinline__ void eig_jacobi(const double *Cp, double *ev, double 
     }
 }
 
-template <int DIM, bool EIG>
+// grad F of lattice seed p from its 2 DIM auxiliary points (lcs_seed_aux): per axis b the
+// difference of the two points' final positions over that of their FP32 starting points,
+// RN operations in FP64; NaN unless every point is OK
+template <int DIM>
+__device__ __forceinline__ void aux_gradient(const CgLaunch &L, int job, long long p, double (*G)[DIM])
+{
+    const long long M = L.npts;
+    const float *X = L.xyz + (size_t)job * DIM * M;
+    const unsigned char *S = L.status + (size_t)job * M;
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < 2 * DIM; ++q) ok &= S[p * 2 * DIM + q] == LCS_TRACER_OK;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+        const long long i0 = (p * DIM + b) * 2, i1 = i0 + 1;
+        const double den = __dsub_rn((double)L.x0aux[b * M + i0], (double)L.x0aux[b * M + i1]);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+            G[a][b] = ok ? __ddiv_rn(__dsub_rn((double)X[a * M + i0], (double)X[a * M + i1]), den) : nan;
+    }
+}
+
+template <int DIM, bool EIG, bool AUX>
 __global__ void __launch_bounds__(256) cg_ftle_kernel(CgLaunch L)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -115,10 +138,13 @@ __global__ void __launch_bounds__(256) cg_ftle_kernel(CgLaunch L)
     const long long N = L.N;
     if (p >= N) return;
     constexpr int NP = DIM == 2 ? 3 : 6;
+    double G[DIM][DIM];
+    if constexpr (AUX) {
+        aux_gradient<DIM>(L, job, p, G);
+    } else {
     const float *X = L.xyz + (size_t)job * DIM * N;
     const unsigned char *S = L.status + (size_t)job * N;
     const long long idx[3] = {p % L.n[0], (p / L.n[0]) % L.n[1], DIM == 3 ? p / ((long long)L.n[0] * L.n[1]) : 0};
-    double G[DIM][DIM];
     bool valid = S[p] == LCS_TRACER_OK;
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
@@ -154,6 +180,7 @@ __global__ void __launch_bounds__(256) cg_ftle_kernel(CgLaunch L)
             }
             G[a][b] = d;
         }
+    }
     }
     // Eq. 1: C_ij = sum_a G_ai G_aj, packed upper triangle row by row
     double C[NP];
@@ -203,10 +230,19 @@ cudaError_t launch_cg_ftle(const CgLaunch &L0, cudaStream_t s)
     }
     int bt = 256;
     dim3 grid((unsigned)((L.N + bt - 1) / bt), (unsigned)L.njobs);
-    const bool eig = L.eigval || L.eigvec;
-    if (L.dim == 2)
-        eig ? cg_ftle_kernel<2, true><<<grid, bt, 0, s>>>(L) : cg_ftle_kernel<2, false><<<grid, bt, 0, s>>>(L);
-    else
-        eig ? cg_ftle_kernel<3, true><<<grid, bt, 0, s>>>(L) : cg_ftle_kernel<3, false><<<grid, bt, 0, s>>>(L);
+    const bool eig = L.eigval || L.eigvec, aux = L.x0aux != nullptr;
+#define CG_LAUNCH(D, E, A) cg_ftle_kernel<D, E, A><<<grid, bt, 0, s>>>(L)
+    if (L.dim == 2) {
+        if (aux)
+            eig ? CG_LAUNCH(2, true, true) : CG_LAUNCH(2, false, true);
+        else
+            eig ? CG_LAUNCH(2, true, false) : CG_LAUNCH(2, false, false);
+    } else {
+        if (aux)
+            eig ? CG_LAUNCH(3, true, true) : CG_LAUNCH(3, false, true);
+        else
+            eig ? CG_LAUNCH(3, true, false) : CG_LAUNCH(3, false, false);
+    }
+#undef CG_LAUNCH
     return cudaGetLastError();
 }

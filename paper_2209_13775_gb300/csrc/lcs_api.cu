@@ -497,6 +497,63 @@ cudaError_t launch_seed_grid(int dim, const int n[3], const double lo[3], const 
     return cudaGetLastError();
 }
 
+// auxiliary point (p * dim + b) * 2 + s = seed p moved by (1 - 2s) delta[b] along axis b
+__global__ void seed_aux_kernel(int dim, const float *__restrict__ lat, long long N, double d0, double d1,
+                                double d2, float *__restrict__ out)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long M = N * 2 * dim;
+    if (t >= M) return;
+    const long long p = t / (2 * dim);
+    const int b = (int)((t / 2) % dim), sgn = (int)(t & 1);
+    const double d = b == 0 ? d0 : (b == 1 ? d1 : d2);
+    for (int a = 0; a < dim; ++a) {
+        const float x = lat[a * N + p];
+        out[a * M + t] = a == b ? __double2float_rn(__dadd_rn((double)x, sgn ? -d : d)) : x;
+    }
+}
+
+cudaError_t launch_seed_aux(int dim, const float *lattice, long long N, const double *delta, float *out,
+                            cudaStream_t s)
+{
+    const long long M = N * 2 * dim;
+    if (M == 0) return cudaSuccess;
+    seed_aux_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(dim, lattice, N, delta[0], delta[1],
+                                                                  dim > 2 ? delta[2] : 0.0, out);
+    return cudaGetLastError();
+}
+
+extern "C" lcs_status lcs_seed_aux(lcs_ctx *ctx, const lcs_seeds *lat, const double *delta, lcs_seeds **out)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!lat || !delta || !out) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_aux: null argument");
+    *out = nullptr;
+    if (lat->aux_base_N > 0 || lat->d_cells)
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_aux: needs a lattice made on a rectilinear field");
+    for (int a = 0; a < lat->dim; ++a)
+        if (!(delta[a] > 0.0) || !isfinite(delta[a]))
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_aux: delta[%d] = %g must be finite and > 0", a, delta[a]);
+    if (lat->N > ((1LL << 31) - 1) / (2 * lat->dim)) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_aux: too many seeds");
+    lcs_seeds *s = new (std::nothrow) lcs_seeds(*lat);
+    if (!s) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
+    s->uid = lcs_next_uid();
+    s->aux_base_N = lat->N;
+    s->N = lat->N * 2 * lat->dim;
+    for (int a = 0; a < 3; ++a) s->aux_delta[a] = a < lat->dim ? delta[a] : 0.0;
+    s->d_xyz = nullptr;
+    s->d_cells = nullptr;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_xyz, sizeof(float) * s->dim * (size_t)s->N);
+    if (e == cudaSuccess) e = launch_seed_aux(s->dim, lat->d_xyz, lat->N, s->aux_delta, s->d_xyz, ctx->stream);
+    if (e != cudaSuccess) {
+        lcs_free_seeds(s);
+        return lcs_fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_seed_aux: %s",
+                        cudaGetErrorString(e));
+    }
+    *out = s;
+    return LCS_OK;
+}
+
 extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const lcs_field *field, lcs_seeds **out)
 {
     if (!ctx) return LCS_EINVAL;
@@ -997,11 +1054,13 @@ static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *f
     if (!fm) return lcs_fail(ctx, LCS_EINVAL, "%s: null flow map", who);
     if (job < -1 || job >= fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "%s: job %d out of range", who, job);
     const lcs_seeds *s = fm->seeds;
-    for (int a = 0; a < s->dim; ++a)
-        if (s->n[a] < 3) return lcs_fail(ctx, LCS_EINVAL, "%s: the lattice needs >= 3 seeds per axis", who);
+    const bool aux = s->aux_base_N > 0;
+    if (!aux)
+        for (int a = 0; a < s->dim; ++a)
+            if (s->n[a] < 3) return lcs_fail(ctx, LCS_EINVAL, "%s: the lattice needs >= 3 seeds per axis", who);
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     int j0 = job < 0 ? 0 : job, nj = job < 0 ? fm->njobs : 1;
-    size_t N = (size_t)fm->N;
+    size_t N = (size_t)(aux ? s->aux_base_N : fm->N);   // outputs per job: one per lattice seed
     int np = fm->dim == 2 ? 3 : 6;
     CgLaunch L;
     L.dim = fm->dim;
@@ -1011,12 +1070,14 @@ static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *f
         L.h[a] = s->h[a];
         L.period[a] = s->period[a];
     }
-    L.N = fm->N;
+    L.N = (long long)N;
     L.job0 = j0;
     L.njobs = nj;
     L.xyz = fm->d_xyz;
     L.status = fm->d_status;
     L.absT = fm->d_absT;
+    L.x0aux = aux ? s->d_xyz : nullptr;
+    L.npts = fm->N;
     const size_t dim = (size_t)fm->dim;
     size_t bC = C ? sizeof(double) * np * N * nj : 0, bL = lam ? sizeof(double) * N * nj : 0,
            bF = ftle ? sizeof(float) * N * nj : 0, bE = eigval ? sizeof(double) * dim * N * nj : 0,
@@ -1076,6 +1137,7 @@ extern "C" lcs_status lcs_ftle_early(lcs_ctx *ctx, const lcs_field *f, const lcs
     if (o->method != LCS_RK4 || f->kind != LCS_RECTILINEAR)
         return lcs_fail(ctx, LCS_EUNSUPPORTED, "%s: fixed-step RK4 on a rectilinear field only", who);
     if (f->dim != s->dim || fm->seeds != s) return lcs_fail(ctx, LCS_EINVAL, "%s: field, seeds and flow map differ", who);
+    if (s->aux_base_N > 0) return lcs_fail(ctx, LCS_EUNSUPPORTED, "%s: not for auxiliary points", who);
     const int njobs = o->njobs > 1 ? o->njobs : 1;
     if (job < 0 || job >= njobs || njobs > fm->njobs)
         return lcs_fail(ctx, LCS_EINVAL, "%s: job %d out of range of the options' %d jobs", who, job, njobs);

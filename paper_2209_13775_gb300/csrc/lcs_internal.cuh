@@ -114,6 +114,8 @@ struct lcs_seeds {
     unsigned long long field_uid = 0;  // the tet field the cells refer to
     double h[3] = {1, 1, 1};           // lattice step per axis
     double period[3] = {0, 0, 0};      // hi - lo on periodic axes
+    long long aux_base_N = 0;          // > 0: auxiliary points of a lattice of that many seeds (lcs_seed_aux)
+    double aux_delta[3] = {0, 0, 0};
 };
 
 struct lcs_flowmap {
@@ -243,6 +245,8 @@ struct CgLaunch {
     const float *xyz;            // flow map base [njobs_total][dim][N]
     const unsigned char *status; // [njobs_total][N]
     const float *texit = nullptr; // [njobs_total][N] (early evaluation only)
+    const float *x0aux = nullptr; // auxiliary points: their FP32 starting points [dim][npts]; null: lattice
+    long long npts = 0;          // auxiliary points per job (N * 2 dim)
     const double *absT;          // [njobs_total] |T|
     double *C;                   // [njobs][N][np] or null
     double *lam;                 // [njobs][N] or null
@@ -291,6 +295,8 @@ lcs_status lcs_fail(lcs_ctx *ctx, lcs_status st, const char *fmt, ...);
 
 // ------------------------------------------------------------------ misc
 
+cudaError_t launch_seed_aux(int dim, const float *lattice, long long N, const double *delta, float *out,
+                            cudaStream_t s);
 cudaError_t launch_seed_grid(int dim, const int n[3], const double lo[3], const double hi[3],
                              const int periodic[3], long long N, float *out, cudaStream_t s);
 

@@ -1,0 +1,134 @@
+"""Auxiliary-point flow-map gradient (Sec. 2 "Seed" and "Cauchy-Green") through lcs_seed_aux and the
+CG calls: the auxiliary points bit-identical to the oracle's, their FTLE against the oracle's within
+the fixed-step tolerances, C bit-identical to the oracle's from the same FP32 positions, and, with the
+lattice step as spacing on a dyadic lattice, equal to the lattice differences inside the lattice.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_13775_gb300 import inputs, lcs
+from gpu_util import check_ftle, rect_desc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    c = lcs.lcs_create(0, torch.cuda.current_stream())
+    yield c
+    lcs.lcs_destroy(c)
+
+
+def run_aux(ctx, g, n, lo, hi, periodic, delta, T, dt, variant=0):
+    field = lcs.lcs_load_field(ctx, rect_desc(g), g.frames)
+    lat = lcs.lcs_seed_grid(ctx, lcs.seed_desc(g.dim, n, lo, hi, periodic))
+    aux = lcs.lcs_seed_aux(ctx, lat, delta)
+    N, M = lcs.lcs_seeds_count(lat), lcs.lcs_seeds_count(aux)
+    assert M == N * 2 * g.dim
+    xa = np.empty((g.dim, M), dtype=np.float32)
+    lcs.lcs_seeds_get(ctx, aux, xa)
+    fm = lcs.lcs_flowmap_create(ctx, aux, 1)
+    lcs.lcs_advect(ctx, field, aux, lcs.advect_opts(lcs.RK4, T=T, dt=dt, variant=variant), fm)
+    x = np.empty((g.dim, M), dtype=np.float32)
+    st = np.empty(M, dtype=np.uint8)
+    lcs.lcs_flowmap_get(ctx, fm, 0, x, st)
+    f = np.empty(N, dtype=np.float32)
+    C = np.empty((N, 3 if g.dim == 2 else 6))
+    lcs.lcs_ftle(ctx, fm, 0, f, None, C)
+    ev = np.empty((N, g.dim))
+    lcs.lcs_cg_eigen(ctx, fm, 0, ev)
+    lcs.lcs_synchronize(ctx)
+    out = dict(xa=xa, x=x, st=st, ftle=f, C=C, ev=ev)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(aux)
+    lcs.lcs_free_seeds(lat)
+    lcs.lcs_free_field(field)
+    return out
+
+
+def oracle_aux(g, n, lo, hi, periodic, delta, T, dt):
+    F = oracle.RectField(g.frames, g.times, g.origin, g.spacing, g.periodic, g.time_periodic, g.period)
+    endpoint = [0 if p else 1 for p in periodic]
+    xa = oracle.aux_points(oracle.seed_grid(g.dim, n, lo, hi, endpoint), delta)
+    xT, st, _ = oracle.rk4(F, xa.astype(np.float64), 0.0, T, dt)
+    G = oracle.aux_gradient(xa, xT, st)
+    C = oracle.cauchy_green(G)
+    lam, sig = oracle.ftle(C, g.dim, T)
+    return xa, st, sig
+
+
+def test_aux_gyre(ctx):
+    g = inputs.double_gyre()
+    n, lo, hi, T, dt = (96, 48), (0.0, 0.0), (2.0, 1.0), 5.0, 0.05
+    delta = [2.0 / 95 / 8, 1.0 / 47 / 8]
+    r = run_aux(ctx, g, n, lo, hi, (0, 0), delta, T, dt)
+    xa, st, sig = oracle_aux(g, n, lo, hi, (0, 0), delta, T, dt)
+    np.testing.assert_array_equal(r["xa"], xa)
+    np.testing.assert_array_equal(r["st"], st)
+    check_ftle(r["ftle"], sig)
+    # C from the GPU's own positions: the oracle's formula on them, bit for bit
+    G = oracle.aux_gradient(r["xa"], r["x"].astype(np.float64), r["st"])
+    np.testing.assert_array_equal(r["C"], oracle.cauchy_green(G))
+    np.testing.assert_allclose(r["ev"][:, -1], oracle.ftle(r["C"], 2, T)[0], rtol=1e-12)
+
+
+@pytest.mark.parametrize("variant", [1, 3])
+def test_aux_abc(ctx, variant):
+    g = inputs.abc(n=32, nframes=17, t_end=2.0)
+    L = 2 * np.pi
+    n, lo, hi, T, dt = (20, 18, 16), (0.0, 0.0, 0.0), (L, L, L), 2.0, 0.02
+    delta = [L / 20 / 4, L / 18 / 4, L / 16 / 4]
+    r = run_aux(ctx, g, n, lo, hi, (1, 1, 1), delta, T, dt, variant=variant)
+    xa, st, sig = oracle_aux(g, n, lo, hi, (1, 1, 1), delta, T, dt)
+    np.testing.assert_array_equal(r["xa"], xa)
+    check_ftle(r["ftle"], sig)
+    G = oracle.aux_gradient(r["xa"], r["x"].astype(np.float64), r["st"])
+    np.testing.assert_array_equal(r["C"], oracle.cauchy_green(G))
+
+
+def test_aux_with_lattice_step_equals_lattice(ctx):
+    g = inputs.double_gyre()
+    n, lo, hi, T, dt = (65, 33), (0.0, 0.0), (2.0, 1.0), 4.0, 0.05     # steps 1/32: dyadic
+    r = run_aux(ctx, g, n, lo, hi, (0, 0), [1.0 / 32, 1.0 / 32], T, dt)
+    field = lcs.lcs_load_field(ctx, rect_desc(g), g.frames)
+    lat = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, lo, hi))
+    N = lcs.lcs_seeds_count(lat)
+    fm = lcs.lcs_flowmap_create(ctx, lat, 1)
+    lcs.lcs_advect(ctx, field, lat, lcs.advect_opts(lcs.RK4, T=T, dt=dt), fm)
+    C = np.empty((N, 3))
+    lcs.lcs_cauchy_green(ctx, fm, 0, C)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(lat)
+    lcs.lcs_free_field(field)
+    ii, jj = np.meshgrid(np.arange(1, n[0] - 1), np.arange(1, n[1] - 1))
+    inner = (jj * n[0] + ii).ravel()
+    np.testing.assert_array_equal(r["C"][inner], C[inner])
+
+
+def test_aux_rejects(ctx):
+    g = inputs.double_gyre(nx=17, ny=9, nframes=3, t_end=1.0)
+    lat = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (8, 4), (0.0, 0.0), (2.0, 1.0)))
+    try:
+        for d in ([0.0, 0.1], [0.1, -1.0], [float("nan"), 0.1]):
+            with pytest.raises(lcs.LcsError) as e:
+                lcs.lcs_seed_aux(ctx, lat, d)
+            assert e.value.status == 1
+        aux = lcs.lcs_seed_aux(ctx, lat, [0.01, 0.01])
+        with pytest.raises(lcs.LcsError):      # auxiliary points of auxiliary points
+            lcs.lcs_seed_aux(ctx, aux, [0.01, 0.01])
+        field = lcs.lcs_load_field(ctx, rect_desc(g), g.frames)
+        fm = lcs.lcs_flowmap_create(ctx, aux, 1)
+        opts = lcs.advect_opts(lcs.RK4, T=1.0, dt=0.05)
+        lcs.lcs_advect(ctx, field, aux, opts, fm)
+        with pytest.raises(lcs.LcsError) as e:
+            lcs.lcs_ftle_early(ctx, field, aux, opts, fm, 0, np.empty(32, dtype=np.float32))
+        assert e.value.status == 7
+        lcs.lcs_free_flowmap(fm)
+        lcs.lcs_free_field(field)
+        lcs.lcs_free_seeds(aux)
+    finally:
+        lcs.lcs_free_seeds(lat)
