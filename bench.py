@@ -58,11 +58,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seeds-side", type=int, default=N_SIDE,
                    help="seed lattice side (default 256; smaller only for profiling captures)")
-    p.add_argument("--config", default="c2", choices=["c2", "c3", "c3x", "c4", "c5"],
+    p.add_argument("--config", default="c2", choices=["c2", "c3", "c3x", "c4", "c5", "next"],
                    help="c2: the 3D ABC workload (default, the headline); c3: the batched sliding-window "
                         "workload; c3x: its full cross product of horizons from multi-horizon snapshots; "
-                        "c4: adaptive DP5(4) on the tetrahedral pipe; c5: the learned surrogate")
+                        "c4: adaptive DP5(4) on the tetrahedral pipe; c5: the learned surrogate; next: the "
+                        "eigenvectors, early Cauchy-Green and auxiliary-point passes")
     p.add_argument("--train-epochs", type=int, default=4, help="c5: training epochs over the 50M samples")
+    p.add_argument("--c5-side", type=int, default=16384,
+                   help="c5: seed lattice side along x (y is half; default 16384, smaller only for profiling)")
     p.add_argument("--grid", type=int, default=N_GRID,
                    help="velocity grid side (default 128; smaller only for profiling captures)")
     return p.parse_args()
@@ -782,7 +785,8 @@ def c5_arm(args, rank, world, local):
                                                                    dt=C5_DT), samples)
     t_train = time.perf_counter() - t_train
     del samples
-    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, C5_N, (0.0, 0.0), (2.0, 1.0)))
+    c5n = (args.c5_side, args.c5_side // 2)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, c5n, (0.0, 0.0), (2.0, 1.0)))
     N = lcs.lcs_seeds_count(seeds)
     T = C5_K * C5_TAU
     fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
@@ -834,7 +838,9 @@ def c5_arm(args, rank, world, local):
         "metric": METRIC, "value": N * 1.0 / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 (network), f32 (integrator)", "data": "synthetic",
-        "config": {"workload": C5_WORKLOAD, "seeds": N, "K": C5_K, "tau": C5_TAU, "gate_tol": C5_TOL,
+        "config": {"workload": C5_WORKLOAD if c5n == C5_N else
+                   C5_WORKLOAD.replace("16384x8192 seed lattice (2^27 seeds)", "%dx%d seed lattice" % c5n),
+                   "seeds": N, "K": C5_K, "tau": C5_TAU, "gate_tol": C5_TOL,
                    "train_samples": C5_SAMPLES, "train_batch": C5_BATCH, "train_epochs": args.train_epochs,
                    "l2": "no flush: each step writes 2.7 GB of flow map and FTLE (> 129 MB L2)"},
         "surrogate": {"train_s": round(t_train, 2), "loss_per_epoch": [float(x) for x in hist],
@@ -882,6 +888,105 @@ def _src_sha():
     return h.hexdigest()[:12]
 
 
+# ------------------------------------- eigenvectors, early CG, auxiliary points
+
+def next_arm(args, rank, world, local):
+    """Times of the passes that widen the pipeline: all eigenpairs of C on the 3D ABC lattice (256^3),
+    the early Cauchy-Green evaluation on the double gyre cut to x in [0, 1.5] (2^21 seeds, T = 6),
+    and the auxiliary-point FTLE of a 1024x512 gyre lattice (4 points per seed)."""
+    import torch
+
+    from paper_2209_13775_gb300 import inputs, lcs
+    from dataclasses import replace
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = lcs.lcs_create(local, stream)
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        a, b = ev()
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    out = {}
+    # 1. eigenpairs of C on the ABC lattice (the flow map of one C2 step)
+    g = inputs.abc(n=N_GRID, nframes=N_FRAMES, t_end=T_END)
+    field = lcs.lcs_load_field(ctx, lcs.field_desc(3, g.n, g.origin, g.spacing, g.periodic, g.times),
+                               torch.from_numpy(g.frames).cuda())
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, (N_SIDE,) * 3, (0.0,) * 3, (L,) * 3, (1, 1, 1)))
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, t0=0.0, T=T_END, dt=DT), fm)
+    eigval = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    eigvec = torch.empty((N, 3, 3), dtype=torch.float64, device="cuda")
+    ftle = torch.empty(N, dtype=torch.float32, device="cuda")
+    ms_eig = timed(lambda: lcs.lcs_cg_eigen(ctx, fm, 0, eigval, eigvec), max(args.steps, 3))
+    ms_ftle = timed(lambda: lcs.lcs_ftle(ctx, fm, 0, ftle), max(args.steps, 3))
+    out["eigen_abc_256cubed"] = {"ms": ms_eig, "seeds_per_s": N / ms_eig * 1e3, "ftle_pass_ms": ms_ftle,
+                                 "bytes_written": N * 96, "write_gbs": N * 96 / ms_eig / 1e6}
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    # 2. early CG on the truncated gyre
+    g2 = inputs.double_gyre()
+    g2 = replace(g2, frames=np.ascontiguousarray(g2.frames[:, :, :97]))
+    f2 = lcs.lcs_load_field(ctx, lcs.field_desc(2, g2.n, g2.origin, g2.spacing, g2.periodic, g2.times,
+                                                g2.time_periodic, g2.period), g2.frames)
+    s2 = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (2048, 1024), (0.0, 0.0), (1.5, 1.0)))
+    N2 = lcs.lcs_seeds_count(s2)
+    fm2 = lcs.lcs_flowmap_create(ctx, s2, 1)
+    o2 = lcs.advect_opts(lcs.RK4, t0=0.0, T=6.0, dt=0.05)
+    lcs.lcs_advect(ctx, f2, s2, o2, fm2)
+    fe = torch.empty(N2, dtype=torch.float32, device="cuda")
+    te = torch.empty(N2, dtype=torch.float32, device="cuda")
+    ms_early = timed(lambda: lcs.lcs_ftle_early(ctx, f2, s2, o2, fm2, 0, fe, te), max(args.steps, 3))
+    ms_adv2 = timed(lambda: lcs.lcs_advect(ctx, f2, s2, o2, fm2), 2)
+    n_early = int(((te > 0) & (te < 6.0)).sum().item())
+    out["early_cg_gyre_2M"] = {"ms": ms_early, "early_seeds": n_early, "seeds": N2, "advect_ms": ms_adv2,
+                               "note": "the early seeds' stencils (5 tracers each) are re-integrated"}
+    lcs.lcs_free_flowmap(fm2)
+    # 3. auxiliary-point FTLE on a 1024x512 gyre lattice (full gyre box)
+    lat = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (1024, 512), (0.0, 0.0), (2.0, 1.0)))
+    aux = lcs.lcs_seed_aux(ctx, lat, [2.0 / 1023 / 8, 1.0 / 511 / 8])
+    M = lcs.lcs_seeds_count(aux)
+    g3 = inputs.double_gyre()
+    f3 = lcs.lcs_load_field(ctx, lcs.field_desc(2, g3.n, g3.origin, g3.spacing, g3.periodic, g3.times,
+                                                g3.time_periodic, g3.period), g3.frames)
+    fm3 = lcs.lcs_flowmap_create(ctx, aux, 1)
+    o3 = lcs.advect_opts(lcs.RK4, t0=0.0, T=10.0, dt=0.05)
+    fa = torch.empty(1024 * 512, dtype=torch.float32, device="cuda")
+
+    def aux_step():
+        lcs.lcs_advect(ctx, f3, aux, o3, fm3)
+        lcs.lcs_ftle(ctx, fm3, 0, fa)
+
+    ms_aux = timed(aux_step, max(args.steps, 3))
+    out["aux_points_gyre_1024x512"] = {"ms": ms_aux, "points": M, "ftle_seeds_per_s": 1024 * 512 / ms_aux * 1e3,
+                                       "tracer_steps_per_s": M * 200 / ms_aux * 1e3}
+    for h in (fm3,):
+        lcs.lcs_free_flowmap(h)
+    for h in (aux, lat, s2):
+        lcs.lcs_free_seeds(h)
+    for h in (f2, f3):
+        lcs.lcs_free_field(h)
+    lcs.lcs_destroy(ctx)
+    line = {"metric": METRIC, "value": out["eigen_abc_256cubed"]["seeds_per_s"], "unit": "seeds/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (eigen), f32 (tracers)", "data": "synthetic",
+            "config": {"workload": "widening passes: eigenpairs of C (ABC 256^3 after the C2 integration), early "
+                                   "CG (gyre cut to x<=1.5, 2048x1024 seeds, T=6), auxiliary-point FTLE "
+                                   "(gyre 1024x512, delta = 1/8 lattice step, T=10)"},
+            "passes": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -896,6 +1001,9 @@ def main():
         return
     if args.config == "c4":
         c4_arm(args, rank, world, local)
+        return
+    if args.config == "next":
+        next_arm(args, rank, world, local)
         return
     if args.config == "c5":
         c5_arm(args, rank, world, local)
