@@ -462,7 +462,9 @@ def c3_arm(args, rank, world, local):
         "tracer_steps_per_s": tracer_steps * args.steps / el,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,
-                     "kernel": "rk4_ring2d_kernel (variant %d)" % opts.variant, "flop_per_launch": flops,
+                     "kernel": {1: "rk4_gather_kernel", 2: "rk4_ring2d_kernel", 4: "rk4_ring2d_kernel (persistent)",
+                                5: "rk4_slice2d_kernel (with slice2d_fill_kernel)"}.get(opts.variant, "?")
+                               + " (variant %d)" % opts.variant, "flop_per_launch": flops,
                      "avg_launch_ms": adv_ms / max(adv_n, 1), "launches": adv_n,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, pk_kind)},
         "phases_ms": {"advect": adv_ms, "cg_ftle": cg_ms},

@@ -406,6 +406,156 @@ __global__ void __launch_bounds__(512, 1) rk4_ring2d_kernel(RectParams P, const 
     __syncthreads();
 }
 
+// ========================================================== 2D time slices
+
+// Variant 5 (2D): every stage time of every job gets its own time slice, the field blended
+// to that time once (interp's node-first arithmetic, FP32), stored per node as two float4
+// quads (u(i,j), u(i1,j), u(i,j1), u(i1,j1)) and the same for v, with i1, j1 the next node
+// (wrapped on a periodic axis, clamped on a closed one).  A stage evaluation is then the
+// cell and weights of make_stencil and two 16-byte loads, with the products of interp in
+// interp's order: bit-identical to the other variants.  Slice (job, n, stage) is number
+// off[job] + 3 n + stage, each 2 * nodes float4.
+struct Slice2dOffsets {
+    long long off[LCS_MAX_JOBS];
+};
+
+__global__ void slice2d_fill_kernel(RectParams P, const char *__restrict__ frames, size_t fstride, int storage,
+                                    const SchedEntry *__restrict__ sched, int nsteps_max,
+                                    const int *__restrict__ job_nsteps, Slice2dOffsets O, long long nodes,
+                                    float4 *__restrict__ slices)
+{
+    const int job = blockIdx.y;
+    const long long per_job = 3LL * job_nsteps[job] * nodes;
+    const SchedEntry *sc = sched + (size_t)job * nsteps_max * 3;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < per_job;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long l = t / nodes, v = t % nodes;
+        const SchedEntry e = load_sched(sc + l);   // slice l of the job = schedule entry l (= 3 n + stage)
+        const int i = (int)(v % P.n[0]), j = (int)(v / P.n[0]);
+        const int i1 = P.periodic[0] ? (i + 1 == P.n[0] ? 0 : i + 1) : min(i + 1, P.n[0] - 1);
+        const int j1 = P.periodic[1] ? (j + 1 == P.n[1] ? 0 : j + 1) : min(j + 1, P.n[1] - 1);
+        const int corner[4] = {(int)(i + j * P.sy), (int)(i1 + j * P.sy), (int)(i + j1 * P.sy),
+                               (int)(i1 + j1 * P.sy)};
+        const char *fa = frames + (size_t)e.k * fstride;
+        float u[4][2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float va[2], vb[2];
+            if (storage == LCS_F32)
+                Node<2, LCS_F32>::ld(fa, corner[q], va);
+            else if (storage == LCS_F16)
+                Node<2, LCS_F16>::ld(fa, corner[q], va);
+            else
+                Node<2, LCS_BF16>::ld(fa, corner[q], va);
+            if (e.a == 0.0f) {   // frame k + 1 is not read (it may not exist)
+                u[q][0] = va[0];
+                u[q][1] = va[1];
+                continue;
+            }
+            const char *fb = fa + fstride;
+            if (storage == LCS_F32)
+                Node<2, LCS_F32>::ld(fb, corner[q], vb);
+            else if (storage == LCS_F16)
+                Node<2, LCS_F16>::ld(fb, corner[q], vb);
+            else
+                Node<2, LCS_BF16>::ld(fb, corner[q], vb);
+            const float g = 1.0f - e.a;
+            u[q][0] = tblend(va[0], vb[0], e.a, g);
+            u[q][1] = tblend(va[1], vb[1], e.a, g);
+        }
+        float4 *o = slices + (O.off[job] + l) * 2 * nodes + 2 * v;
+        o[0] = make_float4(u[0][0], u[1][0], u[2][0], u[3][0]);
+        o[1] = make_float4(u[0][1], u[1][1], u[2][1], u[3][1]);
+    }
+}
+
+// u(x) from a 2D slice: make_stencil's cell and weights, interp's products and order
+__device__ __forceinline__ void interp2s(const RectParams &P, const float *x, const float4 *__restrict__ sl, float *u)
+{
+    Stencil<2> S;
+    make_stencil<2>(P, x, S);
+    const float4 qu = __ldg(sl + 2 * S.v[0]), qv = __ldg(sl + 2 * S.v[0] + 1);
+    u[0] = fmaf(S.w[3], qu.w, fmaf(S.w[2], qu.z, fmaf(S.w[1], qu.y, fmaf(S.w[0], qu.x, 0.0f))));
+    u[1] = fmaf(S.w[3], qv.w, fmaf(S.w[2], qv.z, fmaf(S.w[1], qv.y, fmaf(S.w[0], qv.x, 0.0f))));
+}
+
+__global__ void __launch_bounds__(256) rk4_slice2d_kernel(RectParams P, const float4 *__restrict__ slices,
+                                                          long long nodes, Slice2dOffsets O, Rk4Args A)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int job = blockIdx.y;
+    if (i >= A.N) return;
+    float x[2] = {A.seeds[i], A.seeds[A.N + i]};
+    int img[2] = {0, 0};
+    wrap_periodic<2>(P, x, img);
+    const int ns = A.job_nsteps[job];
+    const float h = A.job_h[job];
+    const float4 *sj = slices + O.off[job] * 2 * nodes;
+    const size_t ss = 2 * (size_t)nodes;
+    unsigned char st = LCS_TRACER_OK;
+    float te = A.job_tend[job];
+    int si = 0;   // next snapshot
+    for (int n = 0; n < ns; ++n) {
+        const float4 *s0 = sj + (size_t)(3 * n) * ss;
+        float k1[2], k2[2], k3[2], k4[2], y[2];
+        const float hh = 0.5f * h;
+        interp2s(P, x, s0, k1);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) y[c] = fmaf(hh, k1[c], x[c]);
+        interp2s(P, y, s0 + ss, k2);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) y[c] = fmaf(hh, k2[c], x[c]);
+        interp2s(P, y, s0 + ss, k3);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) y[c] = fmaf(h, k3[c], x[c]);
+        interp2s(P, y, s0 + 2 * ss, k4);
+        const float h6 = h * (1.0f / 6.0f);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
+        wrap_periodic<2>(P, x, img);
+        if (rect_left<2>(P, x)) {
+            st = LCS_TRACER_LEFT;
+            te = fmaf((float)(n + 1), h, A.job_t0[job]);
+            break;
+        }
+        for (; si < A.nsnap && snap_step(A, si, ns) == n + 1; ++si)
+            store_tracer<2>(P, A, snap_slot(A, job, si), i, x, img, st, snap_exit(A, job, si, st, te));
+    }
+    for (; si < A.nsnap; ++si)
+        store_tracer<2>(P, A, snap_slot(A, job, si), i, x, img, st, snap_exit(A, job, si, st, te));
+    store_tracer<2>(P, A, job, i, x, img, st, te);
+}
+
+size_t rk4_slice2d_bytes(const lcs_field *f, int njobs, const int *host_nsteps)
+{
+    long long n = 0;
+    for (int j = 0; j < njobs; ++j) n += 3LL * host_nsteps[j];
+    return (size_t)n * 2 * (size_t)f->nodes * sizeof(float4);
+}
+
+static cudaError_t launch_slice2d(const RectParams &P, const lcs_field *f, const Rk4Args &A, const Rk4Launch &L,
+                                  int bt, cudaStream_t s)
+{
+    Slice2dOffsets O;
+    long long acc = 0;
+    for (int j = 0; j < L.njobs; ++j) {
+        O.off[j] = acc;
+        acc += 3LL * L.host_nsteps[j];
+    }
+    float4 *slices = (float4 *)L.work;
+    const long long nodes = f->nodes;
+    lcs_tm_begin(L.ctx, 2, s);
+    slice2d_fill_kernel<<<dim3(1024, (unsigned)L.njobs), 256, 0, s>>>(P, (const char *)f->d_frames, f->frame_stride,
+                                                                      f->storage, A.sched, A.nsteps_max,
+                                                                      A.job_nsteps, O, nodes, slices);
+    lcs_tm_end(L.ctx, 2, s);
+    lcs_tm_begin(L.ctx, 0, s);
+    dim3 grid((unsigned)((A.N + bt - 1) / bt), (unsigned)L.njobs);
+    rk4_slice2d_kernel<<<grid, bt, 0, s>>>(P, slices, nodes, O, A);
+    lcs_tm_end(L.ctx, 0, s);
+    return cudaGetLastError();
+}
+
 // ================================================================ dispatch
 
 RectParams make_rect_params(const lcs_field *f)
@@ -513,8 +663,14 @@ int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
     if (variant == 4 && !queue_ok) variant = 2;
     if (variant == 3 && !sorted_ok) variant = 1;
     cudaError_t e;
+    if (variant == 5 && !(f->dim == 2 && L.work != nullptr)) variant = 1;
     if (variant == 3) {
         e = launch_rk4_episodes(P, f, A, L, s);
+        return e == cudaSuccess ? variant : -1;
+    }
+    if (variant == 5) {
+        int bt = L.block_threads > 0 && L.block_threads <= 256 ? L.block_threads : 256;
+        e = launch_slice2d(P, f, A, L, bt, s);
         return e == cudaSuccess ? variant : -1;
     }
     lcs_tm_begin(ctx, 0, s);

@@ -111,6 +111,9 @@ extern "C" lcs_status lcs_autotune(lcs_ctx *ctx, const lcs_field *f, const lcs_s
         const bool ring = 3 * f->frame_stride <= ctx->smem_optin;
         for (int bt : {128, 256})
             cands.push_back({1, bt, 1, 0});
+        if (f->kind == LCS_RECTILINEAR)
+            for (int bt : {128, 256})
+                cands.push_back({5, bt, 1, 0});
         if (ring)
             for (int v : {2, 4}) {
                 if (v == 4 && njobs < 2) continue;

@@ -683,7 +683,7 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct AdvectLayout {
     size_t jb, sb, wb;
-    bool want_sorted;
+    bool want_work;
     int E;
 };
 
@@ -693,9 +693,14 @@ static AdvectLayout advect_layout(const lcs_field *f, const lcs_seeds *s, const 
     Ly.jb = 2 * align256(sizeof(int) * J.njobs) + 3 * align256(sizeof(float) * J.njobs) + 256 +
             align256(sizeof(int) * LCS_MAX_SNAP) + align256(sizeof(float) * J.njobs * LCS_MAX_SNAP);
     Ly.sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
-    Ly.want_sorted = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
+    Ly.want_work = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
     Ly.E = o->episode_steps > 0 ? std::min(o->episode_steps, 1024) : LCS_EPISODE_STEPS;
-    Ly.wb = Ly.want_sorted ? rk4_sorted_scratch_bytes(s->N, f, Ly.E) : 0;
+    Ly.wb = Ly.want_work ? rk4_sorted_scratch_bytes(s->N, f, Ly.E) : 0;
+    if (f->dim == 2 && f->kind == LCS_RECTILINEAR && o->variant == 5) {
+        const size_t b = rk4_slice2d_bytes(f, J.njobs, J.nsteps);
+        Ly.want_work = b <= LCS_SLICE2D_MAX_BYTES;   // working memory in the same place as the 3D path's
+        Ly.wb = Ly.want_work ? b : 0;
+    }
     return Ly;
 }
 
@@ -704,7 +709,7 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
 {
     const AdvectLayout Ly = advect_layout(f, s, o, J);
     const size_t jb = Ly.jb, sb = Ly.sb;
-    const bool want_sorted = Ly.want_sorted;
+    const bool want_work = Ly.want_work;
     const int E = Ly.E;
     lcs_status st = lcs_scratch_reserve(ctx, jb + sb + Ly.wb);
     if (st != LCS_OK) return st;
@@ -757,7 +762,7 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.snap_n = D.snap_n;
     L.host_snap_n = J.snap_n;
     L.snap_te = D.snap_te;
-    L.work = want_sorted ? (char *)ctx->d_scratch + jb + sb : nullptr;
+    L.work = want_work ? (char *)ctx->d_scratch + jb + sb : nullptr;
     if (f->kind == LCS_TET) {
         cudaError_t e = launch_rk4_tet(ctx, L, s->d_cells, o->walk_limit, ctx->stream);
         if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(e));

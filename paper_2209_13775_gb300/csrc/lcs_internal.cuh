@@ -199,7 +199,8 @@ struct Rk4Launch {
     float *out_texit;
     int block_threads;
     int variant;              // 1 gather, 2 shared-memory ring (2D), 3 re-bundled episodes (3D),
-                              // 4 persistent shared-memory ring over a job/tile work queue (2D)
+                              // 4 persistent shared-memory ring over a job/tile work queue (2D),
+                              // 5 per-stage time slices (2D)
     int episode_steps;        // variant 3: steps between re-bundling (0 = default)
     const int *host_nsteps;   // [njobs] host copy of the step counts
     void *work;               // variant 3 working memory (rk4_sorted_scratch_bytes), or null
@@ -218,6 +219,9 @@ struct Rk4Launch {
 #define LCS_EPISODE_STEPS 32
 
 size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int episode_steps);
+// variant 5 (2D time slices): their bytes for these jobs, and the most lcs_advect reserves for them
+size_t rk4_slice2d_bytes(const lcs_field *f, int njobs, const int *host_nsteps);
+#define LCS_SLICE2D_MAX_BYTES (16ULL << 30)
 
 RectParams make_rect_params(const lcs_field *f);
 

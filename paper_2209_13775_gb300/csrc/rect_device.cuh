@@ -262,43 +262,41 @@ __device__ __forceinline__ void node_load(const char *f, int v, float *u)
         Node<DIM, ST>::lss(f, v, u);
 }
 
-// u = (1 - a) I[frame fa](x) + a I[frame fb](x); frame fb is not read when a == 0
-template <int DIM, int ST, int SRC>
-__device__ __forceinline__ void interp(const Stencil<DIM> &S, const char *fa, const char *fb, float a, float *u)
-{
-    float ua[DIM], ub[DIM], v[DIM];
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) ua[c] = 0.0f;
-#pragma unroll
-    for (int q = 0; q < (1 << DIM); ++q) {
-        node_load<DIM, ST, SRC>(fa, S.v[q], v);
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) ua[c] = fmaf(S.w[q], v[c], ua[c]);
-    }
-    if (a == 0.0f) {
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) u[c] = ua[c];
-        return;
-    }
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) ub[c] = 0.0f;
-#pragma unroll
-    for (int q = 0; q < (1 << DIM); ++q) {
-        node_load<DIM, ST, SRC>(fb, S.v[q], v);
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) ub[c] = fmaf(S.w[q], v[c], ub[c]);
-    }
-    float g = 1.0f - a;
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) u[c] = fmaf(a, ub[c], g * ua[c]);
-}
-
 // Time blend of one node, FP32: u = (1 - a) u_k + a u_{k+1} (exactly u_k when a == 0).
-// 3D fields blend at the nodes first, then interpolate in space; both orders are the
-// same linear map, and every 3D kernel uses this one so that they agree bit for bit.
+// Every kernel blends at the nodes first, then interpolates in space: both orders are the
+// same linear map, and one order everywhere makes the kernels agree bit for bit (and lets
+// a whole field be blended to a stage time once, as a time slice, with the same result).
 __device__ __forceinline__ float tblend(float ua, float ub, float a, float g)
 {
     return fmaf(a, ub, g * ua);
+}
+
+// u = I[(1 - a) frame fa + a frame fb](x), node blends first; frame fb is not read when a == 0
+template <int DIM, int ST, int SRC>
+__device__ __forceinline__ void interp(const Stencil<DIM> &S, const char *fa, const char *fb, float a, float *u)
+{
+    float acc[DIM], va[DIM], vb[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] = 0.0f;
+    if (a == 0.0f) {
+#pragma unroll
+        for (int q = 0; q < (1 << DIM); ++q) {
+            node_load<DIM, ST, SRC>(fa, S.v[q], va);
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) acc[c] = fmaf(S.w[q], va[c], acc[c]);
+        }
+    } else {
+        const float g = 1.0f - a;
+#pragma unroll
+        for (int q = 0; q < (1 << DIM); ++q) {
+            node_load<DIM, ST, SRC>(fa, S.v[q], va);
+            node_load<DIM, ST, SRC>(fb, S.v[q], vb);
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) acc[c] = fmaf(S.w[q], tblend(va[c], vb[c], a, g), acc[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) u[c] = acc[c];
 }
 
 // 3D: u(x, t) from the interval pair k with weight a of frame k + 1

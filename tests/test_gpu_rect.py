@@ -52,7 +52,7 @@ def test_seed_lattice_bit_exact(ctx, dim, n, lo, hi, periodic):
     np.testing.assert_array_equal(dev.cpu().numpy(), got)
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 5])
 @pytest.mark.parametrize("n", [(256, 128), (250, 130)])
 def test_gyre_rk4_parity(ctx, gyre, variant, n):
     lo, hi, T, dt = (0.0, 0.0), (2.0, 1.0), 10.0, 0.05
@@ -65,12 +65,19 @@ def test_gyre_rk4_parity(ctx, gyre, variant, n):
     np.testing.assert_allclose(g["t_exit"][0], np.float32(T), rtol=0, atol=0)
 
 
-def test_ring_and_gather_agree(ctx, gyre):
-    # both kernels evaluate the same FP32 arithmetic; shared-memory staging must not change a bit
-    a = gpu_run(ctx, gyre, (200, 100), (0.0, 0.0), (2.0, 1.0), (0, 0), 5.0, 0.05, t0=2.5, variant=1)
-    b = gpu_run(ctx, gyre, (200, 100), (0.0, 0.0), (2.0, 1.0), (0, 0), 5.0, 0.05, t0=2.5, variant=2)
-    np.testing.assert_array_equal(a["xyz"][0], b["xyz"][0])
-    np.testing.assert_array_equal(a["ftle"][0], b["ftle"][0])
+@pytest.mark.parametrize("storage", [lcs.F32, lcs.F16])
+def test_ring_slices_and_gather_agree(ctx, gyre, storage):
+    # the kernels evaluate the same FP32 arithmetic: shared-memory staging (2) and per-stage time
+    # slices blended once (5) must not change a bit of the one-pass kernel's result (1); the box is
+    # wider than the gyre's so that tracers leave too
+    kw = dict(t0=2.5, storage=storage)
+    a = gpu_run(ctx, gyre, (200, 100), (-0.05, 0.0), (2.05, 1.0), (0, 0), 5.0, 0.05, variant=1, **kw)
+    for v in (2, 5):
+        b = gpu_run(ctx, gyre, (200, 100), (-0.05, 0.0), (2.05, 1.0), (0, 0), 5.0, 0.05, variant=v, **kw)
+        np.testing.assert_array_equal(a["xyz"][0], b["xyz"][0])
+        np.testing.assert_array_equal(a["status"][0], b["status"][0])
+        np.testing.assert_array_equal(a["t_exit"][0], b["t_exit"][0])
+        np.testing.assert_array_equal(a["ftle"][0], b["ftle"][0])
 
 
 def test_gyre_backward_and_periodic_time_wrap(ctx, gyre):
@@ -97,7 +104,7 @@ def test_batched_jobs_equal_single_jobs(ctx, gyre):
     np.testing.assert_array_equal(b["xyz"][3], b["seeds"])
 
 
-@pytest.mark.parametrize("variant,bt,tpt", [(2, 256, 1), (4, 512, 1), (4, 256, 2), (4, 128, 2)])
+@pytest.mark.parametrize("variant,bt,tpt", [(2, 256, 1), (4, 512, 1), (4, 256, 2), (4, 128, 2), (5, 256, 1), (5, 128, 1)])
 def test_persistent_batch_equals_single_jobs(ctx, gyre, variant, bt, tpt):
     # the work-queue kernel (longest jobs first, frame ring kept across items) changes which block
     # runs a tile, never a tracer's arithmetic
@@ -135,8 +142,9 @@ def test_graph_replay_equals_direct_launch(ctx, gyre):
     seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, lo, hi))
     fm = lcs.lcs_flowmap_create(ctx, seeds, 3)
     N = n[0] * n[1]
-    for rep in range(3):
-        o = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1], use_graph=True)
+    for rep in range(4):
+        o = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1], use_graph=True,
+                            variant=5 if rep >= 2 else 0)
         lcs.lcs_advect(ctx, field, seeds, o, fm)
         for j in range(3):
             x = np.empty((2, N), dtype=np.float32)
@@ -162,7 +170,7 @@ def test_autotune_picks_valid_options_and_caches(ctx, gyre, tmp_path):
     cache = str(tmp_path / "tune.txt")
     o = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1])
     lcs.lcs_autotune(ctx, field, seeds, o, cache)
-    assert o.variant in (1, 2, 4) and o.block_threads in (128, 256, 512) and o.tracers_per_thread in (1, 2)
+    assert o.variant in (1, 2, 4, 5) and o.block_threads in (128, 256, 512) and o.tracers_per_thread in (1, 2)
     lines = open(cache).read().strip().splitlines()
     assert len(lines) == 1 and "\t" in lines[0]
     o2 = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1])

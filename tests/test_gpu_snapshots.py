@@ -76,7 +76,7 @@ def check_against_separate(ctx, g, n, lo, hi, periodic, jobs, snap_T, dt, **kw):
     return got
 
 
-@pytest.mark.parametrize("variant,bt,tpt", [(1, 256, 1), (2, 256, 1), (4, 256, 2)])
+@pytest.mark.parametrize("variant,bt,tpt", [(1, 256, 1), (2, 256, 1), (4, 256, 2), (5, 256, 1)])
 def test_snapshots_2d_equal_separate_runs(ctx, gyre, variant, bt, tpt):
     # forward and backward jobs; the last snapshot lies beyond the short job's horizon (it holds
     # that job's final state); seeds on a box larger than the gyre's so that some tracers leave
