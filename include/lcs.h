@@ -229,7 +229,8 @@ typedef struct {
                                    4 = persistent shared-memory ring pulling (job, tile)
                                        items longest-job first (2D, batches);
                                    5 = the field blended once to every stage time of
-                                       every job (2D time slices; up to 16 GiB)         */
+                                       every job (2D time slices; up to 16 GiB; the
+                                       default in 2D when they take at most 2 GiB)     */
     const void *surrogate;      /* LCS_SURROGATE: the lcs_mlp to step with            */
     int episode_steps;          /* variant 3: RK4 steps between re-bundlings (0 = 32) */
     int tracers_per_thread;     /* variants 2 and 4: 1 or 2 tracers per thread (0 = 1) */

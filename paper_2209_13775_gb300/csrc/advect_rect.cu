@@ -655,10 +655,11 @@ int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
     bool sorted_ok = f->dim == 3 && L.work != nullptr;
     bool queue_ok = L.queue != nullptr && L.job_order != nullptr;
     int variant = L.variant;
-    // default: the cached gather in 2D (the autotuner's choice on GB300 whenever the field stays in
-    // L2: the shared-memory ring's per-step block barriers cost more than the loads they save),
+    // default: 2D time slices when lcs_advect reserved them (at most 2 GiB; the autotuner's choice on
+    // GB300 for the sliding-window batches), else the cached gather in 2D (the shared-memory ring's
+    // per-step block barriers cost more than the loads they save while the field stays in L2);
     // re-bundled episodes for large 3D lattices
-    if (variant == 0) variant = sorted_ok && L.N >= LCS_SORTED_MIN_SEEDS ? 3 : 1;
+    if (variant == 0) variant = sorted_ok && L.N >= LCS_SORTED_MIN_SEEDS ? 3 : (f->dim == 2 && L.work ? 5 : 1);
     if ((variant == 2 || variant == 4) && !ring_fits) variant = 1;
     if (variant == 4 && !queue_ok) variant = 2;
     if (variant == 3 && !sorted_ok) variant = 1;

@@ -696,9 +696,10 @@ static AdvectLayout advect_layout(const lcs_field *f, const lcs_seeds *s, const 
     Ly.want_work = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
     Ly.E = o->episode_steps > 0 ? std::min(o->episode_steps, 1024) : LCS_EPISODE_STEPS;
     Ly.wb = Ly.want_work ? rk4_sorted_scratch_bytes(s->N, f, Ly.E) : 0;
-    if (f->dim == 2 && f->kind == LCS_RECTILINEAR && o->variant == 5) {
+    if (f->dim == 2 && f->kind == LCS_RECTILINEAR && (o->variant == 5 || o->variant == 0)) {
+        // 2D time slices: asked for (up to 16 GiB), or by default when they take at most 2 GiB
         const size_t b = rk4_slice2d_bytes(f, J.njobs, J.nsteps);
-        Ly.want_work = b <= LCS_SLICE2D_MAX_BYTES;   // working memory in the same place as the 3D path's
+        Ly.want_work = b <= (o->variant == 5 ? LCS_SLICE2D_MAX_BYTES : LCS_SLICE2D_DEFAULT_BYTES);
         Ly.wb = Ly.want_work ? b : 0;
     }
     return Ly;

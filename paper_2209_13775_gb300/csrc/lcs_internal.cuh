@@ -222,6 +222,7 @@ size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int episode_ste
 // variant 5 (2D time slices): their bytes for these jobs, and the most lcs_advect reserves for them
 size_t rk4_slice2d_bytes(const lcs_field *f, int njobs, const int *host_nsteps);
 #define LCS_SLICE2D_MAX_BYTES (16ULL << 30)
+#define LCS_SLICE2D_DEFAULT_BYTES (2ULL << 30)
 
 RectParams make_rect_params(const lcs_field *f);
 
