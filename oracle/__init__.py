@@ -78,6 +78,9 @@ def lib() -> ctypes.CDLL:
             L.ora_tet_velocity.argtypes = [P, P, D, P, P]
             L.ora_seed_grid.argtypes = [I, P, P, P, P, P]
             L.ora_rk4.argtypes = [I, P, I, LL, P, P, D, D, D, P, P, P]
+            L.ora_rk4_var.argtypes = [P, LL, P, D, D, D, P, P, P, P]
+            L.ora_rk4_var.restype = LL
+            L.ora_rect_velocity_grad.argtypes = [P, P, D, P, P]
             L.ora_rk4.restype = LL
             L.ora_dp45.argtypes = [I, P, I, LL, P, P, D, D, D, D, D, LL, I, I, P, P, P, P]
             L.ora_dp45.restype = LL
@@ -283,6 +286,29 @@ def seed_grid(dim, n, lo, hi, endpoint=(1, 1, 1)):
 
 def lattice_spacing(dim, n, lo, hi, endpoint=(1, 1, 1)):
     return np.array([(hi[a] - lo[a]) / ((n[a] - 1) if endpoint[a] else n[a]) for a in range(dim)])
+
+
+def rk4_var(field, x0, t0, T, dt):
+    """RK4 with the variational equations dM/dt = J M (rectilinear fields).  x0 [dim][N] ->
+    (xT, M [N][dim][dim], status, t_exit)."""
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    dim, n = x0.shape
+    xT = np.empty_like(x0)
+    M = np.empty((n, dim, dim))
+    st = np.empty(n, dtype=np.uint8)
+    te = np.empty(n, dtype=np.float64)
+    lib().ora_rk4_var(ctypes.byref(field.struct), n, _p(x0), float(t0), float(T), float(dt), _p(xT), _p(M),
+                      _p(st), _p(te))
+    return xT, M, st, te
+
+
+def velocity_grad(field, x, t):
+    """u(x, t) and its spatial Jacobian (rectilinear fields)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    u = np.empty(field.dim)
+    J = np.empty((field.dim, field.dim))
+    lib().ora_rect_velocity_grad(ctypes.byref(field.struct), _p(x), float(t), _p(u), _p(J))
+    return u, J
 
 
 def rk4(field, x0, t0, T, dt, cells=None):

@@ -141,6 +141,77 @@ int ora_rect_velocity(const ora_rect_field *f, const double *x, double t, double
     return 0;
 }
 
+/* Spatial Jacobian of the bilinear / trilinear interpolant of one frame at x:
+ * J[c][d] = d u_c / d x_d inside the cell of x (the derivative of the weights times the node
+ * values); along a non-periodic axis where x lies outside the box the clamped field is
+ * constant, so that column is zero.                                                       */
+static void rect_frame_grad(const ora_rect_field *f, int frame, const double *x, double J[3][3])
+{
+    int i0, i1, j0, j1, k0 = 0, k1 = 0;
+    double fx, fy, fz = 0.0;
+    axis_cell(x[0], f->origin[0], f->spacing[0], f->n[0], f->periodic[0], &i0, &i1, &fx);
+    axis_cell(x[1], f->origin[1], f->spacing[1], f->n[1], f->periodic[1], &j0, &j1, &fy);
+    if (f->dim == 3)
+        axis_cell(x[2], f->origin[2], f->spacing[2], f->n[2], f->periodic[2], &k0, &k1, &fz);
+    double on[3];
+    for (int d = 0; d < f->dim; ++d) {
+        double hi = f->origin[d] + (double)(f->n[d] - 1) * f->spacing[d];
+        on[d] = (f->periodic[d] || (x[d] >= f->origin[d] && x[d] <= hi)) ? 1.0 : 0.0;
+    }
+    for (int c = 0; c < f->dim; ++c) {
+        if (f->dim == 2) {
+            double u00 = rect_node(f, frame, i0, j0, 0, c), u10 = rect_node(f, frame, i1, j0, 0, c);
+            double u01 = rect_node(f, frame, i0, j1, 0, c), u11 = rect_node(f, frame, i1, j1, 0, c);
+            J[c][0] = on[0] * ((1.0 - fy) * (u10 - u00) + fy * (u11 - u01)) / f->spacing[0];
+            J[c][1] = on[1] * ((1.0 - fx) * (u01 - u00) + fx * (u11 - u10)) / f->spacing[1];
+        } else {
+            double v[2][2][2];
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    for (int e = 0; e < 2; ++e)
+                        v[a][b][e] = rect_node(f, frame, a ? i1 : i0, b ? j1 : j0, e ? k1 : k0, c);
+            double dx = 0.0, dy = 0.0, dz = 0.0;
+            for (int b = 0; b < 2; ++b)
+                for (int e = 0; e < 2; ++e) {
+                    double wy = b ? fy : 1.0 - fy, wz = e ? fz : 1.0 - fz;
+                    dx += wy * wz * (v[1][b][e] - v[0][b][e]);
+                }
+            for (int a = 0; a < 2; ++a)
+                for (int e = 0; e < 2; ++e) {
+                    double wx = a ? fx : 1.0 - fx, wz = e ? fz : 1.0 - fz;
+                    dy += wx * wz * (v[a][1][e] - v[a][0][e]);
+                }
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) {
+                    double wx = a ? fx : 1.0 - fx, wy = b ? fy : 1.0 - fy;
+                    dz += wx * wy * (v[a][b][1] - v[a][b][0]);
+                }
+            J[c][0] = on[0] * dx / f->spacing[0];
+            J[c][1] = on[1] * dy / f->spacing[1];
+            J[c][2] = on[2] * dz / f->spacing[2];
+        }
+    }
+}
+
+/* u(x, t) and its spatial Jacobian, both linear in time between the bracketing frames */
+int ora_rect_velocity_grad(const ora_rect_field *f, const double *x, double t, double *u, double *Jflat)
+{
+    int k;
+    double a;
+    double ua[3], ub[3], Ja[3][3], Jb[3][3];
+    ora_time_locate(f->times, f->nframes, f->time_periodic, f->period, t, &k, &a);
+    int k1 = (f->nframes > 1) ? k + 1 : k;
+    rect_frame_interp(f, k, x, ua);
+    rect_frame_interp(f, k1, x, ub);
+    rect_frame_grad(f, k, x, Ja);
+    rect_frame_grad(f, k1, x, Jb);
+    for (int c = 0; c < f->dim; ++c) {
+        u[c] = (1.0 - a) * ua[c] + a * ub[c];
+        for (int d = 0; d < f->dim; ++d) Jflat[c * f->dim + d] = (1.0 - a) * Ja[c][d] + a * Jb[c][d];
+    }
+    return 0;
+}
+
 /* rectilinear tracer has left: more than one cell outside a non-periodic axis */
 static int rect_left(const ora_rect_field *f, const double *x)
 {
@@ -549,6 +620,56 @@ long long ora_rk4(int field_kind, const void *field, int dim, long long n,
             }
         }
         for (int a = 0; a < dim; ++a) xT[a * n + p] = x[a];
+        status[p] = st;
+        t_exit[p] = te;
+    }
+    return nsteps;
+}
+
+/* RK4 on Eq. 2 together with its variational equation dM/dt = J(x, t) M, M(t0) = I, on a
+ * rectilinear field (Sec. 1: the linearised flow map, the alternative to finite differences of
+ * the seed grid).  Same steps, stage times and leaving rule as ora_rk4; M [n][dim][dim] is the
+ * derivative of the final position with respect to the seed, frozen with the tracer.          */
+long long ora_rk4_var(const ora_rect_field *f, long long n, const double *x0, double t0, double T, double dt,
+                      double *xT, double *Mout, unsigned char *status, double *t_exit)
+{
+    const int dim = f->dim;
+    double adt = fabs(dt);
+    long long nsteps = (long long)floor(fabs(T) / adt + 0.5);
+    double h = (T < 0.0) ? -adt : adt;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long long p = 0; p < n; ++p) {
+        double x[3] = {0, 0, 0}, M[9] = {0}, y[3], Y[9], ku[4][3], kM[4][9], J[9];
+        for (int a = 0; a < dim; ++a) {
+            x[a] = x0[a * n + p];
+            M[a * dim + a] = 1.0;
+        }
+        unsigned char st = ORA_OK;
+        double te = t0 + T;
+        for (long long s = 0; s < nsteps && st == ORA_OK; ++s) {
+            double t = t0 + (double)s * h;
+            const double ct[4] = {0.0, 0.5, 0.5, 1.0};
+            for (int q = 0; q < 4; ++q) {
+                for (int a = 0; a < dim; ++a) y[a] = q == 0 ? x[a] : x[a] + ct[q] * h * ku[q - 1][a];
+                for (int e = 0; e < dim * dim; ++e) Y[e] = q == 0 ? M[e] : M[e] + ct[q] * h * kM[q - 1][e];
+                ora_rect_velocity_grad(f, y, t + ct[q] * h, ku[q], J);
+                for (int a = 0; a < dim; ++a)
+                    for (int b = 0; b < dim; ++b) {
+                        double acc = 0.0;
+                        for (int c = 0; c < dim; ++c) acc += J[a * dim + c] * Y[c * dim + b];
+                        kM[q][a * dim + b] = acc;
+                    }
+            }
+            for (int a = 0; a < dim; ++a) x[a] = x[a] + h / 6.0 * (ku[0][a] + 2.0 * ku[1][a] + 2.0 * ku[2][a] + ku[3][a]);
+            for (int e = 0; e < dim * dim; ++e)
+                M[e] = M[e] + h / 6.0 * (kM[0][e] + 2.0 * kM[1][e] + 2.0 * kM[2][e] + kM[3][e]);
+            if (rect_left(f, x)) {
+                st = ORA_LEFT;
+                te = t + h;
+            }
+        }
+        for (int a = 0; a < dim; ++a) xT[a * n + p] = x[a];
+        for (int e = 0; e < dim * dim; ++e) Mout[p * dim * dim + e] = M[e];
         status[p] = st;
         t_exit[p] = te;
     }

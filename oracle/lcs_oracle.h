@@ -94,6 +94,8 @@ void ora_time_locate(const double *times, int nframes, int time_periodic,
 /* u(x, t) on rectilinear frames.  Returns 0.  Queries on a non-periodic axis
  * are clamped to the grid box.                                              */
 int ora_rect_velocity(const ora_rect_field *f, const double *x, double t, double *u);
+/* u and its spatial Jacobian J[c * dim + d] = d u_c / d x_d (zero across a clamped axis). */
+int ora_rect_velocity_grad(const ora_rect_field *f, const double *x, double t, double *u, double *J);
 
 /* u(x, t) from an analytic field.  Returns 0.                               */
 int ora_analytic_velocity(const ora_analytic_field *f, const double *x, double t, double *u);
@@ -124,6 +126,11 @@ void ora_seed_grid(int dim, const int n[3], const double lo[3], const double hi[
  * start of the step, t_exit = t_n.  cells (tet only, may be NULL otherwise) is
  * the start cell per seed, -1 = seed outside (status OUTSIDE).
  * Returns the number of steps per tracer.                                   */
+/* RK4 on Eq. 2 with the variational equation dM/dt = J M, M(t0) = I (rectilinear
+ * fields): final positions, M [n][dim][dim], status and exit time as ora_rk4.     */
+long long ora_rk4_var(const ora_rect_field *f, long long n, const double *x0, double t0, double T, double dt,
+                      double *xT, double *M, unsigned char *status, double *t_exit);
+
 long long ora_rk4(int field_kind, const void *field, int dim, long long n,
                   const double *x0, const int *cells, double t0, double T, double dt,
                   double *xT, unsigned char *status, double *t_exit);
