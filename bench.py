@@ -933,6 +933,23 @@ def next_arm(args, rank, world, local):
     ms_ftle = timed(lambda: lcs.lcs_ftle(ctx, fm, 0, ftle), max(args.steps, 3))
     out["eigen_abc_256cubed"] = {"ms": ms_eig, "seeds_per_s": N / ms_eig * 1e3, "ftle_pass_ms": ms_ftle,
                                  "bytes_written": N * 96, "write_gbs": N * 96 / ms_eig / 1e6}
+    # grad F by the variational equations on the same lattice, against the default finite-difference step
+    ov = lcs.advect_opts(lcs.RK4, t0=0.0, T=T_END, dt=DT, variational=True)
+    od = lcs.advect_opts(lcs.RK4, t0=0.0, T=T_END, dt=DT)
+
+    def var_step():
+        lcs.lcs_advect(ctx, field, seeds, ov, fm)
+        lcs.lcs_ftle_variational(ctx, fm, 0, ftle)
+
+    def fd_step():
+        lcs.lcs_advect(ctx, field, seeds, od, fm)
+        lcs.lcs_ftle(ctx, fm, 0, ftle)
+
+    ms_var = timed(var_step, 3)
+    ms_fd = timed(fd_step, 3)
+    out["variational_abc_256cubed"] = {"ms": ms_var, "seeds_per_s": N / ms_var * 1e3, "fd_step_ms": ms_fd,
+                                       "note": "one-pass kernel: x and the 3x3 M per tracer, frames from "
+                                               "global memory; fd_step = the default re-bundled path + FD"}
     lcs.lcs_free_flowmap(fm)
     lcs.lcs_free_seeds(seeds)
     lcs.lcs_free_field(field)
@@ -972,7 +989,18 @@ def next_arm(args, rank, world, local):
     ms_aux = timed(aux_step, max(args.steps, 3))
     out["aux_points_gyre_1024x512"] = {"ms": ms_aux, "points": M, "ftle_seeds_per_s": 1024 * 512 / ms_aux * 1e3,
                                        "tracer_steps_per_s": M * 200 / ms_aux * 1e3}
-    for h in (fm3,):
+    # 4. the same seeds' grad F by the variational equations (one tracer per seed)
+    fm4 = lcs.lcs_flowmap_create(ctx, lat, 1)
+    o4 = lcs.advect_opts(lcs.RK4, t0=0.0, T=10.0, dt=0.05, variational=True)
+
+    def var2_step():
+        lcs.lcs_advect(ctx, f3, lat, o4, fm4)
+        lcs.lcs_ftle_variational(ctx, fm4, 0, fa)
+
+    ms_var2 = timed(var2_step, max(args.steps, 3))
+    out["variational_gyre_1024x512"] = {"ms": ms_var2, "ftle_seeds_per_s": 1024 * 512 / ms_var2 * 1e3,
+                                        "aux_points_ms": ms_aux}
+    for h in (fm3, fm4):
         lcs.lcs_free_flowmap(h)
     for h in (aux, lat, s2):
         lcs.lcs_free_seeds(h)
@@ -984,7 +1012,8 @@ def next_arm(args, rank, world, local):
             "vs_baseline": None, "dtype": "f64 (eigen), f32 (tracers)", "data": "synthetic",
             "config": {"workload": "widening passes: eigenpairs of C (ABC 256^3 after the C2 integration), early "
                                    "CG (gyre cut to x<=1.5, 2048x1024 seeds, T=6), auxiliary-point FTLE "
-                                   "(gyre 1024x512, delta = 1/8 lattice step, T=10)"},
+                                   "(gyre 1024x512, delta = 1/8 lattice step, T=10), variational grad F "
+                                   "(ABC 256^3 T=8 and gyre 1024x512 T=10)"},
             "passes": out}
     print(json.dumps(line), flush=True)
 

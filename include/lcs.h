@@ -242,6 +242,9 @@ typedef struct {
     int nsnap;                  /* 0..LCS_MAX_SNAP snapshots per integration        */
     const double *snap_T;       /* HOST [nsnap]: horizon magnitudes, > 0, strictly
                                    increasing, each a whole number of steps dt    */
+    int variational;            /* LCS_RK4 on rectilinear fields, no snapshots: also
+                                   integrate grad F by the variational equations
+                                   (lcs_flowmap_grad, lcs_ftle_variational)       */
 } lcs_advect_opts;
 
 /* Flow-map storage for `njobs` integrations of one lattice.                 */
@@ -261,6 +264,16 @@ lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *see
  * periodic axes), status [N] uint8, exit time [N] FP32.  Any may be NULL.   */
 lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *xyz,
                            unsigned char *status, float *t_exit, int on_device);
+
+/* grad F of every tracer of job `job` from the variational equations (Sec. 1:
+ * the linearised flow map, the alternative to differencing the seed grid):
+ * lcs_advect with opts.variational integrates dM/dt = J(x, t) M, M(t0) = I,
+ * next to Eq. 2 with the same RK4 stages, J the spatial Jacobian of the
+ * interpolant (piecewise, zero across an axis where the query is clamped to
+ * the box); M is frozen with a tracer that leaves.  grad [N][dim][dim] FP32,
+ * grad[(p*dim + a)*dim + b] = d x_a(T) / d x0_b.
+ * Errors: LCS_EINVAL when no variational integration wrote this flow map.   */
+lcs_status lcs_flowmap_grad(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *grad, int on_device);
 
 /* Per-tracer step counts of job `job` ([N] int32).  After LCS_RK45: accepted
  * steps (32 consecutive seeds step together, so the tracers of a group that
@@ -387,6 +400,12 @@ lcs_status lcs_cauchy_green(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double
  * pass.  lambda_max and C may be NULL.  job = -1 writes every job.         */
 lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
                     double *C, int on_device);
+
+/* FTLE (and optionally lambda_max and C, as lcs_ftle) from the variational
+ * grad F of lcs_flowmap_grad instead of finite differences: C = M^T M in FP64
+ * from the FP32 M, per tracer, NaN for a tracer that is not OK.            */
+lcs_status lcs_ftle_variational(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
+                                double *C, int on_device);
 
 /* Early Cauchy-Green evaluation (Sec. 2 "Flow Map": for trajectories that exit
  * the data, the CG tensor is formed ahead of the horizon wherever such a

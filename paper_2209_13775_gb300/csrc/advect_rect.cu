@@ -158,6 +158,136 @@ __global__ void __launch_bounds__(256) rk4_gather_kernel(RectParams P, const cha
     store_tracer<DIM>(P, A, job, i, x, img, st, te);
 }
 
+// ============================================================ variational
+
+// u and its spatial Jacobian J[c][d] at x, linear in time between two frames: u with
+// interp's arithmetic (node blends first, then make_stencil's weights in order), J from the
+// same blended corner values and the derivatives of the weights inside the cell; a
+// non-periodic axis on which x lies outside the box gives a zero column (the clamped query
+// does not move with x).
+template <int DIM, int ST>
+__device__ __forceinline__ void interp_grad(const RectParams &P, const float *x, const char *fa, const char *fb,
+                                            float a, float *u, float (*J)[DIM])
+{
+    Stencil<DIM> S;
+    make_stencil<DIM>(P, x, S);
+    float f[DIM], on[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        int i0, i1;
+        axis_cell<-1>(P, d, x[d], i0, i1, f[d]);
+        on[d] = (P.periodic[d] || (x[d] >= P.origin[d] && x[d] <= P.hi_node[d])) ? P.inv_h[d] : 0.0f;
+    }
+    float uq[1 << DIM][DIM], va[DIM], vb[DIM];
+    const float g = 1.0f - a;
+#pragma unroll
+    for (int q = 0; q < (1 << DIM); ++q) {
+        if constexpr (DIM == 2) {   // frames: fa = frame k, fb = frame k + 1 (read only when a != 0)
+            node_load<2, ST, SRC_GLOBAL>(fa, S.v[q], va);
+            if (a != 0.0f) node_load<2, ST, SRC_GLOBAL>(fb, S.v[q], vb);
+        } else {                    // interval pairs: fa = pair k holds both frames of a node
+            Pair3<ST>::ld(fa, S.v[q], va, vb);
+        }
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) uq[q][c] = a == 0.0f ? va[c] : tblend(va[c], vb[c], a, g);
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < (1 << DIM); ++q) acc = fmaf(S.w[q], uq[q][c], acc);
+        u[c] = acc;
+    }
+    // corner q has offsets (q & 1, (q >> 1) & 1, (q >> 2) & 1); d w_q / d x_d = +-(product of the
+    // other axes' weights) / h_d
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int q = 0; q < (1 << DIM); ++q) {
+                float w = ((q >> d) & 1) ? 1.0f : -1.0f;
+#pragma unroll
+                for (int e = 0; e < DIM; ++e)
+                    if (e != d) w *= ((q >> e) & 1) ? f[e] : 1.0f - f[e];
+                acc = fmaf(w, uq[q][c], acc);
+            }
+            J[c][d] = acc * on[d];
+        }
+}
+
+// RK4 with the variational equations dM/dt = J M: the position follows rk4_step's arithmetic
+// exactly (so x(T) equals the other kernels'), M the same stages in FP32
+template <int DIM, int ST>
+__global__ void __launch_bounds__(256) rk4_var_kernel(RectParams P, const char *__restrict__ frames, size_t fstride,
+                                                      Rk4Args A)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int job = blockIdx.y;
+    if (i >= A.N) return;
+    float x[DIM], M[DIM][DIM];
+    int img[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        x[d] = A.seeds[d * A.N + i];
+        img[d] = 0;
+#pragma unroll
+        for (int e = 0; e < DIM; ++e) M[d][e] = d == e ? 1.0f : 0.0f;
+    }
+    wrap_periodic<DIM>(P, x, img);
+    const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
+    const int ns = A.job_nsteps[job];
+    const float h = A.job_h[job], hh = 0.5f * h, h6 = h * (1.0f / 6.0f);
+    unsigned char st = LCS_TRACER_OK;
+    float te = A.job_tend[job];
+    for (int n = 0; n < ns; ++n) {
+        const SchedEntry es[3] = {load_sched(sc + 3 * n), load_sched(sc + 3 * n + 1), load_sched(sc + 3 * n + 2)};
+        float k[4][DIM], K[4][DIM][DIM], y[DIM], Y[DIM][DIM], J[DIM][DIM];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const SchedEntry e = es[q == 0 ? 0 : (q == 3 ? 2 : 1)];
+            const float c = q == 0 ? 0.0f : (q == 3 ? h : hh);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                y[a] = q == 0 ? x[a] : fmaf(c, k[q - 1][a], x[a]);
+#pragma unroll
+                for (int b = 0; b < DIM; ++b) Y[a][b] = q == 0 ? M[a][b] : fmaf(c, K[q - 1][a][b], M[a][b]);
+            }
+            const char *fa = frames + (size_t)e.k * fstride;
+            interp_grad<DIM, ST>(P, y, fa, DIM == 2 ? fa + fstride : fa, e.a, k[q], J);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                for (int b = 0; b < DIM; ++b) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int cc = 0; cc < DIM; ++cc) acc = fmaf(J[a][cc], Y[cc][b], acc);
+                    K[q][a][b] = acc;
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            x[a] = fmaf(h6, (k[0][a] + k[3][a]) + 2.0f * (k[1][a] + k[2][a]), x[a]);
+#pragma unroll
+            for (int b = 0; b < DIM; ++b)
+                M[a][b] = fmaf(h6, (K[0][a][b] + K[3][a][b]) + 2.0f * (K[1][a][b] + K[2][a][b]), M[a][b]);
+        }
+        wrap_periodic<DIM>(P, x, img);
+        if (rect_left<DIM>(P, x)) {
+            st = LCS_TRACER_LEFT;
+            te = fmaf((float)(n + 1), h, A.job_t0[job]);
+            break;
+        }
+    }
+    store_tracer<DIM>(P, A, job, i, x, img, st, te);
+    float *o = A.out_grad + ((size_t)job * A.N + i) * DIM * DIM;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) o[a * DIM + b] = M[a][b];
+}
+
 // ============================================================== ring kernel
 
 // Three frame slots in shared memory, tagged with the frame they hold.  Thread 0
@@ -646,6 +776,7 @@ int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
     A.out_xyz = L.out_xyz;
     A.out_status = L.out_status;
     A.out_texit = L.out_texit;
+    A.out_grad = L.out_grad;
     A.njobs = L.njobs;
     A.nsnap = L.nsnap;
     A.snap_n = L.snap_n;
@@ -664,6 +795,25 @@ int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
     if (variant == 4 && !queue_ok) variant = 2;
     if (variant == 3 && !sorted_ok) variant = 1;
     cudaError_t e;
+    if (A.out_grad) {   // the variational equations: their own one-pass kernel
+        const int bt = L.block_threads > 0 && L.block_threads <= 256 ? L.block_threads : 256;
+        dim3 grid((unsigned)((A.N + bt - 1) / bt), (unsigned)L.njobs);
+        const char *fr = (const char *)f->d_frames;
+        lcs_tm_begin(ctx, 0, s);
+#define VAR_LAUNCH(D, ST) rk4_var_kernel<D, ST><<<grid, bt, 0, s>>>(P, fr, f->frame_stride, A)
+        if (f->dim == 2) {
+            if (f->storage == LCS_F32) VAR_LAUNCH(2, LCS_F32);
+            else if (f->storage == LCS_F16) VAR_LAUNCH(2, LCS_F16);
+            else VAR_LAUNCH(2, LCS_BF16);
+        } else {
+            if (f->storage == LCS_F32) VAR_LAUNCH(3, LCS_F32);
+            else if (f->storage == LCS_F16) VAR_LAUNCH(3, LCS_F16);
+            else VAR_LAUNCH(3, LCS_BF16);
+        }
+#undef VAR_LAUNCH
+        lcs_tm_end(ctx, 0, s);
+        return cudaGetLastError() == cudaSuccess ? 6 : -1;
+    }
     if (variant == 5 && !(f->dim == 2 && L.work != nullptr)) variant = 1;
     if (variant == 3) {
         e = launch_rk4_episodes(P, f, A, L, s);

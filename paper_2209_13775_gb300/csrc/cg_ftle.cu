@@ -129,7 +129,11 @@ __device__ __forceinline__ void aux_gradient(const CgLaunch &L, int job, long lo
     }
 }
 
-template <int DIM, bool EIG, bool AUX>
+// gradient sources: finite differences over the lattice, over auxiliary points, or the
+// variational grad F integrated with the flow map
+enum { GM_LATTICE = 0, GM_AUX = 1, GM_VAR = 2 };
+
+template <int DIM, bool EIG, int GM>
 __global__ void __launch_bounds__(256) cg_ftle_kernel(CgLaunch L)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -139,8 +143,16 @@ __global__ void __launch_bounds__(256) cg_ftle_kernel(CgLaunch L)
     if (p >= N) return;
     constexpr int NP = DIM == 2 ? 3 : 6;
     double G[DIM][DIM];
-    if constexpr (AUX) {
+    if constexpr (GM == GM_AUX) {
         aux_gradient<DIM>(L, job, p, G);
+    } else if constexpr (GM == GM_VAR) {
+        const bool ok = L.status[(size_t)job * N + p] == LCS_TRACER_OK;
+        const float *Mp = L.grad + ((size_t)job * N + p) * DIM * DIM;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int b = 0; b < DIM; ++b)
+                G[a][b] = ok ? (double)Mp[a * DIM + b] : __longlong_as_double(0x7ff8000000000000LL);
     } else {
     const float *X = L.xyz + (size_t)job * DIM * N;
     const unsigned char *S = L.status + (size_t)job * N;
@@ -230,18 +242,18 @@ cudaError_t launch_cg_ftle(const CgLaunch &L0, cudaStream_t s)
     }
     int bt = 256;
     dim3 grid((unsigned)((L.N + bt - 1) / bt), (unsigned)L.njobs);
-    const bool eig = L.eigval || L.eigvec, aux = L.x0aux != nullptr;
-#define CG_LAUNCH(D, E, A) cg_ftle_kernel<D, E, A><<<grid, bt, 0, s>>>(L)
+    const bool eig = L.eigval || L.eigvec;
+    const int gm = L.grad ? GM_VAR : (L.x0aux ? GM_AUX : GM_LATTICE);
+#define CG_LAUNCH(D, G) (eig ? cg_ftle_kernel<D, true, G><<<grid, bt, 0, s>>>(L) \
+                             : cg_ftle_kernel<D, false, G><<<grid, bt, 0, s>>>(L))
     if (L.dim == 2) {
-        if (aux)
-            eig ? CG_LAUNCH(2, true, true) : CG_LAUNCH(2, false, true);
-        else
-            eig ? CG_LAUNCH(2, true, false) : CG_LAUNCH(2, false, false);
+        if (gm == GM_VAR) CG_LAUNCH(2, GM_VAR);
+        else if (gm == GM_AUX) CG_LAUNCH(2, GM_AUX);
+        else CG_LAUNCH(2, GM_LATTICE);
     } else {
-        if (aux)
-            eig ? CG_LAUNCH(3, true, true) : CG_LAUNCH(3, false, true);
-        else
-            eig ? CG_LAUNCH(3, true, false) : CG_LAUNCH(3, false, false);
+        if (gm == GM_VAR) CG_LAUNCH(3, GM_VAR);
+        else if (gm == GM_AUX) CG_LAUNCH(3, GM_AUX);
+        else CG_LAUNCH(3, GM_LATTICE);
     }
 #undef CG_LAUNCH
     return cudaGetLastError();

@@ -670,6 +670,7 @@ extern "C" void lcs_free_flowmap(lcs_flowmap *fm)
     cudaFree(fm->d_texit);
     cudaFree(fm->d_absT);
     cudaFree(fm->d_steps);
+    cudaFree(fm->d_grad);
     delete fm;
 }
 
@@ -759,6 +760,7 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.tracers_per_thread = o->tracers_per_thread >= 2 ? 2 : 1;
     L.queue = queue;
     L.job_order = D.order;
+    L.out_grad = o->variational ? fm->d_grad : nullptr;
     L.nsnap = J.nsnap;
     L.snap_n = D.snap_n;
     L.host_snap_n = J.snap_n;
@@ -870,9 +872,9 @@ static std::string graph_key(const lcs_ctx *ctx, const lcs_field *f, const lcs_s
 {
     std::string k;
     char buf[160];
-    snprintf(buf, sizeof buf, "%llu/%llu/%llu/%p/%zu/%d/%d/%d/%d/%d/%d/%a|", f->uid, s->uid, fm->uid, ctx->d_scratch,
-             ctx->scratch_bytes, o->method, o->variant, o->block_threads, o->episode_steps, o->tracers_per_thread,
-             J.njobs, o->dt);
+    snprintf(buf, sizeof buf, "%llu/%llu/%llu/%p/%zu/%d/%d/%d/%d/%d/%d/%a/v%d|", f->uid, s->uid, fm->uid,
+             ctx->d_scratch, ctx->scratch_bytes, o->method, o->variant, o->block_threads, o->episode_steps,
+             o->tracers_per_thread, J.njobs, o->dt, o->variational);
     k += buf;
     for (int j = 0; j < J.njobs; ++j) {
         snprintf(buf, sizeof buf, "%a,%a;", J.t0[j], J.T[j]);
@@ -990,6 +992,10 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
     if (njobs > fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: %d jobs > flow map's %d", njobs, fm->njobs);
     if (o->nsnap < 0 || o->nsnap > LCS_MAX_SNAP || (o->nsnap > 0 && !o->snap_T))
         return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: nsnap must be 0..%d with snap_T given", LCS_MAX_SNAP);
+    if (o->variational && (o->method != LCS_RK4 || f->kind != LCS_RECTILINEAR || o->nsnap > 0 || s->aux_base_N > 0))
+        return lcs_fail(ctx, LCS_EUNSUPPORTED,
+                        "lcs_advect: the variational equations need LCS_RK4 on a rectilinear field, a lattice and "
+                        "no snapshots");
     if (o->nsnap > 0) {
         if (o->method != LCS_RK4 || f->kind != LCS_RECTILINEAR)
             return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: snapshots need LCS_RK4 on a rectilinear field");
@@ -1022,6 +1028,9 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
     std::stable_sort(J->order, J->order + njobs, [&](int a, int b) { return J->nsteps[a] > J->nsteps[b]; });
     lcs_status st;
     cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess && o->variational && !fm->d_grad)
+        e = cudaMalloc(&fm->d_grad, sizeof(float) * fm->dim * fm->dim * (size_t)fm->N * fm->njobs);
+    fm->grad_valid = o->variational != 0;
     if (e != cudaSuccess)
         st = lcs_fail(ctx, LCS_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
     else if (o->use_graph)
@@ -1054,14 +1063,17 @@ extern "C" lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int j
 // ------------------------------------------------------ grad F, C, FTLE
 
 static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lam, double *C,
-                          int on_device, const char *who, double *eigval = nullptr, double *eigvec = nullptr)
+                          int on_device, const char *who, double *eigval = nullptr, double *eigvec = nullptr,
+                          bool variational = false)
 {
     if (!ctx) return LCS_EINVAL;
     if (!fm) return lcs_fail(ctx, LCS_EINVAL, "%s: null flow map", who);
     if (job < -1 || job >= fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "%s: job %d out of range", who, job);
     const lcs_seeds *s = fm->seeds;
     const bool aux = s->aux_base_N > 0;
-    if (!aux)
+    if (variational && !(fm->d_grad && fm->grad_valid))
+        return lcs_fail(ctx, LCS_EINVAL, "%s: no variational integration wrote this flow map", who);
+    if (!aux && !variational)
         for (int a = 0; a < s->dim; ++a)
             if (s->n[a] < 3) return lcs_fail(ctx, LCS_EINVAL, "%s: the lattice needs >= 3 seeds per axis", who);
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
@@ -1084,6 +1096,7 @@ static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *f
     L.absT = fm->d_absT;
     L.x0aux = aux ? s->d_xyz : nullptr;
     L.npts = fm->N;
+    L.grad = variational ? fm->d_grad : nullptr;
     const size_t dim = (size_t)fm->dim;
     size_t bC = C ? sizeof(double) * np * N * nj : 0, bL = lam ? sizeof(double) * N * nj : 0,
            bF = ftle ? sizeof(float) * N * nj : 0, bE = eigval ? sizeof(double) * dim * N * nj : 0,
@@ -1268,6 +1281,28 @@ extern "C" lcs_status lcs_ftle_early(lcs_ctx *ctx, const lcs_field *f, const lcs
     cudaFreeAsync(tmp, ctx->stream);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+    return LCS_OK;
+}
+
+extern "C" lcs_status lcs_ftle_variational(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle,
+                                           double *lambda_max, double *C, int on_device)
+{
+    if (ctx && !ftle) return lcs_fail(ctx, LCS_EINVAL, "lcs_ftle_variational: null output");
+    return cg_call(ctx, fm, job, ftle, lambda_max, C, on_device, "lcs_ftle_variational", nullptr, nullptr, true);
+}
+
+extern "C" lcs_status lcs_flowmap_grad(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *grad, int on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    if (!fm || !grad) return lcs_fail(ctx, LCS_EINVAL, "lcs_flowmap_grad: null argument");
+    if (job < 0 || job >= fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "lcs_flowmap_grad: job %d out of range", job);
+    if (!fm->d_grad || !fm->grad_valid)
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_flowmap_grad: no variational integration wrote this flow map");
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const size_t b = sizeof(float) * fm->dim * fm->dim * (size_t)fm->N;
+    CUDA_TRY(ctx, cudaMemcpyAsync(grad, (const char *)fm->d_grad + b * job, b,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
+    if (!on_device) CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return LCS_OK;
 }
 

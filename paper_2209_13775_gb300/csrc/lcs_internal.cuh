@@ -128,6 +128,8 @@ struct lcs_flowmap {
     unsigned char *d_status = nullptr; // [njobs][N]
     float *d_texit = nullptr;          // [njobs][N]
     int *d_steps = nullptr;            // [njobs][N] accepted adaptive steps (after an RK45 advect)
+    float *d_grad = nullptr;           // [njobs][N][dim][dim] variational grad F (opts.variational)
+    bool grad_valid = false;
     std::vector<double> T;             // per job
     double *d_absT = nullptr;          // [njobs] |T|, written by the schedule kernel
 };
@@ -207,6 +209,7 @@ struct Rk4Launch {
     int tracers_per_thread;   // ring kernels: 1 or 2
     unsigned *queue;          // variant 4: work-queue counter in device scratch, or null
     const int *job_order;     // variant 4: [njobs] jobs by decreasing step count (device), or null
+    float *out_grad = nullptr;  // variational grad F [njobs][N][dim][dim], or null
     int nsnap = 0;            // snapshots per job: slot njobs + job * nsnap + s after min(snap_n[s], nsteps)
     const int *snap_n = nullptr;  // [nsnap] on the device (written by the schedule kernel)
     const int *host_snap_n = nullptr;  // [nsnap] the same on the host
@@ -251,6 +254,7 @@ struct CgLaunch {
     const unsigned char *status; // [njobs_total][N]
     const float *texit = nullptr; // [njobs_total][N] (early evaluation only)
     const float *x0aux = nullptr; // auxiliary points: their FP32 starting points [dim][npts]; null: lattice
+    const float *grad = nullptr;  // variational grad F [njobs_total][N][dim][dim]; null: differences
     long long npts = 0;          // auxiliary points per job (N * 2 dim)
     const double *absT;          // [njobs_total] |T|
     double *C;                   // [njobs][N][np] or null

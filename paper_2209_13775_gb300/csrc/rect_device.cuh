@@ -336,6 +336,7 @@ struct Rk4Args {
     float *out_xyz;
     unsigned char *out_status;
     float *out_texit;
+    float *out_grad = nullptr;       // variational grad F [njobs][N][dim][dim], or null
     int njobs = 0;                   // jobs of the call: snapshot s of job j goes to slot njobs + j nsnap + s
     int nsnap = 0;
     const int *snap_n = nullptr;     // [nsnap] snapshot step counts (device; capped per job at use)

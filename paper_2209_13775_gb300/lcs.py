@@ -26,7 +26,8 @@ EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs
            "lcs_load_field", "lcs_update_frames", "lcs_free_field", "lcs_seed_grid", "lcs_seed_aux", "lcs_seeds_count",
            "lcs_seeds_get", "lcs_free_seeds", "lcs_flowmap_create", "lcs_advect", "lcs_flowmap_get",
            "lcs_flowmap_steps",
-           "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_cg_eigen", "lcs_ftle_early",
+           "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_cg_eigen", "lcs_ftle_early", "lcs_ftle_variational",
+           "lcs_flowmap_grad",
            "lcs_timing_enable",
            "lcs_timing_read",
            "lcs_advect_rk4_noalloc", "lcs_gemm_bf16", "lcs_mlp_create", "lcs_mlp_set_params",
@@ -66,7 +67,8 @@ class AdvectOpts(ctypes.Structure):
                 ("h0", ctypes.c_double), ("max_steps", ctypes.c_longlong), ("walk_limit", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("variant", ctypes.c_int), ("surrogate", ctypes.c_void_p),
                 ("episode_steps", ctypes.c_int), ("tracers_per_thread", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("gate_tol", ctypes.c_double), ("nsnap", ctypes.c_int), ("snap_T", ctypes.c_void_p)]
+                ("gate_tol", ctypes.c_double), ("nsnap", ctypes.c_int), ("snap_T", ctypes.c_void_p),
+                ("variational", ctypes.c_int)]
 
 
 _lib = None
@@ -96,6 +98,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_flowmap_get": ([P, P, I, P, P, P, I], S), "lcs_free_flowmap": ([P], None),
         "lcs_cauchy_green": ([P, P, I, P, I], S), "lcs_ftle": ([P, P, I, P, P, P, I], S),
         "lcs_cg_eigen": ([P, P, I, P, P, I], S), "lcs_ftle_early": ([P, P, P, P, P, I, P, P, I], S),
+        "lcs_ftle_variational": ([P, P, I, P, P, P, I], S), "lcs_flowmap_grad": ([P, P, I, P, I], S),
         "lcs_advect_rk4_noalloc": ([P, P, P, LL, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P], S),
         "lcs_timing_enable": ([P, I], S), "lcs_timing_read": ([P, I, P, P], S),
         "lcs_autotune": ([P, P, P, P, ctypes.c_char_p], S),
@@ -264,7 +267,7 @@ def lcs_free_seeds(seeds):
 
 def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol=1e-6, atol=1e-6, h0=0.01,
                 max_steps=0, walk_limit=0, block_threads=0, variant=0, episode_steps=0, tracers_per_thread=0,
-                use_graph=False, surrogate=None, gate_tol=1e-3, snap_T=None):
+                use_graph=False, surrogate=None, gate_tol=1e-3, snap_T=None, variational=False):
     o = AdvectOpts()
     o.method, o.t0, o.T, o.dt = int(method), float(t0), float(T), float(dt)
     o.rtol, o.atol, o.h0, o.max_steps = float(rtol), float(atol), float(h0), int(max_steps)
@@ -274,6 +277,7 @@ def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol
     o.use_graph = int(bool(use_graph))
     o.surrogate = surrogate
     o.gate_tol = float(gate_tol)
+    o.variational = int(bool(variational))
     keep = []
     if snap_T is not None and len(snap_T) > 0:
         sn = np.ascontiguousarray(snap_T, dtype=np.float64)
@@ -352,6 +356,21 @@ def lcs_ftle_early(ctx, field, seeds, opts: AdvectOpts, fm, job, ftle, t_eval=No
         raise ValueError("outputs must all be host or all be device buffers")
     _check(ctx, load().lcs_ftle_early(ctx, field, seeds, ctypes.byref(opts), fm, int(job),
                                       *[ctypes.c_void_p(p) for p, _ in ptrs], devs.pop()))
+
+
+def lcs_ftle_variational(ctx, fm, job, ftle, lambda_max=None, C=None):
+    """FTLE from the variational grad F (after lcs_advect with variational=True)."""
+    ptrs = [_ptr(a) for a in (ftle, lambda_max, C)]
+    devs = {d for (p, d), a in zip(ptrs, (ftle, lambda_max, C)) if a is not None}
+    if len(devs) > 1:
+        raise ValueError("outputs must all be host or all be device buffers")
+    _check(ctx, load().lcs_ftle_variational(ctx, fm, int(job), *[ctypes.c_void_p(p) for p, _ in ptrs], devs.pop()))
+
+
+def lcs_flowmap_grad(ctx, fm, job, grad):
+    """Variational grad F [N][dim][dim] of job `job`."""
+    p, d = _ptr(grad)
+    _check(ctx, load().lcs_flowmap_grad(ctx, fm, int(job), ctypes.c_void_p(p), d))
 
 
 def lcs_cg_eigen(ctx, fm, job, eigval=None, eigvec=None):

@@ -1,0 +1,213 @@
+"""grad F by the variational equations (Sec. 1: the linearised flow map as the alternative to
+differencing the seed grid) through lcs_advect(variational=True), lcs_flowmap_grad and
+lcs_ftle_variational:
+
+* the positions, status and exit times are bit-identical to the plain fixed-step RK4 kernel's (the
+  position part of the integration is the same arithmetic);
+* grad F against the oracle's FP64 rk4_var within the fixed-step tolerances, and the FTLE formed
+  from it against the oracle's;
+* C bit-identical to the oracle's Eq. 1 applied to the GPU's own FP32 grad F;
+* a linear flow (interpolation exact): grad F = R(hA)^N, R the RK4 stability polynomial;
+* invalid combinations are rejected and leave the context usable.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_13775_gb300 import inputs, lcs
+from gpu_util import check_ftle, rect_desc, round_fp16
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    c = lcs.lcs_create(0, torch.cuda.current_stream())
+    yield c
+    lcs.lcs_destroy(c)
+
+
+def var_run(ctx, g, n, lo, hi, periodic, dt, jobs, storage=lcs.F32, **kw):
+    """Variational and plain (variant 1) runs of the same jobs; host arrays per job."""
+    dim = g.dim
+    field = lcs.lcs_load_field(ctx, rect_desc(g, storage), g.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(dim, n, lo, hi, periodic))
+    N = lcs.lcs_seeds_count(seeds)
+    nj = len(jobs[0])
+    out = {"N": N, "seeds": np.empty((dim, N), dtype=np.float32)}
+    lcs.lcs_seeds_get(ctx, seeds, out["seeds"])
+    for tag, extra in (("var", dict(variational=True, **kw)), ("plain", dict(variant=1))):
+        fm = lcs.lcs_flowmap_create(ctx, seeds, nj)
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1], **extra),
+                       fm)
+        res = []
+        for j in range(nj):
+            r = {"x": np.empty((dim, N), dtype=np.float32), "st": np.empty(N, dtype=np.uint8),
+                 "te": np.empty(N, dtype=np.float32)}
+            lcs.lcs_flowmap_get(ctx, fm, j, r["x"], r["st"], r["te"])
+            if tag == "var":
+                r["M"] = np.empty((N, dim, dim), dtype=np.float32)
+                lcs.lcs_flowmap_grad(ctx, fm, j, r["M"])
+                r["ftle"] = np.empty(N, dtype=np.float32)
+                r["lam"] = np.empty(N)
+                r["C"] = np.empty((N, 3 if dim == 2 else 6))
+                lcs.lcs_ftle_variational(ctx, fm, j, r["ftle"], r["lam"], r["C"])
+                # device outputs give the same values
+                fd = torch.empty(N, dtype=torch.float32, device="cuda")
+                lcs.lcs_ftle_variational(ctx, fm, j, fd)
+                Md = torch.empty((N, dim, dim), dtype=torch.float32, device="cuda")
+                lcs.lcs_flowmap_grad(ctx, fm, j, Md)
+                lcs.lcs_synchronize(ctx)
+                np.testing.assert_array_equal(fd.cpu().numpy(), r["ftle"])
+                np.testing.assert_array_equal(Md.cpu().numpy(), r["M"])
+            res.append(r)
+        lcs.lcs_synchronize(ctx)
+        lcs.lcs_free_flowmap(fm)
+        out[tag] = res
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return out
+
+
+def check_grad(M, Mo, ok):
+    """FP32 grad F against the FP64 oracle's, per OK seed, relative to the tensor's size: median
+    <= 1e-5, 99th percentile <= 1e-3, all <= 5e-2.  The interpolant's Jacobian jumps across cell
+    faces, so a stage that lands on the other side of a face in FP32 than in FP64 takes a different
+    J for that stage: an error of order h |dJ| |M| rather than of the rounding, for the few tracers
+    (about the position error over the spacing, per stage and axis) that pass that close to a face."""
+    rel = np.abs(M[ok] - Mo[ok]).max(axis=(1, 2)) / np.abs(Mo[ok]).max(axis=(1, 2))
+    print(f"grad F rel err: median {np.median(rel):.3g} p99 {np.quantile(rel, 0.99):.3g} "
+          f"p99.9 {np.quantile(rel, 0.999):.3g} max {rel.max():.3g} n {rel.size}")
+    assert np.median(rel) <= 1e-5, np.median(rel)
+    assert np.quantile(rel, 0.99) <= 1e-3, np.quantile(rel, 0.99)
+    assert rel.max() <= 5e-2, rel.max()
+
+
+def check_against_oracle(g, r, dt, jobs):
+    F = oracle.RectField(g.frames, g.times, g.origin, g.spacing, g.periodic, g.time_periodic, g.period)
+    x0 = r["seeds"].astype(np.float64)
+    for j, (t0, T) in enumerate(zip(*jobs)):
+        v, p = r["var"][j], r["plain"][j]
+        # the position part: the plain kernel's, bit for bit
+        np.testing.assert_array_equal(v["x"], p["x"])
+        np.testing.assert_array_equal(v["st"], p["st"])
+        np.testing.assert_array_equal(v["te"], p["te"])
+        xT, Mo, sto, _ = oracle.rk4_var(F, x0, t0, T, dt)
+        np.testing.assert_array_equal(v["st"], sto)
+        ok = sto == oracle.OK
+        assert ok.sum() > 0
+        check_grad(v["M"], Mo, ok)
+        lam, sig = oracle.ftle(oracle.cauchy_green(np.where(ok[:, None, None], Mo, np.nan)), g.dim, T)
+        check_ftle(v["ftle"], sig)
+        assert np.isnan(v["ftle"][~ok]).all()
+        # Eq. 1 on the GPU's own grad F, bit for bit
+        Gg = np.where(ok[:, None, None], v["M"].astype(np.float64), np.nan)
+        np.testing.assert_array_equal(v["C"], oracle.cauchy_green(Gg))
+
+
+def test_variational_gyre(ctx):
+    g = inputs.double_gyre()
+    n, lo, hi, dt = (96, 48), (0.0, 0.0), (2.0, 1.0), 0.05
+    jobs = ([0.0, 2.5], [5.0, 4.0])
+    r = var_run(ctx, g, n, lo, hi, (0, 0), dt, jobs)
+    check_against_oracle(g, r, dt, jobs)
+
+
+def test_variational_gyre_backward_with_exits(ctx):
+    # the double gyre cut at x = 1.5: tracers leave, their grad F and FTLE are NaN
+    g = inputs.double_gyre()
+    g = replace(g, frames=np.ascontiguousarray(g.frames[:, :, :97]))
+    n, lo, hi, dt = (90, 60), (0.0, 0.0), (1.5, 1.0), 0.05
+    jobs = ([6.0], [-6.0])
+    r = var_run(ctx, g, n, lo, hi, (0, 0), dt, jobs)
+    assert (r["var"][0]["st"] != 0).sum() > 100
+    check_against_oracle(g, r, dt, jobs)
+
+
+@pytest.mark.parametrize("storage", [lcs.F32, lcs.F16])
+def test_variational_abc(ctx, storage):
+    g = inputs.abc(n=32, nframes=17, t_end=2.0)
+    if storage == lcs.F16:
+        g = replace(g, frames=round_fp16(g.frames))
+    L = 2 * np.pi
+    n, lo, hi, dt = (21, 19, 18), (0.0, 0.0, 0.0), (L, L, L), 0.02
+    jobs = ([0.0], [2.0])
+    r = var_run(ctx, g, n, lo, hi, (1, 1, 1), dt, jobs, storage=storage)
+    check_against_oracle(g, r, dt, jobs)
+
+
+def test_variational_abc_bounded(ctx):
+    # non-periodic 3D: tracers leave the box
+    g = replace(inputs.abc(n=32, nframes=17, t_end=2.0), periodic=(0, 0, 0))
+    n, lo, hi, dt = (20, 18, 17), (0.3, 0.2, 0.4), (5.5, 5.7, 5.6), 0.02
+    jobs = ([0.0], [1.5])
+    r = var_run(ctx, g, n, lo, hi, (0, 0, 0), dt, jobs)
+    assert (r["var"][0]["st"] != 0).sum() > 100
+    check_against_oracle(g, r, dt, jobs)
+
+
+def _R(Z):
+    I = np.eye(len(Z))
+    return I + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_variational_linear_flow(ctx, dim):
+    rng = np.random.default_rng(60 + dim)
+    A = np.round(rng.normal(size=(dim, dim)) * 0.4 * 16) / 16
+    nn = (33,) * dim
+    g = inputs.affine_frames(A, np.zeros((dim, dim)), np.zeros(dim), nn, (-4.0,) * dim, (0.25,) * dim, [0.0, 5.0])
+    n = (24,) * dim
+    dt, T = 0.0625, 1.0
+    r = var_run(ctx, g, n, (-1.0,) * dim, (1.0,) * dim, (0,) * dim, dt, ([0.0], [T]))
+    v = r["var"][0]
+    assert (v["st"] == 0).all()
+    want = np.linalg.matrix_power(_R(dt * A), int(round(T / dt)))
+    err = np.abs(v["M"] - want[None]).max() / np.abs(want).max()
+    assert err <= 1e-5, err
+
+
+def test_variational_rejects(ctx):
+    g = inputs.double_gyre(nx=17, ny=9, nframes=3, t_end=1.0)
+    field = lcs.lcs_load_field(ctx, rect_desc(g), g.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (8, 4), (0.0, 0.0), (2.0, 1.0)))
+    aux = lcs.lcs_seed_aux(ctx, seeds, [0.01, 0.01])
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 2)
+    fa = lcs.lcs_flowmap_create(ctx, aux, 1)
+    f = np.empty(32, dtype=np.float32)
+    M = np.empty((32, 2, 2), dtype=np.float32)
+    try:
+        for kw in (dict(method=lcs.RK45, T=1.0), dict(method=lcs.RK4, T=1.0, dt=0.05, snap_T=[0.5])):
+            with pytest.raises(lcs.LcsError) as e:
+                lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(variational=True, **kw), fm)
+            assert e.value.status == 7, kw
+        with pytest.raises(lcs.LcsError) as e:
+            lcs.lcs_advect(ctx, field, aux, lcs.advect_opts(lcs.RK4, T=1.0, dt=0.05, variational=True), fa)
+        assert e.value.status == 7
+        # a flow map no variational run wrote
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=1.0, dt=0.05), fm)
+        for call in (lambda: lcs.lcs_flowmap_grad(ctx, fm, 0, M), lambda: lcs.lcs_ftle_variational(ctx, fm, 0, f)):
+            with pytest.raises(lcs.LcsError) as e:
+                call()
+            assert e.value.status == 1
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=1.0, dt=0.05, variational=True), fm)
+        with pytest.raises(lcs.LcsError) as e:
+            lcs.lcs_flowmap_grad(ctx, fm, 2, M)
+        assert e.value.status == 1
+        lcs.lcs_flowmap_grad(ctx, fm, 0, M)
+        # a later plain run invalidates the gradient
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=1.0, dt=0.05), fm)
+        with pytest.raises(lcs.LcsError):
+            lcs.lcs_ftle_variational(ctx, fm, 0, f)
+        lcs.lcs_synchronize(ctx)
+    finally:
+        lcs.lcs_free_flowmap(fa)
+        lcs.lcs_free_flowmap(fm)
+        lcs.lcs_free_seeds(aux)
+        lcs.lcs_free_seeds(seeds)
+        lcs.lcs_free_field(field)
