@@ -10,7 +10,7 @@ arithmetic).
 The C part (``lcs_oracle.c``) is the literal FP64 definition of each step of the
 paper's path (arXiv 2209.13775): the linear-in-time, (bi/tri)linear-in-space
 Interpolator and the Seed, Flow Map and Cauchy-Green filters of Sec. 2, Eq. 1 and
-Eq. 2, and the local tetrahedral cell search of Sec. 3.1.  This module only
+Eq. 2, and the local cell search of Sec. 3.1 on tetrahedra and triangles.  This module only
 marshals numpy arrays into it.  ``oracle.mlp`` holds the FP64 network oracle.
 """
 from __future__ import annotations
@@ -62,6 +62,14 @@ class _Tet(ctypes.Structure):
                 ("frames", ctypes.c_void_p), ("walk_limit", ctypes.c_int)]
 
 
+class _Tri(ctypes.Structure):
+    _fields_ = [("nnodes", ctypes.c_longlong), ("ncells", ctypes.c_longlong),
+                ("xy", ctypes.c_void_p), ("tris", ctypes.c_void_p), ("nbrs", ctypes.c_void_p),
+                ("nframes", ctypes.c_int), ("times", ctypes.c_void_p),
+                ("time_periodic", ctypes.c_int), ("period", ctypes.c_double),
+                ("frames", ctypes.c_void_p), ("walk_limit", ctypes.c_int)]
+
+
 class _Analytic(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("dim", ctypes.c_int), ("p", ctypes.c_double * 24)]
 
@@ -96,6 +104,13 @@ def lib() -> ctypes.CDLL:
             L.ora_tet_locate_brute.restype = LL
             L.ora_tet_locate_walk.argtypes = [P, LL, P]
             L.ora_tet_locate_walk.restype = LL
+            L.ora_tri_velocity.argtypes = [P, P, D, P, P]
+            L.ora_orient2d_exact.argtypes = [P, P, P]
+            L.ora_tri_contains.argtypes = [P, LL, P, P]
+            L.ora_tri_locate_brute.argtypes = [P, P]
+            L.ora_tri_locate_brute.restype = LL
+            L.ora_tri_locate_walk.argtypes = [P, LL, P]
+            L.ora_tri_locate_walk.restype = LL
             L.ora_set_threads.argtypes = [I]
             _lib = L
     return _lib
@@ -252,6 +267,73 @@ class TetField:
             if c >= 0:
                 start = c
         return out
+
+
+class TriField:
+    """Triangle mesh with nodal frames [nframes][nnodes][2] FP32 (2D unstructured data, Sec. 4)."""
+
+    kind = 3
+    dim = 2
+
+    def __init__(self, xy, tris, nbrs, frames, times, time_periodic=False, period=0.0,
+                 walk_limit=100000):
+        self.xy = np.ascontiguousarray(xy, dtype=np.float32)
+        self.tris = np.ascontiguousarray(tris, dtype=np.int32)
+        self.nbrs = np.ascontiguousarray(nbrs, dtype=np.int32)
+        self.frames = np.ascontiguousarray(frames, dtype=np.float32)
+        self.times = np.ascontiguousarray(times, dtype=np.float64)
+        s = _Tri()
+        s.nnodes = self.xy.shape[0]
+        s.ncells = self.tris.shape[0]
+        s.xy = self.xy.ctypes.data
+        s.tris = self.tris.ctypes.data
+        s.nbrs = self.nbrs.ctypes.data
+        s.nframes = int(self.frames.shape[0])
+        s.times = self.times.ctypes.data
+        s.time_periodic = int(bool(time_periodic))
+        s.period = float(period)
+        s.frames = self.frames.ctypes.data
+        s.walk_limit = int(walk_limit)
+        self.struct = s
+
+    def velocity(self, x, t, cell=0):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        u = np.zeros(2)
+        c = ctypes.c_int(int(cell))
+        out = lib().ora_tri_velocity(ctypes.byref(self.struct), _p(x), float(t), ctypes.byref(c), _p(u))
+        return (None if out else u), c.value
+
+    def contains(self, t, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        onb = ctypes.c_int(0)
+        r = lib().ora_tri_contains(ctypes.byref(self.struct), int(t), _p(p), ctypes.byref(onb))
+        return bool(r), bool(onb.value)
+
+    def locate_brute(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        return int(lib().ora_tri_locate_brute(ctypes.byref(self.struct), _p(p)))
+
+    def locate_walk(self, p, start=0):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        return int(lib().ora_tri_locate_walk(ctypes.byref(self.struct), int(start), _p(p)))
+
+    def locate_seeds(self, seeds_soa):
+        """Exact cell of every FP32 seed (-1 outside), walking from the previous seed's cell."""
+        s = np.ascontiguousarray(np.asarray(seeds_soa, dtype=np.float32).T)
+        out = np.empty(s.shape[0], dtype=np.int32)
+        start = 0
+        for i in range(s.shape[0]):
+            c = self.locate_walk(s[i], start)
+            out[i] = c
+            if c >= 0:
+                start = c
+        return out
+
+
+def orient2d(a, b, c):
+    """Exact sign of (b - a) x (c - a) for FP32 points."""
+    a, b, c = (np.ascontiguousarray(v, dtype=np.float32) for v in (a, b, c))
+    return int(lib().ora_orient2d_exact(_p(a), _p(b), _p(c)))
 
 
 def time_locate(times, t, time_periodic=False, period=0.0):

@@ -529,6 +529,193 @@ int ora_tet_velocity(const ora_tet_field *f, const double *x, double t, int *cel
 }
 
 /* ====================================================================
+ * Triangle meshes (2D unstructured velocity data, e.g. the stenosis
+ * geometries of Sec. 4): the same exact predicates, walk, tie-break and P1
+ * interpolation as the tets, one dimension lower.  orient2d sums six
+ * products of two FP32 coordinates, each exact in FP64, into a
+ * nonoverlapping expansion (Shewchuk 1997).
+ * ==================================================================== */
+int ora_orient2d_exact(const float *a, const float *b, const float *c)
+{
+    /* (b-a) x (c-a) = bx cy - by cx - ax cy + ay cx + ax by - ay bx */
+    const double terms[6] = {(double)b[0] * (double)c[1], -((double)b[1] * (double)c[0]),
+                             -((double)a[0] * (double)c[1]), (double)a[1] * (double)c[0],
+                             (double)a[0] * (double)b[1], -((double)a[1] * (double)b[0])};
+    double e[16], h[16];
+    int len = 0;
+    for (int i = 0; i < 6; ++i) {
+        int n = grow_expansion(len, e, terms[i], h);
+        for (int k = 0; k < n; ++k) e[k] = h[k];
+        len = n;
+    }
+    for (int i = len - 1; i >= 0; --i) {
+        if (e[i] > 0.0) return 1;
+        if (e[i] < 0.0) return -1;
+    }
+    return 0;
+}
+
+static const float *tri_vertex(const ora_tri_field *f, long long t, int v)
+{
+    return f->xy + 2LL * f->tris[3 * t + v];
+}
+
+static void tri_bary_signs(const ora_tri_field *f, long long t, const float *p, int *sg)
+{
+    const float *v[3];
+    for (int i = 0; i < 3; ++i) v[i] = tri_vertex(f, t, i);
+    int D = ora_orient2d_exact(v[0], v[1], v[2]);
+    for (int i = 0; i < 3; ++i) {
+        const float *w[3] = {v[0], v[1], v[2]};
+        w[i] = p;
+        sg[i] = D * ora_orient2d_exact(w[0], w[1], w[2]);
+    }
+}
+
+int ora_tri_contains(const ora_tri_field *f, long long t, const float *p, int *on_boundary)
+{
+    int sg[3];
+    tri_bary_signs(f, t, p, sg);
+    int inside = 1, onb = 0;
+    for (int i = 0; i < 3; ++i) {
+        if (sg[i] < 0) inside = 0;
+        if (sg[i] == 0) onb = 1;
+    }
+    if (on_boundary) *on_boundary = inside && onb;
+    return inside;
+}
+
+long long ora_tri_locate_brute(const ora_tri_field *f, const float *p)
+{
+    for (long long t = 0; t < f->ncells; ++t)
+        if (ora_tri_contains(f, t, p, NULL)) return t;
+    return -1;
+}
+
+/* FP64 barycentric coordinates of x in triangle t (Cramer's rule on differences) */
+static void tri_bary(const ora_tri_field *f, long long t, const double *x, double *lam)
+{
+    const float *a = tri_vertex(f, t, 0), *b = tri_vertex(f, t, 1), *c = tri_vertex(f, t, 2);
+    double e1[2] = {(double)b[0] - a[0], (double)b[1] - a[1]};
+    double e2[2] = {(double)c[0] - a[0], (double)c[1] - a[1]};
+    double r[2] = {x[0] - a[0], x[1] - a[1]};
+    double D = e1[0] * e2[1] - e1[1] * e2[0];
+    lam[1] = (r[0] * e2[1] - r[1] * e2[0]) / D;
+    lam[2] = (e1[0] * r[1] - e1[1] * r[0]) / D;
+    lam[0] = 1.0 - lam[1] - lam[2];
+}
+
+long long ora_tri_locate_walk(const ora_tri_field *f, long long start, const float *p)
+{
+    long long t = (start >= 0 && start < f->ncells) ? start : 0;
+    int found = 0;
+    int limit = f->walk_limit > 0 ? f->walk_limit : 100000;
+    double xp[2] = {p[0], p[1]};
+    for (int step = 0; step < limit; ++step) {
+        int sg[3];
+        tri_bary_signs(f, t, p, sg);
+        int best = -1;
+        double bestv = 0.0, lam[3];
+        tri_bary(f, t, xp, lam);
+        for (int i = 0; i < 3; ++i)
+            if (sg[i] < 0 && (best < 0 || lam[i] < bestv)) {
+                best = i;
+                bestv = lam[i];
+            }
+        if (best < 0) {
+            found = 1;
+            break;
+        }
+        long long nb = f->nbrs[3 * t + best];
+        /* a boundary edge separates p from this triangle: outside a convex mesh, but a
+         * non-convex one (a channel with a constriction) may still hold p elsewhere */
+        if (nb < 0) return ora_tri_locate_brute(f, p);
+        t = nb;
+    }
+    if (!found) return ora_tri_locate_brute(f, p);
+    int onb = 0;
+    ora_tri_contains(f, t, p, &onb);
+    if (!onb) return t;
+    /* p on an edge or a vertex: lowest id among the closed triangles holding p,
+     * collected across edges that contain p                                  */
+    long long stack[1024], seen[1024];
+    int ns = 0, nseen = 0;
+    stack[ns++] = t;
+    seen[nseen++] = t;
+    long long best = t;
+    while (ns > 0) {
+        long long c = stack[--ns];
+        if (c < best) best = c;
+        int sg[3];
+        tri_bary_signs(f, c, p, sg);
+        for (int i = 0; i < 3; ++i) {
+            if (sg[i] != 0) continue;
+            long long nb = f->nbrs[3 * c + i];
+            if (nb < 0) continue;
+            int dup = 0;
+            for (int s = 0; s < nseen; ++s)
+                if (seen[s] == nb) dup = 1;
+            if (dup) continue;
+            if (!ora_tri_contains(f, nb, p, NULL)) continue;
+            if (nseen >= 1024 || ns >= 1024) return ora_tri_locate_brute(f, p);
+            seen[nseen++] = nb;
+            stack[ns++] = nb;
+        }
+    }
+    return best;
+}
+
+static long long tri_locate_fp64(const ora_tri_field *f, long long start, const double *x, double *lam)
+{
+    const double tol = 1e-12;
+    long long t = (start >= 0 && start < f->ncells) ? start : 0;
+    int limit = f->walk_limit > 0 ? f->walk_limit : 100000;
+    for (int step = 0; step < limit; ++step) {
+        tri_bary(f, t, x, lam);
+        int best = -1;
+        double bestv = -tol;
+        for (int i = 0; i < 3; ++i)
+            if (lam[i] < bestv) {
+                best = i;
+                bestv = lam[i];
+            }
+        if (best < 0) return t;
+        long long nb = f->nbrs[3 * t + best];
+        if (nb < 0) break; /* across a boundary edge: settled by testing every triangle */
+        t = nb;
+    }
+    for (long long c = 0; c < f->ncells; ++c) {
+        tri_bary(f, c, x, lam);
+        if (lam[0] >= -tol && lam[1] >= -tol && lam[2] >= -tol) return c;
+    }
+    return -1;
+}
+
+int ora_tri_velocity(const ora_tri_field *f, const double *x, double t, int *cell, double *u)
+{
+    double lam[3];
+    long long c = tri_locate_fp64(f, *cell, x, lam);
+    if (c < 0) return 1;
+    *cell = (int)c;
+    int k;
+    double a;
+    ora_time_locate(f->times, f->nframes, f->time_periodic, f->period, t, &k, &a);
+    int k1 = (f->nframes > 1) ? k + 1 : k;
+    const float *fa = f->frames + 2LL * f->nnodes * k;
+    const float *fb = f->frames + 2LL * f->nnodes * k1;
+    for (int comp = 0; comp < 2; ++comp) {
+        double sa = 0.0, sb = 0.0;
+        for (int v = 0; v < 3; ++v) {
+            long long node = f->tris[3 * c + v];
+            sa += lam[v] * (double)fa[2 * node + comp];
+            sb += lam[v] * (double)fb[2 * node + comp];
+        }
+        u[comp] = (1.0 - a) * sa + a * sb;
+    }
+    return 0;
+}
+
+/* ====================================================================
  * Seed lattice (Sec. 2 "Seed": structured grid of seed points).
  * ==================================================================== */
 void ora_seed_grid(int dim, const int n[3], const double lo[3], const double hi[3],
@@ -564,11 +751,12 @@ typedef struct {
     int dim;
 } vel_src;
 
-/* returns 0 inside, 1 outside (only tets can be outside) */
+/* returns 0 inside, 1 outside (only meshes can be outside) */
 static int eval_u(const vel_src *s, const double *x, double t, int *cell, double *u)
 {
     if (s->kind == 0) return ora_rect_velocity((const ora_rect_field *)s->field, x, t, u);
     if (s->kind == 1) return ora_analytic_velocity((const ora_analytic_field *)s->field, x, t, u);
+    if (s->kind == 3) return ora_tri_velocity((const ora_tri_field *)s->field, x, t, cell, u);
     return ora_tet_velocity((const ora_tet_field *)s->field, x, t, cell, u);
 }
 
@@ -587,7 +775,7 @@ long long ora_rk4(int field_kind, const void *field, int dim, long long n,
         int cell = cells ? cells[p] : 0;
         unsigned char st = ORA_OK;
         double te = t0 + T;
-        if (field_kind == 2 && cell < 0) {
+        if (field_kind >= 2 && cell < 0) {
             st = ORA_OUTSIDE;
             te = t0;
         }
@@ -777,7 +965,7 @@ long long ora_dp45(int field_kind, const void *field, int dim, long long n,
             tr[q].cell = cells ? cells[p] : 0;
             tr[q].st = ORA_OK;
             tr[q].te = tend;
-            if (field_kind == 2 && tr[q].cell < 0) {
+            if (field_kind >= 2 && tr[q].cell < 0) {
                 tr[q].st = ORA_OUTSIDE;
                 tr[q].te = t0;
             }

@@ -17,7 +17,8 @@
  *   Sec. 2 "Flow Map": single-step Runge-Kutta integration; trajectories that
  *          leave the data domain.
  *   Sec. 2 "Cauchy-Green": central differences of final positions, eigenvalues.
- *   Sec. 3.1: local cell search on tetrahedral grids.
+ *   Sec. 3.1: local cell search on tetrahedral grids (triangular grids in 2D),
+ *          used for the 2D unstructured stenosis data of Sec. 4.
  *
  * Arrays are plain C arrays.  Positions are SoA: x[0..N), then y[0..N), then
  * z[0..N).  Seed index is x-fastest: id = i + nx*(j + ny*k).
@@ -71,6 +72,21 @@ typedef struct {
     int walk_limit;        /* cap on walk steps before brute force          */
 } ora_tet_field;
 
+/* Velocity frames on a triangle mesh (2D unstructured data such as the
+ * stenosis geometries of Sec. 4; P1 interpolation inside a triangle).       */
+typedef struct {
+    long long nnodes, ncells;
+    const float *xy;       /* [nnodes][2]                                   */
+    const int *tris;       /* [ncells][3] node ids                          */
+    const int *nbrs;       /* [ncells][3] triangle across the edge opposite vertex v, -1 = boundary */
+    int nframes;
+    const double *times;
+    int time_periodic;
+    double period;
+    const float *frames;   /* [nframes][nnodes][2]                          */
+    int walk_limit;        /* cap on walk steps before brute force          */
+} ora_tri_field;
+
 /* Analytic velocity fields.  Used by the pins that need a smooth field
  * (order of convergence, conservation laws); they never feed the GPU.       */
 #define ORA_AN_GYRE 0     /* double gyre: p[0]=A, p[1]=eps, p[2]=omega                  */
@@ -105,6 +121,12 @@ int ora_analytic_velocity(const ora_analytic_field *f, const double *x, double t
  * Returns 0 inside, 1 outside the mesh.                                     */
 int ora_tet_velocity(const ora_tet_field *f, const double *x, double t, int *cell, double *u);
 
+/* u(x, t) on a triangle mesh: FP64 walk from *cell (barycentric tolerance
+ * 1e-12), every triangle tested when the walk reaches a boundary edge, P1
+ * interpolation.  *cell is the walk's start (in) and the containing triangle (out).
+ * Returns 0 inside, 1 outside the mesh.                                     */
+int ora_tri_velocity(const ora_tri_field *f, const double *x, double t, int *cell, double *u);
+
 /* ---------------------------------------------------------- seed grid (a2) */
 
 /* Structured seed lattice (Sec. 2, "Seed"): along axis a,
@@ -118,12 +140,13 @@ void ora_seed_grid(int dim, const int n[3], const double lo[3], const double hi[
 
 /* Fixed-step classical RK4 on Eq. 2 (Sec. 2 "Flow Map"; Sec. 3.1).
  *   dt carries the sign of T; nsteps = round(|T|/|dt|); t_n = t0 + n*dt.
- * field_kind: 0 = rectilinear (ora_rect_field), 1 = analytic, 2 = tet.
+ * field_kind: 0 = rectilinear (ora_rect_field), 1 = analytic, 2 = tet,
+ * 3 = triangle mesh (ora_tri_field).
  * x0 is [dim][n] FP64 SoA; xT the same layout.  status/t_exit per seed.
  * Rectilinear: a tracer more than one cell outside a non-periodic axis after
  * a step is LEFT, frozen there, t_exit = end time of that step.
- * Tet: a stage point outside the mesh makes the tracer LEFT, frozen at the
- * start of the step, t_exit = t_n.  cells (tet only, may be NULL otherwise) is
+ * Tet / triangle: a stage point outside the mesh makes the tracer LEFT, frozen at the
+ * start of the step, t_exit = t_n.  cells (meshes only, may be NULL otherwise) is
  * the start cell per seed, -1 = seed outside (status OUTSIDE).
  * Returns the number of steps per tracer.                                   */
 /* RK4 on Eq. 2 with the variational equation dM/dt = J M, M(t0) = I (rectilinear
@@ -205,6 +228,25 @@ long long ora_tet_locate_brute(const ora_tet_field *f, const float *p);
  * closed tets holding p.  Falls back to brute force past walk_limit.
  * Returns the tet id or -1 if p is outside the mesh.                        */
 long long ora_tet_locate_walk(const ora_tet_field *f, long long start, const float *p);
+
+/* ------------------------------------------------- triangle geometry */
+
+/* Sign of the orientation determinant (b - a) x (c - a) of three FP32 points,
+ * evaluated exactly: +1 when c lies left of the directed line a -> b.       */
+int ora_orient2d_exact(const float *a, const float *b, const float *c);
+
+/* Exact containment of p in the closed triangle t (as ora_tet_contains).   */
+int ora_tri_contains(const ora_tri_field *f, long long t, const float *p, int *on_boundary);
+
+/* Lowest id among the closed triangles containing p; -1 when none does.    */
+long long ora_tri_locate_brute(const ora_tri_field *f, const float *p);
+
+/* Walk from start across edges whose line separates p from the triangle,
+ * then the lowest-id tie-break among the closed triangles holding p (as
+ * ora_tet_locate_walk).  A walk that reaches a boundary edge falls back to
+ * brute force (the mesh need not be convex).  Returns the triangle id or -1
+ * outside the mesh.                                                         */
+long long ora_tri_locate_walk(const ora_tri_field *f, long long start, const float *p);
 
 /* Set the OpenMP thread count (<= 0: leave the runtime default).  Returns
  * the count in effect.                                                      */

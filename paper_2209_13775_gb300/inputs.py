@@ -16,6 +16,10 @@ are not available:
 * ``pipe_mesh`` / ``pipe_frames``: a Delaunay tetrahedralisation of a jittered
   lattice in a cylinder (R = 1, L = 10) carrying pulsatile Poiseuille flow plus
   a random-phase swirl; stands in for the 3D unstructured aneurysm data.
+* ``stenosis_mesh`` / ``stenosis_frames``: a body-fitted triangulation of a 2D
+  channel with a Gaussian constriction carrying pulsatile, flux-conserving
+  Poiseuille flow plus a travelling wall-bounded wave; stands in for the 2D
+  unstructured stenosis data.
 * ``affine_frames``: u = (A0 + t A1) x + b, which bilinear/trilinear/P1
   interpolation reproduces exactly (used by parity tests with closed forms).
 """
@@ -199,6 +203,102 @@ def pipe_frames(mesh: TetInput, nframes=50, period=1.0, R=1.0, L=10.0, seed=SEED
     mesh.time_periodic = True
     mesh.period = period
     mesh.extra.update({"phases": phases, "amp": amp})
+    return mesh
+
+
+def tri_neighbours(tris):
+    """Triangle across the edge opposite vertex j of each triangle (-1 on the boundary)."""
+    tris = np.asarray(tris, dtype=np.int64)
+    nc = tris.shape[0]
+    nbrs = np.full((nc, 3), -1, dtype=np.int32)
+    seen = {}
+    for t in range(nc):
+        for j in range(3):
+            a, b = sorted((int(tris[t, (j + 1) % 3]), int(tris[t, (j + 2) % 3])))
+            other = seen.pop((a, b), None)
+            if other is None:
+                seen[(a, b)] = (t, j)
+            else:
+                nbrs[t, j] = other[0]
+                nbrs[other[0], other[1]] = t
+    return nbrs
+
+
+def stenosis_halfwidth(x, H=1.0, depth=0.5, xc=3.0, w=0.75):
+    """Channel half-width H (1 - depth exp(-((x - xc) / w)^2)) and its x-derivative."""
+    e = np.exp(-((x - xc) / w) ** 2)
+    return H * (1.0 - depth * e), 2.0 * H * depth * e * (x - xc) / (w * w)
+
+
+def stenosis_mesh(h=0.05, L=10.0, H=1.0, depth=0.5, xc=3.0, w=0.75, jitter=0.2, seed=SEED,
+                  with_neighbours=True) -> TetInput:
+    """Body-fitted triangles of the channel 0 <= x <= L, |y| <= hw(x) (stenosis_halfwidth).
+
+    Columns x_i = i L / nx (nx = round(L / h)); on column i, nodes at y = hw(x_i) s_j with
+    s_j = -1 + 2 j / ny (ny = 2 round(H / h)), so every column has the same node count and the
+    walls are node rows.  Interior nodes move by +-jitter (x and s, in units of the column and
+    row spacing; x fixed on the inlet and outlet columns, s fixed on the walls).  Each quad splits
+    along a diagonal chosen per quad from the seeded generator; triangles are counter-clockwise.
+    Returned as TetInput with xyz = xy [nnodes][2], tets = triangles [ncells][3] and, when
+    with_neighbours, nbrs [ncells][3] (across the edge opposite vertex j), else None.
+    """
+    rng = np.random.default_rng(seed)
+    nx = int(round(L / h))
+    ny = 2 * int(round(H / h))
+    i = np.arange(nx + 1, dtype=np.float64)
+    j = np.arange(ny + 1, dtype=np.float64)
+    I, Jg = np.meshgrid(i, j, indexing="xy")          # [ny+1][nx+1]
+    jx = rng.uniform(-jitter, jitter, I.shape)
+    js = rng.uniform(-jitter, jitter, I.shape)
+    jx[:, 0] = jx[:, -1] = 0.0
+    js[0, :] = js[-1, :] = 0.0
+    X = (I + jx) * (L / nx)
+    S = -1.0 + (Jg + js) * (2.0 / ny)
+    hw, _ = stenosis_halfwidth(X, H, depth, xc, w)
+    xy = np.stack([X.ravel(), (hw * S).ravel()], axis=1).astype(np.float32)
+    node = lambda a, b: b * (nx + 1) + a
+    a, b = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    a, b = a.ravel(), b.ravel()
+    v00, v10, v01, v11 = node(a, b), node(a + 1, b), node(a, b + 1), node(a + 1, b + 1)
+    diag = rng.integers(0, 2, a.size).astype(bool)
+    t1 = np.where(diag[:, None], np.stack([v00, v10, v11], 1), np.stack([v00, v10, v01], 1))
+    t2 = np.where(diag[:, None], np.stack([v00, v11, v01], 1), np.stack([v10, v11, v01], 1))
+    tris = np.empty((2 * a.size, 3), dtype=np.int32)
+    tris[0::2] = t1
+    tris[1::2] = t2
+    nbrs = tri_neighbours(tris) if with_neighbours else None
+    return TetInput(xy, tris, nbrs, extra={"L": L, "H": H, "depth": depth, "xc": xc, "w": w, "h": h})
+
+
+def stenosis_frames(mesh: TetInput, nframes=40, period=1.0, eps=0.05, wavelength=2.0, speed=2.0) -> TetInput:
+    """Stream function psi = Q(t) f(s) + eps g(s) sin(k (x - c t)), s = y / hw(x):
+    f(s) = (3 s - s^3) / 2 carries the flux Q(t) = 1 + 0.5 sin(2 pi t / period) through every
+    section, g(s) = (1 - s^2)^2 a wave travelling downstream; u = d psi / dy, v = -d psi / dx,
+    so the field is divergence-free and vanishes on the walls.  nframes frames per period plus the
+    closing frame (equal to the first), time-periodic."""
+    x = mesh.xyz[:, 0].astype(np.float64)
+    y = mesh.xyz[:, 1].astype(np.float64)
+    ex = mesh.extra
+    hw, dhw = stenosis_halfwidth(x, ex["H"], ex["depth"], ex["xc"], ex["w"])
+    s = y / hw
+    ds_dx = -s * dhw / hw
+    fp = 1.5 * (1.0 - s * s)
+    g = (1.0 - s * s) ** 2
+    gp = -4.0 * s * (1.0 - s * s)
+    k = 2 * np.pi / wavelength
+    times = np.array([period * q / nframes for q in range(nframes + 1)], dtype=np.float64)
+    frames = np.empty((nframes + 1, x.size, 2), dtype=np.float32)
+    for q, t in enumerate(times):
+        Q = 1.0 + 0.5 * np.sin(2 * np.pi * t / period)
+        ph = k * (x - speed * t)
+        u = Q * fp / hw + eps * gp * np.sin(ph) / hw
+        v = -(Q * fp * ds_dx + eps * (gp * ds_dx * np.sin(ph) + g * k * np.cos(ph)))
+        frames[q, :, 0] = u
+        frames[q, :, 1] = v
+    mesh.frames = frames
+    mesh.times = times
+    mesh.time_periodic = True
+    mesh.period = period
     return mesh
 
 

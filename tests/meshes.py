@@ -31,3 +31,23 @@ def kuhn_mesh(n):
             else:
                 faces[key] = (t, j)
     return pts, tets, nbrs
+
+
+def tri_grid_mesh(n, seed=7):
+    """n^2 unit squares with integer nodes, each split into 2 triangles along a diagonal chosen
+    per square; the vertex order of about half the triangles is reversed (clockwise), so location
+    and interpolation are exercised on both orientations.  Neighbours by edge matching."""
+    from paper_2209_13775_gb300.inputs import tri_neighbours
+
+    rng = np.random.default_rng(seed)
+    idx = lambda i, j: i + (n + 1) * j
+    pts = np.array([[i, j] for j in range(n + 1) for i in range(n + 1)], dtype=np.float32)
+    tris = []
+    for j in range(n):
+        for i in range(n):
+            a, b, c, d = idx(i, j), idx(i + 1, j), idx(i, j + 1), idx(i + 1, j + 1)
+            pair = [[a, b, d], [a, d, c]] if rng.integers(2) else [[a, b, c], [b, d, c]]
+            for t in pair:
+                tris.append(t[::-1] if rng.integers(2) else t)
+    tris = np.array(tris, dtype=np.int32)
+    return pts, tris, tri_neighbours(tris)
