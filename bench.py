@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seeds-side", type=int, default=N_SIDE,
                    help="seed lattice side (default 256; smaller only for profiling captures)")
-    p.add_argument("--config", default="c2", choices=["c2", "c3", "c3x", "c4", "c5", "next"],
+    p.add_argument("--config", default="c2", choices=["c2", "c3", "c3x", "c4", "c5", "tri", "next"],
                    help="c2: the 3D ABC workload (default, the headline); c3: the batched sliding-window "
                         "workload; c3x: its full cross product of horizons from multi-horizon snapshots; "
                         "c4: adaptive DP5(4) on the tetrahedral pipe; c5: the learned surrogate; next: the "
@@ -725,6 +725,157 @@ def c4_arm(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ triangle-mesh arm
+
+TRI_WORKLOAD = ("stenosis on triangles: body-fitted triangulation of a channel 0<=x<=10, |y|<=1-0.5exp(-((x-3)/0.75)^2) "
+                "(2000x400 jittered quads, 1.6M triangles), pulsatile flux-conserving Poiseuille flow + travelling "
+                "wall wave, 40 FP32 frames per period 1 (time-periodic); 4096x1024 seed lattice on [0,10]x[-1,1] "
+                "(4,194,304 seeds, those beside the constriction outside the mesh); RK4 dt=0.002, t0=0, T=1 "
+                "(500 steps), cell walk per stage; FD grad F, 2x2 Cauchy-Green (FP64) and FTLE")
+TRI_N, TRI_LO, TRI_HI = (4096, 1024), (0.0, -1.0), (10.0, 1.0)
+TRI_T, TRI_DT, TRI_H = 1.0, 0.002, 0.005
+# algorithmic bytes of one stage evaluation on triangles: one walk step (16 B inverse map + 8 B vertex 0),
+# 16 B connectivity, 3 vertices x 16 B frame pairs (u_k, v_k, u_k+1, v_k+1)
+TRI_BYTES_PER_STAGE = 16 + 8 + 16 + 48
+# FP32 flops of one RK4 step on triangles: per stage the barycentric coordinates (10), the P1 and time
+# blend of 3 vertices x 2 components (30 + 1), the stage point (4, stages 2-4); the update (12 + 2)
+TRI_FLOP_PER_STEP = 4 * (10 + 31) + 3 * 4 + 14
+
+
+def alu_peak():
+    """FP32 ALU peak (TFLOP/s) at the measured maximum SM clock, and its basis."""
+    pk, pk_kind = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    return (152 * 128 * 2 * sm_mhz * 1e6 / 1e12,
+            "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, pk_kind))
+
+
+def tri_oracle_block(mesh, ni, nj, threads=0):
+    """Oracle RK4 + FD/CG/FTLE on an ni x nj block of the triangle lattice at the channel centre
+    downstream of the constriction, with a 2-seed stencil halo; returns (interior seeds, seconds,
+    threads, integrated)."""
+    import oracle
+
+    oracle.build()
+    nth = oracle.set_threads(threads)
+    h = [(TRI_HI[a] - TRI_LO[a]) / (TRI_N[a] - 1) for a in range(2)]
+    c = [int(TRI_N[0] * 0.6) - ni // 2, TRI_N[1] // 2 - nj // 2]
+    m = (ni + 4, nj + 4)
+    axes = [(TRI_LO[a] + (c[a] - 2 + np.arange(m[a])) * h[a]).astype(np.float32) for a in range(2)]
+    Y, X = np.meshgrid(axes[1], axes[0], indexing="ij")
+    x0 = np.stack([X.ravel(), Y.ravel()])
+    F = oracle.TriField(mesh.xyz, mesh.tets, mesh.nbrs, mesh.frames, mesh.times, True, mesh.period)
+    t = time.perf_counter()
+    cells = F.locate_seeds(x0)
+    xT, st, _ = oracle.rk4(F, x0.astype(np.float64), 0.0, TRI_T, TRI_DT, cells=cells)
+    G = oracle.flowmap_gradient(2, m, h, (0, 0), (0, 0), xT, st)
+    lam, sig = oracle.ftle(oracle.cauchy_green(G), 2, TRI_T)
+    return ni * nj, time.perf_counter() - t, nth, x0.shape[1]
+
+
+def tri_arm(args, rank, world, local):
+    import torch
+
+    from paper_2209_13775_gb300 import inputs, lcs
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = lcs.lcs_create(local, stream)
+    t_mesh = time.perf_counter()
+    mesh = inputs.stenosis_frames(inputs.stenosis_mesh(h=TRI_H), nframes=40, period=1.0)
+    t_mesh = time.perf_counter() - t_mesh
+    st_kind = {"f32": lcs.F32, "f16": lcs.F16, "bf16": lcs.BF16}[args.storage]
+    desc = lcs.field_desc(2, times=mesh.times, time_periodic=True, period=mesh.period, kind=lcs.TRI,
+                          storage=st_kind, mesh=(mesh.xyz, mesh.tets, mesh.nbrs))
+    t_load = time.perf_counter()
+    field = lcs.lcs_load_field(ctx, desc, mesh.frames)
+    lcs.lcs_synchronize(ctx)
+    t_load = time.perf_counter() - t_load
+    t_seed = time.perf_counter()
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, TRI_N, TRI_LO, TRI_HI), field)
+    lcs.lcs_synchronize(ctx)
+    t_seed = time.perf_counter() - t_seed
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    opts = lcs.advect_opts(lcs.RK4, t0=0.0, T=TRI_T, dt=TRI_DT)
+    ftle = torch.empty(N, dtype=torch.float32, device="cuda")
+    C = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+
+    def step():
+        lcs.lcs_advect(ctx, field, seeds, opts, fm)
+        lcs.lcs_ftle(ctx, fm, 0, ftle, None, C)
+
+    for _ in range(args.warmup):
+        step()
+    lcs.lcs_synchronize(ctx)
+    for ph in range(4):
+        lcs.lcs_timing_read(ctx, ph)
+    lcs.lcs_timing_enable(ctx, True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+    el = a.elapsed_time(b) / 1e3
+    adv_ms, adv_n = lcs.lcs_timing_read(ctx, 0)
+    cg_ms, _ = lcs.lcs_timing_read(ctx, 3)
+    lcs.lcs_timing_enable(ctx, False)
+    status = np.empty(N, dtype=np.uint8)
+    te = np.empty(N, dtype=np.float32)
+    lcs.lcs_flowmap_get(ctx, fm, 0, None, status, te)
+    counts = {name: int((status == v).sum()) for name, v in
+              (("ok", lcs.TRACER_OK), ("left", lcs.TRACER_LEFT), ("outside", lcs.TRACER_OUTSIDE))}
+    nsteps = int(round(TRI_T / TRI_DT))
+    # steps actually taken: all for OK tracers, up to the exit for LEFT ones
+    taken = np.where(status == lcs.TRACER_OK, nsteps,
+                     np.where(status == lcs.TRACER_LEFT, np.rint(te / TRI_DT), 0)).astype(np.int64)
+    tracer_steps = int(taken.sum())
+    launch_s = adv_ms / max(adv_n, 1) / 1e3
+    alg_bytes = float(tracer_steps) * 4 * TRI_BYTES_PER_STAGE
+    flop = float(tracer_steps) * TRI_FLOP_PER_STEP
+    achieved = flop / launch_s / 1e12
+    fp32_peak, peak_basis = alu_peak()
+    line = {
+        "metric": METRIC, "value": N * args.steps / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": TRI_WORKLOAD, "seeds": N, "nodes": int(mesh.xyz.shape[0]),
+                   "triangles": int(mesh.tets.shape[0]), "storage": args.storage,
+                   "mesh_build_s": round(t_mesh, 1), "field_load_ms": round(t_load * 1e3, 1),
+                   "seed_location_ms": round(t_seed * 1e3, 1), "status": counts,
+                   "l2": "no flush: each step writes %.0f MB of outputs (C + FTLE) > 129 MB L2" % (N * 28 / 1e6)},
+        "tracer_steps_per_s": tracer_steps * args.steps / el,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None, "kernel": "rk4_tri_kernel<%s>" % args.storage,
+                     "flop_per_launch": flop, "avg_launch_ms": launch_s * 1e3, "launches": adv_n,
+                     "peak_basis": peak_basis,
+                     "basis": "%d FP32 flops per tracer-step x tracer-steps taken" % TRI_FLOP_PER_STEP,
+                     "gathers": {"bytes_per_launch": alg_bytes, "gbs": alg_bytes / launch_s / 1e9,
+                                 "basis": "%d B per stage x 4 stages (served mostly by L1/L2)"
+                                          % TRI_BYTES_PER_STAGE}},
+        "phases_ms_per_step": {"advect": adv_ms / args.steps, "cg_ftle": cg_ms / args.steps},
+        "clocks": clk.summary(),
+        # per step: the schedule kernel, the RK4 kernel, FD/CG/FTLE
+        "gpu_launches": 3 * args.steps,
+    }
+    if not args.no_cpu_baseline:
+        _, dts, _, _ = tri_oracle_block(mesh, 16, 16)           # calibration
+        per = dts / 400
+        nj = int(max(4, min(400, (12.0 / max(per, 1e-9)) / 104 - 4)))
+        s, dt, nth, integrated = tri_oracle_block(mesh, 100, nj)
+        line["cpu_baseline"] = {"value": s / dt, "unit": "seeds/s", "cores": nth, "kind": "oracle",
+                                "sample": "100x%d block of the 4096x1024 lattice at x = 6 with its 2-seed halo "
+                                          "(%d tracers, RK4), FD/CG/FTLE; %.1f s" % (nj, integrated, dt)}
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    lcs.lcs_destroy(ctx)
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ surrogate arm
 
 C5_WORKLOAD = ("learned surrogate on the double gyre (129x65 FP32, 101 frames, period 10): MLP 7->128x4->3 (SiLU, "
@@ -1035,6 +1186,9 @@ def main():
         return
     if args.config == "next":
         next_arm(args, rank, world, local)
+        return
+    if args.config == "tri":
+        tri_arm(args, rank, world, local)
         return
     if args.config == "c5":
         c5_arm(args, rank, world, local)

@@ -43,7 +43,7 @@ typedef enum {
 } lcs_status;
 
 /* grid kinds, storage precisions, integrators */
-enum { LCS_RECTILINEAR = 0, LCS_TET = 1 };
+enum { LCS_RECTILINEAR = 0, LCS_TET = 1, LCS_TRI = 2 };
 enum { LCS_F32 = 0, LCS_F16 = 1, LCS_BF16 = 2 };
 enum { LCS_RK4 = 0, LCS_RK45 = 1, LCS_SURROGATE = 2 };
 
@@ -86,15 +86,16 @@ lcs_status lcs_synchronize(lcs_ctx *ctx);
 
 /* Velocity data (Sec. 2 "Reader"/"Cache"/"Interpolator"): nodal velocity
  * frames at increasing times, interpolated linearly in time and
- * bilinearly / trilinearly (rectilinear) or piecewise-linearly (tets) in
+ * bilinearly / trilinearly (rectilinear) or piecewise-linearly (tets in 3D,
+ * triangles in 2D: Sec. 3.1, Sec. 4's 2D unstructured stenosis data) in
  * space.  Rectilinear node (i,j,k) sits at origin + (i,j,k)*spacing; a
  * periodic axis has n cells (node n-1 joins node 0) and period n*spacing;
  * queries on a non-periodic axis are clamped to the box.  Time outside
  * [t_first, t_last] uses the end frame unless time_periodic, which wraps t
  * into [t_first, t_first + period).                                         */
 typedef struct {
-    int dim;                    /* 2 or 3 (tets: 3)                                  */
-    int kind;                   /* LCS_RECTILINEAR | LCS_TET                          */
+    int dim;                    /* 2 or 3 (tets: 3, triangles: 2)                    */
+    int kind;                   /* LCS_RECTILINEAR | LCS_TET | LCS_TRI                */
     int n[3];                   /* rectilinear nodes per axis (n[2] unused in 2D)     */
     double origin[3];
     double spacing[3];
@@ -104,16 +105,19 @@ typedef struct {
     int time_periodic;
     double period;
     int storage;                /* LCS_F32 | LCS_F16 | LCS_BF16 (velocity storage)    */
-    /* tetrahedral meshes (kind == LCS_TET), HOST arrays:                              */
+    /* tetrahedral meshes (kind == LCS_TET) and triangle meshes (LCS_TRI), HOST:     */
     long long nnodes, ncells;
-    const float *node_xyz;      /* [nnodes][3]                                        */
-    const int *tets;            /* [ncells][4] node ids                               */
-    const int *nbrs;            /* [ncells][4] tet across the face opposite vertex j,
-                                   -1 on the boundary; NULL: built by the library     */
+    const float *node_xyz;      /* [nnodes][3] (tets) or [nnodes][2] (triangles)      */
+    const int *tets;            /* [ncells][4] node ids (tets), [ncells][3] (triangles,
+                                   either orientation; the mesh need not be convex)   */
+    const int *nbrs;            /* [ncells][4] tet across the face opposite vertex j
+                                   ([ncells][3]: triangle across the edge opposite
+                                   vertex j), -1 on the boundary; NULL: built by the
+                                   library                                           */
 } lcs_field_desc;
 
 /* Copy velocity frames into device storage.  frames is FP32,
- * [nframes][nz][ny][nx][dim] (rectilinear) or [nframes][nnodes][3] (tets),
+ * [nframes][nz][ny][nx][dim] (rectilinear) or [nframes][nnodes][dim] (meshes),
  * in host memory or, if frames_on_device, device memory.  The library
  * converts to desc->storage (FP16/BF16 round to nearest).  The call checks
  * every value for finiteness on the device and synchronises the stream.
@@ -145,10 +149,11 @@ typedef struct {
     int periodic[3];
 } lcs_seed_desc;
 
-/* Generate the lattice on the device.  If `field` is a tet mesh, also locate
- * the tet holding each seed with exact orientation predicates: the lowest
- * tet id among the closed tets containing the seed, -1 if none (Sec. 2
- * "Seed": the cell of each seed on unstructured data).  field may be NULL.
+/* Generate the lattice on the device.  If `field` is a tet or triangle mesh,
+ * also locate the cell holding each seed with exact orientation predicates:
+ * the lowest cell id among the closed cells containing the seed, -1 if none
+ * (Sec. 2 "Seed": the cell of each seed on unstructured data).  field may be
+ * NULL.
  * Errors: LCS_EINVAL, LCS_ENOMEM, LCS_ECUDA.                                */
 lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *desc, const lcs_field *field,
                          lcs_seeds **out);
@@ -157,7 +162,7 @@ lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *desc, const lcs_fiel
 long long lcs_seeds_count(const lcs_seeds *seeds);
 
 /* Copy seed positions ([dim][N] FP32) and/or cell ids ([N] int32, -1 outside,
- * only for seeds made on a tet field) to host or device buffers (either may be
+ * only for seeds made on a mesh field) to host or device buffers (either may be
  * NULL).                                                                    */
 lcs_status lcs_seeds_get(lcs_ctx *ctx, const lcs_seeds *seeds, float *xyz, int *cells,
                          int on_device);
@@ -190,7 +195,8 @@ lcs_status lcs_seed_aux(lcs_ctx *ctx, const lcs_seeds *lattice, const double *de
  *            (32 consecutive seed ids): a step is accepted only when every
  *            live lane accepts (err <= 1, err = max_i |e_i| / (atol + rtol *
  *            max(|x_i|, |x_new_i|))), and the next step is the smallest lane
- *            proposal h * min(5, max(0.2, 0.9 err^-1/5)).
+ *            proposal h * min(5, max(0.2, 0.9 err^-1/5)).  On tets,
+ *            triangles and 3D rectilinear fields.
  *  LCS_SURROGATE  2D non-periodic rectilinear fields, one job, T = K tau > 0
  *            with tau the network's step and tau = S dt: per sub-interval k
  *            every tracer proposes x + displacement(x, t0 + k tau); in each
@@ -221,7 +227,8 @@ typedef struct {
     double dt;                  /* RK4 step magnitude                                 */
     double rtol, atol, h0;      /* RK45                                               */
     long long max_steps;        /* RK45 attempted-step cap per warp (0 = 10^6)        */
-    int walk_limit;             /* tet walk steps per point location (0 = 512)        */
+    int walk_limit;             /* mesh walk steps per point location (0 = 512); on
+                                   triangles the bin lists settle a walk that stops  */
     int block_threads;          /* 0 = library choice                                 */
     int variant;                /* 0 = library choice; 1 = cached gather;
                                    2 = shared-memory frame ring (2D rectilinear);
@@ -253,8 +260,8 @@ lcs_status lcs_flowmap_create(lcs_ctx *ctx, const lcs_seeds *seeds, int njobs, l
 /* Advect every seed through the field and write x(t0 + T) per job into fm,
  * with per-tracer status and exit time (a tracer leaving the domain is
  * frozen: rectilinear when more than one cell outside a non-periodic axis
- * after a step, at that step's end time; tets when a stage point falls
- * outside the mesh, at the start of that step).
+ * after a step, at that step's end time; tets and triangles when a stage
+ * point falls outside the mesh, at the start of that step).
  * Errors: LCS_EINVAL (options, a flow map with too few slots),
  * LCS_EUNSUPPORTED (e.g. snapshots with RK45, the surrogate or tets), LCS_ECUDA. */
 lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *seeds,

@@ -13,7 +13,7 @@
 // warp's lanes never diverge in time.  Tracers whose stage point leaves the mesh stop
 // (status LEFT, frozen at the start of that step) and stop voting.
 #include "rect_device.cuh"
-#include "tet_device.cuh"
+#include "tri_device.cuh"
 #include "dp45_args.cuh"
 
 #include <math.h>
@@ -70,6 +70,55 @@ __global__ void __launch_bounds__(256) rk4_tet_kernel(TetDev T, Rk4Args A, const
     A.out_texit[(size_t)job * A.N + i] = te;
 }
 
+// ------------------------------------------------------------- RK4 on triangles
+
+template <int ST>
+__global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const int *__restrict__ cells0)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int job = blockIdx.y;
+    if (i >= A.N) return;
+    float x[2] = {A.seeds[i], A.seeds[A.N + i]};
+    int cell = cells0[i];
+    unsigned char st = LCS_TRACER_OK;
+    float te = A.job_tend[job];
+    if (cell < 0) {
+        st = LCS_TRACER_OUTSIDE;
+        te = A.job_t0[job];
+    }
+    const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
+    const int ns = A.job_nsteps[job];
+    const float h = A.job_h[job], hh = 0.5f * h;
+    for (int n = 0; n < ns && st == LCS_TRACER_OK; ++n) {
+        const SchedEntry e[3] = {load_sched(sc + 3 * n), load_sched(sc + 3 * n + 1), load_sched(sc + 3 * n + 2)};
+        float k[4][2], y[2], lam[3];
+        int r = TET_INSIDE;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float c = s == 0 ? 0.0f : (s == 3 ? h : hh);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) y[q] = s == 0 ? x[q] : fmaf(c, k[s - 1][q], x[q]);
+            const SchedEntry &es = e[s == 0 ? 0 : (s == 3 ? 2 : 1)];
+            r = tri_locate(T, y, &cell, lam);
+            if (r != TET_INSIDE) break;
+            tri_interp<ST>(T, cell, lam, T.pairs + (size_t)es.k * T.fstride, es.a, k[s]);
+        }
+        if (r != TET_INSIDE) {  // a stage point left the mesh: freeze at the start of the step
+            st = LCS_TRACER_LEFT;
+            te = fmaf((float)n, h, A.job_t0[job]);
+            break;
+        }
+        const float h6 = h * (1.0f / 6.0f);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) x[q] = fmaf(h6, (k[0][q] + k[3][q]) + 2.0f * (k[1][q] + k[2][q]), x[q]);
+    }
+    float *o = A.out_xyz + (size_t)job * 2 * A.N;
+    o[i] = x[0];
+    o[A.N + i] = x[1];
+    A.out_status[(size_t)job * A.N + i] = st;
+    A.out_texit[(size_t)job * A.N + i] = te;
+}
+
 // ------------------------------------------------------- time bracket (FP32)
 
 // largest k with t_k <= t (after the periodic wrap), clamped to [0, nf-2]; the weight of
@@ -102,6 +151,7 @@ __device__ __forceinline__ void bracket_f32(const float *times, int nf, int tp, 
 // velocity at (x, t) on a tet mesh; walks from *cell.  Returns TET_INSIDE / OUTSIDE / WALKFAIL
 template <int ST>
 struct TetEval {
+    static constexpr int DIM = 3;
     TetDev T;
     __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u) const
     {
@@ -113,8 +163,23 @@ struct TetEval {
 };
 
 // velocity at (x, t) on a 3D rectilinear field of interval pairs (queries clamped into the box)
+// velocity at (x, t) on a triangle mesh; walks from *cell (the bin lists settle boundary edges)
+template <int ST>
+struct TriEval {
+    static constexpr int DIM = 2;
+    TriDev T;
+    __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u) const
+    {
+        float lam[3];
+        int r = tri_locate(T, x, cell, lam);
+        if (r == TET_INSIDE) tri_interp<ST>(T, *cell, lam, T.pairs + (size_t)k * T.fstride, a, u);
+        return r;
+    }
+};
+
 template <int ST>
 struct Rect3Eval {
+    static constexpr int DIM = 3;
     RectParams P;
     const char *pairs;
     size_t fstride;
@@ -168,7 +233,10 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
     const int job = blockIdx.y;
     const bool active = i < A.N;
     const unsigned FULL = 0xffffffffu;
-    float x[3] = {0.0f, 0.0f, 0.0f}, k1[3] = {0.0f, 0.0f, 0.0f};
+    constexpr int D = EV::DIM;
+    float x[D], k1[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) x[q] = k1[q] = 0.0f;
     int cell = 0, steps = 0;
     bool have_k1 = false;
     unsigned char st = active ? LCS_TRACER_OK : LCS_TRACER_OUTSIDE;
@@ -177,9 +245,8 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
     const float dir = A.job_T[job] < 0.0 ? -1.0f : 1.0f;
     float te = tend;
     if (active) {
-        x[0] = A.seeds[i];
-        x[1] = A.seeds[A.N + i];
-        x[2] = A.seeds[2 * A.N + i];
+#pragma unroll
+        for (int q = 0; q < D; ++q) x[q] = A.seeds[q * A.N + i];
         if (A.cells0) {
             cell = A.cells0[i];
             if (cell < 0) {
@@ -205,7 +272,7 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
         const bool last = dir * (t + h - tend) >= 0.0f;
         const float hs = last ? tend - t : h;
         ++attempts;
-        float err = 0.0f, xn[3], kk[7][3];
+        float err = 0.0f, xn[D], kk[7][D];
         int r = TET_INSIDE;
         if (live) {
             if (!have_k1) {
@@ -213,13 +280,13 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
                 if (r == TET_INSIDE) have_k1 = true;
             }
 #pragma unroll
-            for (int q = 0; q < 3; ++q) kk[0][q] = k1[q];
+            for (int q = 0; q < D; ++q) kk[0][q] = k1[q];
 #pragma unroll
             for (int s = 1; s < 7; ++s) {
                 if (r != TET_INSIDE) break;
-                float y[3];
+                float y[D];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
+                for (int q = 0; q < D; ++q) {
                     float acc = 0.0f;
 #pragma unroll
                     for (int j = 0; j < 6; ++j)
@@ -230,7 +297,7 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
             }
             if (r == TET_INSIDE) {
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
+                for (int q = 0; q < D; ++q) {
                     float acc = 0.0f, ea = 0.0f;
 #pragma unroll
                     for (int j = 0; j < 6; ++j) acc = fmaf(DPA[6][j], kk[j][q], acc);
@@ -257,12 +324,12 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
         if (all_ok) {
             if (live) {
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
+                for (int q = 0; q < D; ++q) {
                     x[q] = xn[q];
                     k1[q] = kk[6][q];
                 }
                 ++steps;
-                if (A.rect_left && rect_left<3>(P, x)) {
+                if (D == 3 && A.rect_left && rect_left<3>(P, x)) {
                     st = LCS_TRACER_LEFT;
                     te = last ? tend : t + hs;
                 }
@@ -272,10 +339,9 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
         if (pm != __float_as_uint(INFINITY)) h = dir * __uint_as_float(pm);
     }
     if (!active) return;
-    float *o = A.out_xyz + (size_t)job * 3 * A.N;
-    o[i] = x[0];
-    o[A.N + i] = x[1];
-    o[2 * A.N + i] = x[2];
+    float *o = A.out_xyz + (size_t)job * D * A.N;
+#pragma unroll
+    for (int q = 0; q < D; ++q) o[q * A.N + i] = x[q];
     A.out_status[(size_t)job * A.N + i] = st;
     A.out_texit[(size_t)job * A.N + i] = te;
     if (A.out_steps) A.out_steps[(size_t)job * A.N + i] = steps;
@@ -316,6 +382,18 @@ cudaError_t launch_rk4_tet(lcs_ctx *ctx, const Rk4Launch &L, const int *cells0, 
     if (L.N == 0) return cudaSuccess;
     const int bt = L.block_threads > 0 && L.block_threads <= 256 ? L.block_threads : 128;
     dim3 grid((unsigned)((L.N + bt - 1) / bt), (unsigned)L.njobs);
+    if (f->kind == LCS_TRI) {
+        const TriDev T = tri_dev(f, walk_limit);
+        lcs_tm_begin(ctx, 0, s);
+        if (f->storage == LCS_F32)
+            rk4_tri_kernel<LCS_F32><<<grid, bt, 0, s>>>(T, A, cells0);
+        else if (f->storage == LCS_F16)
+            rk4_tri_kernel<LCS_F16><<<grid, bt, 0, s>>>(T, A, cells0);
+        else
+            rk4_tri_kernel<LCS_BF16><<<grid, bt, 0, s>>>(T, A, cells0);
+        lcs_tm_end(ctx, 0, s);
+        return cudaGetLastError();
+    }
     const TetDev T = tet_dev(f, walk_limit);
     lcs_tm_begin(ctx, 0, s);
     if (f->storage == LCS_F32)
@@ -356,7 +434,16 @@ cudaError_t launch_dp45(lcs_ctx *ctx, const lcs_field *f, const Dp45Args &A0, in
     cudaError_t e;
     lcs_tm_begin(ctx, 0, s);
     RectParams P = make_rect_params(f);
-    if (f->kind == LCS_TET) {
+    if (f->kind == LCS_TRI) {
+        A.rect_left = 0;
+        const TriDev T = tri_dev(f, walk_limit);
+        if (f->storage == LCS_F32)
+            e = dp45_go(TriEval<LCS_F32>{T}, A, P, njobs, bt, s);
+        else if (f->storage == LCS_F16)
+            e = dp45_go(TriEval<LCS_F16>{T}, A, P, njobs, bt, s);
+        else
+            e = dp45_go(TriEval<LCS_BF16>{T}, A, P, njobs, bt, s);
+    } else if (f->kind == LCS_TET) {
         A.rect_left = 0;
         const TetDev T = tet_dev(f, walk_limit);
         if (f->storage == LCS_F32)

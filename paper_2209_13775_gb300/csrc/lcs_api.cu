@@ -222,7 +222,8 @@ __device__ __forceinline__ __half to_store<__half>(float v) { return __float2hal
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 
-// 2D: slab f = frame f, node v = (u, v).  3D: slab k = interval pair (k, k+1), node v =
+// 2D rectilinear: slab f = frame f, node v = (u, v).  Triangles: slab k = interval pair
+// (k, k+1), node v = (u_k, v_k, u_{k+1}, v_{k+1}).  3D: slab k = interval pair, node v =
 // (u_k, 0, u_{k+1}, 0) so that one load brings both frames of a node (a single frame is
 // paired with itself).
 template <typename T>
@@ -233,10 +234,17 @@ __global__ void convert_rect_kernel(const float *__restrict__ src, int nframes, 
     if (idx >= (long long)nslabs * nodes) return;
     long long f = idx / nodes, v = idx % nodes;
     T *o = reinterpret_cast<T *>(dst + (size_t)f * slab_stride) + v * vec;
-    if (dim == 2) {
+    if (dim == 2 && vec == 2) {
         const float *s = src + idx * 2;
         o[0] = to_store<T>(s[0]);
         o[1] = to_store<T>(s[1]);
+    } else if (dim == 2) {  // triangle meshes: (u_k, v_k, u_{k+1}, v_{k+1}) per node
+        long long f1 = f + 1 < nframes ? f + 1 : f;
+        const float *a = src + (f * nodes + v) * 2, *b = src + (f1 * nodes + v) * 2;
+        o[0] = to_store<T>(a[0]);
+        o[1] = to_store<T>(a[1]);
+        o[2] = to_store<T>(b[0]);
+        o[3] = to_store<T>(b[1]);
     } else {
         long long f1 = f + 1 < nframes ? f + 1 : f;
         const float *a = src + (f * nodes + v) * 3, *b = src + (f1 * nodes + v) * 3;
@@ -311,14 +319,18 @@ static lcs_status upload_frames(lcs_ctx *ctx, lcs_field *f, const float *frames,
     return LCS_OK;
 }
 
-// Tetrahedral mesh (Sec. 3.1): frames as interval pairs per node, plus the mesh store.
+// Tetrahedral (Sec. 3.1) or triangle (2D) mesh: frames as interval pairs per node, plus the
+// mesh store.
 static lcs_status load_tet_field(lcs_ctx *ctx, const lcs_field_desc *d, const float *frames, int frames_on_device,
                                  lcs_field **out)
 {
-    if (d->dim != 3) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: tet meshes are 3D");
+    const bool tri = d->kind == LCS_TRI;
+    const int dim = tri ? 2 : 3, nv = dim + 1;
+    if (d->dim != dim)
+        return lcs_fail(ctx, LCS_EINVAL, tri ? "lcs_load_field: triangle meshes are 2D" : "lcs_load_field: tet meshes are 3D");
     if (d->storage < LCS_F32 || d->storage > LCS_BF16) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: storage");
-    if (d->nnodes < 4 || d->ncells < 1 || !d->node_xyz || !d->tets)
-        return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: a tet mesh needs nnodes >= 4, ncells >= 1, node_xyz, tets");
+    if (d->nnodes < nv || d->ncells < 1 || !d->node_xyz || !d->tets)
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: a mesh needs nnodes >= %d, ncells >= 1, node_xyz, cells", nv);
     if (d->nnodes >= (1LL << 31) || d->ncells >= (1LL << 31))
         return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: more than 2^31 nodes or tets");
     if (d->nframes < 1 || !d->frame_times) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: need >= 1 frame");
@@ -326,21 +338,21 @@ static lcs_status load_tet_field(lcs_ctx *ctx, const lcs_field_desc *d, const fl
         if (!(d->frame_times[k] > d->frame_times[k - 1]))
             return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: frame_times must increase");
     if (d->time_periodic && !(d->period > 0.0)) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: period must be > 0");
-    for (long long q = 0; q < 4 * d->ncells; ++q) {
+    for (long long q = 0; q < nv * d->ncells; ++q) {
         if (d->tets[q] < 0 || d->tets[q] >= d->nnodes)
-            return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: tet %lld names node %d", q / 4, d->tets[q]);
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: cell %lld names node %d", q / nv, d->tets[q]);
         if (d->nbrs && (d->nbrs[q] < -1 || d->nbrs[q] >= d->ncells))
-            return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: tet %lld has neighbour %d", q / 4, d->nbrs[q]);
+            return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: cell %lld has neighbour %d", q / nv, d->nbrs[q]);
     }
-    for (long long q = 0; q < 3 * d->nnodes; ++q)
+    for (long long q = 0; q < (long long)dim * d->nnodes; ++q)
         if (!isfinite(d->node_xyz[q])) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: non-finite node coordinate");
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     lcs_field *f = new (std::nothrow) lcs_field();
     if (!f) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
     f->ctx = ctx;
     f->uid = lcs_next_uid();
-    f->dim = 3;
-    f->kind = LCS_TET;
+    f->dim = dim;
+    f->kind = d->kind;
     f->storage = d->storage;
     f->nframes = d->nframes;
     f->times.assign(d->frame_times, d->frame_times + d->nframes);
@@ -348,7 +360,7 @@ static lcs_status load_tet_field(lcs_ctx *ctx, const lcs_field_desc *d, const fl
     f->period = d->period;
     f->nodes = d->nnodes;
     f->ncells = d->ncells;
-    f->vec = 8;
+    f->vec = tri ? 4 : 8;
     f->nslabs = f->nframes > 1 ? f->nframes - 1 : 1;
     f->elem_bytes = d->storage == LCS_F32 ? 4 : 2;
     f->frame_bytes = (size_t)f->nodes * f->vec * f->elem_bytes;
@@ -358,7 +370,9 @@ static lcs_status load_tet_field(lcs_ctx *ctx, const lcs_field_desc *d, const fl
     if (e == cudaSuccess) e = cudaMalloc(&f->d_times, sizeof(double) * f->nframes);
     if (e == cudaSuccess)
         e = cudaMemcpy(f->d_times, f->times.data(), sizeof(double) * f->nframes, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = tet_build_store(f, d->node_xyz, d->tets, d->nbrs, ctx->stream);
+    if (e == cudaSuccess)
+        e = tri ? tri_build_store(f, d->node_xyz, d->tets, d->nbrs, ctx->stream)
+                : tet_build_store(f, d->node_xyz, d->tets, d->nbrs, ctx->stream);
     if (e != cudaSuccess)
         st = lcs_fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_load_field: %s",
                   cudaGetErrorString(e));
@@ -378,7 +392,7 @@ extern "C" lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *d, cons
     if (!ctx) return LCS_EINVAL;
     if (!d || !frames || !out) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: null argument");
     *out = nullptr;
-    if (d->kind == LCS_TET) return load_tet_field(ctx, d, frames, frames_on_device, out);
+    if (d->kind == LCS_TET || d->kind == LCS_TRI) return load_tet_field(ctx, d, frames, frames_on_device, out);
     if (d->kind != LCS_RECTILINEAR) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: unknown kind %d", d->kind);
     if (d->dim != 2 && d->dim != 3) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: dim must be 2 or 3");
     if (d->storage < LCS_F32 || d->storage > LCS_BF16) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: storage");
@@ -458,6 +472,11 @@ extern "C" void lcs_free_field(lcs_field *f)
     cudaFree(f->d_nbrs);
     cudaFree(f->d_tetmap);
     cudaFree(f->d_bins);
+    cudaFree(f->d_xy);
+    cudaFree(f->d_trimap);
+    cudaFree(f->d_triv0);
+    cudaFree(f->d_bstart);
+    cudaFree(f->d_blist);
     delete f;
 }
 
@@ -561,7 +580,7 @@ extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const 
     *out = nullptr;
     if (d->dim != 2 && d->dim != 3) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_grid: dim must be 2 or 3");
     if (field && field->dim != d->dim) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_grid: dim differs from the field's");
-    if (field && field->kind == LCS_TET && d->dim != 3) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_grid: tets are 3D");
+
     long long N = 1;
     for (int a = 0; a < d->dim; ++a) {
         if (d->n[a] < 1) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_grid: n[%d] < 1", a);
@@ -589,10 +608,12 @@ extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const 
     }
     cudaError_t e = cudaMalloc(&s->d_xyz, sizeof(float) * s->dim * (size_t)N);
     if (e == cudaSuccess) e = launch_seed_grid(s->dim, s->n, s->lo, s->hi, s->periodic, N, s->d_xyz, ctx->stream);
-    if (e == cudaSuccess && field && field->kind == LCS_TET) {
+    if (e == cudaSuccess && field && lcs_is_mesh(field)) {
         s->field_uid = field->uid;
         e = cudaMalloc(&s->d_cells, sizeof(int) * (size_t)N);
-        if (e == cudaSuccess) e = tet_locate_seeds(field, s->d_xyz, N, 1 << 16, s->d_cells, ctx->stream);
+        if (e == cudaSuccess)
+            e = field->kind == LCS_TRI ? tri_locate_seeds(field, s->d_xyz, N, s->d_cells, ctx->stream)
+                                       : tet_locate_seeds(field, s->d_xyz, N, 1 << 16, s->d_cells, ctx->stream);
     }
     if (e != cudaSuccess) {
         lcs_free_seeds(s);
@@ -766,7 +787,7 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.host_snap_n = J.snap_n;
     L.snap_te = D.snap_te;
     L.work = want_work ? (char *)ctx->d_scratch + jb + sb : nullptr;
-    if (f->kind == LCS_TET) {
+    if (lcs_is_mesh(f)) {
         cudaError_t e = launch_rk4_tet(ctx, L, s->d_cells, o->walk_limit, ctx->stream);
         if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(e));
         return LCS_OK;
@@ -780,7 +801,8 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
 static lcs_status advect_rk45(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
                               lcs_flowmap *fm)
 {
-    if (f->dim != 3) return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: RK45 on 2D fields not built in");
+    if (f->dim != 3 && f->kind != LCS_TRI)
+        return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: RK45 on 2D rectilinear fields not built in");
     const int njobs = o->njobs > 1 ? o->njobs : 1;
     const double rtol = o->rtol > 0 ? o->rtol : 1e-6, atol = o->atol > 0 ? o->atol : 1e-6;
     const double h0 = o->h0 != 0 ? fabs(o->h0) : 0.01;
@@ -836,7 +858,7 @@ static lcs_status advect_rk45(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds 
     Dp45Args A;
     memset(&A, 0, sizeof A);
     A.seeds = s->d_xyz;
-    A.cells0 = f->kind == LCS_TET ? s->d_cells : nullptr;
+    A.cells0 = lcs_is_mesh(f) ? s->d_cells : nullptr;
     A.N = s->N;
     A.job_t0 = D.t0d;
     A.job_T = D.Td;
@@ -1007,8 +1029,8 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
     if (o->method != LCS_RK4 && o->method != LCS_RK45 && o->method != LCS_SURROGATE)
         return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: method %d not built in", o->method);
     if (o->method == LCS_SURROGATE) return advect_surrogate(ctx, f, s, o, fm);
-    if (f->kind == LCS_TET && (!s->d_cells || s->field_uid != f->uid))
-        return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: on a tet field the seeds must come from lcs_seed_grid on that field");
+    if (lcs_is_mesh(f) && (!s->d_cells || s->field_uid != f->uid))
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: on a mesh field the seeds must come from lcs_seed_grid on that field");
     if (o->method == LCS_RK45) return advect_rk45(ctx, f, s, o, fm);
     JobTable *J = new (std::nothrow) JobTable();
     if (!J) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");

@@ -1,0 +1,181 @@
+// tri_device.cuh -- device building blocks for velocity data on triangle meshes (2D
+// unstructured data such as the stenosis geometries of Sec. 4; Sec. 3.1: the local cell
+// search of tetrahedral grids, triangles in 2D).
+//
+//  * tri_locate: the hot loop's local walk on FP32 barycentric coordinates from a per-
+//    triangle inverse affine map (stop when no coordinate is below -tol, else cross the
+//    edge of the most negative one).  A walk that meets a boundary edge, or its step limit,
+//    is settled by the triangles listed for the point's bin, so meshes need not be convex
+//    (a channel with a constriction is not).
+//  * tri_interp: P1 interpolation of the frame pair k, blended in time at the vertices.
+//  * orient2d_sign: exact orientation of three FP32 points (FP64 filter, exact expansion
+//    sum of the six two-factor products when the filter cannot decide).
+#pragma once
+
+#include "tet_device.cuh"
+
+struct TriDev {
+    const float2 *xy;     // [nnodes]
+    const int4 *tris;     // [ncells] (a, b, c, 0)
+    const int4 *nbrs;     // [ncells] (across the edge opposite vertex 0, 1, 2; -1 boundary)
+    const float4 *tmap;   // [ncells] (M00, M01, M10, M11): lambda_{r+1} = M_r . (x - v0)
+    const float2 *tv0;    // [ncells] vertex 0
+    const int *bstart;    // [nbins + 1] CSR of the triangles whose bounding box meets a bin
+    const int *blist;     //   (ids increasing within a bin)
+    float blo[2], binv[2];
+    int bn[2];
+    const char *pairs;    // [nslabs][nnodes] (u_k, v_k, u_{k+1}, v_{k+1}) in storage precision
+    size_t fstride;
+    long long ncells;
+    int walk_limit;
+    float tol;
+};
+
+TriDev tri_dev(const lcs_field *f, int walk_limit);  // tri_store.cu
+
+// bin of a point: floor((x - lo) * inv) clamped to the grid (monotone in x, so a triangle's
+// bounding-box bins always include the bin of every point it holds)
+__device__ __forceinline__ int tri_bin_axis(float x, float lo, float inv, int n)
+{
+    const float s = (x - lo) * inv;
+    const int v = isfinite(s) ? (int)fminf(fmaxf(floorf(s), 0.0f), (float)(n - 1)) : 0;
+    return v;
+}
+
+__device__ __forceinline__ void tri_bary(const TriDev &T, int c, const float *x, float *lam)
+{
+    const float4 m = __ldg(T.tmap + c);
+    const float2 v = __ldg(T.tv0 + c);
+    const float dx = x[0] - v.x, dy = x[1] - v.y;
+    lam[1] = fmaf(m.x, dx, m.y * dy);
+    lam[2] = fmaf(m.z, dx, m.w * dy);
+    lam[0] = 1.0f - lam[1] - lam[2];
+}
+
+// the triangles listed for x's bin, in id order: the first whose coordinates all reach -tol
+__device__ __forceinline__ int tri_bin_scan(const TriDev &T, const float *x, int *cell, float *lam)
+{
+    if (!(isfinite(x[0]) && isfinite(x[1]))) return TET_OUTSIDE;
+    const int b = tri_bin_axis(x[0], T.blo[0], T.binv[0], T.bn[0]) +
+                  T.bn[0] * tri_bin_axis(x[1], T.blo[1], T.binv[1], T.bn[1]);
+    const int q1 = __ldg(T.bstart + b + 1);
+    for (int q = __ldg(T.bstart + b); q < q1; ++q) {
+        const int c = __ldg(T.blist + q);
+        tri_bary(T, c, x, lam);
+        if (fminf(lam[0], fminf(lam[1], lam[2])) >= -T.tol) {
+            *cell = c;
+            return TET_INSIDE;
+        }
+    }
+    return TET_OUTSIDE;
+}
+
+__device__ __forceinline__ int tri_locate(const TriDev &T, const float *x, int *cell, float *lam)
+{
+    int c = *cell;
+    if (c < 0 || c >= T.ncells) c = 0;
+    for (int it = 0; it < T.walk_limit; ++it) {
+        tri_bary(T, c, x, lam);
+        int jm = 0;
+        float lm = lam[0];
+        if (lam[1] < lm) {
+            lm = lam[1];
+            jm = 1;
+        }
+        if (lam[2] < lm) {
+            lm = lam[2];
+            jm = 2;
+        }
+        if (lm >= -T.tol) {
+            *cell = c;
+            return TET_INSIDE;
+        }
+        const int4 nb = __ldg(T.nbrs + c);
+        const int n = jm == 0 ? nb.x : jm == 1 ? nb.y : nb.z;
+        if (n < 0) break;
+        c = n;
+    }
+    return tri_bin_scan(T, x, cell, lam);
+}
+
+template <int ST>
+struct TriPair;
+
+template <>
+struct TriPair<LCS_F32> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *ua, float *ub)
+    {
+        const float4 r = __ldg(reinterpret_cast<const float4 *>(f) + v);
+        ua[0] = r.x;
+        ua[1] = r.y;
+        ub[0] = r.z;
+        ub[1] = r.w;
+    }
+};
+
+template <>
+struct TriPair<LCS_F16> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *ua, float *ub)
+    {
+        const uint2 r = __ldg(reinterpret_cast<const uint2 *>(f) + v);
+        const float2 a = tet_h2f(r.x), b = tet_h2f(r.y);
+        ua[0] = a.x;
+        ua[1] = a.y;
+        ub[0] = b.x;
+        ub[1] = b.y;
+    }
+};
+
+template <>
+struct TriPair<LCS_BF16> {
+    static __device__ __forceinline__ void ld(const char *f, int v, float *ua, float *ub)
+    {
+        const uint2 r = __ldg(reinterpret_cast<const uint2 *>(f) + v);
+        const float2 a = tet_b2f(r.x), b = tet_b2f(r.y);
+        ua[0] = a.x;
+        ua[1] = a.y;
+        ub[0] = b.x;
+        ub[1] = b.y;
+    }
+};
+
+// u = sum_i lam_i [(1 - a) u_k + a u_{k+1}](vertex i) from the interval pair at fp
+template <int ST>
+__device__ __forceinline__ void tri_interp(const TriDev &T, int c, const float *lam, const char *fp, float a, float *u)
+{
+    const int4 t = __ldg(T.tris + c);
+    const int vs[3] = {t.x, t.y, t.z};
+    const float g = 1.0f - a;
+    float acc[2] = {0.0f, 0.0f}, va[2], vb[2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        TriPair<ST>::ld(fp, vs[i], va, vb);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[q] = fmaf(lam[i], a == 0.0f ? va[q] : fmaf(a, vb[q], g * va[q]), acc[q]);
+    }
+    u[0] = acc[0];
+    u[1] = acc[1];
+}
+
+// sign of (b - a) x (c - a) for FP32 points, exactly
+static __device__ __noinline__ int orient2d_sign(const float *a, const float *b, const float *c)
+{
+    // filter: FP64 on differences (each difference of FP32 values is exact unless their
+    // exponents are far apart; the bound covers the rounding of both products and the sum)
+    const double ux = (double)b[0] - a[0], uy = (double)b[1] - a[1];
+    const double vx = (double)c[0] - a[0], vy = (double)c[1] - a[1];
+    const double det = ux * vy - uy * vx;
+    const double perm = fabs(ux * vy) + fabs(uy * vx);
+    if (fabs(det) > 1e-14 * perm) return det > 0.0 ? 1 : -1;
+    // exact: bx cy - by cx - ax cy + ay cx + ax by - ay bx, each product exact in FP64
+    const double terms[6] = {__dmul_rn(b[0], c[1]), -__dmul_rn(b[1], c[0]), -__dmul_rn(a[0], c[1]),
+                             __dmul_rn(a[1], c[0]),  __dmul_rn(a[0], b[1]), -__dmul_rn(a[1], b[0])};
+    double h[8];
+    int n = 0;
+    for (int i = 0; i < 6; ++i) n = e_grow(h, n, terms[i]);
+    for (int i = n - 1; i >= 0; --i) {
+        if (h[i] > 0.0) return 1;
+        if (h[i] < 0.0) return -1;
+    }
+    return 0;
+}

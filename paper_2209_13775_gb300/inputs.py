@@ -210,18 +210,17 @@ def tri_neighbours(tris):
     """Triangle across the edge opposite vertex j of each triangle (-1 on the boundary)."""
     tris = np.asarray(tris, dtype=np.int64)
     nc = tris.shape[0]
-    nbrs = np.full((nc, 3), -1, dtype=np.int32)
-    seen = {}
-    for t in range(nc):
-        for j in range(3):
-            a, b = sorted((int(tris[t, (j + 1) % 3]), int(tris[t, (j + 2) % 3])))
-            other = seen.pop((a, b), None)
-            if other is None:
-                seen[(a, b)] = (t, j)
-            else:
-                nbrs[t, j] = other[0]
-                nbrs[other[0], other[1]] = t
-    return nbrs
+    u = np.stack([tris[:, 1], tris[:, 2], tris[:, 0]], axis=1).ravel()   # edge j: vertices j+1, j+2
+    v = np.stack([tris[:, 2], tris[:, 0], tris[:, 1]], axis=1).ravel()
+    key = np.minimum(u, v) * (int(tris.max()) + 1) + np.maximum(u, v)
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    nbrs = np.full(nc * 3, -1, dtype=np.int64)
+    pair = np.nonzero(ks[1:] == ks[:-1])[0]          # an interior edge appears exactly twice
+    a, b = order[pair], order[pair + 1]
+    nbrs[a] = b // 3
+    nbrs[b] = a // 3
+    return nbrs.reshape(nc, 3).astype(np.int32)
 
 
 def stenosis_halfwidth(x, H=1.0, depth=0.5, xc=3.0, w=0.75):

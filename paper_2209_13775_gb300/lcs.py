@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-RECTILINEAR, TET = 0, 1
+RECTILINEAR, TET, TRI = 0, 1, 2
 F32, F16, BF16 = 0, 1, 2
 RK4, RK45, SURROGATE = 0, 1, 2
 TRACER_OK, TRACER_LEFT, TRACER_OUTSIDE, TRACER_MAXSTEPS, TRACER_WALKFAIL = 0, 1, 2, 3, 4

@@ -139,3 +139,17 @@ def round_bf16(a):
 
 def round_fp16(a):
     return np.asarray(a, dtype=np.float32).astype(np.float16).astype(np.float32)
+
+
+def check_exit_statuses(st_g, te_g, st_o, te_o, dt, frac=2e-3):
+    """Mesh fields: statuses agree except where an exit was decided one step apart (stage points
+    within rounding of a boundary face or edge); returns the seeds where both are OK or both left
+    at the same step."""
+    diff = st_g != st_o
+    assert diff.mean() <= frac, diff.sum()
+    assert set(np.unique(st_g[diff])) <= {lcs.TRACER_OK, lcs.TRACER_LEFT}
+    dte = np.abs(te_g.astype(np.float64) - te_o)
+    assert (dte[diff] <= dt * (1 + 1e-4)).all(), dte[diff].max()
+    same = ~diff & (dte <= 1e-4 * dt)
+    assert ((~diff) & ~same).sum() <= frac * len(st_g)
+    return same

@@ -23,7 +23,7 @@ from scipy.linalg import expm
 import oracle
 from meshes import kuhn_mesh
 from paper_2209_13775_gb300 import inputs, lcs
-from gpu_util import round_bf16, round_fp16
+from gpu_util import check_exit_statuses, round_bf16, round_fp16
 
 pytestmark = pytest.mark.gpu
 
@@ -156,19 +156,6 @@ def _pipe_oracle(pipe, frames, n, lo, hi, t0, T, dt):
     x0 = ora_seeds(n, lo, hi)
     cells = F.locate_seeds(x0)
     return F, x0, cells, oracle.rk4(F, x0.astype(np.float64), t0, T, dt, cells=cells)
-
-
-def check_exit_statuses(st_g, te_g, st_o, te_o, dt, frac=2e-3):
-    """Statuses agree except where an exit was decided one step apart (stage points within
-    rounding of a boundary face); returns the seeds where both are OK or both left at the same step."""
-    diff = st_g != st_o
-    assert diff.mean() <= frac, diff.sum()
-    assert set(np.unique(st_g[diff])) <= {lcs.TRACER_OK, lcs.TRACER_LEFT}
-    dte = np.abs(te_g.astype(np.float64) - te_o)
-    assert (dte[diff] <= dt * (1 + 1e-4)).all(), dte[diff].max()
-    same = ~diff & (dte <= 1e-4 * dt)
-    assert ((~diff) & ~same).sum() <= frac * len(st_g)
-    return same
 
 
 @pytest.mark.parametrize("storage", [lcs.F32, lcs.F16, lcs.BF16])

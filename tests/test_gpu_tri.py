@@ -1,0 +1,290 @@
+"""GPU parity of the triangle-mesh path (2D unstructured data such as the stenosis geometries of
+Sec. 4; the Sec. 3.1 cell search one dimension lower) through the C ABI against the FP64 oracle.
+
+* Seed cells (Sec. 2 "Seed" on unstructured data): the lowest-id closed triangle holding each FP32
+  seed, -1 outside, decided on both sides with exact orientation predicates, so the comparison is
+  bit-exact -- on a grid triangulation with mixed orientations whose seeds sit on vertices and
+  edges (ties) and on the non-convex stenosis mesh.
+* Fixed-step RK4 (P1 interpolation, a walk per stage point, the bin lists where the walk meets a
+  boundary edge): closed form on affine fields, a uniform stream's leaving time, and the stenosis
+  flow against the oracle with the tet path's tolerances (statuses may differ only where an exit
+  was decided one step apart).
+* DP5(4) with one step size per warp: the closed-form flow of an affine field and the oracle's
+  32-lane mode on the stenosis.
+* The FTLE of a triangle-mesh flow map against the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+from scipy.linalg import expm
+
+import oracle
+from meshes import tri_grid_mesh
+from paper_2209_13775_gb300 import inputs, lcs
+from gpu_util import check_exit_statuses, check_ftle, round_bf16, round_fp16
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    c = lcs.lcs_create(0, torch.cuda.current_stream())
+    yield c
+    lcs.lcs_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def sten():
+    m = inputs.stenosis_mesh(h=0.05, L=10.0)
+    return inputs.stenosis_frames(m, nframes=40, period=1.0)
+
+
+def tri_desc(xy, tris, nbrs, times, storage=lcs.F32, time_periodic=False, period=0.0):
+    return lcs.field_desc(2, times=times, time_periodic=time_periodic, period=period, storage=storage,
+                          kind=lcs.TRI, mesh=(xy, tris, nbrs))
+
+
+def sten_desc(m, storage=lcs.F32, nbrs="mesh"):
+    return tri_desc(m.xyz, m.tets, m.nbrs if nbrs == "mesh" else nbrs, m.times, storage, True, m.period)
+
+
+def gpu_tri(ctx, desc, frames, n, lo, hi, opts, want_steps=False, want_ftle=False):
+    """Load a triangle field, seed a lattice on it, advect; host arrays per job."""
+    field = lcs.lcs_load_field(ctx, desc, frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, lo, hi), field)
+    N = lcs.lcs_seeds_count(seeds)
+    out = {"seeds": np.empty((2, N), dtype=np.float32), "cells": np.empty(N, dtype=np.int32)}
+    lcs.lcs_seeds_get(ctx, seeds, out["seeds"], out["cells"])
+    if opts is not None:
+        njobs = max(1, opts.njobs)
+        fm = lcs.lcs_flowmap_create(ctx, seeds, njobs)
+        lcs.lcs_advect(ctx, field, seeds, opts, fm)
+        for k in ("xyz", "status", "t_exit", "steps", "ftle"):
+            out[k] = []
+        for j in range(njobs):
+            x = np.empty((2, N), dtype=np.float32)
+            s = np.empty(N, dtype=np.uint8)
+            te = np.empty(N, dtype=np.float32)
+            lcs.lcs_flowmap_get(ctx, fm, j, x, s, te)
+            out["xyz"].append(x)
+            out["status"].append(s)
+            out["t_exit"].append(te)
+            if want_steps:
+                ns = np.empty(N, dtype=np.int32)
+                lcs.lcs_flowmap_steps(ctx, fm, j, ns)
+                out["steps"].append(ns)
+            if want_ftle:
+                f = np.empty(N, dtype=np.float32)
+                lcs.lcs_ftle(ctx, fm, j, f)
+                out["ftle"].append(f)
+        lcs.lcs_free_flowmap(fm)
+    lcs.lcs_synchronize(ctx)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return out
+
+
+def ora_seeds(n, lo, hi):
+    return oracle.seed_grid(2, n, lo, hi)
+
+
+# ------------------------------------------------------------------ seed cells
+
+def test_seed_cells_on_grid_mesh_with_ties(ctx):
+    # lattice step 1/4 on integer nodes: many seeds lie on a vertex or an edge shared by several
+    # triangles; the lattice also reaches a cell outside the mesh on every side
+    pts, tris, nbrs = tri_grid_mesh(6)
+    F = oracle.TriField(pts, tris, nbrs, np.zeros((1, len(pts), 2), np.float32), [0.0])
+    n, lo, hi = (33, 33), (-1.0, -1.0), (7.0, 7.0)
+    g = gpu_tri(ctx, tri_desc(pts, tris, nbrs, [0.0]), np.zeros((1, len(pts), 2), np.float32), n, lo, hi, None)
+    x0 = ora_seeds(n, lo, hi)
+    np.testing.assert_array_equal(g["seeds"], x0)
+    want = F.locate_seeds(x0)
+    np.testing.assert_array_equal(g["cells"], want)
+    ties = sum(len([t for t in range(len(tris)) if F.contains(t, x0[:, i])[0]]) > 1
+               for i in range(x0.shape[1]) if want[i] >= 0)
+    assert ties > 200 and (want < 0).sum() > 300 and (want >= 0).sum() > 500
+
+
+def test_seed_cells_on_stenosis_mesh(ctx, sten):
+    # the channel narrows to half its width: seeds beside the constriction are outside a non-convex mesh
+    n, lo, hi = (201, 41), (0.0, -1.0), (10.0, 1.0)
+    F = oracle.TriField(sten.xyz, sten.tets, sten.nbrs, sten.frames[:1], [0.0])
+    x0 = ora_seeds(n, lo, hi)
+    want = F.locate_seeds(x0)
+    for nbrs in ("mesh", None):   # None: the library builds the edge neighbours itself
+        g = gpu_tri(ctx, sten_desc(sten, nbrs=nbrs), sten.frames, n, lo, hi, None)
+        np.testing.assert_array_equal(g["cells"], want)
+    assert (want < 0).sum() > 300 and (want >= 0).sum() > 5000
+
+
+# ------------------------------------------------------------------ RK4 on triangles
+
+def test_rk4_tri_affine_rotation_closed_form(ctx):
+    pts, tris, nbrs = tri_grid_mesh(4)
+    pts = pts - np.float32(2.0)                       # box [-2, 2]^2
+    A = np.array([[0.0, -0.5], [0.5, 0.0]])
+    fr = np.stack([pts @ A.T, pts @ A.T]).astype(np.float32)
+    n, lo, hi = (17, 15), (-1.0, -1.1), (1.0, 1.1)
+    g = gpu_tri(ctx, tri_desc(pts, tris, nbrs, [0.0, 10.0]), fr, n, lo, hi,
+                lcs.advect_opts(lcs.RK4, t0=0.0, T=2.0, dt=0.1))
+    x0 = ora_seeds(n, lo, hi).astype(np.float64)
+    Z = 0.1 * A
+    R = np.eye(2) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+    assert (g["status"][0] == lcs.TRACER_OK).all()
+    err = np.abs(g["xyz"][0] - np.linalg.matrix_power(R, 20) @ x0).max()
+    assert err <= 4e-6, err
+
+
+def test_rk4_tri_uniform_stream_leaves(ctx):
+    # u = (1, 0) on [-2, 2]^2: frozen at the start of the first step with a stage point past x = 2,
+    # t_e = dt floor((2 - x0) / dt) (the lattice keeps (2 - x0) / dt 0.3 away from an integer)
+    pts, tris, nbrs = tri_grid_mesh(4)
+    pts = pts - np.float32(2.0)
+    fr = np.zeros((2, len(pts), 2), np.float32)
+    fr[..., 0] = 1.0
+    n, lo, hi = (9, 5), (-1.73, -1.5), (1.47, 1.5)
+    g = gpu_tri(ctx, tri_desc(pts, tris, nbrs, [0.0, 10.0]), fr, n, lo, hi,
+                lcs.advect_opts(lcs.RK4, t0=0.0, T=5.0, dt=0.1))
+    x0 = ora_seeds(n, lo, hi).astype(np.float64)
+    te_want = 0.1 * np.floor((2.0 - x0[0]) / 0.1)
+    assert (g["status"][0] == lcs.TRACER_LEFT).all()
+    np.testing.assert_allclose(g["t_exit"][0], te_want, rtol=0, atol=2e-6)
+    np.testing.assert_allclose(g["xyz"][0][0], x0[0] + te_want, rtol=0, atol=4e-6)
+    np.testing.assert_array_equal(g["xyz"][0][1], x0[1].astype(np.float32))
+
+
+def _sten_oracle(m, frames, n, lo, hi, t0, T, dt):
+    F = oracle.TriField(m.xyz, m.tets, m.nbrs, frames, m.times, True, m.period)
+    x0 = ora_seeds(n, lo, hi)
+    cells = F.locate_seeds(x0)
+    return F, x0, cells, oracle.rk4(F, x0.astype(np.float64), t0, T, dt, cells=cells)
+
+
+@pytest.mark.parametrize("storage", [lcs.F32, lcs.F16, lcs.BF16])
+def test_rk4_tri_stenosis_matches_oracle(ctx, sten, storage):
+    # seeds over the whole box (some outside the constriction); the jet carries many out at x = 10
+    n, lo, hi = (120, 40), (0.02, -0.98), (9.98, 0.98)
+    frames = sten.frames
+    if storage == lcs.F16:
+        frames = round_fp16(frames)
+    elif storage == lcs.BF16:
+        frames = round_bf16(frames)
+    t0, T, dt = 0.3, 1.0, 0.01
+    g = gpu_tri(ctx, sten_desc(sten, storage), sten.frames, n, lo, hi, lcs.advect_opts(lcs.RK4, t0=t0, T=T, dt=dt))
+    F, x0, cells, (xT, st, te) = _sten_oracle(sten, frames, n, lo, hi, t0, T, dt)
+    np.testing.assert_array_equal(g["cells"], cells)
+    assert (st == oracle.LEFT).sum() > 150 and (st == oracle.OK).sum() > 3000 and (st == oracle.OUTSIDE).sum() > 100
+    same = check_exit_statuses(g["status"][0], g["t_exit"][0], st, te, dt)
+    err = np.abs(g["xyz"][0][:, same].astype(np.float64) - xT[:, same]).max()
+    assert err <= 2e-5, err
+
+
+def test_rk4_tri_backward_batched_and_ftle(ctx, sten):
+    # two jobs (one backward, out through the inlet) in one launch equal single-job launches bit for
+    # bit; the FTLE of the lattice flow map against the oracle's
+    n, lo, hi = (100, 33), (0.05, -0.96), (9.95, 0.96)
+    desc = sten_desc(sten)
+    both = gpu_tri(ctx, desc, sten.frames, n, lo, hi,
+                   lcs.advect_opts(lcs.RK4, dt=0.02, job_t0=[0.1, 0.9], job_T=[0.6, -0.8]), want_ftle=True)
+    one = gpu_tri(ctx, desc, sten.frames, n, lo, hi, lcs.advect_opts(lcs.RK4, t0=0.9, T=-0.8, dt=0.02))
+    np.testing.assert_array_equal(both["xyz"][1], one["xyz"][0])
+    np.testing.assert_array_equal(both["status"][1], one["status"][0])
+    _, x0, _, (xT, st, te) = _sten_oracle(sten, sten.frames, n, lo, hi, 0.9, -0.8, 0.02)
+    same = check_exit_statuses(one["status"][0], one["t_exit"][0], st, te, 0.02)
+    assert np.abs(one["xyz"][0][:, same] - xT[:, same]).max() <= 2e-5
+    assert (st == oracle.LEFT).sum() > 50
+    # FTLE of job 0 from the oracle's flow map of the same lattice
+    _, _, _, (xT0, st0, _) = _sten_oracle(sten, sten.frames, n, lo, hi, 0.1, 0.6, 0.02)
+    h = oracle.lattice_spacing(2, n, lo, hi, [1, 1])
+    G = oracle.flowmap_gradient(2, n, h, [0, 0], [0.0, 0.0], xT0, st0)
+    _, sig = oracle.ftle(oracle.cauchy_green(G), 2, 0.6)
+    ok = np.isfinite(sig) & np.isfinite(both["ftle"][0])
+    assert ok.sum() > 2000
+    check_ftle(both["ftle"][0], sig)
+
+
+# ------------------------------------------------------------------ DP5(4)
+
+def test_rk45_tri_affine_closed_form(ctx):
+    pts, tris, nbrs = tri_grid_mesh(4)
+    pts = pts - np.float32(2.0)
+    A = np.array([[-0.125, -0.5], [0.5, -0.125]])
+    fr = np.stack([pts @ A.T, pts @ A.T]).astype(np.float32)
+    n, lo, hi = (16, 12), (-1.5, -1.5), (1.5, 1.5)
+    T = 4.0
+    opts = lcs.advect_opts(lcs.RK45, t0=0.0, T=T, rtol=1e-5, atol=1e-5, h0=0.05)
+    g = gpu_tri(ctx, tri_desc(pts, tris, nbrs, [0.0, 10.0]), fr, n, lo, hi, opts, want_steps=True)
+    x0 = ora_seeds(n, lo, hi).astype(np.float64)
+    assert (g["status"][0] == lcs.TRACER_OK).all()
+    assert np.abs(g["xyz"][0] - expm(T * A) @ x0).max() <= 2e-4
+    F = oracle.TriField(pts, tris, nbrs, fr, [0.0, 10.0])
+    xo, so, _, nso = oracle.dp45(F, x0, 0.0, T, h0=0.05, rtol=1e-5, atol=1e-5, group=32,
+                                 cells=F.locate_seeds(x0))
+    assert np.abs(g["xyz"][0] - xo).max() <= 1e-4
+    assert np.abs(g["steps"][0].astype(np.int64) - nso).max() <= 3
+
+
+def test_rk45_tri_stenosis_matches_oracle(ctx, sten):
+    n, lo, hi = (64, 24), (0.1, -0.9), (9.9, 0.9)
+    t0, T = 0.2, 1.0
+    opts = lcs.advect_opts(lcs.RK45, t0=t0, T=T, rtol=1e-6, atol=1e-6, h0=0.01)
+    g = gpu_tri(ctx, sten_desc(sten), sten.frames, n, lo, hi, opts, want_steps=True)
+    F = oracle.TriField(sten.xyz, sten.tets, sten.nbrs, sten.frames, sten.times, True, sten.period)
+    x0 = ora_seeds(n, lo, hi)
+    cells = F.locate_seeds(x0)
+    xo, so, teo, nso = oracle.dp45(F, x0.astype(np.float64), t0, T, h0=0.01, rtol=1e-6, atol=1e-6,
+                                   group=32, cells=cells)
+    st = g["status"][0]
+    assert (so == oracle.LEFT).sum() > 50 and (so == oracle.OK).sum() > 800
+    diff = st != so
+    assert diff.mean() <= 5e-3, diff.sum()
+    # P1 velocity has kinks across every edge, which the embedded error estimate does not see, so
+    # at rtol = 1e-6 the oracle itself is off the converged flow by up to ~3e-4; the GPU (FP32
+    # error norms, so a different accept/reject sequence) is held to the oracle's own accuracy
+    # against a converged run (rtol 1e-10) rather than to a fixed distance from it
+    xr, sr, _, _ = oracle.dp45(F, x0.astype(np.float64), t0, T, h0=0.01, rtol=1e-10, atol=1e-10, cells=cells)
+    ok = (st == so) & (so == oracle.OK) & (sr == oracle.OK)
+    e_ora = np.abs(xo[:, ok] - xr[:, ok]).max(axis=0)
+    e_gpu = np.abs(g["xyz"][0][:, ok] - xr[:, ok]).max(axis=0)
+    assert np.median(e_gpu) <= 2 * np.median(e_ora) + 1e-6, (np.median(e_gpu), np.median(e_ora))
+    assert e_gpu.max() <= 2 * e_ora.max() + 1e-5, (e_gpu.max(), e_ora.max())
+    steps_ok = np.abs(g["steps"][0].astype(np.int64) - nso)
+    assert np.median(steps_ok) <= 1 and steps_ok.max() <= 10
+
+
+# ------------------------------------------------------------------ errors
+
+def test_tri_argument_errors(ctx, sten):
+    bad = lcs.field_desc(3, times=sten.times, kind=lcs.TRI, mesh=(sten.xyz, sten.tets, sten.nbrs))
+    with pytest.raises(lcs.LcsError) as e:
+        lcs.lcs_load_field(ctx, bad, sten.frames)
+    assert e.value.status == 1
+    tris = sten.tets.copy()
+    tris[5, 1] = len(sten.xyz)              # a node id past the end
+    with pytest.raises(lcs.LcsError) as e:
+        lcs.lcs_load_field(ctx, tri_desc(sten.xyz, tris, None, sten.times), sten.frames)
+    assert e.value.status == 1
+    field = lcs.lcs_load_field(ctx, sten_desc(sten), sten.frames)
+    plain = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (8, 8), (0.0, -1.0), (10.0, 1.0)))
+    fm = lcs.lcs_flowmap_create(ctx, plain, 1)
+    try:
+        with pytest.raises(lcs.LcsError) as e:   # seeds not located on this field
+            lcs.lcs_advect(ctx, field, plain, lcs.advect_opts(lcs.RK4, T=0.5, dt=0.05), fm)
+        assert e.value.status == 1
+        seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (8, 8), (0.0, -1.0), (10.0, 1.0)), field)
+        fm2 = lcs.lcs_flowmap_create(ctx, seeds, 1)
+        for kw in (dict(snap_T=[0.25]), dict(variational=True)):
+            with pytest.raises(lcs.LcsError) as e:
+                lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=0.5, dt=0.05, **kw), fm2)
+            assert e.value.status == 7
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=0.5, dt=0.05), fm2)
+        lcs.lcs_synchronize(ctx)
+        lcs.lcs_free_flowmap(fm2)
+        lcs.lcs_free_seeds(seeds)
+    finally:
+        lcs.lcs_free_flowmap(fm)
+        lcs.lcs_free_seeds(plain)
+        lcs.lcs_free_field(field)
