@@ -439,7 +439,9 @@ long long ora_tet_locate_walk(const ora_tet_field *f, long long start, const flo
             break;
         }
         long long nb = f->nbrs[4 * t + best];
-        if (nb < 0) return -1; /* separated from the convex hull by a boundary face */
+        /* a boundary face separates p from this tet: outside a convex mesh, but a non-convex
+         * one (a curved vessel, an aneurysm) may still hold p elsewhere */
+        if (nb < 0) return ora_tet_locate_brute(f, p);
         t = nb;
     }
     if (!found) return ora_tet_locate_brute(f, p);
@@ -494,7 +496,7 @@ static long long tet_locate_fp64(const ora_tet_field *f, long long start, const 
             }
         if (best < 0) return t;
         long long nb = f->nbrs[4 * t + best];
-        if (nb < 0) return -1;
+        if (nb < 0) break; /* across a boundary face: settled by testing every tet */
         t = nb;
     }
     for (long long c = 0; c < f->ncells; ++c) {

@@ -116,7 +116,8 @@ int ora_rect_velocity_grad(const ora_rect_field *f, const double *x, double t, d
 /* u(x, t) from an analytic field.  Returns 0.                               */
 int ora_analytic_velocity(const ora_analytic_field *f, const double *x, double t, double *u);
 
-/* u(x, t) on a tet mesh: exact point location, P1 interpolation.
+/* u(x, t) on a tet mesh: FP64 walk from *cell (barycentric tolerance 1e-12),
+ * every tet tested when the walk reaches a boundary face, P1 interpolation.
  * *cell is the walk's start (in) and the containing tet (out).
  * Returns 0 inside, 1 outside the mesh.                                     */
 int ora_tet_velocity(const ora_tet_field *f, const double *x, double t, int *cell, double *u);
@@ -225,7 +226,8 @@ long long ora_tet_locate_brute(const ora_tet_field *f, const float *p);
 
 /* Walk from start (Sec. 3.1 local search): cross a face whose plane separates
  * p from the tet until none does; then the tie-break of lowest id among the
- * closed tets holding p.  Falls back to brute force past walk_limit.
+ * closed tets holding p.  Falls back to brute force past walk_limit or when
+ * the walk reaches a boundary face (the mesh need not be convex).
  * Returns the tet id or -1 if p is outside the mesh.                        */
 long long ora_tet_locate_walk(const ora_tet_field *f, long long start, const float *p);
 

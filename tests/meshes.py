@@ -33,6 +33,31 @@ def kuhn_mesh(n):
     return pts, tets, nbrs
 
 
+def l_kuhn_mesh(n):
+    """kuhn_mesh(n) without the cubes with i >= n/2 and j >= n/2 (an L-shaped prism: non-convex),
+    ids renumbered; neighbours by face matching."""
+    pts, tets, _ = kuhn_mesh(n)
+    c = pts[tets].mean(axis=1)
+    keep = ~((c[:, 0] > n / 2) & (c[:, 1] > n / 2))
+    tets = tets[keep]
+    used = np.unique(tets)
+    remap = -np.ones(len(pts), dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    pts = pts[used]
+    tets = remap[tets].astype(np.int32)
+    faces = {}
+    nbrs = -np.ones_like(tets)
+    for t, vs in enumerate(tets):
+        for j in range(4):
+            key = tuple(sorted(np.delete(vs, j)))
+            if key in faces:
+                s, sj = faces[key]
+                nbrs[t, j], nbrs[s, sj] = s, t
+            else:
+                faces[key] = (t, j)
+    return pts, tets, nbrs
+
+
 def tri_grid_mesh(n, seed=7):
     """n^2 unit squares with integer nodes, each split into 2 triangles along a diagonal chosen
     per square; the vertex order of about half the triangles is reversed (clockwise), so location

@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 from paper_2209_13775_gb300 import inputs
-from meshes import kuhn_mesh
+from meshes import kuhn_mesh, l_kuhn_mesh
 
 
 def _orient_exact(a, b, c, d):
@@ -87,6 +87,32 @@ def test_walk_equals_brute_force_with_tie_break(ora):
         for start in rng.choice(len(tets), 3):
             assert f.locate_walk(q, int(start)) == brute
     assert n_ties > 60          # the tie-break path really ran
+
+
+def test_walk_on_non_convex_mesh(ora):
+    # an L-shaped prism: from a start in one arm, the straight walk to a point in the other arm
+    # crosses the notch and meets a boundary face, yet the point is inside
+    pts, tets, nbrs = l_kuhn_mesh(4)
+    f = _field(ora, pts, tets, nbrs)
+    rng = np.random.default_rng(34)
+    arm_a = rng.uniform([2.1, 0.1, 0.1], [3.9, 1.9, 3.9], (40, 3)).astype(np.float32)   # x-arm
+    arm_b = rng.uniform([0.1, 2.1, 0.1], [1.9, 3.9, 3.9], (40, 3)).astype(np.float32)   # y-arm
+    notch = rng.uniform([2.1, 2.1, 0.1], [3.9, 3.9, 3.9], (20, 3)).astype(np.float32)   # outside
+    start_a = f.locate_brute(np.float32([3.5, 0.5, 2.0]))
+    start_b = f.locate_brute(np.float32([0.5, 3.5, 2.0]))
+    for p in arm_a:
+        assert f.locate_walk(p, start_b) == f.locate_brute(p) >= 0
+    for p in arm_b:
+        assert f.locate_walk(p, start_a) == f.locate_brute(p) >= 0
+    for p in notch:
+        assert f.locate_walk(p, start_a) == -1
+    # the interpolation-time location too: u of an affine field from a start across the notch
+    A = np.array([[0.5, -1.0, 0.25], [1.0, 0.0, -0.5], [0.125, 0.75, -0.5]])
+    fr = np.stack([pts @ A.T]).astype(np.float32)
+    g = _field(ora, pts, tets, nbrs, fr, (0.0,))
+    for p in arm_b[:10]:
+        u, c = g.velocity(p.astype(np.float64), 0.0, cell=start_a)
+        np.testing.assert_allclose(u, A @ p.astype(np.float64), rtol=0, atol=1e-12)
 
 
 def test_walk_on_delaunay_pipe_mesh(ora):
