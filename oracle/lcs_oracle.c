@@ -378,10 +378,25 @@ int ora_tet_contains(const ora_tet_field *f, long long t, const float *p, int *o
     return inside;
 }
 
+/* a closed tet lies inside the bounding box of its vertices */
+static int tet_bbox_holds(const ora_tet_field *f, long long t, const float *p)
+{
+    for (int c = 0; c < 3; ++c) {
+        float lo = tet_vertex(f, t, 0)[c], hi = lo;
+        for (int v = 1; v < 4; ++v) {
+            float q = tet_vertex(f, t, v)[c];
+            if (q < lo) lo = q;
+            if (q > hi) hi = q;
+        }
+        if (p[c] < lo || p[c] > hi) return 0;
+    }
+    return 1;
+}
+
 long long ora_tet_locate_brute(const ora_tet_field *f, const float *p)
 {
     for (long long t = 0; t < f->ncells; ++t)
-        if (ora_tet_contains(f, t, p, NULL)) return t;
+        if (tet_bbox_holds(f, t, p) && ora_tet_contains(f, t, p, NULL)) return t;
     return -1;
 }
 
@@ -480,6 +495,23 @@ long long ora_tet_locate_walk(const ora_tet_field *f, long long start, const flo
 /* Interpolation-time location of an FP64 point: walk on FP64 barycentric
  * coordinates (P1 interpolation is continuous across faces, so which of two
  * face-sharing tets is found does not change u beyond rounding).          */
+/* x within the vertices' bounding box widened by 1e-9 (1 + extent) per axis: a cell whose
+ * barycentric coordinates of x are all >= -1e-12 always passes, so the test only skips work */
+static int near_bbox(const float *pts, const int *cell, int nv, int dim, const double *x)
+{
+    for (int c = 0; c < dim; ++c) {
+        double lo = pts[(long long)dim * cell[0] + c], hi = lo;
+        for (int v = 1; v < nv; ++v) {
+            double q = pts[(long long)dim * cell[v] + c];
+            if (q < lo) lo = q;
+            if (q > hi) hi = q;
+        }
+        double m = 1e-9 * (1.0 + hi - lo);
+        if (x[c] < lo - m || x[c] > hi + m) return 0;
+    }
+    return 1;
+}
+
 static long long tet_locate_fp64(const ora_tet_field *f, long long start, const double *x, double *lam)
 {
     const double tol = 1e-12;
@@ -500,6 +532,7 @@ static long long tet_locate_fp64(const ora_tet_field *f, long long start, const 
         t = nb;
     }
     for (long long c = 0; c < f->ncells; ++c) {
+        if (!near_bbox(f->xyz, f->tets + 4 * c, 4, 3, x)) continue;
         tet_bary(f, c, x, lam);
         if (lam[0] >= -tol && lam[1] >= -tol && lam[2] >= -tol && lam[3] >= -tol) return c;
     }
@@ -587,10 +620,25 @@ int ora_tri_contains(const ora_tri_field *f, long long t, const float *p, int *o
     return inside;
 }
 
+/* a closed triangle lies inside the bounding box of its vertices */
+static int tri_bbox_holds(const ora_tri_field *f, long long t, const float *p)
+{
+    for (int c = 0; c < 2; ++c) {
+        float lo = tri_vertex(f, t, 0)[c], hi = lo;
+        for (int v = 1; v < 3; ++v) {
+            float q = tri_vertex(f, t, v)[c];
+            if (q < lo) lo = q;
+            if (q > hi) hi = q;
+        }
+        if (p[c] < lo || p[c] > hi) return 0;
+    }
+    return 1;
+}
+
 long long ora_tri_locate_brute(const ora_tri_field *f, const float *p)
 {
     for (long long t = 0; t < f->ncells; ++t)
-        if (ora_tri_contains(f, t, p, NULL)) return t;
+        if (tri_bbox_holds(f, t, p) && ora_tri_contains(f, t, p, NULL)) return t;
     return -1;
 }
 
@@ -687,6 +735,7 @@ static long long tri_locate_fp64(const ora_tri_field *f, long long start, const 
         t = nb;
     }
     for (long long c = 0; c < f->ncells; ++c) {
+        if (!near_bbox(f->xy, f->tris + 3 * c, 3, 2, x)) continue;
         tri_bary(f, c, x, lam);
         if (lam[0] >= -tol && lam[1] >= -tol && lam[2] >= -tol) return c;
     }

@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(256) rk4_tet_kernel(TetDev T, Rk4Args A, const
 // ------------------------------------------------------------- RK4 on triangles
 
 template <int ST>
-__global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const int *__restrict__ cells0)
+__global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const int *__restrict__ cells0,
+                                                      unsigned *errword)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int job = blockIdx.y;
@@ -104,7 +105,8 @@ __global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const
             tri_interp<ST>(T, cell, lam, T.pairs + (size_t)es.k * T.fstride, es.a, k[s]);
         }
         if (r != TET_INSIDE) {  // a stage point left the mesh: freeze at the start of the step
-            st = LCS_TRACER_LEFT;
+            st = r == TET_OUTSIDE ? LCS_TRACER_LEFT : LCS_TRACER_WALKFAIL;
+            if (r == TET_WALKFAIL) atomicOr(errword, LCS_ERRBIT_WALK);
             te = fmaf((float)n, h, A.job_t0[job]);
             break;
         }
@@ -349,21 +351,6 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
 
 // ------------------------------------------------------------------ launchers
 
-static TetDev tet_dev(const lcs_field *f, int walk_limit)
-{
-    TetDev T;
-    T.xyz = f->d_xyz;
-    T.tets = f->d_tets;
-    T.nbrs = f->d_nbrs;
-    T.tmap = f->d_tetmap;
-    T.pairs = (const char *)f->d_frames;
-    T.fstride = f->frame_stride;
-    T.ncells = f->ncells;
-    T.walk_limit = walk_limit > 0 ? walk_limit : 512;
-    T.tol = 1e-6f;
-    return T;
-}
-
 cudaError_t launch_rk4_tet(lcs_ctx *ctx, const Rk4Launch &L, const int *cells0, int walk_limit, cudaStream_t s)
 {
     const lcs_field *f = L.field;
@@ -386,11 +373,11 @@ cudaError_t launch_rk4_tet(lcs_ctx *ctx, const Rk4Launch &L, const int *cells0, 
         const TriDev T = tri_dev(f, walk_limit);
         lcs_tm_begin(ctx, 0, s);
         if (f->storage == LCS_F32)
-            rk4_tri_kernel<LCS_F32><<<grid, bt, 0, s>>>(T, A, cells0);
+            rk4_tri_kernel<LCS_F32><<<grid, bt, 0, s>>>(T, A, cells0, ctx->d_errword);
         else if (f->storage == LCS_F16)
-            rk4_tri_kernel<LCS_F16><<<grid, bt, 0, s>>>(T, A, cells0);
+            rk4_tri_kernel<LCS_F16><<<grid, bt, 0, s>>>(T, A, cells0, ctx->d_errword);
         else
-            rk4_tri_kernel<LCS_BF16><<<grid, bt, 0, s>>>(T, A, cells0);
+            rk4_tri_kernel<LCS_BF16><<<grid, bt, 0, s>>>(T, A, cells0, ctx->d_errword);
         lcs_tm_end(ctx, 0, s);
         return cudaGetLastError();
     }

@@ -471,7 +471,6 @@ extern "C" void lcs_free_field(lcs_field *f)
     cudaFree(f->d_tets);
     cudaFree(f->d_nbrs);
     cudaFree(f->d_tetmap);
-    cudaFree(f->d_bins);
     cudaFree(f->d_xy);
     cudaFree(f->d_trimap);
     cudaFree(f->d_triv0);
@@ -613,7 +612,7 @@ extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const 
         e = cudaMalloc(&s->d_cells, sizeof(int) * (size_t)N);
         if (e == cudaSuccess)
             e = field->kind == LCS_TRI ? tri_locate_seeds(field, s->d_xyz, N, s->d_cells, ctx->stream)
-                                       : tet_locate_seeds(field, s->d_xyz, N, 1 << 16, s->d_cells, ctx->stream);
+                                       : tet_locate_seeds(field, s->d_xyz, N, s->d_cells, ctx->stream);
     }
     if (e != cudaSuccess) {
         lcs_free_seeds(s);

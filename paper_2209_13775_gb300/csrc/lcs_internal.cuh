@@ -90,26 +90,28 @@ struct lcs_field {
     int4 *d_tets = nullptr;            // [ncells]
     int4 *d_nbrs = nullptr;            // [ncells]
     float4 *d_tetmap = nullptr;        // [ncells][3]: rows of the inverse affine map + v0
-    int *d_bins = nullptr;             // walk starts: a tet near each bin of a uniform grid
-    int bin_n[3] = {0, 0, 0};
+    int bin_n[3] = {0, 0, 0};          // bin grid over the nodes' bounding box (meshes)
     float bin_lo[3] = {0, 0, 0}, bin_inv[3] = {0, 0, 0};
     // triangle mesh (d_tets, d_nbrs hold (a, b, c, 0) and (n0, n1, n2, -1))
     float2 *d_xy = nullptr;            // [nodes]
     float4 *d_trimap = nullptr;        // [ncells] (M00, M01, M10, M11) of the inverse affine map
     float2 *d_triv0 = nullptr;         // [ncells] vertex 0
-    int *d_bstart = nullptr;           // [nbins + 1] CSR: triangles whose bounding box meets a bin
+    int *d_bstart = nullptr;           // [nbins + 1] CSR (meshes): cells whose bounding box meets a bin
     int *d_blist = nullptr;
     long long nbins = 0;
+    int convex = 0;                    // mesh proven convex: a walk that meets the boundary is outside
 };
 
 static inline bool lcs_is_mesh(const lcs_field *f) { return f->kind == LCS_TET || f->kind == LCS_TRI; }
 
+// true when the cells form one component across their nv neighbours per cell (-1: none)
+bool mesh_connected(const int *nbrs, long long nc, int nv);
+
 // tetrahedral store (tet_store.cu): positions, tets, neighbours (built when null), inverse
-// affine maps and the bin grid; exact seed location
+// affine maps and the bin lists; exact seed location
 cudaError_t tet_build_store(lcs_field *f, const float *xyz_host, const int *tets_host, const int *nbrs_host,
                             cudaStream_t s);
-cudaError_t tet_locate_seeds(const lcs_field *f, const float *seeds, long long N, int walk_limit, int *cells,
-                             cudaStream_t s);
+cudaError_t tet_locate_seeds(const lcs_field *f, const float *seeds, long long N, int *cells, cudaStream_t s);
 
 // triangle store (tri_store.cu): positions, triangles, neighbours (built when null), inverse
 // affine maps and the bin lists; exact seed location

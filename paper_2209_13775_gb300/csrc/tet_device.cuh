@@ -3,7 +3,10 @@
 //
 //  * tet_locate: the local walk of the hot loop, FP32 barycentric coordinates from a
 //    per-tet inverse affine map: stop when no coordinate is below -tol, else cross the
-//    face of the most negative one; a boundary face means the point left the mesh.
+//    face of the most negative one.  A walk that meets a boundary face means the point is
+//    outside when the mesh is convex (checked at load time); otherwise the tets listed for
+//    the point's bin (every tet whose bounding box meets the bin) decide, so the mesh need
+//    not be convex.  A walk past its step limit reports WALKFAIL.
 //  * tet_interp: piecewise-linear (P1) interpolation of the frame pair k, blended in
 //    time at the four vertices.
 //  * orient3d_sign: exact orientation of four FP32 points (filtered FP64 evaluation,
@@ -20,14 +23,36 @@ struct TetDev {
     const int4 *tets;     // [ncells] node ids
     const int4 *nbrs;     // [ncells] tet across the face opposite vertex j, -1 boundary
     const float4 *tmap;   // [ncells][3]: row r = (M_r0, M_r1, M_r2, v0_r), lambda_{r+1} = M_r . (x - v0)
+    const int *bstart;    // [nbins + 1] CSR of the tets whose bounding box meets a bin
+    const int *blist;     //   (ids increasing within a bin)
+    float blo[3], binv[3];
+    int bn[3];
     const char *pairs;    // [nslabs][nnodes] (u_k, 0, u_{k+1}, 0) in storage precision
     size_t fstride;       // bytes per slab
     long long ncells;
     int walk_limit;
     float tol;            // barycentric tolerance of the FP32 walk
+    int convex;           // the mesh is convex: a boundary face separates the point from the mesh
 };
 
 enum { TET_INSIDE = 0, TET_OUTSIDE = 1, TET_WALKFAIL = 2 };
+
+TetDev tet_dev(const lcs_field *f, int walk_limit);  // tet_store.cu
+
+// bin of a coordinate: floor((x - lo) * inv) clamped to the grid (monotone in x, so a cell's
+// bounding-box bins always include the bin of every point it holds)
+__device__ __forceinline__ int mesh_bin_axis(float x, float lo, float inv, int n)
+{
+    const float s = (x - lo) * inv;
+    return isfinite(s) ? (int)fminf(fmaxf(floorf(s), 0.0f), (float)(n - 1)) : 0;
+}
+
+__device__ __forceinline__ int tet_bin(const TetDev &T, const float *x)
+{
+    return mesh_bin_axis(x[0], T.blo[0], T.binv[0], T.bn[0]) +
+           T.bn[0] * (mesh_bin_axis(x[1], T.blo[1], T.binv[1], T.bn[1]) +
+                      T.bn[1] * mesh_bin_axis(x[2], T.blo[2], T.binv[2], T.bn[2]));
+}
 
 // barycentric coordinates of x in tet c (FP32)
 __device__ __forceinline__ void tet_bary(const TetDev &T, int c, const float *x, float *lam)
@@ -39,6 +64,23 @@ __device__ __forceinline__ void tet_bary(const TetDev &T, int c, const float *x,
     lam[2] = fmaf(r1.x, dx, fmaf(r1.y, dy, r1.z * dz));
     lam[3] = fmaf(r2.x, dx, fmaf(r2.y, dy, r2.z * dz));
     lam[0] = 1.0f - lam[1] - lam[2] - lam[3];
+}
+
+// the tets listed for x's bin, in id order: the first whose coordinates all reach -tol
+static __device__ __noinline__ int tet_bin_scan(const TetDev &T, const float *x, int *cell, float *lam)
+{
+    if (!(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]))) return TET_OUTSIDE;
+    const int b = tet_bin(T, x);
+    const int q1 = __ldg(T.bstart + b + 1);
+    for (int q = __ldg(T.bstart + b); q < q1; ++q) {
+        const int c = __ldg(T.blist + q);
+        tet_bary(T, c, x, lam);
+        if (fminf(fminf(lam[0], lam[1]), fminf(lam[2], lam[3])) >= -T.tol) {
+            *cell = c;
+            return TET_INSIDE;
+        }
+    }
+    return TET_OUTSIDE;
 }
 
 // walk from *cell to the tet holding x; lam receives its barycentric coordinates
@@ -64,7 +106,7 @@ __device__ __forceinline__ int tet_locate(const TetDev &T, const float *x, int *
         const int n = jm == 0 ? nb.x : jm == 1 ? nb.y : jm == 2 ? nb.z : nb.w;
         if (n < 0) {
             *cell = c;
-            return TET_OUTSIDE;
+            return T.convex ? TET_OUTSIDE : tet_bin_scan(T, x, cell, lam);
         }
         c = n;
     }

@@ -1,26 +1,18 @@
-// tet_store.cu -- tetrahedral velocity fields: device store, inverse affine maps, a
-// bin grid of walk starts, and the exact location of seeds (Sec. 2 "Seed": on
-// unstructured data the Seed filter finds the cell holding each seed; Sec. 3.1: the
-// local cell search on tetrahedra).
+// tet_store.cu -- tetrahedral velocity fields: device store, inverse affine maps, the
+// bin lists, and the exact location of seeds (Sec. 2 "Seed": on unstructured data the
+// Seed filter finds the cell holding each seed; Sec. 3.1: the local cell search on
+// tetrahedra).
+//
+// Bins: a uniform grid over the nodes' bounding box with about two tets per bin; each bin
+// lists, in increasing id, every tet whose bounding box meets it.  A point's bin therefore
+// lists every tet that holds it: the seed location's walks and the integrator's walk fall back
+// to that list when they meet a boundary face, so the mesh need not be convex.
 #include "tet_device.cuh"
 
 #include <math.h>
 
 #include <algorithm>
 #include <vector>
-
-#define BIN_EMPTY 0x7f7f7f7f  // what a 0x7f byte fill leaves in an int
-
-// 32-bit integer hash (Wellons' lowbias32): face order of the stochastic walk
-__device__ __forceinline__ unsigned lowbias32_t(unsigned x)
-{
-    x ^= x >> 16;
-    x *= 0x7feb352du;
-    x ^= x >> 15;
-    x *= 0x846ca68bu;
-    x ^= x >> 16;
-    return x;
-}
 
 // ------------------------------------------------------------ device kernels
 
@@ -66,57 +58,62 @@ struct BinGrid {
     int n[3];
 };
 
-__device__ __forceinline__ long long bin_of(const BinGrid &B, float x, float y, float z)
+__device__ __forceinline__ void tet_bbox_bins(const BinGrid &B, const float4 *xyz, int4 q, int *b0, int *b1)
 {
-    const float p[3] = {x, y, z};
-    int c[3];
-    for (int d = 0; d < 3; ++d) {
-        float s = (p[d] - B.lo[d]) * B.inv[d];
-        int v = isfinite(s) ? (int)floorf(s) : 0;
-        c[d] = min(max(v, 0), B.n[d] - 1);
-    }
-    return c[0] + (long long)B.n[0] * (c[1] + (long long)B.n[1] * c[2]);
-}
-
-// each bin remembers the lowest-id tet whose centroid falls in it
-__global__ void tet_bin_kernel(const float4 *__restrict__ xyz, const int4 *__restrict__ tets, long long nc, BinGrid B,
-                               int *__restrict__ bins)
-{
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= nc) return;
-    const int4 q = tets[t];
     const float4 a = xyz[q.x], b = xyz[q.y], c = xyz[q.z], d = xyz[q.w];
-    atomicMin(bins + bin_of(B, 0.25f * (a.x + b.x + c.x + d.x), 0.25f * (a.y + b.y + c.y + d.y),
-                            0.25f * (a.z + b.z + c.z + d.z)),
-              (int)t);
+    const float lo[3] = {fminf(fminf(a.x, b.x), fminf(c.x, d.x)), fminf(fminf(a.y, b.y), fminf(c.y, d.y)),
+                         fminf(fminf(a.z, b.z), fminf(c.z, d.z))};
+    const float hi[3] = {fmaxf(fmaxf(a.x, b.x), fmaxf(c.x, d.x)), fmaxf(fmaxf(a.y, b.y), fmaxf(c.y, d.y)),
+                         fmaxf(fmaxf(a.z, b.z), fmaxf(c.z, d.z))};
+    for (int k = 0; k < 3; ++k) {
+        b0[k] = mesh_bin_axis(lo[k], B.lo[k], B.inv[k], B.n[k]);
+        b1[k] = mesh_bin_axis(hi[k], B.lo[k], B.inv[k], B.n[k]);
+    }
 }
 
-// empty bins borrow the tet of the nearest filled bin within two rings, else tet 0
-__global__ void tet_bin_fill_kernel(BinGrid B, const int *__restrict__ in, int *__restrict__ out)
+__global__ void tet_bin_count_kernel(const float4 *__restrict__ xyz, const int4 *__restrict__ tets, long long nc,
+                                     BinGrid B, int *__restrict__ count)
 {
-    long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long nb = (long long)B.n[0] * B.n[1] * B.n[2];
-    if (b >= nb) return;
-    int v = in[b];
-    if (v != BIN_EMPTY) {
-        out[b] = v;
-        return;
-    }
-    const int x = (int)(b % B.n[0]), y = (int)((b / B.n[0]) % B.n[1]), z = (int)(b / ((long long)B.n[0] * B.n[1]));
-    int best = BIN_EMPTY, bestd = 1 << 30;
-    for (int dz = -2; dz <= 2; ++dz)
-        for (int dy = -2; dy <= 2; ++dy)
-            for (int dx = -2; dx <= 2; ++dx) {
-                int X = x + dx, Y = y + dy, Z = z + dz;
-                if (X < 0 || Y < 0 || Z < 0 || X >= B.n[0] || Y >= B.n[1] || Z >= B.n[2]) continue;
-                int w = in[X + (long long)B.n[0] * (Y + (long long)B.n[1] * Z)];
-                int dd = dx * dx + dy * dy + dz * dz;
-                if (w != BIN_EMPTY && (dd < bestd || (dd == bestd && w < best))) {
-                    best = w;
-                    bestd = dd;
-                }
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nc) return;
+    int b0[3], b1[3];
+    tet_bbox_bins(B, xyz, tets[t], b0, b1);
+    for (int z = b0[2]; z <= b1[2]; ++z)
+        for (int y = b0[1]; y <= b1[1]; ++y)
+            for (int x = b0[0]; x <= b1[0]; ++x) atomicAdd(count + x + B.n[0] * (y + (long long)B.n[1] * z), 1);
+}
+
+__global__ void tet_bin_fill_kernel(const float4 *__restrict__ xyz, const int4 *__restrict__ tets, long long nc,
+                                    BinGrid B, const int *__restrict__ start, int *__restrict__ cursor,
+                                    int *__restrict__ list)
+{
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= nc) return;
+    int b0[3], b1[3];
+    tet_bbox_bins(B, xyz, tets[t], b0, b1);
+    for (int z = b0[2]; z <= b1[2]; ++z)
+        for (int y = b0[1]; y <= b1[1]; ++y)
+            for (int x = b0[0]; x <= b1[0]; ++x) {
+                const long long b = x + B.n[0] * (y + (long long)B.n[1] * z);
+                list[start[b] + atomicAdd(cursor + b, 1)] = (int)t;
             }
-    out[b] = best == BIN_EMPTY ? 0 : best;
+}
+
+// each bin's list in increasing id (insertion sort: lists are short)
+__global__ void tet_bin_sort_kernel(const int *__restrict__ start, long long nbins, int *__restrict__ list)
+{
+    const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int s = start[b], e = start[b + 1];
+    for (int i = s + 1; i < e; ++i) {
+        const int v = list[i];
+        int j = i - 1;
+        while (j >= s && list[j] > v) {
+            list[j + 1] = list[j];
+            --j;
+        }
+        list[j + 1] = v;
+    }
 }
 
 __device__ __forceinline__ void vtx(const TetDev &T, int node, float *p)
@@ -150,29 +147,59 @@ __device__ bool exact_contains(const TetDev &T, int c, const float *p)
     return sg[0] >= 0 && sg[1] >= 0 && sg[2] >= 0 && sg[3] >= 0;
 }
 
-__device__ int exact_brute(const TetDev &T, const float *p)
+// 32-bit integer hash (Wellons' lowbias32): face order of the stochastic walk
+__device__ __forceinline__ unsigned lowbias32_t(unsigned x)
 {
-    for (long long c = 0; c < T.ncells; ++c)
-        if (exact_contains(T, (int)c, p)) return (int)c;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// lowest id among the closed tets of bin b holding p (the bin lists every holder of its points,
+// in increasing id), -1 if none; a tet whose bounding box misses p is skipped without the exact test
+__device__ int exact_bin_scan(const TetDev &T, int b, const float *p)
+{
+    for (int q = T.bstart[b]; q < T.bstart[b + 1]; ++q) {
+        const int c = T.blist[q];
+        const int4 v = T.tets[c];
+        const float4 A = T.xyz[v.x], B = T.xyz[v.y], C = T.xyz[v.z], D = T.xyz[v.w];
+        if (p[0] < fminf(fminf(A.x, B.x), fminf(C.x, D.x)) || p[0] > fmaxf(fmaxf(A.x, B.x), fmaxf(C.x, D.x)) ||
+            p[1] < fminf(fminf(A.y, B.y), fminf(C.y, D.y)) || p[1] > fmaxf(fmaxf(A.y, B.y), fmaxf(C.y, D.y)) ||
+            p[2] < fminf(fminf(A.z, B.z), fminf(C.z, D.z)) || p[2] > fmaxf(fmaxf(A.z, B.z), fmaxf(C.z, D.z)))
+            continue;
+        if (exact_contains(T, c, p)) return c;
+    }
     return -1;
 }
 
 // Lowest id among the closed tets holding p, -1 outside the mesh.
-//  1. An FP32 walk (as in the integrator) from the bin's tet gets next to p cheaply.
+//  1. An FP32 walk (as in the integrator) from the first tet listed for p's bin gets next to p.
 //  2. An exact walk from there: exact orientation signs decide containment, and among the faces
 //     whose exact sign is negative the walk crosses the first one in an order rotated by a
 //     hash of (seed, step) -- a remembering stochastic walk, which cannot cycle on degenerate
-//     (cospherical) configurations the way a deterministic choice can.  The result does not
-//     depend on the path: it is the unique lowest-id closed tet holding p.
+//     (cospherical) configurations the way a deterministic choice can.  A walk that meets a
+//     boundary face (the mesh need not be convex) or its step limit is settled by the bin list.
 //  3. Where p lies on a face, edge or vertex, a breadth-first search over the closed tets across
 //     faces holding p collects every holder and keeps the lowest id.
-__global__ void tet_seed_locate_kernel(TetDev T, const float *__restrict__ seeds, long long N, BinGrid B,
-                                       const int *__restrict__ bins, int walk_limit, int *__restrict__ cells)
+__global__ void tet_seed_locate_kernel(TetDev T, const float *__restrict__ seeds, long long N, int walk_limit,
+                                       int *__restrict__ cells)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float p[3] = {seeds[i], seeds[N + i], seeds[2 * N + i]};
-    int c = bins[bin_of(B, p[0], p[1], p[2])];
+    if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) {
+        cells[i] = -1;
+        return;
+    }
+    const int b = tet_bin(T, p);
+    if (T.bstart[b] == T.bstart[b + 1]) {  // no tet's bounding box meets the bin
+        cells[i] = -1;
+        return;
+    }
+    int c = T.blist[T.bstart[b]];
     {   // 1. FP32 walk, bounded
         float lam[4];
         for (int it = 0; it < 1024; ++it) {
@@ -192,6 +219,7 @@ __global__ void tet_seed_locate_kernel(TetDev T, const float *__restrict__ seeds
         }
     }
     int res = -2;
+    bool it_boundary = false;
     int sg[4];
     for (int it = 0; it < walk_limit; ++it) {  // 2. exact walk
         exact_signs(T, c, p, sg);
@@ -211,16 +239,16 @@ __global__ void tet_seed_locate_kernel(TetDev T, const float *__restrict__ seeds
         const int4 nb = T.nbrs[c];
         const int n = jm == 0 ? nb.x : jm == 1 ? nb.y : jm == 2 ? nb.z : nb.w;
         if (n < 0) {
-            res = -1;
+            it_boundary = true;
             break;
         }
         c = n;
     }
-    if (res == -2) {  // walk limit: fall back to testing every tet
-        cells[i] = exact_brute(T, p);
+    if (res < 0) {  // a boundary face (outside, if the mesh is convex) or the walk limit: the bin list decides
+        cells[i] = T.convex && it_boundary ? -1 : exact_bin_scan(T, b, p);
         return;
     }
-    if (res < 0 || (sg[0] > 0 && sg[1] > 0 && sg[2] > 0 && sg[3] > 0)) {
+    if (sg[0] > 0 && sg[1] > 0 && sg[2] > 0 && sg[3] > 0) {
         cells[i] = res;
         return;
     }
@@ -243,7 +271,7 @@ __global__ void tet_seed_locate_kernel(TetDev T, const float *__restrict__ seeds
             for (int q = 0; q < nseen; ++q) dup |= seen[q] == nn[j];
             if (dup || !exact_contains(T, nn[j], p)) continue;
             if (nseen >= CAP || ns >= CAP) {
-                cells[i] = exact_brute(T, p);
+                cells[i] = exact_bin_scan(T, b, p);
                 return;
             }
             seen[nseen++] = nn[j];
@@ -253,7 +281,99 @@ __global__ void tet_seed_locate_kernel(TetDev T, const float *__restrict__ seeds
     cells[i] = best;
 }
 
+// a boundary face (a, b, c) with the tet's fourth vertex `in` on its interior side: the mesh is
+// concave at an edge of the face when the neighbouring boundary face's far vertex w lies strictly
+// on the other side (exact signs)
+__global__ void tet_convex_kernel(const float4 *__restrict__ xyz, const int *__restrict__ chk, long long n,
+                                  int *__restrict__ convex)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int *q = chk + 5 * i;
+    float v[5][3];
+    for (int k = 0; k < 5; ++k) {
+        const float4 p = xyz[q[k]];
+        v[k][0] = p.x;
+        v[k][1] = p.y;
+        v[k][2] = p.z;
+    }
+    const int s_in = orient3d_sign(v[0], v[1], v[2], v[3]), s_w = orient3d_sign(v[0], v[1], v[2], v[4]);
+    if (s_in * s_w < 0) atomicExch(convex, 0);
+}
+
 // ------------------------------------------------------------------ host side
+
+bool mesh_connected(const int *nbrs, long long nc, int nv)
+{
+    if (nc == 0) return true;
+    std::vector<char> seen((size_t)nc, 0);
+    std::vector<int> stack(1, 0);
+    seen[0] = 1;
+    long long count = 1;
+    while (!stack.empty()) {
+        const int c = stack.back();
+        stack.pop_back();
+        for (int j = 0; j < nv; ++j) {
+            const int n = nbrs[(size_t)nv * c + j];
+            if (n >= 0 && !seen[(size_t)n]) {
+                seen[(size_t)n] = 1;
+                ++count;
+                stack.push_back(n);
+            }
+        }
+    }
+    return count == nc;
+}
+
+// For every boundary edge shared by exactly two boundary faces, two checks (face, interior vertex,
+// far vertex of the other face) as 5 node ids each.  Returns false when some boundary edge is not
+// shared by exactly two boundary faces (then the mesh is not treated as convex).
+static bool tet_convexity_checks(const int *tets, const int *nbrs, long long nc, std::vector<int> &chk)
+{
+    struct E {
+        int u, v;
+        long long tj;  // boundary face: tet * 4 + j
+        int w;         // the face's vertex off the edge
+    };
+    std::vector<E> e;
+    for (long long t = 0; t < nc; ++t)
+        for (int j = 0; j < 4; ++j) {
+            if (nbrs[4 * t + j] >= 0) continue;
+            int f[3], m = 0;
+            for (int k = 0; k < 4; ++k)
+                if (k != j) f[m++] = tets[4 * t + k];
+            for (int k = 0; k < 3; ++k) {
+                int u = f[k], v = f[(k + 1) % 3];
+                if (u > v) std::swap(u, v);
+                e.push_back({u, v, 4 * t + j, f[(k + 2) % 3]});
+            }
+        }
+    std::sort(e.begin(), e.end(), [](const E &x, const E &y) {
+        if (x.u != y.u) return x.u < y.u;
+        if (x.v != y.v) return x.v < y.v;
+        return x.tj < y.tj;
+    });
+    auto face = [&](long long tj, int *q) {
+        const long long t = tj / 4;
+        const int j = (int)(tj % 4);
+        int m = 0;
+        for (int k = 0; k < 4; ++k)
+            if (k != j) q[m++] = tets[4 * t + k];
+        q[3] = tets[4 * t + j];
+    };
+    for (size_t i = 0; i < e.size();) {
+        size_t k = i;
+        while (k < e.size() && e[k].u == e[i].u && e[k].v == e[i].v) ++k;
+        if (k - i != 2) return false;
+        int q[4];
+        for (int s = 0; s < 2; ++s) {
+            face(e[i + s].tj, q);
+            chk.insert(chk.end(), {q[0], q[1], q[2], q[3], e[i + 1 - s].w});
+        }
+        i = k;
+    }
+    return true;
+}
 
 // tet across the face opposite vertex j, by matching sorted vertex triples
 static void build_neighbours(const int *tets, long long nc, std::vector<int> &nbrs)
@@ -311,64 +431,110 @@ cudaError_t tet_build_store(lcs_field *f, const float *xyz_host, const int *tets
         B.inv[d] = (float)(B.n[d] / ext);
     }
     const long long nbins = (long long)B.n[0] * B.n[1] * B.n[2];
-    f->bin_n[0] = B.n[0];
-    f->bin_n[1] = B.n[1];
-    f->bin_n[2] = B.n[2];
     for (int d = 0; d < 3; ++d) {
+        f->bin_n[d] = B.n[d];
         f->bin_lo[d] = B.lo[d];
         f->bin_inv[d] = B.inv[d];
     }
+    f->nbins = nbins;
     float *dxyz = nullptr;
-    int *tmpbins = nullptr;
+    int *count = nullptr, *cursor = nullptr;
     cudaError_t e = cudaMalloc(&f->d_xyz, sizeof(float4) * nn);
     if (e == cudaSuccess) e = cudaMalloc(&f->d_tets, sizeof(int4) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&f->d_nbrs, sizeof(int4) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&f->d_tetmap, sizeof(float4) * 3 * nc);
-    if (e == cudaSuccess) e = cudaMalloc(&f->d_bins, sizeof(int) * nbins);
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_bstart, sizeof(int) * (nbins + 1));
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&dxyz, sizeof(float) * 3 * nn, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&tmpbins, sizeof(int) * nbins, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&count, sizeof(int) * nbins, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&cursor, sizeof(int) * nbins, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dxyz, xyz_host, sizeof(float) * 3 * nn, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f->d_tets, tets_host, sizeof(int4) * nc, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(f->d_nbrs, nbrs_host, sizeof(int4) * nc, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tmpbins, 0x7f, sizeof(int) * nbins, s);  // BIN_EMPTY
-    if (e != cudaSuccess) {
-        if (dxyz) cudaFreeAsync(dxyz, s);
-        if (tmpbins) cudaFreeAsync(tmpbins, s);
-        return e;
-    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(int) * nbins, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(int) * nbins, s);
     const int bt = 256;
-    tet_xyz_kernel<<<(unsigned)((nn + bt - 1) / bt), bt, 0, s>>>(dxyz, nn, f->d_xyz);
-    tet_map_kernel<<<(unsigned)((nc + bt - 1) / bt), bt, 0, s>>>(f->d_xyz, f->d_tets, nc, f->d_tetmap);
-    tet_bin_kernel<<<(unsigned)((nc + bt - 1) / bt), bt, 0, s>>>(f->d_xyz, f->d_tets, nc, B, tmpbins);
-    tet_bin_fill_kernel<<<(unsigned)((nbins + bt - 1) / bt), bt, 0, s>>>(B, tmpbins, f->d_bins);
-    e = cudaGetLastError();
-    cudaFreeAsync(dxyz, s);
-    cudaFreeAsync(tmpbins, s);
+    const unsigned gc = (unsigned)((nc + bt - 1) / bt);
+    if (e == cudaSuccess) {
+        tet_xyz_kernel<<<(unsigned)((nn + bt - 1) / bt), bt, 0, s>>>(dxyz, nn, f->d_xyz);
+        tet_map_kernel<<<gc, bt, 0, s>>>(f->d_xyz, f->d_tets, nc, f->d_tetmap);
+        tet_bin_count_kernel<<<gc, bt, 0, s>>>(f->d_xyz, f->d_tets, nc, B, count);
+        e = cudaGetLastError();
+    }
+    // the CSR offsets on the host (load time only)
+    std::vector<int> h((size_t)nbins), st((size_t)nbins + 1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), count, sizeof(int) * nbins, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    long long total = 0;
+    if (e == cudaSuccess) {
+        for (long long b = 0; b < nbins; ++b) {
+            st[(size_t)b] = (int)total;
+            total += h[(size_t)b];
+        }
+        st[(size_t)nbins] = (int)total;
+        if (total >= (1LL << 31)) e = cudaErrorInvalidValue;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_blist, sizeof(int) * std::max(total, 1LL));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f->d_bstart, st.data(), sizeof(int) * (nbins + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        tet_bin_fill_kernel<<<gc, bt, 0, s>>>(f->d_xyz, f->d_tets, nc, B, f->d_bstart, cursor, f->d_blist);
+        tet_bin_sort_kernel<<<(unsigned)((nbins + bt - 1) / bt), bt, 0, s>>>(f->d_bstart, nbins, f->d_blist);
+        e = cudaGetLastError();
+    }
+    // convex (connected, every boundary edge convex): then a walk that meets the boundary is outside
+    std::vector<int> chk;
+    int convex = mesh_connected(nbrs_host, nc, 4) && tet_convexity_checks(tets_host, nbrs_host, nc, chk) ? 1 : 0;
+    int *dchk = nullptr, *dflag = nullptr;
+    const long long nchk = (long long)chk.size() / 5;
+    if (e == cudaSuccess && convex && nchk > 0) {
+        e = cudaMallocAsync((void **)&dchk, sizeof(int) * chk.size(), s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&dflag, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dchk, chk.data(), sizeof(int) * chk.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dflag, &convex, sizeof(int), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            tet_convex_kernel<<<(unsigned)((nchk + bt - 1) / bt), bt, 0, s>>>(f->d_xyz, dchk, nchk, dflag);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&convex, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    if (dxyz) cudaFreeAsync(dxyz, s);
+    if (count) cudaFreeAsync(count, s);
+    if (cursor) cudaFreeAsync(cursor, s);
+    if (dchk) cudaFreeAsync(dchk, s);
+    if (dflag) cudaFreeAsync(dflag, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host values above go out of scope
+    f->convex = e == cudaSuccess ? convex : 0;
     return e;
 }
 
-cudaError_t tet_locate_seeds(const lcs_field *f, const float *seeds, long long N, int walk_limit, int *cells,
-                             cudaStream_t s)
+TetDev tet_dev(const lcs_field *f, int walk_limit)
 {
-    if (N == 0) return cudaSuccess;
     TetDev T;
     T.xyz = f->d_xyz;
     T.tets = f->d_tets;
     T.nbrs = f->d_nbrs;
     T.tmap = f->d_tetmap;
+    T.bstart = f->d_bstart;
+    T.blist = f->d_blist;
+    for (int d = 0; d < 3; ++d) {
+        T.blo[d] = f->bin_lo[d];
+        T.binv[d] = f->bin_inv[d];
+        T.bn[d] = f->bin_n[d];
+    }
     T.pairs = (const char *)f->d_frames;
     T.fstride = f->frame_stride;
     T.ncells = f->ncells;
-    T.walk_limit = walk_limit;
-    T.tol = 0.0f;
-    BinGrid B;
-    for (int d = 0; d < 3; ++d) {
-        B.n[d] = f->bin_n[d];
-        B.lo[d] = f->bin_lo[d];
-        B.inv[d] = f->bin_inv[d];
-    }
+    T.walk_limit = walk_limit > 0 ? walk_limit : 512;
+    T.tol = 1e-6f;
+    T.convex = f->convex;
+    return T;
+}
+
+cudaError_t tet_locate_seeds(const lcs_field *f, const float *seeds, long long N, int *cells, cudaStream_t s)
+{
+    if (N == 0) return cudaSuccess;
+    const TetDev T = tet_dev(f, 0);
     const int bt = 128;
-    tet_seed_locate_kernel<<<(unsigned)((N + bt - 1) / bt), bt, 0, s>>>(T, seeds, N, B, f->d_bins, walk_limit,
-                                                                        cells);
+    tet_seed_locate_kernel<<<(unsigned)((N + bt - 1) / bt), bt, 0, s>>>(T, seeds, N, 1 << 16, cells);
     return cudaGetLastError();
 }

@@ -4,9 +4,9 @@
 //
 //  * tri_locate: the hot loop's local walk on FP32 barycentric coordinates from a per-
 //    triangle inverse affine map (stop when no coordinate is below -tol, else cross the
-//    edge of the most negative one).  A walk that meets a boundary edge, or its step limit,
-//    is settled by the triangles listed for the point's bin, so meshes need not be convex
-//    (a channel with a constriction is not).
+//    edge of the most negative one).  A walk that meets a boundary edge is settled by the
+//    triangles listed for the point's bin, so meshes need not be convex (a channel with a
+//    constriction is not); a walk past its step limit reports WALKFAIL.
 //  * tri_interp: P1 interpolation of the frame pair k, blended in time at the vertices.
 //  * orient2d_sign: exact orientation of three FP32 points (FP64 filter, exact expansion
 //    sum of the six two-factor products when the filter cannot decide).
@@ -29,18 +29,10 @@ struct TriDev {
     long long ncells;
     int walk_limit;
     float tol;
+    int convex;           // the mesh is convex: a boundary edge separates the point from the mesh
 };
 
 TriDev tri_dev(const lcs_field *f, int walk_limit);  // tri_store.cu
-
-// bin of a point: floor((x - lo) * inv) clamped to the grid (monotone in x, so a triangle's
-// bounding-box bins always include the bin of every point it holds)
-__device__ __forceinline__ int tri_bin_axis(float x, float lo, float inv, int n)
-{
-    const float s = (x - lo) * inv;
-    const int v = isfinite(s) ? (int)fminf(fmaxf(floorf(s), 0.0f), (float)(n - 1)) : 0;
-    return v;
-}
 
 __device__ __forceinline__ void tri_bary(const TriDev &T, int c, const float *x, float *lam)
 {
@@ -56,8 +48,8 @@ __device__ __forceinline__ void tri_bary(const TriDev &T, int c, const float *x,
 __device__ __forceinline__ int tri_bin_scan(const TriDev &T, const float *x, int *cell, float *lam)
 {
     if (!(isfinite(x[0]) && isfinite(x[1]))) return TET_OUTSIDE;
-    const int b = tri_bin_axis(x[0], T.blo[0], T.binv[0], T.bn[0]) +
-                  T.bn[0] * tri_bin_axis(x[1], T.blo[1], T.binv[1], T.bn[1]);
+    const int b = mesh_bin_axis(x[0], T.blo[0], T.binv[0], T.bn[0]) +
+                  T.bn[0] * mesh_bin_axis(x[1], T.blo[1], T.binv[1], T.bn[1]);
     const int q1 = __ldg(T.bstart + b + 1);
     for (int q = __ldg(T.bstart + b); q < q1; ++q) {
         const int c = __ldg(T.blist + q);
@@ -92,10 +84,11 @@ __device__ __forceinline__ int tri_locate(const TriDev &T, const float *x, int *
         }
         const int4 nb = __ldg(T.nbrs + c);
         const int n = jm == 0 ? nb.x : jm == 1 ? nb.y : nb.z;
-        if (n < 0) break;
+        if (n < 0) return T.convex ? TET_OUTSIDE : tri_bin_scan(T, x, cell, lam);
         c = n;
     }
-    return tri_bin_scan(T, x, cell, lam);
+    *cell = c;
+    return TET_WALKFAIL;
 }
 
 template <int ST>

@@ -42,8 +42,8 @@ __device__ __forceinline__ void tri_bbox_bins(const TriBins &B, const float2 *xy
     const float lo[2] = {fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y))};
     const float hi[2] = {fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y))};
     for (int d = 0; d < 2; ++d) {
-        b0[d] = tri_bin_axis(lo[d], B.lo[d], B.inv[d], B.n[d]);
-        b1[d] = tri_bin_axis(hi[d], B.lo[d], B.inv[d], B.n[d]);
+        b0[d] = mesh_bin_axis(lo[d], B.lo[d], B.inv[d], B.n[d]);
+        b1[d] = mesh_bin_axis(hi[d], B.lo[d], B.inv[d], B.n[d]);
     }
 }
 
@@ -109,15 +109,74 @@ __global__ void tri_seed_locate_kernel(TriDev T, const float *__restrict__ seeds
     const float p[2] = {seeds[i], seeds[N + i]};
     int res = -1;
     if (isfinite(p[0]) && isfinite(p[1])) {
-        const int b = tri_bin_axis(p[0], T.blo[0], T.binv[0], T.bn[0]) +
-                      T.bn[0] * tri_bin_axis(p[1], T.blo[1], T.binv[1], T.bn[1]);
-        for (int q = T.bstart[b]; q < T.bstart[b + 1]; ++q)
+        const int b = mesh_bin_axis(p[0], T.blo[0], T.binv[0], T.bn[0]) +
+                      T.bn[0] * mesh_bin_axis(p[1], T.blo[1], T.binv[1], T.bn[1]);
+        for (int q = T.bstart[b]; q < T.bstart[b + 1]; ++q) {
+            const int4 v = T.tris[T.blist[q]];
+            const float2 A = T.xy[v.x], B = T.xy[v.y], C = T.xy[v.z];
+            if (p[0] < fminf(A.x, fminf(B.x, C.x)) || p[0] > fmaxf(A.x, fmaxf(B.x, C.x)) ||
+                p[1] < fminf(A.y, fminf(B.y, C.y)) || p[1] > fmaxf(A.y, fmaxf(B.y, C.y)))
+                continue;  // the bounding box misses p: not a holder
             if (tri_exact_contains(T, T.blist[q], p)) {
                 res = T.blist[q];  // ids increase along the list: the first holder is the lowest
                 break;
             }
+        }
     }
     cells[i] = res;
+}
+
+// a boundary edge (a, b) with the triangle's third vertex `in` on its interior side: the mesh is
+// concave at a vertex of the edge when the neighbouring boundary edge's far vertex w lies strictly
+// on the other side (exact signs)
+__global__ void tri_convex_kernel(const float2 *__restrict__ xy, const int *__restrict__ chk, long long n,
+                                  int *__restrict__ convex)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int *q = chk + 4 * i;
+    float v[4][2];
+    for (int k = 0; k < 4; ++k) {
+        const float2 p = xy[q[k]];
+        v[k][0] = p.x;
+        v[k][1] = p.y;
+    }
+    const int s_in = orient2d_sign(v[0], v[1], v[2]), s_w = orient2d_sign(v[0], v[1], v[3]);
+    if (s_in * s_w < 0) atomicExch(convex, 0);
+}
+
+// For every boundary vertex shared by exactly two boundary edges, two checks (edge, interior
+// vertex, far vertex of the other edge) as 4 node ids each; false when some boundary vertex is
+// not (then the mesh is not treated as convex).
+bool tri_convexity_checks(const int *tris, const int *nbrs, long long nc, std::vector<int> &chk)
+{
+    struct V {
+        int v;
+        long long tj;  // boundary edge: triangle * 3 + j
+        int w;         // the edge's other end
+    };
+    std::vector<V> e;
+    for (long long t = 0; t < nc; ++t)
+        for (int j = 0; j < 3; ++j) {
+            if (nbrs[3 * t + j] >= 0) continue;
+            const int a = tris[3 * t + (j + 1) % 3], b = tris[3 * t + (j + 2) % 3];
+            e.push_back({a, 3 * t + j, b});
+            e.push_back({b, 3 * t + j, a});
+        }
+    std::sort(e.begin(), e.end(), [](const V &x, const V &y) { return x.v != y.v ? x.v < y.v : x.tj < y.tj; });
+    for (size_t i = 0; i < e.size();) {
+        size_t k = i;
+        while (k < e.size() && e[k].v == e[i].v) ++k;
+        if (k - i != 2) return false;
+        for (int s = 0; s < 2; ++s) {
+            const long long t = e[i + s].tj / 3;
+            const int j = (int)(e[i + s].tj % 3);
+            chk.insert(chk.end(), {tris[3 * t + (j + 1) % 3], tris[3 * t + (j + 2) % 3], tris[3 * t + j],
+                                   e[i + 1 - s].w});
+        }
+        i = k;
+    }
+    return true;
 }
 
 // triangle across the edge opposite vertex j, by matching sorted vertex pairs
@@ -227,9 +286,28 @@ cudaError_t tri_build_store(lcs_field *f, const float *xy_host, const int *tris_
         tri_bin_sort_kernel<<<(unsigned)((nbins + bt - 1) / bt), bt, 0, s>>>(f->d_bstart, nbins, f->d_blist);
         e = cudaGetLastError();
     }
+    // convex (connected, every boundary vertex convex): then a walk that meets the boundary is outside
+    std::vector<int> chk;
+    int convex = mesh_connected(nbrs_host, nc, 3) && tri_convexity_checks(tris_host, nbrs_host, nc, chk) ? 1 : 0;
+    int *dchk = nullptr, *dflag = nullptr;
+    const long long nchk = (long long)chk.size() / 4;
+    if (e == cudaSuccess && convex && nchk > 0) {
+        e = cudaMallocAsync((void **)&dchk, sizeof(int) * chk.size(), s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void **)&dflag, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dchk, chk.data(), sizeof(int) * chk.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dflag, &convex, sizeof(int), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            tri_convex_kernel<<<(unsigned)((nchk + bt - 1) / bt), bt, 0, s>>>(f->d_xy, dchk, nchk, dflag);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&convex, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
     if (count) cudaFreeAsync(count, s);
     if (cursor) cudaFreeAsync(cursor, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host vectors above go out of scope
+    if (dchk) cudaFreeAsync(dchk, s);
+    if (dflag) cudaFreeAsync(dflag, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host values above go out of scope
+    f->convex = e == cudaSuccess ? convex : 0;
     return e;
 }
 
@@ -253,6 +331,7 @@ TriDev tri_dev(const lcs_field *f, int walk_limit)
     T.ncells = f->ncells;
     T.walk_limit = walk_limit > 0 ? walk_limit : 512;
     T.tol = 1e-6f;
+    T.convex = f->convex;
     return T;
 }
 

@@ -76,3 +76,17 @@ def tri_grid_mesh(n, seed=7):
                 tris.append(t[::-1] if rng.integers(2) else t)
     tris = np.array(tris, dtype=np.int32)
     return pts, tris, tri_neighbours(tris)
+
+
+def l_tri_grid_mesh(n, seed=7):
+    """tri_grid_mesh(n) without the squares with i >= n/2 and j >= n/2 (L-shaped: non-convex)."""
+    from paper_2209_13775_gb300.inputs import tri_neighbours
+
+    pts, tris, _ = tri_grid_mesh(n, seed)
+    c = pts[tris].mean(axis=1)
+    tris = tris[~((c[:, 0] > n / 2) & (c[:, 1] > n / 2))]
+    used = np.unique(tris)
+    remap = -np.ones(len(pts), dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    tris = remap[tris].astype(np.int32)
+    return pts[used], tris, tri_neighbours(tris)

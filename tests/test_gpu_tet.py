@@ -21,7 +21,7 @@ import torch
 from scipy.linalg import expm
 
 import oracle
-from meshes import kuhn_mesh
+from meshes import kuhn_mesh, l_kuhn_mesh
 from paper_2209_13775_gb300 import inputs, lcs
 from gpu_util import check_exit_statuses, round_bf16, round_fp16
 
@@ -111,6 +111,31 @@ def test_seed_cells_on_delaunay_pipe(ctx, pipe):
         g = gpu_tet(ctx, tet_desc(pipe.xyz, pipe.tets, nbrs, [0.0]), pipe.frames[:1], n, lo, hi, None)
         np.testing.assert_array_equal(g["cells"], want)
     assert (want < 0).sum() > 1000 and (want >= 0).sum() > 5000
+
+
+def test_seed_cells_and_stages_on_non_convex_mesh(ctx):
+    # an L-shaped prism: seed cells bit-exact (ties included); u = (1, -1, 0) with one step of h = 1
+    # from the y-arm puts every stage point inside but across the notch from the previous cell, so the
+    # walk meets a boundary face and the bin lists must settle it: x0 + (1, -1, 0), all OK
+    pts, tets, nbrs = l_kuhn_mesh(4)
+    F = oracle.TetField(pts, tets, nbrs, np.zeros((1, len(pts), 3), np.float32), [0.0])
+    n, lo, hi = (13, 13, 9), (-1.0, -1.0, 0.0), (5.0, 5.0, 4.0)
+    g = gpu_tet(ctx, tet_desc(pts, tets, nbrs, [0.0]), np.zeros((1, len(pts), 3), np.float32), n, lo, hi, None)
+    want = F.locate_seeds(ora_seeds(n, lo, hi))
+    np.testing.assert_array_equal(g["cells"], want)
+    assert (want < 0).sum() > 300 and (want >= 0).sum() > 300
+    fr = np.zeros((2, len(pts), 3), np.float32)
+    fr[..., 0], fr[..., 1] = 1.0, -1.0
+    # DP5(4) samples the line at c = 0.2, 0.3, 0.8, 8/9, 1: seeds less than 0.2 above y = 2 keep every
+    # stage point out of the notch
+    for method in (lcs.RK4, lcs.RK45):
+        n, lo, hi = ((5, 5, 4), (1.55, 2.05, 0.5), (1.95, 2.45, 3.5)) if method == lcs.RK4 else ((5, 5, 4), (1.55, 2.02, 0.5), (1.95, 2.18, 3.5))
+        opts = (lcs.advect_opts(lcs.RK4, t0=0.0, T=1.0, dt=1.0) if method == lcs.RK4 else
+                lcs.advect_opts(lcs.RK45, t0=0.0, T=1.0, h0=1.0, rtol=1e-3, atol=1e-3))
+        g = gpu_tet(ctx, tet_desc(pts, tets, nbrs, [0.0, 10.0]), fr, n, lo, hi, opts)
+        x0 = ora_seeds(n, lo, hi).astype(np.float64)
+        assert (g["status"][0] == lcs.TRACER_OK).all()
+        np.testing.assert_allclose(g["xyz"][0], x0 + np.array([[1.0], [-1.0], [0.0]]), rtol=0, atol=4e-6)
 
 
 # ------------------------------------------------------------------ RK4 on tets

@@ -19,7 +19,7 @@ import torch
 from scipy.linalg import expm
 
 import oracle
-from meshes import tri_grid_mesh
+from meshes import l_tri_grid_mesh, tri_grid_mesh
 from paper_2209_13775_gb300 import inputs, lcs
 from gpu_util import check_exit_statuses, check_ftle, round_bf16, round_fp16
 
@@ -118,6 +118,24 @@ def test_seed_cells_on_stenosis_mesh(ctx, sten):
         g = gpu_tri(ctx, sten_desc(sten, nbrs=nbrs), sten.frames, n, lo, hi, None)
         np.testing.assert_array_equal(g["cells"], want)
     assert (want < 0).sum() > 300 and (want >= 0).sum() > 5000
+
+
+def test_stages_across_the_notch_of_a_non_convex_mesh(ctx):
+    # u = (1, -1) with one step of h = 1 from the y-arm of an L-shaped mesh: every stage point is
+    # inside but across the notch from the previous cell; the bin lists settle the walk
+    pts, tris, nbrs = l_tri_grid_mesh(4)
+    fr = np.zeros((2, len(pts), 2), np.float32)
+    fr[..., 0], fr[..., 1] = 1.0, -1.0
+    # DP5(4) samples the line at c = 0.2, 0.3, 0.8, 8/9, 1: seeds less than 0.2 above y = 2 keep every
+    # stage point out of the notch
+    for method in (lcs.RK4, lcs.RK45):
+        n, lo, hi = ((9, 9), (1.55, 2.05), (1.95, 2.45)) if method == lcs.RK4 else ((9, 9), (1.55, 2.02), (1.95, 2.18))
+        opts = (lcs.advect_opts(lcs.RK4, t0=0.0, T=1.0, dt=1.0) if method == lcs.RK4 else
+                lcs.advect_opts(lcs.RK45, t0=0.0, T=1.0, h0=1.0, rtol=1e-3, atol=1e-3))
+        g = gpu_tri(ctx, tri_desc(pts, tris, nbrs, [0.0, 10.0]), fr, n, lo, hi, opts)
+        x0 = ora_seeds(n, lo, hi).astype(np.float64)
+        assert (g["status"][0] == lcs.TRACER_OK).all()
+        np.testing.assert_allclose(g["xyz"][0], x0 + np.array([[1.0], [-1.0]]), rtol=0, atol=4e-6)
 
 
 # ------------------------------------------------------------------ RK4 on triangles

@@ -115,6 +115,20 @@ def test_walk_on_non_convex_mesh(ora):
         np.testing.assert_allclose(u, A @ p.astype(np.float64), rtol=0, atol=1e-12)
 
 
+def test_rk4_stages_across_the_notch(ora):
+    # u = (1, -1, 0), one step of h = 1 from the y-arm of an L-shaped prism: every stage point is in
+    # the mesh (the later ones in the x-arm), but the straight line to them crosses the notch, so a
+    # walk that stopped at the boundary face would freeze the tracer; the flow map is x0 + (1, -1, 0)
+    pts, tets, nbrs = l_kuhn_mesh(4)
+    fr = np.zeros((2, len(pts), 3), np.float32)
+    fr[..., 0], fr[..., 1] = 1.0, -1.0
+    f = _field(ora, pts, tets, nbrs, fr, (0.0, 10.0))
+    x0 = ora.seed_grid(3, (5, 5, 4), (1.55, 2.05, 0.5), (1.95, 2.45, 3.5))
+    xT, st, _ = ora.rk4(f, x0.astype(np.float64), 0.0, 1.0, 1.0, cells=f.locate_seeds(x0))
+    assert (st == ora.OK).all()
+    np.testing.assert_allclose(xT, x0 + np.array([[1.0], [-1.0], [0.0]]), rtol=0, atol=1e-12)
+
+
 def test_walk_on_delaunay_pipe_mesh(ora):
     m = inputs.pipe_mesh(h=0.25, L=2.0)
     f = _field(ora, m.xyz, m.tets, m.nbrs)

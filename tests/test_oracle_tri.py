@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 from paper_2209_13775_gb300 import inputs
-from meshes import tri_grid_mesh
+from meshes import l_tri_grid_mesh, tri_grid_mesh
 
 
 @pytest.fixture(scope="module")
@@ -151,3 +151,16 @@ def test_rk4_and_dp45_on_tri_affine_field_and_leaving(ora):
     assert st[0] == ora.LEFT and abs(te[0] - 3.5) < 1e-9 and abs(xT[0, 0] - 2.0) < 1e-9
     _, st, _ = ora.rk4(f2, x0, 0.0, 1.0, 0.1, cells=np.array([-1], dtype=np.int32))
     assert st[0] == ora.OUTSIDE
+
+
+def test_rk4_stages_across_the_notch(ora):
+    # as on tets: u = (1, -1), one step of h = 1 from the y-arm of an L-shaped mesh; every stage point
+    # is inside but the straight line to the later ones crosses the notch
+    pts, tris, nbrs = l_tri_grid_mesh(4)
+    fr = np.zeros((2, len(pts), 2), np.float32)
+    fr[..., 0], fr[..., 1] = 1.0, -1.0
+    f = _field(ora, pts, tris, nbrs, fr, (0.0, 10.0))
+    x0 = ora.seed_grid(2, (9, 9), (1.55, 2.05), (1.95, 2.45))
+    xT, st, _ = ora.rk4(f, x0.astype(np.float64), 0.0, 1.0, 1.0, cells=f.locate_seeds(x0))
+    assert (st == ora.OK).all()
+    np.testing.assert_allclose(xT, x0 + np.array([[1.0], [-1.0]]), rtol=0, atol=1e-12)
