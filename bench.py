@@ -1099,8 +1099,9 @@ def next_arm(args, rank, world, local):
     ms_var = timed(var_step, 3)
     ms_fd = timed(fd_step, 3)
     out["variational_abc_256cubed"] = {"ms": ms_var, "seeds_per_s": N / ms_var * 1e3, "fd_step_ms": ms_fd,
-                                       "note": "one-pass kernel: x and the 3x3 M per tracer, frames from "
-                                               "global memory; fd_step = the default re-bundled path + FD"}
+                                       "note": "re-bundled episodes carrying the 3x3 M per tracer (time slices, "
+                                               "127 registers, 2 blocks of 256 per SM); fd_step = the default "
+                                               "re-bundled path + FD"}
     lcs.lcs_free_flowmap(fm)
     lcs.lcs_free_seeds(seeds)
     lcs.lcs_free_field(field)

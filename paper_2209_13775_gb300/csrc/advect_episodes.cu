@@ -189,13 +189,28 @@ __global__ void __launch_bounds__(1024) scan_down_kernel(const unsigned *__restr
     }
 }
 
+// record i to its bucket's next slot; the variational grad F ([9][N] planes) moves with it
 __global__ void ep_scatter_kernel(const Tracer *__restrict__ A, Tracer *__restrict__ B, long long N,
-                                  const unsigned *__restrict__ keys, unsigned *__restrict__ cursor)
+                                  const unsigned *__restrict__ keys, unsigned *__restrict__ cursor,
+                                  const float *__restrict__ MA, float *__restrict__ MB)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
     unsigned p = atomicAdd(cursor + keys[i], 1u);
     B[p] = A[i];
+    if (MA) {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) MB[e * N + p] = MA[e * N + i];
+    }
+}
+
+// grad F = I in seed order ([9][N] planes)
+__global__ void ep_var_init_kernel(float *__restrict__ M, long long N)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) M[e * N + i] = e % 4 == 0 ? 1.0f : 0.0f;
 }
 
 // ------------------------------------------------------------- time slices
@@ -431,6 +446,156 @@ __device__ __forceinline__ void rk4_step3q(const RectParams &P, const SliceGeom 
     for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
 }
 
+// ------------------------------------------------- variational equations
+
+// stencil_ext plus, for the Jacobian, the fractions and the per-axis factor d s / d x: 1 / h
+// where the query moves with x, 0 on a non-periodic axis where x lies outside the box (the
+// clamped query does not move)
+template <int PM>
+__device__ __forceinline__ int stencil_ext_grad(const RectParams &P, const SliceGeom &G, const float *x, float *w,
+                                                float *f, float *on)
+{
+    int r[3];
+    bool out = false;
+    int ix = axis_cell_ext<PM>(P, G, 0, x[0], f[0], r[0], out);
+    int iy = axis_cell_ext<PM>(P, G, 1, x[1], f[1], r[1], out);
+    int iz = axis_cell_ext<PM>(P, G, 2, x[2], f[2], r[2], out);
+    if (out) {
+        if (per_axis<PM>(P, 0)) ix = wrap_index_slow(r[0], P.n[0]) + G.H[0];
+        if (per_axis<PM>(P, 1)) iy = wrap_index_slow(r[1], P.n[1]) + G.H[1];
+        if (per_axis<PM>(P, 2)) iz = wrap_index_slow(r[2], P.n[2]) + G.H[2];
+    }
+    const float gx = 1.0f - f[0], gy = 1.0f - f[1], gz = 1.0f - f[2];
+    const float a = gy * gz, b = f[1] * gz, c = gy * f[2], d = f[1] * f[2];
+    w[0] = gx * a;
+    w[1] = f[0] * a;
+    w[2] = gx * b;
+    w[3] = f[0] * b;
+    w[4] = gx * c;
+    w[5] = f[0] * c;
+    w[6] = gx * d;
+    w[7] = f[0] * d;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        on[k] = (per_axis<PM>(P, k) || (x[k] >= P.origin[k] && x[k] <= P.hi_node[k])) ? P.inv_h[k] : 0.0f;
+    return ix + iy * G.N[0] + iz * (int)G.nxy;
+}
+
+// u(x) as interp3q and its Jacobian J[c][d] = sum_q (d w_q / d x_d) u_q[c], corner q with offsets
+// (q & 1, (q >> 1) & 1, q >> 2), the one-pass variational kernel's products in its order
+__device__ __forceinline__ void interp3q_grad(int v0, const float *w, const float *f, const float *on,
+                                              const float4 *__restrict__ pl, int slice, size_t plane_stride, int nxy,
+                                              QuadCache &cc, float *u, float (*J)[3])
+{
+    interp3q(v0, w, pl, slice, plane_stride, nxy, cc, u);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float wq = ((q >> d) & 1) ? 1.0f : -1.0f;
+#pragma unroll
+                for (int e = 0; e < 3; ++e)
+                    if (e != d) wq *= ((q >> e) & 1) ? f[e] : 1.0f - f[e];
+                const float4 qv = cc.q[q >> 2][c];
+                const float uq = (q & 3) == 0 ? qv.x : (q & 3) == 1 ? qv.y : (q & 3) == 2 ? qv.z : qv.w;
+                acc = fmaf(wq, uq, acc);
+            }
+            J[c][d] = acc * on[d];
+        }
+}
+
+// Steps [s0, min(s1, nsteps)) of every tracer record with the variational equations dM/dt = J M
+// next to Eq. 2: x follows rk4_step3q's arithmetic, M ([9][N] planes, slot-ordered like S) the
+// one-pass variational kernel's, so both match the other paths bit for bit.
+template <int PM>
+__global__ void __launch_bounds__(256, 2) ep_var3_kernel(RectParams P, SliceGeom G, const float4 *__restrict__ slices,
+                                                        size_t plane_stride, const int *__restrict__ smap, Rk4Args A,
+                                                        Tracer *__restrict__ S, float *__restrict__ M9, int job,
+                                                        int s0, int s1, int shift, unsigned *__restrict__ keys,
+                                                        unsigned *__restrict__ hist)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= A.N) return;
+    const long long N = A.N;
+    Tracer t = S[i];
+    float x[3] = {t.x, t.y, t.z};
+    if (t.st == LCS_TRACER_OK) {
+        int img[3] = {t.ix, t.iy, t.iz};
+        float M[3][3];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) M[e / 3][e % 3] = M9[e * N + i];
+        const int ns = A.job_nsteps[job];
+        const float h = A.job_h[job], hh = 0.5f * h, h6 = h * (1.0f / 6.0f);
+        const size_t ss = 3 * plane_stride;
+        const int nxy = (int)G.nxy;
+        const int e1 = min(s1, ns);
+        QuadCache cc;
+        cc.v0 = -1;
+        cc.slice = -1;
+        for (int n = s0; n < e1; ++n) {
+            const int *m = smap + 3 * (n - s0);
+            const int ms[3] = {__ldg(m), __ldg(m + 1), __ldg(m + 2)};
+            float k[4][3], S03[3][3], S12[3][3], Kp[3][3];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int sl = ms[q == 0 ? 0 : (q == 3 ? 2 : 1)];
+                const float c = q == 0 ? 0.0f : (q == 3 ? h : hh);
+                float y[3], Y[3][3], w[8], f[3], on[3], J[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    y[a] = q == 0 ? x[a] : fmaf(c, k[q - 1][a], x[a]);
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) Y[a][b] = q == 0 ? M[a][b] : fmaf(c, Kp[a][b], M[a][b]);
+                }
+                const int v = stencil_ext_grad<PM>(P, G, y, w, f, on);
+                interp3q_grad(v, w, f, on, slices + (size_t)sl * ss, sl, plane_stride, nxy, cc, k[q], J);
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int cc2 = 0; cc2 < 3; ++cc2) acc = fmaf(J[a][cc2], Y[cc2][b], acc);
+                        Kp[a][b] = acc;
+                        if (q == 0) S03[a][b] = acc;
+                        else if (q == 1) S12[a][b] = acc;
+                        else if (q == 2) S12[a][b] = S12[a][b] + acc;
+                        else S03[a][b] = S03[a][b] + acc;
+                    }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                x[a] = fmaf(h6, (k[0][a] + k[3][a]) + 2.0f * (k[1][a] + k[2][a]), x[a]);
+#pragma unroll
+                for (int b = 0; b < 3; ++b) M[a][b] = fmaf(h6, S03[a][b] + 2.0f * S12[a][b], M[a][b]);
+            }
+            wrap_periodic<3, PM>(P, x, img);
+            if (rect_left<3, PM>(P, x)) {
+                t.st = LCS_TRACER_LEFT;
+                t.te = fmaf((float)(n + 1), h, A.job_t0[job]);
+                break;
+            }
+        }
+        t.x = x[0];
+        t.y = x[1];
+        t.z = x[2];
+        t.ix = (short)img[0];
+        t.iy = (short)img[1];
+        t.iz = (short)img[2];
+        S[i] = t;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) M9[e * N + i] = M[e / 3][e % 3];
+    }
+    if (keys) {
+        unsigned k = cell_key(P, x, shift);
+        keys[i] = k;
+        atomicAdd(hist + k, 1u);
+    }
+}
+
 // ---------------------------------------------------------------- advection
 
 // tracer record t into output slot `slot`; snap >= 0: the slot is snapshot entry snap
@@ -505,13 +670,19 @@ __global__ void ep_snapshot_kernel(RectParams P, const Tracer *__restrict__ S, R
 }
 
 // final state of every tracer record into slot `job`, and into the job's snapshot slots whose
-// horizon is the whole integration
-__global__ void ep_finalize_kernel(RectParams P, const Tracer *__restrict__ S, Rk4Args A, int job)
+// horizon is the whole integration; with M9, the variational grad F of the job
+__global__ void ep_finalize_kernel(RectParams P, const Tracer *__restrict__ S, Rk4Args A, int job,
+                                   const float *__restrict__ M9)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= A.N) return;
     const Tracer t = S[i];
     ep_store(P, A, job, t, -1);
+    if (M9) {
+        float *o = A.out_grad + ((size_t)job * A.N + t.id) * 9;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) o[e] = M9[e * A.N + i];
+    }
     const int ns = A.job_nsteps[job];
     for (int q = 0; q < A.nsnap; ++q)
         if (snap_step(A, q, ns) == ns) ep_store(P, A, snap_slot(A, job, q), t, job * A.nsnap + q);
@@ -536,13 +707,14 @@ static size_t slice_bytes(const SliceGeom &G, int E)
            256;
 }
 
-size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int E)
+size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int E, bool variational)
 {
     const long long keys = key_space(f);
     long long nbins = ((keys - 1) >> sort_shift(keys)) + 1;
     long long nb = (nbins + SCAN_TILE - 1) / SCAN_TILE;
     size_t b = 2 * al256(sizeof(Tracer) * N) + al256(4 * N) + 2 * al256(4 * nbins) + al256(4 * nb);
     b += slice_bytes(slice_geom(f), E);
+    if (variational) b += 2 * al256(sizeof(float) * 9 * N);   // grad F planes, ping-pong with the records
     return b;
 }
 
@@ -585,6 +757,13 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
         p += al256(sizeof(SchedEntry) * 3 * E);
         nsl = (int *)p;
     }
+    // variational grad F: [9][N] planes after the rest of the working memory, moved with the records
+    const bool var = A.out_grad != nullptr;
+    float *MA = nullptr, *MB = nullptr;
+    if (var) {
+        MA = (float *)((char *)L.work + rk4_sorted_scratch_bytes(N, f, E, false));
+        MB = (float *)((char *)MA + al256(sizeof(float) * 9 * N));
+    }
     const int bt = 256;
     const unsigned grid = (unsigned)((N + bt - 1) / bt);
     const int abt = L.block_threads > 0 && L.block_threads <= 256 ? L.block_threads : 256;
@@ -593,6 +772,7 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
         const int ns = L.host_nsteps[job];
         cudaMemsetAsync(hist, 0, 4 * nbins, s);
         ep_init_kernel<<<grid, bt, 0, s>>>(P, A.seeds, N, SA, A.job_tend, job, shift, keys, hist);
+        if (var) ep_var_init_kernel<<<grid, bt, 0, s>>>(MA, N);
         int snext = 0;   // next snapshot before the end of the job: episodes end there
         while (snext < L.nsnap && L.host_snap_n[snext] <= 0) ++snext;
         for (int s0 = 0, s1; s0 < ns; s0 = s1) {
@@ -608,7 +788,7 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
             scan_reduce_kernel<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum);
             scan_top_kernel<<<1, 1024, 0, s>>>(bsum, (int)nb);
             scan_down_kernel<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum, cursor);
-            ep_scatter_kernel<<<grid, bt, 0, s>>>(SA, SB, N, keys, cursor);
+            ep_scatter_kernel<<<grid, bt, 0, s>>>(SA, SB, N, keys, cursor, MA, MB);
             if (!last) cudaMemsetAsync(hist, 0, 4 * nbins, s);
             lcs_tm_end(L.ctx, 1, s);
             lcs_tm_begin(L.ctx, 2, s);
@@ -620,7 +800,17 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
             // compile-time periodicity for the common all-periodic and non-periodic boxes
             const int pm = P.periodic[0] | (P.periodic[1] << 1) | (P.periodic[2] << 2);
             unsigned *kk = last ? nullptr : keys;
-            if (pm == 7)
+            if (var) {
+                if (pm == 7)
+                    ep_var3_kernel<7><<<agrid, abt, 0, s>>>(P, G, slices, plane_stride, smap, A, SB, MB, job, s0, s1,
+                                                           shift, kk, hist);
+                else if (pm == 0)
+                    ep_var3_kernel<0><<<agrid, abt, 0, s>>>(P, G, slices, plane_stride, smap, A, SB, MB, job, s0, s1,
+                                                           shift, kk, hist);
+                else
+                    ep_var3_kernel<-1><<<agrid, abt, 0, s>>>(P, G, slices, plane_stride, smap, A, SB, MB, job, s0,
+                                                            s1, shift, kk, hist);
+            } else if (pm == 7)
                 ep_advect3_kernel<7><<<agrid, abt, 0, s>>>(P, G, slices, plane_stride, smap, A, SB, job, s0, s1, shift,
                                                           kk, hist);
             else if (pm == 0)
@@ -635,8 +825,11 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
             Tracer *tmp = SA;
             SA = SB;
             SB = tmp;
+            float *mt = MA;
+            MA = MB;
+            MB = mt;
         }
-        ep_finalize_kernel<<<grid, bt, 0, s>>>(P, SA, A, job);
+        ep_finalize_kernel<<<grid, bt, 0, s>>>(P, SA, A, job, MA);
     }
     return cudaGetLastError();
 }

@@ -795,7 +795,11 @@ int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
     if (variant == 4 && !queue_ok) variant = 2;
     if (variant == 3 && !sorted_ok) variant = 1;
     cudaError_t e;
-    if (A.out_grad) {   // the variational equations: their own one-pass kernel
+    if (A.out_grad && variant == 3) {   // the variational equations in the re-bundled episodes
+        e = launch_rk4_episodes(P, f, A, L, s);
+        return e == cudaSuccess ? variant : -1;
+    }
+    if (A.out_grad) {   // the variational equations elsewhere: their own one-pass kernel
         const int bt = L.block_threads > 0 && L.block_threads <= 256 ? L.block_threads : 256;
         dim3 grid((unsigned)((A.N + bt - 1) / bt), (unsigned)L.njobs);
         const char *fr = (const char *)f->d_frames;

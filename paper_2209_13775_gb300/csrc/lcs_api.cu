@@ -716,7 +716,7 @@ static AdvectLayout advect_layout(const lcs_field *f, const lcs_seeds *s, const 
     Ly.sb = align256(sizeof(SchedEntry) * 3 * (size_t)J.njobs * std::max(J.nsteps_max, 1));
     Ly.want_work = f->dim == 3 && (o->variant == 3 || (o->variant == 0 && s->N >= LCS_SORTED_MIN_SEEDS));
     Ly.E = o->episode_steps > 0 ? std::min(o->episode_steps, 1024) : LCS_EPISODE_STEPS;
-    Ly.wb = Ly.want_work ? rk4_sorted_scratch_bytes(s->N, f, Ly.E) : 0;
+    Ly.wb = Ly.want_work ? rk4_sorted_scratch_bytes(s->N, f, Ly.E, o->variational != 0) : 0;
     if (f->dim == 2 && f->kind == LCS_RECTILINEAR && (o->variant == 5 || o->variant == 0)) {
         // 2D time slices: asked for (up to 16 GiB), or by default when they take at most 2 GiB
         const size_t b = rk4_slice2d_bytes(f, J.njobs, J.nsteps);

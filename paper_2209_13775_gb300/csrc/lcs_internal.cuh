@@ -238,7 +238,7 @@ struct Rk4Launch {
 // default RK4 steps per re-bundled episode
 #define LCS_EPISODE_STEPS 32
 
-size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int episode_steps);
+size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int episode_steps, bool variational);
 // variant 5 (2D time slices): their bytes for these jobs, and the most lcs_advect reserves for them
 size_t rk4_slice2d_bytes(const lcs_field *f, int njobs, const int *host_nsteps);
 #define LCS_SLICE2D_MAX_BYTES (16ULL << 30)

@@ -211,3 +211,49 @@ def test_variational_rejects(ctx):
         lcs.lcs_free_seeds(aux)
         lcs.lcs_free_seeds(seeds)
         lcs.lcs_free_field(field)
+
+
+def grad_run(ctx, g, n, lo, hi, periodic, dt, t0, T, storage, variant, variational):
+    field = lcs.lcs_load_field(ctx, rect_desc(g, storage), g.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(g.dim, n, lo, hi, periodic))
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, t0=t0, T=T, dt=dt, variant=variant,
+                                                      variational=variational), fm)
+    out = {"x": np.empty((g.dim, N), dtype=np.float32), "st": np.empty(N, dtype=np.uint8),
+           "te": np.empty(N, dtype=np.float32)}
+    lcs.lcs_flowmap_get(ctx, fm, 0, out["x"], out["st"], out["te"])
+    if variational:
+        out["M"] = np.empty((N, g.dim, g.dim), dtype=np.float32)
+        lcs.lcs_flowmap_grad(ctx, fm, 0, out["M"])
+    lcs.lcs_synchronize(ctx)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return out
+
+
+@pytest.mark.parametrize("storage,bounded", [(lcs.F32, False), (lcs.F16, False), (lcs.F32, True)])
+def test_variational_episodes_equal_one_pass(ctx, storage, bounded):
+    # the re-bundled episodes (variant 3) carry M with the tracer records through the sort; the
+    # Jacobian comes from the same time-slice corners with the one-pass kernel's products, so M, x,
+    # status and exit times equal the one-pass variational kernel's bit for bit, and x the plain
+    # episode path's
+    g = inputs.abc(n=32, nframes=17, t_end=2.0)
+    if storage == lcs.F16:
+        g = replace(g, frames=round_fp16(g.frames))
+    L = 2 * np.pi
+    if bounded:
+        g = replace(g, periodic=(0, 0, 0))
+        n, lo, hi, per, T = (20, 18, 17), (0.3, 0.2, 0.4), (5.5, 5.7, 5.6), (0, 0, 0), 1.5
+    else:
+        n, lo, hi, per, T = (21, 19, 18), (0.0, 0.0, 0.0), (L, L, L), (1, 1, 1), 2.0
+    ep = grad_run(ctx, g, n, lo, hi, per, 0.02, 0.0, T, storage, 3, True)
+    one = grad_run(ctx, g, n, lo, hi, per, 0.02, 0.0, T, storage, 1, True)
+    plain = grad_run(ctx, g, n, lo, hi, per, 0.02, 0.0, T, storage, 3, False)
+    for k in ("x", "st", "te", "M"):
+        np.testing.assert_array_equal(ep[k], one[k])
+    for k in ("x", "st", "te"):
+        np.testing.assert_array_equal(ep[k], plain[k])
+    if bounded:
+        assert (ep["st"] != 0).sum() > 100
