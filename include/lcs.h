@@ -195,8 +195,8 @@ lcs_status lcs_seed_aux(lcs_ctx *ctx, const lcs_seeds *lattice, const double *de
  *            (32 consecutive seed ids): a step is accepted only when every
  *            live lane accepts (err <= 1, err = max_i |e_i| / (atol + rtol *
  *            max(|x_i|, |x_new_i|))), and the next step is the smallest lane
- *            proposal h * min(5, max(0.2, 0.9 err^-1/5)).  On tets,
- *            triangles and 3D rectilinear fields.
+ *            proposal h * min(5, max(0.2, 0.9 err^-1/5)).  On every
+ *            field kind.
  *  LCS_SURROGATE  2D non-periodic rectilinear fields, one job, T = K tau > 0
  *            with tau the network's step and tau = S dt: per sub-interval k
  *            every tracer proposes x + displacement(x, t0 + k tau); in each

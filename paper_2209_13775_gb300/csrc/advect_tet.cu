@@ -1,5 +1,5 @@
-// advect_tet.cu -- advection on tetrahedral meshes (RK4) and adaptive Dormand-Prince
-// 5(4) with one step size per warp (tets and 3D rectilinear fields).
+// advect_tet.cu -- advection on tetrahedral and triangle meshes (RK4) and adaptive
+// Dormand-Prince 5(4) with one step size per warp (meshes and rectilinear fields).
 //
 // Paper: Eq. 2 integrated with a Runge-Kutta method (Sec. 2 "Flow Map"); on
 // unstructured data every stage evaluation needs a cell search (Sec. 3.1: local
@@ -179,6 +179,22 @@ struct TriEval {
     }
 };
 
+// velocity at (x, t) on a 2D rectilinear field of per-frame slabs (queries clamped into the box)
+template <int ST>
+struct Rect2Eval {
+    static constexpr int DIM = 2;
+    RectParams P;
+    const char *frames;
+    size_t fstride;
+    __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u) const
+    {
+        Stencil<2> S;
+        make_stencil<2>(P, x, S);
+        interp<2, ST, SRC_GLOBAL>(S, frames + (size_t)k * fstride, frames + (size_t)(k + 1) * fstride, a, u);
+        return TET_INSIDE;
+    }
+};
+
 template <int ST>
 struct Rect3Eval {
     static constexpr int DIM = 3;
@@ -331,7 +347,7 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
                     k1[q] = kk[6][q];
                 }
                 ++steps;
-                if (D == 3 && A.rect_left && rect_left<3>(P, x)) {
+                if (A.rect_left && rect_left<D>(P, x)) {
                     st = LCS_TRACER_LEFT;
                     te = last ? tend : t + hs;
                 }
@@ -439,6 +455,15 @@ cudaError_t launch_dp45(lcs_ctx *ctx, const lcs_field *f, const Dp45Args &A0, in
             e = dp45_go(TetEval<LCS_F16>{T}, A, P, njobs, bt, s);
         else
             e = dp45_go(TetEval<LCS_BF16>{T}, A, P, njobs, bt, s);
+    } else if (f->dim == 2) {
+        A.rect_left = 1;
+        const char *fr = (const char *)f->d_frames;
+        if (f->storage == LCS_F32)
+            e = dp45_go(Rect2Eval<LCS_F32>{P, fr, f->frame_stride}, A, P, njobs, bt, s);
+        else if (f->storage == LCS_F16)
+            e = dp45_go(Rect2Eval<LCS_F16>{P, fr, f->frame_stride}, A, P, njobs, bt, s);
+        else
+            e = dp45_go(Rect2Eval<LCS_BF16>{P, fr, f->frame_stride}, A, P, njobs, bt, s);
     } else {
         A.rect_left = 1;
         if (f->storage == LCS_F32)

@@ -796,12 +796,10 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     return LCS_OK;
 }
 
-// Adaptive DP5(4) with one step per warp (tets, 3D rectilinear fields)
+// Adaptive DP5(4) with one step per warp (every field kind)
 static lcs_status advect_rk45(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,
                               lcs_flowmap *fm)
 {
-    if (f->dim != 3 && f->kind != LCS_TRI)
-        return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: RK45 on 2D rectilinear fields not built in");
     const int njobs = o->njobs > 1 ? o->njobs : 1;
     const double rtol = o->rtol > 0 ? o->rtol : 1e-6, atol = o->atol > 0 ? o->atol : 1e-6;
     const double h0 = o->h0 != 0 ? fabs(o->h0) : 0.01;

@@ -267,6 +267,57 @@ def test_rk45_rect_affine_matches_expm_and_oracle(ctx):
     assert np.abs(ns.astype(np.int64) - nso).max() <= 3
 
 
+def gpu_rect2_rk45(ctx, g, n, lo, hi, opts):
+    desc = lcs.field_desc(2, g.n, g.origin, g.spacing, g.periodic, g.times, g.time_periodic, g.period)
+    field = lcs.lcs_load_field(ctx, desc, g.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, lo, hi))
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    lcs.lcs_advect(ctx, field, seeds, opts, fm)
+    x = np.empty((2, N), dtype=np.float32)
+    s = np.empty(N, dtype=np.uint8)
+    ns = np.empty(N, dtype=np.int32)
+    lcs.lcs_flowmap_get(ctx, fm, 0, x, s)
+    lcs.lcs_flowmap_steps(ctx, fm, 0, ns)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return x, s, ns
+
+
+def test_rk45_rect2d_affine_and_gyre(ctx):
+    # 2D rectilinear DP5(4): the closed form on an affine spiral (bilinear interpolation is exact), and the
+    # double gyre against a converged oracle run, held to twice the oracle's own error at the same
+    # tolerance (bilinear kinks at cell edges escape the embedded estimate, as P1 kinks do on meshes)
+    A = np.array([[-0.25, -1.0], [1.0, -0.25]])
+    g = inputs.affine_frames(A, np.zeros((2, 2)), np.zeros(2), (17, 17), (-2.0, -2.0), (0.25, 0.25), [0.0, 100.0])
+    n, lo, hi, T = (12, 10), (-1.2, -1.1), (1.2, 1.1), 3.0
+    x, s, ns = gpu_rect2_rk45(ctx, g, n, lo, hi, lcs.advect_opts(lcs.RK45, t0=0.0, T=T, rtol=1e-5, atol=1e-5,
+                                                                 h0=0.01))
+    x0 = oracle.seed_grid(2, n, lo, hi).astype(np.float64)
+    assert (s == lcs.TRACER_OK).all()
+    assert np.abs(x - expm(T * A) @ x0).max() <= 2e-4
+    F = oracle.RectField(g.frames, g.times, g.origin, g.spacing)
+    xo, _, _, nso = oracle.dp45(F, x0, 0.0, T, h0=0.01, rtol=1e-5, atol=1e-5, group=32)
+    assert np.abs(x - xo).max() <= 1e-4 and np.abs(ns.astype(np.int64) - nso).max() <= 3
+    gy = inputs.double_gyre()
+    n, lo, hi, T = (64, 32), (0.0, 0.0), (2.0, 1.0), 5.0
+    x, s, ns = gpu_rect2_rk45(ctx, gy, n, lo, hi, lcs.advect_opts(lcs.RK45, t0=0.0, T=T, rtol=1e-6, atol=1e-6,
+                                                                  h0=0.01))
+    F = oracle.RectField(gy.frames, gy.times, gy.origin, gy.spacing, gy.periodic, gy.time_periodic, gy.period)
+    x0 = oracle.seed_grid(2, n, lo, hi).astype(np.float64)
+    xo, so, _, nso = oracle.dp45(F, x0, 0.0, T, h0=0.01, rtol=1e-6, atol=1e-6, group=32)
+    xr, sr, _, _ = oracle.dp45(F, x0, 0.0, T, h0=0.01, rtol=1e-11, atol=1e-11)
+    np.testing.assert_array_equal(s, so)
+    ok = (so == oracle.OK) & (sr == oracle.OK)
+    e_ora = np.abs(xo[:, ok] - xr[:, ok]).max(axis=0)
+    e_gpu = np.abs(x[:, ok] - xr[:, ok]).max(axis=0)
+    assert np.median(e_gpu) <= 2 * np.median(e_ora) + 1e-6, (np.median(e_gpu), np.median(e_ora))
+    assert e_gpu.max() <= 2 * e_ora.max() + 1e-5, (e_gpu.max(), e_ora.max())
+    steps = np.abs(ns.astype(np.int64) - nso)
+    assert np.median(steps) <= 1 and steps.max() <= 10
+
+
 def test_rk45_rect_uniform_stream_leaves(ctx):
     # a uniform stream has a zero error estimate up to FP32 rounding of the interpolation weights
     # (about 1e-3 of a 1e-6 tolerance, 1e-6 of a 1e-3 one): at tolerance 1e-3 every step grows
@@ -335,8 +386,8 @@ def test_rk45_and_tet_argument_errors(ctx, pipe):
     seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (8, 8), (0, 0), (2, 1)))
     fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
     with pytest.raises(lcs.LcsError) as e:
-        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK45, T=1.0), fm)
-    assert e.value.status == 7                      # LCS_EUNSUPPORTED: no 2D adaptive path
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK45, T=1.0, snap_T=[0.5]), fm)
+    assert e.value.status == 7                      # LCS_EUNSUPPORTED: no adaptive snapshots
     lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=1.0, dt=0.1), fm)
     with pytest.raises(lcs.LcsError) as e:          # no adaptive integration wrote step counts
         lcs.lcs_flowmap_steps(ctx, fm, 0, np.empty(64, dtype=np.int32))
