@@ -208,7 +208,7 @@ lcs_status lcs_seed_aux(lcs_ctx *ctx, const lcs_seeds *lattice, const double *de
  *            gate_tol = 0 reproduces it bit for bit.
  * Batches: njobs > 1 integrates the same seeds for each (job_t0[j], job_T[j])
  * pair in one persistent launch.
- * Snapshots (LCS_RK4 on rectilinear fields): nsnap > 0 also keeps the flow
+ * Snapshots (LCS_RK4, every field kind): nsnap > 0 also keeps the flow
  * map at intermediate horizons of every integration, so one run yields the
  * Cauchy-Green tensor at several times (Sec. 3.1 and Sec. 4: the flow map of
  * an interval from the steps of a longer integration).  Snapshot s of job j
@@ -263,7 +263,7 @@ lcs_status lcs_flowmap_create(lcs_ctx *ctx, const lcs_seeds *seeds, int njobs, l
  * after a step, at that step's end time; tets and triangles when a stage
  * point falls outside the mesh, at the start of that step).
  * Errors: LCS_EINVAL (options, a flow map with too few slots),
- * LCS_EUNSUPPORTED (e.g. snapshots with RK45, the surrogate or tets), LCS_ECUDA. */
+ * LCS_EUNSUPPORTED (e.g. snapshots with RK45 or the surrogate), LCS_ECUDA.      */
 lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *seeds,
                       const lcs_advect_opts *opts, lcs_flowmap *fm);
 

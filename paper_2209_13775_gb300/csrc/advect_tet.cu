@@ -20,6 +20,18 @@
 
 // ------------------------------------------------------------------ RK4 on tets
 
+// tracer state into flow-map slot `slot` (mesh fields: no periodic images)
+template <int DIM>
+__device__ __forceinline__ void mesh_store(const Rk4Args &A, int slot, long long i, const float *x, unsigned char st,
+                                           float te)
+{
+    float *o = A.out_xyz + (size_t)slot * DIM * A.N;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o[d * A.N + i] = x[d];
+    A.out_status[(size_t)slot * A.N + i] = st;
+    A.out_texit[(size_t)slot * A.N + i] = te;
+}
+
 template <int ST>
 __global__ void __launch_bounds__(256) rk4_tet_kernel(TetDev T, Rk4Args A, const int *__restrict__ cells0,
                                                       unsigned *errword)
@@ -38,6 +50,7 @@ __global__ void __launch_bounds__(256) rk4_tet_kernel(TetDev T, Rk4Args A, const
     const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
     const int ns = A.job_nsteps[job];
     const float h = A.job_h[job], hh = 0.5f * h;
+    int si = 0;   // next snapshot
     for (int n = 0; n < ns && st == LCS_TRACER_OK; ++n) {
         const SchedEntry e[3] = {load_sched(sc + 3 * n), load_sched(sc + 3 * n + 1), load_sched(sc + 3 * n + 2)};
         float k[4][3], y[3], lam[4];
@@ -61,13 +74,12 @@ __global__ void __launch_bounds__(256) rk4_tet_kernel(TetDev T, Rk4Args A, const
         const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
         for (int q = 0; q < 3; ++q) x[q] = fmaf(h6, (k[0][q] + k[3][q]) + 2.0f * (k[1][q] + k[2][q]), x[q]);
+        for (; si < A.nsnap && snap_step(A, si, ns) == n + 1; ++si)
+            mesh_store<3>(A, snap_slot(A, job, si), i, x, st, snap_exit(A, job, si, st, te));
     }
-    float *o = A.out_xyz + (size_t)job * 3 * A.N;
-    o[i] = x[0];
-    o[A.N + i] = x[1];
-    o[2 * A.N + i] = x[2];
-    A.out_status[(size_t)job * A.N + i] = st;
-    A.out_texit[(size_t)job * A.N + i] = te;
+    for (; si < A.nsnap; ++si)  // snapshots after the tracer stopped
+        mesh_store<3>(A, snap_slot(A, job, si), i, x, st, snap_exit(A, job, si, st, te));
+    mesh_store<3>(A, job, i, x, st, te);
 }
 
 // ------------------------------------------------------------- RK4 on triangles
@@ -90,6 +102,7 @@ __global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const
     const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
     const int ns = A.job_nsteps[job];
     const float h = A.job_h[job], hh = 0.5f * h;
+    int si = 0;   // next snapshot
     for (int n = 0; n < ns && st == LCS_TRACER_OK; ++n) {
         const SchedEntry e[3] = {load_sched(sc + 3 * n), load_sched(sc + 3 * n + 1), load_sched(sc + 3 * n + 2)};
         float k[4][2], y[2], lam[3];
@@ -113,12 +126,12 @@ __global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const
         const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
         for (int q = 0; q < 2; ++q) x[q] = fmaf(h6, (k[0][q] + k[3][q]) + 2.0f * (k[1][q] + k[2][q]), x[q]);
+        for (; si < A.nsnap && snap_step(A, si, ns) == n + 1; ++si)
+            mesh_store<2>(A, snap_slot(A, job, si), i, x, st, snap_exit(A, job, si, st, te));
     }
-    float *o = A.out_xyz + (size_t)job * 2 * A.N;
-    o[i] = x[0];
-    o[A.N + i] = x[1];
-    A.out_status[(size_t)job * A.N + i] = st;
-    A.out_texit[(size_t)job * A.N + i] = te;
+    for (; si < A.nsnap; ++si)  // snapshots after the tracer stopped
+        mesh_store<2>(A, snap_slot(A, job, si), i, x, st, snap_exit(A, job, si, st, te));
+    mesh_store<2>(A, job, i, x, st, te);
 }
 
 // ------------------------------------------------------- time bracket (FP32)
@@ -382,6 +395,10 @@ cudaError_t launch_rk4_tet(lcs_ctx *ctx, const Rk4Launch &L, const int *cells0, 
     A.out_xyz = L.out_xyz;
     A.out_status = L.out_status;
     A.out_texit = L.out_texit;
+    A.njobs = L.njobs;
+    A.nsnap = L.nsnap;
+    A.snap_n = L.snap_n;
+    A.snap_te = L.snap_te;
     if (L.N == 0) return cudaSuccess;
     const int bt = L.block_threads > 0 && L.block_threads <= 256 ? L.block_threads : 128;
     dim3 grid((unsigned)((L.N + bt - 1) / bt), (unsigned)L.njobs);

@@ -1016,8 +1016,8 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
                         "lcs_advect: the variational equations need LCS_RK4 on a rectilinear field, a lattice and "
                         "no snapshots");
     if (o->nsnap > 0) {
-        if (o->method != LCS_RK4 || f->kind != LCS_RECTILINEAR)
-            return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: snapshots need LCS_RK4 on a rectilinear field");
+        if (o->method != LCS_RK4)
+            return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: snapshots need LCS_RK4");
         if ((long long)njobs * (1 + o->nsnap) > fm->njobs)
             return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: %d jobs with %d snapshots need %lld flow-map slots, not %d",
                             njobs, o->nsnap, (long long)njobs * (1 + o->nsnap), fm->njobs);

@@ -153,3 +153,33 @@ def check_exit_statuses(st_g, te_g, st_o, te_o, dt, frac=2e-3):
     same = ~diff & (dte <= 1e-4 * dt)
     assert ((~diff) & ~same).sum() <= frac * len(st_g)
     return same
+
+
+def mesh_snapshots_equal_separate_runs(ctx, desc, frames, dim, n, lo, hi, jobs, snap_T, dt):
+    """A run with snapshots against separate runs over each snapshot horizon: bit for bit."""
+    field = lcs.lcs_load_field(ctx, desc, frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(dim, n, lo, hi), field)
+    N = lcs.lcs_seeds_count(seeds)
+    nj, ns = len(jobs[0]), len(snap_T)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, nj * (1 + ns))
+    lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, dt=dt, job_t0=jobs[0], job_T=jobs[1], snap_T=snap_T), fm)
+    one = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    left = 0
+    for j, (t0, T) in enumerate(zip(*jobs)):
+        for q, a in enumerate(list(snap_T) + [abs(T)]):
+            slot = j if q == ns else nj + j * ns + q
+            h = min(a, abs(T))
+            lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, t0=t0, T=h if T > 0 else -h, dt=dt), one)
+            got = [np.empty((dim, N), np.float32), np.empty(N, np.uint8), np.empty(N, np.float32)]
+            want = [np.empty((dim, N), np.float32), np.empty(N, np.uint8), np.empty(N, np.float32)]
+            lcs.lcs_flowmap_get(ctx, fm, slot, *got)
+            lcs.lcs_flowmap_get(ctx, one, 0, *want)
+            for a_, b_ in zip(got, want):
+                np.testing.assert_array_equal(a_, b_)
+            left += int((want[1] == lcs.TRACER_LEFT).sum())
+    lcs.lcs_synchronize(ctx)
+    for fmx in (fm, one):
+        lcs.lcs_free_flowmap(fmx)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return left

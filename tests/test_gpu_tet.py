@@ -23,7 +23,7 @@ from scipy.linalg import expm
 import oracle
 from meshes import kuhn_mesh, l_kuhn_mesh
 from paper_2209_13775_gb300 import inputs, lcs
-from gpu_util import check_exit_statuses, round_bf16, round_fp16
+from gpu_util import check_exit_statuses, mesh_snapshots_equal_separate_runs, round_bf16, round_fp16
 
 pytestmark = pytest.mark.gpu
 
@@ -217,6 +217,13 @@ def test_rk4_tet_backward_and_batched_jobs(ctx, pipe):
     same = check_exit_statuses(one["status"][0], one["t_exit"][0], st, te, 0.02)
     assert np.abs(one["xyz"][0][:, same] - xT[:, same]).max() <= 2e-5
     assert (st == oracle.LEFT).sum() > 50     # backwards through the inlet z = 0
+
+
+def test_snapshots_on_tets(ctx, pipe):
+    desc = tet_desc(pipe.xyz, pipe.tets, pipe.nbrs, pipe.times, lcs.F32, True, pipe.period)
+    left = mesh_snapshots_equal_separate_runs(ctx, desc, pipe.frames, 3, (12, 12, 16), (-0.6, -0.6, 0.2),
+                                              (0.6, 0.6, 1.8), ([0.1, 0.9], [0.6, -0.8]), [0.2, 0.4], 0.02)
+    assert left > 50
 
 
 # ------------------------------------------------------------------ DP5(4)

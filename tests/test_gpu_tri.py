@@ -21,7 +21,7 @@ from scipy.linalg import expm
 import oracle
 from meshes import l_tri_grid_mesh, tri_grid_mesh
 from paper_2209_13775_gb300 import inputs, lcs
-from gpu_util import check_exit_statuses, check_ftle, round_bf16, round_fp16
+from gpu_util import check_exit_statuses, check_ftle, mesh_snapshots_equal_separate_runs, round_bf16, round_fp16
 
 pytestmark = pytest.mark.gpu
 
@@ -224,6 +224,12 @@ def test_rk4_tri_backward_batched_and_ftle(ctx, sten):
     check_ftle(both["ftle"][0], sig)
 
 
+def test_snapshots_on_triangles(ctx, sten):
+    left = mesh_snapshots_equal_separate_runs(ctx, sten_desc(sten), sten.frames, 2, (100, 33), (0.05, -0.96),
+                                              (9.95, 0.96), ([0.1, 0.9], [0.6, -0.8]), [0.2, 0.5], 0.02)
+    assert left > 100
+
+
 # ------------------------------------------------------------------ DP5(4)
 
 def test_rk45_tri_affine_closed_form(ctx):
@@ -294,9 +300,9 @@ def test_tri_argument_errors(ctx, sten):
         assert e.value.status == 1
         seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (8, 8), (0.0, -1.0), (10.0, 1.0)), field)
         fm2 = lcs.lcs_flowmap_create(ctx, seeds, 1)
-        for kw in (dict(snap_T=[0.25]), dict(variational=True)):
+        for kw in (dict(method=lcs.RK45, snap_T=[0.25]), dict(method=lcs.RK4, dt=0.05, variational=True)):
             with pytest.raises(lcs.LcsError) as e:
-                lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=0.5, dt=0.05, **kw), fm2)
+                lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(T=0.5, **kw), fm2)
             assert e.value.status == 7
         lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=0.5, dt=0.05), fm2)
         lcs.lcs_synchronize(ctx)
