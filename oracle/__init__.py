@@ -88,6 +88,10 @@ def lib() -> ctypes.CDLL:
             L.ora_rk4.argtypes = [I, P, I, LL, P, P, D, D, D, P, P, P]
             L.ora_rk4_var.argtypes = [P, LL, P, D, D, D, P, P, P, P]
             L.ora_rk4_var.restype = LL
+            L.ora_rk4_var_kind.argtypes = [I, P, I, LL, P, P, D, D, D, P, P, P, P]
+            L.ora_rk4_var_kind.restype = LL
+            L.ora_tet_velocity_grad.argtypes = [P, P, D, P, P, P]
+            L.ora_tri_velocity_grad.argtypes = [P, P, D, P, P, P]
             L.ora_rect_velocity_grad.argtypes = [P, P, D, P, P]
             L.ora_rk4.restype = LL
             L.ora_dp45.argtypes = [I, P, I, LL, P, P, D, D, D, D, D, LL, I, I, P, P, P, P]
@@ -370,27 +374,33 @@ def lattice_spacing(dim, n, lo, hi, endpoint=(1, 1, 1)):
     return np.array([(hi[a] - lo[a]) / ((n[a] - 1) if endpoint[a] else n[a]) for a in range(dim)])
 
 
-def rk4_var(field, x0, t0, T, dt):
-    """RK4 with the variational equations dM/dt = J M (rectilinear fields).  x0 [dim][N] ->
-    (xT, M [N][dim][dim], status, t_exit)."""
+def rk4_var(field, x0, t0, T, dt, cells=None):
+    """RK4 with the variational equations dM/dt = J M (any field kind; cells as for rk4).
+    x0 [dim][N] -> (xT, M [N][dim][dim], status, t_exit)."""
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     dim, n = x0.shape
     xT = np.empty_like(x0)
     M = np.empty((n, dim, dim))
     st = np.empty(n, dtype=np.uint8)
     te = np.empty(n, dtype=np.float64)
-    lib().ora_rk4_var(ctypes.byref(field.struct), n, _p(x0), float(t0), float(T), float(dt), _p(xT), _p(M),
-                      _p(st), _p(te))
+    c = None if cells is None else np.ascontiguousarray(cells, dtype=np.int32)
+    lib().ora_rk4_var_kind(field.kind, ctypes.byref(field.struct), dim, n, _p(x0), None if c is None else _p(c),
+                           float(t0), float(T), float(dt), _p(xT), _p(M), _p(st), _p(te))
     return xT, M, st, te
 
 
-def velocity_grad(field, x, t):
-    """u(x, t) and its spatial Jacobian (rectilinear fields)."""
+def velocity_grad(field, x, t, cell=0):
+    """u(x, t) and its spatial Jacobian (rectilinear fields; on meshes also the cell, None outside)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     u = np.empty(field.dim)
     J = np.empty((field.dim, field.dim))
-    lib().ora_rect_velocity_grad(ctypes.byref(field.struct), _p(x), float(t), _p(u), _p(J))
-    return u, J
+    if field.kind == 0:
+        lib().ora_rect_velocity_grad(ctypes.byref(field.struct), _p(x), float(t), _p(u), _p(J))
+        return u, J
+    c = ctypes.c_int(int(cell))
+    fn = lib().ora_tri_velocity_grad if field.kind == 3 else lib().ora_tet_velocity_grad
+    out = fn(ctypes.byref(field.struct), _p(x), float(t), ctypes.byref(c), _p(u), _p(J))
+    return (None, None) if out else (u, J)
 
 
 def rk4(field, x0, t0, T, dt, cells=None):

@@ -766,6 +766,93 @@ int ora_tri_velocity(const ora_tri_field *f, const double *x, double t, int *cel
     return 0;
 }
 
+/* u(x, t) and its spatial Jacobian on meshes: P1 is affine inside a cell, so J is constant
+ * there, J[c][d] = sum_v u_v[c] d lambda_v / d x_d with the lambda gradients from Cramer's
+ * rule (lambda_1 = (x - v0) . (e2 x e3) / D and cyclically; lambda_0 = 1 - the others).  */
+int ora_tet_velocity_grad(const ora_tet_field *f, const double *x, double t, int *cell, double *u, double *J)
+{
+    double lam[4];
+    long long c = tet_locate_fp64(f, *cell, x, lam);
+    if (c < 0) return 1;
+    *cell = (int)c;
+    double v[4][3], e[3][3], g[4][3];
+    for (int i = 0; i < 4; ++i)
+        for (int d = 0; d < 3; ++d) v[i][d] = tet_vertex(f, c, i)[d];
+    for (int r = 0; r < 3; ++r)
+        for (int d = 0; d < 3; ++d) e[r][d] = v[r + 1][d] - v[0][d];
+    const double D = det3d(e[0], e[1], e[2]);
+    for (int r = 0; r < 3; ++r) {   /* gradient of lambda_{r+1}: e_{r+1} x e_{r+2} / D */
+        const double *a = e[(r + 1) % 3], *b = e[(r + 2) % 3];
+        g[r + 1][0] = (a[1] * b[2] - a[2] * b[1]) / D;
+        g[r + 1][1] = (a[2] * b[0] - a[0] * b[2]) / D;
+        g[r + 1][2] = (a[0] * b[1] - a[1] * b[0]) / D;
+    }
+    for (int d = 0; d < 3; ++d) g[0][d] = -(g[1][d] + g[2][d] + g[3][d]);
+    int k;
+    double a;
+    ora_time_locate(f->times, f->nframes, f->time_periodic, f->period, t, &k, &a);
+    int k1 = (f->nframes > 1) ? k + 1 : k;
+    const float *fa = f->frames + 3LL * f->nnodes * k;
+    const float *fb = f->frames + 3LL * f->nnodes * k1;
+    for (int comp = 0; comp < 3; ++comp) {
+        double sa = 0.0, sb = 0.0, ja[3] = {0, 0, 0}, jb[3] = {0, 0, 0};
+        for (int i = 0; i < 4; ++i) {
+            long long node = f->tets[4 * c + i];
+            const double ua = fa[3 * node + comp], ub = fb[3 * node + comp];
+            sa += lam[i] * ua;
+            sb += lam[i] * ub;
+            for (int d = 0; d < 3; ++d) {
+                ja[d] += g[i][d] * ua;
+                jb[d] += g[i][d] * ub;
+            }
+        }
+        u[comp] = (1.0 - a) * sa + a * sb;
+        for (int d = 0; d < 3; ++d) J[comp * 3 + d] = (1.0 - a) * ja[d] + a * jb[d];
+    }
+    return 0;
+}
+
+int ora_tri_velocity_grad(const ora_tri_field *f, const double *x, double t, int *cell, double *u, double *J)
+{
+    double lam[3];
+    long long c = tri_locate_fp64(f, *cell, x, lam);
+    if (c < 0) return 1;
+    *cell = (int)c;
+    const float *p0 = tri_vertex(f, c, 0), *p1 = tri_vertex(f, c, 1), *p2 = tri_vertex(f, c, 2);
+    const double e1[2] = {(double)p1[0] - p0[0], (double)p1[1] - p0[1]};
+    const double e2[2] = {(double)p2[0] - p0[0], (double)p2[1] - p0[1]};
+    const double D = e1[0] * e2[1] - e1[1] * e2[0];
+    double g[3][2];
+    g[1][0] = e2[1] / D;        /* lambda_1 = (r0 e2_1 - r1 e2_0) / D */
+    g[1][1] = -e2[0] / D;
+    g[2][0] = -e1[1] / D;       /* lambda_2 = (e1_0 r1 - e1_1 r0) / D */
+    g[2][1] = e1[0] / D;
+    g[0][0] = -(g[1][0] + g[2][0]);
+    g[0][1] = -(g[1][1] + g[2][1]);
+    int k;
+    double a;
+    ora_time_locate(f->times, f->nframes, f->time_periodic, f->period, t, &k, &a);
+    int k1 = (f->nframes > 1) ? k + 1 : k;
+    const float *fa = f->frames + 2LL * f->nnodes * k;
+    const float *fb = f->frames + 2LL * f->nnodes * k1;
+    for (int comp = 0; comp < 2; ++comp) {
+        double sa = 0.0, sb = 0.0, ja[2] = {0, 0}, jb[2] = {0, 0};
+        for (int i = 0; i < 3; ++i) {
+            long long node = f->tris[3 * c + i];
+            const double ua = fa[2 * node + comp], ub = fb[2 * node + comp];
+            sa += lam[i] * ua;
+            sb += lam[i] * ub;
+            for (int d = 0; d < 2; ++d) {
+                ja[d] += g[i][d] * ua;
+                jb[d] += g[i][d] * ub;
+            }
+        }
+        u[comp] = (1.0 - a) * sa + a * sb;
+        for (int d = 0; d < 2; ++d) J[comp * 2 + d] = (1.0 - a) * ja[d] + a * jb[d];
+    }
+    return 0;
+}
+
 /* ====================================================================
  * Seed lattice (Sec. 2 "Seed": structured grid of seed points).
  * ==================================================================== */
@@ -869,10 +956,18 @@ long long ora_rk4(int field_kind, const void *field, int dim, long long n,
  * rectilinear field (Sec. 1: the linearised flow map, the alternative to finite differences of
  * the seed grid).  Same steps, stage times and leaving rule as ora_rk4; M [n][dim][dim] is the
  * derivative of the final position with respect to the seed, frozen with the tracer.          */
-long long ora_rk4_var(const ora_rect_field *f, long long n, const double *x0, double t0, double T, double dt,
-                      double *xT, double *Mout, unsigned char *status, double *t_exit)
+/* velocity and Jacobian of any field kind; 0 inside, 1 outside (meshes) */
+static int eval_uJ(int kind, const void *field, const double *x, double t, int *cell, double *u, double *J)
 {
-    const int dim = f->dim;
+    if (kind == 0) return ora_rect_velocity_grad((const ora_rect_field *)field, x, t, u, J);
+    if (kind == 3) return ora_tri_velocity_grad((const ora_tri_field *)field, x, t, cell, u, J);
+    return ora_tet_velocity_grad((const ora_tet_field *)field, x, t, cell, u, J);
+}
+
+long long ora_rk4_var_kind(int field_kind, const void *field, int dim, long long n, const double *x0, const int *cells,
+                           double t0, double T, double dt, double *xT, double *Mout, unsigned char *status,
+                           double *t_exit)
+{
     double adt = fabs(dt);
     long long nsteps = (long long)floor(fabs(T) / adt + 0.5);
     double h = (T < 0.0) ? -adt : adt;
@@ -883,15 +978,22 @@ long long ora_rk4_var(const ora_rect_field *f, long long n, const double *x0, do
             x[a] = x0[a * n + p];
             M[a * dim + a] = 1.0;
         }
+        int cell = cells ? cells[p] : 0;
         unsigned char st = ORA_OK;
         double te = t0 + T;
+        if (field_kind >= 2 && cell < 0) {
+            st = ORA_OUTSIDE;
+            te = t0;
+        }
         for (long long s = 0; s < nsteps && st == ORA_OK; ++s) {
             double t = t0 + (double)s * h;
             const double ct[4] = {0.0, 0.5, 0.5, 1.0};
-            for (int q = 0; q < 4; ++q) {
+            int out = 0;
+            for (int q = 0; q < 4 && !out; ++q) {
                 for (int a = 0; a < dim; ++a) y[a] = q == 0 ? x[a] : x[a] + ct[q] * h * ku[q - 1][a];
                 for (int e = 0; e < dim * dim; ++e) Y[e] = q == 0 ? M[e] : M[e] + ct[q] * h * kM[q - 1][e];
-                ora_rect_velocity_grad(f, y, t + ct[q] * h, ku[q], J);
+                out = eval_uJ(field_kind, field, y, t + ct[q] * h, &cell, ku[q], J);
+                if (out) break;
                 for (int a = 0; a < dim; ++a)
                     for (int b = 0; b < dim; ++b) {
                         double acc = 0.0;
@@ -899,10 +1001,15 @@ long long ora_rk4_var(const ora_rect_field *f, long long n, const double *x0, do
                         kM[q][a * dim + b] = acc;
                     }
             }
+            if (out) { /* meshes: a stage left the mesh, freeze at the start of the step */
+                st = ORA_LEFT;
+                te = t;
+                break;
+            }
             for (int a = 0; a < dim; ++a) x[a] = x[a] + h / 6.0 * (ku[0][a] + 2.0 * ku[1][a] + 2.0 * ku[2][a] + ku[3][a]);
             for (int e = 0; e < dim * dim; ++e)
                 M[e] = M[e] + h / 6.0 * (kM[0][e] + 2.0 * kM[1][e] + 2.0 * kM[2][e] + kM[3][e]);
-            if (rect_left(f, x)) {
+            if (field_kind == 0 && rect_left((const ora_rect_field *)field, x)) {
                 st = ORA_LEFT;
                 te = t + h;
             }
@@ -913,6 +1020,12 @@ long long ora_rk4_var(const ora_rect_field *f, long long n, const double *x0, do
         t_exit[p] = te;
     }
     return nsteps;
+}
+
+long long ora_rk4_var(const ora_rect_field *f, long long n, const double *x0, double t0, double T, double dt,
+                      double *xT, double *Mout, unsigned char *status, double *t_exit)
+{
+    return ora_rk4_var_kind(0, f, f->dim, n, x0, NULL, t0, T, dt, xT, Mout, status, t_exit);
 }
 
 /* Dormand-Prince 5(4) tableau (Dormand & Prince 1980). */

@@ -150,8 +150,16 @@ void ora_seed_grid(int dim, const int n[3], const double lo[3], const double hi[
  * start of the step, t_exit = t_n.  cells (meshes only, may be NULL otherwise) is
  * the start cell per seed, -1 = seed outside (status OUTSIDE).
  * Returns the number of steps per tracer.                                   */
-/* RK4 on Eq. 2 with the variational equation dM/dt = J M, M(t0) = I (rectilinear
- * fields): final positions, M [n][dim][dim], status and exit time as ora_rk4.     */
+/* RK4 on Eq. 2 with the variational equation dM/dt = J M, M(t0) = I: final positions,
+ * M [n][dim][dim], status and exit time as ora_rk4 (field_kind and cells as there;
+ * ora_rk4_var is the rectilinear case).                                            */
+long long ora_rk4_var_kind(int field_kind, const void *field, int dim, long long n, const double *x0, const int *cells,
+                           double t0, double T, double dt, double *xT, double *M, unsigned char *status,
+                           double *t_exit);
+/* u and its spatial Jacobian J [dim][dim] on meshes (constant inside a cell); as ora_tet_velocity /
+ * ora_tri_velocity otherwise.                                                                       */
+int ora_tet_velocity_grad(const ora_tet_field *f, const double *x, double t, int *cell, double *u, double *J);
+int ora_tri_velocity_grad(const ora_tri_field *f, const double *x, double t, int *cell, double *u, double *J);
 long long ora_rk4_var(const ora_rect_field *f, long long n, const double *x0, double t0, double T, double dt,
                       double *xT, double *M, unsigned char *status, double *t_exit);
 
