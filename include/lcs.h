@@ -249,9 +249,9 @@ typedef struct {
     int nsnap;                  /* 0..LCS_MAX_SNAP snapshots per integration        */
     const double *snap_T;       /* HOST [nsnap]: horizon magnitudes, > 0, strictly
                                    increasing, each a whole number of steps dt    */
-    int variational;            /* LCS_RK4 on rectilinear fields, no snapshots: also
-                                   integrate grad F by the variational equations
-                                   (lcs_flowmap_grad, lcs_ftle_variational)       */
+    int variational;            /* LCS_RK4, no snapshots: also integrate grad F by
+                                   the variational equations (lcs_flowmap_grad,
+                                   lcs_ftle_variational); every field kind         */
 } lcs_advect_opts;
 
 /* Flow-map storage for `njobs` integrations of one lattice.                 */
@@ -276,8 +276,9 @@ lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *
  * the linearised flow map, the alternative to differencing the seed grid):
  * lcs_advect with opts.variational integrates dM/dt = J(x, t) M, M(t0) = I,
  * next to Eq. 2 with the same RK4 stages, J the spatial Jacobian of the
- * interpolant (piecewise, zero across an axis where the query is clamped to
- * the box); M is frozen with a tracer that leaves.  grad [N][dim][dim] FP32,
+ * interpolant (piecewise: per cell on meshes, zero across an axis where a
+ * rectilinear query is clamped to the box); M is frozen with a tracer that
+ * leaves.  grad [N][dim][dim] FP32,
  * grad[(p*dim + a)*dim + b] = d x_a(T) / d x0_b.
  * Errors: LCS_EINVAL when no variational integration wrote this flow map.   */
 lcs_status lcs_flowmap_grad(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *grad, int on_device);

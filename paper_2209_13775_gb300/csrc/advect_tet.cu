@@ -134,6 +134,91 @@ __global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const
     mesh_store<2>(A, job, i, x, st, te);
 }
 
+// ------------------------------------------------ variational equations on meshes
+
+// RK4 with dM/dt = J M on tets (DIM 3, MD = TetDev) or triangles (DIM 2, TriDev): the position
+// follows the plain mesh kernels' arithmetic (so x, status and exit time equal theirs), M the
+// rectilinear variational kernel's, with the cell's constant P1 gradient as J
+template <int DIM, int ST, class MD>
+__global__ void __launch_bounds__(256) rk4_mesh_var_kernel(MD T, Rk4Args A, const int *__restrict__ cells0,
+                                                           unsigned *errword)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int job = blockIdx.y;
+    if (i >= A.N) return;
+    float x[DIM], M[DIM][DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        x[d] = A.seeds[d * A.N + i];
+#pragma unroll
+        for (int e = 0; e < DIM; ++e) M[d][e] = d == e ? 1.0f : 0.0f;
+    }
+    int cell = cells0[i];
+    unsigned char st = LCS_TRACER_OK;
+    float te = A.job_tend[job];
+    if (cell < 0) {
+        st = LCS_TRACER_OUTSIDE;
+        te = A.job_t0[job];
+    }
+    const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
+    const int ns = A.job_nsteps[job];
+    const float h = A.job_h[job], hh = 0.5f * h, h6 = h * (1.0f / 6.0f);
+    for (int n = 0; n < ns && st == LCS_TRACER_OK; ++n) {
+        const SchedEntry e[3] = {load_sched(sc + 3 * n), load_sched(sc + 3 * n + 1), load_sched(sc + 3 * n + 2)};
+        float k[4][DIM], K[4][DIM][DIM], y[DIM], Y[DIM][DIM], lam[DIM + 1], J[DIM][DIM];
+        int r = TET_INSIDE;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float c = q == 0 ? 0.0f : (q == 3 ? h : hh);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                y[a] = q == 0 ? x[a] : fmaf(c, k[q - 1][a], x[a]);
+#pragma unroll
+                for (int b = 0; b < DIM; ++b) Y[a][b] = q == 0 ? M[a][b] : fmaf(c, K[q - 1][a][b], M[a][b]);
+            }
+            const SchedEntry &es = e[q == 0 ? 0 : (q == 3 ? 2 : 1)];
+            const char *fp = T.pairs + (size_t)es.k * T.fstride;
+            if constexpr (DIM == 3) {
+                r = tet_locate(T, y, &cell, lam);
+                if (r != TET_INSIDE) break;
+                tet_interp_grad<ST>(T, cell, lam, fp, es.a, k[q], J);
+            } else {
+                r = tri_locate(T, y, &cell, lam);
+                if (r != TET_INSIDE) break;
+                tri_interp_grad<ST>(T, cell, lam, fp, es.a, k[q], J);
+            }
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+#pragma unroll
+                for (int b = 0; b < DIM; ++b) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int cc = 0; cc < DIM; ++cc) acc = fmaf(J[a][cc], Y[cc][b], acc);
+                    K[q][a][b] = acc;
+                }
+        }
+        if (r != TET_INSIDE) {  // a stage point left the mesh: freeze at the start of the step
+            st = r == TET_OUTSIDE ? LCS_TRACER_LEFT : LCS_TRACER_WALKFAIL;
+            if (r == TET_WALKFAIL) atomicOr(errword, LCS_ERRBIT_WALK);
+            te = fmaf((float)n, h, A.job_t0[job]);
+            break;
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            x[a] = fmaf(h6, (k[0][a] + k[3][a]) + 2.0f * (k[1][a] + k[2][a]), x[a]);
+#pragma unroll
+            for (int b = 0; b < DIM; ++b)
+                M[a][b] = fmaf(h6, (K[0][a][b] + K[3][a][b]) + 2.0f * (K[1][a][b] + K[2][a][b]), M[a][b]);
+        }
+    }
+    mesh_store<DIM>(A, job, i, x, st, te);
+    float *o = A.out_grad + ((size_t)job * A.N + i) * DIM * DIM;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) o[a * DIM + b] = M[a][b];
+}
+
 // ------------------------------------------------------- time bracket (FP32)
 
 // largest k with t_k <= t (after the periodic wrap), clamped to [0, nf-2]; the weight of
@@ -399,9 +484,32 @@ cudaError_t launch_rk4_tet(lcs_ctx *ctx, const Rk4Launch &L, const int *cells0, 
     A.nsnap = L.nsnap;
     A.snap_n = L.snap_n;
     A.snap_te = L.snap_te;
+    A.out_grad = L.out_grad;
     if (L.N == 0) return cudaSuccess;
     const int bt = L.block_threads > 0 && L.block_threads <= 256 ? L.block_threads : 128;
     dim3 grid((unsigned)((L.N + bt - 1) / bt), (unsigned)L.njobs);
+    if (A.out_grad) {   // the variational equations
+        lcs_tm_begin(ctx, 0, s);
+        if (f->kind == LCS_TRI) {
+            const TriDev T = tri_dev(f, walk_limit);
+            if (f->storage == LCS_F32)
+                rk4_mesh_var_kernel<2, LCS_F32><<<grid, bt, 0, s>>>(T, A, cells0, ctx->d_errword);
+            else if (f->storage == LCS_F16)
+                rk4_mesh_var_kernel<2, LCS_F16><<<grid, bt, 0, s>>>(T, A, cells0, ctx->d_errword);
+            else
+                rk4_mesh_var_kernel<2, LCS_BF16><<<grid, bt, 0, s>>>(T, A, cells0, ctx->d_errword);
+        } else {
+            const TetDev T = tet_dev(f, walk_limit);
+            if (f->storage == LCS_F32)
+                rk4_mesh_var_kernel<3, LCS_F32><<<grid, bt, 0, s>>>(T, A, cells0, ctx->d_errword);
+            else if (f->storage == LCS_F16)
+                rk4_mesh_var_kernel<3, LCS_F16><<<grid, bt, 0, s>>>(T, A, cells0, ctx->d_errword);
+            else
+                rk4_mesh_var_kernel<3, LCS_BF16><<<grid, bt, 0, s>>>(T, A, cells0, ctx->d_errword);
+        }
+        lcs_tm_end(ctx, 0, s);
+        return cudaGetLastError();
+    }
     if (f->kind == LCS_TRI) {
         const TriDev T = tri_dev(f, walk_limit);
         lcs_tm_begin(ctx, 0, s);

@@ -1011,10 +1011,9 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
     if (njobs > fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: %d jobs > flow map's %d", njobs, fm->njobs);
     if (o->nsnap < 0 || o->nsnap > LCS_MAX_SNAP || (o->nsnap > 0 && !o->snap_T))
         return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: nsnap must be 0..%d with snap_T given", LCS_MAX_SNAP);
-    if (o->variational && (o->method != LCS_RK4 || f->kind != LCS_RECTILINEAR || o->nsnap > 0 || s->aux_base_N > 0))
+    if (o->variational && (o->method != LCS_RK4 || o->nsnap > 0 || s->aux_base_N > 0))
         return lcs_fail(ctx, LCS_EUNSUPPORTED,
-                        "lcs_advect: the variational equations need LCS_RK4 on a rectilinear field, a lattice and "
-                        "no snapshots");
+                        "lcs_advect: the variational equations need LCS_RK4, a lattice and no snapshots");
     if (o->nsnap > 0) {
         if (o->method != LCS_RK4)
             return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: snapshots need LCS_RK4");

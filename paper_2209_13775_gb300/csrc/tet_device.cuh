@@ -195,6 +195,43 @@ __device__ __forceinline__ void tet_interp(const TetDev &T, int c, const float *
     u[2] = acc[2];
 }
 
+// tet_interp's u plus the Jacobian of the P1 interpolant, constant in the tet:
+// J[c][d] = sum_i u_i[c] d lambda_i / d x_d, the lambda gradients being the inverse map's rows
+// (lambda_0's their negated sum)
+template <int ST>
+__device__ __forceinline__ void tet_interp_grad(const TetDev &T, int c, const float *lam, const char *fp, float a,
+                                                float *u, float (*J)[3])
+{
+    const int4 t = __ldg(T.tets + c);
+    const int vs[4] = {t.x, t.y, t.z, t.w};
+    const float4 r0 = __ldg(T.tmap + 3 * (size_t)c), r1 = __ldg(T.tmap + 3 * (size_t)c + 1),
+                 r2 = __ldg(T.tmap + 3 * (size_t)c + 2);
+    const float gr[4][3] = {{-(r0.x + r1.x + r2.x), -(r0.y + r1.y + r2.y), -(r0.z + r1.z + r2.z)},
+                            {r0.x, r0.y, r0.z},
+                            {r1.x, r1.y, r1.z},
+                            {r2.x, r2.y, r2.z}};
+    const float g = 1.0f - a;
+    float acc[3] = {0.0f, 0.0f, 0.0f}, va[3], vb[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) J[q][d] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        TetPair<ST>::ld(fp, vs[i], va, vb);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float ub = a == 0.0f ? va[q] : fmaf(a, vb[q], g * va[q]);
+            acc[q] = fmaf(lam[i], ub, acc[q]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) J[q][d] = fmaf(gr[i][d], ub, J[q][d]);
+        }
+    }
+    u[0] = acc[0];
+    u[1] = acc[1];
+    u[2] = acc[2];
+}
+
 // ------------------------------------------------------------ exact orientation
 
 // error-free transformations (Knuth's TwoSum; the FMA residual of a product)

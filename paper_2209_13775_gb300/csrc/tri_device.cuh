@@ -150,6 +150,36 @@ __device__ __forceinline__ void tri_interp(const TriDev &T, int c, const float *
     u[1] = acc[1];
 }
 
+// tri_interp's u plus the Jacobian of the P1 interpolant, constant in the triangle
+template <int ST>
+__device__ __forceinline__ void tri_interp_grad(const TriDev &T, int c, const float *lam, const char *fp, float a,
+                                                float *u, float (*J)[2])
+{
+    const int4 t = __ldg(T.tris + c);
+    const int vs[3] = {t.x, t.y, t.z};
+    const float4 m = __ldg(T.tmap + c);
+    const float gr[3][2] = {{-(m.x + m.z), -(m.y + m.w)}, {m.x, m.y}, {m.z, m.w}};
+    const float g = 1.0f - a;
+    float acc[2] = {0.0f, 0.0f}, va[2], vb[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int d = 0; d < 2; ++d) J[q][d] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        TriPair<ST>::ld(fp, vs[i], va, vb);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float ub = a == 0.0f ? va[q] : fmaf(a, vb[q], g * va[q]);
+            acc[q] = fmaf(lam[i], ub, acc[q]);
+#pragma unroll
+            for (int d = 0; d < 2; ++d) J[q][d] = fmaf(gr[i][d], ub, J[q][d]);
+        }
+    }
+    u[0] = acc[0];
+    u[1] = acc[1];
+}
+
 // sign of (b - a) x (c - a) for FP32 points, exactly
 static __device__ __noinline__ int orient2d_sign(const float *a, const float *b, const float *c)
 {

@@ -300,7 +300,7 @@ def test_tri_argument_errors(ctx, sten):
         assert e.value.status == 1
         seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (8, 8), (0.0, -1.0), (10.0, 1.0)), field)
         fm2 = lcs.lcs_flowmap_create(ctx, seeds, 1)
-        for kw in (dict(method=lcs.RK45, snap_T=[0.25]), dict(method=lcs.RK4, dt=0.05, variational=True)):
+        for kw in (dict(method=lcs.RK45, snap_T=[0.25]), dict(method=lcs.RK45, variational=True)):
             with pytest.raises(lcs.LcsError) as e:
                 lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(T=0.5, **kw), fm2)
             assert e.value.status == 7

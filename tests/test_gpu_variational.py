@@ -257,3 +257,90 @@ def test_variational_episodes_equal_one_pass(ctx, storage, bounded):
         np.testing.assert_array_equal(ep[k], plain[k])
     if bounded:
         assert (ep["st"] != 0).sum() > 100
+
+
+# ------------------------------------------------------------------ meshes
+
+def mesh_var_run(ctx, desc, frames, dim, n, lo, hi, t0, T, dt):
+    field = lcs.lcs_load_field(ctx, desc, frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(dim, n, lo, hi), field)
+    N = lcs.lcs_seeds_count(seeds)
+    out = {"seeds": np.empty((dim, N), dtype=np.float32), "cells": np.empty(N, dtype=np.int32)}
+    lcs.lcs_seeds_get(ctx, seeds, out["seeds"], out["cells"])
+    for tag, var in (("var", True), ("plain", False)):
+        fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, t0=t0, T=T, dt=dt, variational=var), fm)
+        r = {"x": np.empty((dim, N), dtype=np.float32), "st": np.empty(N, dtype=np.uint8),
+             "te": np.empty(N, dtype=np.float32)}
+        lcs.lcs_flowmap_get(ctx, fm, 0, r["x"], r["st"], r["te"])
+        if var:
+            r["M"] = np.empty((N, dim, dim), dtype=np.float32)
+            lcs.lcs_flowmap_grad(ctx, fm, 0, r["M"])
+            r["ftle"] = np.empty(N, dtype=np.float32)
+            lcs.lcs_ftle_variational(ctx, fm, 0, r["ftle"])
+        lcs.lcs_synchronize(ctx)
+        lcs.lcs_free_flowmap(fm)
+        out[tag] = r
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    return out
+
+
+def check_mesh_against_oracle(F, r, t0, T, dt, dim):
+    v, p = r["var"], r["plain"]
+    for k in ("x", "st", "te"):
+        np.testing.assert_array_equal(v[k], p[k])
+    x0 = r["seeds"].astype(np.float64)
+    _, Mo, so, teo = oracle.rk4_var(F, x0, t0, T, dt, cells=r["cells"])
+    from gpu_util import check_exit_statuses
+    same = check_exit_statuses(v["st"], v["te"], so, teo, dt)
+    ok = same & (so == oracle.OK)
+    assert ok.sum() > 500
+    check_grad(v["M"], Mo, ok)
+    _, sig = oracle.ftle(oracle.cauchy_green(np.where(ok[:, None, None], Mo, np.nan)), dim, T)
+    both = ok & np.isfinite(v["ftle"])
+    check_ftle(np.where(both, v["ftle"], np.nan), np.where(both, sig, np.nan))
+
+
+def test_variational_triangles(ctx):
+    m = inputs.stenosis_frames(inputs.stenosis_mesh(h=0.05, L=10.0), nframes=40, period=1.0)
+    desc = lcs.field_desc(2, times=m.times, time_periodic=True, period=m.period, kind=lcs.TRI,
+                          mesh=(m.xyz, m.tets, m.nbrs))
+    n, lo, hi, t0, T, dt = (100, 33), (0.05, -0.96), (9.95, 0.96), 0.2, 0.6, 0.01
+    r = mesh_var_run(ctx, desc, m.frames, 2, n, lo, hi, t0, T, dt)
+    F = oracle.TriField(m.xyz, m.tets, m.nbrs, m.frames, m.times, True, m.period)
+    check_mesh_against_oracle(F, r, t0, T, dt, 2)
+
+
+def test_variational_tets(ctx):
+    p = inputs.pipe_frames(inputs.pipe_mesh(h=0.1, R=1.0, L=2.0), nframes=50, period=1.0, L=2.0)
+    desc = lcs.field_desc(3, times=p.times, time_periodic=True, period=p.period, kind=lcs.TET,
+                          mesh=(p.xyz, p.tets, p.nbrs))
+    n, lo, hi, t0, T, dt = (16, 16, 20), (-0.6, -0.6, 0.2), (0.6, 0.6, 1.8), 0.3, 0.8, 0.01
+    r = mesh_var_run(ctx, desc, p.frames, 3, n, lo, hi, t0, T, dt)
+    F = oracle.TetField(p.xyz, p.tets, p.nbrs, p.frames, p.times, True, p.period)
+    check_mesh_against_oracle(F, r, t0, T, dt, 3)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_variational_mesh_linear_flow(ctx, dim):
+    from meshes import kuhn_mesh, tri_grid_mesh
+    rng = np.random.default_rng(70 + dim)
+    A = np.round(rng.normal(size=(dim, dim)) * 0.3 * 16) / 16
+    if dim == 2:
+        pts, cells, nbrs = tri_grid_mesh(8)
+        pts = (pts - np.float32(4.0)) * np.float32(0.5)
+        kind = lcs.TRI
+    else:
+        pts, cells, nbrs = kuhn_mesh(4)
+        pts = pts - np.float32(2.0)
+        kind = lcs.TET
+    fr = np.stack([pts @ A.T, pts @ A.T]).astype(np.float32)
+    desc = lcs.field_desc(dim, times=[0.0, 10.0], kind=kind, mesh=(pts, cells, nbrs))
+    dt, T = 0.0625, 1.0
+    r = mesh_var_run(ctx, desc, fr, dim, (9,) * dim, (-0.6,) * dim, (0.6,) * dim, 0.0, T, dt)
+    v = r["var"]
+    assert (v["st"] == 0).all()
+    want = np.linalg.matrix_power(_R(dt * A), int(round(T / dt)))
+    err = np.abs(v["M"] - want[None]).max() / np.abs(want).max()
+    assert err <= 1e-5, err
