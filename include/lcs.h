@@ -181,9 +181,20 @@ void lcs_free_seeds(lcs_seeds *seeds);
  *   grad F[a][b] = (F_a(p, b, 0) - F_a(p, b, 1)) / (x0_b(p, b, 0) - x0_b(p, b, 1))
  * in FP64 from the FP32 positions, x0 the FP32 starting points (so the divisor
  * is the spacing the points really have); NaN unless all 2 dim points are OK.
- * delta [dim] HOST, each > 0 and finite.  Not for tet fields or
- * lcs_ftle_early.  Errors: LCS_EINVAL, LCS_ENOMEM, LCS_ECUDA.               */
+ * delta [dim] HOST, each > 0 and finite.  Not for lcs_ftle_early; for a
+ * lattice made on a mesh field use lcs_seed_aux_field.
+ * Errors: LCS_EINVAL, LCS_ENOMEM, LCS_ECUDA.                               */
 lcs_status lcs_seed_aux(lcs_ctx *ctx, const lcs_seeds *lattice, const double *delta, lcs_seeds **out);
+
+/* lcs_seed_aux for a lattice made by lcs_seed_grid on `field`: on a tet or
+ * triangle field the auxiliary points also get their exact cells (as
+ * lcs_seed_grid locates seeds), so lcs_advect takes them on that field; a
+ * point outside the mesh is OUTSIDE and its seed's grad F NaN.  On a
+ * rectilinear field (or NULL) it is lcs_seed_aux.
+ * Errors: LCS_EINVAL (a lattice not made on this mesh field), LCS_ENOMEM,
+ * LCS_ECUDA.                                                                */
+lcs_status lcs_seed_aux_field(lcs_ctx *ctx, const lcs_seeds *lattice, const lcs_field *field, const double *delta,
+                              lcs_seeds **out);
 
 /* ------------------------------------------------- flow map (a3-a8, a12) */
 

@@ -541,17 +541,23 @@ cudaError_t launch_seed_aux(int dim, const float *lattice, long long N, const do
     return cudaGetLastError();
 }
 
-extern "C" lcs_status lcs_seed_aux(lcs_ctx *ctx, const lcs_seeds *lat, const double *delta, lcs_seeds **out)
+// auxiliary points of a lattice; on a mesh field (the lattice made on it) also their exact cells
+static lcs_status seed_aux(lcs_ctx *ctx, const lcs_seeds *lat, const lcs_field *field, const double *delta,
+                           lcs_seeds **out, const char *who)
 {
     if (!ctx) return LCS_EINVAL;
-    if (!lat || !delta || !out) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_aux: null argument");
+    if (!lat || !delta || !out) return lcs_fail(ctx, LCS_EINVAL, "%s: null argument", who);
     *out = nullptr;
-    if (lat->aux_base_N > 0 || lat->d_cells)
-        return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_aux: needs a lattice made on a rectilinear field");
+    const bool mesh = field && lcs_is_mesh(field);
+    if (lat->aux_base_N > 0) return lcs_fail(ctx, LCS_EINVAL, "%s: auxiliary points of auxiliary points", who);
+    if (mesh && (!lat->d_cells || lat->field_uid != field->uid))
+        return lcs_fail(ctx, LCS_EINVAL, "%s: the lattice must come from lcs_seed_grid on this mesh field", who);
+    if (!mesh && lat->d_cells)
+        return lcs_fail(ctx, LCS_EINVAL, "%s: a lattice made on a mesh field needs that field", who);
     for (int a = 0; a < lat->dim; ++a)
         if (!(delta[a] > 0.0) || !isfinite(delta[a]))
-            return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_aux: delta[%d] = %g must be finite and > 0", a, delta[a]);
-    if (lat->N > ((1LL << 31) - 1) / (2 * lat->dim)) return lcs_fail(ctx, LCS_EINVAL, "lcs_seed_aux: too many seeds");
+            return lcs_fail(ctx, LCS_EINVAL, "%s: delta[%d] = %g must be finite and > 0", who, a, delta[a]);
+    if (lat->N > ((1LL << 31) - 1) / (2 * lat->dim)) return lcs_fail(ctx, LCS_EINVAL, "%s: too many seeds", who);
     lcs_seeds *s = new (std::nothrow) lcs_seeds(*lat);
     if (!s) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");
     s->uid = lcs_next_uid();
@@ -563,13 +569,31 @@ extern "C" lcs_status lcs_seed_aux(lcs_ctx *ctx, const lcs_seeds *lat, const dou
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_xyz, sizeof(float) * s->dim * (size_t)s->N);
     if (e == cudaSuccess) e = launch_seed_aux(s->dim, lat->d_xyz, lat->N, s->aux_delta, s->d_xyz, ctx->stream);
+    if (e == cudaSuccess && mesh) {
+        s->field_uid = field->uid;
+        e = cudaMalloc(&s->d_cells, sizeof(int) * (size_t)s->N);
+        if (e == cudaSuccess)
+            e = field->kind == LCS_TRI ? tri_locate_seeds(field, s->d_xyz, s->N, s->d_cells, ctx->stream)
+                                       : tet_locate_seeds(field, s->d_xyz, s->N, s->d_cells, ctx->stream);
+    }
     if (e != cudaSuccess) {
         lcs_free_seeds(s);
-        return lcs_fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "lcs_seed_aux: %s",
+        return lcs_fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "%s: %s", who,
                         cudaGetErrorString(e));
     }
     *out = s;
     return LCS_OK;
+}
+
+extern "C" lcs_status lcs_seed_aux(lcs_ctx *ctx, const lcs_seeds *lat, const double *delta, lcs_seeds **out)
+{
+    return seed_aux(ctx, lat, nullptr, delta, out, "lcs_seed_aux");
+}
+
+extern "C" lcs_status lcs_seed_aux_field(lcs_ctx *ctx, const lcs_seeds *lat, const lcs_field *field,
+                                         const double *delta, lcs_seeds **out)
+{
+    return seed_aux(ctx, lat, field, delta, out, "lcs_seed_aux_field");
 }
 
 extern "C" lcs_status lcs_seed_grid(lcs_ctx *ctx, const lcs_seed_desc *d, const lcs_field *field, lcs_seeds **out)

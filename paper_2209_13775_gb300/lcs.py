@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "LCS_OK", 1: "LCS_EINVAL", 2: "LCS_ENOMEM", 3: "LCS_ECUDA", 4
                 5: "LCS_EWALK", 6: "LCS_EMAXSTEPS", 7: "LCS_EUNSUPPORTED"}
 
 EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs_synchronize",
-           "lcs_load_field", "lcs_update_frames", "lcs_free_field", "lcs_seed_grid", "lcs_seed_aux", "lcs_seeds_count",
+           "lcs_load_field", "lcs_update_frames", "lcs_free_field", "lcs_seed_grid", "lcs_seed_aux", "lcs_seed_aux_field",
+           "lcs_seeds_count",
            "lcs_seeds_get", "lcs_free_seeds", "lcs_flowmap_create", "lcs_advect", "lcs_flowmap_get",
            "lcs_flowmap_steps",
            "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_cg_eigen", "lcs_ftle_early", "lcs_ftle_variational",
@@ -92,7 +93,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_set_stream": ([P, P], S), "lcs_synchronize": ([P], S),
         "lcs_load_field": ([P, P, P, I, P], S), "lcs_update_frames": ([P, P, P, I], S),
         "lcs_free_field": ([P], None), "lcs_seed_grid": ([P, P, P, P], S), "lcs_seeds_count": ([P], LL),
-        "lcs_seed_aux": ([P, P, P, P], S),
+        "lcs_seed_aux": ([P, P, P, P], S), "lcs_seed_aux_field": ([P, P, P, P, P], S),
         "lcs_seeds_get": ([P, P, P, P, I], S), "lcs_free_seeds": ([P], None),
         "lcs_flowmap_create": ([P, P, I, P], S), "lcs_advect": ([P, P, P, P, P], S),
         "lcs_flowmap_get": ([P, P, I, P, P, P, I], S), "lcs_free_flowmap": ([P], None),
@@ -238,11 +239,21 @@ def lcs_seed_grid(ctx, desc: SeedDesc, field=None):
     return out.value
 
 
-def lcs_seed_aux(ctx, lattice, delta):
-    """The 2 dim auxiliary points around every seed of a lattice, at +-delta[b] along each axis b."""
+def lcs_seed_aux_field(ctx, lattice, field, delta):
+    """lcs_seed_aux for a lattice made on `field` (mesh fields: the points get their exact cells)."""
+    return lcs_seed_aux(ctx, lattice, delta, field)
+
+
+def lcs_seed_aux(ctx, lattice, delta, field=None):
+    """The 2 dim auxiliary points around every seed of a lattice, at +-delta[b] along each axis b
+    (located on `field` when the lattice was made on a mesh field)."""
     d = np.ascontiguousarray(delta, dtype=np.float64)
     out = ctypes.c_void_p()
-    _check(ctx, load().lcs_seed_aux(ctx, lattice, d.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out)))
+    if field is None:
+        _check(ctx, load().lcs_seed_aux(ctx, lattice, d.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out)))
+    else:
+        _check(ctx, load().lcs_seed_aux_field(ctx, lattice, field, d.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.byref(out)))
     return out.value
 
 

@@ -132,3 +132,60 @@ def test_aux_rejects(ctx):
         lcs.lcs_free_seeds(aux)
     finally:
         lcs.lcs_free_seeds(lat)
+
+
+@pytest.mark.parametrize("kind", ["tri", "tet"])
+def test_aux_on_meshes(ctx, kind):
+    # auxiliary points on a mesh field: located exactly (bit-identical cells), advected with the mesh
+    # rules, differenced per seed; FTLE against the oracle's, C bit-identical on the GPU's positions
+    from gpu_util import check_exit_statuses
+    if kind == "tri":
+        m = inputs.stenosis_frames(inputs.stenosis_mesh(h=0.05, L=10.0), nframes=40, period=1.0)
+        F = oracle.TriField(m.xyz, m.tets, m.nbrs, m.frames, m.times, True, m.period)
+        dim, n, lo, hi, lk = 2, (80, 30), (0.05, -0.96), (9.95, 0.96), lcs.TRI
+        delta = [0.5 * (hi[0] - lo[0]) / (n[0] - 1), 0.5 * (hi[1] - lo[1]) / (n[1] - 1)]
+    else:
+        m = inputs.pipe_frames(inputs.pipe_mesh(h=0.1, R=1.0, L=2.0), nframes=50, period=1.0, L=2.0)
+        F = oracle.TetField(m.xyz, m.tets, m.nbrs, m.frames, m.times, True, m.period)
+        dim, n, lo, hi, lk = 3, (12, 12, 14), (-0.75, -0.75, 0.1), (0.75, 0.75, 1.9), lcs.TET
+        delta = [0.5 * (hi[a] - lo[a]) / (n[a] - 1) for a in range(3)]
+    t0, T, dt = 0.2, 0.6, 0.01
+    desc = lcs.field_desc(dim, times=m.times, time_periodic=True, period=m.period, kind=lk,
+                          mesh=(m.xyz, m.tets, m.nbrs))
+    field = lcs.lcs_load_field(ctx, desc, m.frames)
+    lat = lcs.lcs_seed_grid(ctx, lcs.seed_desc(dim, n, lo, hi), field)
+    with pytest.raises(lcs.LcsError):            # a mesh lattice needs its field
+        lcs.lcs_seed_aux(ctx, lat, delta)
+    aux = lcs.lcs_seed_aux(ctx, lat, delta, field)
+    N, M = lcs.lcs_seeds_count(lat), lcs.lcs_seeds_count(aux)
+    xa = np.empty((dim, M), dtype=np.float32)
+    ca = np.empty(M, dtype=np.int32)
+    lcs.lcs_seeds_get(ctx, aux, xa, ca)
+    fm = lcs.lcs_flowmap_create(ctx, aux, 1)
+    lcs.lcs_advect(ctx, field, aux, lcs.advect_opts(lcs.RK4, t0=t0, T=T, dt=dt), fm)
+    x = np.empty((dim, M), dtype=np.float32)
+    st = np.empty(M, dtype=np.uint8)
+    te = np.empty(M, dtype=np.float32)
+    lcs.lcs_flowmap_get(ctx, fm, 0, x, st, te)
+    f = np.empty(N, dtype=np.float32)
+    C = np.empty((N, 3 if dim == 2 else 6))
+    lcs.lcs_ftle(ctx, fm, 0, f, None, C)
+    lcs.lcs_synchronize(ctx)
+    for h_ in (fm,):
+        lcs.lcs_free_flowmap(h_)
+    lcs.lcs_free_seeds(aux)
+    lcs.lcs_free_seeds(lat)
+    lcs.lcs_free_field(field)
+    xo = oracle.aux_points(oracle.seed_grid(dim, n, lo, hi), delta)
+    np.testing.assert_array_equal(xa, xo)
+    co = F.locate_seeds(xo)
+    np.testing.assert_array_equal(ca, co)
+    xT, so, teo = oracle.rk4(F, xo.astype(np.float64), t0, T, dt, cells=co)
+    same = check_exit_statuses(st, te, so, teo, dt)
+    assert (so == oracle.OUTSIDE).sum() > 10 and (so == oracle.OK).sum() > 1000
+    G = oracle.aux_gradient(xa, x.astype(np.float64), st)
+    np.testing.assert_array_equal(C, oracle.cauchy_green(G))
+    Go = oracle.aux_gradient(xo, xT, so)
+    _, sig = oracle.ftle(oracle.cauchy_green(Go), dim, T)
+    seed_same = same.reshape(N, 2 * dim).all(axis=1)
+    check_ftle(np.where(seed_same, f, np.nan), np.where(seed_same, sig, np.nan))
