@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) mlp_step_kernel(MlpStepArgs A)
     __shared__ uint64_t bar_w, bar_g[NWG];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag[NWG];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int g = warp >> 2;           // warpgroup
     const int r = tid & 127;           // tile row = TMEM lane
     const int wq = warp & 3;
