@@ -483,39 +483,53 @@ def cg_eigen(C, dim):
     return e, v
 
 
-def fd_stencil_members(dim, n, periodic):
-    """Lattice neighbours the finite differences of a seed use by geometry alone (Sec. 2
-    "Cauchy-Green"): per axis the two central neighbours, or at a non-periodic lattice edge the two
-    on the inner side.  Returns [N][2 dim] seed ids."""
+def fd_stencil_members(dim, n, periodic, valid0=None):
+    """Lattice neighbours the finite differences of a seed use (Sec. 2 "Cauchy-Green"), chosen as the
+    difference rule chooses them from the seeds valid at the start (valid0; all of them when None):
+    per axis the two central neighbours when both are valid, else the two on a side whose two
+    neighbours are valid (forward first), else none (-1).  On a lattice whose seeds are all valid
+    that is: central, or the two inner neighbours at a non-periodic edge.  Returns [N][2 dim] ids."""
     N = int(np.prod(n[:dim]))
     p = np.arange(N)
     idx = [(p // int(np.prod(n[:a]))) % n[a] for a in range(dim)]
     strides = [int(np.prod(n[:a])) for a in range(dim)]
+    valid = np.ones(N, dtype=bool) if valid0 is None else np.asarray(valid0, dtype=bool)
     out = np.empty((N, 2 * dim), dtype=np.int64)
     for a in range(dim):
         i = idx[a]
-        if periodic[a]:
-            o1, o2 = (i + 1) % n[a] - i, (i - 1) % n[a] - i
-        else:
-            central = (i >= 1) & (i <= n[a] - 2)
-            fwd = i == 0
-            o1 = np.where(central, 1, np.where(fwd, 1, -1))
-            o2 = np.where(central, -1, np.where(fwd, 2, -2))
-        out[:, 2 * a] = p + o1 * strides[a]
-        out[:, 2 * a + 1] = p + o2 * strides[a]
+
+        def nbr(o):
+            j = i + o
+            if periodic[a]:
+                return p + ((j % n[a]) - i) * strides[a]
+            inside = (j >= 0) & (j < n[a])
+            return np.where(inside, p + o * strides[a], -1)
+
+        q = {o: nbr(o) for o in (1, -1, 2, -2)}
+        ok = {o: (q[o] >= 0) & valid[np.maximum(q[o], 0)] for o in q}
+        central = ok[1] & ok[-1]
+        fwd = ~central & ok[1] & ok[2]
+        bwd = ~central & ~fwd & ok[-1] & ok[-2]
+        out[:, 2 * a] = np.where(central, q[1], np.where(fwd, q[1], np.where(bwd, q[-1], -1)))
+        out[:, 2 * a + 1] = np.where(central, q[-1], np.where(fwd, q[2], np.where(bwd, q[-2], -1)))
     return out
 
 
-def ftle_early(field, n, lo, hi, periodic, t0, T, dt, xT, status, t_exit, endpoint=None):
+def ftle_early(field, n, lo, hi, periodic, t0, T, dt, xT, status, t_exit, endpoint=None, cells=None):
     """Early Cauchy-Green evaluation (Sec. 2 "Flow Map": for trajectories that exit the data, the CG tensor
-    is formed ahead of the horizon wherever such a trajectory is used) for fixed-step RK4 on a rectilinear
-    field, from a full run's (xT, status, t_exit) over (t0, t0 + T).
+    is formed ahead of the horizon wherever such a trajectory is used) for fixed-step RK4, from a full
+    run's (xT, status, t_exit) over (t0, t0 + T).
 
     Per seed: m = the fewest steps that the seed or any lattice neighbour its finite differences use
     (fd_stencil_members) stayed in the domain -- all steps for a tracer still OK at the end, one less
     than the step it left in otherwise.  m = all steps: the regular FTLE over |T|.  0 < m: grad F
     from those tracers re-integrated over m steps, C (Eq. 1), lambda_max and
-    sigma = ln sqrt(lambda_max) / (m dt).  m = 0: NaN.  Returns (ftle, t_eval)."""
+    sigma = ln sqrt(lambda_max) / (m dt).  m = 0: NaN.  Returns (ftle, t_eval).
+
+    Mesh fields (cells: each seed's start cell, -1 outside): a tracer that leaves is frozen at the
+    start of the step it failed in, so its in-domain steps are |t_exit - t0| / dt; the stencil is the
+    one the differences choose from the seeds inside the mesh at the start."""
+    mesh = cells is not None
     dim = len(n)
     N = int(np.prod(n[:dim]))
     endpoint = endpoint if endpoint is not None else [0 if q else 1 for q in periodic]
@@ -523,10 +537,10 @@ def ftle_early(field, n, lo, hi, periodic, t0, T, dt, xT, status, t_exit, endpoi
     period = [hi[a] - lo[a] if periodic[a] else 0.0 for a in range(dim)]
     adt = abs(dt)
     ns = int(round(abs(T) / adt))
-    ne = np.where(status == OK, ns, np.rint(np.abs(t_exit - t0) / adt).astype(np.int64) - 1)
-    ne = np.maximum(ne, 0)
-    mem = fd_stencil_members(dim, n, periodic)
-    m = np.minimum(ne, ne[mem].min(axis=1))
+    ne = np.where(status == OK, ns, np.rint(np.abs(t_exit - t0) / adt).astype(np.int64) - (0 if mesh else 1))
+    ne = np.where((status == OK) | (status == LEFT), np.maximum(ne, 0), 0)
+    mem = fd_stencil_members(dim, n, periodic, None if not mesh else np.asarray(cells) >= 0)
+    m = np.where((mem < 0).any(axis=1), 0, np.minimum(ne, ne[np.maximum(mem, 0)].min(axis=1)))
     G = flowmap_gradient(dim, n, h, periodic, period, xT, status)
     lam, sig = ftle(cauchy_green(G), dim, T)
     t_eval = np.full(N, abs(T))
@@ -539,7 +553,7 @@ def ftle_early(field, n, lo, hi, periodic, t0, T, dt, xT, status, t_exit, endpoi
             sig[seeds] = np.nan
             continue
         ids = np.unique(np.concatenate([seeds, mem[seeds].ravel()]))
-        xm, stm, _ = rk4(field, x0[:, ids], t0, sgn * mm * adt, dt)
+        xm, stm, _ = rk4(field, x0[:, ids], t0, sgn * mm * adt, dt, cells=None if not mesh else np.asarray(cells)[ids])
         assert (stm == OK).all()
         xf = np.zeros((dim, N))
         sf = np.full(N, LEFT, dtype=np.uint8)

@@ -110,3 +110,51 @@ def test_early_cg_backward(ora):
     np.testing.assert_allclose(sig[fin], (np.log(np.sqrt(lam)) / mdt)[fin], rtol=1e-11, atol=1e-13)
     # every seed's early horizon is at most its own in-domain time
     assert np.all(np.round(t_eval / dt) <= np.where(ne == ns, ns, ne))
+
+
+def test_early_on_a_mesh_uniform_stream(ora):
+    # u = (1, 0) on a triangulated box [-2, 2]^2: a tracer at x is frozen at the start of the step whose
+    # stage point passes x = 2, so it stays floor((2 - x) / dt) steps; a seed's horizon is that of its
+    # right-most stencil member (x + h inside, the seed itself at the right edge, whose stencil is
+    # backward); the flow map is a translation, so every early FTLE is 0; seeds outside the mesh: NaN
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from meshes import tri_grid_mesh
+    pts, tris, nbrs = tri_grid_mesh(4)
+    pts = pts - np.float32(2.0)
+    fr = np.zeros((2, len(pts), 2), np.float32)
+    fr[..., 0] = 1.0
+    F = ora.TriField(pts, tris, nbrs, fr, [0.0, 10.0])
+    n, lo, hi, dt, T = (23, 9), (-2.55, -1.6), (1.85, 1.6), 0.1, 4.0
+    x0 = ora.seed_grid(2, n, lo, hi, [1, 1])
+    cells = F.locate_seeds(x0)
+    xT, st, te = ora.rk4(F, x0.astype(np.float64), 0.0, T, dt, cells=cells)
+    sig, t_eval = ora.ftle_early(F, n, lo, hi, (0, 0), 0.0, T, dt, xT, st, te, cells=cells)
+    h = (hi[0] - lo[0]) / (n[0] - 1)
+    X = x0[0].astype(np.float64).reshape(n[1], n[0])
+    inside = (cells >= 0).reshape(n[1], n[0])
+    i = np.arange(n[0])
+    v = lambda j, k: 0 <= k < n[0] and inside[j, k]
+    checked = 0
+    for j in range(1, n[1] - 1):          # rows whose y-stencil is central
+        for k in i[inside[j]]:
+            if not (v(j - 1, k) and v(j + 1, k)):
+                continue
+            if v(j, k - 1) and v(j, k + 1):
+                right = X[j, k + 1]        # central
+            elif v(j, k + 1) and v(j, k + 2):
+                right = X[j, k + 2]        # forward
+            elif v(j, k - 1) and v(j, k - 2):
+                right = X[j, k]            # backward: the seed is the right-most
+            else:
+                continue
+            want = dt * np.floor((2.0 - right) / dt)
+            assert abs(t_eval[j * n[0] + k] - min(want, T)) < 1e-9, (j, k, t_eval[j * n[0] + k], want)
+            checked += 1
+    assert checked > 100
+    # a translation: grad F is the identity up to the FP32 rounding of the seeds against the FP64
+    # lattice step (~1e-7 relative), so ln sqrt(lambda_max) = sigma * t_eval stays below 1e-6
+    ok = np.isfinite(sig)
+    assert ok.sum() > 100
+    assert np.abs(sig[ok] * t_eval[ok]).max() < 1e-6
+    assert np.isnan(sig[~inside.ravel()]).all()
