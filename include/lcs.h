@@ -429,11 +429,13 @@ lcs_status lcs_ftle_variational(lcs_ctx *ctx, const lcs_flowmap *fm, int job, fl
 /* Early Cauchy-Green evaluation (Sec. 2 "Flow Map": for trajectories that exit
  * the data, the CG tensor is formed ahead of the horizon wherever such a
  * trajectory is used).  fm holds job `job` of an lcs_advect call made with field, seeds and
- * opts (LCS_RK4 on a rectilinear field).  Each seed's finite differences use
- * fixed lattice neighbours (as lcs_cauchy_green: central, or one-sided at a
- * non-periodic lattice edge); m = the fewest steps the seed or one of them
- * stayed in the domain (all steps if still OK at the end, one less than the
- * step it left in otherwise).  m = all steps: the FTLE of lcs_ftle; 0 < m:
+ * opts (LCS_RK4, any field kind).  Each seed's finite differences use the
+ * lattice neighbours the differences choose from the seeds valid at the start
+ * (as lcs_cauchy_green: central, or one-sided at a non-periodic lattice edge
+ * or beside seeds outside a mesh); m = the fewest steps the seed or one of
+ * them stayed in the domain (all steps if still OK at the end; otherwise one
+ * less than the step it left in on rectilinear fields, the steps before the
+ * one it failed in on meshes).  m = all steps: the FTLE of lcs_ftle; 0 < m:
  * grad F from those tracers re-integrated over m steps (the same arithmetic,
  * so the positions they had after step m), C, lambda_max and
  * sigma = ln(sqrt(lambda_max)) / (m |dt|); m = 0: NaN.  ftle [N] FP32,

@@ -18,51 +18,67 @@
 // thread per listed seed).  The list is short where few tracers leave.
 #include "cg_device.cuh"
 #include "rect_device.cuh"
+#include "tri_device.cuh"
 
 namespace {
 
-// stencil member s (0: the seed, then two per axis) of seed idx on a lattice of L.n, by
-// geometry only: central (+1, -1) on periodic axes and inside, forward (+1, +2) at the low
-// edge, backward (-1, -2) at the high edge.  Returns the id; *wrap = periods crossed.
-__device__ __forceinline__ long long member(const CgLaunch &L, const long long *idx, int s, int *wrap, int *mode)
+// a lattice seed that is valid at the start: all of them on rectilinear fields, those inside
+// the mesh (cell >= 0) on mesh fields
+__device__ __forceinline__ bool valid0(const int *cells0, long long q) { return q >= 0 && (!cells0 || cells0[q] >= 0); }
+
+// the difference rule along axis b, chosen as the regular pass chooses it from the seeds valid at
+// the start: 1 central (+1, -1), 2 forward (+1, +2), 3 backward (-1, -2), 0 none.  On a lattice of
+// valid seeds: central on periodic axes and inside, forward at the low edge, backward at the high.
+__device__ __forceinline__ int axis_mode(const CgLaunch &L, const long long *idx, int b, const int *cells0)
+{
+    int w;
+    const bool p1 = valid0(cells0, lattice_nbr(L, idx, b, 1, &w)), m1 = valid0(cells0, lattice_nbr(L, idx, b, -1, &w));
+    if (p1 && m1) return 1;
+    if (p1 && valid0(cells0, lattice_nbr(L, idx, b, 2, &w))) return 2;
+    if (m1 && valid0(cells0, lattice_nbr(L, idx, b, -2, &w))) return 3;
+    return 0;
+}
+
+// stencil member s (0: the seed, then two per axis) of seed idx for the rule `mode` of its axis.
+// Returns the id (-1 when the axis has no rule); *wrap = periods crossed.
+__device__ __forceinline__ long long member(const CgLaunch &L, const long long *idx, int s, int mode, int *wrap)
 {
     *wrap = 0;
     if (s == 0) return idx[0] + (long long)L.n[0] * (idx[1] + (long long)L.n[1] * idx[2]);
     const int b = (s - 1) >> 1, second = (s - 1) & 1;
-    int m;
-    if (L.periodic[b] || (idx[b] >= 1 && idx[b] <= L.n[b] - 2))
-        m = 1;
-    else
-        m = idx[b] == 0 ? 2 : 3;
-    *mode = m;
-    const int off = m == 1 ? (second ? -1 : 1) : m == 2 ? (second ? 2 : 1) : (second ? -2 : -1);
+    if (mode == 0) return -1;
+    const int off = mode == 1 ? (second ? -1 : 1) : mode == 2 ? (second ? 2 : 1) : (second ? -2 : -1);
     return lattice_nbr(L, idx, b, off, wrap);
 }
 
-// steps a tracer of this slot stayed in the domain
-__device__ __forceinline__ int in_steps(unsigned char st, float te, int ns, double t0, double adt)
+// steps a tracer of this slot stayed in the domain: a rectilinear tracer leaves at the end of a
+// step (the one before it counts), a mesh tracer at the start of the step it failed in
+__device__ __forceinline__ int in_steps(unsigned char st, float te, int ns, double t0, double adt, bool mesh)
 {
     if (st == LCS_TRACER_OK) return ns;
     if (st != LCS_TRACER_LEFT) return 0;
-    const int n1 = (int)rint(fabs((double)te - t0) / adt);   // the step it left in
-    return max(n1 - 1, 0);
+    const int n1 = (int)rint(fabs((double)te - t0) / adt);
+    return mesh ? n1 : max(n1 - 1, 0);
 }
 
 template <int DIM>
 __global__ void early_scan_kernel(CgLaunch L, int job, int ns, double t0, double adt, float absT,
-                                  unsigned *__restrict__ count, int2 *__restrict__ list, float *__restrict__ t_eval)
+                                  const int *__restrict__ cells0, unsigned *__restrict__ count,
+                                  int2 *__restrict__ list, float *__restrict__ t_eval)
 {
     const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= L.N) return;
     const unsigned char *S = L.status + (size_t)job * L.N;
     const float *TE = L.texit + (size_t)job * L.N;
     const long long idx[3] = {p % L.n[0], (p / L.n[0]) % L.n[1], DIM == 3 ? p / ((long long)L.n[0] * L.n[1]) : 0};
+    const bool mesh = cells0 != nullptr;
     int m = ns;
 #pragma unroll
     for (int s = 0; s < 2 * DIM + 1; ++s) {
-        int w, mode;
-        const long long q = member(L, idx, s, &w, &mode);
-        m = min(m, q < 0 ? 0 : in_steps(S[q], TE[q], ns, t0, adt));
+        int w;
+        const int mode = s == 0 ? 1 : axis_mode(L, idx, (s - 1) >> 1, cells0);
+        const long long q = member(L, idx, s, mode, &w);
+        m = min(m, q < 0 ? 0 : in_steps(S[q], TE[q], ns, t0, adt, mesh));
     }
     if (m >= ns) {
         if (t_eval) t_eval[p] = absT;
@@ -90,8 +106,8 @@ __global__ void early_advect_kernel(CgLaunch L, RectParams P, const char *__rest
     const int2 it = list[e];
     const long long p = it.x;
     const long long idx[3] = {p % L.n[0], (p / L.n[0]) % L.n[1], DIM == 3 ? p / ((long long)L.n[0] * L.n[1]) : 0};
-    int w, mode;
-    const long long q = member(L, idx, s, &w, &mode);
+    int w;
+    const long long q = member(L, idx, s, s == 0 ? 1 : axis_mode(L, idx, (s - 1) >> 1, nullptr), &w);
     float x[DIM];
     int img[DIM];
 #pragma unroll
@@ -119,10 +135,61 @@ __global__ void early_advect_kernel(CgLaunch L, RectParams P, const char *__rest
     for (int d = 0; d < DIM; ++d) o[d] = P.periodic[d] ? fmaf((float)img[d], P.L[d], x[d]) : x[d];
 }
 
+// the same on a tet (DIM 3, MD = TetDev) or triangle (DIM 2, TriDev) field: member q from its seed
+// and start cell with the plain mesh kernels' arithmetic (the listed members stayed inside for m steps)
+template <int DIM, int ST, class MD>
+__global__ void early_advect_mesh_kernel(CgLaunch L, MD T, Rk4Args A, const int *__restrict__ cells0, int job,
+                                         const unsigned *__restrict__ count, const int2 *__restrict__ list,
+                                         float *__restrict__ pos)
+{
+    constexpr int NM = 2 * DIM + 1;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long e = t / NM;
+    const int s = (int)(t % NM);
+    if (e >= (long long)*count) return;
+    const int2 it = list[e];
+    const long long p = it.x;
+    const long long idx[3] = {p % L.n[0], (p / L.n[0]) % L.n[1], DIM == 3 ? p / ((long long)L.n[0] * L.n[1]) : 0};
+    int w;
+    const long long q = member(L, idx, s, s == 0 ? 1 : axis_mode(L, idx, (s - 1) >> 1, cells0), &w);
+    float x[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) x[d] = A.seeds[d * A.N + q];
+    int cell = cells0[q];
+    const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
+    const float h = A.job_h[job], hh = 0.5f * h;
+    for (int n = 0; n < it.y; ++n) {
+        const SchedEntry es3[3] = {load_sched(sc + 3 * n), load_sched(sc + 3 * n + 1), load_sched(sc + 3 * n + 2)};
+        float k[4][DIM], y[DIM], lam[DIM + 1];
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {
+            const float c = st == 0 ? 0.0f : (st == 3 ? h : hh);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) y[d] = st == 0 ? x[d] : fmaf(c, k[st - 1][d], x[d]);
+            const SchedEntry &es = es3[st == 0 ? 0 : (st == 3 ? 2 : 1)];
+            const char *fp = T.pairs + (size_t)es.k * T.fstride;
+            if constexpr (DIM == 3) {
+                tet_locate(T, y, &cell, lam);
+                tet_interp<ST>(T, cell, lam, fp, es.a, k[st]);
+            } else {
+                tri_locate(T, y, &cell, lam);
+                tri_interp<ST>(T, cell, lam, fp, es.a, k[st]);
+            }
+        }
+        const float h6 = h * (1.0f / 6.0f);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) x[d] = fmaf(h6, (k[0][d] + k[3][d]) + 2.0f * (k[1][d] + k[2][d]), x[d]);
+    }
+    float *o = pos + (size_t)t * DIM;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o[d] = x[d];
+}
+
 // grad F from the re-integrated stencil (the regular pass's formulas), C, lambda_max, FTLE
 template <int DIM>
-__global__ void early_fd_kernel(CgLaunch L, const unsigned *__restrict__ count, const int2 *__restrict__ list,
-                                const float *__restrict__ pos, double adt, float *__restrict__ ftle)
+__global__ void early_fd_kernel(CgLaunch L, const int *__restrict__ cells0, const unsigned *__restrict__ count,
+                                const int2 *__restrict__ list, const float *__restrict__ pos, double adt,
+                                float *__restrict__ ftle)
 {
     constexpr int NM = 2 * DIM + 1;
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -134,9 +201,10 @@ __global__ void early_fd_kernel(CgLaunch L, const unsigned *__restrict__ count, 
     double G[DIM][DIM];
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
-        int w1, w2, mode;
-        member(L, idx, 1 + 2 * b, &w1, &mode);
-        member(L, idx, 2 + 2 * b, &w2, &mode);
+        int w1, w2;
+        const int mode = axis_mode(L, idx, b, cells0);
+        member(L, idx, 1 + 2 * b, mode, &w1);
+        member(L, idx, 2 + 2 * b, mode, &w2);
         const double h2 = L.h2[b], rh2 = L.rh2[b], sh = L.period[b];
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
@@ -184,9 +252,11 @@ cudaError_t launch_early_cg(const EarlyLaunch &E, cudaStream_t s)
     const unsigned grid = (unsigned)((L.N + bt - 1) / bt);
     if (E.phase == 0) {
         if (L.dim == 2)
-            early_scan_kernel<2><<<grid, bt, 0, s>>>(L, E.job, E.ns, E.t0, E.adt, E.absT, E.count, E.list, E.t_eval);
+            early_scan_kernel<2><<<grid, bt, 0, s>>>(L, E.job, E.ns, E.t0, E.adt, E.absT, E.cells0, E.count, E.list,
+                                                      E.t_eval);
         else
-            early_scan_kernel<3><<<grid, bt, 0, s>>>(L, E.job, E.ns, E.t0, E.adt, E.absT, E.count, E.list, E.t_eval);
+            early_scan_kernel<3><<<grid, bt, 0, s>>>(L, E.job, E.ns, E.t0, E.adt, E.absT, E.cells0, E.count, E.list,
+                                                      E.t_eval);
         return cudaGetLastError();
     }
     if (E.nlisted == 0) return cudaSuccess;
@@ -207,6 +277,21 @@ cudaError_t launch_early_cg(const EarlyLaunch &E, cudaStream_t s)
     const int nm = 2 * L.dim + 1;
     const unsigned ga = (unsigned)((E.nlisted * nm + bt - 1) / bt);
     const char *fr = (const char *)f->d_frames;
+    if (lcs_is_mesh(f)) {
+#define EARLY_MESH(D, ST, MD, T) early_advect_mesh_kernel<D, ST, MD><<<ga, bt, 0, s>>>(L, T, A, E.cells0, E.job, E.count, E.list, E.pos)
+        if (f->kind == LCS_TRI) {
+            const TriDev T = tri_dev(f, E.walk_limit);
+            if (f->storage == LCS_F32) EARLY_MESH(2, LCS_F32, TriDev, T);
+            else if (f->storage == LCS_F16) EARLY_MESH(2, LCS_F16, TriDev, T);
+            else EARLY_MESH(2, LCS_BF16, TriDev, T);
+        } else {
+            const TetDev T = tet_dev(f, E.walk_limit);
+            if (f->storage == LCS_F32) EARLY_MESH(3, LCS_F32, TetDev, T);
+            else if (f->storage == LCS_F16) EARLY_MESH(3, LCS_F16, TetDev, T);
+            else EARLY_MESH(3, LCS_BF16, TetDev, T);
+        }
+#undef EARLY_MESH
+    } else {
 #define EARLY_ADVECT(D, ST) early_advect_kernel<D, ST><<<ga, bt, 0, s>>>(L, P, fr, f->frame_stride, A, E.job, E.count, E.list, E.pos)
     if (L.dim == 2) {
         if (f->storage == LCS_F32) EARLY_ADVECT(2, LCS_F32);
@@ -218,10 +303,11 @@ cudaError_t launch_early_cg(const EarlyLaunch &E, cudaStream_t s)
         else EARLY_ADVECT(3, LCS_BF16);
     }
 #undef EARLY_ADVECT
+    }
     const unsigned gf = (unsigned)((E.nlisted + bt - 1) / bt);
     if (L.dim == 2)
-        early_fd_kernel<2><<<gf, bt, 0, s>>>(L, E.count, E.list, E.pos, E.adt, E.ftle);
+        early_fd_kernel<2><<<gf, bt, 0, s>>>(L, E.cells0, E.count, E.list, E.pos, E.adt, E.ftle);
     else
-        early_fd_kernel<3><<<gf, bt, 0, s>>>(L, E.count, E.list, E.pos, E.adt, E.ftle);
+        early_fd_kernel<3><<<gf, bt, 0, s>>>(L, E.cells0, E.count, E.list, E.pos, E.adt, E.ftle);
     return cudaGetLastError();
 }

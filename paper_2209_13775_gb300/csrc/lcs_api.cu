@@ -1195,9 +1195,10 @@ extern "C" lcs_status lcs_ftle_early(lcs_ctx *ctx, const lcs_field *f, const lcs
     if (!ctx) return LCS_EINVAL;
     const char *who = "lcs_ftle_early";
     if (!f || !s || !o || !fm || !ftle) return lcs_fail(ctx, LCS_EINVAL, "%s: null argument", who);
-    if (o->method != LCS_RK4 || f->kind != LCS_RECTILINEAR)
-        return lcs_fail(ctx, LCS_EUNSUPPORTED, "%s: fixed-step RK4 on a rectilinear field only", who);
+    if (o->method != LCS_RK4) return lcs_fail(ctx, LCS_EUNSUPPORTED, "%s: fixed-step RK4 only", who);
     if (f->dim != s->dim || fm->seeds != s) return lcs_fail(ctx, LCS_EINVAL, "%s: field, seeds and flow map differ", who);
+    if (lcs_is_mesh(f) && (!s->d_cells || s->field_uid != f->uid))
+        return lcs_fail(ctx, LCS_EINVAL, "%s: on a mesh field the seeds must come from lcs_seed_grid on it", who);
     if (s->aux_base_N > 0) return lcs_fail(ctx, LCS_EUNSUPPORTED, "%s: not for auxiliary points", who);
     const int njobs = o->njobs > 1 ? o->njobs : 1;
     if (job < 0 || job >= njobs || njobs > fm->njobs)
@@ -1300,6 +1301,8 @@ extern "C" lcs_status lcs_ftle_early(lcs_ctx *ctx, const lcs_field *f, const lcs
     E.nsteps_max = nsteps_max;
     E.sched = sched;
     E.job_h = D.h;
+    E.cells0 = lcs_is_mesh(f) ? s->d_cells : nullptr;
+    E.walk_limit = o->walk_limit;
     unsigned nl = 0;
     if (e == cudaSuccess) e = launch_early_cg(E, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&nl, count, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream);

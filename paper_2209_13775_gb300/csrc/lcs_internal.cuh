@@ -301,6 +301,8 @@ struct EarlyLaunch {
     int nsteps_max;
     const SchedEntry *sched;     // [njobs][nsteps_max][3]
     const float *job_h;          // [njobs]
+    const int *cells0 = nullptr; // mesh fields: [N] start cells of the seeds (-1 outside)
+    int walk_limit = 0;          // mesh fields: walk steps per location
 };
 
 cudaError_t launch_early_cg(const EarlyLaunch &E, cudaStream_t s);

@@ -133,3 +133,65 @@ def test_early_rejects(ctx):
         lcs.lcs_free_flowmap(fm)
         lcs.lcs_free_seeds(seeds)
         lcs.lcs_free_field(field)
+
+
+def mesh_early(ctx, desc, frames, F, dim, n, lo, hi, t0, T, dt):
+    field = lcs.lcs_load_field(ctx, desc, frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(dim, n, lo, hi), field)
+    N = lcs.lcs_seeds_count(seeds)
+    cells = np.empty(N, dtype=np.int32)
+    lcs.lcs_seeds_get(ctx, seeds, None, cells)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    opts = lcs.advect_opts(lcs.RK4, t0=t0, T=T, dt=dt)
+    lcs.lcs_advect(ctx, field, seeds, opts, fm)
+    x = np.empty((dim, N), np.float32)
+    st = np.empty(N, np.uint8)
+    te = np.empty(N, np.float32)
+    lcs.lcs_flowmap_get(ctx, fm, 0, x, st, te)
+    f = np.empty(N, np.float32)
+    tev = np.empty(N, np.float32)
+    lcs.lcs_ftle_early(ctx, field, seeds, opts, fm, 0, f, tev)
+    # each early value equals the FTLE of a run over its own horizon (same positions, same formulas)
+    ms = np.rint(tev[(tev > 0) & (tev < abs(T))] / dt).astype(int)
+    vals, cnt = np.unique(ms, return_counts=True)
+    one = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    for m in vals[np.argsort(-cnt)][:3]:
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, t0=t0, T=np.sign(T) * m * dt, dt=dt), one)
+        fr = np.empty(N, np.float32)
+        lcs.lcs_ftle(ctx, one, 0, fr)
+        at = np.rint(tev / dt).astype(int) == m
+        np.testing.assert_array_equal(f[at], fr[at])
+    lcs.lcs_synchronize(ctx)
+    for h in (fm, one):
+        lcs.lcs_free_flowmap(h)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    # against the oracle, from its own flow map of the same seeds
+    x0 = oracle.seed_grid(dim, n, lo, hi)
+    xT, so, teo = oracle.rk4(F, x0.astype(np.float64), t0, T, dt, cells=cells)
+    sig, t_eval = oracle.ftle_early(F, n, lo, hi, (0,) * dim, t0, T, dt, xT, so, teo, cells=cells)
+    from gpu_util import check_exit_statuses
+    same = check_exit_statuses(st, te, so, teo, dt)
+    agree = np.abs(tev - t_eval.astype(np.float32)) == 0
+    assert agree.mean() > 0.99, agree.mean()
+    early = (t_eval < abs(T)) & (t_eval > 0)
+    assert early.sum() > 200
+    check_ftle(np.where(agree, f, np.nan), np.where(agree, sig, np.nan))
+    return f, tev
+
+
+@pytest.mark.parametrize("T", [1.0, -1.0])
+def test_early_on_triangles(ctx, T):
+    m = inputs.stenosis_frames(inputs.stenosis_mesh(h=0.05, L=10.0), nframes=40, period=1.0)
+    desc = lcs.field_desc(2, times=m.times, time_periodic=True, period=m.period, kind=lcs.TRI,
+                          mesh=(m.xyz, m.tets, m.nbrs))
+    F = oracle.TriField(m.xyz, m.tets, m.nbrs, m.frames, m.times, True, m.period)
+    mesh_early(ctx, desc, m.frames, F, 2, (100, 33), (0.05, -0.96), (9.95, 0.96), 0.2 if T > 0 else 1.2, T, 0.01)
+
+
+def test_early_on_tets(ctx):
+    p = inputs.pipe_frames(inputs.pipe_mesh(h=0.1, R=1.0, L=2.0), nframes=50, period=1.0, L=2.0)
+    desc = lcs.field_desc(3, times=p.times, time_periodic=True, period=p.period, kind=lcs.TET,
+                          mesh=(p.xyz, p.tets, p.nbrs))
+    F = oracle.TetField(p.xyz, p.tets, p.nbrs, p.frames, p.times, True, p.period)
+    mesh_early(ctx, desc, p.frames, F, 3, (14, 14, 18), (-0.9, -0.9, 0.1), (0.9, 0.9, 1.9), 0.3, 0.8, 0.01)
