@@ -600,15 +600,18 @@ __global__ void slice2d_fill_kernel(RectParams P, const char *__restrict__ frame
 }
 
 // u(x) from a 2D slice: make_stencil's cell and weights, interp's products and order
+template <int PM>
 __device__ __forceinline__ void interp2s(const RectParams &P, const float *x, const float4 *__restrict__ sl, float *u)
 {
     Stencil<2> S;
-    make_stencil<2>(P, x, S);
+    make_stencil<2, PM>(P, x, S);
     const float4 qu = __ldg(sl + 2 * S.v[0]), qv = __ldg(sl + 2 * S.v[0] + 1);
     u[0] = fmaf(S.w[3], qu.w, fmaf(S.w[2], qu.z, fmaf(S.w[1], qu.y, fmaf(S.w[0], qu.x, 0.0f))));
     u[1] = fmaf(S.w[3], qv.w, fmaf(S.w[2], qv.z, fmaf(S.w[1], qv.y, fmaf(S.w[0], qv.x, 0.0f))));
 }
 
+// PM: compile-time periodicity (bit d: axis d periodic; -1: read from P)
+template <int PM>
 __global__ void __launch_bounds__(256) rk4_slice2d_kernel(RectParams P, const float4 *__restrict__ slices,
                                                           long long nodes, Slice2dOffsets O, Rk4Args A)
 {
@@ -617,7 +620,7 @@ __global__ void __launch_bounds__(256) rk4_slice2d_kernel(RectParams P, const fl
     if (i >= A.N) return;
     float x[2] = {A.seeds[i], A.seeds[A.N + i]};
     int img[2] = {0, 0};
-    wrap_periodic<2>(P, x, img);
+    wrap_periodic<2, PM>(P, x, img);
     const int ns = A.job_nsteps[job];
     const float h = A.job_h[job];
     const float4 *sj = slices + O.off[job] * 2 * nodes;
@@ -629,21 +632,21 @@ __global__ void __launch_bounds__(256) rk4_slice2d_kernel(RectParams P, const fl
         const float4 *s0 = sj + (size_t)(3 * n) * ss;
         float k1[2], k2[2], k3[2], k4[2], y[2];
         const float hh = 0.5f * h;
-        interp2s(P, x, s0, k1);
+        interp2s<PM>(P, x, s0, k1);
 #pragma unroll
         for (int c = 0; c < 2; ++c) y[c] = fmaf(hh, k1[c], x[c]);
-        interp2s(P, y, s0 + ss, k2);
+        interp2s<PM>(P, y, s0 + ss, k2);
 #pragma unroll
         for (int c = 0; c < 2; ++c) y[c] = fmaf(hh, k2[c], x[c]);
-        interp2s(P, y, s0 + ss, k3);
+        interp2s<PM>(P, y, s0 + ss, k3);
 #pragma unroll
         for (int c = 0; c < 2; ++c) y[c] = fmaf(h, k3[c], x[c]);
-        interp2s(P, y, s0 + 2 * ss, k4);
+        interp2s<PM>(P, y, s0 + 2 * ss, k4);
         const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
         for (int c = 0; c < 2; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
-        wrap_periodic<2>(P, x, img);
-        if (rect_left<2>(P, x)) {
+        wrap_periodic<2, PM>(P, x, img);
+        if (rect_left<2, PM>(P, x)) {
             st = LCS_TRACER_LEFT;
             te = fmaf((float)(n + 1), h, A.job_t0[job]);
             break;
@@ -681,7 +684,13 @@ static cudaError_t launch_slice2d(const RectParams &P, const lcs_field *f, const
     lcs_tm_end(L.ctx, 2, s);
     lcs_tm_begin(L.ctx, 0, s);
     dim3 grid((unsigned)((A.N + bt - 1) / bt), (unsigned)L.njobs);
-    rk4_slice2d_kernel<<<grid, bt, 0, s>>>(P, slices, nodes, O, A);
+    const int pm = P.periodic[0] | (P.periodic[1] << 1);
+    if (pm == 0)
+        rk4_slice2d_kernel<0><<<grid, bt, 0, s>>>(P, slices, nodes, O, A);
+    else if (pm == 3)
+        rk4_slice2d_kernel<3><<<grid, bt, 0, s>>>(P, slices, nodes, O, A);
+    else
+        rk4_slice2d_kernel<-1><<<grid, bt, 0, s>>>(P, slices, nodes, O, A);
     lcs_tm_end(L.ctx, 0, s);
     return cudaGetLastError();
 }
