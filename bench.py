@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seeds-side", type=int, default=N_SIDE,
                    help="seed lattice side (default 256; smaller only for profiling captures)")
-    p.add_argument("--config", default="c2", choices=["c2", "c3", "c3x", "c4", "c5", "tri", "next"],
+    p.add_argument("--config", default="c2", choices=["c2", "c3", "c3x", "c4", "c5", "tri", "next", "peaks"],
                    help="c2: the 3D ABC workload (default, the headline); c3: the batched sliding-window "
                         "workload; c3x: its full cross product of horizons from multi-horizon snapshots; "
                         "c4: adaptive DP5(4) on the tetrahedral pipe; c5: the learned surrogate; next: the "
@@ -1170,6 +1170,30 @@ def next_arm(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def peaks_arm(args, rank, world, local):
+    """The rates plain loops reach on this GPU (FP32/FP64 FMA, L2-resident and HBM reads), next to the
+    measured copy bandwidth and the FP32 ALU figure the advection rooflines use."""
+    import torch
+
+    from paper_2209_13775_gb300 import lcs
+
+    torch.cuda.set_device(local)
+    ctx = lcs.lcs_create(local, torch.cuda.current_stream())
+    runs = [lcs.lcs_probe_peaks(ctx) for _ in range(max(args.steps, 3))]
+    lcs.lcs_destroy(ctx)
+    med = {k: float(np.median([r[k] for r in runs])) for k in runs[0]}
+    alu, basis = alu_peak()
+    pk, pk_kind = peaks()
+    line = {"metric": "plain-loop peaks on 1 GB300", "value": med["fp32_tflops"], "unit": "TFLOP/s (FP32 FMA)",
+            "n_gpus": 1, "steps": len(runs), "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": "FMA chains (8 per thread, 16 blocks of 256 per SM); reads of a 32 MB buffer "
+                                   "x256 and of a 4 GiB buffer x1 (16-byte loads, grid-stride)"},
+            "peaks": med, "fp32_alu_formula_tflops": alu, "fp32_alu_formula": basis,
+            "driver_hbm_copy_gbs": pk.get("hbm_gbs"), "driver_peaks": pk_kind}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -1190,6 +1214,9 @@ def main():
         return
     if args.config == "tri":
         tri_arm(args, rank, world, local)
+        return
+    if args.config == "peaks":
+        peaks_arm(args, rank, world, local)
         return
     if args.config == "c5":
         c5_arm(args, rank, world, local)

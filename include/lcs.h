@@ -507,6 +507,16 @@ lcs_status lcs_advect_rk4_noalloc(lcs_ctx *ctx, const lcs_field *field, const fl
                                   double t0, double T, double dt, float *xyz, unsigned char *status,
                                   float *t_exit);
 
+/* ------------------------------------------------------------ measurement */
+
+/* The rates this GPU reaches with plain loops, the denominators against which
+ * the advection (FP32), Cauchy-Green (FP64) and gather (L2, HBM) kernels are
+ * judged.  peaks[4] HOST: FP32 FMA TFLOP/s, FP64 FMA TFLOP/s, read GB/s from a
+ * 32 MB L2-resident buffer, read GB/s from a 4 GiB buffer.  Allocates 4 GiB
+ * for the duration of the call and synchronises the context's stream.
+ * Errors: LCS_EINVAL, LCS_ECUDA.                                            */
+lcs_status lcs_probe_peaks(lcs_ctx *ctx, double *peaks);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs
            "lcs_timing_read",
            "lcs_advect_rk4_noalloc", "lcs_gemm_bf16", "lcs_mlp_create", "lcs_mlp_set_params",
            "lcs_mlp_get_params", "lcs_mlp_free", "lcs_mlp_forward", "lcs_mlp_loss_grad", "lcs_mlp_adam",
-           "lcs_surrogate_train"]
+           "lcs_surrogate_train", "lcs_probe_peaks"]
 PHASE_ADVECT, PHASE_REBUNDLE, PHASE_SLICES, PHASE_CG = 0, 1, 2, 3
 NOALLOC_MAX_STEPS = 43680
 MAX_SNAP = 8
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_set_stream": ([P, P], S), "lcs_synchronize": ([P], S),
         "lcs_load_field": ([P, P, P, I, P], S), "lcs_update_frames": ([P, P, P, I], S),
         "lcs_free_field": ([P], None), "lcs_seed_grid": ([P, P, P, P], S), "lcs_seeds_count": ([P], LL),
+        "lcs_probe_peaks": ([P, P], S),
         "lcs_seed_aux": ([P, P, P, P], S), "lcs_seed_aux_field": ([P, P, P, P, P], S),
         "lcs_seeds_get": ([P, P, P, P, I], S), "lcs_free_seeds": ([P], None),
         "lcs_flowmap_create": ([P, P, I, P], S), "lcs_advect": ([P, P, P, P, P], S),
@@ -520,3 +521,10 @@ def lcs_surrogate_train(ctx, field, mlp, desc, samples):
     _check(ctx, load().lcs_surrogate_train(ctx, field, mlp, ctypes.byref(desc), samples.shape[1], ctypes.c_void_p(p),
                                            dev, out.ctypes.data))
     return out
+
+
+def lcs_probe_peaks(ctx):
+    """FP32 and FP64 FMA TFLOP/s, L2-resident and HBM read GB/s measured with plain loops."""
+    out = np.zeros(4)
+    _check(ctx, load().lcs_probe_peaks(ctx, out.ctypes.data_as(ctypes.c_void_p)))
+    return {"fp32_tflops": out[0], "fp64_tflops": out[1], "l2_read_gbs": out[2], "hbm_read_gbs": out[3]}
