@@ -309,13 +309,14 @@ def our_arm(args, rank, world, local):
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s at the maximum SM clock
     achieved = flops / adv_launch_s / 1e12
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "ep_advect3_traffic.json")
+    prof = os.path.join(ROOT, "profiles", "ep_advect3_traffic.md")
     if os.path.exists(prof) and (args.seeds_side, args.grid, args.storage) == (N_SIDE, N_GRID, "f32"):
         try:
-            tj = json.load(open(prof))
+            text = open(prof).read()
+            tj = json.loads(text.split("```json", 1)[1].split("```", 1)[0])
             if tj.get("source_sha") == _src_sha():
                 traffic = tj.get("bytes_per_launch")
-        except (OSError, ValueError):
+        except (OSError, ValueError, IndexError):
             traffic = None
     n_ep = adv_launches / max(args.steps, 1)
     line = {
