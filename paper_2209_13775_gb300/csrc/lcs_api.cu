@@ -915,9 +915,9 @@ static std::string graph_key(const lcs_ctx *ctx, const lcs_field *f, const lcs_s
 {
     std::string k;
     char buf[160];
-    snprintf(buf, sizeof buf, "%llu/%llu/%llu/%p/%zu/%d/%d/%d/%d/%d/%d/%a/v%d|", f->uid, s->uid, fm->uid,
+    snprintf(buf, sizeof buf, "%llu/%llu/%llu/%p/%zu/%d/%d/%d/%d/%d/%d/%a/v%d/w%d|", f->uid, s->uid, fm->uid,
              ctx->d_scratch, ctx->scratch_bytes, o->method, o->variant, o->block_threads, o->episode_steps,
-             o->tracers_per_thread, J.njobs, o->dt, o->variational);
+             o->tracers_per_thread, J.njobs, o->dt, o->variational, o->walk_limit);
     k += buf;
     for (int j = 0; j < J.njobs; ++j) {
         snprintf(buf, sizeof buf, "%a,%a;", J.t0[j], J.T[j]);

@@ -312,3 +312,29 @@ def test_tri_argument_errors(ctx, sten):
         lcs.lcs_free_flowmap(fm)
         lcs.lcs_free_seeds(plain)
         lcs.lcs_free_field(field)
+
+
+def test_tri_graph_replay_equals_direct(ctx, sten):
+    # a captured CUDA graph of the triangle RK4 path (two jobs), replayed, equals direct launches
+    field = lcs.lcs_load_field(ctx, sten_desc(sten), sten.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, (100, 33), (0.05, -0.96), (9.95, 0.96)), field)
+    N = lcs.lcs_seeds_count(seeds)
+    outs = []
+    for use_graph in (False, True, True):
+        fm = lcs.lcs_flowmap_create(ctx, seeds, 2)
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, dt=0.02, job_t0=[0.1, 0.9], job_T=[0.6, -0.8],
+                                                          use_graph=use_graph), fm)
+        r = []
+        for j in range(2):
+            x = np.empty((2, N), np.float32)
+            st = np.empty(N, np.uint8)
+            lcs.lcs_flowmap_get(ctx, fm, j, x, st)
+            r += [x, st]
+        lcs.lcs_synchronize(ctx)
+        lcs.lcs_free_flowmap(fm)
+        outs.append(r)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            np.testing.assert_array_equal(a, b)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
