@@ -61,8 +61,9 @@ def parse():
     p.add_argument("--config", default="c2", choices=["c2", "c3", "c3x", "c4", "c5", "tri", "next", "peaks"],
                    help="c2: the 3D ABC workload (default, the headline); c3: the batched sliding-window "
                         "workload; c3x: its full cross product of horizons from multi-horizon snapshots; "
-                        "c4: adaptive DP5(4) on the tetrahedral pipe; c5: the learned surrogate; next: the "
-                        "eigenvectors, early Cauchy-Green and auxiliary-point passes")
+                        "c4: adaptive DP5(4) on the tetrahedral pipe; c5: the learned surrogate; tri: RK4 on "
+                        "the triangulated stenosis; next: the eigenvectors, early Cauchy-Green, auxiliary-point "
+                        "and variational passes; peaks: plain-loop FMA and read rates")
     p.add_argument("--train-epochs", type=int, default=4, help="c5: training epochs over the 50M samples")
     p.add_argument("--c5-side", type=int, default=16384,
                    help="c5: seed lattice side along x (y is half; default 16384, smaller only for profiling)")
