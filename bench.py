@@ -196,6 +196,19 @@ def reference_arm(args, rank, world):
 
 # ------------------------------------------------------------------ our arm
 
+def max_over_ranks(x, world, device="cuda"):
+    """MAX of a per-rank float over all ranks (the timing rule: the slowest rank sets the time);
+    the value itself for one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def our_arm(args, rank, world, local):
     import torch
 
@@ -257,14 +270,8 @@ def our_arm(args, rank, world, local):
     phase = {name: lcs.lcs_timing_read(ctx, ph) for ph, name in
              enumerate(("advect", "rebundle", "slices", "cg_ftle"))}
     lcs.lcs_timing_enable(ctx, False)
-    elapsed = t_start.elapsed_time(t_stop) / 1e3
+    elapsed = max_over_ranks(t_start.elapsed_time(t_stop) / 1e3, world)
     adv_ms = [a.elapsed_time(b) for a, b in adv_events]
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
     ms_per_step = elapsed / args.steps * 1e3
     value = world * N * args.steps / elapsed
     clocks = clk.summary()
@@ -289,13 +296,7 @@ def our_arm(args, rank, world, local):
         barrier()
         if k > 0:  # the first round is a warm-up of the allocator paths
             e2e_t.append(time.perf_counter() - t0)
-    e2e_el = sum(e2e_t) / len(e2e_t) if e2e_t else float("nan")
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([e2e_el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_el = float(t.item())
+    e2e_el = max_over_ranks(sum(e2e_t) / len(e2e_t) if e2e_t else float("nan"), world)
     h2d = g.frames.nbytes
     d2h = ftle_h.numel() * 4 + C_h.numel() * 8
 
