@@ -121,8 +121,8 @@ typedef struct {
  * in host memory or, if frames_on_device, device memory.  The library
  * converts to desc->storage (FP16/BF16 round to nearest).  The call checks
  * every value for finiteness on the device and synchronises the stream.
- * Errors: LCS_EINVAL (descriptor, a non-finite velocity), LCS_ENOMEM,
- * LCS_ECUDA.                                                                */
+ * Errors: LCS_EINVAL (descriptor, a non-finite velocity or node coordinate,
+ * a mesh cell of zero area or volume), LCS_ENOMEM, LCS_ECUDA.               */
 lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *desc, const float *frames,
                           int frames_on_device, lcs_field **out);
 

@@ -346,6 +346,19 @@ static lcs_status load_tet_field(lcs_ctx *ctx, const lcs_field_desc *d, const fl
     }
     for (long long q = 0; q < (long long)dim * d->nnodes; ++q)
         if (!isfinite(d->node_xyz[q])) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: non-finite node coordinate");
+    // a cell of zero area or volume has no inverse map (its barycentric coordinates would not exist)
+    for (long long c = 0; c < d->ncells; ++c) {
+        const int *v = d->tets + (long long)nv * c;
+        const float *a = d->node_xyz + (long long)dim * v[0];
+        double e[3][3];
+        for (int r = 0; r < dim; ++r)
+            for (int k = 0; k < dim; ++k) e[r][k] = (double)d->node_xyz[(long long)dim * v[r + 1] + k] - a[k];
+        const double det = tri ? e[0][0] * e[1][1] - e[0][1] * e[1][0]
+                               : e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                                     e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                                     e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+        if (!(det != 0.0)) return lcs_fail(ctx, LCS_EINVAL, "lcs_load_field: cell %lld is degenerate", c);
+    }
     CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     lcs_field *f = new (std::nothrow) lcs_field();
     if (!f) return lcs_fail(ctx, LCS_ENOMEM, "host allocation");

@@ -338,3 +338,21 @@ def test_tri_graph_replay_equals_direct(ctx, sten):
             np.testing.assert_array_equal(a, b)
     lcs.lcs_free_seeds(seeds)
     lcs.lcs_free_field(field)
+
+
+def test_degenerate_cells_are_rejected(ctx):
+    from meshes import kuhn_mesh
+    pts, tris, nbrs = tri_grid_mesh(3)
+    bad = tris.copy()
+    bad[4] = [bad[4][0], bad[4][0], bad[4][1]]          # two equal vertices: zero area
+    with pytest.raises(lcs.LcsError) as e:
+        lcs.lcs_load_field(ctx, tri_desc(pts, bad, None, [0.0]), np.zeros((1, len(pts), 2), np.float32))
+    assert e.value.status == 1
+    p3, tets, _ = kuhn_mesh(2)
+    p3 = p3.copy()
+    t = tets[0]
+    p3[t[3]] = p3[t[0]] + 0.5 * (p3[t[1]] - p3[t[0]]) + 0.5 * (p3[t[2]] - p3[t[0]])   # coplanar: zero volume
+    desc = lcs.field_desc(3, times=[0.0], kind=lcs.TET, mesh=(p3, tets, None))
+    with pytest.raises(lcs.LcsError) as e:
+        lcs.lcs_load_field(ctx, desc, np.zeros((1, len(p3), 3), np.float32))
+    assert e.value.status == 1
