@@ -103,6 +103,8 @@ __global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const
     const int ns = A.job_nsteps[job];
     const float h = A.job_h[job], hh = 0.5f * h;
     int si = 0;   // next snapshot
+    TriCache cc;
+    tri_cache_init(cc);
     for (int n = 0; n < ns && st == LCS_TRACER_OK; ++n) {
         const SchedEntry e[3] = {load_sched(sc + 3 * n), load_sched(sc + 3 * n + 1), load_sched(sc + 3 * n + 2)};
         float k[4][2], y[2], lam[3];
@@ -113,9 +115,9 @@ __global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const
 #pragma unroll
             for (int q = 0; q < 2; ++q) y[q] = s == 0 ? x[q] : fmaf(c, k[s - 1][q], x[q]);
             const SchedEntry &es = e[s == 0 ? 0 : (s == 3 ? 2 : 1)];
-            r = tri_locate(T, y, &cell, lam);
+            r = tri_locate_cached(T, y, &cell, lam, cc);
             if (r != TET_INSIDE) break;
-            tri_interp<ST>(T, cell, lam, T.pairs + (size_t)es.k * T.fstride, es.a, k[s]);
+            tri_interp_cached<ST>(T, cell, es.k, lam, T.pairs + (size_t)es.k * T.fstride, es.a, k[s], cc);
         }
         if (r != TET_INSIDE) {  // a stage point left the mesh: freeze at the start of the step
             st = r == TET_OUTSIDE ? LCS_TRACER_LEFT : LCS_TRACER_WALKFAIL;

@@ -8,6 +8,7 @@
 //    triangles listed for the point's bin, so meshes need not be convex (a channel with a
 //    constriction is not); a walk past its step limit reports WALKFAIL.
 //  * tri_interp: P1 interpolation of the frame pair k, blended in time at the vertices.
+//  * TriCache: the RK4 kernel's registers holding the last cell's map and vertex pairs.
 //  * orient2d_sign: exact orientation of three FP32 points (FP64 filter, exact expansion
 //    sum of the six two-factor products when the filter cannot decide).
 #pragma once
@@ -34,14 +35,18 @@ struct TriDev {
 
 TriDev tri_dev(const lcs_field *f, int walk_limit);  // tri_store.cu
 
-__device__ __forceinline__ void tri_bary(const TriDev &T, int c, const float *x, float *lam)
+// barycentric coordinates of x from a triangle's map m and vertex 0
+__device__ __forceinline__ void tri_bary_mv(const float4 m, const float2 v, const float *x, float *lam)
 {
-    const float4 m = __ldg(T.tmap + c);
-    const float2 v = __ldg(T.tv0 + c);
     const float dx = x[0] - v.x, dy = x[1] - v.y;
     lam[1] = fmaf(m.x, dx, m.y * dy);
     lam[2] = fmaf(m.z, dx, m.w * dy);
     lam[0] = 1.0f - lam[1] - lam[2];
+}
+
+__device__ __forceinline__ void tri_bary(const TriDev &T, int c, const float *x, float *lam)
+{
+    tri_bary_mv(__ldg(T.tmap + c), __ldg(T.tv0 + c), x, lam);
 }
 
 // the triangles listed for x's bin, in id order: the first whose coordinates all reach -tol
@@ -68,6 +73,62 @@ __device__ __forceinline__ int tri_locate(const TriDev &T, const float *x, int *
     if (c < 0 || c >= T.ncells) c = 0;
     for (int it = 0; it < T.walk_limit; ++it) {
         tri_bary(T, c, x, lam);
+        int jm = 0;
+        float lm = lam[0];
+        if (lam[1] < lm) {
+            lm = lam[1];
+            jm = 1;
+        }
+        if (lam[2] < lm) {
+            lm = lam[2];
+            jm = 2;
+        }
+        if (lm >= -T.tol) {
+            *cell = c;
+            return TET_INSIDE;
+        }
+        const int4 nb = __ldg(T.nbrs + c);
+        const int n = jm == 0 ? nb.x : jm == 1 ? nb.y : nb.z;
+        if (n < 0) return T.convex ? TET_OUTSIDE : tri_bin_scan(T, x, cell, lam);
+        c = n;
+    }
+    *cell = c;
+    return TET_WALKFAIL;
+}
+
+// The RK4 kernel's register cache: the map of the cell its last walk ended in, and the vertex
+// pairs of the cell and frame interval it last interpolated.  Consecutive stage points of a
+// tracer mostly share a cell and an interval (steps are short against cells and frame gaps), so
+// a walk that starts in the held cell and stays there, and an interpolation in the held cell
+// and interval, issue no loads.  A hit reuses exactly the values a reload would read: results
+// are bit-identical to the uncached walk and interpolation.
+struct TriCache {
+    float4 m;
+    float2 v;
+    int mc;        // cell of m, v (-1: none)
+    int pc, pk;    // cell and interval of ua, ub (-1: none)
+    float ua[3][2], ub[3][2];
+};
+
+__device__ __forceinline__ void tri_cache_init(TriCache &cc)
+{
+    cc.mc = -1;
+    cc.pc = -1;
+    cc.pk = -1;
+}
+
+// tri_locate with the map of each visited cell taken from, or put into, the cache
+__device__ __forceinline__ int tri_locate_cached(const TriDev &T, const float *x, int *cell, float *lam, TriCache &cc)
+{
+    int c = *cell;
+    if (c < 0 || c >= T.ncells) c = 0;
+    for (int it = 0; it < T.walk_limit; ++it) {
+        if (c != cc.mc) {
+            cc.m = __ldg(T.tmap + c);
+            cc.v = __ldg(T.tv0 + c);
+            cc.mc = c;
+        }
+        tri_bary_mv(cc.m, cc.v, x, lam);
         int jm = 0;
         float lm = lam[0];
         if (lam[1] < lm) {
@@ -132,22 +193,47 @@ struct TriPair<LCS_BF16> {
     }
 };
 
-// u = sum_i lam_i [(1 - a) u_k + a u_{k+1}](vertex i) from the interval pair at fp
+// u = sum_i lam_i [(1 - a) u_k + a u_{k+1}](vertex i) from the vertices' pairs (u_k, u_{k+1})
+__device__ __forceinline__ void tri_blend(const float *lam, const float (*ua)[2], const float (*ub)[2], float a,
+                                          float *u)
+{
+    const float g = 1.0f - a;
+    float acc[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+            acc[q] = fmaf(lam[i], a == 0.0f ? ua[i][q] : fmaf(a, ub[i][q], g * ua[i][q]), acc[q]);
+    u[0] = acc[0];
+    u[1] = acc[1];
+}
+
+// tri_blend of cell c's vertices from the interval pair at fp
 template <int ST>
 __device__ __forceinline__ void tri_interp(const TriDev &T, int c, const float *lam, const char *fp, float a, float *u)
 {
     const int4 t = __ldg(T.tris + c);
-    const int vs[3] = {t.x, t.y, t.z};
-    const float g = 1.0f - a;
-    float acc[2] = {0.0f, 0.0f}, va[2], vb[2];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        TriPair<ST>::ld(fp, vs[i], va, vb);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) acc[q] = fmaf(lam[i], a == 0.0f ? va[q] : fmaf(a, vb[q], g * va[q]), acc[q]);
+    float ua[3][2], ub[3][2];
+    TriPair<ST>::ld(fp, t.x, ua[0], ub[0]);
+    TriPair<ST>::ld(fp, t.y, ua[1], ub[1]);
+    TriPair<ST>::ld(fp, t.z, ua[2], ub[2]);
+    tri_blend(lam, ua, ub, a, u);
+}
+
+// tri_interp in interval k (pairs at fp) with the vertex pairs taken from, or put into, the cache
+template <int ST>
+__device__ __forceinline__ void tri_interp_cached(const TriDev &T, int c, int k, const float *lam, const char *fp,
+                                                  float a, float *u, TriCache &cc)
+{
+    if (c != cc.pc || k != cc.pk) {
+        const int4 t = __ldg(T.tris + c);
+        TriPair<ST>::ld(fp, t.x, cc.ua[0], cc.ub[0]);
+        TriPair<ST>::ld(fp, t.y, cc.ua[1], cc.ub[1]);
+        TriPair<ST>::ld(fp, t.z, cc.ua[2], cc.ub[2]);
+        cc.pc = c;
+        cc.pk = k;
     }
-    u[0] = acc[0];
-    u[1] = acc[1];
+    tri_blend(lam, cc.ua, cc.ub, a, u);
 }
 
 // tri_interp's u plus the Jacobian of the P1 interpolant, constant in the triangle
