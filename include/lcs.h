@@ -283,6 +283,19 @@ lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *field, const lcs_seeds *see
 lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *xyz,
                            unsigned char *status, float *t_exit, int on_device);
 
+/* Overwrite job `job` of a flow map with caller-supplied tracer end states,
+ * so that lcs_cauchy_green / lcs_ftle / lcs_cg_eigen evaluate Eq. 1 and the
+ * FTLE on a flow map computed elsewhere (another integrator, a file).
+ * xyz [dim][N] FP32 (unwrapped across periodic axes), status [N] uint8
+ * (LCS_TRACER_* codes), t_exit [N] FP32 or NULL (left unchanged); T is the
+ * job's integration time (its sign the direction; the FTLE divides by |T|).
+ * Buffers are all host or all device (on_device); the library copies them.
+ * The flow map's variational grad F (every job), if any, is invalidated.
+ * Errors: LCS_EINVAL (null flow map or xyz/status, job out of range, T zero or
+ * not finite, a host status value above LCS_TRACER_WALKFAIL), LCS_ECUDA.      */
+lcs_status lcs_flowmap_set(lcs_ctx *ctx, lcs_flowmap *fm, int job, const float *xyz,
+                           const unsigned char *status, const float *t_exit, double T, int on_device);
+
 /* grad F of every tracer of job `job` from the variational equations (Sec. 1:
  * the linearised flow map, the alternative to differencing the seed grid):
  * lcs_advect with opts.variational integrates dM/dt = J(x, t) M, M(t0) = I,

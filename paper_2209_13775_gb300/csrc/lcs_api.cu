@@ -1115,6 +1115,34 @@ extern "C" lcs_status lcs_flowmap_get(lcs_ctx *ctx, const lcs_flowmap *fm, int j
     return LCS_OK;
 }
 
+extern "C" lcs_status lcs_flowmap_set(lcs_ctx *ctx, lcs_flowmap *fm, int job, const float *xyz,
+                                      const unsigned char *status, const float *t_exit, double T, int on_device)
+{
+    if (!ctx) return LCS_EINVAL;
+    const char *who = "lcs_flowmap_set";
+    if (!fm || !xyz || !status) return lcs_fail(ctx, LCS_EINVAL, "%s: null argument", who);
+    if (job < 0 || job >= fm->njobs) return lcs_fail(ctx, LCS_EINVAL, "%s: job %d out of range", who, job);
+    if (!(T != 0.0 && std::isfinite(T))) return lcs_fail(ctx, LCS_EINVAL, "%s: T must be finite and nonzero", who);
+    size_t N = (size_t)fm->N;
+    if (!on_device)
+        for (size_t i = 0; i < N; ++i)
+            if (status[i] > LCS_TRACER_WALKFAIL)
+                return lcs_fail(ctx, LCS_EINVAL, "%s: status[%zu] = %d is not a tracer status", who, i, (int)status[i]);
+    CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CUDA_TRY(ctx, cudaMemcpyAsync(fm->d_xyz + (size_t)job * fm->dim * N, xyz, sizeof(float) * fm->dim * N, k,
+                                  ctx->stream));
+    CUDA_TRY(ctx, cudaMemcpyAsync(fm->d_status + (size_t)job * N, status, N, k, ctx->stream));
+    if (t_exit)
+        CUDA_TRY(ctx, cudaMemcpyAsync(fm->d_texit + (size_t)job * N, t_exit, sizeof(float) * N, k, ctx->stream));
+    const double absT = fabs(T);
+    CUDA_TRY(ctx, cudaMemcpyAsync(fm->d_absT + job, &absT, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));   // absT lives on this frame
+    fm->T[job] = T;
+    fm->grad_valid = false;
+    return LCS_OK;
+}
+
 // ------------------------------------------------------ grad F, C, FTLE
 
 static lcs_status cg_call(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lam, double *C,

@@ -26,7 +26,7 @@ EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs
            "lcs_load_field", "lcs_update_frames", "lcs_free_field", "lcs_seed_grid", "lcs_seed_aux", "lcs_seed_aux_field",
            "lcs_seeds_count",
            "lcs_seeds_get", "lcs_free_seeds", "lcs_flowmap_create", "lcs_advect", "lcs_flowmap_get",
-           "lcs_flowmap_steps",
+           "lcs_flowmap_set", "lcs_flowmap_steps",
            "lcs_free_flowmap", "lcs_autotune", "lcs_cauchy_green", "lcs_ftle", "lcs_cg_eigen", "lcs_ftle_early", "lcs_ftle_variational",
            "lcs_flowmap_grad",
            "lcs_timing_enable",
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "lcs_seeds_get": ([P, P, P, P, I], S), "lcs_free_seeds": ([P], None),
         "lcs_flowmap_create": ([P, P, I, P], S), "lcs_advect": ([P, P, P, P, P], S),
         "lcs_flowmap_get": ([P, P, I, P, P, P, I], S), "lcs_free_flowmap": ([P], None),
+        "lcs_flowmap_set": ([P, P, I, P, P, P, ctypes.c_double, I], S),
         "lcs_cauchy_green": ([P, P, I, P, I], S), "lcs_ftle": ([P, P, I, P, P, P, I], S),
         "lcs_cg_eigen": ([P, P, I, P, P, I], S), "lcs_ftle_early": ([P, P, P, P, P, I, P, P, I], S),
         "lcs_ftle_variational": ([P, P, I, P, P, P, I], S), "lcs_flowmap_grad": ([P, P, I, P, I], S),
@@ -325,6 +326,18 @@ def lcs_flowmap_get(ctx, fm, job=0, xyz=None, status=None, t_exit=None):
     if len(devs) > 1:
         raise ValueError("outputs must all be host or all be device buffers")
     _check(ctx, load().lcs_flowmap_get(ctx, fm, int(job), *[ctypes.c_void_p(p) for p, _ in ptrs],
+                                       devs.pop() if devs else 0))
+
+
+def lcs_flowmap_set(ctx, fm, job, xyz, status, T, t_exit=None):
+    """Overwrite job `job` with end states computed elsewhere: xyz [dim][N] float32, status [N] uint8,
+    t_exit [N] float32 or None, T the job's integration time."""
+    arrs = (xyz, status, t_exit)
+    ptrs = [_ptr(a) for a in arrs]
+    devs = {d for (p, d), a in zip(ptrs, arrs) if a is not None}
+    if len(devs) > 1:
+        raise ValueError("inputs must all be host or all be device buffers")
+    _check(ctx, load().lcs_flowmap_set(ctx, fm, int(job), *[ctypes.c_void_p(p) for p, _ in ptrs], float(T),
                                        devs.pop() if devs else 0))
 
 

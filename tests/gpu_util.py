@@ -59,6 +59,24 @@ def gpu_run(ctx, g, n, lo, hi, periodic, T, dt, t0=0.0, storage=lcs.F32, variant
     return out
 
 
+def gpu_cg_of(ctx, seeds, xT, st, T, nout, dim, want_eig=False):
+    """The library's grad F / Eq. 1 / FTLE (and eigenpairs) on a flow map made elsewhere: xT [dim][M]
+    (rounded to FP32) and st [M] go in through lcs_flowmap_set over `seeds`; nout values per output
+    (the lattice seeds).  Lets a test feed the oracle's own flow map to the library's FD/CG/FTLE."""
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    lcs.lcs_flowmap_set(ctx, fm, 0, np.ascontiguousarray(xT, dtype=np.float32),
+                        np.ascontiguousarray(st, dtype=np.uint8), T)
+    out = {"ftle": np.empty(nout, dtype=np.float32), "lam": np.empty(nout),
+           "C": np.empty((nout, 3 if dim == 2 else 6))}
+    lcs.lcs_ftle(ctx, fm, 0, out["ftle"], out["lam"], out["C"])
+    if want_eig:
+        out["ev"] = np.empty((nout, dim))
+        lcs.lcs_cg_eigen(ctx, fm, 0, out["ev"])
+    lcs.lcs_synchronize(ctx)
+    lcs.lcs_free_flowmap(fm)
+    return out
+
+
 def oracle_field(g):
     return oracle.RectField(g.frames, g.times, g.origin, g.spacing, g.periodic, g.time_periodic, g.period)
 

@@ -47,10 +47,18 @@ def gpu_curve(ctx, desc, frames, dim, n, lo, hi, periodic, t0, T, dt, fracs, mes
     lcs.lcs_free_flowmap(fm)
     lcs.lcs_free_seeds(seeds)
     lcs.lcs_free_field(field)
+    endpoint = [0 if p else 1 for p in periodic]
+    np.testing.assert_array_equal(x0, oracle.seed_grid(dim, n, lo, hi, endpoint))
     return x0, cells, xs, sts
 
 
-def e_s_curve(F, x0, cells, xs, sts, t0, T, dt, fracs, L, periodic):
+def e_s_curve(F, n, lo, hi, gpu_cells, xs, sts, t0, T, dt, fracs, L, periodic):
+    """e_S from the oracle's own seeds (and, on meshes, its own seed cells, which the library's equal)."""
+    x0 = oracle.seed_grid(len(n), n, lo, hi, [0 if p else 1 for p in periodic])
+    cells = None
+    if gpu_cells is not None:
+        cells = F.locate_seeds(x0)
+        np.testing.assert_array_equal(gpu_cells, cells)
     out = []
     for f, xg, sg in zip(fracs, xs, sts):
         xo, so, _ = oracle.rk4(F, x0.astype(np.float64), t0, f * T, dt, cells=cells)
@@ -86,7 +94,7 @@ def test_e_s_double_gyre(ctx):
     n, lo, hi, T, dt = (64, 64), (0.0, 0.0), (2.0, 1.0), 10.0, 0.05
     x0, _, xs, sts = gpu_curve(ctx, rect_desc(g), g.frames, 2, n, lo, hi, (0, 0), 0.0, T, dt, FRACS)
     F = oracle.RectField(g.frames, g.times, g.origin, g.spacing, g.periodic, g.time_periodic, g.period)
-    curve = e_s_curve(F, x0, None, xs, sts, 0.0, T, dt, FRACS, (2.0, 1.0), (0, 0))
+    curve = e_s_curve(F, n, lo, hi, None, xs, sts, 0.0, T, dt, FRACS, (2.0, 1.0), (0, 0))
     report("double gyre (4096 tracers)", curve)
     smax = sigma_max(F, 2, n, lo, hi, (0, 0), 0.0, T, dt)
     for f, e, nok in curve:
@@ -99,7 +107,7 @@ def test_e_s_abc(ctx):
     n, lo, hi, T, dt = (16, 16, 16), (0.0, 0.0, 0.0), (L, L, L), 2.0, 0.02
     x0, _, xs, sts = gpu_curve(ctx, rect_desc(g), g.frames, 3, n, lo, hi, (1, 1, 1), 0.0, T, dt, FRACS)
     F = oracle.RectField(g.frames, g.times, g.origin, g.spacing, g.periodic, g.time_periodic, g.period)
-    curve = e_s_curve(F, x0, None, xs, sts, 0.0, T, dt, FRACS, (L, L, L), (1, 1, 1))
+    curve = e_s_curve(F, n, lo, hi, None, xs, sts, 0.0, T, dt, FRACS, (L, L, L), (1, 1, 1))
     report("ABC (4096 tracers)", curve)
     smax = sigma_max(F, 3, n, lo, hi, (1, 1, 1), 0.0, T, dt)
     for f, e, nok in curve:
@@ -113,7 +121,7 @@ def test_e_s_pipe_on_tets(ctx):
     n, lo, hi, T, dt = (16, 16, 16), (-0.6, -0.6, 0.1), (0.6, 0.6, 1.3), 1.0, 0.01
     x0, cells, xs, sts = gpu_curve(ctx, desc, p.frames, 3, n, lo, hi, (0, 0, 0), 0.0, T, dt, FRACS, mesh=True)
     F = oracle.TetField(p.xyz, p.tets, p.nbrs, p.frames, p.times, True, p.period)
-    curve = e_s_curve(F, x0, cells, xs, sts, 0.0, T, dt, FRACS, (2.0, 2.0, 2.0), (0, 0, 0))
+    curve = e_s_curve(F, n, lo, hi, cells, xs, sts, 0.0, T, dt, FRACS, (2.0, 2.0, 2.0), (0, 0, 0))
     report("pipe on tets (4096 tracers)", curve)
     for f, e, nok in curve:
         assert nok > 2000 and e <= 2e-5, (f, e)     # the tet path's flow-map tolerance

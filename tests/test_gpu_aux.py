@@ -9,7 +9,7 @@ import torch
 
 import oracle
 from paper_2209_13775_gb300 import inputs, lcs
-from gpu_util import check_ftle, rect_desc
+from gpu_util import check_ftle, gpu_cg_of, rect_desc
 
 pytestmark = pytest.mark.gpu
 
@@ -58,7 +58,25 @@ def oracle_aux(g, n, lo, hi, periodic, delta, T, dt):
     G = oracle.aux_gradient(xa, xT, st)
     C = oracle.cauchy_green(G)
     lam, sig = oracle.ftle(C, g.dim, T)
-    return xa, st, sig
+    return xa, st, sig, xT
+
+
+def cg_on_oracle_flowmap(ctx, g, n, lo, hi, periodic, delta, xa, xT, st, T):
+    """The oracle's auxiliary-point flow map, rounded to FP32, through the library's differences and
+    Eq. 1 (lcs_flowmap_set on an auxiliary seed set) and through the oracle's: C bit for bit, and the
+    largest eigenvalue of both eigen paths within rounding of the oracle's."""
+    lat = lcs.lcs_seed_grid(ctx, lcs.seed_desc(g.dim, n, lo, hi, periodic))
+    aux = lcs.lcs_seed_aux(ctx, lat, delta)
+    N = lcs.lcs_seeds_count(lat)
+    x32 = xT.astype(np.float32)
+    r = gpu_cg_of(ctx, aux, x32, st, T, N, g.dim, want_eig=True)
+    lcs.lcs_free_seeds(aux)
+    lcs.lcs_free_seeds(lat)
+    C = oracle.cauchy_green(oracle.aux_gradient(xa, x32.astype(np.float64), st))
+    np.testing.assert_array_equal(r["C"], C)
+    lam, _ = oracle.ftle(C, g.dim, T)
+    np.testing.assert_allclose(r["lam"], lam, rtol=1e-12)
+    np.testing.assert_allclose(r["ev"][:, -1], lam, rtol=1e-12)
 
 
 def test_aux_gyre(ctx):
@@ -66,14 +84,11 @@ def test_aux_gyre(ctx):
     n, lo, hi, T, dt = (96, 48), (0.0, 0.0), (2.0, 1.0), 5.0, 0.05
     delta = [2.0 / 95 / 8, 1.0 / 47 / 8]
     r = run_aux(ctx, g, n, lo, hi, (0, 0), delta, T, dt)
-    xa, st, sig = oracle_aux(g, n, lo, hi, (0, 0), delta, T, dt)
+    xa, st, sig, xT = oracle_aux(g, n, lo, hi, (0, 0), delta, T, dt)
     np.testing.assert_array_equal(r["xa"], xa)
     np.testing.assert_array_equal(r["st"], st)
     check_ftle(r["ftle"], sig)
-    # C from the GPU's own positions: the oracle's formula on them, bit for bit
-    G = oracle.aux_gradient(r["xa"], r["x"].astype(np.float64), r["st"])
-    np.testing.assert_array_equal(r["C"], oracle.cauchy_green(G))
-    np.testing.assert_allclose(r["ev"][:, -1], oracle.ftle(r["C"], 2, T)[0], rtol=1e-12)
+    cg_on_oracle_flowmap(ctx, g, n, lo, hi, (0, 0), delta, xa, xT, st, T)
 
 
 @pytest.mark.parametrize("variant", [1, 3])
@@ -83,11 +98,10 @@ def test_aux_abc(ctx, variant):
     n, lo, hi, T, dt = (20, 18, 16), (0.0, 0.0, 0.0), (L, L, L), 2.0, 0.02
     delta = [L / 20 / 4, L / 18 / 4, L / 16 / 4]
     r = run_aux(ctx, g, n, lo, hi, (1, 1, 1), delta, T, dt, variant=variant)
-    xa, st, sig = oracle_aux(g, n, lo, hi, (1, 1, 1), delta, T, dt)
+    xa, st, sig, xT = oracle_aux(g, n, lo, hi, (1, 1, 1), delta, T, dt)
     np.testing.assert_array_equal(r["xa"], xa)
     check_ftle(r["ftle"], sig)
-    G = oracle.aux_gradient(r["xa"], r["x"].astype(np.float64), r["st"])
-    np.testing.assert_array_equal(r["C"], oracle.cauchy_green(G))
+    cg_on_oracle_flowmap(ctx, g, n, lo, hi, (1, 1, 1), delta, xa, xT, st, T)
 
 
 def test_aux_with_lattice_step_equals_lattice(ctx):
@@ -137,7 +151,7 @@ def test_aux_rejects(ctx):
 @pytest.mark.parametrize("kind", ["tri", "tet"])
 def test_aux_on_meshes(ctx, kind):
     # auxiliary points on a mesh field: located exactly (bit-identical cells), advected with the mesh
-    # rules, differenced per seed; FTLE against the oracle's, C bit-identical on the GPU's positions
+    # rules, differenced per seed; FTLE against the oracle's, C bit-identical on the oracle's positions
     from gpu_util import check_exit_statuses
     if kind == "tri":
         m = inputs.stenosis_frames(inputs.stenosis_mesh(h=0.05, L=10.0), nframes=40, period=1.0)
@@ -171,11 +185,7 @@ def test_aux_on_meshes(ctx, kind):
     C = np.empty((N, 3 if dim == 2 else 6))
     lcs.lcs_ftle(ctx, fm, 0, f, None, C)
     lcs.lcs_synchronize(ctx)
-    for h_ in (fm,):
-        lcs.lcs_free_flowmap(h_)
-    lcs.lcs_free_seeds(aux)
-    lcs.lcs_free_seeds(lat)
-    lcs.lcs_free_field(field)
+    lcs.lcs_free_flowmap(fm)
     xo = oracle.aux_points(oracle.seed_grid(dim, n, lo, hi), delta)
     np.testing.assert_array_equal(xa, xo)
     co = F.locate_seeds(xo)
@@ -183,8 +193,13 @@ def test_aux_on_meshes(ctx, kind):
     xT, so, teo = oracle.rk4(F, xo.astype(np.float64), t0, T, dt, cells=co)
     same = check_exit_statuses(st, te, so, teo, dt)
     assert (so == oracle.OUTSIDE).sum() > 10 and (so == oracle.OK).sum() > 1000
-    G = oracle.aux_gradient(xa, x.astype(np.float64), st)
-    np.testing.assert_array_equal(C, oracle.cauchy_green(G))
+    # the oracle's flow map through the library's differences and Eq. 1: C bit for bit
+    x32 = xT.astype(np.float32)
+    r = gpu_cg_of(ctx, aux, x32, so, T, N, dim)
+    lcs.lcs_free_seeds(aux)
+    lcs.lcs_free_seeds(lat)
+    lcs.lcs_free_field(field)
+    np.testing.assert_array_equal(r["C"], oracle.cauchy_green(oracle.aux_gradient(xo, x32.astype(np.float64), so)))
     Go = oracle.aux_gradient(xo, xT, so)
     _, sig = oracle.ftle(oracle.cauchy_green(Go), dim, T)
     seed_same = same.reshape(N, 2 * dim).all(axis=1)

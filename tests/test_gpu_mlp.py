@@ -124,11 +124,13 @@ def run_surrogate(ctx, g, m, n, T, tol, dt=0.05, t0=0.0):
     lcs.lcs_flowmap_get(ctx, fm, 0, x, st)
     if m is not None:
         lcs.lcs_flowmap_steps(ctx, fm, 0, cnt)
-    x0 = np.empty((2, N), dtype=np.float32)
-    lcs.lcs_seeds_get(ctx, seeds, x0)
+    x0g = np.empty((2, N), dtype=np.float32)
+    lcs.lcs_seeds_get(ctx, seeds, x0g)
     lcs.lcs_free_flowmap(fm)
     lcs.lcs_free_seeds(seeds)
     lcs.lcs_free_field(field)
+    x0 = oracle.seed_grid(2, n, (0.0, 0.0), (2.0, 1.0))     # the oracle's own seeds; the library's equal them
+    np.testing.assert_array_equal(x0g, x0)
     return x0, x, st, cnt
 
 

@@ -12,8 +12,8 @@ import torch
 
 import oracle
 from paper_2209_13775_gb300 import inputs, lcs
-from gpu_util import (check_flowmap, check_ftle, gpu_run, oracle_ftle_at, oracle_run, round_bf16,
-                      round_fp16)
+from gpu_util import (check_flowmap, check_ftle, gpu_cg_of, gpu_run, oracle_field, oracle_ftle_at, oracle_run,
+                      round_bf16, round_fp16)
 
 pytestmark = pytest.mark.gpu
 
@@ -188,17 +188,29 @@ def test_autotune_picks_valid_options_and_caches(ctx, gyre, tmp_path):
         np.testing.assert_array_equal(a["xyz"][j], b["xyz"][j])
 
 
-def test_cauchy_green_matches_oracle_on_gpu_positions(ctx, gyre):
-    # same FP32 positions in: grad F and C are bit-identical, lambda_max within rounding
+def test_cauchy_green_matches_oracle_on_the_same_positions(ctx, gyre):
+    # the oracle's flow map, rounded to FP32, into both (the library's through lcs_flowmap_set):
+    # grad F and C bit-identical, lambda_max within rounding; a cut-out block of LEFT tracers makes
+    # the one-sided and invalid stencils run
     n, lo, hi, T = (128, 64), (0.0, 0.0), (2.0, 1.0), 10.0
-    g = gpu_run(ctx, gyre, n, lo, hi, (0, 0), T, 0.05, want_C=True)
-    x = g["xyz"][0].astype(np.float64)
-    G = oracle.flowmap_gradient(2, n, oracle.lattice_spacing(2, n, lo, hi), (0, 0), (0, 0), x, g["status"][0])
+    x0 = oracle.seed_grid(2, n, lo, hi)
+    xT, st, _ = oracle.rk4(oracle_field(gyre), x0.astype(np.float64), 0.0, T, 0.05)
+    st = st.copy()
+    st.reshape(n[1], n[0])[20:23, 40:70] = oracle.LEFT
+    x32 = xT.astype(np.float32)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, lo, hi))
+    g = gpu_cg_of(ctx, seeds, x32, st, T, n[0] * n[1], 2)
+    lcs.lcs_free_seeds(seeds)
+    G = oracle.flowmap_gradient(2, n, oracle.lattice_spacing(2, n, lo, hi), (0, 0), (0, 0),
+                                x32.astype(np.float64), st)
     C = oracle.cauchy_green(G)
-    np.testing.assert_array_equal(g["C"][0], C)
+    np.testing.assert_array_equal(g["C"], C)
     lam, sig = oracle.ftle(C, 2, T)
-    np.testing.assert_allclose(g["lam"][0], lam, rtol=1e-13, atol=0)
-    np.testing.assert_allclose(g["ftle"][0], sig.astype(np.float32), rtol=1e-6, atol=0)
+    assert np.isnan(sig).sum() > 0
+    np.testing.assert_array_equal(np.isfinite(g["ftle"]), np.isfinite(sig))
+    ok = np.isfinite(sig)
+    np.testing.assert_allclose(g["lam"][ok], lam[ok], rtol=1e-13, atol=0)
+    np.testing.assert_allclose(g["ftle"][ok], sig[ok].astype(np.float32), rtol=1e-6, atol=0)
 
 
 def test_affine_field_closed_form(ctx):
@@ -210,7 +222,7 @@ def test_affine_field_closed_form(ctx):
     Z = dt * A
     R = np.eye(2) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
     M = np.linalg.matrix_power(R, 40)
-    expect = M @ r["seeds"].astype(np.float64)
+    expect = M @ oracle.seed_grid(2, n, lo, hi).astype(np.float64)
     assert np.abs(r["xyz"][0] - expect).max() < 2e-5
     # grad F = M everywhere, so C and FTLE are constant
     lam_exact = np.linalg.eigvalsh(M.T @ M)[-1]
@@ -285,26 +297,32 @@ def test_abc_periodic_3d_parity(ctx, abc_small, storage):
     check_ftle(r["ftle"][0], o["ftle"])
 
 
-def test_cauchy_green_3d_matches_oracle_on_gpu_positions(ctx, abc_small):
-    # same FP32 positions in: grad F and C bit-identical (the division by 2h is correctly rounded),
-    # lambda_max within 1e-12 of the oracle's Jacobi eigenvalue, FTLE within a few FP32 ulps
+def test_cauchy_green_3d_matches_oracle_on_the_same_positions(ctx, abc_small):
+    # the oracle's flow map, rounded to FP32, into both: grad F and C bit-identical (the division by
+    # 2h is correctly rounded), lambda_max within 1e-12 of the oracle's Jacobi eigenvalue, FTLE within
+    # a few FP32 ulps; periodic (unwrapped positions, shift by the period) and bounded lattices
     L = 2 * np.pi
     cases = [((37, 30, 29), (0.0, 0.0, 0.0), (L, L, L), (1, 1, 1), 2.0),
              ((21, 19, 17), (0.5, 1.0, 0.25), (5.5, 4.0, 6.0), (0, 0, 0), -1.5)]
+    F = oracle_field(abc_small)
     for n, lo, hi, per, T in cases:
-        g = gpu_run(ctx, abc_small, n, lo, hi, per, T, 0.02, want_C=True)
-        x = g["xyz"][0].astype(np.float64)
         endpoint = [0 if p else 1 for p in per]
+        x0 = oracle.seed_grid(3, n, lo, hi, endpoint)
+        xT, st, _ = oracle.rk4(F, x0.astype(np.float64), 0.0, T, 0.02)
+        x32 = xT.astype(np.float32)
+        seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, n, lo, hi, per))
+        g = gpu_cg_of(ctx, seeds, x32, st, T, n[0] * n[1] * n[2], 3)
+        lcs.lcs_free_seeds(seeds)
         h = oracle.lattice_spacing(3, n, lo, hi, endpoint)
         period = [hi[a] - lo[a] if per[a] else 0.0 for a in range(3)]
-        G = oracle.flowmap_gradient(3, n, h, per, period, x, g["status"][0])
+        G = oracle.flowmap_gradient(3, n, h, per, period, x32.astype(np.float64), st)
         C = oracle.cauchy_green(G)
-        np.testing.assert_array_equal(g["C"][0], C)
+        np.testing.assert_array_equal(g["C"], C)
         lam, sig = oracle.ftle(C, 3, T)
         ok = np.isfinite(lam)
-        np.testing.assert_array_equal(np.isfinite(g["lam"][0]), ok)
-        np.testing.assert_allclose(g["lam"][0][ok], lam[ok], rtol=1e-12, atol=0)
-        np.testing.assert_allclose(g["ftle"][0][ok], sig[ok].astype(np.float32), rtol=1e-6, atol=0)
+        np.testing.assert_array_equal(np.isfinite(g["lam"]), ok)
+        np.testing.assert_allclose(g["lam"][ok], lam[ok], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(g["ftle"][ok], sig[ok].astype(np.float32), rtol=1e-6, atol=0)
 
 
 @pytest.mark.parametrize("storage", [lcs.F32, lcs.F16, lcs.BF16])

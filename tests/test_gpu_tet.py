@@ -385,6 +385,85 @@ def test_rk45_tet_pipe_matches_oracle(ctx, pipe):
     assert np.median(steps_ok) <= 1 and steps_ok.max() <= 10
 
 
+def test_full_size_pipe_rk45_sampled(ctx):
+    """The benchmark's tetrahedral workload at full size -- the 2.36M-tet pipe, 64x64x512 seeds,
+    DP5(4) rtol = atol = 1e-6, T = 1, the same launch options -- against the oracle at sampled seeds.
+    The kernel shares one step size per warp of 32 consecutive seeds, so the oracle integrates, in
+    its 32-lane mode, every whole group holding a sampled seed or a member of its stencil."""
+    mesh = inputs.pipe_frames(inputs.pipe_mesh(), nframes=50, period=1.0)
+    n, lo, hi, T = (64, 64, 512), (-1.0, -1.0, 0.0), (1.0, 1.0, 10.0), 1.0
+    field = lcs.lcs_load_field(ctx, tet_desc(mesh.xyz, mesh.tets, mesh.nbrs, mesh.times, lcs.F32, True,
+                                             mesh.period), mesh.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, n, lo, hi), field)
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK45, t0=0.0, T=T, rtol=1e-6, atol=1e-6, h0=0.01), fm)
+    cells = np.empty(N, dtype=np.int32)
+    lcs.lcs_seeds_get(ctx, seeds, None, cells)
+    x = np.empty((3, N), dtype=np.float32)
+    st = np.empty(N, dtype=np.uint8)
+    te = np.empty(N, dtype=np.float32)
+    lcs.lcs_flowmap_get(ctx, fm, 0, x, st, te)
+    ftle = np.empty(N, dtype=np.float32)
+    lcs.lcs_ftle(ctx, fm, 0, ftle)
+    lcs.lcs_synchronize(ctx)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
+    assert N == 64 * 64 * 512 and (st == lcs.TRACER_WALKFAIL).sum() == 0
+    # samples: seeds whose six neighbours exist on the lattice, spread over the pipe's length
+    rng = np.random.default_rng(44)
+    cand = np.flatnonzero(np.isfinite(ftle))
+    ix, iy, iz = cand % 64, (cand // 64) % 64, cand // 4096
+    cand = cand[(ix > 1) & (ix < 62) & (iy > 1) & (iy < 62) & (iz > 1) & (iz < 510)]
+    sample = np.sort(rng.choice(cand, 32, replace=False))
+    # +-1 and +-2 along each axis: near the wall a one-sided difference needs the second neighbour
+    stencil = np.concatenate([sample + s * o for o in (1, 64, 4096) for s in (-2, -1, 0, 1, 2)])
+    groups = np.unique(stencil // 32)
+    ids = (groups[:, None] * 32 + np.arange(32)[None, :]).ravel()
+    x0 = oracle.seed_grid(3, n, lo, hi)[:, ids]
+    F = oracle.TetField(mesh.xyz, mesh.tets, mesh.nbrs, mesh.frames, mesh.times, True, mesh.period)
+    oc = F.locate_seeds(x0)
+    np.testing.assert_array_equal(oc, cells[ids])          # seed cells bit-exact
+    xo, so, teo, _ = oracle.dp45(F, x0.astype(np.float64), 0.0, T, h0=0.01, rtol=1e-6, atol=1e-6,
+                                 group=32, cells=oc)
+    diff = st[ids] != so                                   # exits decided a step apart, near the outlet
+    assert diff.mean() <= 2e-2, diff.sum()
+    # P1 velocity has kinks across every face, which the embedded error estimate does not see, so
+    # the oracle itself is off the converged flow by up to a few 1e-4 at rtol 1e-6; the kernel (FP32
+    # error norms, so its own accept/reject sequence) is held to the oracle's accuracy against a
+    # converged run (rtol 1e-10), as on the small pipe and the stenosis
+    xr, sr, _, _ = oracle.dp45(F, x0.astype(np.float64), 0.0, T, h0=0.01, rtol=1e-10, atol=1e-10, cells=oc)
+    ok = (st[ids] == so) & (so == oracle.OK) & (sr == oracle.OK)
+    assert ok.sum() > 1000
+    e_ora = np.abs(xo[:, ok] - xr[:, ok]).max(axis=0)
+    e_gpu = np.abs(x[:, ids][:, ok] - xr[:, ok]).max(axis=0)
+    assert np.median(e_gpu) <= 2 * np.median(e_ora) + 1e-6, (np.median(e_gpu), np.median(e_ora))
+    assert e_gpu.max() <= 2 * e_ora.max() + 1e-5, (e_gpu.max(), e_ora.max())
+    # FTLE at the samples from the oracle's own flow map of the integrated groups.  Weyl's inequality
+    # bounds the change of grad F's largest singular value s_max by the norm of the change of grad F;
+    # each column of that change is a combination of position differences over 2h (central: weights
+    # 1, 1; one-sided: 3, 4, 1), so with E the largest position difference over a sample's stencil,
+    # |d sigma| <= ln(1 + 4 sqrt(3) E / h_min) / T, as s_max >= 1 for this volume-preserving flow
+    h = oracle.lattice_spacing(3, n, lo, hi)
+    xT = np.zeros((3, N))
+    sT = np.full(N, oracle.LEFT, dtype=np.uint8)
+    xT[:, ids] = xo
+    sT[ids] = so
+    G = oracle.flowmap_gradient(3, n, h, (0, 0, 0), (0, 0, 0), xT, sT)[sample]
+    _, sig = oracle.ftle(oracle.cauchy_green(G), 3, T)
+    members = stencil.reshape(15, len(sample))
+    agree = (st[members] == sT[members]).all(axis=0)
+    use = agree & np.isfinite(sig)
+    assert use.sum() >= 24
+    E = np.abs(x[:, members].astype(np.float64) - xT[:, members]).max(axis=(0, 1))
+    bound = np.log1p(4 * np.sqrt(3) * E / min(h)) / T + 1e-6
+    d = np.abs(ftle[sample].astype(np.float64) - sig)
+    print("\nC4 full size, %d sampled seeds: FTLE |d| median %.2e max %.2e (bound median %.2e)"
+          % (use.sum(), np.median(d[use]), d[use].max(), np.median(bound[use])))
+    assert (d[use] <= bound[use]).all(), (d[use] - bound[use]).max()
+
+
 # ------------------------------------------------------------------ errors
 
 def test_rk45_and_tet_argument_errors(ctx, pipe):
