@@ -168,8 +168,10 @@ def mesh_early(ctx, desc, frames, F, dim, n, lo, hi, t0, T, dt):
     lcs.lcs_free_field(field)
     # against the oracle, from its own flow map of the same seeds
     x0 = oracle.seed_grid(dim, n, lo, hi)
-    xT, so, teo = oracle.rk4(F, x0.astype(np.float64), t0, T, dt, cells=cells)
-    sig, t_eval = oracle.ftle_early(F, n, lo, hi, (0,) * dim, t0, T, dt, xT, so, teo, cells=cells)
+    ocells = F.locate_seeds(x0)
+    np.testing.assert_array_equal(cells, ocells)
+    xT, so, teo = oracle.rk4(F, x0.astype(np.float64), t0, T, dt, cells=ocells)
+    sig, t_eval = oracle.ftle_early(F, n, lo, hi, (0,) * dim, t0, T, dt, xT, so, teo, cells=ocells)
     from gpu_util import check_exit_statuses
     same = check_exit_statuses(st, te, so, teo, dt)
     agree = np.abs(tev - t_eval.astype(np.float32)) == 0

@@ -1,8 +1,9 @@
 """Eigenvalues and eigenvectors of the Cauchy-Green tensor at every seed (Sec. 2 "Cauchy-Green")
 through lcs_cg_eigen, against the FP64 oracle's Jacobi eigen-decomposition of the same C.
 
-C itself is bit-identical to the oracle's from the same FP32 positions (lcs_cauchy_green), so the
-comparison isolates the eigen-solver: eigenvalues to 1e-12 of lambda_max (and 1e-10 relative for the
+The oracle's own flow map, rounded to FP32, goes into the library (lcs_flowmap_set); C is then
+bit-identical to the oracle's from the same positions (lcs_cauchy_green), so the comparison isolates
+the eigen-solver: eigenvalues to 1e-12 of lambda_max (and 1e-10 relative for the
 small ones), eigenvectors to 1e-10 in direction wherever the eigenvalue is separated from the others
 by more than 1e-6 lambda_max, residuals |C v - lambda v| at rounding level everywhere, and the
 library's sign convention (largest-magnitude component positive).
@@ -28,14 +29,25 @@ def ctx():
 
 
 def run(ctx, g, n, lo, hi, periodic, T, dt):
-    field = lcs.lcs_load_field(ctx, rect_desc(g), g.frames)
+    """The oracle's flow map of the lattice, rounded to FP32, through the library's C, FTLE and eigen
+    calls (lcs_flowmap_set); returns the oracle's C (asserted bit-identical to the library's) and the
+    library's lambda_max, eigenvalues and eigenvectors."""
+    endpoint = [0 if p else 1 for p in periodic]
+    x0 = oracle.seed_grid(g.dim, n, lo, hi, endpoint)
+    F = oracle.RectField(g.frames, g.times, g.origin, g.spacing, g.periodic, g.time_periodic, g.period)
+    xT, st, _ = oracle.rk4(F, x0.astype(np.float64), 0.0, T, dt)
+    x32 = xT.astype(np.float32)
+    h = oracle.lattice_spacing(g.dim, n, lo, hi, endpoint)
+    period = [hi[a] - lo[a] if periodic[a] else 0.0 for a in range(g.dim)]
+    Co = oracle.cauchy_green(oracle.flowmap_gradient(g.dim, n, h, periodic, period, x32.astype(np.float64), st))
     seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(g.dim, n, lo, hi, periodic))
     N = lcs.lcs_seeds_count(seeds)
     fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
-    lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, T=T, dt=dt), fm)
+    lcs.lcs_flowmap_set(ctx, fm, 0, x32, st, T)
     d, np_ = g.dim, (3 if g.dim == 2 else 6)
     C = np.empty((N, np_))
     lcs.lcs_cauchy_green(ctx, fm, 0, C)
+    np.testing.assert_array_equal(C, Co)
     f = np.empty(N, dtype=np.float32)
     lam = np.empty(N)
     lcs.lcs_ftle(ctx, fm, 0, f, lam)
@@ -49,8 +61,7 @@ def run(ctx, g, n, lo, hi, periodic, T, dt):
     np.testing.assert_array_equal(evd.cpu().numpy(), ev)
     lcs.lcs_free_flowmap(fm)
     lcs.lcs_free_seeds(seeds)
-    lcs.lcs_free_field(field)
-    return C, lam, ev, V
+    return Co, lam, ev, V
 
 
 def unpack(C, d):
