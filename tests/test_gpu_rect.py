@@ -12,7 +12,7 @@ import torch
 
 import oracle
 from paper_2209_13775_gb300 import inputs, lcs
-from gpu_util import (check_flowmap, check_ftle, gpu_cg_of, gpu_run, oracle_field, oracle_ftle_at, oracle_run,
+from gpu_util import (check_flowmap, check_ftle, gpu_cg_of, gpu_run, oracle_field, oracle_ftle_at, oracle_run, rect_desc,
                       round_bf16, round_fp16)
 
 pytestmark = pytest.mark.gpu
@@ -418,3 +418,42 @@ def test_full_size_abc_storage_error(ctx, storage):
           % (np.median(d), np.quantile(d, 0.999), d.max(), dx.max()))
     assert np.median(d) <= 5e-2 and np.isfinite(r["ftle"][0]).all()
 
+
+
+def test_full_size_sliding_window_sampled(ctx, gyre, tmp_path):
+    """The batched sliding-window workload at full size -- 64 jobs (32 t0 spaced 0.25, forward and
+    backward, |T| in {2, 4, 8}) of 2048x1024 seeds on the double gyre, launched as the benchmark does
+    (autotuned options, CUDA graph, replayed) -- against the oracle at sampled seeds of every job."""
+    n, lo, hi, dt = (2048, 1024), (0.0, 0.0), (2.0, 1.0), 0.05
+    t0s = [0.25 * k for k in range(32)] * 2
+    Ts = [(2.0, 4.0, 8.0)[k % 3] for k in range(32)] + [-(2.0, 4.0, 8.0)[k % 3] for k in range(32)]
+    field = lcs.lcs_load_field(ctx, rect_desc(gyre), gyre.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, lo, hi))
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 64)
+    opts = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=t0s, job_T=Ts, use_graph=True)
+    lcs.lcs_autotune(ctx, field, seeds, opts, str(tmp_path / "tune.txt"))
+    for _ in range(2):                       # capture, then replay
+        lcs.lcs_advect(ctx, field, seeds, opts, fm)
+    ftle = torch.empty((64, N), dtype=torch.float32, device="cuda")
+    lcs.lcs_ftle(ctx, fm, -1, ftle)
+    lcs.lcs_synchronize(ctx)
+    rng = np.random.default_rng(33)
+    x = np.empty((2, N), dtype=np.float32)
+    st = np.empty(N, dtype=np.uint8)
+    worst = 0.0
+    for j in range(64):
+        i, k = rng.integers(2, n[0] - 2, 6), rng.integers(2, n[1] - 2, 6)
+        sample = np.unique(i + n[0] * k)
+        o = oracle_run(gyre, n, lo, hi, (0, 0), Ts[j], dt, t0=t0s[j], sample=sample)
+        lcs.lcs_flowmap_get(ctx, fm, j, x, st)
+        ids = o["ids"]
+        sig, _, _ = oracle_ftle_at(sample, 2, n, o["h"], (0, 0), o["period"], o["xT"], o["st"], Ts[j])
+        check_flowmap(x[:, ids], o["xyz_s"], st[ids], o["status_s"], 2.0, float(np.nanmax(sig)), Ts[j])
+        d = np.abs(ftle[j, torch.from_numpy(sample).cuda()].cpu().numpy().astype(np.float64) - sig)
+        assert d.max() <= 1e-3, (j, d.max())
+        worst = max(worst, float(d.max()))
+    print("\nC3 full size, 64 jobs x 6 sampled seeds: FTLE |d| max %.2e" % worst)
+    lcs.lcs_free_flowmap(fm)
+    lcs.lcs_free_seeds(seeds)
+    lcs.lcs_free_field(field)
