@@ -266,6 +266,18 @@ def test_invalid_arguments_raise(ctx, gyre):
         assert e.value.status == 1
     with pytest.raises(lcs.LcsError):
         lcs.lcs_flowmap_get(ctx, fm, 3, np.empty((2, 64), dtype=np.float32))
+    # lcs_flowmap_set: job out of range, T zero or not finite, a status that is no tracer status
+    xs, ss = np.zeros((2, 64), dtype=np.float32), np.zeros(64, dtype=np.uint8)
+    for job, T, bad_st in ((1, 1.0, 0), (0, 0.0, 0), (0, float("inf"), 0), (0, 1.0, 9)):
+        ss[5] = bad_st
+        with pytest.raises(lcs.LcsError) as e:
+            lcs.lcs_flowmap_set(ctx, fm, job, xs, ss, T)
+        assert e.value.status == 1
+    ss[5] = 0
+    lcs.lcs_flowmap_set(ctx, fm, 0, xs, ss, -2.0)     # accepted; every seed at the origin: C = 0
+    C = np.empty((64, 3))
+    lcs.lcs_cauchy_green(ctx, fm, 0, C)
+    assert (C == 0).all()
     bad_desc = lcs.field_desc(2, (1, 5), (0, 0), (1, 1), times=[0.0])
     with pytest.raises(lcs.LcsError):
         lcs.lcs_load_field(ctx, bad_desc, np.zeros((1, 5, 1, 2), dtype=np.float32))
