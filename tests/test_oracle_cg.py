@@ -167,6 +167,15 @@ def test_oracle_matches_stored_gyre_fixture(ora):
     spec.loader.exec_module(mg)
     stored = np.loadtxt(os.path.join(here, "gyre_ftle_32x16.txt"))
     np.testing.assert_allclose(mg.gyre_ftle_32x16(), stored, rtol=1e-12, atol=1e-13)
+    # the mesh paths: triangle walk + P1 + RK4 + FD/CG/FTLE, and tets with DP5(4) in 32-lane mode
+    st = np.loadtxt(os.path.join(here, "stenosis_ftle_24x8.txt"))
+    got = mg.stenosis_ftle_24x8()
+    np.testing.assert_array_equal(got[:, 0], st[:, 0])
+    np.testing.assert_allclose(got[:, 1], st[:, 1], rtol=1e-12, atol=1e-13)
+    kd = np.loadtxt(os.path.join(here, "kuhn_dp45_4x4x4.txt"))
+    got = mg.kuhn_dp45_4x4x4()
+    np.testing.assert_allclose(got[:, :3], kd[:, :3], rtol=1e-12, atol=1e-13)
+    np.testing.assert_array_equal(got[:, 3:], kd[:, 3:])
 
 
 def _packed(M):
