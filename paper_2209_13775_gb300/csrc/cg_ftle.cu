@@ -12,99 +12,16 @@
 //    method below), so both equal the plain FP64 definition bit for bit;
 //  * lambda_max: 2x2 from the quadratic formula; 3x3 from the characteristic cubic of
 //    the shifted, scaled matrix (Smith 1961), whose trigonometric root is taken in FP32
-//    and polished by two FP64 Newton steps (relative error ~1e-16 for a simple root);
-//  * FTLE = log1p(lambda_max - 1) / (2 |T|) in FP32 from the FP64 difference, which
-//    keeps its relative accuracy (a few FP32 ulps) also where lambda_max is near 1.
+//    and polished by two FP64 Newton steps (relative error ~1e-15 for a simple root),
+//    and by Jacobi rotations where the two largest eigenvalues (nearly) coincide;
+//  * FTLE = ln(lambda_max) / (2 |T|) in FP32: log1p of the FP64 difference lambda_max - 1
+//    near 1, which keeps its relative accuracy (a few FP32 ulps) where sigma is near 0, and
+//    log of lambda_max elsewhere (log_lambda).
 #include "lcs_internal.cuh"
 
 #include <math.h>
 
 #include "cg_device.cuh"
-
-// All eigenpairs of the packed symmetric C by cyclic Jacobi rotations in FP64.  Each
-// rotation zeroes a_pq with t = tan(theta) the smaller root of t^2 + 2 tau t - 1 = 0,
-// tau = (a_qq - a_pp) / (2 a_pq), updates the diagonal as a_pp - t a_pq and a_qq + t a_pq
-// (Rutishauser's form), rotates the other row of the pair and accumulates V <- V J.  A pair
-// counts as converged when |a_pq| <= 1e-18 sqrt(|a_pp a_qq|), a relative test that keeps
-// the small eigenvalues of a graded C accurate; at most 16 sweeps.  Ascending order, each
-// eigenvector with its largest-magnitude component positive.
-template <int DIM>
-__device__ __forceinline__ void eig_jacobi(const double *Cp, double *ev, double *V)
-{
-    double A[DIM][DIM];
-    int o = 0;
-#pragma unroll
-    for (int i = 0; i < DIM; ++i)
-#pragma unroll
-        for (int j = i; j < DIM; ++j) {
-            A[i][j] = Cp[o];
-            A[j][i] = Cp[o];
-            ++o;
-        }
-    double W[DIM][DIM];
-#pragma unroll
-    for (int i = 0; i < DIM; ++i)
-#pragma unroll
-        for (int j = 0; j < DIM; ++j) W[i][j] = i == j ? 1.0 : 0.0;
-    bool bad = false;
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) bad |= isnan(A[i][i]);
-    for (int sweep = 0; sweep < 16 && !bad; ++sweep) {
-        bool rotated = false;
-#pragma unroll
-        for (int p = 0; p < DIM - 1; ++p)
-#pragma unroll
-            for (int q = p + 1; q < DIM; ++q) {
-                const double apq = A[p][q];
-                if (!(fabs(apq) > 1e-18 * sqrt(fabs(A[p][p] * A[q][q])))) continue;
-                rotated = true;
-                const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-                const double t = copysign(1.0, tau) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
-                const double c = rsqrt(fma(t, t, 1.0)), s = t * c;
-                A[p][p] = fma(-t, apq, A[p][p]);
-                A[q][q] = fma(t, apq, A[q][q]);
-                A[p][q] = A[q][p] = 0.0;
-#pragma unroll
-                for (int r = 0; r < DIM; ++r) {
-                    if (r == p || r == q) continue;
-                    const double arp = A[r][p], arq = A[r][q];
-                    A[r][p] = A[p][r] = c * arp - s * arq;
-                    A[r][q] = A[q][r] = s * arp + c * arq;
-                }
-#pragma unroll
-                for (int r = 0; r < DIM; ++r) {
-                    const double wp = W[r][p], wq = W[r][q];
-                    W[r][p] = c * wp - s * wq;
-                    W[r][q] = s * wp + c * wq;
-                }
-            }
-        if (!rotated) break;
-    }
-    int ord[DIM];
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) ord[i] = i;
-#pragma unroll
-    for (int i = 0; i < DIM; ++i)
-#pragma unroll
-        for (int j = i + 1; j < DIM; ++j)
-            if (A[ord[j]][ord[j]] < A[ord[i]][ord[i]]) {
-                const int t = ord[i];
-                ord[i] = ord[j];
-                ord[j] = t;
-            }
-    const double nan = __longlong_as_double(0x7ff8000000000000LL);
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-        int m = 0;
-#pragma unroll
-        for (int r = 1; r < DIM; ++r)
-            if (fabs(W[r][ord[k]]) > fabs(W[m][ord[k]])) m = r;
-        const double sg = W[m][ord[k]] < 0.0 ? -1.0 : 1.0;
-        ev[k] = bad ? nan : A[ord[k]][ord[k]];
-#pragma unroll
-        for (int r = 0; r < DIM; ++r) V[k * DIM + r] = bad ? nan : sg * W[r][ord[k]];
-    }
-}
 
 // grad F of lattice seed p from its 2 DIM auxiliary points (lcs_seed_aux): per axis b the
 // difference of the two points' final positions over that of their FP32 starting points,
@@ -227,8 +144,8 @@ __global__ void __launch_bounds__(256) cg_ftle_kernel(CgLaunch L)
     if (L.lam || L.ftle) {
         const double lm = DIM == 2 ? eig_max2(C) : eig_max3(C);
         if (L.lam) L.lam[out] = lm;
-        // sigma = ln(sqrt(lm)) / |T| = log1p(lm - 1) / (2 |T|)
-        if (L.ftle) L.ftle[out] = log1pf((float)(lm - 1.0)) * (0.5f / (float)L.absT[job]);
+        // sigma = ln(sqrt(lm)) / |T| = ln(lm) / (2 |T|)
+        if (L.ftle) L.ftle[out] = log_lambda(lm) * (0.5f / (float)L.absT[job]);
     }
 }
 

@@ -236,7 +236,7 @@ __global__ void early_fd_kernel(CgLaunch L, const int *__restrict__ cells0, cons
         }
     const double lm = DIM == 2 ? eig_max2(C) : eig_max3(C);
     // sigma = ln(sqrt(lm)) / (m |h|), as the regular pass forms it
-    ftle[p] = log1pf((float)(lm - 1.0)) * (0.5f / (float)((double)it.y * adt));
+    ftle[p] = log_lambda(lm) * (0.5f / (float)((double)it.y * adt));
 }
 
 }  // namespace

@@ -130,3 +130,73 @@ def test_eigen_rejects_null_outputs(ctx):
         lcs.lcs_free_flowmap(fm)
         lcs.lcs_free_seeds(seeds)
         lcs.lcs_free_field(field)
+
+
+def near_double_case(rng, gaps, reps):
+    """Positions on a 4M x 3 x 3 lattice (spacing 1) whose central differences give, at the centre
+    seeds (1 + 4m, 1, 1), chosen gradients G = diag(s) Q^T with Q a random rotation: C = G^T G =
+    Q diag(s^2) Q^T has eigenvalues scale * (1, 1 - gap, mu), the two largest a gap apart.  Each
+    difference 2 G[i][j] = A - B is split into FP32 values A = fl(2G) and B = fl(A - 2G), so A - B
+    (exact in FP64) carries 2G to about 48 bits and the gap survives down to ~1e-14.  The centres'
+    stencils are disjoint; every other position stays 0."""
+    cases = [(g, r) for g in gaps for r in range(reps)]
+    M = len(cases)
+    n = (4 * M, 3, 3)
+    N = n[0] * n[1] * n[2]
+    x = np.zeros((3, N), dtype=np.float32)
+    centres, lams = [], []
+    idx = lambda i, j, k: i + n[0] * (j + n[1] * k)
+    for m, (gap, _) in enumerate(cases):
+        Q, _r = np.linalg.qr(rng.standard_normal((3, 3)))
+        scale = [1e-4, 1.0, 3e7][m % 3]
+        lam = scale * np.array([1.0, 1.0 - gap, rng.uniform(1e-9, 0.9)])
+        G = np.sqrt(lam)[:, None] * Q.T
+        c = (1 + 4 * m, 1, 1)
+        for j in range(3):
+            plus, minus = list(c), list(c)
+            plus[j] += 1
+            minus[j] -= 1
+            D = 2.0 * G[:, j]
+            A = D.astype(np.float32)
+            B = (A.astype(np.float64) - D).astype(np.float32)
+            x[:, idx(*plus)] = A
+            x[:, idx(*minus)] = B
+        centres.append(idx(*c))
+        lams.append(lam)
+    return n, x, np.array(centres), np.array(lams)
+
+
+def test_lambda_max_near_double_root(ctx):
+    """lambda_max where the two largest eigenvalues of C coincide or nearly do (gaps from 0 to 1e-1 of
+    lambda_max): the characteristic cubic has a double root there, which no cubic-based polish resolves
+    in FP64, so the library switches to Jacobi rotations; against the oracle's Jacobi on the
+    bit-identical C, relative 1e-12 at every gap, both sides of the switch included."""
+    rng = np.random.default_rng(20261204)
+    gaps = [0.0, 1e-12, 1e-9, 1e-6, 1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1]
+    n, x, centres, lams = near_double_case(rng, gaps, 12)
+    N = x.shape[1]
+    st = np.zeros(N, dtype=np.uint8)
+    h = np.ones(3)
+    Co = oracle.cauchy_green(oracle.flowmap_gradient(3, n, h, (0, 0, 0), (0, 0, 0), x.astype(np.float64), st))
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, n, (0.0, 0.0, 0.0), (n[0] - 1.0, 2.0, 2.0)))
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    try:
+        lcs.lcs_flowmap_set(ctx, fm, 0, x, st, 1.0)
+        C = np.empty((N, 6))
+        lam = np.empty(N)
+        f = np.empty(N, dtype=np.float32)
+        lcs.lcs_ftle(ctx, fm, 0, f, lam, C)
+        lcs.lcs_synchronize(ctx)
+    finally:
+        lcs.lcs_free_flowmap(fm)
+        lcs.lcs_free_seeds(seeds)
+    np.testing.assert_array_equal(C, Co)
+    Cc = Co[centres]
+    eo, _ = oracle.cg_eigen(Cc, 3)
+    # the construction holds: the oracle's two largest eigenvalues are the designed gap apart
+    designed = (lams[:, 0] - lams[:, 1]) / lams[:, 0]
+    got_gap = (eo[:, 2] - eo[:, 1]) / eo[:, 2]
+    assert np.all(np.abs(got_gap - designed) <= 1e-13 + 1e-6 * designed)
+    rel = np.abs(lam[centres] - eo[:, 2]) / eo[:, 2]
+    assert np.all(rel <= 1e-12), (rel.max(), designed[rel.argmax()])
+    np.testing.assert_allclose(f[centres], np.log(eo[:, 2]) / 2.0, rtol=1e-6, atol=1e-7)
