@@ -249,13 +249,22 @@ __global__ void ep_slice_table_kernel(const SchedEntry *__restrict__ sched, int 
 // the components rather than keeping three planes cut the episode kernel from 113.2 to
 // 111.2 ms per 400 steps at C2), and stencil points a few cells outside the periodic box need
 // no index wrapping: the halo holds the wrapped values.
+//
+// Rows and planes of a slice are padded (pitches R and Q nodes, R = 4 and Q = 2 mod 8) so that
+// the 8 nodes of any 2 x 2 x 2 block of cells start in 8 different 16-byte bank groups of a
+// 128-byte line: the L1 data stage serves the 8 lanes of a quarter warp in one wavefront only
+// when no two of them read different addresses in the same bank group, and the stencil loads of
+// nearby tracers then rarely collide.  Unpadded, z-neighbours (Q = 132^2 = 0 mod 8 on the ABC
+// grid) always collided; a count of the collisions along RK4 trajectories of the ABC flow gave
+// 1.78 wavefronts per quarter warp unpadded, 1.01 padded.
 #define SLICE_HALO 2
 
 struct SliceGeom {
     int H[3];        // halo nodes on each side of an axis (periodic axes only)
     int N[3];        // extended node counts n + 2H
-    long long nxy;   // N[0] * N[1]
-    long long nodes; // extended nodes of one plane
+    int R;           // row pitch in nodes (>= N[0], = 4 mod 8)
+    long long nxy;   // plane pitch in nodes (>= R * N[1], = 2 mod 8)
+    long long nodes; // nodes of one slice plane, padding included (nxy * N[2])
 };
 
 static SliceGeom slice_geom(const lcs_field *f)
@@ -265,7 +274,9 @@ static SliceGeom slice_geom(const lcs_field *f)
         G.H[d] = f->periodic[d] ? SLICE_HALO : 0;
         G.N[d] = f->n[d] + 2 * G.H[d];
     }
-    G.nxy = (long long)G.N[0] * G.N[1];
+    G.R = G.N[0] + ((4 - G.N[0]) & 7);
+    const long long q = (long long)G.R * G.N[1];
+    G.nxy = q + ((2 - q) & 7);
     G.nodes = G.nxy * G.N[2];
     return G;
 }
@@ -288,17 +299,19 @@ __global__ void ep_slice_fill_kernel(RectParams P, SliceGeom G, const char *__re
                                      float4 *__restrict__ slices, size_t plane_stride)
 {
     // a block's 256 nodes are consecutive, so their interleaved quads (3 per node) form one run
-    // of 768 float4 per slice: staged in shared memory and stored coalesced
+    // of 768 float4 per slice: staged in shared memory and stored coalesced (padding nodes get 0)
     __shared__ float4 stage[256 * 3];
     const long long vb = (long long)blockIdx.x * 256;
     const long long v = vb + threadIdx.x;
     const int nb = (int)min(256LL, G.nodes - vb);
-    const bool live = v < G.nodes;
+    bool live = v < G.nodes;
     int corner[4] = {0, 0, 0, 0};
     if (live) {
-        const int I = (int)(v % G.N[0]);
-        const int J = (int)((v / G.N[0]) % G.N[1]);
         const int K = (int)(v / G.nxy);
+        const long long rem = v - (long long)K * G.nxy;
+        const int J = (int)(rem / G.R);
+        const int I = (int)(rem - (long long)J * G.R);
+        live = J < G.N[1] && I < G.N[0];
         const bool px = P.periodic[0], py = P.periodic[1];
         const int i = slice_src(I, G.H[0], P.n[0], px);
         const int jj = slice_src(J, G.H[1], P.n[1], py);
@@ -306,10 +319,12 @@ __global__ void ep_slice_fill_kernel(RectParams P, SliceGeom G, const char *__re
         const int i1 = px ? (i + 1 == P.n[0] ? 0 : i + 1) : min(i + 1, P.n[0] - 1);
         const int j1 = py ? (jj + 1 == P.n[1] ? 0 : jj + 1) : min(jj + 1, P.n[1] - 1);
         const long long zk = k * P.sz;
-        corner[0] = (int)(i + jj * P.sy + zk);
-        corner[1] = (int)(i1 + jj * P.sy + zk);
-        corner[2] = (int)(i + j1 * P.sy + zk);
-        corner[3] = (int)(i1 + j1 * P.sy + zk);
+        if (live) {
+            corner[0] = (int)(i + jj * P.sy + zk);
+            corner[1] = (int)(i1 + jj * P.sy + zk);
+            corner[2] = (int)(i + j1 * P.sy + zk);
+            corner[3] = (int)(i1 + j1 * P.sy + zk);
+        }
     }
     const int m = __ldg(nsl);
     float ua[4][3], ub[4][3];
@@ -331,6 +346,9 @@ __global__ void ep_slice_fill_kernel(RectParams P, SliceGeom G, const char *__re
                 for (int q = 0; q < 4; ++q) u[q] = e.a == 0.0f ? ua[q][c] : tblend(ua[q][c], ub[q][c], e.a, g);
                 stage[3 * threadIdx.x + c] = make_float4(u[0], u[1], u[2], u[3]);
             }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) stage[3 * threadIdx.x + c] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
         __syncthreads();
         float4 *base = slices + (size_t)j * 3 * plane_stride + 3 * vb;
@@ -390,7 +408,7 @@ __device__ __forceinline__ int stencil_ext(const RectParams &P, const SliceGeom 
     w[5] = fx * c;
     w[6] = gx * d;
     w[7] = fx * d;
-    return ix + iy * G.N[0] + iz * (int)G.nxy;
+    return ix + iy * G.R + iz * (int)G.nxy;
 }
 
 // Corner cache: the two z-row quads of the 3 components of the cell a tracer's last stage
@@ -495,7 +513,7 @@ __device__ __forceinline__ int stencil_ext_grad(const RectParams &P, const Slice
 #pragma unroll
     for (int k = 0; k < 3; ++k)
         on[k] = (per_axis<PM>(P, k) || (x[k] >= P.origin[k] && x[k] <= P.hi_node[k])) ? P.inv_h[k] : 0.0f;
-    return ix + iy * G.N[0] + iz * (int)G.nxy;
+    return ix + iy * G.R + iz * (int)G.nxy;
 }
 
 // u(x) as interp3q and its Jacobian J[c][d] = sum_q (d w_q / d x_d) u_q[c], corner q with offsets
