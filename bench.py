@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--storage-passes", type=int, default=3,
+                   help="c2 with f32: steps of the FP32/FP16/BF16 storage passes after the timed region (0 = none)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seeds-side", type=int, default=N_SIDE,
                    help="seed lattice side (default 256; smaller only for profiling captures)")
@@ -138,19 +140,22 @@ class ClockSampler:
 
 # ------------------------------------------------------------- reference arm
 
-def oracle_sample_run(g, side, threads=0):
-    """Oracle FTLE on a side^3 block of the 256^3 lattice (its stencils included); returns (seeds, s)."""
+def oracle_sample_run(g, side, threads=0, want_ftle=False):
+    """Oracle FTLE on a side^3 block of the 256^3 lattice (its stencils included); returns (seeds, s,
+    threads, tracers integrated), and with want_ftle also (lattice ids of the block's seeds, their FTLE)."""
     import oracle
 
     oracle.build()
     nthreads = oracle.set_threads(threads)
     n = (N_SIDE, N_SIDE, N_SIDE)
     h = L / N_SIDE
-    # block of side^3 seeds at the lattice origin plus a 2-seed halo (stencil neighbours, periodic)
-    idx = np.arange(-2, side + 2) % N_SIDE
-    xs = (idx * h).astype(np.float32)
+    # block of side^3 seeds at the lattice origin plus a 2-seed halo (stencil neighbours, periodic): a
+    # halo seed across the wrap starts at its lattice seed's FP32 position minus the period, as the
+    # library's differences shift it, so the block's central differences are the lattice's
+    idx = np.arange(-2, side + 2)
+    xs = (idx % N_SIDE * h).astype(np.float32).astype(np.float64) - np.where(idx < 0, L, 0.0)
     Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
-    x0 = np.stack([X.ravel(), Y.ravel(), Z.ravel()]).astype(np.float64)
+    x0 = np.stack([X.ravel(), Y.ravel(), Z.ravel()])
     F = oracle.RectField(g.frames, g.times, g.origin, g.spacing, g.periodic)
     t = time.perf_counter()
     xT, st, _ = oracle.rk4(F, x0, 0.0, T_END, DT)
@@ -160,7 +165,17 @@ def oracle_sample_run(g, side, threads=0):
     C = oracle.cauchy_green(G)
     lam, sig = oracle.ftle(C, 3, T_END)
     dt = time.perf_counter() - t
-    return side ** 3, dt, nthreads, x0.shape[1]
+    if not want_ftle:
+        return side ** 3, dt, nthreads, x0.shape[1]
+    # interior seeds (i, j, k) in [0, side)^3 of the halo block: their central differences are those of
+    # the full periodic lattice
+    b = np.arange(2, side + 2)
+    K, J, I = np.meshgrid(b, b, b, indexing="ij")
+    inner = (I + m * (J + m * K)).ravel()
+    i0 = np.arange(side)
+    K0, J0, I0 = np.meshgrid(i0, i0, i0, indexing="ij")
+    ids = (I0 + N_SIDE * (J0 + N_SIDE * K0)).ravel()
+    return side ** 3, dt, nthreads, x0.shape[1], ids, sig[inner]
 
 
 def reference_arm(args, rank, world):
@@ -366,14 +381,52 @@ def our_arm(args, rank, world, local):
         line["ftle_err_vs_f32_storage"] = {"median": float(np.median(dd)), "p99.9": float(np.quantile(dd, 0.999)),
                                            "max": float(dd.max()), "ftle_range": [float(b[ok].min()),
                                                                                   float(b[ok].max())]}
+    # the same workload with FP32, FP16 and BF16 velocity storage (FP32 tracers and arithmetic),
+    # outside the timed region: step time, and the FTLE of every pass kept for its error below
+    passes, pass_ftle = {}, {}
+    if args.storage_passes > 0 and args.storage == "f32":
+        for name, st in (("f32", lcs.F32), ("f16", lcs.F16), ("bf16", lcs.BF16)):
+            dsc = lcs.field_desc(3, g.n, g.origin, g.spacing, g.periodic, g.times, storage=st)
+            fp = lcs.lcs_load_field(ctx, dsc, frames_dev)
+            fo = torch.empty(N, dtype=torch.float32, device="cuda")
+            lcs.lcs_advect(ctx, fp, seeds, opts, fm)
+            lcs.lcs_ftle(ctx, fm, 0, fo)
+            a, b = ev(), ev()
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(args.storage_passes):
+                lcs.lcs_advect(ctx, fp, seeds, opts, fm)
+                lcs.lcs_ftle(ctx, fm, 0, fo)
+            b.record(stream)
+            lcs.lcs_synchronize(ctx)
+            ms = a.elapsed_time(b) / args.storage_passes
+            passes[name] = {"ms_per_step": ms, "seeds_per_s": N / (ms / 1e3),
+                            "field_bytes": int(g.frames.nbytes // (1 if st == lcs.F32 else 2))}
+            pass_ftle[name] = fo
+            lcs.lcs_free_field(fp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         _, dts, _, _ = oracle_sample_run(g, 4)                 # calibration: 8^3 tracers
         side = int(max(4, min(96, (10.0 / max(dts / 512.0, 1e-9)) ** (1 / 3) - 4)))
-        s, dt, nth, integrated = oracle_sample_run(g, side)
+        s, dt, nth, integrated, ids, sig = oracle_sample_run(g, side, want_ftle=True)
         line["cpu_baseline"] = {"value": s / dt, "unit": "seeds/s", "cores": nth, "kind": "oracle",
                                 "sample": "%d^3-seed block of the 256^3 lattice with its 2-seed stencil halo "
                                           "(%d tracers integrated, 400 steps each), FD/CG/FTLE; %.1f s"
                                           % (side, integrated, dt)}
+        # FTLE error of each storage pass against the FP64 oracle (on the FP32-sampled field) at the
+        # baseline's seeds
+        idt = torch.from_numpy(ids).cuda()
+        for name, fo in pass_ftle.items():
+            got = fo[idt].cpu().double().numpy()
+            ok = np.isfinite(got) & np.isfinite(sig)
+            d = np.abs(got[ok] - sig[ok])
+            passes[name]["ftle_err_vs_oracle"] = {"median": float(np.median(d)), "p99.9": float(np.quantile(d, 0.999)),
+                                                  "max": float(d.max()), "seeds": int(ok.sum())}
+    if passes:
+        line["storage_passes"] = passes
+        line["storage_passes_note"] = ("the default workload with each velocity storage type, %d untimed-region "
+                                       "steps each after one warm-up (CUDA events); FTLE error against the FP64 "
+                                       "oracle on the FP32-sampled frames at the cpu_baseline block's seeds"
+                                       % args.storage_passes)
     lcs.lcs_free_flowmap(fm)
     lcs.lcs_free_seeds(seeds)
     lcs.lcs_free_field(field)
@@ -1173,27 +1226,70 @@ def next_arm(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+PROBE_SRC = os.path.join(ROOT, "bench_peaks.cu")
+PROBE_LIB = os.path.join(ROOT, "_build", "libbench_peaks.so")
+
+
+def build_probes() -> str:
+    """Compile bench_peaks.cu (the measurement probes; not part of liblcs) for sm_103a when stale."""
+    if not os.path.exists(PROBE_LIB) or os.path.getmtime(PROBE_LIB) < os.path.getmtime(PROBE_SRC):
+        os.makedirs(os.path.dirname(PROBE_LIB), exist_ok=True)
+        nvcc = "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc"
+        tmp = PROBE_LIB + ".tmp.%d" % os.getpid()
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-Xcompiler", "-fPIC", "-shared",
+                        "-o", tmp, PROBE_SRC], check=True, capture_output=True)
+        os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
+def probe_peaks(device):
+    """FP32 and FP64 FMA TFLOP/s, L2-resident and HBM read GB/s measured with plain loops."""
+    import ctypes
+
+    lib = ctypes.CDLL(build_probes())
+    out = np.zeros(4)
+    rc = lib.bench_probe_peaks(int(device), ctypes.c_void_p(out.ctypes.data))
+    if rc != 0:
+        raise RuntimeError("bench_probe_peaks: CUDA error %d" % rc)
+    return {"fp32_tflops": out[0], "fp64_tflops": out[1], "l2_read_gbs": out[2], "hbm_read_gbs": out[3]}
+
+
+L1_PATTERNS = ["1 line per quarter warp", "2 lines, distinct bank groups", "4 lines, distinct bank groups",
+               "8 lines, distinct bank groups", "8 lines, one bank group", "2 lines, one bank group"]
+
+
+def probe_l1(device):
+    """SM cycles per warp-wide 16-byte gather request for lane patterns of the L1 data stage."""
+    import ctypes
+
+    lib = ctypes.CDLL(build_probes())
+    out = np.zeros(len(L1_PATTERNS))
+    rc = lib.bench_probe_l1(int(device), ctypes.c_void_p(out.ctypes.data))
+    if rc != 0:
+        raise RuntimeError("bench_probe_l1: CUDA error %d" % rc)
+    return dict(zip(L1_PATTERNS, [float(v) for v in out]))
+
+
 def peaks_arm(args, rank, world, local):
-    """The rates plain loops reach on this GPU (FP32/FP64 FMA, L2-resident and HBM reads), next to the
-    measured copy bandwidth and the FP32 ALU figure the advection rooflines use."""
+    """The rates plain loops reach on this GPU (FP32/FP64 FMA, L2-resident and HBM reads, the L1 gather
+    patterns), next to the measured copy bandwidth and the FP32 ALU figure the advection
+    rooflines use."""
     import torch
 
-    from paper_2209_13775_gb300 import lcs
-
     torch.cuda.set_device(local)
-    ctx = lcs.lcs_create(local, torch.cuda.current_stream())
-    runs = [lcs.lcs_probe_peaks(ctx) for _ in range(max(args.steps, 3))]
-    lcs.lcs_destroy(ctx)
+    runs = [probe_peaks(local) for _ in range(max(args.steps, 3))]
     med = {k: float(np.median([r[k] for r in runs])) for k in runs[0]}
+    l1 = probe_l1(local)
     alu, basis = alu_peak()
     pk, pk_kind = peaks()
     line = {"metric": "plain-loop peaks on 1 GB300", "value": med["fp32_tflops"], "unit": "TFLOP/s (FP32 FMA)",
             "n_gpus": 1, "steps": len(runs), "warmup": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
             "config": {"workload": "FMA chains (8 per thread, 16 blocks of 256 per SM); reads of a 32 MB buffer "
-                                   "x256 and of a 4 GiB buffer x1 (16-byte loads, grid-stride)"},
-            "peaks": med, "fp32_alu_formula_tflops": alu, "fp32_alu_formula": basis,
-            "driver_hbm_copy_gbs": pk.get("hbm_gbs"), "driver_peaks": pk_kind}
+                                   "x256 and of a 4 GiB buffer x1 (16-byte loads, grid-stride); 16-byte gathers "
+                                   "from a 128 KB buffer per lane pattern"},
+            "peaks": med, "l1_gather_clk_per_request": l1, "fp32_alu_formula_tflops": alu,
+            "fp32_alu_formula": basis, "driver_hbm_copy_gbs": pk.get("hbm_gbs"), "driver_peaks": pk_kind}
     print(json.dumps(line), flush=True)
 
 

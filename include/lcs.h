@@ -78,6 +78,10 @@ const char *lcs_last_error(const lcs_ctx *ctx);
 /* Switch the stream later calls queue on.                                   */
 lcs_status lcs_set_stream(lcs_ctx *ctx, void *stream);
 
+/* The CUDA device index of ctx (-1 for NULL), so that a binding can check
+ * that caller-owned device buffers sit on it.                              */
+int lcs_context_device(const lcs_ctx *ctx);
+
 /* Wait for the context's stream, then read and clear the device-side error
  * word: LCS_EWALK / LCS_ETIMEOUT / LCS_EMAXSTEPS when a kernel recorded one.  */
 lcs_status lcs_synchronize(lcs_ctx *ctx);
@@ -87,7 +91,7 @@ lcs_status lcs_synchronize(lcs_ctx *ctx);
 /* Velocity data (Sec. 2 "Reader"/"Cache"/"Interpolator"): nodal velocity
  * frames at increasing times, interpolated linearly in time and
  * bilinearly / trilinearly (rectilinear) or piecewise-linearly (tets in 3D,
- * triangles in 2D: Sec. 3.1, Sec. 4's 2D unstructured stenosis data) in
+ * triangles in 2D: Sec. 3.1, Sec. 3.2's 2D unstructured stenosis data) in
  * space.  Rectilinear node (i,j,k) sits at origin + (i,j,k)*spacing; a
  * periodic axis has n cells (node n-1 joins node 0) and period n*spacing;
  * queries on a non-periodic axis are clamped to the box.  Time outside
@@ -125,6 +129,9 @@ typedef struct {
  * a mesh cell of zero area or volume), LCS_ENOMEM, LCS_ECUDA.               */
 lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *desc, const float *frames,
                           int frames_on_device, lcs_field **out);
+
+/* Spatial dimension of a loaded field (2 or 3; 0 for NULL).                 */
+int lcs_field_dim(const lcs_field *field);
 
 /* Replace the frames of a loaded field with new data of the same shape
  * (same conventions and finiteness check as lcs_load_field).               */
@@ -263,6 +270,15 @@ typedef struct {
     int variational;            /* LCS_RK4, no snapshots: also integrate grad F by
                                    the variational equations (lcs_flowmap_grad,
                                    lcs_ftle_variational); every field kind         */
+    double wait_limit;          /* seconds a block of the shared-memory frame ring
+                                   (variants 2 and 4) waits for a frame copy before
+                                   it stops integrating and the next lcs_synchronize
+                                   reports LCS_ETIMEOUT (the flow map of that call is
+                                   then incomplete); 0 = 1 s, at most 60 s; under
+                                   1e-6 a copy not complete at its first test counts
+                                   as late.  Copies already issued are always waited
+                                   for (with the 1 s bound) before a block exits.  A
+                                   short limit lets a caller fail fast             */
 } lcs_advect_opts;
 
 /* Flow-map storage for `njobs` integrations of one lattice.                 */
@@ -519,16 +535,6 @@ lcs_status lcs_timing_read(lcs_ctx *ctx, int phase, double *ms, long long *launc
 lcs_status lcs_advect_rk4_noalloc(lcs_ctx *ctx, const lcs_field *field, const float *seeds, long long n,
                                   double t0, double T, double dt, float *xyz, unsigned char *status,
                                   float *t_exit);
-
-/* ------------------------------------------------------------ measurement */
-
-/* The rates this GPU reaches with plain loops, the denominators against which
- * the advection (FP32), Cauchy-Green (FP64) and gather (L2, HBM) kernels are
- * judged.  peaks[4] HOST: FP32 FMA TFLOP/s, FP64 FMA TFLOP/s, read GB/s from a
- * 32 MB L2-resident buffer, read GB/s from a 4 GiB buffer.  Allocates 4 GiB
- * for the duration of the call and synchronises the context's stream.
- * Errors: LCS_EINVAL, LCS_ECUDA.                                            */
-lcs_status lcs_probe_peaks(lcs_ctx *ctx, double *peaks);
 
 #ifdef __cplusplus
 }

@@ -348,7 +348,7 @@ __device__ __forceinline__ bool in_list(const int *F, int m, int f)
 
 // thread 0: load frame f into a slot that holds none of the protected frames
 __device__ int ring_load(RingState &R, char *slots, const char *frames, size_t fstride, int f, const int *keep,
-                         int nkeep, unsigned *errword)
+                         int nkeep, unsigned *errword, uint64_t wait_ns)
 {
     int v = -1;
     for (int s = 0; s < RING_SLOTS && v < 0; ++s)
@@ -356,7 +356,7 @@ __device__ int ring_load(RingState &R, char *slots, const char *frames, size_t f
     for (int s = 0; s < RING_SLOTS && v < 0; ++s)
         if (!in_list(keep, nkeep, R.tag[s])) v = s;
     if (v < 0) return RING_GLOBAL;
-    if (R.nload[v] > 0 && !mbar_wait_bounded(&R.bar[v], (R.nload[v] - 1) & 1)) {  // previous copy into v
+    if (R.nload[v] > 0 && !mbar_wait_limit(&R.bar[v], (R.nload[v] - 1) & 1, wait_ns)) {  // previous copy into v
         atomicOr(errword, LCS_ERRBIT_TIMEOUT);
         R.abort = 1;
         return RING_GLOBAL;
@@ -408,7 +408,7 @@ __device__ __forceinline__ void ring_tile(const RectParams &P, const char *__res
             int F[6], Fn[6];
             int m = step_frames(e, F);
             for (int r = 0; r < m; ++r)
-                if (ring_find(R, F[r]) < 0) ring_load(R, slots, frames, fstride, F[r], F, m, errword);
+                if (ring_find(R, F[r]) < 0) ring_load(R, slots, frames, fstride, F[r], F, m, errword, A.wait_ns);
             for (int s = 0; s < 3; ++s) {
                 int fa = e[s].k, fb = e[s].k + 1;
                 int sa = ring_find(R, fa);
@@ -430,7 +430,7 @@ __device__ __forceinline__ void ring_tile(const RectParams &P, const char *__res
                 for (int r = 0; r < m; ++r) keep[nk++] = F[r];
                 for (int r = 0; r < mn; ++r) keep[nk++] = Fn[r];
                 for (int r = 0; r < mn; ++r)
-                    if (ring_find(R, Fn[r]) < 0) ring_load(R, slots, frames, fstride, Fn[r], keep, nk, errword);
+                    if (ring_find(R, Fn[r]) < 0) ring_load(R, slots, frames, fstride, Fn[r], keep, nk, errword, A.wait_ns);
             }
         }
         __syncthreads();
@@ -438,7 +438,7 @@ __device__ __forceinline__ void ring_tile(const RectParams &P, const char *__res
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             int s = R.slot[q];
-            if (s >= 0 && !R.abort && !mbar_wait_bounded(&R.bar[s], (R.nload[s] - 1) & 1)) {
+            if (s >= 0 && !R.abort && !mbar_wait_limit(&R.bar[s], (R.nload[s] - 1) & 1, A.wait_ns)) {
                 atomicOr(errword, LCS_ERRBIT_TIMEOUT);
                 R.abort = 1;
             }
@@ -527,7 +527,8 @@ __global__ void __launch_bounds__(512, 1) rk4_ring2d_kernel(RectParams P, const 
             ring_tile<ST, TPT>(P, frames, fstride, A, errword, slots, R, job, item % W.tiles_per_job);
         }
     }
-    // drain copies still in flight (prefetches nobody read) before the block exits
+    // drain copies still in flight (prefetches nobody read, or copies a shortened wait gave up on)
+    // before the block exits, with the full bound whatever the call's wait limit
     __syncthreads();
     if (tid == 0)
         for (int s = 0; s < RING_SLOTS; ++s)
@@ -790,6 +791,7 @@ int launch_rk4_rect(lcs_ctx *ctx, const Rk4Launch &L, cudaStream_t s)
     A.nsnap = L.nsnap;
     A.snap_n = L.snap_n;
     A.snap_te = L.snap_te;
+    A.wait_ns = L.wait_ns;
     if (L.N == 0 || L.njobs == 0) return 1;
     bool ring_fits = f->dim == 2 && RING_SLOTS * f->frame_stride <= ctx->smem_optin;
     bool sorted_ok = f->dim == 3 && L.work != nullptr;

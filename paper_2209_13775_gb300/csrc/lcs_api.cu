@@ -170,6 +170,10 @@ extern "C" const char *lcs_last_error(const lcs_ctx *ctx)
     return ctx ? ctx->err.c_str() : "null context";
 }
 
+extern "C" int lcs_context_device(const lcs_ctx *ctx) { return ctx ? ctx->device : -1; }
+
+extern "C" int lcs_field_dim(const lcs_field *f) { return f ? f->dim : 0; }
+
 extern "C" lcs_status lcs_set_stream(lcs_ctx *ctx, void *stream)
 {
     if (!ctx) return LCS_EINVAL;
@@ -823,6 +827,7 @@ static lcs_status advect_rk4_rect(lcs_ctx *ctx, const lcs_field *f, const lcs_se
     L.host_snap_n = J.snap_n;
     L.snap_te = D.snap_te;
     L.work = want_work ? (char *)ctx->d_scratch + jb + sb : nullptr;
+    if (o->wait_limit > 0.0) L.wait_ns = (unsigned long long)(o->wait_limit * 1e9);
     if (lcs_is_mesh(f)) {
         cudaError_t e = launch_rk4_tet(ctx, L, s->d_cells, o->walk_limit, ctx->stream);
         if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_advect: launch failed: %s", cudaGetErrorString(e));
@@ -927,10 +932,10 @@ static std::string graph_key(const lcs_ctx *ctx, const lcs_field *f, const lcs_s
                              const lcs_flowmap *fm, const JobTable &J)
 {
     std::string k;
-    char buf[160];
-    snprintf(buf, sizeof buf, "%llu/%llu/%llu/%p/%zu/%d/%d/%d/%d/%d/%d/%a/v%d/w%d|", f->uid, s->uid, fm->uid,
+    char buf[256];
+    snprintf(buf, sizeof buf, "%llu/%llu/%llu/%p/%zu/%d/%d/%d/%d/%d/%d/%a/v%d/w%d/l%a|", f->uid, s->uid, fm->uid,
              ctx->d_scratch, ctx->scratch_bytes, o->method, o->variant, o->block_threads, o->episode_steps,
-             o->tracers_per_thread, J.njobs, o->dt, o->variational, o->walk_limit);
+             o->tracers_per_thread, J.njobs, o->dt, o->variational, o->walk_limit, o->wait_limit);
     k += buf;
     for (int j = 0; j < J.njobs; ++j) {
         snprintf(buf, sizeof buf, "%a,%a;", J.t0[j], J.T[j]);
@@ -1059,6 +1064,8 @@ extern "C" lcs_status lcs_advect(lcs_ctx *ctx, const lcs_field *f, const lcs_see
                             njobs, o->nsnap, (long long)njobs * (1 + o->nsnap), fm->njobs);
     }
     if (o->njobs > 1 && (!o->job_t0 || !o->job_T)) return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: job arrays missing");
+    if (!(o->wait_limit >= 0.0 && o->wait_limit <= 60.0))
+        return lcs_fail(ctx, LCS_EINVAL, "lcs_advect: wait_limit must be 0..60 s");
     if (o->method != LCS_RK4 && o->method != LCS_RK45 && o->method != LCS_SURROGATE)
         return lcs_fail(ctx, LCS_EUNSUPPORTED, "lcs_advect: method %d not built in", o->method);
     if (o->method == LCS_SURROGATE) return advect_surrogate(ctx, f, s, o, fm);

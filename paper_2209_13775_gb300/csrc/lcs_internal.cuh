@@ -231,6 +231,7 @@ struct Rk4Launch {
     const int *snap_n = nullptr;  // [nsnap] on the device (written by the schedule kernel)
     const int *host_snap_n = nullptr;  // [nsnap] the same on the host
     const float *snap_te = nullptr;    // [njobs][nsnap] snapshot end times (device)
+    unsigned long long wait_ns = LCS_WAIT_LIMIT_NS;  // ring kernels: bound on a wait for a frame copy
 };
 
 // smallest seed count for which lcs_advect picks the re-bundled kernel by default
@@ -391,14 +392,44 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// bounded wait for the phase with the given parity; false when the time limit ran out
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+// non-blocking test of the phase with the given parity
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, unsigned parity)
 {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase with the given parity; false when limit_ns ran out.  try_wait may
+// itself suspend the thread for a system-dependent time (microseconds) before it answers, so a
+// limit shorter than the default polls with the non-blocking test_wait instead, and a limit under
+// a microsecond (below what %globaltimer resolves) is a single test.
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, unsigned parity, uint64_t limit_ns)
+{
+    if (limit_ns < 1000) return mbar_test_wait(bar, parity);
+    if (limit_ns < LCS_WAIT_LIMIT_NS) {
+        if (mbar_test_wait(bar, parity)) return true;
+        const uint64_t t0 = global_ns();
+        while (!mbar_test_wait(bar, parity))
+            if (global_ns() - t0 > limit_ns) return false;
+        return true;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > LCS_WAIT_LIMIT_NS) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+{
+    return mbar_wait_limit(bar, parity, LCS_WAIT_LIMIT_NS);
 }
 
 #endif  // __CUDACC__

@@ -15,11 +15,19 @@
 // Working memory of lcs_advect_rk4_noalloc.  Every GPU that loads the library
 // holds this 1 MiB array until the process exits.
 #define LCS_NOALLOC_SCRATCH_BYTES (1u << 20)
-#define LCS_NOALLOC_HEADER 256u                // per-job values
+#define LCS_NOALLOC_HEADER 256u                // per-job values: offsets 0, 16, 32, 48 (4 bytes), 64 (8 bytes)
 #define LCS_NOALLOC_MAX_DEVICES 64
 static __device__ __align__(256) unsigned char g_noalloc_scratch[LCS_NOALLOC_SCRATCH_BYTES];
-static_assert(LCS_NOALLOC_HEADER + (size_t)LCS_NOALLOC_MAX_STEPS * 3 * sizeof(SchedEntry) <= LCS_NOALLOC_SCRATCH_BYTES,
-              "LCS_NOALLOC_MAX_STEPS does not fit the scratch array");
+// the step limit published in lcs.h is exactly what the array holds after the header: three
+// schedule entries (one per distinct RK4 stage time) per step
+static_assert(LCS_NOALLOC_MAX_STEPS ==
+                  (LCS_NOALLOC_SCRATCH_BYTES - LCS_NOALLOC_HEADER) / (3 * sizeof(SchedEntry)),
+              "LCS_NOALLOC_MAX_STEPS must be the step count the scratch array holds");
+static_assert(64 + sizeof(double) <= LCS_NOALLOC_HEADER, "the per-job values must fit the header");
+static_assert(LCS_NOALLOC_HEADER % 16 == 0, "schedule entries must start 16-byte aligned");
+
+#define NA_STR2(x) #x
+#define NA_STR(x) NA_STR2(x)
 
 // device address of g_noalloc_scratch per device, looked up once per device
 static std::mutex g_noalloc_mu;
@@ -50,12 +58,27 @@ extern "C" lcs_status lcs_advect_rk4_noalloc(lcs_ctx *ctx, const lcs_field *f, c
         return na_fail(ctx, LCS_EINVAL, "lcs_advect_rk4_noalloc: |T|/|dt| is not an integer");
     if (ns > LCS_NOALLOC_MAX_STEPS)
         return na_fail(ctx, LCS_EINVAL,
-                       "lcs_advect_rk4_noalloc: |T|/|dt| exceeds LCS_NOALLOC_MAX_STEPS (43680), the most RK4 "
-                       "steps its fixed 1 MiB scratch holds; use lcs_advect");
+                       "lcs_advect_rk4_noalloc: |T|/|dt| exceeds LCS_NOALLOC_MAX_STEPS (" NA_STR(LCS_NOALLOC_MAX_STEPS)
+                       "), the most RK4 steps its fixed " NA_STR(LCS_NOALLOC_SCRATCH_BYTES) "-byte scratch holds; "
+                       "use lcs_advect");
     if (ctx->device < 0 || ctx->device >= LCS_NOALLOC_MAX_DEVICES)
         return na_fail(ctx, LCS_EINVAL, "lcs_advect_rk4_noalloc: device index too large");
     if (cudaSetDevice(ctx->device) != cudaSuccess)
         return na_fail(ctx, LCS_ECUDA, "lcs_advect_rk4_noalloc: cudaSetDevice failed");
+    if (f->dim != 2 && f->dim != 3) return na_fail(ctx, LCS_EINVAL, "lcs_advect_rk4_noalloc: field dim must be 2 or 3");
+    // the kernels dereference these pointers: refuse host memory and other devices' memory before any
+    // launch (the sizes behind them cannot be checked here; the caller guarantees them)
+    const void *bufs[4] = {seeds, xyz, status, t_exit};
+    for (const void *b : bufs) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, b) != cudaSuccess) {
+            cudaGetLastError();
+            return na_fail(ctx, LCS_EINVAL, "lcs_advect_rk4_noalloc: a buffer is not CUDA memory");
+        }
+        if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != ctx->device)
+            return na_fail(ctx, LCS_EINVAL, "lcs_advect_rk4_noalloc: every buffer must be device memory on the "
+                                            "context's device");
+    }
     void *base;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);

@@ -341,6 +341,7 @@ struct Rk4Args {
     int nsnap = 0;
     const int *snap_n = nullptr;     // [nsnap] snapshot step counts (device; capped per job at use)
     const float *snap_te = nullptr;  // [njobs][nsnap] snapshot end times, the exit time of a tracer OK there
+    unsigned long long wait_ns = LCS_WAIT_LIMIT_NS;  // ring kernels: bound on a wait for a frame copy
 };
 
 // Step after which snapshot s of a job with ns steps is taken.

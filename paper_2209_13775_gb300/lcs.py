@@ -33,7 +33,7 @@ EXPORTS = ["lcs_create", "lcs_destroy", "lcs_last_error", "lcs_set_stream", "lcs
            "lcs_timing_read",
            "lcs_advect_rk4_noalloc", "lcs_gemm_bf16", "lcs_mlp_create", "lcs_mlp_set_params",
            "lcs_mlp_get_params", "lcs_mlp_free", "lcs_mlp_forward", "lcs_mlp_loss_grad", "lcs_mlp_adam",
-           "lcs_surrogate_train", "lcs_probe_peaks"]
+           "lcs_surrogate_train", "lcs_context_device", "lcs_field_dim"]
 PHASE_ADVECT, PHASE_REBUNDLE, PHASE_SLICES, PHASE_CG = 0, 1, 2, 3
 NOALLOC_MAX_STEPS = 43680
 MAX_SNAP = 8
@@ -69,7 +69,7 @@ class AdvectOpts(ctypes.Structure):
                 ("block_threads", ctypes.c_int), ("variant", ctypes.c_int), ("surrogate", ctypes.c_void_p),
                 ("episode_steps", ctypes.c_int), ("tracers_per_thread", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("gate_tol", ctypes.c_double), ("nsnap", ctypes.c_int), ("snap_T", ctypes.c_void_p),
-                ("variational", ctypes.c_int)]
+                ("variational", ctypes.c_int), ("wait_limit", ctypes.c_double)]
 
 
 _lib = None
@@ -91,9 +91,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     sig = {
         "lcs_create": ([P, I, P], S), "lcs_destroy": ([P], None), "lcs_last_error": ([P], ctypes.c_char_p),
         "lcs_set_stream": ([P, P], S), "lcs_synchronize": ([P], S),
+        "lcs_context_device": ([P], I), "lcs_field_dim": ([P], I),
         "lcs_load_field": ([P, P, P, I, P], S), "lcs_update_frames": ([P, P, P, I], S),
         "lcs_free_field": ([P], None), "lcs_seed_grid": ([P, P, P, P], S), "lcs_seeds_count": ([P], LL),
-        "lcs_probe_peaks": ([P, P], S),
         "lcs_seed_aux": ([P, P, P, P], S), "lcs_seed_aux_field": ([P, P, P, P, P], S),
         "lcs_seeds_get": ([P, P, P, P, I], S), "lcs_free_seeds": ([P], None),
         "lcs_flowmap_create": ([P, P, I, P], S), "lcs_advect": ([P, P, P, P, P], S),
@@ -174,6 +174,14 @@ def lcs_set_stream(ctx, stream):
 
 def lcs_synchronize(ctx):
     _check(ctx, load().lcs_synchronize(ctx))
+
+
+def lcs_context_device(ctx) -> int:
+    return int(load().lcs_context_device(ctx))
+
+
+def lcs_field_dim(field) -> int:
+    return int(load().lcs_field_dim(field))
 
 
 # ----------------------------------------------------------------- field
@@ -280,7 +288,7 @@ def lcs_free_seeds(seeds):
 
 def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol=1e-6, atol=1e-6, h0=0.01,
                 max_steps=0, walk_limit=0, block_threads=0, variant=0, episode_steps=0, tracers_per_thread=0,
-                use_graph=False, surrogate=None, gate_tol=1e-3, snap_T=None, variational=False):
+                use_graph=False, surrogate=None, gate_tol=1e-3, snap_T=None, variational=False, wait_limit=0.0):
     o = AdvectOpts()
     o.method, o.t0, o.T, o.dt = int(method), float(t0), float(T), float(dt)
     o.rtol, o.atol, o.h0, o.max_steps = float(rtol), float(atol), float(h0), int(max_steps)
@@ -291,6 +299,7 @@ def advect_opts(method=RK4, t0=0.0, T=0.0, dt=0.0, job_t0=None, job_T=None, rtol
     o.surrogate = surrogate
     o.gate_tol = float(gate_tol)
     o.variational = int(bool(variational))
+    o.wait_limit = float(wait_limit)
     keep = []
     if snap_T is not None and len(snap_T) > 0:
         sn = np.ascontiguousarray(snap_T, dtype=np.float64)
@@ -430,10 +439,26 @@ def lcs_advect_rk4_noalloc(ctx, field, seeds, t0, T, dt, xyz, status, t_exit):
     For callers that cannot allocate device memory (see include/lcs.h).  `seeds` is a [dim][n] FP32
     device tensor; `xyz` [dim][n] FP32, `status` [n] uint8 and `t_exit` [n] FP32 are device outputs.
     """
+    import torch
+
+    L = load()
+    dim, dev = L.lcs_field_dim(field), L.lcs_context_device(ctx)
+    if dim not in (2, 3) or dev < 0:
+        raise ValueError("lcs_advect_rk4_noalloc: null field or context")
+    # the C entry point cannot see buffer sizes: every shape, type and device is checked here
+    for name, a in (("seeds", seeds), ("xyz", xyz), ("status", status), ("t_exit", t_exit)):
+        if not (hasattr(a, "is_cuda") and a.is_cuda and a.device.index == dev):
+            raise ValueError("lcs_advect_rk4_noalloc: %s must be a tensor on the context's device cuda:%d" % (name, dev))
+    if seeds.dim() != 2 or seeds.shape[0] != dim or seeds.dtype != torch.float32:
+        raise ValueError("lcs_advect_rk4_noalloc: seeds must be [%d][n] float32" % dim)
+    n = int(seeds.shape[1])
+    if tuple(xyz.shape) != (dim, n) or xyz.dtype != torch.float32:
+        raise ValueError("lcs_advect_rk4_noalloc: xyz must be [%d][%d] float32" % (dim, n))
+    if tuple(status.shape) != (n,) or status.dtype != torch.uint8:
+        raise ValueError("lcs_advect_rk4_noalloc: status must be [%d] uint8" % n)
+    if tuple(t_exit.shape) != (n,) or t_exit.dtype != torch.float32:
+        raise ValueError("lcs_advect_rk4_noalloc: t_exit must be [%d] float32" % n)
     ptrs = [_ptr(a) for a in (seeds, xyz, status, t_exit)]
-    if not all(d for _, d in ptrs):
-        raise ValueError("lcs_advect_rk4_noalloc takes device tensors only")
-    n = int(seeds.shape[-1])
     _check(ctx, load().lcs_advect_rk4_noalloc(ctx, field, ctypes.c_void_p(ptrs[0][0]), n, float(t0), float(T),
                                               float(dt), *[ctypes.c_void_p(p) for p, _ in ptrs[1:]]))
 
@@ -535,9 +560,3 @@ def lcs_surrogate_train(ctx, field, mlp, desc, samples):
                                            dev, out.ctypes.data))
     return out
 
-
-def lcs_probe_peaks(ctx):
-    """FP32 and FP64 FMA TFLOP/s, L2-resident and HBM read GB/s measured with plain loops."""
-    out = np.zeros(4)
-    _check(ctx, load().lcs_probe_peaks(ctx, out.ctypes.data_as(ctypes.c_void_p)))
-    return {"fp32_tflops": out[0], "fp64_tflops": out[1], "l2_read_gbs": out[2], "hbm_read_gbs": out[3]}

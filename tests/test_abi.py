@@ -55,3 +55,12 @@ def test_built_for_sm_103a():
     from paper_2209_13775_gb300 import build
 
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_binding_constants_match_the_header():
+    from paper_2209_13775_gb300 import lcs
+
+    src = open(os.path.join(ROOT, "include", "lcs.h")).read()
+    for name, value in (("LCS_NOALLOC_MAX_STEPS", lcs.NOALLOC_MAX_STEPS), ("LCS_MAX_SNAP", lcs.MAX_SNAP)):
+        m = re.search(r"#define\s+%s\s+(\d+)" % name, src)
+        assert m and int(m.group(1)) == value, name

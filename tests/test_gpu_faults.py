@@ -93,3 +93,58 @@ def test_step_cap_reports_maxsteps(ctx, pipe):
     assert err == 6                                             # LCS_EMAXSTEPS
     assert (st == lcs.TRACER_MAXSTEPS).sum() > 0
     assert set(np.unique(st)) <= {lcs.TRACER_OK, lcs.TRACER_LEFT, lcs.TRACER_MAXSTEPS}
+
+
+def test_frame_copy_wait_limit_reports_timeout(ctx):
+    """A bounded device wait that gives up (Sec. 3: the frames of the current interval staged into
+    on-chip memory; here the shared-memory frame ring).  With wait_limit under a microsecond a block
+    tests each frame copy once when it first needs it; a copy still in flight then counts as late:
+    the block stops, sets the error word and drains its copies before it exits (those waits keep the
+    full 1 s bound), and lcs_synchronize reports LCS_ETIMEOUT.  Whether some copy is still in flight
+    depends on timing, so the workload makes many fresh copies (64 one-step jobs whose start times
+    need other frames, each block loading its own) and the call is repeated up to five times; on
+    GB300 the first call already reported the timeout.  The same context then integrates normally
+    and matches the oracle.  Nothing traps or spins without bound."""
+    from gpu_util import check_flowmap, check_ftle, oracle_run, rect_desc
+
+    g = inputs.double_gyre()    # 129 x 65 FP32 frames: 67 KB copies, three ring slots
+    n, lo, hi, T, dt = (128, 64), (0.0, 0.0), (2.0, 1.0), 2.0, 0.05
+    field = lcs.lcs_load_field(ctx, rect_desc(g), g.frames)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, lo, hi))
+    N = lcs.lcs_seeds_count(seeds)
+    t0s = [0.15 * k for k in range(64)]
+    fm = lcs.lcs_flowmap_create(ctx, seeds, len(t0s))
+    try:
+        for variant in (2, 4):
+            opts = lcs.advect_opts(lcs.RK4, dt=dt, job_t0=t0s, job_T=[dt] * len(t0s), variant=variant,
+                                   wait_limit=1e-9)
+            seen = []
+            for attempt in range(5):
+                lcs.lcs_advect(ctx, field, seeds, opts, fm)
+                try:
+                    lcs.lcs_synchronize(ctx)
+                    seen.append(0)
+                except lcs.LcsError as e:
+                    seen.append(e.status)
+                    break
+            assert seen[-1] == 4, (variant, seen)                 # LCS_ETIMEOUT
+            assert set(seen) <= {0, 4}
+            lcs.lcs_synchronize(ctx)                              # the error word was cleared
+        with pytest.raises(lcs.LcsError) as e:
+            lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, t0=0.0, T=T, dt=dt, wait_limit=-1.0), fm)
+        assert e.value.status == 1
+        # the same context, the default limit: a normal integration that matches the oracle
+        lcs.lcs_advect(ctx, field, seeds, lcs.advect_opts(lcs.RK4, t0=0.0, T=T, dt=dt, variant=2), fm)
+        x = np.empty((2, N), np.float32)
+        st = np.empty(N, np.uint8)
+        f = np.empty(N, np.float32)
+        lcs.lcs_flowmap_get(ctx, fm, 0, x, st)
+        lcs.lcs_ftle(ctx, fm, 0, f)
+        lcs.lcs_synchronize(ctx)
+    finally:
+        lcs.lcs_free_flowmap(fm)
+        lcs.lcs_free_seeds(seeds)
+        lcs.lcs_free_field(field)
+    o = oracle_run(g, n, lo, hi, (0, 0), T, dt)
+    check_flowmap(x, o["xyz"], st, o["status"], 2.0, float(np.nanmax(o["ftle"])), T)
+    check_ftle(f, o["ftle"])
