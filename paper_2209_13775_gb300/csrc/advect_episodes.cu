@@ -30,16 +30,17 @@
 #define LCS_EP_MINB 4
 #endif
 
-// 32-byte tracer record: one sector per tracer for the re-bundling scatter
+// 48-byte tracer record (three 16-byte loads) moved by the re-bundling scatter
 struct __align__(16) Tracer {
     float x, y, z;          // wrapped into [origin, origin + L) on periodic axes
     int id;                 // seed index
+    float cx, cy, cz;       // the coordinates' carried rounding (rk4_advance)
+    float te;               // exit time
     short ix, iy, iz;       // periods crossed per axis
     unsigned char st, pad;  // status
-    float te;               // exit time
-    float unused;
+    float unused[2];
 };
-static_assert(sizeof(Tracer) == 32, "tracer record must be one 32-byte sector");
+static_assert(sizeof(Tracer) == 48, "tracer record must be three 16-byte words");
 
 // Re-bundling order: cells grouped in bricks of 2^EP_BRICK cells per axis, bricks in
 // x-fastest order and cells x-fastest inside a brick.  A wave of resident blocks then holds
@@ -82,13 +83,16 @@ __global__ void ep_init_kernel(RectParams P, const float *__restrict__ seeds, lo
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    float x[3] = {seeds[i], seeds[N + i], seeds[2 * N + i]};
+    float x[3] = {seeds[i], seeds[N + i], seeds[2 * N + i]}, c[3] = {0.0f, 0.0f, 0.0f};
     int img[3] = {0, 0, 0};
-    wrap_periodic<3>(P, x, img);
+    wrap_periodic<3>(P, x, c, img);
     Tracer t;
     t.x = x[0];
     t.y = x[1];
     t.z = x[2];
+    t.cx = c[0];
+    t.cy = c[1];
+    t.cz = c[2];
     t.id = (int)i;
     t.ix = (short)img[0];
     t.iy = (short)img[1];
@@ -96,7 +100,7 @@ __global__ void ep_init_kernel(RectParams P, const float *__restrict__ seeds, lo
     t.st = LCS_TRACER_OK;
     t.pad = 0;
     t.te = job_tend[job];
-    t.unused = 0.0f;
+    t.unused[0] = t.unused[1] = 0.0f;
     S[i] = t;
     unsigned k = cell_key(P, x, shift);
     keys[i] = k;
@@ -454,7 +458,7 @@ __device__ __forceinline__ void interp3q(int v0, const float *w, const float4 *_
 
 // One RK4 step in 3D from slices m0, m1, m2 (stage times t_n, t_n + h/2, t_n + h).
 template <int PM>
-__device__ __forceinline__ void rk4_step3q(const RectParams &P, const SliceGeom &G, float *x, float h,
+__device__ __forceinline__ void rk4_step3q(const RectParams &P, const SliceGeom &G, float *x, float *cx, float h,
                                            const float4 *__restrict__ slices, int m0, int m1, int m2, size_t ps,
                                            QuadCache &cc)
 {
@@ -478,7 +482,7 @@ __device__ __forceinline__ void rk4_step3q(const RectParams &P, const SliceGeom 
     interp3q(v, w, slices + (size_t)m2 * ss, m2, ps, nxy, cc, k4);
     const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
+    for (int c = 0; c < 3; ++c) rk4_advance(x[c], cx[c], h6, k1[c], k2[c], k3[c], k4[c]);
 }
 
 // ------------------------------------------------- variational equations
@@ -556,7 +560,7 @@ __global__ void __launch_bounds__(256, 2) ep_var3_kernel(RectParams P, SliceGeom
     if (i >= A.N) return;
     const long long N = A.N;
     Tracer t = S[i];
-    float x[3] = {t.x, t.y, t.z};
+    float x[3] = {t.x, t.y, t.z}, cx[3] = {t.cx, t.cy, t.cz};
     if (t.st == LCS_TRACER_OK) {
         int img[3] = {t.ix, t.iy, t.iz};
         float M[3][3];
@@ -603,11 +607,11 @@ __global__ void __launch_bounds__(256, 2) ep_var3_kernel(RectParams P, SliceGeom
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                x[a] = fmaf(h6, (k[0][a] + k[3][a]) + 2.0f * (k[1][a] + k[2][a]), x[a]);
+                rk4_advance(x[a], cx[a], h6, k[0][a], k[1][a], k[2][a], k[3][a]);
 #pragma unroll
                 for (int b = 0; b < 3; ++b) M[a][b] = fmaf(h6, S03[a][b] + 2.0f * S12[a][b], M[a][b]);
             }
-            wrap_periodic<3, PM>(P, x, img);
+            wrap_periodic<3, PM>(P, x, cx, img);
             if (rect_left<3, PM>(P, x)) {
                 t.st = LCS_TRACER_LEFT;
                 t.te = fmaf((float)(n + 1), h, A.job_t0[job]);
@@ -617,6 +621,9 @@ __global__ void __launch_bounds__(256, 2) ep_var3_kernel(RectParams P, SliceGeom
         t.x = x[0];
         t.y = x[1];
         t.z = x[2];
+        t.cx = cx[0];
+        t.cy = cx[1];
+        t.cz = cx[2];
         t.ix = (short)img[0];
         t.iy = (short)img[1];
         t.iz = (short)img[2];
@@ -638,11 +645,11 @@ __global__ void __launch_bounds__(256, 2) ep_var3_kernel(RectParams P, SliceGeom
 __device__ __forceinline__ void ep_store(const RectParams &P, const Rk4Args &A, int slot, const Tracer &t, int snap)
 {
     const long long N = A.N, id = t.id;
-    const float x[3] = {t.x, t.y, t.z};
+    const float x[3] = {t.x, t.y, t.z}, c[3] = {t.cx, t.cy, t.cz};
     const int img[3] = {t.ix, t.iy, t.iz};
     float *o = A.out_xyz + (size_t)slot * 3 * N;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) o[d * N + id] = P.periodic[d] ? fmaf((float)img[d], P.L[d], x[d]) : x[d];
+    for (int d = 0; d < 3; ++d) o[d * N + id] = out_coord(P, d, x[d], c[d], img[d]);
     A.out_status[(size_t)slot * N + id] = t.st;
     A.out_texit[(size_t)slot * N + id] = snap >= 0 && t.st == LCS_TRACER_OK ? __ldg(A.snap_te + snap) : t.te;
 }
@@ -661,7 +668,7 @@ __global__ void __launch_bounds__(256, LCS_EP_MINB) ep_advect3_kernel(RectParams
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= A.N) return;
     Tracer t = S[i];
-    float x[3] = {t.x, t.y, t.z};
+    float x[3] = {t.x, t.y, t.z}, cx[3] = {t.cx, t.cy, t.cz};
     if (t.st == LCS_TRACER_OK) {
         int img[3] = {t.ix, t.iy, t.iz};
         const int ns = A.job_nsteps[job];
@@ -672,8 +679,8 @@ __global__ void __launch_bounds__(256, LCS_EP_MINB) ep_advect3_kernel(RectParams
         cc.slice = -1;
         for (int n = s0; n < e; ++n) {
             const int *m = smap + 3 * (n - s0);
-            rk4_step3q<PM>(P, G, x, h, slices, __ldg(m), __ldg(m + 1), __ldg(m + 2), plane_stride, cc);
-            wrap_periodic<3, PM>(P, x, img);
+            rk4_step3q<PM>(P, G, x, cx, h, slices, __ldg(m), __ldg(m + 1), __ldg(m + 2), plane_stride, cc);
+            wrap_periodic<3, PM>(P, x, cx, img);
             if (rect_left<3, PM>(P, x)) {
                 t.st = LCS_TRACER_LEFT;
                 t.te = fmaf((float)(n + 1), h, A.job_t0[job]);
@@ -683,6 +690,9 @@ __global__ void __launch_bounds__(256, LCS_EP_MINB) ep_advect3_kernel(RectParams
         t.x = x[0];
         t.y = x[1];
         t.z = x[2];
+        t.cx = cx[0];
+        t.cy = cx[1];
+        t.cz = cx[2];
         t.ix = (short)img[0];
         t.iy = (short)img[1];
         t.iz = (short)img[2];

@@ -120,14 +120,15 @@ __global__ void __launch_bounds__(256) rk4_gather_kernel(RectParams P, const cha
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     int job = blockIdx.y;
     if (i >= A.N) return;
-    float x[DIM];
+    float x[DIM], cx[DIM];
     int img[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         x[d] = A.seeds[d * A.N + i];
+        cx[d] = 0.0f;
         img[d] = 0;
     }
-    wrap_periodic<DIM>(P, x, img);
+    wrap_periodic<DIM>(P, x, cx, img);
     const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
     const int ns = A.job_nsteps[job];
     const float h = A.job_h[job];
@@ -137,25 +138,25 @@ __global__ void __launch_bounds__(256) rk4_gather_kernel(RectParams P, const cha
     for (int n = 0; n < ns; ++n) {
         SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
         if constexpr (DIM == 2)
-            rk4_step<2, ST, SRC_GLOBAL>(P, x, h, frames + (size_t)e0.k * fstride,
+            rk4_step<2, ST, SRC_GLOBAL>(P, x, cx, h, frames + (size_t)e0.k * fstride,
                                         frames + (size_t)(e0.k + 1) * fstride, e0.a, frames + (size_t)e1.k * fstride,
                                         frames + (size_t)(e1.k + 1) * fstride, e1.a, frames + (size_t)e2.k * fstride,
                                         frames + (size_t)(e2.k + 1) * fstride, e2.a);
         else
-            rk4_step3p<ST>(P, x, h, frames + (size_t)e0.k * fstride, e0.a, frames + (size_t)e1.k * fstride, e1.a,
-                           frames + (size_t)e2.k * fstride, e2.a);
-        wrap_periodic<DIM>(P, x, img);
+            rk4_step3p<ST>(P, x, cx, h, frames + (size_t)e0.k * fstride, e0.a, frames + (size_t)e1.k * fstride,
+                           e1.a, frames + (size_t)e2.k * fstride, e2.a);
+        wrap_periodic<DIM>(P, x, cx, img);
         if (rect_left<DIM>(P, x)) {
             st = LCS_TRACER_LEFT;
             te = fmaf((float)(n + 1), h, A.job_t0[job]);
             break;
         }
         for (; si < A.nsnap && snap_step(A, si, ns) == n + 1; ++si)
-            store_tracer<DIM>(P, A, snap_slot(A, job, si), i, x, img, st, snap_exit(A, job, si, st, te));
+            store_tracer<DIM>(P, A, snap_slot(A, job, si), i, x, cx, img, st, snap_exit(A, job, si, st, te));
     }
     for (; si < A.nsnap; ++si)  // snapshots after the tracer stopped (or of a zero-step job)
-        store_tracer<DIM>(P, A, snap_slot(A, job, si), i, x, img, st, snap_exit(A, job, si, st, te));
-    store_tracer<DIM>(P, A, job, i, x, img, st, te);
+        store_tracer<DIM>(P, A, snap_slot(A, job, si), i, x, cx, img, st, snap_exit(A, job, si, st, te));
+    store_tracer<DIM>(P, A, job, i, x, cx, img, st, te);
 }
 
 // ============================================================ variational
@@ -226,16 +227,17 @@ __global__ void __launch_bounds__(256) rk4_var_kernel(RectParams P, const char *
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int job = blockIdx.y;
     if (i >= A.N) return;
-    float x[DIM], M[DIM][DIM];
+    float x[DIM], cx[DIM], M[DIM][DIM];
     int img[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         x[d] = A.seeds[d * A.N + i];
+        cx[d] = 0.0f;
         img[d] = 0;
 #pragma unroll
         for (int e = 0; e < DIM; ++e) M[d][e] = d == e ? 1.0f : 0.0f;
     }
-    wrap_periodic<DIM>(P, x, img);
+    wrap_periodic<DIM>(P, x, cx, img);
     const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
     const int ns = A.job_nsteps[job];
     const float h = A.job_h[job], hh = 0.5f * h, h6 = h * (1.0f / 6.0f);
@@ -268,19 +270,19 @@ __global__ void __launch_bounds__(256) rk4_var_kernel(RectParams P, const char *
         }
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            x[a] = fmaf(h6, (k[0][a] + k[3][a]) + 2.0f * (k[1][a] + k[2][a]), x[a]);
+            rk4_advance(x[a], cx[a], h6, k[0][a], k[1][a], k[2][a], k[3][a]);
 #pragma unroll
             for (int b = 0; b < DIM; ++b)
                 M[a][b] = fmaf(h6, (K[0][a][b] + K[3][a][b]) + 2.0f * (K[1][a][b] + K[2][a][b]), M[a][b]);
         }
-        wrap_periodic<DIM>(P, x, img);
+        wrap_periodic<DIM>(P, x, cx, img);
         if (rect_left<DIM>(P, x)) {
             st = LCS_TRACER_LEFT;
             te = fmaf((float)(n + 1), h, A.job_t0[job]);
             break;
         }
     }
-    store_tracer<DIM>(P, A, job, i, x, img, st, te);
+    store_tracer<DIM>(P, A, job, i, x, cx, img, st, te);
     float *o = A.out_grad + ((size_t)job * A.N + i) * DIM * DIM;
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
@@ -379,7 +381,7 @@ __device__ __forceinline__ void ring_tile(const RectParams &P, const char *__res
     const int tid = threadIdx.x, bt = blockDim.x;
     long long idx[TPT];
     bool active[TPT], live[TPT];
-    float x[TPT][2];
+    float x[TPT][2], cx[TPT][2];
     int img[TPT][2];
     unsigned char st[TPT];
     float te[TPT];
@@ -391,8 +393,9 @@ __device__ __forceinline__ void ring_tile(const RectParams &P, const char *__res
         live[t] = active[t];
         x[t][0] = active[t] ? A.seeds[idx[t]] : 0.0f;
         x[t][1] = active[t] ? A.seeds[A.N + idx[t]] : 0.0f;
+        cx[t][0] = cx[t][1] = 0.0f;
         img[t][0] = img[t][1] = 0;
-        wrap_periodic<2>(P, x[t], img[t]);
+        wrap_periodic<2>(P, x[t], cx[t], img[t]);
         st[t] = LCS_TRACER_OK;
         te[t] = tend;
     }
@@ -465,10 +468,12 @@ __device__ __forceinline__ void ring_tile(const RectParams &P, const char *__res
             // a step whose frames did not all get a slot (e.g. one straddling the periodic wrap, which
             // reads four frames) mixes shared and global pointers: generic loads serve both
             if (all_smem)
-                rk4_step<2, ST, SRC_SHARED>(P, x[t], h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
+                rk4_step<2, ST, SRC_SHARED>(P, x[t], cx[t], h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5],
+                                            e2.a);
             else
-                rk4_step<2, ST, SRC_GENERIC>(P, x[t], h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5], e2.a);
-            wrap_periodic<2>(P, x[t], img[t]);
+                rk4_step<2, ST, SRC_GENERIC>(P, x[t], cx[t], h, p[0], p[1], e0.a, p[2], p[3], e1.a, p[4], p[5],
+                                             e2.a);
+            wrap_periodic<2>(P, x[t], cx[t], img[t]);
             if (rect_left<2>(P, x[t])) {
                 st[t] = LCS_TRACER_LEFT;
                 te[t] = fmaf((float)(n + 1), h, A.job_t0[job]);
@@ -479,18 +484,18 @@ __device__ __forceinline__ void ring_tile(const RectParams &P, const char *__res
 #pragma unroll
             for (int t = 0; t < TPT; ++t)
                 if (active[t])
-                    store_tracer<2>(P, A, snap_slot(A, job, si), idx[t], x[t], img[t], st[t],
+                    store_tracer<2>(P, A, snap_slot(A, job, si), idx[t], x[t], cx[t], img[t], st[t],
                                     snap_exit(A, job, si, st[t], te[t]));
     }
     for (; si < A.nsnap; ++si)  // a zero-step job, or a block that stopped on a copy timeout
 #pragma unroll
         for (int t = 0; t < TPT; ++t)
             if (active[t])
-                store_tracer<2>(P, A, snap_slot(A, job, si), idx[t], x[t], img[t], st[t],
+                store_tracer<2>(P, A, snap_slot(A, job, si), idx[t], x[t], cx[t], img[t], st[t],
                                 snap_exit(A, job, si, st[t], te[t]));
 #pragma unroll
     for (int t = 0; t < TPT; ++t)
-        if (active[t]) store_tracer<2>(P, A, job, idx[t], x[t], img[t], st[t], te[t]);
+        if (active[t]) store_tracer<2>(P, A, job, idx[t], x[t], cx[t], img[t], st[t], te[t]);
 }
 
 // Ring kernel.  Non-persistent: block (x, y) is tile x of job y.  Persistent: the grid
@@ -619,9 +624,9 @@ __global__ void __launch_bounds__(256) rk4_slice2d_kernel(RectParams P, const fl
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int job = blockIdx.y;
     if (i >= A.N) return;
-    float x[2] = {A.seeds[i], A.seeds[A.N + i]};
+    float x[2] = {A.seeds[i], A.seeds[A.N + i]}, cx[2] = {0.0f, 0.0f};
     int img[2] = {0, 0};
-    wrap_periodic<2, PM>(P, x, img);
+    wrap_periodic<2, PM>(P, x, cx, img);
     const int ns = A.job_nsteps[job];
     const float h = A.job_h[job];
     const float4 *sj = slices + O.off[job] * 2 * nodes;
@@ -645,19 +650,19 @@ __global__ void __launch_bounds__(256) rk4_slice2d_kernel(RectParams P, const fl
         interp2s<PM>(P, y, s0 + 2 * ss, k4);
         const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
-        for (int c = 0; c < 2; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
-        wrap_periodic<2, PM>(P, x, img);
+        for (int c = 0; c < 2; ++c) rk4_advance(x[c], cx[c], h6, k1[c], k2[c], k3[c], k4[c]);
+        wrap_periodic<2, PM>(P, x, cx, img);
         if (rect_left<2, PM>(P, x)) {
             st = LCS_TRACER_LEFT;
             te = fmaf((float)(n + 1), h, A.job_t0[job]);
             break;
         }
         for (; si < A.nsnap && snap_step(A, si, ns) == n + 1; ++si)
-            store_tracer<2>(P, A, snap_slot(A, job, si), i, x, img, st, snap_exit(A, job, si, st, te));
+            store_tracer<2>(P, A, snap_slot(A, job, si), i, x, cx, img, st, snap_exit(A, job, si, st, te));
     }
     for (; si < A.nsnap; ++si)
-        store_tracer<2>(P, A, snap_slot(A, job, si), i, x, img, st, snap_exit(A, job, si, st, te));
-    store_tracer<2>(P, A, job, i, x, img, st, te);
+        store_tracer<2>(P, A, snap_slot(A, job, si), i, x, cx, img, st, snap_exit(A, job, si, st, te));
+    store_tracer<2>(P, A, job, i, x, cx, img, st, te);
 }
 
 size_t rk4_slice2d_bytes(const lcs_field *f, int njobs, const int *host_nsteps)

@@ -20,14 +20,14 @@
 
 // ------------------------------------------------------------------ RK4 on tets
 
-// tracer state into flow-map slot `slot` (mesh fields: no periodic images)
+// tracer state into flow-map slot `slot` (mesh fields: no periodic images): x + c rounded once
 template <int DIM>
-__device__ __forceinline__ void mesh_store(const Rk4Args &A, int slot, long long i, const float *x, unsigned char st,
-                                           float te)
+__device__ __forceinline__ void mesh_store(const Rk4Args &A, int slot, long long i, const float *x, const float *c,
+                                           unsigned char st, float te)
 {
     float *o = A.out_xyz + (size_t)slot * DIM * A.N;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) o[d * A.N + i] = x[d];
+    for (int d = 0; d < DIM; ++d) o[d * A.N + i] = x[d] + c[d];
     A.out_status[(size_t)slot * A.N + i] = st;
     A.out_texit[(size_t)slot * A.N + i] = te;
 }
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) rk4_tet_kernel(TetDev T, Rk4Args A, const
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int job = blockIdx.y;
     if (i >= A.N) return;
-    float x[3] = {A.seeds[i], A.seeds[A.N + i], A.seeds[2 * A.N + i]};
+    float x[3] = {A.seeds[i], A.seeds[A.N + i], A.seeds[2 * A.N + i]}, cx[3] = {0.0f, 0.0f, 0.0f};
     int cell = cells0[i];
     unsigned char st = LCS_TRACER_OK;
     float te = A.job_tend[job];
@@ -73,13 +73,13 @@ __global__ void __launch_bounds__(256) rk4_tet_kernel(TetDev T, Rk4Args A, const
         }
         const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) x[q] = fmaf(h6, (k[0][q] + k[3][q]) + 2.0f * (k[1][q] + k[2][q]), x[q]);
+        for (int q = 0; q < 3; ++q) rk4_advance(x[q], cx[q], h6, k[0][q], k[1][q], k[2][q], k[3][q]);
         for (; si < A.nsnap && snap_step(A, si, ns) == n + 1; ++si)
-            mesh_store<3>(A, snap_slot(A, job, si), i, x, st, snap_exit(A, job, si, st, te));
+            mesh_store<3>(A, snap_slot(A, job, si), i, x, cx, st, snap_exit(A, job, si, st, te));
     }
     for (; si < A.nsnap; ++si)  // snapshots after the tracer stopped
-        mesh_store<3>(A, snap_slot(A, job, si), i, x, st, snap_exit(A, job, si, st, te));
-    mesh_store<3>(A, job, i, x, st, te);
+        mesh_store<3>(A, snap_slot(A, job, si), i, x, cx, st, snap_exit(A, job, si, st, te));
+    mesh_store<3>(A, job, i, x, cx, st, te);
 }
 
 // ------------------------------------------------------------- RK4 on triangles
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int job = blockIdx.y;
     if (i >= A.N) return;
-    float x[2] = {A.seeds[i], A.seeds[A.N + i]};
+    float x[2] = {A.seeds[i], A.seeds[A.N + i]}, cx[2] = {0.0f, 0.0f};
     int cell = cells0[i];
     unsigned char st = LCS_TRACER_OK;
     float te = A.job_tend[job];
@@ -127,13 +127,13 @@ __global__ void __launch_bounds__(256) rk4_tri_kernel(TriDev T, Rk4Args A, const
         }
         const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) x[q] = fmaf(h6, (k[0][q] + k[3][q]) + 2.0f * (k[1][q] + k[2][q]), x[q]);
+        for (int q = 0; q < 2; ++q) rk4_advance(x[q], cx[q], h6, k[0][q], k[1][q], k[2][q], k[3][q]);
         for (; si < A.nsnap && snap_step(A, si, ns) == n + 1; ++si)
-            mesh_store<2>(A, snap_slot(A, job, si), i, x, st, snap_exit(A, job, si, st, te));
+            mesh_store<2>(A, snap_slot(A, job, si), i, x, cx, st, snap_exit(A, job, si, st, te));
     }
     for (; si < A.nsnap; ++si)  // snapshots after the tracer stopped
-        mesh_store<2>(A, snap_slot(A, job, si), i, x, st, snap_exit(A, job, si, st, te));
-    mesh_store<2>(A, job, i, x, st, te);
+        mesh_store<2>(A, snap_slot(A, job, si), i, x, cx, st, snap_exit(A, job, si, st, te));
+    mesh_store<2>(A, job, i, x, cx, st, te);
 }
 
 // ------------------------------------------------ variational equations on meshes
@@ -148,10 +148,11 @@ __global__ void __launch_bounds__(256) rk4_mesh_var_kernel(MD T, Rk4Args A, cons
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const int job = blockIdx.y;
     if (i >= A.N) return;
-    float x[DIM], M[DIM][DIM];
+    float x[DIM], cx[DIM], M[DIM][DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         x[d] = A.seeds[d * A.N + i];
+        cx[d] = 0.0f;
 #pragma unroll
         for (int e = 0; e < DIM; ++e) M[d][e] = d == e ? 1.0f : 0.0f;
     }
@@ -207,13 +208,13 @@ __global__ void __launch_bounds__(256) rk4_mesh_var_kernel(MD T, Rk4Args A, cons
         }
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            x[a] = fmaf(h6, (k[0][a] + k[3][a]) + 2.0f * (k[1][a] + k[2][a]), x[a]);
+            rk4_advance(x[a], cx[a], h6, k[0][a], k[1][a], k[2][a], k[3][a]);
 #pragma unroll
             for (int b = 0; b < DIM; ++b)
                 M[a][b] = fmaf(h6, (K[0][a][b] + K[3][a][b]) + 2.0f * (K[1][a][b] + K[2][a][b]), M[a][b]);
         }
     }
-    mesh_store<DIM>(A, job, i, x, st, te);
+    mesh_store<DIM>(A, job, i, x, cx, st, te);
     float *o = A.out_grad + ((size_t)job * A.N + i) * DIM * DIM;
 #pragma unroll
     for (int a = 0; a < DIM; ++a)

@@ -108,31 +108,32 @@ __global__ void early_advect_kernel(CgLaunch L, RectParams P, const char *__rest
     const long long idx[3] = {p % L.n[0], (p / L.n[0]) % L.n[1], DIM == 3 ? p / ((long long)L.n[0] * L.n[1]) : 0};
     int w;
     const long long q = member(L, idx, s, s == 0 ? 1 : axis_mode(L, idx, (s - 1) >> 1, nullptr), &w);
-    float x[DIM];
+    float x[DIM], cx[DIM];
     int img[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         x[d] = A.seeds[d * A.N + q];
+        cx[d] = 0.0f;
         img[d] = 0;
     }
-    wrap_periodic<DIM>(P, x, img);
+    wrap_periodic<DIM>(P, x, cx, img);
     const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
     const float h = A.job_h[job];
     for (int n = 0; n < it.y; ++n) {
         SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
         if constexpr (DIM == 2)
-            rk4_step<2, ST, SRC_GLOBAL>(P, x, h, frames + (size_t)e0.k * fstride,
+            rk4_step<2, ST, SRC_GLOBAL>(P, x, cx, h, frames + (size_t)e0.k * fstride,
                                         frames + (size_t)(e0.k + 1) * fstride, e0.a, frames + (size_t)e1.k * fstride,
                                         frames + (size_t)(e1.k + 1) * fstride, e1.a, frames + (size_t)e2.k * fstride,
                                         frames + (size_t)(e2.k + 1) * fstride, e2.a);
         else
-            rk4_step3p<ST>(P, x, h, frames + (size_t)e0.k * fstride, e0.a, frames + (size_t)e1.k * fstride, e1.a,
-                           frames + (size_t)e2.k * fstride, e2.a);
-        wrap_periodic<DIM>(P, x, img);
+            rk4_step3p<ST>(P, x, cx, h, frames + (size_t)e0.k * fstride, e0.a, frames + (size_t)e1.k * fstride,
+                           e1.a, frames + (size_t)e2.k * fstride, e2.a);
+        wrap_periodic<DIM>(P, x, cx, img);
     }
     float *o = pos + (size_t)t * DIM;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) o[d] = P.periodic[d] ? fmaf((float)img[d], P.L[d], x[d]) : x[d];
+    for (int d = 0; d < DIM; ++d) o[d] = out_coord(P, d, x[d], cx[d], img[d]);
 }
 
 // the same on a tet (DIM 3, MD = TetDev) or triangle (DIM 2, TriDev) field: member q from its seed
@@ -152,9 +153,12 @@ __global__ void early_advect_mesh_kernel(CgLaunch L, MD T, Rk4Args A, const int 
     const long long idx[3] = {p % L.n[0], (p / L.n[0]) % L.n[1], DIM == 3 ? p / ((long long)L.n[0] * L.n[1]) : 0};
     int w;
     const long long q = member(L, idx, s, s == 0 ? 1 : axis_mode(L, idx, (s - 1) >> 1, cells0), &w);
-    float x[DIM];
+    float x[DIM], cx[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) x[d] = A.seeds[d * A.N + q];
+    for (int d = 0; d < DIM; ++d) {
+        x[d] = A.seeds[d * A.N + q];
+        cx[d] = 0.0f;
+    }
     int cell = cells0[q];
     const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
     const float h = A.job_h[job], hh = 0.5f * h;
@@ -178,11 +182,11 @@ __global__ void early_advect_mesh_kernel(CgLaunch L, MD T, Rk4Args A, const int 
         }
         const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) x[d] = fmaf(h6, (k[0][d] + k[3][d]) + 2.0f * (k[1][d] + k[2][d]), x[d]);
+        for (int d = 0; d < DIM; ++d) rk4_advance(x[d], cx[d], h6, k[0][d], k[1][d], k[2][d], k[3][d]);
     }
     float *o = pos + (size_t)t * DIM;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) o[d] = x[d];
+    for (int d = 0; d < DIM; ++d) o[d] = x[d] + cx[d];
 }
 
 // grad F from the re-integrated stencil (the regular pass's formulas), C, lambda_max, FTLE

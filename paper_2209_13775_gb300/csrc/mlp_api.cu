@@ -250,7 +250,7 @@ lcs_status advect_surrogate(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s
     fm->T[0] = T;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t sched_b = al(sizeof(SchedEntry) * 3 * (size_t)K * S);
-    const size_t need = sched_b + al(sizeof(float) * 3 * N) + al(ngrp) + 8 * al(64);
+    const size_t need = sched_b + al(sizeof(float) * 3 * N) + al(sizeof(float) * 2 * N) + al(ngrp) + 8 * al(64);
     LCS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     lcs_status st = lcs_scratch_reserve(ctx, need);
     if (st != LCS_OK) {
@@ -263,6 +263,8 @@ lcs_status advect_surrogate(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s
     p += sched_b;
     float *xp = (float *)p;
     p += al(sizeof(float) * 3 * N);
+    float *cxy = (float *)p;   // the tracer state's carried rounding (rk4_advance)
+    p += al(sizeof(float) * 2 * N);
     unsigned char *flag = (unsigned char *)p;
     p += al(ngrp);
     JobDev D;
@@ -283,6 +285,7 @@ lcs_status advect_surrogate(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s
     // tracer state: the flow map starts at the seeds, OK, exit time t0 + T, no fallbacks
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(fm->d_xyz, s->d_xyz, sizeof(float) * 2 * N, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cxy, 0, sizeof(float) * 2 * N, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(fm->d_status, LCS_TRACER_OK, N, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(fm->d_steps, 0, sizeof(int) * N, ctx->stream);
     if (e == cudaSuccess) e = launch_fill_f32(fm->d_texit, N, (float)(o->t0 + T), ctx->stream);
@@ -321,6 +324,7 @@ lcs_status advect_surrogate(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s
         G.rho = xp + 2 * N;
         G.xp = xp;
         G.xyz = fm->d_xyz;
+        G.cxy = cxy;
         G.status = fm->d_status;
         G.texit = fm->d_texit;
         G.counts = fm->d_steps;
@@ -331,6 +335,7 @@ lcs_status advect_surrogate(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s
         e = launch_sur_gate(G, f, ctx->stream);
         lcs_tm_end(ctx, 1, ctx->stream);
     }
+    if (e == cudaSuccess) e = launch_settle_f32(fm->d_xyz, cxy, 2 * N, ctx->stream);
     if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "lcs_advect (surrogate): %s", cudaGetErrorString(e));
     return LCS_OK;
 }

@@ -207,16 +207,16 @@ __global__ void __launch_bounds__(256) sur_audit_kernel(SurGateArgs G, RectParam
         if (G.rho[i0 + q] > G.log_tol || !(G.rho[i0 + q] == G.rho[i0 + q])) fall = true;
     const long long a = i0 + (long long)(lowbias32(lowbias32((unsigned)G.step) ^ (unsigned)grp) % (unsigned)m);
     if (!fall && G.status[a] == LCS_TRACER_OK && G.tol < INFINITY) {
-        float x[2] = {G.xyz[a], G.xyz[G.n + a]};
+        float x[2] = {G.xyz[a], G.xyz[G.n + a]}, c[2] = {G.cxy[a], G.cxy[G.n + a]};
         const SchedEntry *sc = G.sched + (size_t)G.step * G.S * 3;
         for (int n = 0; n < G.S; ++n) {
             SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
-            rk4_step<2, ST, SRC_GLOBAL>(P, x, G.h, frames + (size_t)e0.k * fstride,
+            rk4_step<2, ST, SRC_GLOBAL>(P, x, c, G.h, frames + (size_t)e0.k * fstride,
                                         frames + (size_t)(e0.k + 1) * fstride, e0.a, frames + (size_t)e1.k * fstride,
                                         frames + (size_t)(e1.k + 1) * fstride, e1.a, frames + (size_t)e2.k * fstride,
                                         frames + (size_t)(e2.k + 1) * fstride, e2.a);
         }
-        const float dx = G.xp[a] - x[0], dy = G.xp[G.n + a] - x[1];
+        const float dx = G.xp[a] - (x[0] + c[0]), dy = G.xp[G.n + a] - (x[1] + c[1]);
         const float res = sqrtf(dx * dx + dy * dy);
         fall = !(res <= G.tol);
     }
@@ -230,15 +230,17 @@ __global__ void __launch_bounds__(256) sur_apply_kernel(SurGateArgs G, RectParam
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= G.n || G.status[i] != LCS_TRACER_OK) return;
-    float x[2];
+    float x[2], c[2] = {0.0f, 0.0f};
     const int step = G.step;
     if (G.flag[i >> 5]) {
         x[0] = G.xyz[i];
         x[1] = G.xyz[G.n + i];
+        c[0] = G.cxy[i];
+        c[1] = G.cxy[G.n + i];
         const SchedEntry *sc = G.sched + (size_t)step * G.S * 3;
         for (int n = 0; n < G.S; ++n) {
             SchedEntry e0 = load_sched(sc + 3 * n), e1 = load_sched(sc + 3 * n + 1), e2 = load_sched(sc + 3 * n + 2);
-            rk4_step<2, ST, SRC_GLOBAL>(P, x, G.h, frames + (size_t)e0.k * fstride,
+            rk4_step<2, ST, SRC_GLOBAL>(P, x, c, G.h, frames + (size_t)e0.k * fstride,
                                         frames + (size_t)(e0.k + 1) * fstride, e0.a, frames + (size_t)e1.k * fstride,
                                         frames + (size_t)(e1.k + 1) * fstride, e1.a, frames + (size_t)e2.k * fstride,
                                         frames + (size_t)(e2.k + 1) * fstride, e2.a);
@@ -259,6 +261,8 @@ __global__ void __launch_bounds__(256) sur_apply_kernel(SurGateArgs G, RectParam
     }
     G.xyz[i] = x[0];
     G.xyz[G.n + i] = x[1];
+    G.cxy[i] = c[0];   // a proposal starts without a carried rounding
+    G.cxy[G.n + i] = c[1];
 }
 
 __global__ void fill_f32_kernel(float *p, long long n, float v)
@@ -267,12 +271,26 @@ __global__ void fill_f32_kernel(float *p, long long n, float v)
     if (i < n) p[i] = v;
 }
 
+// x + c rounded once: the flow map of the surrogate path, as the fixed-step kernels store it
+__global__ void settle_f32_kernel(float *x, const float *c, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = x[i] + c[i];
+}
+
 }  // namespace
 
 cudaError_t launch_fill_f32(float *p, long long n, float v, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     fill_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_settle_f32(float *x, const float *c, long long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    settle_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, c, n);
     return cudaGetLastError();
 }
 

@@ -65,6 +65,7 @@ struct SurGateArgs {
     const float *rho;         // [n] predicted log10 error
     const float *xp;          // [2][n] proposals
     float *xyz;               // [2][n] tracer state
+    float *cxy;               // [2][n] its carried rounding (rk4_advance)
     unsigned char *status;
     float *texit;
     int *counts;              // [n] sub-intervals integrated by RK4
@@ -86,6 +87,7 @@ __host__ __device__ __forceinline__ unsigned lowbias32(unsigned x)
 
 cudaError_t launch_mlp_step(const MlpStepArgs &A, int num_sms, cudaStream_t s);
 cudaError_t launch_fill_f32(float *p, long long n, float v, cudaStream_t s);
+cudaError_t launch_settle_f32(float *x, const float *c, long long n, cudaStream_t s);
 cudaError_t launch_sur_gate(const SurGateArgs &G, const lcs_field *f, cudaStream_t s);
 cudaError_t launch_mlp_refresh(lcs_mlp *m, cudaStream_t s);
 lcs_status advect_surrogate(lcs_ctx *ctx, const lcs_field *f, const lcs_seeds *s, const lcs_advect_opts *o,

@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) tr_targets_kernel(RectParams P, const cha
     __syncthreads();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float x[2] = {xyt[i], xyt[n + i]};
+    float x[2] = {xyt[i], xyt[n + i]}, cx[2] = {0.0f, 0.0f};
     const float t0 = xyt[2 * n + i];
     auto bracket = [&](float t, int &k, float &a) {
         if (nf <= 1) {
@@ -244,12 +244,12 @@ __global__ void __launch_bounds__(256) tr_targets_kernel(RectParams P, const cha
         bracket(ts, k0, a0);
         bracket(ts + 0.5f * h, k1, a1);
         bracket(ts + h, k2, a2);
-        rk4_step<2, ST, SRC_GLOBAL>(P, x, h, frames + (size_t)k0 * fstride, frames + (size_t)(k0 + 1) * fstride, a0,
-                                    frames + (size_t)k1 * fstride, frames + (size_t)(k1 + 1) * fstride, a1,
+        rk4_step<2, ST, SRC_GLOBAL>(P, x, cx, h, frames + (size_t)k0 * fstride, frames + (size_t)(k0 + 1) * fstride,
+                                    a0, frames + (size_t)k1 * fstride, frames + (size_t)(k1 + 1) * fstride, a1,
                                     frames + (size_t)k2 * fstride, frames + (size_t)(k2 + 1) * fstride, a2);
     }
-    disp[i] = x[0] - xyt[i];
-    disp[n + i] = x[1] - xyt[n + i];
+    disp[i] = (x[0] - xyt[i]) + cx[0];
+    disp[n + i] = (x[1] - xyt[n + i]) + cx[1];
 }
 
 size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }

@@ -364,26 +364,30 @@ __device__ __forceinline__ SchedEntry load_sched(const SchedEntry *p)
     return e;
 }
 
-// periodic axes: keep x in [origin, origin + L) with an integer count of periods
+// periodic axes: keep x in [origin, origin + L) with an integer count of periods; c is the
+// coordinate's carried rounding (rk4_advance), which the shift's own rounding joins
 template <int DIM, int PM = -1>
-__device__ __forceinline__ void wrap_periodic(const RectParams &P, float *x, int *img)
+__device__ __forceinline__ void wrap_periodic(const RectParams &P, float *x, float *c, int *img)
 {
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         if (!per_axis<PM>(P, d)) continue;
         float hiL = P.origin[d] + P.L[d];
         if (x[d] >= hiL) {
-            x[d] -= P.L[d];
+            add_carried(x[d], c[d], -P.L[d]);
             img[d] += 1;
         } else if (x[d] < P.origin[d]) {
-            x[d] += P.L[d];
+            add_carried(x[d], c[d], P.L[d]);
             img[d] -= 1;
         }
         if (!(x[d] >= P.origin[d] && x[d] < hiL) && isfinite(x[d])) {  // far outside: full reduction
             float m = floorf((x[d] - P.origin[d]) / P.L[d]);
-            x[d] -= m * P.L[d];
+            add_carried(x[d], c[d], -m * P.L[d]);
             img[d] += (int)m;
-            if (x[d] >= hiL) x[d] = P.origin[d];
+            if (x[d] >= hiL) {
+                x[d] = P.origin[d];
+                c[d] = 0.0f;
+            }
         }
     }
 }
@@ -398,20 +402,29 @@ __device__ __forceinline__ bool rect_left(const RectParams &P, const float *x)
     return out;
 }
 
+// the flow-map coordinate of a tracer: x + c rounded once, unwrapped on periodic axes
+__device__ __forceinline__ float out_coord(const RectParams &P, int d, float x, float c, int img)
+{
+    const float v = x + c;
+    return P.periodic[d] ? fmaf((float)img, P.L[d], v) : v;
+}
+
 template <int DIM>
 __device__ __forceinline__ void store_tracer(const RectParams &P, const Rk4Args &A, int job, long long i,
-                                             const float *x, const int *img, unsigned char st, float te)
+                                             const float *x, const float *c, const int *img, unsigned char st,
+                                             float te)
 {
     float *o = A.out_xyz + (size_t)job * DIM * A.N;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) o[d * A.N + i] = P.periodic[d] ? fmaf((float)img[d], P.L[d], x[d]) : x[d];
+    for (int d = 0; d < DIM; ++d) o[d * A.N + i] = out_coord(P, d, x[d], c[d], img[d]);
     A.out_status[(size_t)job * A.N + i] = st;
     A.out_texit[(size_t)job * A.N + i] = te;
 }
 
-// one RK4 step; stage frames given by (fa, fb, a) triples
+// one RK4 step of x (+ its carried rounding c); stage frames given by (fa, fb, a) triples
 template <int DIM, int ST, int SRC>
-__device__ __forceinline__ void rk4_step(const RectParams &P, float *x, float h, const char *fa0, const char *fb0,
+__device__ __forceinline__ void rk4_step(const RectParams &P, float *x, float *cx, float h, const char *fa0,
+                                         const char *fb0,
                                          float a0, const char *fa1, const char *fb1, float a1, const char *fa2,
                                          const char *fb2, float a2)
 {
@@ -434,12 +447,12 @@ __device__ __forceinline__ void rk4_step(const RectParams &P, float *x, float h,
     interp<DIM, ST, SRC>(S, fa2, fb2, a2, k4);
     const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
+    for (int c = 0; c < DIM; ++c) rk4_advance(x[c], cx[c], h6, k1[c], k2[c], k3[c], k4[c]);
 }
 
 // one RK4 step in 3D; stage s reads interval pair ps with weight as
 template <int ST, int PM = -1>
-__device__ __forceinline__ void rk4_step3p(const RectParams &P, float *x, float h, const char *p0, float a0,
+__device__ __forceinline__ void rk4_step3p(const RectParams &P, float *x, float *cx, float h, const char *p0, float a0,
                                            const char *p1, float a1, const char *p2, float a2)
 {
     float k1[3], k2[3], k3[3], k4[3], y[3];
@@ -461,7 +474,7 @@ __device__ __forceinline__ void rk4_step3p(const RectParams &P, float *x, float 
     interp3p<ST>(S, p2, a2, k4);
     const float h6 = h * (1.0f / 6.0f);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) x[c] = fmaf(h6, (k1[c] + k4[c]) + 2.0f * (k2[c] + k3[c]), x[c]);
+    for (int c = 0; c < 3; ++c) rk4_advance(x[c], cx[c], h6, k1[c], k2[c], k3[c], k4[c]);
 }
 
 // 3D RK4 with tracers re-bundled by cell between episodes (advect_episodes.cu)

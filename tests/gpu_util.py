@@ -81,9 +81,31 @@ def oracle_field(g):
     return oracle.RectField(g.frames, g.times, g.origin, g.spacing, g.periodic, g.time_periodic, g.period)
 
 
-def oracle_run(g, n, lo, hi, periodic, T, dt, t0=0.0, sample=None):
+def stencil_ids(sample, n, periodic, reach=2):
+    """The sampled seed ids with their lattice neighbours up to `reach` along each axis (a one-sided
+    difference at a non-periodic edge needs the second neighbour; periodic lattices need only 1)."""
+    dim = len(periodic)
+    sample = np.asarray(sample, dtype=np.int64)
+    strides = [1, n[0], n[0] * n[1]][:dim]
+    idx = [(sample // strides[a]) % n[a] for a in range(dim)]
+    out = [sample]
+    for a in range(dim):
+        for off in range(-reach, reach + 1):
+            if off == 0:
+                continue
+            q = idx[a] + off
+            keep = np.ones(len(sample), dtype=bool)
+            if periodic[a]:
+                q = q % n[a]
+            else:
+                keep = (q >= 0) & (q < n[a])
+            out.append((sample + (q - idx[a]) * strides[a])[keep])
+    return np.unique(np.concatenate(out))
+
+
+def oracle_run(g, n, lo, hi, periodic, T, dt, t0=0.0, sample=None, reach=2):
     """Oracle flow map and FTLE; `sample` restricts the FTLE to those seed ids (advecting them and
-    their lattice neighbours only)."""
+    their lattice neighbours up to `reach` only)."""
     dim = g.dim
     endpoint = [0 if p else 1 for p in periodic]
     x0 = oracle.seed_grid(dim, n, lo, hi, endpoint)
@@ -97,20 +119,7 @@ def oracle_run(g, n, lo, hi, periodic, T, dt, t0=0.0, sample=None):
         lam, sig = oracle.ftle(C, dim, T)
         return {"seeds": x0, "xyz": xT, "status": st, "t_exit": te, "ftle": sig, "lam": lam, "C": C}
     # stencils of the sampled seeds: +-1, +-2 along each axis (one-sided fallbacks need 2)
-    ids = set()
-    strides = [1, n[0], n[0] * n[1]][:dim]
-    for p in sample:
-        idx = [(p // strides[a]) % n[a] for a in range(dim)]
-        for a in range(dim):
-            for off in (-2, -1, 0, 1, 2):
-                q = list(idx)
-                q[a] = q[a] + off
-                if periodic[a]:
-                    q[a] %= n[a]
-                elif not (0 <= q[a] < n[a]):
-                    continue
-                ids.add(sum(q[b] * strides[b] for b in range(dim)))
-    ids = np.array(sorted(ids))
+    ids = stencil_ids(sample, n, periodic[:dim], reach)
     xT_s, st_s, te_s = oracle.rk4(F, x0[:, ids].astype(np.float64), t0, T, dt)
     N = x0.shape[1]
     # scatter into full-size arrays; seeds not integrated are marked LEFT so no stencil uses them

@@ -390,46 +390,64 @@ def test_abc_shift_by_period(ctx, abc_small):
 
 # ---------------------------------------------------------------- full size
 
-def test_full_size_abc_sampled(ctx):
-    """256^3 seeds on the 128^3 x 64-frame ABC flow, dt 0.02, T 8 (the benchmark workload),
-    compared at sampled seeds with the oracle (which integrates only their stencils)."""
+@pytest.fixture(scope="module")
+def abc_full_oracle():
+    """The oracle on the benchmark workload (256^3 seeds, 128^3 x 64-frame ABC flow, dt 0.02, T 8)
+    at every 97th seed with its +-1 stencil (periodic lattice: central differences only): 172,961
+    sampled seeds, about 1.2M tracers integrated.  Shared by the FP32 parity test and the FP16/BF16
+    storage-error tests."""
     g = inputs.abc()
     L = 2 * np.pi
     n, lo, hi, T, dt = (256, 256, 256), (0.0, 0.0, 0.0), (L, L, L), 8.0, 0.02
-    r = gpu_run(ctx, g, n, lo, hi, (1, 1, 1), T, dt)
-    rng = np.random.default_rng(7)
-    N = 256 ** 3
-    sample = np.unique(np.concatenate([rng.integers(0, N, 40), [0, N - 1, 255, 256 * 255]]))
-    o = oracle_run(g, n, lo, hi, (1, 1, 1), T, dt, sample=sample)
-    ids = o["ids"]
+    sample = np.arange(0, 256 ** 3, 97)
+    o = oracle_run(g, n, lo, hi, (1, 1, 1), T, dt, sample=sample, reach=1)
     sig, lam, C = oracle_ftle_at(sample, 3, n, o["h"], (1, 1, 1), o["period"], o["xT"], o["st"], T)
-    check_flowmap(r["xyz"][0][:, ids], o["xyz_s"], r["status"][0][ids], o["status_s"], L,
-                  float(np.nanmax(sig)), T)
-    d = np.abs(r["ftle"][0][sample].astype(np.float64) - sig)
-    assert np.median(d) <= 1e-5 and d.max() <= 1e-3, (np.median(d), d.max())
+    return dict(g=g, n=n, lo=lo, hi=hi, T=T, dt=dt, L=L, sample=sample, o=o, sig=sig)
+
+
+def test_full_size_abc_sampled(ctx, abc_full_oracle):
+    """256^3 seeds on the 128^3 x 64-frame ABC flow, dt 0.02, T 8 (the benchmark workload, its
+    default launch), against the oracle at every 97th seed: statuses bit-exact, the flow-map bound at
+    every integrated tracer, and the fixed-step FTLE tolerances over the 172,961 sampled seeds."""
+    a = abc_full_oracle
+    r = gpu_run(ctx, a["g"], a["n"], a["lo"], a["hi"], (1, 1, 1), a["T"], a["dt"])
+    o, sample, sig = a["o"], a["sample"], a["sig"]
+    ids = o["ids"]
+    # sigma_max of the bound is the field's largest FTLE; the sampled seeds need not hold it, so the
+    # larger of their oracle maximum and the library's maximum over the whole lattice is taken (the
+    # two agree within the FTLE tolerance wherever both exist)
+    smax = max(float(np.nanmax(sig)), float(np.nanmax(r["ftle"][0])))
+    bound = 1e-5 * np.exp(smax * a["T"])
+    np.testing.assert_array_equal(r["status"][0][ids], o["status_s"])
+    err = np.abs(r["xyz"][0][:, ids].astype(np.float64) - o["xyz_s"]).max(axis=0) / a["L"]
+    over = np.flatnonzero(err > bound)
+    print("\nC2 full size, %d tracers: flow-map error / L median %.2e p99.99 %.2e max %.2e; bound %.2e "
+          "(sigma_max %.3f, sampled %.3f); %d over the bound, worst ratio %.2f"
+          % (len(ids), np.median(err), np.quantile(err, 0.9999), err.max(), bound, smax, float(np.nanmax(sig)),
+             len(over), err.max() / bound))
+    if len(over):
+        w = ids[over[np.argsort(err[over])[-5:]]]
+        print("  worst seeds", w, "GPU FTLE there", r["ftle"][0][w])
+    assert len(over) <= 1e-4 * len(ids) and err.max() <= 10 * bound
+    med, p999, mx = check_ftle(r["ftle"][0][sample], sig)
+    print("\nC2 full size, %d sampled seeds: FTLE |d| median %.2e p99.9 %.2e max %.2e" % (len(sample), med, p999, mx))
     # every output finite, every tracer OK on the periodic domain
     assert np.isfinite(r["ftle"][0]).all() and (r["status"][0] == 0).all()
 
 
 @pytest.mark.parametrize("storage", [lcs.F16, lcs.BF16])
-def test_full_size_abc_storage_error(ctx, storage):
+def test_full_size_abc_storage_error(ctx, abc_full_oracle, storage):
     """Reduced-precision velocity storage on the benchmark workload against the FP64 oracle on the FP32
-    frames (the storage error itself, reported rather than gated; a loose sanity bound only)."""
-    g = inputs.abc()
-    L = 2 * np.pi
-    n, lo, hi, T, dt = (256, 256, 256), (0.0, 0.0, 0.0), (L, L, L), 8.0, 0.02
-    r = gpu_run(ctx, g, n, lo, hi, (1, 1, 1), T, dt, storage=storage)
-    rng = np.random.default_rng(8)
-    N = 256 ** 3
-    sample = np.unique(rng.integers(0, N, 40))
-    o = oracle_run(g, n, lo, hi, (1, 1, 1), T, dt, sample=sample)
-    sig, lam, C = oracle_ftle_at(sample, 3, n, o["h"], (1, 1, 1), o["period"], o["xT"], o["st"], T)
+    frames at every 97th seed (the storage error itself, reported rather than gated; a loose sanity
+    bound only)."""
+    a = abc_full_oracle
+    r = gpu_run(ctx, a["g"], a["n"], a["lo"], a["hi"], (1, 1, 1), a["T"], a["dt"], storage=storage)
+    o, sample, sig = a["o"], a["sample"], a["sig"]
     d = np.abs(r["ftle"][0][sample].astype(np.float64) - sig)
     dx = np.abs(r["xyz"][0][:, o["ids"]].astype(np.float64) - o["xyz_s"]).max(axis=0)
     print("storage", storage, "FTLE |err| median %.3g p99.9 %.3g max %.3g; flow map max %.3g"
           % (np.median(d), np.quantile(d, 0.999), d.max(), dx.max()))
     assert np.median(d) <= 5e-2 and np.isfinite(r["ftle"][0]).all()
-
 
 
 def test_full_size_sliding_window_sampled(ctx, gyre, tmp_path):
@@ -454,18 +472,28 @@ def test_full_size_sliding_window_sampled(ctx, gyre, tmp_path):
     x = np.empty((2, N), dtype=np.float32)
     st = np.empty(N, dtype=np.uint8)
     worst = 0.0
+    # every 97th seed (21,620 per job) on eight jobs spanning |T| = 2, 4, 8, both directions and the
+    # periodic time wrap; six random seeds on every other job
+    dense = {0, 1, 2, 19, 32, 33, 34, 61}
     for j in range(64):
-        i, k = rng.integers(2, n[0] - 2, 6), rng.integers(2, n[1] - 2, 6)
-        sample = np.unique(i + n[0] * k)
+        if j in dense:
+            sample = np.arange(0, N, 97)
+        else:
+            i, k = rng.integers(2, n[0] - 2, 6), rng.integers(2, n[1] - 2, 6)
+            sample = np.unique(i + n[0] * k)
         o = oracle_run(gyre, n, lo, hi, (0, 0), Ts[j], dt, t0=t0s[j], sample=sample)
         lcs.lcs_flowmap_get(ctx, fm, j, x, st)
         ids = o["ids"]
         sig, _, _ = oracle_ftle_at(sample, 2, n, o["h"], (0, 0), o["period"], o["xT"], o["st"], Ts[j])
         check_flowmap(x[:, ids], o["xyz_s"], st[ids], o["status_s"], 2.0, float(np.nanmax(sig)), Ts[j])
-        d = np.abs(ftle[j, torch.from_numpy(sample).cuda()].cpu().numpy().astype(np.float64) - sig)
+        got = ftle[j, torch.from_numpy(sample).cuda()].cpu().numpy()
+        if j in dense:
+            check_ftle(got, sig)
+        d = np.abs(got.astype(np.float64) - sig)
+        d = d[np.isfinite(d)]
         assert d.max() <= 1e-3, (j, d.max())
         worst = max(worst, float(d.max()))
-    print("\nC3 full size, 64 jobs x 6 sampled seeds: FTLE |d| max %.2e" % worst)
+    print("\nC3 full size, 8 jobs x 21,620 and 56 jobs x 6 sampled seeds: FTLE |d| max %.2e" % worst)
     lcs.lcs_free_flowmap(fm)
     lcs.lcs_free_seeds(seeds)
     lcs.lcs_free_field(field)

@@ -389,7 +389,8 @@ def test_full_size_pipe_rk45_sampled(ctx):
     """The benchmark's tetrahedral workload at full size -- the 2.36M-tet pipe, 64x64x512 seeds,
     DP5(4) rtol = atol = 1e-6, T = 1, the same launch options -- against the oracle at sampled seeds.
     The kernel shares one step size per warp of 32 consecutive seeds, so the oracle integrates, in
-    its 32-lane mode, every whole group holding a sampled seed or a member of its stencil."""
+    its 32-lane mode, every whole group holding one of 120 sampled seeds or a member of their
+    stencils: at least 1000 groups (about 34K tracers)."""
     mesh = inputs.pipe_frames(inputs.pipe_mesh(), nframes=50, period=1.0)
     n, lo, hi, T = (64, 64, 512), (-1.0, -1.0, 0.0), (1.0, 1.0, 10.0), 1.0
     field = lcs.lcs_load_field(ctx, tet_desc(mesh.xyz, mesh.tets, mesh.nbrs, mesh.times, lcs.F32, True,
@@ -416,10 +417,11 @@ def test_full_size_pipe_rk45_sampled(ctx):
     cand = np.flatnonzero(np.isfinite(ftle))
     ix, iy, iz = cand % 64, (cand // 64) % 64, cand // 4096
     cand = cand[(ix > 1) & (ix < 62) & (iy > 1) & (iy < 62) & (iz > 1) & (iz < 510)]
-    sample = np.sort(rng.choice(cand, 32, replace=False))
+    sample = np.sort(rng.choice(cand, 120, replace=False))
     # +-1 and +-2 along each axis: near the wall a one-sided difference needs the second neighbour
     stencil = np.concatenate([sample + s * o for o in (1, 64, 4096) for s in (-2, -1, 0, 1, 2)])
     groups = np.unique(stencil // 32)
+    assert len(groups) >= 1000
     ids = (groups[:, None] * 32 + np.arange(32)[None, :]).ravel()
     x0 = oracle.seed_grid(3, n, lo, hi)[:, ids]
     F = oracle.TetField(mesh.xyz, mesh.tets, mesh.nbrs, mesh.frames, mesh.times, True, mesh.period)
@@ -433,11 +435,14 @@ def test_full_size_pipe_rk45_sampled(ctx):
     # the oracle itself is off the converged flow by up to a few 1e-4 at rtol 1e-6; the kernel (FP32
     # error norms, so its own accept/reject sequence) is held to the oracle's accuracy against a
     # converged run (rtol 1e-10), as on the small pipe and the stenosis
-    xr, sr, _, _ = oracle.dp45(F, x0.astype(np.float64), 0.0, T, h0=0.01, rtol=1e-10, atol=1e-10, cells=oc)
-    ok = (st[ids] == so) & (so == oracle.OK) & (sr == oracle.OK)
-    assert ok.sum() > 1000
-    e_ora = np.abs(xo[:, ok] - xr[:, ok]).max(axis=0)
-    e_gpu = np.abs(x[:, ids][:, ok] - xr[:, ok]).max(axis=0)
+    # (the converged run, the costly part, on every eighth integrated group)
+    sub = (np.arange(len(ids)) // 32) % 8 == 0
+    xr, sr, _, _ = oracle.dp45(F, x0[:, sub].astype(np.float64), 0.0, T, h0=0.01, rtol=1e-10, atol=1e-10,
+                               cells=oc[sub])
+    ok = (st[ids][sub] == so[sub]) & (so[sub] == oracle.OK) & (sr == oracle.OK)
+    assert ok.sum() > 2000
+    e_ora = np.abs(xo[:, sub][:, ok] - xr[:, ok]).max(axis=0)
+    e_gpu = np.abs(x[:, ids][:, sub][:, ok] - xr[:, ok]).max(axis=0)
     assert np.median(e_gpu) <= 2 * np.median(e_ora) + 1e-6, (np.median(e_gpu), np.median(e_ora))
     assert e_gpu.max() <= 2 * e_ora.max() + 1e-5, (e_gpu.max(), e_ora.max())
     # FTLE at the samples from the oracle's own flow map of the integrated groups.  Weyl's inequality
@@ -455,7 +460,7 @@ def test_full_size_pipe_rk45_sampled(ctx):
     members = stencil.reshape(15, len(sample))
     agree = (st[members] == sT[members]).all(axis=0)
     use = agree & np.isfinite(sig)
-    assert use.sum() >= 24
+    assert use.sum() >= 90
     E = np.abs(x[:, members].astype(np.float64) - xT[:, members]).max(axis=(0, 1))
     bound = np.log1p(4 * np.sqrt(3) * E / min(h)) / T + 1e-6
     d = np.abs(ftle[sample].astype(np.float64) - sig)
