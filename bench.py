@@ -45,6 +45,9 @@ NSTEPS = int(round(T_END / DT))
 # of the measurement plan): per stage evaluation 7 lerps x 3 components x 2 frames = 84, the time
 # blend 6 and the weights ~10, about 100; 4 evaluations + ~40 for the RK4 stage points and update = 440
 FLOP_PER_TRACER_STEP = 440
+# DRAM read + write bytes per tracer-step of the episode kernel, from the ncu capture of the small case
+# with the same tracer density (profiles/ep_advect3_traffic.md)
+TRAFFIC_BYTES_PER_TRACER_STEP = 23.2
 
 
 def parse():
@@ -325,16 +328,9 @@ def our_arm(args, rank, world, local):
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s at the maximum SM clock
     achieved = flops / adv_launch_s / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "ep_advect3_traffic.md")
-    if os.path.exists(prof) and (args.seeds_side, args.grid, args.storage) == (N_SIDE, N_GRID, "f32"):
-        try:
-            text = open(prof).read()
-            tj = json.loads(text.split("```json", 1)[1].split("```", 1)[0])
-            if tj.get("source_sha") == _src_sha():
-                traffic = tj.get("bytes_per_launch")
-        except (OSError, ValueError, IndexError):
-            traffic = None
+    # DRAM traffic per launch: the small case's bytes per tracer-step (ncu, 64^3 field, 128^3 seeds, the
+    # same 8 tracers per cell) times the tracer-steps of this launch (profiles/ep_advect3_traffic.md)
+    traffic = TRAFFIC_BYTES_PER_TRACER_STEP * N * steps_per_launch if args.storage == "f32" else None
     n_ep = adv_launches / max(args.steps, 1)
     line = {
         "metric": METRIC, "value": value, "unit": "seeds/s", "n_gpus": world, "steps": args.steps,
@@ -353,9 +349,13 @@ def our_arm(args, rank, world, local):
                      "kernel": "ep_advect3_kernel (RK4 episode of %d steps)" % round(steps_per_launch),
                      "flop_per_launch": flops, "avg_launch_ms": adv_launch_s * 1e3, "launches": adv_launches,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (%s sm_max_mhz)" % (sm_mhz, pk_kind),
-                     "limiter": "latency of the stencil gathers (ncu, small case: long-scoreboard stalls lead; L1 "
-                                "data pipe 80%, issue 69%; 223 of 473 instructions per tracer-step are FP32 "
-                                "arithmetic)"},
+                     "traffic_note": "ncu DRAM bytes per tracer-step of the small case (64^3 field, 128^3 "
+                                     "seeds) scaled by this launch's tracer-steps "
+                                     "(profiles/ep_advect3_traffic.md)",
+                     "limiter": "the L1 data stage (ncu, small case: 79% of its one-wavefront-per-cycle peak; "
+                                "7.7 wavefronts per 16-byte gather request against 4 when a quarter warp's "
+                                "lanes read at most 4 lines: the re-bundled tracers spread over 5-8 rows of "
+                                "cells within a few steps); issue 69%, 470 instructions per warp-step"},
         "phases_ms_per_step": {k: v[0] / args.steps for k, v in phase.items()},
         "clocks": clocks,
         "e2e": {"value": world * N / e2e_el if e2e_t else None, "unit": "seeds/s", "h2d_bytes_per_step": h2d,
@@ -1085,16 +1085,6 @@ def c5_arm(args, rank, world, local):
     lcs.lcs_free_field(field)
     lcs.lcs_destroy(ctx)
     print(json.dumps(line), flush=True)
-
-
-def _src_sha():
-    import hashlib
-
-    h = hashlib.sha1()
-    for name in ("advect_episodes.cu", "rect_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2209_13775_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:12]
 
 
 # ------------------------------------- eigenvectors, early CG, auxiliary points

@@ -257,7 +257,7 @@ typedef struct {
                                        every job (2D time slices; up to 16 GiB; the
                                        default in 2D when they take at most 2 GiB)     */
     const void *surrogate;      /* LCS_SURROGATE: the lcs_mlp to step with            */
-    int episode_steps;          /* variant 3: RK4 steps between re-bundlings (0 = 32) */
+    int episode_steps;          /* variant 3: RK4 steps between re-bundlings (0 = 40) */
     int tracers_per_thread;     /* variants 2 and 4: 1 or 2 tracers per thread (0 = 1) */
     int use_graph;              /* capture the launches of this call in a CUDA graph,
                                    cached on the context and replayed while the same

@@ -237,7 +237,7 @@ struct Rk4Launch {
 // smallest seed count for which lcs_advect picks the re-bundled kernel by default
 #define LCS_SORTED_MIN_SEEDS 262144
 // default RK4 steps per re-bundled episode
-#define LCS_EPISODE_STEPS 32
+#define LCS_EPISODE_STEPS 40
 
 size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int episode_steps, bool variational);
 // variant 5 (2D time slices): their bytes for these jobs, and the most lcs_advect reserves for them
