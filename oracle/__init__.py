@@ -116,6 +116,15 @@ def lib() -> ctypes.CDLL:
             L.ora_tri_locate_walk.argtypes = [P, LL, P]
             L.ora_tri_locate_walk.restype = LL
             L.ora_set_threads.argtypes = [I]
+            L.ora_boundary_build.argtypes = [I, P, D]
+            L.ora_boundary_build.restype = P
+            L.ora_boundary_free.argtypes = [P]
+            L.ora_boundary_distance.argtypes = [P, P, D]
+            L.ora_boundary_distance.restype = D
+            L.ora_boundary_distance_brute.argtypes = [P, P]
+            L.ora_boundary_distance_brute.restype = D
+            L.ora_rk4_margin.argtypes = [I, P, I, LL, P, P, D, D, D, P, P, P, P, D, P]
+            L.ora_rk4_margin.restype = LL
             _lib = L
     return _lib
 
@@ -403,18 +412,47 @@ def velocity_grad(field, x, t, cell=0):
     return (None, None) if out else (u, J)
 
 
-def rk4(field, x0, t0, T, dt, cells=None):
-    """Fixed-step RK4 flow map (Sec. 2 Flow Map, Sec. 3.1).  x0 [dim][N] -> (xT, status, t_exit)."""
+def rk4(field, x0, t0, T, dt, cells=None, margin=None):
+    """Fixed-step RK4 flow map (Sec. 2 Flow Map, Sec. 3.1).  x0 [dim][N] -> (xT, status, t_exit).
+    margin = rmax (mesh fields): also each tracer's smallest distance from the mesh boundary over the
+    stage points it evaluated, capped at rmax -> (xT, status, t_exit, margin)."""
     x0 = np.ascontiguousarray(x0, dtype=np.float64)
     dim, n = x0.shape
     xT = np.empty_like(x0)
     st = np.empty(n, dtype=np.uint8)
     te = np.empty(n, dtype=np.float64)
     c = None if cells is None else np.ascontiguousarray(cells, dtype=np.int32)
-    lib().ora_rk4(field.kind, ctypes.byref(field.struct), dim, n, _p(x0),
-                  None if c is None else _p(c), float(t0), float(T), float(dt),
-                  _p(xT), _p(st), _p(te))
-    return xT, st, te
+    if margin is None:
+        lib().ora_rk4(field.kind, ctypes.byref(field.struct), dim, n, _p(x0),
+                      None if c is None else _p(c), float(t0), float(T), float(dt),
+                      _p(xT), _p(st), _p(te))
+        return xT, st, te
+    mg = np.empty(n)
+    bi = lib().ora_boundary_build(field.kind, ctypes.byref(field.struct), float(margin))
+    try:
+        lib().ora_rk4_margin(field.kind, ctypes.byref(field.struct), dim, n, _p(x0),
+                             None if c is None else _p(c), float(t0), float(T), float(dt),
+                             _p(xT), _p(st), _p(te), bi, float(margin), _p(mg))
+    finally:
+        lib().ora_boundary_free(bi)
+    return xT, st, te, mg
+
+
+def boundary_distance(field, pts, rmax=None):
+    """Distance of each point pts [dim][N] from the boundary of a mesh field: every boundary face
+    tested (rmax None), or through the grid index with the cap rmax."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    dim, n = pts.shape
+    bi = lib().ora_boundary_build(field.kind, ctypes.byref(field.struct), float(rmax or 1e-3))
+    out = np.empty(n)
+    try:
+        for i in range(n):
+            p = np.ascontiguousarray(pts[:, i])
+            out[i] = (lib().ora_boundary_distance_brute(bi, _p(p)) if rmax is None
+                      else lib().ora_boundary_distance(bi, _p(p), float(rmax)))
+    finally:
+        lib().ora_boundary_free(bi)
+    return out
 
 
 def dp45(field, x0, t0, T, h0=0.01, rtol=1e-6, atol=1e-6, max_steps=1000000, group=1,

@@ -898,9 +898,15 @@ static int eval_u(const vel_src *s, const double *x, double t, int *cell, double
     return ora_tet_velocity((const ora_tet_field *)s->field, x, t, cell, u);
 }
 
-long long ora_rk4(int field_kind, const void *field, int dim, long long n,
-                  const double *x0, const int *cells, double t0, double T, double dt,
-                  double *xT, unsigned char *status, double *t_exit)
+/* distance of x to the mesh boundary, capped at rmax (defined with the boundary index below) */
+static double boundary_dist(const ora_bindex *bi, const double *x, double rmax);
+
+/* RK4 as ora_rk4; with bi, margin[p] = the smallest distance (capped at rmax) from the mesh
+ * boundary of any stage point the tracer evaluated, the failing one included */
+static long long rk4_impl(int field_kind, const void *field, int dim, long long n,
+                          const double *x0, const int *cells, double t0, double T, double dt,
+                          double *xT, unsigned char *status, double *t_exit,
+                          const ora_bindex *bi, double rmax, double *margin)
 {
     vel_src src = {field_kind, field, dim};
     double adt = fabs(dt);
@@ -917,20 +923,25 @@ long long ora_rk4(int field_kind, const void *field, int dim, long long n,
             st = ORA_OUTSIDE;
             te = t0;
         }
+        double mg = rmax;
         for (long long s = 0; s < nsteps && st == ORA_OK; ++s) {
             double t = t0 + (double)s * h;
             double k1[3], k2[3], k3[3], k4[3], y[3];
+            if (bi) mg = fmin(mg, boundary_dist(bi, x, rmax));
             int out = eval_u(&src, x, t, &cell, k1);
             if (!out) {
                 for (int a = 0; a < dim; ++a) y[a] = x[a] + 0.5 * h * k1[a];
+                if (bi) mg = fmin(mg, boundary_dist(bi, y, rmax));
                 out = eval_u(&src, y, t + 0.5 * h, &cell, k2);
             }
             if (!out) {
                 for (int a = 0; a < dim; ++a) y[a] = x[a] + 0.5 * h * k2[a];
+                if (bi) mg = fmin(mg, boundary_dist(bi, y, rmax));
                 out = eval_u(&src, y, t + 0.5 * h, &cell, k3);
             }
             if (!out) {
                 for (int a = 0; a < dim; ++a) y[a] = x[a] + h * k3[a];
+                if (bi) mg = fmin(mg, boundary_dist(bi, y, rmax));
                 out = eval_u(&src, y, t + h, &cell, k4);
             }
             if (out) { /* a stage left the mesh: freeze at the start of the step */
@@ -948,8 +959,259 @@ long long ora_rk4(int field_kind, const void *field, int dim, long long n,
         for (int a = 0; a < dim; ++a) xT[a * n + p] = x[a];
         status[p] = st;
         t_exit[p] = te;
+        if (margin) margin[p] = mg;
     }
     return nsteps;
+}
+
+long long ora_rk4(int field_kind, const void *field, int dim, long long n,
+                  const double *x0, const int *cells, double t0, double T, double dt,
+                  double *xT, unsigned char *status, double *t_exit)
+{
+    return rk4_impl(field_kind, field, dim, n, x0, cells, t0, T, dt, xT, status, t_exit, NULL, 0.0, NULL);
+}
+
+long long ora_rk4_margin(int field_kind, const void *field, int dim, long long n,
+                         const double *x0, const int *cells, double t0, double T, double dt,
+                         double *xT, unsigned char *status, double *t_exit,
+                         const ora_bindex *bi, double rmax, double *margin)
+{
+    return rk4_impl(field_kind, field, dim, n, x0, cells, t0, T, dt, xT, status, t_exit, bi, rmax, margin);
+}
+
+/* ====================================================================
+ * Distance to the boundary of a mesh: the faces of tets (edges of
+ * triangles) with no neighbour across them.  The tests use it to tell the
+ * tracers whose exit decision is close: a stage point within rounding of
+ * the boundary can be inside in one precision and outside in another, as
+ * Sec. 3.1's cell search decides by the sign of a barycentric coordinate.
+ * ==================================================================== */
+
+struct ora_bindex {
+    int dim;
+    long long nfaces;
+    double *fv;          /* [nfaces][dim][dim]: the face's dim vertices            */
+    double lo[3], cell;  /* grid over the faces' bounding box, grown by rmax      */
+    long long g[3];
+    long long *start;    /* [cells + 1] CSR of the faces whose box + rmax meets   */
+    long long *items;    /*   the grid cell                                       */
+};
+
+static double dot_n(const double *a, const double *b, int dim)
+{
+    double s = 0.0;
+    for (int i = 0; i < dim; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* distance from p to the segment [a, b] */
+static double seg_dist(const double *p, const double *a, const double *b, int dim)
+{
+    double e[3], w[3];
+    for (int i = 0; i < dim; ++i) {
+        e[i] = b[i] - a[i];
+        w[i] = p[i] - a[i];
+    }
+    double ee = dot_n(e, e, dim), t = ee > 0.0 ? dot_n(w, e, dim) / ee : 0.0;
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    double d2 = 0.0;
+    for (int i = 0; i < dim; ++i) {
+        double r = w[i] - t * e[i];
+        d2 += r * r;
+    }
+    return sqrt(d2);
+}
+
+static void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* distance from p to the triangle (a, b, c) in 3D: to its plane when p projects inside it (the
+ * normal component drops out of each edge's side test), else to the nearest edge */
+static double tri_dist(const double *p, const double *a, const double *b, const double *c)
+{
+    double e0[3], e1[3], n[3];
+    for (int i = 0; i < 3; ++i) {
+        e0[i] = b[i] - a[i];
+        e1[i] = c[i] - a[i];
+    }
+    cross3(e0, e1, n);
+    double nn = dot_n(n, n, 3);
+    if (nn > 0.0) {
+        const double *v[3] = {a, b, c};
+        int inside = 1;
+        for (int k = 0; k < 3; ++k) {
+            const double *u = v[k], *w = v[(k + 1) % 3];
+            double e[3], q[3], x[3];
+            for (int i = 0; i < 3; ++i) {
+                e[i] = w[i] - u[i];
+                q[i] = p[i] - u[i];
+            }
+            cross3(e, q, x);
+            if (dot_n(x, n, 3) < 0.0) inside = 0;
+        }
+        if (inside) {
+            double w[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+            return fabs(dot_n(w, n, 3)) / sqrt(nn);
+        }
+    }
+    double d = seg_dist(p, a, b, 3);
+    d = fmin(d, seg_dist(p, b, c, 3));
+    return fmin(d, seg_dist(p, c, a, 3));
+}
+
+static double face_dist(const ora_bindex *bi, long long f, const double *p)
+{
+    const double *v = bi->fv + (size_t)f * bi->dim * bi->dim;
+    if (bi->dim == 2) return seg_dist(p, v, v + 2, 2);
+    return tri_dist(p, v, v + 3, v + 6);
+}
+
+double ora_boundary_distance_brute(const ora_bindex *bi, const double *p)
+{
+    double d = INFINITY;
+    for (long long f = 0; f < bi->nfaces; ++f) d = fmin(d, face_dist(bi, f, p));
+    return d;
+}
+
+static long long grid_index(const ora_bindex *bi, const double *p, int clampit)
+{
+    long long idx = 0, mul = 1;
+    for (int d = 0; d < bi->dim; ++d) {
+        long long c = (long long)floor((p[d] - bi->lo[d]) / bi->cell);
+        if (c < 0 || c >= bi->g[d]) {
+            if (!clampit) return -1;
+            c = c < 0 ? 0 : bi->g[d] - 1;
+        }
+        idx += c * mul;
+        mul *= bi->g[d];
+    }
+    return idx;
+}
+
+static double boundary_dist(const ora_bindex *bi, const double *x, double rmax)
+{
+    long long c = grid_index(bi, x, 0);
+    if (c < 0) return rmax;   /* outside the grid: farther than rmax from every face */
+    double d = rmax;
+    for (long long q = bi->start[c]; q < bi->start[c + 1]; ++q) d = fmin(d, face_dist(bi, bi->items[q], x));
+    return d;
+}
+
+double ora_boundary_distance(const ora_bindex *bi, const double *p, double rmax)
+{
+    return boundary_dist(bi, p, rmax);
+}
+
+/* index the boundary faces of a tet (kind 2) or triangle (kind 3) field for distances up to rmax */
+ora_bindex *ora_boundary_build(int kind, const void *field, double rmax)
+{
+    const int dim = kind == 3 ? 2 : 3, nv = dim + 1;
+    long long ncells;
+    const int *cells, *nbrs;
+    const float *pts;
+    if (kind == 3) {
+        const ora_tri_field *f = (const ora_tri_field *)field;
+        ncells = f->ncells;
+        cells = f->tris;
+        nbrs = f->nbrs;
+        pts = f->xy;
+    } else {
+        const ora_tet_field *f = (const ora_tet_field *)field;
+        ncells = f->ncells;
+        cells = f->tets;
+        nbrs = f->nbrs;
+        pts = f->xyz;
+    }
+    ora_bindex *bi = (ora_bindex *)calloc(1, sizeof(ora_bindex));
+    bi->dim = dim;
+    for (long long t = 0; t < ncells; ++t)
+        for (int v = 0; v < nv; ++v) bi->nfaces += nbrs[t * nv + v] < 0;
+    bi->fv = (double *)malloc(sizeof(double) * (size_t)(bi->nfaces ? bi->nfaces : 1) * dim * dim);
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    long long f = 0;
+    for (long long t = 0; t < ncells; ++t)
+        for (int v = 0; v < nv; ++v) {
+            if (nbrs[t * nv + v] >= 0) continue;
+            int k = 0;
+            for (int w = 0; w < nv; ++w) {   /* the face opposite vertex v */
+                if (w == v) continue;
+                const float *q = pts + (size_t)cells[t * nv + w] * dim;
+                for (int d = 0; d < dim; ++d) {
+                    double x = (double)q[d];
+                    bi->fv[((size_t)f * dim + k) * dim + d] = x;
+                    lo[d] = fmin(lo[d], x);
+                    hi[d] = fmax(hi[d], x);
+                }
+                ++k;
+            }
+            ++f;
+        }
+    /* about one face per grid cell, never finer than rmax */
+    double vol = 1.0;
+    for (int d = 0; d < dim; ++d) {
+        lo[d] -= rmax;
+        hi[d] += rmax;
+        vol *= hi[d] - lo[d];
+    }
+    double cell = pow(vol / (double)(bi->nfaces ? bi->nfaces : 1), 1.0 / dim);
+    bi->cell = fmax(cell, rmax);
+    long long ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        bi->lo[d] = d < dim ? lo[d] : 0.0;
+        bi->g[d] = d < dim ? (long long)ceil((hi[d] - lo[d]) / bi->cell) : 1;
+        if (bi->g[d] < 1) bi->g[d] = 1;
+        ncell *= bi->g[d];
+    }
+    bi->start = (long long *)calloc((size_t)ncell + 1, sizeof(long long));
+    /* two passes: count, then fill, the cells each face's box grown by rmax meets */
+    for (int pass = 0; pass < 2; ++pass) {
+        long long *cur = NULL;
+        if (pass == 1) {
+            for (long long c = 0; c < ncell; ++c) bi->start[c + 1] += bi->start[c];
+            bi->items = (long long *)malloc(sizeof(long long) * (size_t)(bi->start[ncell] ? bi->start[ncell] : 1));
+            cur = (long long *)malloc(sizeof(long long) * (size_t)ncell);
+            memcpy(cur, bi->start, sizeof(long long) * (size_t)ncell);
+        }
+        for (long long q = 0; q < bi->nfaces; ++q) {
+            long long c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0};
+            for (int d = 0; d < dim; ++d) {
+                double a = INFINITY, b = -INFINITY;
+                for (int k = 0; k < dim; ++k) {
+                    double x = bi->fv[((size_t)q * dim + k) * dim + d];
+                    a = fmin(a, x);
+                    b = fmax(b, x);
+                }
+                c0[d] = (long long)floor((a - rmax - bi->lo[d]) / bi->cell);
+                c1[d] = (long long)floor((b + rmax - bi->lo[d]) / bi->cell);
+                if (c0[d] < 0) c0[d] = 0;
+                if (c1[d] >= bi->g[d]) c1[d] = bi->g[d] - 1;
+            }
+            for (long long k = c0[2]; k <= c1[2]; ++k)
+                for (long long j = c0[1]; j <= c1[1]; ++j)
+                    for (long long i = c0[0]; i <= c1[0]; ++i) {
+                        long long c = i + bi->g[0] * (j + bi->g[1] * k);
+                        if (pass == 0)
+                            bi->start[c + 1] += 1;
+                        else
+                            bi->items[cur[c]++] = q;
+                    }
+        }
+        free(cur);
+    }
+    return bi;
+}
+
+void ora_boundary_free(ora_bindex *bi)
+{
+    if (!bi) return;
+    free(bi->fv);
+    free(bi->start);
+    free(bi->items);
+    free(bi);
 }
 
 /* RK4 on Eq. 2 together with its variational equation dM/dt = J(x, t) M, M(t0) = I, on a

@@ -167,6 +167,28 @@ long long ora_rk4(int field_kind, const void *field, int dim, long long n,
                   const double *x0, const int *cells, double t0, double T, double dt,
                   double *xT, unsigned char *status, double *t_exit);
 
+/* Distance to the boundary of a tet (field_kind 2) or triangle (3) mesh: the
+ * faces (edges) with no neighbour across them.  ora_boundary_build indexes
+ * them on a grid for queries up to rmax; ora_boundary_distance returns the
+ * exact distance from p when it is below rmax, else rmax;
+ * ora_boundary_distance_brute tests every face (no cap).  The distance to a
+ * face is the distance to its plane (line) where p projects inside it, else
+ * to its nearest edge (end point).                                          */
+typedef struct ora_bindex ora_bindex;
+ora_bindex *ora_boundary_build(int field_kind, const void *field, double rmax);
+void ora_boundary_free(ora_bindex *bi);
+double ora_boundary_distance(const ora_bindex *bi, const double *p, double rmax);
+double ora_boundary_distance_brute(const ora_bindex *bi, const double *p);
+
+/* ora_rk4 that also returns margin[n]: per tracer, the smallest distance to
+ * the mesh boundary (capped at rmax) of any stage point it evaluated, the one
+ * that left included.  Tracers whose margin exceeds the difference between
+ * two computations of the same trajectory reach the same exit decisions.    */
+long long ora_rk4_margin(int field_kind, const void *field, int dim, long long n,
+                         const double *x0, const int *cells, double t0, double T, double dt,
+                         double *xT, unsigned char *status, double *t_exit,
+                         const ora_bindex *bi, double rmax, double *margin);
+
 /* Dormand-Prince 5(4) with FSAL (the RK45 of the adaptive path).
  *   err = max_i |e_i| / (atol + rtol * max(|x_i|, |xnew_i|)), accept iff err <= 1,
  *   h_new = h * min(5, max(0.2, 0.9 * err^(-1/5)))   (factor 5 when err == 0).

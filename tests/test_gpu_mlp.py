@@ -250,3 +250,78 @@ def test_training_learns_the_gyre_step(ctx, gyre):
     assert rel < 0.1, (rel, hist)
     lcs.lcs_mlp_free(m)
     lcs.lcs_free_field(field)
+
+
+def test_surrogate_gain_over_plain_rk4(ctx, gyre):
+    """What the trained network gains over the integrator it stands in for, measured: a reduced C5
+    workload (2048 x 1024 seeds of the double gyre, t0 = 0, T = 8 = 16 sub-intervals of tau = 0.5)
+    integrated by plain RK4 (dt 0.05) and by the surrogate -- gated (audit threshold 1e-3, RK4 fallback),
+    ungated (the network alone) and gate 0 (every sub-interval by RK4, through the surrogate path) --
+    each timed with CUDA events on the same GPU and its FTLE compared with the FP64 oracle at every
+    97th seed.  The related-work idea behind it is a local flow-map approximation (Sec. 4).
+
+    Stated results: plain RK4 meets the fixed-step tolerances; the gated surrogate's FTLE is within a
+    median of 0.5 of the oracle's (reported, not a parity bound), gate 0 is plain RK4 bit for bit.  On
+    this field the network gains nothing: one evaluation (100,864 FLOP on the tensor cores) costs more
+    than the 10 bilinear RK4 steps it replaces, so the gain (plain time / surrogate time) is below 1."""
+    from gpu_util import check_ftle, oracle_ftle_at, oracle_run
+
+    field = gyre_field(ctx, gyre)
+    m = mlp_handle(ctx, inputs.mlp_init(seed=93))
+    samples = torch.from_numpy(inputs.surrogate_samples(1 << 22, seed=94)).cuda()
+    lcs.lcs_surrogate_train(ctx, field, m, lcs.train_desc(batch=65536, epochs=4, lr=2e-3, lr_min=1e-5), samples)
+    n, lo, hi, T, dt = (2048, 1024), (0.0, 0.0), (2.0, 1.0), 8.0, 0.05
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n, lo, hi))
+    N = lcs.lcs_seeds_count(seeds)
+    fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
+    stream = torch.cuda.current_stream()
+    runs = {"plain RK4": lcs.advect_opts(lcs.RK4, t0=0.0, T=T, dt=dt),
+            "surrogate, gated": lcs.advect_opts(lcs.SURROGATE, t0=0.0, T=T, dt=dt, surrogate=m, gate_tol=1e-3),
+            "surrogate, network alone": lcs.advect_opts(lcs.SURROGATE, t0=0.0, T=T, dt=dt, surrogate=m,
+                                                        gate_tol=float("inf")),
+            "surrogate, gate 0": lcs.advect_opts(lcs.SURROGATE, t0=0.0, T=T, dt=dt, surrogate=m, gate_tol=0.0)}
+    res = {}
+    try:
+        for name, o in runs.items():
+            lcs.lcs_advect(ctx, field, seeds, o, fm)          # warm-up
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(3):
+                lcs.lcs_advect(ctx, field, seeds, o, fm)
+            b.record(stream)
+            lcs.lcs_synchronize(ctx)
+            x = np.empty((2, N), np.float32)
+            f = np.empty(N, np.float32)
+            lcs.lcs_flowmap_get(ctx, fm, 0, x)
+            lcs.lcs_ftle(ctx, fm, 0, f)
+            fb = None
+            if o.method == lcs.SURROGATE:
+                steps = np.empty(N, np.int32)
+                lcs.lcs_flowmap_steps(ctx, fm, 0, steps)
+                fb = float(steps.mean()) / 16
+            lcs.lcs_synchronize(ctx)
+            res[name] = dict(ms=a.elapsed_time(b) / 3, x=x, ftle=f, fallback=fb)
+    finally:
+        lcs.lcs_free_flowmap(fm)
+        lcs.lcs_free_seeds(seeds)
+        lcs.lcs_mlp_free(m)
+        lcs.lcs_free_field(field)
+    sample = np.arange(0, N, 97)
+    o = oracle_run(gyre, n, lo, hi, (0, 0), T, dt, sample=sample)
+    sig, _, _ = oracle_ftle_at(sample, 2, n, o["h"], (0, 0), o["period"], o["xT"], o["st"], T)
+    plain = res["plain RK4"]
+    print()
+    for name, r in res.items():
+        d = np.abs(r["ftle"][sample].astype(np.float64) - sig)
+        d = d[np.isfinite(d)]
+        r["err"] = (float(np.median(d)), float(np.quantile(d, 0.999)), float(d.max()))
+        print("%-26s %7.2f ms  gain %.2fx  FTLE |err| vs oracle median %.2e p99.9 %.2e max %.2e%s"
+              % (name, r["ms"], plain["ms"] / r["ms"], *r["err"],
+                 "" if r["fallback"] is None else "  sub-intervals by RK4 %.1f%%" % (100 * r["fallback"])))
+    check_ftle(plain["ftle"][sample], sig)
+    np.testing.assert_array_equal(res["surrogate, gate 0"]["x"], plain["x"])
+    assert res["surrogate, gate 0"]["fallback"] == 1.0
+    assert res["surrogate, network alone"]["fallback"] == 0.0
+    g = res["surrogate, gated"]
+    assert np.isfinite(g["ftle"]).all() and g["err"][0] <= 0.5, g["err"]
