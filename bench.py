@@ -742,6 +742,7 @@ def c4_arm(args, rank, world, local):
     alg_bytes = float(tracer_steps) * C4_STAGES_PER_STEP * C4_BYTES_PER_STAGE
     achieved = alg_bytes / launch_s / 1e9
     hbm = pk.get("hbm_gbs", 6800.0)
+    l2, l2_basis = l2_peak(local)
     line = {
         "metric": METRIC, "value": N * args.steps / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -754,12 +755,13 @@ def c4_arm(args, rank, world, local):
                          % ((mesh.tets.shape[0] * (16 + 16 + 48) + mesh.xyz.shape[0] * 16
                              + 50 * mesh.xyz.shape[0] * 32) / 1e6)},
         "tracer_steps_per_s": tracer_steps * args.steps / el,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+        "roofline": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
                      "traffic": None, "kernel": "dp45_kernel<TetEval<F32>>",
                      "bytes_per_launch": alg_bytes, "avg_launch_ms": launch_s * 1e3, "launches": adv_n,
-                     "peak_basis": "hbm_gbs (%s)" % pk_kind,
-                     "basis": "%d B per stage x 6 stages per accepted step x accepted tracer-steps"
-                              % C4_BYTES_PER_STAGE},
+                     "peak_basis": l2_basis,
+                     "basis": "%d B per stage x 6 stages per accepted step x accepted tracer-steps; the mesh "
+                              "gathers stay in L1/L2 (DRAM reads under 1 GB per launch)" % C4_BYTES_PER_STAGE,
+                     "frac_of_hbm_copy": achieved / hbm},
         "phases_ms_per_step": {"advect": adv_ms / args.steps, "cg_ftle": cg_ms / args.steps},
         "clocks": clk.summary(),
         # per step: the per-job values kernel, the DP5(4) kernel, FD/CG/FTLE
@@ -796,6 +798,13 @@ TRI_BYTES_PER_STAGE = 16 + 8 + 16 + 48
 # FP32 flops of one RK4 step on triangles: per stage the barycentric coordinates (10), the P1 and time
 # blend of 3 vertices x 2 components (30 + 1), the stage point (4, stages 2-4); the update (12 + 2)
 TRI_FLOP_PER_STEP = 4 * (10 + 31) + 3 * 4 + 14
+
+
+def l2_peak(device):
+    """Read rate of an L2-resident buffer on this GPU (bench_peaks.cu, median of 3), the denominator of
+    the gather-bound mesh kernels."""
+    runs = [probe_peaks(device)["l2_read_gbs"] for _ in range(3)]
+    return float(np.median(runs)), "bench_peaks.cu: 16-byte loads re-reading a 32 MB buffer, median of 3"
 
 
 def alu_peak():
@@ -894,6 +903,8 @@ def tri_arm(args, rank, world, local):
     flop = float(tracer_steps) * TRI_FLOP_PER_STEP
     achieved = flop / launch_s / 1e12
     fp32_peak, peak_basis = alu_peak()
+    l2, l2_basis = l2_peak(local)
+    gbs = alg_bytes / launch_s / 1e9
     line = {
         "metric": METRIC, "value": N * args.steps / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -904,14 +915,15 @@ def tri_arm(args, rank, world, local):
                    "seed_location_ms": round(t_seed * 1e3, 1), "status": counts,
                    "l2": "no flush: each step writes %.0f MB of outputs (C + FTLE) > 129 MB L2" % (N * 28 / 1e6)},
         "tracer_steps_per_s": tracer_steps * args.steps / el,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None, "kernel": "rk4_tri_kernel<%s>" % args.storage,
-                     "flop_per_launch": flop, "avg_launch_ms": launch_s * 1e3, "launches": adv_n,
-                     "peak_basis": peak_basis,
-                     "basis": "%d FP32 flops per tracer-step x tracer-steps taken" % TRI_FLOP_PER_STEP,
-                     "gathers": {"bytes_per_launch": alg_bytes, "gbs": alg_bytes / launch_s / 1e9,
-                                 "basis": "%d B per stage x 4 stages (served mostly by L1/L2)"
-                                          % TRI_BYTES_PER_STAGE}},
+        "roofline": {"bound": "l2", "achieved": gbs, "peak": l2, "unit": "GB/s", "frac": gbs / l2,
+                     "traffic": None, "kernel": "rk4_tri_kernel<%s>" % args.storage,
+                     "bytes_per_launch": alg_bytes, "avg_launch_ms": launch_s * 1e3, "launches": adv_n,
+                     "peak_basis": l2_basis,
+                     "basis": "%d B of gathers per stage x 4 stages x tracer-steps taken (map, vertex 0, "
+                              "connectivity, three frame pairs), served by L1/L2" % TRI_BYTES_PER_STAGE,
+                     "alu": {"achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                             "peak_basis": peak_basis,
+                             "basis": "%d FP32 flops per tracer-step" % TRI_FLOP_PER_STEP}},
         "phases_ms_per_step": {"advect": adv_ms / args.steps, "cg_ftle": cg_ms / args.steps},
         "clocks": clk.summary(),
         # per step: the schedule kernel, the RK4 kernel, FD/CG/FTLE
