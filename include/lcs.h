@@ -438,14 +438,18 @@ lcs_status lcs_gemm_bf16(lcs_ctx *ctx, long long M, int N, long long K, const vo
  * (-3F(p) + 4F(p+e_b) - F(p+2e_b)) / 2h_b or backward (3F(p) - 4F(p-e_b) +
  * F(p-2e_b)) / 2h_b, using only lattice points with status OK; none -> NaN.
  * Output packed per seed: 2D (C00, C01, C11), 3D (C00, C01, C02, C11, C12,
- * C22), FP64.  job = -1 writes every job, job-major.                        */
+ * C22), FP64.  job = -1 writes every job, job-major.
+ * Errors: LCS_EINVAL (a lattice with fewer than 3 seeds along an axis, where
+ * no difference rule applies; auxiliary-point and variational flow maps are
+ * exempt), LCS_ECUDA.                                                       */
 lcs_status lcs_cauchy_green(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double *C,
                             int on_device);
 
 /* FTLE sigma = ln(sqrt(lambda_max(C))) / |T| (Sec. 1: the FTLE is derived from
  * the largest eigenvalue of C) as FP32 [N], NaN where C is undefined;
  * optionally lambda_max [N] FP64 and C (as lcs_cauchy_green) from the same
- * pass.  lambda_max and C may be NULL.  job = -1 writes every job.         */
+ * pass.  lambda_max and C may be NULL.  job = -1 writes every job.
+ * Errors: as lcs_cauchy_green.                                              */
 lcs_status lcs_ftle(lcs_ctx *ctx, const lcs_flowmap *fm, int job, float *ftle, double *lambda_max,
                     double *C, int on_device);
 

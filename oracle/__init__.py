@@ -380,7 +380,9 @@ def seed_grid(dim, n, lo, hi, endpoint=(1, 1, 1)):
 
 
 def lattice_spacing(dim, n, lo, hi, endpoint=(1, 1, 1)):
-    return np.array([(hi[a] - lo[a]) / ((n[a] - 1) if endpoint[a] else n[a]) for a in range(dim)])
+    """Lattice step per axis; an axis of one node has no step (1.0 stands in: no difference uses it)."""
+    return np.array([(hi[a] - lo[a]) / ((n[a] - 1) if endpoint[a] else n[a]) if (n[a] > 1 or not endpoint[a])
+                     else 1.0 for a in range(dim)])
 
 
 def rk4_var(field, x0, t0, T, dt, cells=None):
