@@ -163,6 +163,8 @@ __global__ void __launch_bounds__(256) rk4_mesh_var_kernel(MD T, Rk4Args A, cons
         st = LCS_TRACER_OUTSIDE;
         te = A.job_t0[job];
     }
+    TriCache tc;   // triangles only, and only its map (the tet branch never touches it)
+    tri_cache_init(tc);
     const SchedEntry *sc = A.sched + (size_t)job * A.nsteps_max * 3;
     const int ns = A.job_nsteps[job];
     const float h = A.job_h[job], hh = 0.5f * h, h6 = h * (1.0f / 6.0f);
@@ -186,9 +188,9 @@ __global__ void __launch_bounds__(256) rk4_mesh_var_kernel(MD T, Rk4Args A, cons
                 if (r != TET_INSIDE) break;
                 tet_interp_grad<ST>(T, cell, lam, fp, es.a, k[q], J);
             } else {
-                r = tri_locate(T, y, &cell, lam);
+                r = tri_locate_cached(T, y, &cell, lam, tc);
                 if (r != TET_INSIDE) break;
-                tri_interp_grad<ST>(T, cell, lam, fp, es.a, k[q], J);
+                tri_interp_grad<ST>(T, cell, tc.m, lam, fp, es.a, k[q], J);
             }
 #pragma unroll
             for (int a = 0; a < DIM; ++a)
@@ -251,12 +253,18 @@ __device__ __forceinline__ void bracket_f32(const float *times, int nf, int tp, 
 
 // ------------------------------------------------------------ field evaluators
 
+// per-thread state an evaluator keeps between its calls (none, or the triangle register cache)
+struct NoEvalState {};
+__device__ __forceinline__ void eval_state_init(NoEvalState &) {}
+__device__ __forceinline__ void eval_state_init(TriCache &cc) { tri_cache_init(cc); }
+
 // velocity at (x, t) on a tet mesh; walks from *cell.  Returns TET_INSIDE / OUTSIDE / WALKFAIL
 template <int ST>
 struct TetEval {
     static constexpr int DIM = 3;
+    using State = NoEvalState;
     TetDev T;
-    __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u) const
+    __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u, State &) const
     {
         float lam[4];
         int r = tet_locate(T, x, cell, lam);
@@ -265,17 +273,17 @@ struct TetEval {
     }
 };
 
-// velocity at (x, t) on a 3D rectilinear field of interval pairs (queries clamped into the box)
 // velocity at (x, t) on a triangle mesh; walks from *cell (the bin lists settle boundary edges)
 template <int ST>
 struct TriEval {
     static constexpr int DIM = 2;
+    using State = TriCache;   // the seven stage points of a step mostly share a cell and an interval
     TriDev T;
-    __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u) const
+    __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u, State &cc) const
     {
         float lam[3];
-        int r = tri_locate(T, x, cell, lam);
-        if (r == TET_INSIDE) tri_interp<ST>(T, *cell, lam, T.pairs + (size_t)k * T.fstride, a, u);
+        int r = tri_locate_cached(T, x, cell, lam, cc);
+        if (r == TET_INSIDE) tri_interp_cached<ST>(T, *cell, k, lam, T.pairs + (size_t)k * T.fstride, a, u, cc);
         return r;
     }
 };
@@ -284,10 +292,11 @@ struct TriEval {
 template <int ST>
 struct Rect2Eval {
     static constexpr int DIM = 2;
+    using State = NoEvalState;
     RectParams P;
     const char *frames;
     size_t fstride;
-    __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u) const
+    __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u, State &) const
     {
         Stencil<2> S;
         make_stencil<2>(P, x, S);
@@ -296,13 +305,15 @@ struct Rect2Eval {
     }
 };
 
+// velocity at (x, t) on a 3D rectilinear field of interval pairs (queries clamped into the box)
 template <int ST>
 struct Rect3Eval {
     static constexpr int DIM = 3;
+    using State = NoEvalState;
     RectParams P;
     const char *pairs;
     size_t fstride;
-    __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u) const
+    __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u, State &) const
     {
         Stencil<3> S;
         make_stencil<3>(P, x, S);
@@ -334,12 +345,12 @@ __constant__ float DPE[7] = {35.0f / 384.0f - 5179.0f / 57600.0f,
 
 template <class EV>
 __device__ __forceinline__ int dp_eval(const EV &E, const Dp45Args &A, const float *times, const float *x, float t,
-                                       int *cell, float *u)
+                                       int *cell, float *u, typename EV::State &cs)
 {
     int k;
     float a;
     bracket_f32(times, A.nf, A.tp, A.period, t, k, a);
-    return E.eval(x, k, a, cell, u);
+    return E.eval(x, k, a, cell, u, cs);
 }
 
 template <class EV>
@@ -358,6 +369,8 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
     for (int q = 0; q < D; ++q) x[q] = k1[q] = 0.0f;
     int cell = 0, steps = 0;
     bool have_k1 = false;
+    typename EV::State cs;
+    eval_state_init(cs);
     unsigned char st = active ? LCS_TRACER_OK : LCS_TRACER_OUTSIDE;
     const float t0 = (float)A.job_t0[job];
     const float tend = (float)(A.job_t0[job] + A.job_T[job]);
@@ -395,7 +408,7 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
         int r = TET_INSIDE;
         if (live) {
             if (!have_k1) {
-                r = dp_eval(E, A, s_times, x, t, &cell, k1);
+                r = dp_eval(E, A, s_times, x, t, &cell, k1, cs);
                 if (r == TET_INSIDE) have_k1 = true;
             }
 #pragma unroll
@@ -412,7 +425,7 @@ __global__ void __launch_bounds__(256, 4) dp45_kernel(EV E, Dp45Args A, RectPara
                         if (j < s) acc = fmaf(DPA[s][j], kk[j][q], acc);
                     y[q] = fmaf(hs, acc, x[q]);
                 }
-                r = dp_eval(E, A, s_times, y, fmaf(DPC[s], hs, t), &cell, kk[s]);
+                r = dp_eval(E, A, s_times, y, fmaf(DPC[s], hs, t), &cell, kk[s], cs);
             }
             if (r == TET_INSIDE) {
 #pragma unroll

@@ -8,7 +8,8 @@
 //    triangles listed for the point's bin, so meshes need not be convex (a channel with a
 //    constriction is not); a walk past its step limit reports WALKFAIL.
 //  * tri_interp: P1 interpolation of the frame pair k, blended in time at the vertices.
-//  * TriCache: the RK4 kernel's registers holding the last cell's map and vertex pairs.
+//  * TriCache: a tracer's registers holding the last cell's map and vertex pairs (RK4 and
+//    DP5(4) use both; the variational kernel only the map).
 //  * orient2d_sign: exact orientation of three FP32 points (FP64 filter, exact expansion
 //    sum of the six two-factor products when the filter cannot decide).
 #pragma once
@@ -96,7 +97,7 @@ __device__ __forceinline__ int tri_locate(const TriDev &T, const float *x, int *
     return TET_WALKFAIL;
 }
 
-// The RK4 kernel's register cache: the map of the cell its last walk ended in, and the vertex
+// A tracer's register cache: the map of the cell its last walk ended in, and the vertex
 // pairs of the cell and frame interval it last interpolated.  Consecutive stage points of a
 // tracer mostly share a cell and an interval (steps are short against cells and frame gaps), so
 // a walk that starts in the held cell and stays there, and an interpolation in the held cell
@@ -118,8 +119,8 @@ __device__ __forceinline__ void tri_cache_init(TriCache &cc)
 }
 
 // tri_locate with the map of each visited cell taken from, or put into, the cache.  The two
-// walks are kept apart: routing tri_locate through an empty cache costs the DP5(4) and
-// variational triangle kernels registers (56 -> 64 per thread) for no reuse.
+// walks are kept apart: the uncached one serves the seed location and the surrogate gate,
+// which make one walk per tracer and would gain nothing from the cache's registers.
 __device__ __forceinline__ int tri_locate_cached(const TriDev &T, const float *x, int *cell, float *lam, TriCache &cc)
 {
     int c = *cell;
@@ -238,30 +239,34 @@ __device__ __forceinline__ void tri_interp_cached(const TriDev &T, int c, int k,
     tri_blend(lam, cc.ua, cc.ub, a, u);
 }
 
-// tri_interp's u plus the Jacobian of the P1 interpolant, constant in the triangle
+// tri_interp's u plus the Jacobian of the P1 interpolant, constant in the triangle, with c's map m
+// passed in (tri_locate_cached leaves it in TriCache::m).  The vertex pairs are loaded, not cached:
+// in the variational kernel, whose 2x2 M, its four stage slopes and J already hold many registers,
+// keeping the pairs too took it from 62 to 80 registers a thread and made it slower than reloading.
 template <int ST>
-__device__ __forceinline__ void tri_interp_grad(const TriDev &T, int c, const float *lam, const char *fp, float a,
-                                                float *u, float (*J)[2])
+__device__ __forceinline__ void tri_interp_grad(const TriDev &T, int c, const float4 &m, const float *lam,
+                                                const char *fp, float a, float *u, float (*J)[2])
 {
     const int4 t = __ldg(T.tris + c);
-    const int vs[3] = {t.x, t.y, t.z};
-    const float4 m = __ldg(T.tmap + c);
+    float ua[3][2], ub[3][2];
+    TriPair<ST>::ld(fp, t.x, ua[0], ub[0]);
+    TriPair<ST>::ld(fp, t.y, ua[1], ub[1]);
+    TriPair<ST>::ld(fp, t.z, ua[2], ub[2]);
     const float gr[3][2] = {{-(m.x + m.z), -(m.y + m.w)}, {m.x, m.y}, {m.z, m.w}};
     const float g = 1.0f - a;
-    float acc[2] = {0.0f, 0.0f}, va[2], vb[2];
+    float acc[2] = {0.0f, 0.0f};
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int d = 0; d < 2; ++d) J[q][d] = 0.0f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        TriPair<ST>::ld(fp, vs[i], va, vb);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const float ub = a == 0.0f ? va[q] : fmaf(a, vb[q], g * va[q]);
-            acc[q] = fmaf(lam[i], ub, acc[q]);
+            const float v = a == 0.0f ? ua[i][q] : fmaf(a, ub[i][q], g * ua[i][q]);
+            acc[q] = fmaf(lam[i], v, acc[q]);
 #pragma unroll
-            for (int d = 0; d < 2; ++d) J[q][d] = fmaf(gr[i][d], ub, J[q][d]);
+            for (int d = 0; d < 2; ++d) J[q][d] = fmaf(gr[i][d], v, J[q][d]);
         }
     }
     u[0] = acc[0];
