@@ -74,6 +74,10 @@ def parse():
                    help="c5: seed lattice side along x (y is half; default 16384, smaller only for profiling)")
     p.add_argument("--grid", type=int, default=N_GRID,
                    help="velocity grid side (default 128; smaller only for profiling captures)")
+    p.add_argument("--tri-side", type=int, default=TRI_N[0],
+                   help="tri: seed lattice side along x (y is a quarter; default 4096, smaller only for profiling)")
+    p.add_argument("--c4-nz", type=int, default=C4_N[2],
+                   help="c4: seed lattice size along the pipe axis (default 512, smaller only for profiling)")
     return p.parse_args()
 
 
@@ -697,7 +701,8 @@ def c4_arm(args, rank, world, local):
     lcs.lcs_synchronize(ctx)
     t_load = time.perf_counter() - t_load
     t_seed = time.perf_counter()
-    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, C4_N, C4_LO, C4_HI), field)
+    n_lat = (C4_N[0], C4_N[1], args.c4_nz)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(3, n_lat, C4_LO, C4_HI), field)
     lcs.lcs_synchronize(ctx)
     t_seed = time.perf_counter() - t_seed
     N = lcs.lcs_seeds_count(seeds)
@@ -747,7 +752,7 @@ def c4_arm(args, rank, world, local):
         "metric": METRIC, "value": N * args.steps / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": C4_WORKLOAD, "seeds": N, "nodes": int(mesh.xyz.shape[0]),
+        "config": {"workload": C4_WORKLOAD, "lattice": list(n_lat), "seeds": N, "nodes": int(mesh.xyz.shape[0]),
                    "tets": int(mesh.tets.shape[0]), "mesh_build_s": round(t_mesh, 1),
                    "field_load_ms": round(t_load * 1e3, 1), "seed_location_ms": round(t_seed * 1e3, 1),
                    "status": counts, "accepted_steps_per_live_tracer": float(steps[live].mean()),
@@ -857,7 +862,8 @@ def tri_arm(args, rank, world, local):
     lcs.lcs_synchronize(ctx)
     t_load = time.perf_counter() - t_load
     t_seed = time.perf_counter()
-    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, TRI_N, TRI_LO, TRI_HI), field)
+    n_lat = (args.tri_side, args.tri_side // 4)
+    seeds = lcs.lcs_seed_grid(ctx, lcs.seed_desc(2, n_lat, TRI_LO, TRI_HI), field)
     lcs.lcs_synchronize(ctx)
     t_seed = time.perf_counter() - t_seed
     N = lcs.lcs_seeds_count(seeds)
@@ -909,7 +915,7 @@ def tri_arm(args, rank, world, local):
         "metric": METRIC, "value": N * args.steps / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": TRI_WORKLOAD, "seeds": N, "nodes": int(mesh.xyz.shape[0]),
+        "config": {"workload": TRI_WORKLOAD, "lattice": list(n_lat), "seeds": N, "nodes": int(mesh.xyz.shape[0]),
                    "triangles": int(mesh.tets.shape[0]), "storage": args.storage,
                    "mesh_build_s": round(t_mesh, 1), "field_load_ms": round(t_load * 1e3, 1),
                    "seed_location_ms": round(t_seed * 1e3, 1), "status": counts,

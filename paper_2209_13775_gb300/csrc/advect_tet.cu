@@ -282,7 +282,7 @@ struct TriEval {
     __device__ __forceinline__ int eval(const float *x, int k, float a, int *cell, float *u, State &cc) const
     {
         float lam[3];
-        int r = tri_locate_cached(T, x, cell, lam, cc);
+        int r = tri_locate_cached<true>(T, x, cell, lam, cc);   // adaptive steps span many cells
         if (r == TET_INSIDE) tri_interp_cached<ST>(T, *cell, k, lam, T.pairs + (size_t)k * T.fstride, a, u, cc);
         return r;
     }
