@@ -30,7 +30,7 @@
 #define LCS_EP_MINB 4
 #endif
 
-// 48-byte tracer record (three 16-byte loads) moved by the re-bundling scatter
+// 48-byte tracer record (three 16-byte loads) moved by the re-bundling gather
 struct __align__(16) Tracer {
     float x, y, z;          // wrapped into [origin, origin + L) on periodic axes
     int id;                 // seed index
@@ -77,6 +77,21 @@ __device__ __forceinline__ unsigned cell_key(const RectParams &P, const float *x
     return (unsigned)(k >> shift);
 }
 
+// ctr[key] += 1 for every calling lane, one atomic per distinct key among the lanes that arrive
+// together (consecutive records of a re-bundled order mostly share a cell); returns each lane's
+// slot: the counter's old value plus the lane's rank among the lanes with its key
+__device__ __forceinline__ unsigned warp_add_one(unsigned *ctr, unsigned key)
+{
+    const unsigned act = __activemask();
+    const unsigned m = __match_any_sync(act, key);
+    const unsigned lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if ((int)lane == leader) base = atomicAdd(ctr + key, (unsigned)__popc(m));
+    base = __shfl_sync(act, base, leader);
+    return base + (unsigned)__popc(m & ((1u << lane) - 1u));
+}
+
 __global__ void ep_init_kernel(RectParams P, const float *__restrict__ seeds, long long N, Tracer *__restrict__ S,
                                const float *__restrict__ job_tend, int job, int shift, unsigned *__restrict__ keys,
                                unsigned *__restrict__ hist)
@@ -104,7 +119,7 @@ __global__ void ep_init_kernel(RectParams P, const float *__restrict__ seeds, lo
     S[i] = t;
     unsigned k = cell_key(P, x, shift);
     keys[i] = k;
-    atomicAdd(hist + k, 1u);
+    warp_add_one(hist, k);
 }
 
 // ------------------------------------------------------------ counting sort
@@ -193,14 +208,25 @@ __global__ void __launch_bounds__(1024) scan_down_kernel(const unsigned *__restr
     }
 }
 
-// record i to its bucket's next slot; the variational grad F ([9][N] planes) moves with it
-__global__ void ep_scatter_kernel(const Tracer *__restrict__ A, Tracer *__restrict__ B, long long N,
-                                  const unsigned *__restrict__ keys, unsigned *__restrict__ cursor,
-                                  const float *__restrict__ MA, float *__restrict__ MB)
+// the re-bundled order as a permutation: slot p of the new order takes record perm[p] of the old
+__global__ void ep_perm_kernel(long long N, const unsigned *__restrict__ keys, unsigned *__restrict__ cursor,
+                               unsigned *__restrict__ perm)
 {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= N) return;
-    unsigned p = atomicAdd(cursor + keys[i], 1u);
+    perm[warp_add_one(cursor, keys[i])] = (unsigned)i;
+}
+
+// slot p of the new order from record perm[p] of the old: gathered reads, coalesced writes (a
+// scatter writes 48-byte records to scattered slots, which costs more); the variational grad F
+// ([9][N] planes) moves with the records
+__global__ void ep_gather_kernel(const Tracer *__restrict__ A, Tracer *__restrict__ B, long long N,
+                                 const unsigned *__restrict__ perm, const float *__restrict__ MA,
+                                 float *__restrict__ MB)
+{
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const long long i = __ldg(perm + p);
     B[p] = A[i];
     if (MA) {
 #pragma unroll
@@ -634,7 +660,7 @@ __global__ void __launch_bounds__(256, 2) ep_var3_kernel(RectParams P, SliceGeom
     if (keys) {
         unsigned k = cell_key(P, x, shift);
         keys[i] = k;
-        atomicAdd(hist + k, 1u);
+        warp_add_one(hist, k);
     }
 }
 
@@ -701,7 +727,7 @@ __global__ void __launch_bounds__(256, LCS_EP_MINB) ep_advect3_kernel(RectParams
     if (keys) {
         unsigned k = cell_key(P, x, shift);
         keys[i] = k;
-        atomicAdd(hist + k, 1u);
+        warp_add_one(hist, k);
     }
 }
 
@@ -757,7 +783,7 @@ size_t rk4_sorted_scratch_bytes(long long N, const lcs_field *f, int E, bool var
     const long long keys = key_space(f);
     long long nbins = ((keys - 1) >> sort_shift(keys)) + 1;
     long long nb = (nbins + SCAN_TILE - 1) / SCAN_TILE;
-    size_t b = 2 * al256(sizeof(Tracer) * N) + al256(4 * N) + 2 * al256(4 * nbins) + al256(4 * nb);
+    size_t b = 2 * al256(sizeof(Tracer) * N) + 2 * al256(4 * N) + 2 * al256(4 * nbins) + al256(4 * nb);
     b += slice_bytes(slice_geom(f), E);
     if (variational) b += 2 * al256(sizeof(float) * 9 * N);   // grad F planes, ping-pong with the records
     return b;
@@ -772,7 +798,7 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
     const int shift = sort_shift(nkeys);
     const long long nbins = ((nkeys - 1) >> shift) + 1;
     const long long nb = (nbins + SCAN_TILE - 1) / SCAN_TILE;
-    if (nb > 1024 * SCAN_ITEMS) return cudaErrorInvalidValue;
+    if (nb > 1024 * SCAN_ITEMS || N > 0xffffffffLL) return cudaErrorInvalidValue;
     const int E = L.episode_steps > 0 ? L.episode_steps : LCS_EPISODE_STEPS;
     char *p = (char *)L.work;
     Tracer *SA = (Tracer *)p;
@@ -780,6 +806,8 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
     Tracer *SB = (Tracer *)p;
     p += al256(sizeof(Tracer) * N);
     unsigned *keys = (unsigned *)p;
+    p += al256(4 * N);
+    unsigned *perm = (unsigned *)p;
     p += al256(4 * N);
     unsigned *hist = (unsigned *)p;
     p += al256(4 * nbins);
@@ -833,7 +861,8 @@ static cudaError_t episodes(const RectParams &P, const lcs_field *f, const Rk4Ar
             scan_reduce_kernel<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum);
             scan_top_kernel<<<1, 1024, 0, s>>>(bsum, (int)nb);
             scan_down_kernel<<<(unsigned)nb, 1024, 0, s>>>(hist, nbins, bsum, cursor);
-            ep_scatter_kernel<<<grid, bt, 0, s>>>(SA, SB, N, keys, cursor, MA, MB);
+            ep_perm_kernel<<<grid, bt, 0, s>>>(N, keys, cursor, perm);
+            ep_gather_kernel<<<grid, bt, 0, s>>>(SA, SB, N, perm, MA, MB);
             if (!last) cudaMemsetAsync(hist, 0, 4 * nbins, s);
             lcs_tm_end(L.ctx, 1, s);
             lcs_tm_begin(L.ctx, 2, s);
