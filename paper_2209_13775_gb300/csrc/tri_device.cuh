@@ -129,7 +129,7 @@ template <bool LONG_WALKS = false>
 __device__ __forceinline__ int tri_locate_cached(const TriDev &T, const float *x, int *cell, float *lam, TriCache &cc)
 {
     int c = *cell;
-    if (c < 0 || c >= T.ncells) c = 0;
+    if ((unsigned)c >= (unsigned)T.ncells) c = 0;   // one unsigned compare (cell ids fit in an int)
     for (int it = 0; it < T.walk_limit; ++it) {
         int4 nb = make_int4(-1, -1, -1, 0);
         bool have_nb = false;
@@ -207,7 +207,9 @@ struct TriPair<LCS_BF16> {
     }
 };
 
-// u = sum_i lam_i [(1 - a) u_k + a u_{k+1}](vertex i) from the vertices' pairs (u_k, u_{k+1})
+// u = sum_i lam_i [(1 - a) u_k + a u_{k+1}](vertex i) from the vertices' pairs (u_k, u_{k+1}).
+// Every pair holds finite values (a single frame is paired with itself), so a = 0 gives u_k
+// exactly without a select: 0 * u_{k+1} + 1 * u_k.
 __device__ __forceinline__ void tri_blend(const float *lam, const float (*ua)[2], const float (*ub)[2], float a,
                                           float *u)
 {
@@ -217,7 +219,7 @@ __device__ __forceinline__ void tri_blend(const float *lam, const float (*ua)[2]
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int q = 0; q < 2; ++q)
-            acc[q] = fmaf(lam[i], a == 0.0f ? ua[i][q] : fmaf(a, ub[i][q], g * ua[i][q]), acc[q]);
+            acc[q] = fmaf(lam[i], fmaf(a, ub[i][q], g * ua[i][q]), acc[q]);
     u[0] = acc[0];
     u[1] = acc[1];
 }
@@ -274,7 +276,7 @@ __device__ __forceinline__ void tri_interp_grad(const TriDev &T, int c, const fl
     for (int i = 0; i < 3; ++i) {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const float v = a == 0.0f ? ua[i][q] : fmaf(a, ub[i][q], g * ua[i][q]);
+            const float v = fmaf(a, ub[i][q], g * ua[i][q]);
             acc[q] = fmaf(lam[i], v, acc[q]);
 #pragma unroll
             for (int d = 0; d < 2; ++d) J[q][d] = fmaf(gr[i][d], v, J[q][d]);
