@@ -80,6 +80,9 @@ def parse():
                    help="tri: seed lattice side along x (y is a quarter; default 4096, smaller only for profiling)")
     p.add_argument("--c4-nz", type=int, default=C4_N[2],
                    help="c4: seed lattice size along the pipe axis (default 512, smaller only for profiling)")
+    p.add_argument("--mesh-T", type=float, default=None,
+                   help="c4 / tri: integration time (default the workload's T = 1; shorter only for profiling "
+                        "captures, which keeps the seed density and the caches' behaviour)")
     return p.parse_args()
 
 
@@ -724,7 +727,8 @@ def c4_arm(args, rank, world, local):
     t_seed = time.perf_counter() - t_seed
     N = lcs.lcs_seeds_count(seeds)
     fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
-    opts = lcs.advect_opts(lcs.RK45, t0=0.0, T=C4_T, rtol=C4_TOL, atol=C4_TOL, h0=C4_H0)
+    T_run = args.mesh_T if args.mesh_T else C4_T
+    opts = lcs.advect_opts(lcs.RK45, t0=0.0, T=T_run, rtol=C4_TOL, atol=C4_TOL, h0=C4_H0)
     ftle = torch.empty(N, dtype=torch.float32, device="cuda")
     C = torch.empty((N, 6), dtype=torch.float64, device="cuda")
 
@@ -769,7 +773,7 @@ def c4_arm(args, rank, world, local):
         "metric": METRIC, "value": N * args.steps / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": C4_WORKLOAD, "lattice": list(n_lat), "seeds": N, "nodes": int(mesh.xyz.shape[0]),
+        "config": {"workload": C4_WORKLOAD, "lattice": list(n_lat), "T": T_run, "seeds": N, "nodes": int(mesh.xyz.shape[0]),
                    "tets": int(mesh.tets.shape[0]), "mesh_build_s": round(t_mesh, 1),
                    "field_load_ms": round(t_load * 1e3, 1), "seed_location_ms": round(t_seed * 1e3, 1),
                    "status": counts, "accepted_steps_per_live_tracer": float(steps[live].mean()),
@@ -885,7 +889,8 @@ def tri_arm(args, rank, world, local):
     t_seed = time.perf_counter() - t_seed
     N = lcs.lcs_seeds_count(seeds)
     fm = lcs.lcs_flowmap_create(ctx, seeds, 1)
-    opts = lcs.advect_opts(lcs.RK4, t0=0.0, T=TRI_T, dt=TRI_DT)
+    T_run = args.mesh_T if args.mesh_T else TRI_T
+    opts = lcs.advect_opts(lcs.RK4, t0=0.0, T=T_run, dt=TRI_DT)
     ftle = torch.empty(N, dtype=torch.float32, device="cuda")
     C = torch.empty((N, 3), dtype=torch.float64, device="cuda")
 
@@ -916,7 +921,7 @@ def tri_arm(args, rank, world, local):
     lcs.lcs_flowmap_get(ctx, fm, 0, None, status, te)
     counts = {name: int((status == v).sum()) for name, v in
               (("ok", lcs.TRACER_OK), ("left", lcs.TRACER_LEFT), ("outside", lcs.TRACER_OUTSIDE))}
-    nsteps = int(round(TRI_T / TRI_DT))
+    nsteps = int(round(T_run / TRI_DT))
     # steps actually taken: all for OK tracers, up to the exit for LEFT ones
     taken = np.where(status == lcs.TRACER_OK, nsteps,
                      np.where(status == lcs.TRACER_LEFT, np.rint(te / TRI_DT), 0)).astype(np.int64)
@@ -932,7 +937,7 @@ def tri_arm(args, rank, world, local):
         "metric": METRIC, "value": N * args.steps / el, "unit": "seeds/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": TRI_WORKLOAD, "lattice": list(n_lat), "seeds": N, "nodes": int(mesh.xyz.shape[0]),
+        "config": {"workload": TRI_WORKLOAD, "lattice": list(n_lat), "T": T_run, "seeds": N, "nodes": int(mesh.xyz.shape[0]),
                    "triangles": int(mesh.tets.shape[0]), "storage": args.storage,
                    "mesh_build_s": round(t_mesh, 1), "field_load_ms": round(t_load * 1e3, 1),
                    "seed_location_ms": round(t_seed * 1e3, 1), "status": counts,
