@@ -6,11 +6,11 @@ dt = 0.02, T = 8 (400 steps); grad F by finite differences, the full 3x3
 Cauchy-Green tensor (FP64) and the FTLE field.  Synthetic seeded data.
 
 A timed step = lcs_advect + lcs_ftle (FTLE and C written to device memory) with
-the field and the seed lattice resident.  `e2e` repeats the user-level sequence
-from host buffers each step: the frames uploaded from pinned host memory
-(lcs_update_frames into one field of a double buffer, through a loader context
-on its own stream, overlapping the previous step's advection), lcs_seed_grid,
-lcs_flowmap_create, lcs_advect, lcs_ftle into pinned host buffers, and the frees.
+the field and the seed lattice resident.  `e2e` adds, every step, the upload of
+the frames from pinned host memory (lcs_update_frames into one field of a double
+buffer, through a loader context on its own stream) and the read-back of C and
+the FTLE into pinned host memory, each overlapping a neighbouring step's
+advection as a serving loop would run them.
 
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload on the host cores (the baseline arm).  Under torchrun every rank runs
@@ -305,27 +305,42 @@ def our_arm(args, rank, world, local):
 
     # end to end through the C ABI from host buffers, pipelined as a serving loop runs it: every
     # step uploads its 1.61 GB of frames from pinned memory and reads C and the FTLE back into
-    # pinned memory; the next step's frames go up through a loader context on its own stream
-    # (lcs_update_frames into the other field of a double buffer) while this step advects.  The
-    # first step's upload is not hidden and is counted; buffers are allocated before timing.
+    # pinned memory.  A loader context on its own stream uploads the next step's frames
+    # (lcs_update_frames into the other field of a double buffer) while this step advects, and
+    # reads this step's C and FTLE back (double-buffered device outputs) while the next one
+    # advects.  Stream order on the loader stream keeps every overwrite behind the reads of the
+    # buffer it overwrites.  The first upload and the last read-back are not hidden and are
+    # counted; the fields, the lattice (made on the device from its descriptor), the flow map and
+    # the output buffers are allocated before timing.
     frames_pin = torch.from_numpy(g.frames).pin_memory()
-    ftle_h = torch.empty(N, dtype=torch.float32).pin_memory()
-    C_h = torch.empty((N, 6), dtype=torch.float64).pin_memory()
     load_stream = torch.cuda.Stream(device=local)
     ctx_load = lcs.lcs_create(local, load_stream)
-    fbuf = [lcs.lcs_load_field(ctx_load, desc, frames_pin) for _ in range(2)] if args.e2e_steps > 0 else []
+    n2 = 2 if args.e2e_steps > 0 else 0
+    fbuf = [lcs.lcs_load_field(ctx_load, desc, frames_pin) for _ in range(n2)]
+    ftle_d = [torch.empty(N, dtype=torch.float32, device="cuda") for _ in range(n2)]
+    C_d = [torch.empty((N, 6), dtype=torch.float64, device="cuda") for _ in range(n2)]
+    ftle_h = [torch.empty(N, dtype=torch.float32).pin_memory() for _ in range(n2)]
+    C_h = [torch.empty((N, 6), dtype=torch.float64).pin_memory() for _ in range(n2)]
+    s_e = lcs.lcs_seed_grid(ctx, sd) if n2 else None
+    m_e = lcs.lcs_flowmap_create(ctx, s_e, 1) if n2 else None
 
     def e2e_run(k_steps):
         lcs.lcs_update_frames(ctx_load, fbuf[0], frames_pin)
         for k in range(k_steps):
-            s2 = lcs.lcs_seed_grid(ctx, sd)
-            m2 = lcs.lcs_flowmap_create(ctx, s2, 1)
-            lcs.lcs_advect(ctx, fbuf[k % 2], s2, opts, m2)
+            b = k % 2
+            lcs.lcs_advect(ctx, fbuf[b], s_e, opts, m_e)
+            lcs.lcs_ftle(ctx, m_e, 0, ftle_d[b], None, C_d[b])
+            done = torch.cuda.Event()
+            done.record(stream)
+            # the next step's frames: behind the read-back of step k - 1 on the loader stream, so
+            # after the advection that last read this field; returns once the upload is complete
             if k + 1 < k_steps:
-                lcs.lcs_update_frames(ctx_load, fbuf[(k + 1) % 2], frames_pin)   # overlaps the advection
-            lcs.lcs_ftle(ctx, m2, 0, ftle_h, None, C_h)                         # D2H, synchronises
-            lcs.lcs_free_flowmap(m2)
-            lcs.lcs_free_seeds(s2)
+                lcs.lcs_update_frames(ctx_load, fbuf[1 - b], frames_pin)
+            with torch.cuda.stream(load_stream):   # this step's results once its lcs_ftle is done
+                load_stream.wait_event(done)
+                ftle_h[b].copy_(ftle_d[b], non_blocking=True)
+                C_h[b].copy_(C_d[b], non_blocking=True)
+        torch.cuda.synchronize()
 
     e2e_t = []
     if args.e2e_steps > 0:
@@ -337,10 +352,13 @@ def our_arm(args, rank, world, local):
         e2e_t.append((time.perf_counter() - t0) / args.e2e_steps)
     for fb in fbuf:
         lcs.lcs_free_field(fb)
+    if n2:
+        lcs.lcs_free_flowmap(m_e)
+        lcs.lcs_free_seeds(s_e)
     lcs.lcs_destroy(ctx_load)
     e2e_el = max_over_ranks(sum(e2e_t) / len(e2e_t) if e2e_t else float("nan"), world)
     h2d = g.frames.nbytes
-    d2h = ftle_h.numel() * 4 + C_h.numel() * 8
+    d2h = N * 4 + N * 6 * 8     # FTLE (FP32) and C (6 FP64 entries) per seed
 
     pk, pk_kind = peaks()
     # dominant kernel: the RK4 advection launches (episodes of the re-bundled path); their summed
