@@ -21,6 +21,10 @@
  *  - Positions are SoA: x[0..N), y[0..N), z[0..N).  Seed index is x-fastest:
  *    id = i + nx*(j + ny*k).  Batched outputs are job-major.
  *  - A context is not thread-safe; use one per host thread.
+ *  - Handles may be used with any context on the same device.  The library
+ *    orders work only on the calling context's stream: when two contexts touch
+ *    one handle, the caller orders them (events, or a call that synchronises
+ *    its stream, such as lcs_update_frames).
  */
 #ifndef LCS_H
 #define LCS_H
@@ -134,7 +138,11 @@ lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *desc, const float 
 int lcs_field_dim(const lcs_field *field);
 
 /* Replace the frames of a loaded field with new data of the same shape
- * (same conventions and finiteness check as lcs_load_field).               */
+ * (same conventions and finiteness check as lcs_load_field).  Returns once
+ * the new frames are in place (the stream is synchronised), so work queued
+ * afterwards on any stream sees them.  No queued work may still read the
+ * field: to upload while an advection runs, update the other field of a
+ * double buffer, from a second context on its own stream.                  */
 lcs_status lcs_update_frames(lcs_ctx *ctx, lcs_field *field, const float *frames,
                              int frames_on_device);
 
