@@ -12,6 +12,10 @@ buffer, through a loader context on its own stream) and the read-back of C and
 the FTLE into pinned host memory, each overlapping a neighbouring step's
 advection as a serving loop would run them.
 
+The default line also carries `other_configs`: the bench lines of the other
+workloads (c3, c4, tri, c5, next; 3 timed steps each, no CPU baseline), each run
+as a child process after the default workload's measurement.
+
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload on the host cores (the baseline arm).  Under torchrun every rank runs
 its own independent copy of the workload (weak scaling, no data exchange);
@@ -80,6 +84,10 @@ def parse():
                    help="tri: seed lattice side along x (y is a quarter; default 4096, smaller only for profiling)")
     p.add_argument("--c4-nz", type=int, default=C4_N[2],
                    help="c4: seed lattice size along the pipe axis (default 512, smaller only for profiling)")
+    p.add_argument("--no-other-configs", dest="other_configs", action="store_false",
+                   help="c2: skip the other workloads (c3, c4, tri, c5, next) that the default line summarises")
+    p.add_argument("--c3-t0s", type=int, default=32,
+                   help="c3: t0 values per direction (default 32, i.e. 64 jobs; fewer only for profiling)")
     p.add_argument("--mesh-T", type=float, default=None,
                    help="c4 / tri: integration time (default the workload's T = 1; shorter only for profiling "
                         "captures, which keeps the seed density and the caches' behaviour)")
@@ -473,12 +481,46 @@ def our_arm(args, rank, world, local):
     lcs.lcs_free_seeds(seeds)
     lcs.lcs_free_field(field)
     lcs.lcs_destroy(ctx)
+    if rank == 0 and world == 1 and args.other_configs and (args.seeds_side, args.grid) == (N_SIDE, N_GRID):
+        line["other_configs"] = other_configs()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
+
+
+# ------------------------------------------------ the other workloads in the default line
+
+OTHER_CONFIGS = ("c3", "c4", "tri", "c5", "next")
+OTHER_KEYS = ("value", "unit", "ms_per_step", "tracer_steps_per_s", "roofline", "clocks", "phases_ms",
+              "phases_ms_per_step", "surrogate", "passes", "gpu_launches")
+
+
+def other_configs(timeout_s=300):
+    """Each other workload's own bench line (3 timed steps after 3 warm-up steps, no CPU baseline), run
+    as a child process after the default workload's measurement, summarised by its workload and
+    measured keys; a child that fails or runs out of time is recorded as such."""
+    out = {}
+    for cfg in OTHER_CONFIGS:
+        cmd = [sys.executable, os.path.abspath(__file__), "--config", cfg, "--steps", "3", "--warmup", "3",
+               "--no-cpu-baseline"]
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+            lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+            if r.returncode != 0 or not lines:
+                out[cfg] = {"error": "exit %d: %s" % (r.returncode, (r.stderr.strip().splitlines() or [""])[-1][:300])}
+                continue
+            d = json.loads(lines[-1])
+            rec = {"workload": d.get("config", {}).get("workload")}
+            rec.update({k: d[k] for k in OTHER_KEYS if k in d})
+            out[cfg] = rec
+        except subprocess.TimeoutExpired:
+            out[cfg] = {"error": "timed out after %d s" % timeout_s}
+        out[cfg]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 # ------------------------------------------------ batched sliding-window arm
@@ -506,8 +548,9 @@ def c3_arm(args, rank, world, local):
     sd = lcs.seed_desc(2, (2048, 1024), (0.0, 0.0), (2.0, 1.0))
     seeds = lcs.lcs_seed_grid(ctx, sd)
     N = lcs.lcs_seeds_count(seeds)
-    t0s = [0.25 * k for k in range(32)] * 2
-    Ts = [(2.0, 4.0, 8.0)[k % 3] for k in range(32)] + [-(2.0, 4.0, 8.0)[k % 3] for k in range(32)]
+    nt = args.c3_t0s
+    t0s = [0.25 * k for k in range(nt)] * 2
+    Ts = [(2.0, 4.0, 8.0)[k % 3] for k in range(nt)] + [-(2.0, 4.0, 8.0)[k % 3] for k in range(nt)]
     nj = len(t0s)
     tracer_steps = N * sum(int(round(abs(T) / 0.05)) for T in Ts)
     fm = lcs.lcs_flowmap_create(ctx, seeds, nj)
