@@ -89,7 +89,7 @@ struct lcs_field {
     float4 *d_xyz = nullptr;           // [nodes]
     int4 *d_tets = nullptr;            // [ncells]
     int4 *d_nbrs = nullptr;            // [ncells]
-    float4 *d_tetmap = nullptr;        // [ncells][3]: rows of the inverse affine map + v0
+    float4 *d_tetmap = nullptr;        // [ncells][4]: rows of the inverse affine map + v0, then nbrs
     int bin_n[3] = {0, 0, 0};          // bin grid over the nodes' bounding box (meshes)
     float bin_lo[3] = {0, 0, 0}, bin_inv[3] = {0, 0, 0};
     // triangle mesh (d_tets, d_nbrs hold (a, b, c, 0) and (n0, n1, n2, -1))

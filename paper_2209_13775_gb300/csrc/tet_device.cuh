@@ -22,7 +22,8 @@ struct TetDev {
     const float4 *xyz;    // [nnodes]
     const int4 *tets;     // [ncells] node ids
     const int4 *nbrs;     // [ncells] tet across the face opposite vertex j, -1 boundary
-    const float4 *tmap;   // [ncells][3]: row r = (M_r0, M_r1, M_r2, v0_r), lambda_{r+1} = M_r . (x - v0)
+    const float4 *tmap;   // [ncells][4]: row r < 3 = (M_r0, M_r1, M_r2, v0_r), lambda_{r+1} = M_r . (x - v0);
+                          // row 3 = the cell's nbrs entry (int bits), so a walk step is two 32-byte loads
     const int *bstart;    // [nbins + 1] CSR of the tets whose bounding box meets a bin
     const int *blist;     //   (ids increasing within a bin)
     float blo[3], binv[3];
@@ -54,16 +55,40 @@ __device__ __forceinline__ int tet_bin(const TetDev &T, const float *x)
                       T.bn[1] * mesh_bin_axis(x[2], T.blo[2], T.binv[2], T.bn[2]));
 }
 
-// barycentric coordinates of x in tet c (FP32)
-__device__ __forceinline__ void tet_bary(const TetDev &T, int c, const float *x, float *lam)
+// the 64-byte record of tet c: map rows r0..r2 and the neighbours, as two 32-byte loads (lanes
+// gathering 32 bytes each cost the L1 data stage fewer wavefronts per byte than 16-byte gathers)
+__device__ __forceinline__ void tet_record(const TetDev &T, int c, float4 &r0, float4 &r1, float4 &r2, int4 &nb)
 {
-    const float4 r0 = __ldg(T.tmap + 3 * (size_t)c), r1 = __ldg(T.tmap + 3 * (size_t)c + 1),
-                 r2 = __ldg(T.tmap + 3 * (size_t)c + 2);
+    const float4 *p = T.tmap + 4 * (size_t)c;
+    float a[8], b[8];
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a[0]), "=f"(a[1]), "=f"(a[2]), "=f"(a[3]), "=f"(a[4]), "=f"(a[5]), "=f"(a[6]), "=f"(a[7])
+        : "l"(p));
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(b[0]), "=f"(b[1]), "=f"(b[2]), "=f"(b[3]), "=f"(b[4]), "=f"(b[5]), "=f"(b[6]), "=f"(b[7])
+        : "l"(p + 2));
+    r0 = make_float4(a[0], a[1], a[2], a[3]);
+    r1 = make_float4(a[4], a[5], a[6], a[7]);
+    r2 = make_float4(b[0], b[1], b[2], b[3]);
+    nb = make_int4(__float_as_int(b[4]), __float_as_int(b[5]), __float_as_int(b[6]), __float_as_int(b[7]));
+}
+
+// barycentric coordinates of x in the tet with map rows r0..r2 (FP32)
+__device__ __forceinline__ void tet_bary_rows(const float4 &r0, const float4 &r1, const float4 &r2, const float *x,
+                                              float *lam)
+{
     const float dx = x[0] - r0.w, dy = x[1] - r1.w, dz = x[2] - r2.w;
     lam[1] = fmaf(r0.x, dx, fmaf(r0.y, dy, r0.z * dz));
     lam[2] = fmaf(r1.x, dx, fmaf(r1.y, dy, r1.z * dz));
     lam[3] = fmaf(r2.x, dx, fmaf(r2.y, dy, r2.z * dz));
     lam[0] = 1.0f - lam[1] - lam[2] - lam[3];
+}
+
+// barycentric coordinates of x in tet c (FP32)
+__device__ __forceinline__ void tet_bary(const TetDev &T, int c, const float *x, float *lam)
+{
+    const float4 *p = T.tmap + 4 * (size_t)c;
+    tet_bary_rows(__ldg(p), __ldg(p + 1), __ldg(p + 2), x, lam);
 }
 
 // the tets listed for x's bin, in id order: the first whose coordinates all reach -tol
@@ -89,7 +114,10 @@ __device__ __forceinline__ int tet_locate(const TetDev &T, const float *x, int *
     int c = *cell;
     if (c < 0 || c >= T.ncells) c = 0;
     for (int it = 0; it < T.walk_limit; ++it) {
-        tet_bary(T, c, x, lam);
+        float4 r0, r1, r2;
+        int4 nb;
+        tet_record(T, c, r0, r1, r2, nb);
+        tet_bary_rows(r0, r1, r2, x, lam);
         int jm = 0;
         float lm = lam[0];
 #pragma unroll
@@ -102,7 +130,6 @@ __device__ __forceinline__ int tet_locate(const TetDev &T, const float *x, int *
             *cell = c;
             return TET_INSIDE;
         }
-        const int4 nb = __ldg(T.nbrs + c);
         const int n = jm == 0 ? nb.x : jm == 1 ? nb.y : jm == 2 ? nb.z : nb.w;
         if (n < 0) {
             *cell = c;
@@ -204,8 +231,8 @@ __device__ __forceinline__ void tet_interp_grad(const TetDev &T, int c, const fl
 {
     const int4 t = __ldg(T.tets + c);
     const int vs[4] = {t.x, t.y, t.z, t.w};
-    const float4 r0 = __ldg(T.tmap + 3 * (size_t)c), r1 = __ldg(T.tmap + 3 * (size_t)c + 1),
-                 r2 = __ldg(T.tmap + 3 * (size_t)c + 2);
+    const float4 r0 = __ldg(T.tmap + 4 * (size_t)c), r1 = __ldg(T.tmap + 4 * (size_t)c + 1),
+                 r2 = __ldg(T.tmap + 4 * (size_t)c + 2);
     const float gr[4][3] = {{-(r0.x + r1.x + r2.x), -(r0.y + r1.y + r2.y), -(r0.z + r1.z + r2.z)},
                             {r0.x, r0.y, r0.z},
                             {r1.x, r1.y, r1.z},

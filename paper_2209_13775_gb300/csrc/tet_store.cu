@@ -23,9 +23,10 @@ __global__ void tet_xyz_kernel(const float *__restrict__ xyz, long long n, float
     out[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.0f);
 }
 
-// inverse of E = [v1 - v0, v2 - v0, v3 - v0] (columns) in FP64, rounded to FP32 rows
-__global__ void tet_map_kernel(const float4 *__restrict__ xyz, const int4 *__restrict__ tets, long long nc,
-                               float4 *__restrict__ tmap)
+// inverse of E = [v1 - v0, v2 - v0, v3 - v0] (columns) in FP64, rounded to FP32 rows, and the
+// cell's neighbours as the record's fourth row
+__global__ void tet_map_kernel(const float4 *__restrict__ xyz, const int4 *__restrict__ tets,
+                               const int4 *__restrict__ nbrs, long long nc, float4 *__restrict__ tmap)
 {
     long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= nc) return;
@@ -50,7 +51,9 @@ __global__ void tet_map_kernel(const float4 *__restrict__ xyz, const int4 *__res
     m[2][2] = (e[0][0] * e[1][1] - e[0][1] * e[1][0]) * id;
     const float v0[3] = {p0.x, p0.y, p0.z};
     for (int r = 0; r < 3; ++r)
-        tmap[3 * t + r] = make_float4((float)m[r][0], (float)m[r][1], (float)m[r][2], v0[r]);
+        tmap[4 * t + r] = make_float4((float)m[r][0], (float)m[r][1], (float)m[r][2], v0[r]);
+    const int4 nb = nbrs[t];
+    tmap[4 * t + 3] = make_float4(__int_as_float(nb.x), __int_as_float(nb.y), __int_as_float(nb.z), __int_as_float(nb.w));
 }
 
 struct BinGrid {
@@ -442,7 +445,7 @@ cudaError_t tet_build_store(lcs_field *f, const float *xyz_host, const int *tets
     cudaError_t e = cudaMalloc(&f->d_xyz, sizeof(float4) * nn);
     if (e == cudaSuccess) e = cudaMalloc(&f->d_tets, sizeof(int4) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&f->d_nbrs, sizeof(int4) * nc);
-    if (e == cudaSuccess) e = cudaMalloc(&f->d_tetmap, sizeof(float4) * 3 * nc);
+    if (e == cudaSuccess) e = cudaMalloc(&f->d_tetmap, sizeof(float4) * 4 * nc);
     if (e == cudaSuccess) e = cudaMalloc(&f->d_bstart, sizeof(int) * (nbins + 1));
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&dxyz, sizeof(float) * 3 * nn, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&count, sizeof(int) * nbins, s);
@@ -456,7 +459,7 @@ cudaError_t tet_build_store(lcs_field *f, const float *xyz_host, const int *tets
     const unsigned gc = (unsigned)((nc + bt - 1) / bt);
     if (e == cudaSuccess) {
         tet_xyz_kernel<<<(unsigned)((nn + bt - 1) / bt), bt, 0, s>>>(dxyz, nn, f->d_xyz);
-        tet_map_kernel<<<gc, bt, 0, s>>>(f->d_xyz, f->d_tets, nc, f->d_tetmap);
+        tet_map_kernel<<<gc, bt, 0, s>>>(f->d_xyz, f->d_tets, f->d_nbrs, nc, f->d_tetmap);
         tet_bin_count_kernel<<<gc, bt, 0, s>>>(f->d_xyz, f->d_tets, nc, B, count);
         e = cudaGetLastError();
     }
