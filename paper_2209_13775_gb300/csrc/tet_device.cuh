@@ -84,7 +84,8 @@ __device__ __forceinline__ void tet_bary_rows(const float4 &r0, const float4 &r1
     lam[0] = 1.0f - lam[1] - lam[2] - lam[3];
 }
 
-// barycentric coordinates of x in tet c (FP32)
+// barycentric coordinates of x in tet c (FP32).  Plain 16-byte loads: the out-of-line bin scan
+// calls this, and with tet_record's 32-byte loads there the CUDA 13.0 ptxas crashed on this file.
 __device__ __forceinline__ void tet_bary(const TetDev &T, int c, const float *x, float *lam)
 {
     const float4 *p = T.tmap + 4 * (size_t)c;
