@@ -122,9 +122,9 @@ __device__ __forceinline__ void tri_cache_init(TriCache &cc)
 // walks are kept apart: the uncached one serves the seed location and the surrogate gate,
 // which make one walk per tracer and would gain nothing from the cache's registers.
 // LONG_WALKS loads a cell's neighbours together with its map (when the map is not held), so
-// that a walk that goes on waits for one round trip per cell instead of two.  It pays where walks are long (DP5(4) on
-// the stenosis: about 8 cells per stage point, 10% faster) and costs where most walks end in
-// their first cell (RK4 at dt = 0.002: 1.2 cells, 5% slower).
+// that a walk that goes on waits for one round trip per cell instead of two.  It pays where
+// walks are long (DP5(4) on the stenosis: about 8 cells per stage point, 10% faster) and costs
+// where most walks end in their first cell (RK4 at dt = 0.002: 1.2 cells, 5% slower).
 template <bool LONG_WALKS = false>
 __device__ __forceinline__ int tri_locate_cached(const TriDev &T, const float *x, int *cell, float *lam, TriCache &cc)
 {
@@ -143,19 +143,34 @@ __device__ __forceinline__ int tri_locate_cached(const TriDev &T, const float *x
             }
         }
         tri_bary_mv(cc.m, cc.v, x, lam);
+        // the inside test on the smallest coordinate (lam is finite for a finite x) and the face
+        // to cross, the first smallest coordinate: for short walks the face is found only when the
+        // walk goes on (RK4 2.8% faster); long walks find both in one pass (DP5(4) 1.6% faster)
         int jm = 0;
         float lm = lam[0];
-        if (lam[1] < lm) {
-            lm = lam[1];
-            jm = 1;
-        }
-        if (lam[2] < lm) {
-            lm = lam[2];
-            jm = 2;
+        if (LONG_WALKS) {
+            if (lam[1] < lm) {
+                lm = lam[1];
+                jm = 1;
+            }
+            if (lam[2] < lm) {
+                lm = lam[2];
+                jm = 2;
+            }
+        } else {
+            lm = fminf(lam[0], fminf(lam[1], lam[2]));
         }
         if (lm >= -T.tol) {
             *cell = c;
             return TET_INSIDE;
+        }
+        if (!LONG_WALKS) {
+            float lo = lam[0];
+            if (lam[1] < lo) {
+                lo = lam[1];
+                jm = 1;
+            }
+            if (lam[2] < lo) jm = 2;
         }
         if (!have_nb) nb = __ldg(T.nbrs + c);
         const int n = jm == 0 ? nb.x : jm == 1 ? nb.y : nb.z;
