@@ -410,9 +410,9 @@ def our_arm(args, rank, world, local):
         "clocks": clocks,
         "e2e": {"value": world * N / e2e_el if e2e_t else None, "unit": "seeds/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_el * 1e3},
-        # ours per step: schedule, init, finalize, FD/CG/FTLE, and per episode 3 scan + scatter +
-        # slice table + slice fill + advection
-        "gpu_launches": int(round(args.steps * 4 + adv_launches * 7)),
+        # ours per step: schedule, init, finalize, FD/CG/FTLE, and per episode 3 scan + permutation +
+        # gather + slice table + slice fill + advection
+        "gpu_launches": int(round(args.steps * 4 + adv_launches * 8)),
     }
     if args.storage != "f32":
         # reduced-precision storage against FP32 storage on the same lattice (outside the timed region)
