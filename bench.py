@@ -332,8 +332,13 @@ def our_arm(args, rank, world, local):
     s_e = lcs.lcs_seed_grid(ctx, sd) if n2 else None
     m_e = lcs.lcs_flowmap_create(ctx, s_e, 1) if n2 else None
 
+    up_ms = []   # host time of each upload call (it returns once the upload is complete)
+
     def e2e_run(k_steps):
+        up_ms.clear()
+        t = time.perf_counter()
         lcs.lcs_update_frames(ctx_load, fbuf[0], frames_pin)
+        up_ms.append((time.perf_counter() - t) * 1e3)
         for k in range(k_steps):
             b = k % 2
             lcs.lcs_advect(ctx, fbuf[b], s_e, opts, m_e)
@@ -343,7 +348,9 @@ def our_arm(args, rank, world, local):
             # the next step's frames: behind the read-back of step k - 1 on the loader stream, so
             # after the advection that last read this field; returns once the upload is complete
             if k + 1 < k_steps:
+                t = time.perf_counter()
                 lcs.lcs_update_frames(ctx_load, fbuf[1 - b], frames_pin)
+                up_ms.append((time.perf_counter() - t) * 1e3)
             with torch.cuda.stream(load_stream):   # this step's results once its lcs_ftle is done
                 load_stream.wait_event(done)
                 ftle_h[b].copy_(ftle_d[b], non_blocking=True)
@@ -409,7 +416,10 @@ def our_arm(args, rank, world, local):
         "phases_ms_per_step": {k: v[0] / args.steps for k, v in phase.items()},
         "clocks": clocks,
         "e2e": {"value": world * N / e2e_el if e2e_t else None, "unit": "seeds/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_el * 1e3},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_el * 1e3,
+                "upload_call_ms": [round(v, 1) for v in up_ms],
+                "note": "upload_call_ms: host time of each lcs_update_frames of the timed run (the first alone, "
+                        "the others overlapping an advection)"},
         # ours per step: schedule, init, finalize, FD/CG/FTLE, and per episode 3 scan + permutation +
         # gather + slice table + slice fill + advection
         "gpu_launches": int(round(args.steps * 4 + adv_launches * 8)),

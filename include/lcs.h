@@ -129,6 +129,8 @@ typedef struct {
  * in host memory or, if frames_on_device, device memory.  The library
  * converts to desc->storage (FP16/BF16 round to nearest).  The call checks
  * every value for finiteness on the device and synchronises the stream.
+ * Host frames pass through a staging buffer that the context keeps (grown
+ * to the largest upload, freed with the context).
  * Errors: LCS_EINVAL (descriptor, a non-finite velocity or node coordinate,
  * a mesh cell of zero area or volume), LCS_ENOMEM, LCS_ECUDA.               */
 lcs_status lcs_load_field(lcs_ctx *ctx, const lcs_field_desc *desc, const float *frames,

@@ -101,6 +101,8 @@ extern "C" void lcs_destroy(lcs_ctx *ctx)
     cudaSetDevice(ctx->device);
     if (ctx->d_errword) cudaFree(ctx->d_errword);
     if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    if (ctx->d_flag) cudaFree(ctx->d_flag);
     tm_release_all(ctx);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     graph_cache_clear(ctx);
@@ -230,21 +232,26 @@ __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) { retu
 // (k, k+1), node v = (u_k, v_k, u_{k+1}, v_{k+1}).  3D: slab k = interval pair, node v =
 // (u_k, 0, u_{k+1}, 0) so that one load brings both frames of a node (a single frame is
 // paired with itself).
+// Every frame value is read by at least one slab (frame f by slab f, the last one also as the
+// k + 1 side of the last slab), so the pass also flags any non-finite value in *nonfinite.
 template <typename T>
 __global__ void convert_rect_kernel(const float *__restrict__ src, int nframes, int nslabs, long long nodes, int dim,
-                                    int vec, size_t slab_stride, char *__restrict__ dst)
+                                    int vec, size_t slab_stride, char *__restrict__ dst, int *__restrict__ nonfinite)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= (long long)nslabs * nodes) return;
     long long f = idx / nodes, v = idx % nodes;
     T *o = reinterpret_cast<T *>(dst + (size_t)f * slab_stride) + v * vec;
+    bool ok = true;
     if (dim == 2 && vec == 2) {
         const float *s = src + idx * 2;
+        ok = isfinite(s[0]) && isfinite(s[1]);
         o[0] = to_store<T>(s[0]);
         o[1] = to_store<T>(s[1]);
     } else if (dim == 2) {  // triangle meshes: (u_k, v_k, u_{k+1}, v_{k+1}) per node
         long long f1 = f + 1 < nframes ? f + 1 : f;
         const float *a = src + (f * nodes + v) * 2, *b = src + (f1 * nodes + v) * 2;
+        ok = isfinite(a[0]) && isfinite(a[1]) && isfinite(b[0]) && isfinite(b[1]);
         o[0] = to_store<T>(a[0]);
         o[1] = to_store<T>(a[1]);
         o[2] = to_store<T>(b[0]);
@@ -253,16 +260,18 @@ __global__ void convert_rect_kernel(const float *__restrict__ src, int nframes, 
         long long f1 = f + 1 < nframes ? f + 1 : f;
         const float *a = src + (f * nodes + v) * 3, *b = src + (f1 * nodes + v) * 3;
         for (int c = 0; c < 3; ++c) {
+            ok = ok && isfinite(a[c]) && isfinite(b[c]);
             o[c] = to_store<T>(a[c]);
             o[4 + c] = to_store<T>(b[c]);
         }
         o[3] = to_store<T>(0.0f);
         o[7] = to_store<T>(0.0f);
     }
+    if (!ok) atomicOr(nonfinite, 1);
 }
 
 cudaError_t launch_convert_rect(const float *src, int nframes, int nslabs, long long nodes, int dim, int vec,
-                                int storage, size_t slab_stride, void *dst, cudaStream_t s)
+                                int storage, size_t slab_stride, void *dst, int *nonfinite, cudaStream_t s)
 {
     long long total = (long long)nslabs * nodes;
     if (total == 0) return cudaSuccess;
@@ -270,54 +279,48 @@ cudaError_t launch_convert_rect(const float *src, int nframes, int nslabs, long 
     unsigned grid = (unsigned)((total + bt - 1) / bt);
     if (storage == LCS_F32)
         convert_rect_kernel<float>
-            <<<grid, bt, 0, s>>>(src, nframes, nslabs, nodes, dim, vec, slab_stride, (char *)dst);
+            <<<grid, bt, 0, s>>>(src, nframes, nslabs, nodes, dim, vec, slab_stride, (char *)dst, nonfinite);
     else if (storage == LCS_F16)
         convert_rect_kernel<__half>
-            <<<grid, bt, 0, s>>>(src, nframes, nslabs, nodes, dim, vec, slab_stride, (char *)dst);
+            <<<grid, bt, 0, s>>>(src, nframes, nslabs, nodes, dim, vec, slab_stride, (char *)dst, nonfinite);
     else
         convert_rect_kernel<__nv_bfloat16>
-            <<<grid, bt, 0, s>>>(src, nframes, nslabs, nodes, dim, vec, slab_stride, (char *)dst);
+            <<<grid, bt, 0, s>>>(src, nframes, nslabs, nodes, dim, vec, slab_stride, (char *)dst, nonfinite);
     return cudaGetLastError();
-}
-
-// any non-finite value among n floats sets *flag
-__global__ void nonfinite_kernel(const float *__restrict__ p, size_t n, int *__restrict__ flag)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        if (!isfinite(p[i])) {
-            atomicOr(flag, 1);
-            return;
-        }
 }
 
 static lcs_status upload_frames(lcs_ctx *ctx, lcs_field *f, const float *frames, int on_device)
 {
-    size_t n_in = (size_t)f->nframes * f->nodes * f->dim;
+    const size_t n_in = (size_t)f->nframes * f->nodes * f->dim;
     const float *src = frames;
-    float *tmp = nullptr;
+    if (!ctx->d_flag) CUDA_TRY(ctx, cudaMalloc((void **)&ctx->d_flag, sizeof(int)));
     if (!on_device) {
-        CUDA_TRY(ctx, cudaMallocAsync((void **)&tmp, n_in * sizeof(float), ctx->stream));
-        cudaError_t e = cudaMemcpyAsync(tmp, frames, n_in * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(tmp, ctx->stream);
-            return lcs_fail(ctx, LCS_ECUDA, "frame upload: %s", cudaGetErrorString(e));
+        // host frames go through the context's staging buffer, grown when a larger upload comes
+        // (every upload ends with the stream synchronised, so the buffer is free between calls)
+        const size_t bytes = n_in * sizeof(float);
+        if (bytes > ctx->stage_bytes) {
+            if (ctx->d_stage) cudaFree(ctx->d_stage);
+            ctx->d_stage = nullptr;
+            ctx->stage_bytes = 0;
+            cudaError_t e = cudaMalloc((void **)&ctx->d_stage, bytes);
+            if (e != cudaSuccess)
+                return lcs_fail(ctx, e == cudaErrorMemoryAllocation ? LCS_ENOMEM : LCS_ECUDA, "frame staging: %s",
+                                cudaGetErrorString(e));
+            ctx->stage_bytes = bytes;
         }
-        src = tmp;
+        cudaError_t e = cudaMemcpyAsync(ctx->d_stage, frames, bytes, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "frame upload: %s", cudaGetErrorString(e));
+        src = ctx->d_stage;
     }
-    cudaError_t e = launch_convert_rect(src, f->nframes, f->nslabs, f->nodes, f->dim, f->vec, f->storage,
-                                        f->frame_stride, f->d_frames, ctx->stream);
-    // velocity data must be finite (a NaN would spread through every tracer that touches it)
-    int *dflag = nullptr, hflag = 0;
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dflag, sizeof(int), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dflag, 0, sizeof(int), ctx->stream);
-    if (e == cudaSuccess) {
-        nonfinite_kernel<<<(unsigned)std::min<size_t>((n_in + 255) / 256, 4096), 256, 0, ctx->stream>>>(src, n_in, dflag);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    // velocity data must be finite (a NaN would spread through every tracer that touches it): the
+    // conversion flags any non-finite value it reads
+    int hflag = 0;
+    cudaError_t e = cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_convert_rect(src, f->nframes, f->nslabs, f->nodes, f->dim, f->vec, f->storage, f->frame_stride,
+                                f->d_frames, ctx->d_flag, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (dflag) cudaFreeAsync(dflag, ctx->stream);
-    if (tmp) cudaFreeAsync(tmp, ctx->stream);
     if (e != cudaSuccess) return lcs_fail(ctx, LCS_ECUDA, "frame conversion: %s", cudaGetErrorString(e));
     if (hflag) return lcs_fail(ctx, LCS_EINVAL, "frames hold a non-finite velocity value");
     return LCS_OK;

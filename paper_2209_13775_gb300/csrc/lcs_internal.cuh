@@ -38,6 +38,10 @@ struct lcs_ctx {
     // scratch: device memory the library reuses across calls (queue counters)
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    // staging of frames uploaded from host memory (grown as needed) and the finiteness flag
+    float *d_stage = nullptr;
+    size_t stage_bytes = 0;
+    int *d_flag = nullptr;
     // CUDA graphs of lcs_advect calls (opts.use_graph), keyed by handles and options
     struct GraphEntry {
         std::string key;
@@ -330,7 +334,7 @@ cudaError_t launch_seed_grid(int dim, const int n[3], const double lo[3], const 
                              const int periodic[3], long long N, float *out, cudaStream_t s);
 
 cudaError_t launch_convert_rect(const float *src, int nframes, int nslabs, long long nodes, int dim, int vec,
-                                int storage, size_t slab_stride, void *dst, cudaStream_t s);
+                                int storage, size_t slab_stride, void *dst, int *nonfinite, cudaStream_t s);
 
 // ---------------------------------------------------------- device helpers
 
