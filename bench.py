@@ -7,10 +7,10 @@ Cauchy-Green tensor (FP64) and the FTLE field.  Synthetic seeded data.
 
 A timed step = lcs_advect + lcs_ftle (FTLE and C written to device memory) with
 the field and the seed lattice resident.  `e2e` adds, every step, the upload of
-the frames from pinned host memory (lcs_update_frames into one field of a double
-buffer, through a loader context on its own stream) and the read-back of C and
-the FTLE into pinned host memory, each overlapping a neighbouring step's
-advection as a serving loop would run them.
+the frames from pinned host memory (lcs_update_frames into a ring of fields, from
+a loader thread with its own context and stream) and the read-back of C and the
+FTLE into pinned host memory, each overlapping other steps' advection as a
+serving loop would run them.
 
 The default line also carries `other_configs`: the bench lines of the other
 workloads (c3, c4, tri, c5, next; 3 timed steps each, no CPU baseline), each run
@@ -45,6 +45,8 @@ WORKLOAD = ("3D time-modulated ABC flow, periodic 128^3 FP32 velocity grid, 64 f
             "(FP64) and FTLE")
 L = 2 * math.pi
 N_SIDE, N_GRID, N_FRAMES, T_END, DT = 256, 128, 64, 8.0, 0.02
+# fields the end-to-end leg keeps in flight (uploads run up to E2E_FIELDS - 1 steps ahead)
+E2E_FIELDS = 3
 NSTEPS = int(round(T_END / DT))
 # algorithmic FP32 work of one RK4 tracer-step on trilinear, linear-in-time data (the per-unit figure
 # of the measurement plan): per stage evaluation 7 lerps x 3 components x 2 frames = 84, the time
@@ -62,7 +64,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
-    p.add_argument("--e2e-steps", type=int, default=4,
+    p.add_argument("--e2e-steps", type=int, default=6,
                    help="steps of the end-to-end leg from host buffers (0 = none)")
     p.add_argument("--storage-passes", type=int, default=3,
                    help="c2 with f32: steps of the FP32/FP16/BF16 storage passes after the timed region (0 = none)")
@@ -313,53 +315,82 @@ def our_arm(args, rank, world, local):
 
     # end to end through the C ABI from host buffers, pipelined as a serving loop runs it: every
     # step uploads its 1.61 GB of frames from pinned memory and reads C and the FTLE back into
-    # pinned memory.  A loader context on its own stream uploads the next step's frames
-    # (lcs_update_frames into the other field of a double buffer) while this step advects, and
-    # reads this step's C and FTLE back (double-buffered device outputs) while the next one
-    # advects.  Stream order on the loader stream keeps every overwrite behind the reads of the
-    # buffer it overwrites.  The first upload and the last read-back are not hidden and are
-    # counted; the fields, the lattice (made on the device from its descriptor), the flow map and
-    # the output buffers are allocated before timing.
+    # pinned memory.  A loader thread with its own context and stream uploads frames
+    # (lcs_update_frames) into a ring of E2E_FIELDS fields, up to E2E_FIELDS - 1 steps ahead of the
+    # advection, each upload waiting for the step that last read its field; read-backs run on a
+    # third stream behind each step's lcs_ftle (double-buffered device outputs, the next use of a
+    # buffer waiting for its read-back).  The first upload and the last read-back are not hidden and
+    # are counted; the fields, the lattice (made on the device from its descriptor), the flow map
+    # and the output buffers are allocated before timing.
     frames_pin = torch.from_numpy(g.frames).pin_memory()
     load_stream = torch.cuda.Stream(device=local)
+    d2h_stream = torch.cuda.Stream(device=local)
     ctx_load = lcs.lcs_create(local, load_stream)
-    n2 = 2 if args.e2e_steps > 0 else 0
-    fbuf = [lcs.lcs_load_field(ctx_load, desc, frames_pin) for _ in range(n2)]
-    ftle_d = [torch.empty(N, dtype=torch.float32, device="cuda") for _ in range(n2)]
-    C_d = [torch.empty((N, 6), dtype=torch.float64, device="cuda") for _ in range(n2)]
-    ftle_h = [torch.empty(N, dtype=torch.float32).pin_memory() for _ in range(n2)]
-    C_h = [torch.empty((N, 6), dtype=torch.float64).pin_memory() for _ in range(n2)]
-    s_e = lcs.lcs_seed_grid(ctx, sd) if n2 else None
-    m_e = lcs.lcs_flowmap_create(ctx, s_e, 1) if n2 else None
-
-    up_ms = []   # host time of each upload call (it returns once the upload is complete)
+    nf = E2E_FIELDS if args.e2e_steps > 0 else 0
+    fbuf = [lcs.lcs_load_field(ctx_load, desc, frames_pin) for _ in range(nf)]
+    no = 2 if nf else 0
+    ftle_d = [torch.empty(N, dtype=torch.float32, device="cuda") for _ in range(no)]
+    C_d = [torch.empty((N, 6), dtype=torch.float64, device="cuda") for _ in range(no)]
+    ftle_h = [torch.empty(N, dtype=torch.float32).pin_memory() for _ in range(no)]
+    C_h = [torch.empty((N, 6), dtype=torch.float64).pin_memory() for _ in range(no)]
+    s_e = lcs.lcs_seed_grid(ctx, sd) if nf else None
+    m_e = lcs.lcs_flowmap_create(ctx, s_e, 1) if nf else None
+    up_ms = []   # host time of each upload of the timed run (lcs_update_frames returns once it is complete)
 
     def e2e_run(k_steps):
+        ready = [threading.Event() for _ in range(k_steps)]
+        used = [torch.cuda.Event() for _ in range(k_steps)]      # after step k's lcs_ftle
+        used_rec = [threading.Event() for _ in range(k_steps)]   # used[k] has been recorded
+        err = []
         up_ms.clear()
-        t = time.perf_counter()
-        lcs.lcs_update_frames(ctx_load, fbuf[0], frames_pin)
-        up_ms.append((time.perf_counter() - t) * 1e3)
+
+        def loader():
+            try:
+                torch.cuda.set_device(local)
+                for k in range(k_steps):
+                    if k >= nf:   # the field's previous reader, step k - nf, must be done with it
+                        used_rec[k - nf].wait()
+                        used[k - nf].synchronize()
+                    t = time.perf_counter()
+                    lcs.lcs_update_frames(ctx_load, fbuf[k % nf], frames_pin)
+                    up_ms.append(round((time.perf_counter() - t) * 1e3, 1))
+                    ready[k].set()
+            except BaseException as e:   # surfaced by the main thread
+                err.append(e)
+                for r in ready:
+                    r.set()
+
+        th = threading.Thread(target=loader, daemon=True)
+        th.start()
+        copied = [None] * no   # read-back of the step that last wrote each output buffer
         for k in range(k_steps):
-            b = k % 2
-            lcs.lcs_advect(ctx, fbuf[b], s_e, opts, m_e)
+            ready[k].wait()
+            if err:
+                break
+            b = k % no
+            if copied[b] is not None:
+                stream.wait_event(copied[b])
+            lcs.lcs_advect(ctx, fbuf[k % nf], s_e, opts, m_e)
             lcs.lcs_ftle(ctx, m_e, 0, ftle_d[b], None, C_d[b])
-            done = torch.cuda.Event()
-            done.record(stream)
-            # the next step's frames: behind the read-back of step k - 1 on the loader stream, so
-            # after the advection that last read this field; returns once the upload is complete
-            if k + 1 < k_steps:
-                t = time.perf_counter()
-                lcs.lcs_update_frames(ctx_load, fbuf[1 - b], frames_pin)
-                up_ms.append((time.perf_counter() - t) * 1e3)
-            with torch.cuda.stream(load_stream):   # this step's results once its lcs_ftle is done
-                load_stream.wait_event(done)
+            used[k].record(stream)
+            used_rec[k].set()
+            with torch.cuda.stream(d2h_stream):
+                d2h_stream.wait_event(used[k])
                 ftle_h[b].copy_(ftle_d[b], non_blocking=True)
                 C_h[b].copy_(C_d[b], non_blocking=True)
+                copied[b] = torch.cuda.Event()
+                copied[b].record(d2h_stream)
+        if err:   # let the loader see every step as recorded so that it ends
+            for r in used_rec:
+                r.set()
+        th.join()
         torch.cuda.synchronize()
+        if err:
+            raise err[0]
 
     e2e_t = []
     if args.e2e_steps > 0:
-        e2e_run(2)                          # warm-up of the allocator and copy paths
+        e2e_run(3)                          # warm-up of the allocator, copy and thread paths
         barrier()
         t0 = time.perf_counter()
         e2e_run(args.e2e_steps)
@@ -367,7 +398,7 @@ def our_arm(args, rank, world, local):
         e2e_t.append((time.perf_counter() - t0) / args.e2e_steps)
     for fb in fbuf:
         lcs.lcs_free_field(fb)
-    if n2:
+    if nf:
         lcs.lcs_free_flowmap(m_e)
         lcs.lcs_free_seeds(s_e)
     lcs.lcs_destroy(ctx_load)
@@ -417,9 +448,9 @@ def our_arm(args, rank, world, local):
         "clocks": clocks,
         "e2e": {"value": world * N / e2e_el if e2e_t else None, "unit": "seeds/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_el * 1e3,
-                "upload_call_ms": [round(v, 1) for v in up_ms],
-                "note": "upload_call_ms: host time of each lcs_update_frames of the timed run (the first alone, "
-                        "the others overlapping an advection)"},
+                "upload_call_ms": list(up_ms), "fields_in_flight": E2E_FIELDS,
+                "note": "upload_call_ms: host time of each lcs_update_frames of the timed run, issued by a "
+                        "loader thread up to %d steps ahead of the advection" % (E2E_FIELDS - 1)},
         # ours per step: schedule, init, finalize, FD/CG/FTLE, and per episode 3 scan + permutation +
         # gather + slice table + slice fill + advection
         "gpu_launches": int(round(args.steps * 4 + adv_launches * 8)),
