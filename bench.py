@@ -552,15 +552,17 @@ def other_configs(timeout_s=300):
             r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
             lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
             if r.returncode != 0 or not lines:
-                out[cfg] = {"error": "exit %d: %s" % (r.returncode, (r.stderr.strip().splitlines() or [""])[-1][:300])}
-                continue
-            d = json.loads(lines[-1])
-            rec = {"workload": d.get("config", {}).get("workload")}
-            rec.update({k: d[k] for k in OTHER_KEYS if k in d})
-            out[cfg] = rec
+                rec = {"error": "exit %d: %s" % (r.returncode, (r.stderr.strip().splitlines() or [""])[-1][:300])}
+            else:
+                d = json.loads(lines[-1])
+                rec = {"workload": d.get("config", {}).get("workload")}
+                rec.update({k: d[k] for k in OTHER_KEYS if k in d})
         except subprocess.TimeoutExpired:
-            out[cfg] = {"error": "timed out after %d s" % timeout_s}
-        out[cfg]["wall_s"] = round(time.perf_counter() - t0, 1)
+            rec = {"error": "timed out after %d s" % timeout_s}
+        except ValueError as e:   # a line that is not JSON
+            rec = {"error": "unreadable line: %s" % str(e)[:200]}
+        rec["wall_s"] = round(time.perf_counter() - t0, 1)
+        out[cfg] = rec
     return out
 
 
