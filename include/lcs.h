@@ -506,7 +506,7 @@ lcs_status lcs_cg_eigen(lcs_ctx *ctx, const lcs_flowmap *fm, int job, double *ei
  * records per launch).  Phases: */
 enum {
     LCS_PHASE_ADVECT = 0,     /* advection kernels (RK4 step loops)                  */
-    LCS_PHASE_REBUNDLE = 1,   /* re-bundling tracers by cell (scan, permutation, gather) */
+    LCS_PHASE_REBUNDLE = 1,   /* re-bundling by cell (scan, permutation, gather)      */
     LCS_PHASE_SLICES = 2,     /* time slices of the field for an episode              */
     LCS_PHASE_CG = 3          /* finite differences, Cauchy-Green, eigenvalue, FTLE   */
 };
