@@ -9,8 +9,9 @@
 // Tracers of one warp drift apart in a mixing flow, and then the 32 lanes of a warp
 // read unrelated cells: every load splits into many L1 wavefronts.  So the
 // integration runs in episodes of E steps; before each one the tracer records are
-// re-bundled by a counting sort on the x-fastest index of the cell they sit in, and
-// consecutive threads sit in the same rows of cells again.  A tracer's arithmetic
+// re-bundled by a counting sort on the key of the cell they sit in (cells grouped in
+// bricks), the records moved by a gather through the resulting permutation, and
+// consecutive threads sit in the same few cells again.  A tracer's arithmetic
 // does not depend on which thread runs it, so the flow map is bit-identical to the
 // one-pass kernel.
 //
